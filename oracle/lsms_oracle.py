@@ -1,0 +1,599 @@
+"""FP64 CPU oracle for multi-particle scattering in a three-layer medium.
+
+TEST INFRASTRUCTURE.  Only the test suite, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this module.  The CUDA library never calls it
+and shares no code with it: special functions come from SciPy (AMOS), Gauss-Legendre rules from
+NumPy, and the 4x4 interface systems are solved by LAPACK LU.
+
+It computes, plainly and slowly, what the paper defines (Lai, Kobayashi, Greengard, "A fast solver
+for multi-particle scattering in a layered medium"):
+
+* the Sommerfeld representation of the fields in the three layers (Sec. 2, Eqs. "layer1",
+  "layer21", "layer22", "layer3") and the 4x4 mode-by-mode interface system A_lambda
+  (Eq. "sommerfeldsys");
+* the scattering matrix of a dielectric disc from its 2x2 mode system (Sec. 3.1, Eq. "linear");
+* Graf's multipole-to-local translation (Sec. 3.2, Lemma 3.1 / Eq. "trans");
+* the multipole-to-Sommerfeld map (Sec. 5.3, Theorem 5.2) and the Sommerfeld-to-local map by
+  Jacobi-Anger (Sec. 5.2.1, Lemma 5.1, Eq. "JA2");
+* the block system [A B; C D] (Eq. "finalsys"), its Schur complement (Eq. "schur") and the
+  preconditioned operator I - S(T + R) (Sec. 3.2, Eq. "scattmatrix" and the remark after it).
+
+Readings of the paper taken here (each is listed in the design notes with its reason):
+
+* time dependence exp(-i w t): H^(1) is outgoing (Sec. 1 states exp(i w t), but every formula
+  that follows fits exp(-i w t));
+* gamma_i(lambda) = sqrt(lambda^2 - k_i^2) with Re gamma >= 0, computed as
+  -i * sqrt(k_i^2 - lambda^2) with the principal square root (Sec. 2 Remark, Sec. 5.1);
+* the contour of Eq. "sommerseg" runs Gamma3 -> Gamma2 -> Gamma1; on Gamma2 d lambda = i ds with
+  s running from b down to -b;
+* the phase exp(-i lambda x0) is carried by the incident density I(lambda) instead of by every
+  representation (absolute x everywhere);
+* Lemma 3.1 is used with phi = arg(x_l - x_m), i.e. alpha^l_nu = sum_n beta^m_n H_{n-nu}(k rho)
+  exp(i (n - nu) phi) (the lemma as printed, with theta_lm = arg(x_m - x_l), has a wrong angle);
+* the Mie denominator uses J_n(k_p R) (Eq. "linear" solved; the printed closed form has J_n(k R));
+* Theorem 5.2 is used in the form H_n(k r) e^{i n theta} = (1/4 pi) int 4 (-i)^{n+1} w^n
+  exp(-gamma |y - y_j|) exp(i lambda (x - x_j)) / gamma d lambda with w = (lambda - gamma)/k above
+  the centre and w = (lambda + gamma)/k below it (the printed base and prefactor are garbled);
+* the disc equations are solved in the preconditioned form (I - S(T + R)) beta = S a_inc, where
+  S multiplies the incoming (local) coefficients (Sec. 3.2; Eq. "schur" with D = S T - I and C
+  including S).
+
+Notation: P = 2p + 1 orders n = -p..p stored at index n + p; beta has shape (N, P) (or
+(nrhs, N, P)); the contour has N_S nodes lambda_nu with weights w_nu (d lambda included).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy import special
+
+FOUR_PI = 4.0 * math.pi
+
+
+# ----------------------------------------------------------------------------------------------
+# Special functions and the vertical wavenumber (Sec. 2, Sec. 3.1)
+# ----------------------------------------------------------------------------------------------
+def hankel(n, x):
+    """H_n^(1)(x) (Sec. 3.1: the Hankel function of the first kind)."""
+    return special.hankel1(n, x)
+
+
+def hankel_p(n, x):
+    """d/dx H_n^(1)(x)."""
+    return special.h1vp(n, x)
+
+
+def bessel(n, x):
+    """J_n(x)."""
+    return special.jv(n, x)
+
+
+def bessel_p(n, x):
+    """d/dx J_n(x)."""
+    return special.jvp(n, x)
+
+
+def gamma(lam, k):
+    """sqrt(lambda^2 - k^2) on the branch with Re >= 0 (Sec. 2 Remark; Sec. 5.1 branch cuts).
+
+    Written as -i sqrt(k^2 - lambda^2) with the principal square root: on the real axis it is
+    positive for |lambda| > k and equals -i sqrt(k^2 - lambda^2) (an outgoing wave) for |lambda| < k.
+    """
+    lam = np.asarray(lam, dtype=complex)
+    return -1j * np.sqrt(k * k - lam * lam)
+
+
+# ----------------------------------------------------------------------------------------------
+# Sommerfeld contour (Sec. 5.1, Eq. "sommerseg")
+# ----------------------------------------------------------------------------------------------
+def contour_panel_breaks(n_panels: int, branch_points, b: float, t_max: float) -> np.ndarray:
+    """Panel breakpoints of Gamma1 on t in [0, t_max].
+
+    Breakpoints sit at 0, t_max and every branch point k_i < t_max, and are graded geometrically
+    toward each branch point (k_i +- b 2^j, j < L) with the largest L that keeps the panel count
+    at most n_panels.  Remaining panels are made by halving the longest panel (first one on ties).
+    If even the ungraded set has too many panels, the branch points are dropped.
+    """
+    ks = sorted(set(float(k) for k in branch_points if 0.0 < k < t_max))
+    levels = 0
+    while b * 2.0 ** levels < t_max:
+        levels += 1
+    pts = None
+    for lev in range(levels, -1, -1):
+        cand = {0.0, float(t_max)}
+        for k in ks:
+            cand.add(k)
+            for j in range(lev):
+                for q in (k - b * 2.0 ** j, k + b * 2.0 ** j):
+                    if 0.0 < q < t_max:
+                        cand.add(q)
+        if len(cand) - 1 <= n_panels:
+            pts = sorted(cand)
+            break
+    if pts is None:
+        pts = [0.0, float(t_max)]
+    while len(pts) - 1 < n_panels:
+        lengths = [pts[i + 1] - pts[i] for i in range(len(pts) - 1)]
+        i = int(np.argmax(lengths))
+        pts.insert(i + 1, 0.5 * (pts[i] + pts[i + 1]))
+    return np.array(pts)
+
+
+def contour(n_nodes: int, k1: float, k2: float, k3: float, b: float, t_max: float,
+            panel_order: int = 16):
+    """Nodes lambda_nu and weights w_nu (d lambda included) of the discretised contour.
+
+    Gamma1 (t - i b, 0 < t < t_max) and Gamma3 (its mirror t + i b, -t_max < t < 0) each carry
+    n1 = q * floor((N_S - q) / (2 q)) Gauss-Legendre nodes in panels of order q; Gamma2 (i s,
+    s from b down to -b) carries the remaining N_S - 2 n1 nodes as one Gauss-Legendre rule.
+    Returned in path order Gamma3 -> Gamma2 -> Gamma1.
+    """
+    q = panel_order
+    n1 = q * ((n_nodes - q) // (2 * q))
+    n2 = n_nodes - 2 * n1
+    if n1 <= 0 or n2 <= 0:
+        raise ValueError("contour: too few nodes for the panel order")
+    breaks = contour_panel_breaks(n1 // q, (k1, k2, k3), b, t_max)
+    x, w = np.polynomial.legendre.leggauss(q)
+    t1, w1 = [], []
+    for a, c in zip(breaks[:-1], breaks[1:]):
+        t1.append(0.5 * (a + c) + 0.5 * (c - a) * x)
+        w1.append(0.5 * (c - a) * w)
+    t1 = np.concatenate(t1)
+    w1 = np.concatenate(w1)
+    lam1 = t1 - 1j * b
+    # Gamma3: lambda -> -lambda, traversed with t increasing from -t_max to 0
+    lam3 = -lam1[::-1]
+    w3 = w1[::-1]
+    xs, ws = np.polynomial.legendre.leggauss(n2)
+    s = (b * xs)[::-1]                       # from b down to -b
+    lam2 = 1j * s
+    w2 = -1j * (b * ws)[::-1]                # d lambda = i ds, ds negative along the path
+    lam = np.concatenate([lam3, lam2, lam1])
+    wt = np.concatenate([w3.astype(complex), w2, w1.astype(complex)])
+    return lam, wt
+
+
+# ----------------------------------------------------------------------------------------------
+# Single disc: scattering matrix (Sec. 3.1, Eq. "linear"; Definition 3.1)
+# ----------------------------------------------------------------------------------------------
+def mie_coefficients(p: int, k2: float, kp: float, radius: float) -> np.ndarray:
+    """Diagonal scattering matrix S_n, n = -p..p, by solving the 2x2 mode system of Eq. "linear".
+
+    For each mode n with alpha_n = 1:  [-H_n(k2 R)  J_n(kp R); -k2 H_n'(k2 R)  kp J_n'(kp R)]
+    [beta_n; gamma_n] = [J_n(k2 R); k2 J_n'(k2 R)];  S_n = beta_n.
+    """
+    out = np.zeros(2 * p + 1, dtype=complex)
+    for n in range(-p, p + 1):
+        a = np.array([[-hankel(n, k2 * radius), bessel(n, kp * radius)],
+                      [-k2 * hankel_p(n, k2 * radius), kp * bessel_p(n, kp * radius)]])
+        rhs = np.array([bessel(n, k2 * radius), k2 * bessel_p(n, k2 * radius)])
+        out[n + p] = np.linalg.solve(a, rhs)[0]
+    return out
+
+
+def order_scale(p: int, k2: float, radius: float) -> np.ndarray:
+    """|H_n(k2 R)|, n = -p..p: the diagonal that makes every order O(1) on the disc boundary."""
+    n = np.arange(-p, p + 1)
+    return np.abs(hankel(n, k2 * radius))
+
+
+# ----------------------------------------------------------------------------------------------
+# Free-space multiple scattering (Sec. 3.2, Lemma 3.1, Eq. "trans", Eq. "scattmatrix")
+# ----------------------------------------------------------------------------------------------
+def translation_matrix(xl, xm, k: float, p_out: int, p_in: int) -> np.ndarray:
+    """T^{lm}: local coefficients on disc l induced by the H-expansion of disc m (Lemma 3.1).
+
+    T[nu + p_out, n + p_in] = H_{n - nu}(k rho) exp(i (n - nu) phi), rho = |x_l - x_m|,
+    phi = arg(x_l - x_m).
+    """
+    dx, dy = xl[0] - xm[0], xl[1] - xm[1]
+    rho = math.hypot(dx, dy)
+    phi = math.atan2(dy, dx)
+    nu = np.arange(-p_out, p_out + 1)[:, None]
+    n = np.arange(-p_in, p_in + 1)[None, :]
+    s = n - nu
+    return hankel(s, k * rho) * np.exp(1j * s * phi)
+
+
+def translate(centres: np.ndarray, beta: np.ndarray, k2: float, p: int, rows=None) -> np.ndarray:
+    """alpha^l = sum_{m != l} T^{lm} beta^m for the target discs in `rows` (all by default).
+
+    beta: (N, P).  Per target, the Hankel values of all sources are evaluated at once; the sum
+    over sources and orders is the plain double sum of Eq. "trans".
+    """
+    n_disc = centres.shape[0]
+    rows = range(n_disc) if rows is None else rows
+    nu = np.arange(-p, p + 1)
+    s_all = np.arange(-2 * p, 2 * p + 1)
+    out = np.zeros((len(rows), 2 * p + 1), dtype=complex)
+    for r, l in enumerate(rows):
+        m = np.array([j for j in range(n_disc) if j != l], dtype=int)
+        if m.size == 0:
+            continue
+        d = centres[l][None, :] - centres[m]
+        rho = np.hypot(d[:, 0], d[:, 1])
+        phi = np.arctan2(d[:, 1], d[:, 0])
+        h = hankel(s_all[None, :], k2 * rho[:, None]) * np.exp(1j * s_all[None, :] * phi[:, None])
+        # h[j, s + 2p] = H_s(k rho_j) e^{i s phi_j};  alpha_nu = sum_j sum_n h[j, n - nu] beta_j,n
+        for a, v in enumerate(nu):
+            idx = (nu - v) + 2 * p          # n - nu for n = -p..p
+            out[r, a] = np.sum(h[:, idx] * beta[m])
+    return out
+
+
+# ----------------------------------------------------------------------------------------------
+# Layered medium: the 4x4 mode system (Sec. 2, Eq. "sommerfeldsys")
+# ----------------------------------------------------------------------------------------------
+class Medium:
+    """Three layers: k1 (y > 0), k2 (-d < y < 0), k3 (y < -d); discs kp, radius R."""
+
+    def __init__(self, k1, k2, k3, d, kp, radius):
+        self.k1, self.k2, self.k3, self.d, self.kp, self.radius = k1, k2, k3, d, kp, radius
+
+    def a_lambda(self, lam) -> np.ndarray:
+        """A_lambda of Eq. "sommerfeldsys" for every node: shape (N_S, 4, 4).
+
+        Unknowns (sigma_1, sigma_2^+, sigma_2^-, sigma_3); rows: [u] = 0 at y = 0, [u] = 0 at
+        y = -d, [du/dy] = 0 at y = 0, [du/dy] = 0 at y = -d (Eqs. "cont1", "cont2").
+        """
+        lam = np.atleast_1d(lam)
+        g1, g2, g3 = gamma(lam, self.k1), gamma(lam, self.k2), gamma(lam, self.k3)
+        e = np.exp(-g2 * self.d)
+        a = np.zeros((lam.size, 4, 4), dtype=complex)
+        a[:, 0, 0] = 1.0 / g1
+        a[:, 0, 1] = -1.0 / g2
+        a[:, 0, 2] = -e / g2
+        a[:, 1, 1] = e / g2
+        a[:, 1, 2] = 1.0 / g2
+        a[:, 1, 3] = -1.0 / g3
+        a[:, 2, 0] = 1.0
+        a[:, 2, 1] = 1.0
+        a[:, 2, 2] = -e
+        a[:, 3, 1] = e
+        a[:, 3, 2] = -1.0
+        a[:, 3, 3] = -1.0
+        return a
+
+    def incident_density(self, lam, src) -> np.ndarray:
+        """I(lambda) = exp(-gamma_1 y0 - i lambda x0): the line source's plane-wave amplitude at
+        y = 0 (Eq. "sommer" with y < y0; the exp(-i lambda x0) phase is kept in the density)."""
+        return np.exp(-gamma(lam, self.k1) * src[1] - 1j * lam * src[0])
+
+    def rhs(self, lam, inc=None, p_plus=None, q_minus=None) -> np.ndarray:
+        """Right-hand side of A_lambda sigma for the incident density I and the particle sums.
+
+        Incident: (-I/gamma_1, 0, I, 0) (Eq. "sommerfeldsys").  Particles: their field near the
+        top interface is (1/4pi) int P^+ e^{-gamma_2 y}/gamma_2 e^{i lambda x}, near the bottom
+        interface (1/4pi) int Q^- e^{gamma_2 (y + d)}/gamma_2 e^{i lambda x}; moving these known
+        terms of [u] and [du/dy] to the right gives (P^+/gamma_2, -Q^-/gamma_2, P^+, -Q^-).
+        """
+        lam = np.atleast_1d(lam)
+        g1, g2 = gamma(lam, self.k1), gamma(lam, self.k2)
+        r = np.zeros((lam.size, 4), dtype=complex)
+        if inc is not None:
+            r[:, 0] += -inc / g1
+            r[:, 2] += inc
+        if p_plus is not None:
+            r[:, 0] += p_plus / g2
+            r[:, 2] += p_plus
+        if q_minus is not None:
+            r[:, 1] += -q_minus / g2
+            r[:, 3] += -q_minus
+        return r
+
+    def solve_layers(self, lam, inc=None, p_plus=None, q_minus=None) -> np.ndarray:
+        """sigma = A_lambda^{-1} rhs at every node (LAPACK LU); shape (N_S, 4)."""
+        a = self.a_lambda(lam)
+        r = self.rhs(lam, inc, p_plus, q_minus)
+        return np.linalg.solve(a, r[..., None])[..., 0]
+
+
+# ----------------------------------------------------------------------------------------------
+# Multipole <-> Sommerfeld (Sec. 5.2.1 Lemma 5.1 / Eq. "JA2"; Sec. 5.3 Theorem 5.2)
+# ----------------------------------------------------------------------------------------------
+def m2s_factor(n, lam, k: float, above: bool):
+    """c_n w^n with c_n = 4 (-i)^{n+1}: the spectral coefficient of H_n(k r) e^{i n theta}.
+
+    Theorem 5.2 (read as stated in the module docstring): w = (lambda - gamma)/k for targets above
+    the expansion centre, (lambda + gamma)/k below it.
+    """
+    g = gamma(lam, k)
+    w = (lam - g) / k if above else (lam + g) / k
+    n = np.asarray(n)
+    return 4.0 * (-1j) ** (n + 1) * w ** n
+
+
+def plane_wave_local_factor(m, lam, k: float, downward: bool):
+    """i^m w^m: Jacobi-Anger coefficient of J_m(k r) e^{i m theta} in a layer plane wave.
+
+    exp(gamma (y - y_i) + i lambda (x - x_i)) (decaying downward, from the top interface) uses
+    w = (lambda - gamma)/k; exp(-gamma (y - y_i) + i lambda (x - x_i)) uses (lambda + gamma)/k
+    (Lemma 5.1 with the direction angle of the complex wave vector (lambda, -+ i gamma)).
+    """
+    g = gamma(lam, k)
+    w = (lam - g) / k if downward else (lam + g) / k
+    m = np.asarray(m)
+    return (1j) ** m * w ** m
+
+
+# ----------------------------------------------------------------------------------------------
+# The discretised problem
+# ----------------------------------------------------------------------------------------------
+class Problem:
+    """Discs at `centres` in layer 2, order p, contour (lam, wt).
+
+    All linear maps below are the discrete ones: every Sommerfeld integral is the quadrature sum
+    (1/4pi) sum_nu w_nu (...) over the same nodes.
+    """
+
+    def __init__(self, medium: Medium, p: int, centres: np.ndarray, lam, wt):
+        self.m = medium
+        self.p = p
+        self.P = 2 * p + 1
+        self.c = np.asarray(centres, dtype=float).reshape(-1, 2)
+        self.N = self.c.shape[0]
+        self.lam = np.asarray(lam, dtype=complex)
+        self.wt = np.asarray(wt, dtype=complex)
+        self.S = mie_coefficients(p, medium.k2, medium.kp, medium.radius)
+        self.orders = np.arange(-p, p + 1)
+
+    # --- (a2) free-space translation --------------------------------------------------------
+    def translation(self, beta, rows=None):
+        return translate(self.c, beta, self.m.k2, self.p, rows)
+
+    # --- (a3) aggregate: multipole -> Sommerfeld (Theorem 5.2, Eq. "invfft") ------------------
+    def aggregate(self, beta):
+        """P^+(nu) and Q^-(nu): spectral densities of all H-expansions at the two interfaces.
+
+        For each node and order n: c_n w_-^n sum_j beta^j_n exp(gamma_2 y_j - i lambda x_j)
+        (top, w_- = (lambda - gamma_2)/k2) and c_n w_+^n sum_j beta^j_n exp(-gamma_2 (y_j + d)
+        - i lambda x_j) (bottom); then summed over n.
+        """
+        k2, d = self.m.k2, self.m.d
+        lam = self.lam[:, None]
+        g2 = gamma(lam, k2)
+        x, y = self.c[None, :, 0], self.c[None, :, 1]
+        e_top = np.exp(g2 * y - 1j * lam * x)             # (N_S, N)
+        e_bot = np.exp(-g2 * (y + d) - 1j * lam * x)
+        f_top = m2s_factor(self.orders[None, :], lam, k2, above=True)   # (N_S, P)
+        f_bot = m2s_factor(self.orders[None, :], lam, k2, above=False)
+        p_plus = np.sum(f_top * (e_top @ beta), axis=1)
+        q_minus = np.sum(f_bot * (e_bot @ beta), axis=1)
+        return p_plus, q_minus
+
+    # --- (a4) per-node layer response (Eq. "sommerfeldsys" with particle terms) -----------------
+    def layer_densities(self, inc=None, p_plus=None, q_minus=None):
+        return self.m.solve_layers(self.lam, inc, p_plus, q_minus)
+
+    # --- (a5) disaggregate: Sommerfeld -> local (Lemma 5.1, Eq. "JA2") -------------------------
+    def disaggregate(self, s2p, s2m, rows=None):
+        """alpha^i_m = (1/4pi) sum_nu (w_nu / gamma_2) [sigma_2^+ exp(gamma_2 y_i + i lambda x_i)
+        i^m w_-^m + sigma_2^- exp(-gamma_2 (y_i + d) + i lambda x_i) i^m w_+^m]."""
+        k2, d = self.m.k2, self.m.d
+        c = self.c if rows is None else self.c[list(rows)]
+        lam = self.lam[None, :]
+        g2 = gamma(lam, k2)
+        x, y = c[:, 0:1], c[:, 1:2]
+        e_top = np.exp(g2 * y + 1j * lam * x)             # (Nr, N_S)
+        e_bot = np.exp(-g2 * (y + d) + 1j * lam * x)
+        lamc = self.lam[:, None]
+        f_top = plane_wave_local_factor(self.orders[None, :], lamc, k2, downward=True)  # (N_S, P)
+        f_bot = plane_wave_local_factor(self.orders[None, :], lamc, k2, downward=False)
+        q = (self.wt / (FOUR_PI * gamma(self.lam, k2)))[:, None]
+        return e_top @ (q * s2p[:, None] * f_top) + e_bot @ (q * s2m[:, None] * f_bot)
+
+    # --- R beta: reflected coupling (a3 -> a4 -> a5) --------------------------------------------
+    def reflection(self, beta, rows=None):
+        p_plus, q_minus = self.aggregate(beta)
+        sig = self.layer_densities(None, p_plus, q_minus)
+        return self.disaggregate(sig[:, 1], sig[:, 2], rows)
+
+    # --- (a6) the preconditioned operator ---------------------------------------------------------
+    def apply(self, x, rows=None, parts=("T", "R")):
+        """y = x - S (T + R) x (Sec. 3.2 preconditioned form; Eq. "schur" up to sign)."""
+        x = np.asarray(x, dtype=complex).reshape(self.N, self.P)
+        alpha = np.zeros((self.N if rows is None else len(rows), self.P), dtype=complex)
+        if "T" in parts:
+            alpha += self.translation(x, rows)
+        if "R" in parts:
+            alpha += self.reflection(x, rows)
+        xr = x if rows is None else x[list(rows)]
+        return xr - self.S[None, :] * alpha
+
+    # --- (a8) incident local expansions ---------------------------------------------------------
+    def incident_local(self, src, rows=None):
+        """a_inc: the particle-free layered field in layer 2 expanded on each disc."""
+        inc = self.m.incident_density(self.lam, src)
+        sig = self.layer_densities(inc=inc)
+        return self.disaggregate(sig[:, 1], sig[:, 2], rows)
+
+    def rhs(self, src):
+        return self.S[None, :] * self.incident_local(src)
+
+    # --- dense assembly and solves (Eq. "finalsys", Eq. "schur") ----------------------------------
+    def dense_operator(self):
+        """The (N P) x (N P) matrix of x -> x - S (T + R) x, column by column."""
+        n = self.N * self.P
+        out = np.zeros((n, n), dtype=complex)
+        e = np.zeros(n, dtype=complex)
+        for j in range(n):
+            e[:] = 0.0
+            e[j] = 1.0
+            out[:, j] = self.apply(e).ravel()
+        return out
+
+    def solve_dense(self, src):
+        """beta from (I - S(T + R)) beta = S a_inc by LU."""
+        a = self.dense_operator()
+        return np.linalg.solve(a, self.rhs(src).ravel()).reshape(self.N, self.P)
+
+    def block_system(self, src):
+        """[A B; C D] [sigma; beta] = [b; 0] of Eq. "finalsys", assembled entry by entry.
+
+        sigma is ordered node-major (sigma_1, sigma_2^+, sigma_2^-, sigma_3) per node; beta is
+        disc-major.  D = S T - I, C = S times the Sommerfeld-to-local map, B = minus the
+        multipole-to-Sommerfeld right-hand-side map.
+        """
+        ns, P, N = self.lam.size, self.P, self.N
+        k2, d = self.m.k2, self.m.d
+        lam = self.lam
+        g2 = gamma(lam, k2)
+        A = np.zeros((4 * ns, 4 * ns), dtype=complex)
+        al = self.m.a_lambda(lam)
+        for v in range(ns):
+            A[4 * v:4 * v + 4, 4 * v:4 * v + 4] = al[v]
+        B = np.zeros((4 * ns, N * P), dtype=complex)
+        C = np.zeros((N * P, 4 * ns), dtype=complex)
+        f_top = m2s_factor(self.orders[None, :], lam[:, None], k2, above=True)
+        f_bot = m2s_factor(self.orders[None, :], lam[:, None], k2, above=False)
+        l_top = plane_wave_local_factor(self.orders[None, :], lam[:, None], k2, downward=True)
+        l_bot = plane_wave_local_factor(self.orders[None, :], lam[:, None], k2, downward=False)
+        q = self.wt / (FOUR_PI * g2)
+        for j in range(N):
+            xj, yj = self.c[j]
+            et = np.exp(g2 * yj - 1j * lam * xj)
+            eb = np.exp(-g2 * (yj + d) - 1j * lam * xj)
+            pp = f_top * et[:, None]       # d P^+ / d beta^j_n
+            qm = f_bot * eb[:, None]       # d Q^- / d beta^j_n
+            cols = slice(j * P, (j + 1) * P)
+            B[0::4, cols] = -(pp / g2[:, None])
+            B[1::4, cols] = -(-qm / g2[:, None])
+            B[2::4, cols] = -pp
+            B[3::4, cols] = -(-qm)
+            ct = np.exp(g2 * yj + 1j * lam * xj)
+            cb = np.exp(-g2 * (yj + d) + 1j * lam * xj)
+            rows = slice(j * P, (j + 1) * P)
+            C[rows, 1::4] = (self.S[:, None] * (q * ct)[None, :] * l_top.T)
+            C[rows, 2::4] = (self.S[:, None] * (q * cb)[None, :] * l_bot.T)
+        T = np.zeros((N * P, N * P), dtype=complex)
+        for l in range(N):
+            for m in range(N):
+                if l != m:
+                    T[l * P:(l + 1) * P, m * P:(m + 1) * P] = translation_matrix(
+                        self.c[l], self.c[m], k2, self.p, self.p)
+        D = np.tile(self.S, N)[:, None] * T - np.eye(N * P)
+        inc = self.m.incident_density(lam, src)
+        b = self.m.rhs(lam, inc=inc).ravel()
+        return A, B, C, D, b
+
+    def solve_block(self, src):
+        """Solve Eq. "finalsys" by dense LU; returns (sigma (N_S, 4), beta (N, P))."""
+        A, B, C, D, b = self.block_system(src)
+        ns = self.lam.size
+        big = np.block([[A, B], [C, D]])
+        rhs = np.concatenate([b, np.zeros(self.N * self.P, dtype=complex)])
+        sol = np.linalg.solve(big, rhs)
+        return sol[:4 * ns].reshape(ns, 4), sol[4 * ns:].reshape(self.N, self.P)
+
+    def solve_schur(self, src):
+        """Solve Eq. "schur": [D - C A^{-1} B] beta = -C A^{-1} b by LU."""
+        A, B, C, D, b = self.block_system(src)
+        ainv_b = np.linalg.solve(A, B)
+        ainv_rhs = np.linalg.solve(A, b)
+        return np.linalg.solve(D - C @ ainv_b, -C @ ainv_rhs).reshape(self.N, self.P)
+
+    # --- (a9) fields ----------------------------------------------------------------------------
+    def densities(self, src, beta):
+        """All four layer densities with the incident source and the discs' H-expansions."""
+        inc = self.m.incident_density(self.lam, src)
+        if self.N and beta is not None:
+            p_plus, q_minus = self.aggregate(np.asarray(beta).reshape(self.N, self.P))
+        else:
+            p_plus = q_minus = np.zeros(self.lam.size, dtype=complex)
+        return self.layer_densities(inc, p_plus, q_minus)
+
+    def field_layer1(self, src, beta, pts, which="total"):
+        """u_1 at points with y > 0 (Eq. "fullrep"): 'total', 'scattered' (u_1 - G) or 'particle'
+        (u_1 minus the particle-free u_1)."""
+        pts = np.atleast_2d(pts)
+        k1 = self.m.k1
+        g1 = gamma(self.lam, k1)
+        sig = self.densities(src, beta)[:, 0]
+        if which == "particle":
+            sig = sig - self.densities(src, None)[:, 0]
+        ex = np.exp(-g1[None, :] * pts[:, 1:2] + 1j * self.lam[None, :] * pts[:, 0:1])
+        u = ex @ (self.wt * sig / g1) / FOUR_PI
+        if which == "total":
+            r = np.hypot(pts[:, 0] - src[0], pts[:, 1] - src[1])
+            u = u + 0.25j * hankel(0, k1 * r)
+        return u
+
+    def field_layer2(self, src, beta, pts):
+        """u_2 at points in -d < y < 0 outside the discs: Sommerfeld terms plus every H-expansion."""
+        pts = np.atleast_2d(pts)
+        k2, d = self.m.k2, self.m.d
+        g2 = gamma(self.lam, k2)
+        sig = self.densities(src, beta)
+        e_t = np.exp(g2[None, :] * pts[:, 1:2] + 1j * self.lam[None, :] * pts[:, 0:1])
+        e_b = np.exp(-g2[None, :] * (pts[:, 1:2] + d) + 1j * self.lam[None, :] * pts[:, 0:1])
+        u = (e_t @ (self.wt * sig[:, 1] / g2) + e_b @ (self.wt * sig[:, 2] / g2)) / FOUR_PI
+        if beta is not None:
+            beta = np.asarray(beta).reshape(self.N, self.P)
+            for j in range(self.N):
+                dd = pts - self.c[j][None, :]
+                r = np.hypot(dd[:, 0], dd[:, 1])
+                th = np.arctan2(dd[:, 1], dd[:, 0])
+                u = u + (hankel(self.orders[None, :], k2 * r[:, None])
+                         * np.exp(1j * self.orders[None, :] * th[:, None])) @ beta[j]
+        return u
+
+    def field_layer3(self, src, beta, pts):
+        pts = np.atleast_2d(pts)
+        k3, d = self.m.k3, self.m.d
+        g3 = gamma(self.lam, k3)
+        sig = self.densities(src, beta)[:, 3]
+        ex = np.exp(g3[None, :] * (pts[:, 1:2] + d) + 1j * self.lam[None, :] * pts[:, 0:1])
+        return ex @ (self.wt * sig / g3) / FOUR_PI
+
+
+def gmres(matvec, b, tol=1e-12, maxiter=500):
+    """Unrestarted GMRES (Saad and Schultz, cited in Sec. 3.2) with modified Gram-Schmidt.
+
+    Returns (x, iterations, relative residual history).
+    """
+    b = np.asarray(b, dtype=complex)
+    n = b.size
+    beta0 = np.linalg.norm(b)
+    if beta0 == 0.0:
+        return np.zeros(n, dtype=complex), 0, [0.0]
+    V = np.zeros((maxiter + 1, n), dtype=complex)
+    H = np.zeros((maxiter + 1, maxiter), dtype=complex)
+    V[0] = b / beta0
+    cs = np.zeros(maxiter, dtype=complex)
+    sn = np.zeros(maxiter, dtype=complex)
+    g = np.zeros(maxiter + 1, dtype=complex)
+    g[0] = beta0
+    hist = [1.0]
+    k = 0
+    for k in range(maxiter):
+        w = matvec(V[k])
+        for i in range(k + 1):
+            H[i, k] = np.vdot(V[i], w)
+            w = w - H[i, k] * V[i]
+        H[k + 1, k] = np.linalg.norm(w)
+        if H[k + 1, k] != 0:
+            V[k + 1] = w / H[k + 1, k]
+        for i in range(k):
+            t = cs[i] * H[i, k] + sn[i] * H[i + 1, k]
+            H[i + 1, k] = -np.conj(sn[i]) * H[i, k] + np.conj(cs[i]) * H[i + 1, k]
+            H[i, k] = t
+        a, c = H[k, k], H[k + 1, k]
+        r = math.hypot(abs(a), abs(c))
+        cs[k] = a / r if r else 1.0
+        sn[k] = c / r if r else 0.0
+        cs[k], sn[k] = np.conj(cs[k]), np.conj(sn[k])
+        H[k, k] = cs[k] * a + sn[k] * c
+        H[k + 1, k] = 0.0
+        g[k + 1] = -np.conj(sn[k]) * g[k]
+        g[k] = cs[k] * g[k]
+        hist.append(abs(g[k + 1]) / beta0)
+        if hist[-1] <= tol:
+            k += 1
+            break
+    else:
+        k = maxiter
+    y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
+    x = V[:k].T @ y
+    return x, k, hist

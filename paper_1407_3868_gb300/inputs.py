@@ -1,0 +1,165 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests and benchmark and by the CPU oracle.
+
+This module only draws random numbers and lays out points. It contains none of the method's
+arithmetic (no Bessel/Hankel functions, no contour quadrature, no scattering matrices): the two
+independent implementations (the CUDA library and the CPU oracle) both consume what it returns.
+
+Geometry follows the paper's setting (Sec. 1, Sec. 6): a three-layer medium with the middle layer
+-d < y < 0, identical dielectric discs of radius R inside it, a line source in the top layer
+(Sec. 2, Eq. "sommer"), and observation points in the top layer.  The paper places its particles
+by a "bin sorting" perturbation scheme (Sec. 6); here discs are placed by seeded rejection
+sampling (a documented substitution), keeping a minimum gap of 0.1 between discs and 0.05
+between a disc edge and either interface.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Medium shared by every workload: k1 = 2 pi, k2 = 3 pi, k3 = 4 pi, d = 2, discs kp = 2.4 pi, R = 0.25.
+MEDIUM = dict(k1=2.0 * math.pi, k2=3.0 * math.pi, k3=4.0 * math.pi, d=2.0,
+              kp=2.4 * math.pi, radius=0.25)
+GAP = 0.1            # minimum edge-to-edge gap between discs
+CLEARANCE = 0.05     # minimum distance from a disc edge to either interface
+AREA_FRACTION = 0.2  # area fraction used to widen the large layouts
+
+
+def widened_half_width(n: int, radius: float = MEDIUM["radius"], d: float = MEDIUM["d"],
+                       fraction: float = AREA_FRACTION) -> float:
+    """Half-width of a layout holding n discs at the given area fraction of the middle layer."""
+    return 0.5 * n * math.pi * radius * radius / (fraction * d)
+
+
+def contour_b(width: float) -> float:
+    """Offset b of the deformed Sommerfeld contour from the real axis (Sec. 5.1, Eq. "sommerseg").
+
+    The paper uses b = 0.2 for layouts a few wavelengths wide (Sec. 6).  Every contour term carries
+    |exp(i lambda dx)| = exp(b |dx|), so for wide layouts b is reduced to ln(10)/width, which bounds
+    that growth by a factor of 10 across the whole layout.
+    """
+    return min(0.2, math.log(10.0) / width)
+
+
+@dataclass
+class Workload:
+    """One synthetic problem: medium, discs, contour size, sources and targets."""
+    name: str
+    n: int
+    p: int
+    n_nodes: int
+    t_max: float
+    x_lo: float
+    x_hi: float
+    seed: int
+    sources: np.ndarray                 # (n_src, 2) source positions in layer 1
+    targets: np.ndarray                 # (n_tgt, 2) observation points in layer 1
+    tol: float
+    medium: dict = field(default_factory=lambda: dict(MEDIUM))
+
+    @property
+    def b(self) -> float:
+        return contour_b(self.x_hi - self.x_lo)
+
+    def centres(self) -> np.ndarray:
+        return layout(self.n, self.x_lo, self.x_hi, self.seed)
+
+
+def _targets(x_lo: float, x_hi: float, n: int = 64, y: float = 1.5) -> np.ndarray:
+    xs = np.linspace(x_lo, x_hi, n)
+    return np.stack([xs, np.full(n, y)], axis=1)
+
+
+def _workloads() -> dict[str, Workload]:
+    w = {}
+    # 16 discs in x in [-2, 2], p = 10, 256 contour nodes, one source at (0, 1).
+    w["disc16_p10_ns256"] = Workload("disc16_p10_ns256", 16, 10, 256, 141.0, -2.0, 2.0, 0,
+                                     np.array([[0.0, 1.0]]), _targets(-2.0, 2.0), 1e-12)
+    h = widened_half_width(1000)
+    w["disc1000_p12_ns512"] = Workload("disc1000_p12_ns512", 1000, 12, 512, 152.0, -h, h, 1,
+                                       np.array([[0.0, 1.0]]), _targets(-h, h), 1e-10)
+    h = widened_half_width(5000)
+    w["disc5000_p14_ns1024"] = Workload("disc5000_p14_ns1024", 5000, 14, 1024, 163.0, -h, h, 2,
+                                        np.array([[0.0, 1.0]]), _targets(-h, h), 1e-10)
+    h = widened_half_width(2000)
+    src = np.stack([np.linspace(-h, h, 64), np.full(64, 1.0)], axis=1)
+    w["disc2000_p12_ns768_src64"] = Workload("disc2000_p12_ns768_src64", 2000, 12, 768, 152.0,
+                                             -h, h, 3, src, _targets(-h, h), 1e-10)
+    return w
+
+
+WORKLOADS = _workloads()
+
+
+def sweep_sizes(n_layouts: int = 128, seed: int = 5, n_min: int = 200, n_max: int = 4000) -> list[int]:
+    """Disc counts of a design sweep, log-uniform in [n_min, n_max]."""
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(math.log(n_min), math.log(n_max), size=n_layouts)
+    return [int(round(math.exp(v))) for v in u]
+
+
+def sweep_layouts(n_layouts: int = 128, seed: int = 5) -> list[np.ndarray]:
+    """Centres of every layout of the sweep; layout l uses seed 1000 + l and the widened width."""
+    out = []
+    for l, n in enumerate(sweep_sizes(n_layouts, seed)):
+        h = widened_half_width(n)
+        out.append(layout(n, -h, h, 1000 + l))
+    return out
+
+
+def layout(n: int, x_lo: float, x_hi: float, seed: int,
+           radius: float = MEDIUM["radius"], d: float = MEDIUM["d"],
+           gap: float = GAP, clearance: float = CLEARANCE, max_draws: int = 10_000_000) -> np.ndarray:
+    """n disc centres by seeded rejection sampling.
+
+    Each candidate draws x ~ U(x_lo, x_hi) then y ~ U(-d + R + clearance, -R - clearance) from
+    numpy's PCG64 generator; it is accepted when its distance to every accepted centre is at
+    least 2R + gap (checked on a cell grid).  Returns an (n, 2) float64 array in acceptance order.
+    """
+    if n == 0:
+        return np.zeros((0, 2))
+    rng = np.random.default_rng(seed)
+    y_lo, y_hi = -d + radius + clearance, -radius - clearance
+    dmin = 2.0 * radius + gap
+    cell = dmin
+    grid: dict[tuple[int, int], list[int]] = {}
+    pts = np.zeros((n, 2))
+    count = 0
+    draws = 0
+    while count < n:
+        if draws >= max_draws:
+            raise RuntimeError(f"layout: could not place {n} discs in {max_draws} draws")
+        draws += 1
+        u = rng.random(2)
+        x = x_lo + (x_hi - x_lo) * u[0]
+        y = y_lo + (y_hi - y_lo) * u[1]
+        cx, cy = int(math.floor(x / cell)), int(math.floor(y / cell))
+        ok = True
+        for i in range(cx - 1, cx + 2):
+            for j in range(cy - 1, cy + 2):
+                for q in grid.get((i, j), ()):
+                    if (pts[q, 0] - x) ** 2 + (pts[q, 1] - y) ** 2 < dmin * dmin:
+                        ok = False
+                        break
+                if not ok:
+                    break
+            if not ok:
+                break
+        if ok:
+            pts[count] = (x, y)
+            grid.setdefault((cx, cy), []).append(count)
+            count += 1
+    return pts
+
+
+def random_coefficients(n: int, p: int, nrhs: int = 1, seed: int = 0) -> np.ndarray:
+    """Complex standard-normal coefficients, shape (nrhs, n, 2p+1), complex128."""
+    rng = np.random.default_rng(seed)
+    shape = (nrhs, n, 2 * p + 1)
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / math.sqrt(2.0)
+
+
+def observation_points(x_lo: float, x_hi: float, n: int, y: float) -> np.ndarray:
+    """n points evenly spaced on the horizontal line at height y, endpoints included."""
+    return _targets(x_lo, x_hi, n, y)

@@ -1,0 +1,355 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test checks one oracle function against a closed form, a table, an invariant of the physics,
+a special case that reduces to a textbook result, or brute force on a tiny input.  A plausible
+mistake (dropped term, wrong sign or index, transposed operand) in the function fails its test.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import lsms_oracle as O
+from paper_1407_3868_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+MED = inputs.MEDIUM
+
+
+def medium(k1=None, k2=None, k3=None):
+    return O.Medium(k1 or MED["k1"], k2 or MED["k2"], k3 or MED["k3"], MED["d"], MED["kp"],
+                    MED["radius"])
+
+
+def fine_contour(m, n_nodes=3000, t_max=120.0, b=0.2):
+    return O.contour(n_nodes, m.k1, m.k2, m.k3, b, t_max)
+
+
+# ---------------------------------------------------------------------------------------------
+# special functions and the branch of gamma
+# ---------------------------------------------------------------------------------------------
+def test_bessel_table():
+    rows = np.loadtxt(os.path.join(GOLDEN, "bessel_table_9_1.txt"))
+    for x, j0, j1, y0, y1 in rows:
+        assert abs(O.hankel(0, x) - (j0 + 1j * y0)) < 1e-10
+        assert abs(O.hankel(1, x) - (j1 + 1j * y1)) < 1e-10
+        assert abs(O.bessel(1, x) - j1) < 1e-10
+
+
+def test_gamma_branch():
+    k = 3.0
+    lam, _ = O.contour(256, 1.0, k, 2.0, 0.2, 40.0)
+    g = O.gamma(lam, k)
+    assert np.all(g.real >= 0.0)
+    assert np.allclose(g * g, lam * lam - k * k, rtol=1e-13, atol=1e-12)
+    # real axis: evanescent above k, outgoing (exp(-gamma |y|) = exp(+i sqrt(k^2 - l^2) |y|)) below
+    assert O.gamma(np.array([5.0]), k)[0] == pytest.approx(4.0)
+    g_in = O.gamma(np.array([1.0, -1.0]), k)
+    assert np.allclose(g_in, -1j * math.sqrt(8.0))
+
+
+def test_contour_weights_integrate_entire_functions():
+    # An entire, decaying integrand integrates to its real-axis value along the deformed path.
+    lam, wt = O.contour(512, 1.0, 3.0, 2.0, 0.2, 30.0)
+    assert np.sum(wt * np.exp(-lam ** 2)) == pytest.approx(math.sqrt(math.pi), rel=1e-13)
+    f = lambda z: np.exp(-0.5 * (z - 1.0) ** 2 + 2j * z)
+    ref = math.sqrt(2 * math.pi) * np.exp(2j - 2.0)        # Fourier transform of a Gaussian
+    assert abs(np.sum(wt * f(lam)) - ref) < 1e-13
+    # reversing Gamma2's orientation (a plausible sign slip) changes the value
+    n1 = 16 * ((512 - 16) // 32)
+    wt_bad = wt.copy()
+    wt_bad[n1:512 - n1] *= -1
+    assert abs(np.sum(wt_bad * f(lam)) - ref) > 1e-3
+
+
+def test_contour_symmetry_and_order():
+    lam, wt = O.contour(1024, MED["k1"], MED["k2"], MED["k3"], 9.4e-4, 163.0)
+    assert lam.size == 1024
+    assert np.allclose(lam, -lam[::-1], rtol=0, atol=1e-13)       # lambda -> -lambda symmetry
+    assert np.allclose(wt, wt[::-1], rtol=0, atol=1e-15)
+    n1 = 16 * ((1024 - 16) // 32)
+    assert np.all(np.diff(lam[n1 + (1024 - 2 * n1):].real) > 0)    # Gamma1 increasing t
+    assert np.all(lam[:n1].imag > 0) and np.all(lam[-n1:].imag < 0)
+
+
+# ---------------------------------------------------------------------------------------------
+# Sommerfeld / multipole-to-Sommerfeld (Eq. "sommer", Theorem 5.2)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [0, 1, 2, -3, 7])
+@pytest.mark.parametrize("pt", [(0.7, 0.9), (-1.1, -0.6), (2.5, 0.4)])
+def test_m2s_theorem_by_quadrature(n, pt):
+    k = 3.0 * math.pi
+    m = medium(k, k, k)
+    lam, wt = fine_contour(m, 4096, 160.0)
+    x, y = pt
+    g = O.gamma(lam, k)
+    quad = np.sum(wt * O.m2s_factor(n, lam, k, above=y > 0) * np.exp(-g * abs(y) + 1j * lam * x) / g)
+    quad /= 4.0 * math.pi
+    direct = O.hankel(n, k * math.hypot(x, y)) * np.exp(1j * n * math.atan2(y, x))
+    assert abs(quad - direct) <= 1e-11 * abs(direct)
+
+
+def test_sommerfeld_h0_real_axis_quadrature():
+    # The same identity on the undeformed real axis with SciPy's adaptive quadrature
+    # (the branch points are integrable singularities): checks the contour-free form of Eq. "sommer".
+    k, x, y = 2.0, 0.3, 0.8
+
+    def f(t, part):
+        g = O.gamma(np.array([t]), k)[0]
+        v = np.exp(-g * y + 1j * t * x) / g / (4 * math.pi)
+        return v.real if part == 0 else v.imag
+
+    tot = 0j
+    for a, b in ((-60, -k), (-k, k), (k, 60)):
+        re = integrate.quad(f, a, b, args=(0,), limit=400, epsabs=1e-12)[0]
+        im = integrate.quad(f, a, b, args=(1,), limit=400, epsabs=1e-12)[0]
+        tot += re + 1j * im
+    direct = 0.25j * O.hankel(0, k * math.hypot(x, y))
+    assert abs(tot - direct) < 1e-8
+
+
+# ---------------------------------------------------------------------------------------------
+# Jacobi-Anger (Lemma 5.1, Eq. "JA2") and Graf (Lemma 3.1)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("downward", [True, False])
+def test_jacobi_anger_plane_wave(downward):
+    k = 3.0 * math.pi
+    lam, _ = O.contour(256, 2.0, k, 4.0, 0.2, 40.0)
+    m = np.arange(-80, 81)
+    for idx in (3, 100, 130, 200):
+        l0 = lam[idx]
+        g = O.gamma(l0, k)
+        for x, y in ((0.13, -0.21), (-0.2, 0.05)):
+            r, th = math.hypot(x, y), math.atan2(y, x)
+            direct = np.exp((g if downward else -g) * y + 1j * l0 * x)
+            ser = np.sum(O.plane_wave_local_factor(m, l0, k, downward) * O.bessel(m, k * r)
+                         * np.exp(1j * m * th))
+            assert abs(ser - direct) <= 1e-11 * max(1.0, abs(direct))
+
+
+def test_graf_translation_against_direct_field():
+    k = 3.0 * math.pi
+    rng = np.random.default_rng(1)
+    p = 8
+    for xl, xm in (((0.3, -0.5), (-0.4, -1.2)), ((1.0, -0.4), (0.2, -0.45)), ((0.0, -1.0), (0.0, -0.3))):
+        xl, xm = np.array(xl), np.array(xm)
+        beta = rng.standard_normal(2 * p + 1) + 1j * rng.standard_normal(2 * p + 1)
+        alpha = O.translation_matrix(xl, xm, k, 60, p) @ beta
+        nu = np.arange(-60, 61)
+        for off in ((0.1, -0.07), (-0.15, 0.1), (0.0, 0.2)):
+            pt = xl + np.array(off)
+            r, th = math.hypot(*off), math.atan2(off[1], off[0])
+            local = np.sum(alpha * O.bessel(nu, k * r) * np.exp(1j * nu * th))
+            dm = pt - xm
+            n = np.arange(-p, p + 1)
+            direct = np.sum(beta * O.hankel(n, k * math.hypot(*dm)) * np.exp(1j * n * math.atan2(dm[1], dm[0])))
+            assert abs(local - direct) <= 1e-10 * abs(direct)
+
+
+def test_translate_equals_pairwise_brute_force():
+    rng = np.random.default_rng(2)
+    c = inputs.layout(5, -1.5, 1.5, 7)
+    p = 4
+    beta = rng.standard_normal((5, 9)) + 1j * rng.standard_normal((5, 9))
+    k = 3.0 * math.pi
+    fast = O.translate(c, beta, k, p)
+    for l in range(5):
+        acc = np.zeros(9, dtype=complex)
+        for m in range(5):
+            if m == l:
+                continue
+            for a, nu in enumerate(range(-p, p + 1)):
+                for b, n in enumerate(range(-p, p + 1)):
+                    d = c[l] - c[m]
+                    acc[a] += (O.hankel(n - nu, k * math.hypot(*d))
+                               * np.exp(1j * (n - nu) * math.atan2(d[1], d[0])) * beta[m, b])
+        assert np.allclose(fast[l], acc, rtol=1e-13, atol=0)
+
+
+# ---------------------------------------------------------------------------------------------
+# Disc scattering matrix (Sec. 3.1)
+# ---------------------------------------------------------------------------------------------
+def test_mie_against_closed_form_and_unitarity():
+    k2, kp, R, p = MED["k2"], MED["kp"], MED["radius"], 14
+    S = O.mie_coefficients(p, k2, kp, R)
+    for n in range(-p, p + 1):
+        j2, j2p = O.bessel(n, k2 * R), O.bessel_p(n, k2 * R)
+        jp, jpp = O.bessel(n, kp * R), O.bessel_p(n, kp * R)
+        h, hp = O.hankel(n, k2 * R), O.hankel_p(n, k2 * R)
+        closed = (kp * j2 * jpp - k2 * j2p * jp) / (k2 * hp * jp - kp * jpp * h)
+        assert abs(S[n + p] - closed) <= 1e-12 * abs(closed)
+    # lossless disc: every partial wave conserves flux, |1 + 2 S_n| = 1
+    assert np.allclose(np.abs(1 + 2 * S), 1.0, atol=1e-14)
+    assert np.allclose(S, S[::-1], rtol=1e-14, atol=0)                 # S_{-n} = S_n
+    assert np.allclose(O.mie_coefficients(5, k2, k2, R), 0.0, atol=1e-15)  # no contrast
+    # field continuity on the boundary: exterior J + S H equals the interior gamma_n J_n(kp r)
+    for n in (0, 3, -6):
+        h, j2 = O.hankel(n, k2 * R), O.bessel(n, k2 * R)
+        gam = (j2 + S[n + p] * h) / O.bessel(n, kp * R)
+        d_out = k2 * (O.bessel_p(n, k2 * R) + S[n + p] * O.hankel_p(n, k2 * R))
+        d_in = gam * kp * O.bessel_p(n, kp * R)
+        assert abs(d_out - d_in) <= 1e-12 * abs(d_out)
+
+
+# ---------------------------------------------------------------------------------------------
+# Layered medium (Sec. 2, Eq. "sommerfeldsys")
+# ---------------------------------------------------------------------------------------------
+def test_particle_free_reflection_is_fresnel_slab():
+    m = medium()
+    lam, _ = O.contour(256, m.k1, m.k2, m.k3, 0.2, 40.0)
+    src = np.array([0.3, 1.0])
+    inc = m.incident_density(lam, src)
+    sig = m.solve_layers(lam, inc=inc)
+    g1, g2, g3 = (O.gamma(lam, k) for k in (m.k1, m.k2, m.k3))
+    r12 = (g1 - g2) / (g1 + g2)
+    r23 = (g2 - g3) / (g2 + g3)
+    e2 = np.exp(-2 * g2 * m.d)
+    slab = (r12 + r23 * e2) / (1 + r12 * r23 * e2)                # Airy slab reflection
+    assert np.allclose(sig[:, 0] / inc, slab, rtol=1e-12, atol=1e-14)
+
+
+def test_homogeneous_medium_has_no_layer_response():
+    k = 3.0
+    m = medium(k, k, k)
+    lam, _ = O.contour(128, k, k, k, 0.2, 30.0)
+    inc = m.incident_density(lam, np.array([0.0, 1.0]))
+    sig = m.solve_layers(lam, inc=inc)
+    g = O.gamma(lam, k)
+    assert np.allclose(sig[:, 0], 0, atol=1e-13)
+    assert np.allclose(sig[:, 1], inc, rtol=1e-13)
+    assert np.allclose(sig[:, 2], 0, atol=1e-13)
+    assert np.allclose(sig[:, 3], inc * np.exp(-g * m.d), rtol=1e-12, atol=1e-300)
+    # and particle sources pass straight through: no reflected density
+    sig_p = m.solve_layers(lam, p_plus=np.ones(lam.size), q_minus=np.ones(lam.size))
+    assert np.allclose(sig_p[:, 1:3], 0, atol=1e-13)
+
+
+def test_closed_form_two_interface_response():
+    # Unit particle sums through the 4x4 LU against the closed form sigma2+ = R_t (P + R_b e Q)/D,
+    # sigma2- = R_b (Q + R_t e P)/D, D = 1 - R_t R_b e^2 (derived independently by hand).
+    m = medium()
+    lam, _ = O.contour(256, m.k1, m.k2, m.k3, 0.2, 60.0)
+    rng = np.random.default_rng(3)
+    P = rng.standard_normal(lam.size) + 1j * rng.standard_normal(lam.size)
+    Q = rng.standard_normal(lam.size) + 1j * rng.standard_normal(lam.size)
+    sig = m.solve_layers(lam, p_plus=P, q_minus=Q)
+    g1, g2, g3 = (O.gamma(lam, k) for k in (m.k1, m.k2, m.k3))
+    rt, rb = (g2 - g1) / (g2 + g1), (g2 - g3) / (g2 + g3)
+    e = np.exp(-g2 * m.d)
+    dd = 1 - rt * rb * e * e
+    assert np.allclose(sig[:, 1], rt * (P + rb * e * Q) / dd, rtol=1e-12, atol=1e-14)
+    assert np.allclose(sig[:, 2], rb * (Q + rt * e * P) / dd, rtol=1e-12, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------------------------
+# The coupled problem (Sec. 5, Eqs. "fullrep", "finalsys", "schur")
+# ---------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def three_discs():
+    m = medium()
+    lam, wt = fine_contour(m, 3000, 120.0)
+    c = np.array([[0.2, -0.7], [-0.6, -1.3], [0.9, -1.1]])
+    pr = O.Problem(m, 6, c, lam, wt)
+    src = np.array([0.1, 1.0])
+    return pr, src, pr.solve_dense(src)
+
+
+def test_three_solve_routes_agree(three_discs):
+    pr, src, beta = three_discs
+    sig, b_block = pr.solve_block(src)
+    b_schur = pr.solve_schur(src)
+    scale = np.abs(beta).max()
+    assert np.abs(b_block - beta).max() <= 1e-12 * scale
+    assert np.abs(b_schur - beta).max() <= 1e-12 * scale
+    # the block solve's layer densities are the ones the operator form implies
+    sig2 = pr.densities(src, beta)
+    assert np.allclose(sig, sig2, rtol=1e-10, atol=1e-12 * np.abs(sig).max())
+
+
+def test_interface_continuity_of_total_field(three_discs):
+    pr, src, beta = three_discs
+    h = 1e-4
+    for x in (-0.5, 0.3, 1.7):
+        u1 = lambda y: pr.field_layer1(src, beta, np.array([[x, y]]), "total")[0]
+        u2 = lambda y: pr.field_layer2(src, beta, np.array([[x, y]]))[0]
+        u3 = lambda y: pr.field_layer3(src, beta, np.array([[x, y]]))[0]
+        assert abs(u1(0.0) - u2(0.0)) <= 1e-11 * abs(u1(0.0))
+        assert abs(u3(-2.0) - u2(-2.0)) <= 1e-11 * abs(u3(-2.0))
+        # one-sided second-order differences for the normal derivative
+        d1 = (-3 * u1(0.0) + 4 * u1(h) - u1(2 * h)) / (2 * h)
+        d2 = (3 * u2(0.0) - 4 * u2(-h) + u2(-2 * h)) / (2 * h)
+        assert abs(d1 - d2) <= 1e-5 * abs(d1)
+        d3 = (3 * u3(-2.0) - 4 * u3(-2.0 - h) + u3(-2.0 - 2 * h)) / (2 * h)
+        d2b = (-3 * u2(-2.0) + 4 * u2(-2.0 + h) - u2(-2.0 + 2 * h)) / (2 * h)
+        assert abs(d3 - d2b) <= 1e-5 * abs(d3)
+
+
+def test_disc_boundary_conditions_multiple_scattering(three_discs):
+    # On each disc boundary the total exterior field has Fourier modes alpha_n J_n + beta_n H_n with
+    # alpha the full incoming field; the scattering matrix makes them match an interior field.
+    # Check the discrete relation beta = S alpha with alpha from incident + T + R.
+    pr, src, beta = three_discs
+    alpha = pr.incident_local(src) + pr.translation(beta) + pr.reflection(beta)
+    assert np.allclose(beta, pr.S[None, :] * alpha, rtol=1e-10, atol=1e-12 * np.abs(beta).max())
+
+
+def test_single_disc_homogeneous_contour_route_equals_graf():
+    k = 3.0 * math.pi
+    m = O.Medium(k, k, k, 2.0, MED["kp"], MED["radius"])
+    lam, wt = fine_contour(m, 3000, 120.0)
+    c = np.array([[0.35, -0.8]])
+    p = 8
+    pr = O.Problem(m, p, c, lam, wt)
+    src = np.array([-0.4, 1.0])
+    a_contour = pr.incident_local(src)[0]
+    d = src - c[0]
+    n = np.arange(-p, p + 1)
+    a_graf = 0.25j * O.hankel(n, k * math.hypot(*d)) * np.exp(-1j * n * math.atan2(d[1], d[0]))
+    assert np.allclose(a_contour, a_graf, rtol=1e-10, atol=1e-12)
+    beta = pr.solve_dense(src)
+    assert np.allclose(beta[0], pr.S * a_graf, rtol=1e-10, atol=1e-16)
+    assert np.allclose(pr.reflection(beta), 0.0, atol=1e-14)
+
+
+def test_homogeneous_particle_field_matches_direct_hankel_sum():
+    k = 3.0 * math.pi
+    m = O.Medium(k, k, k, 2.0, MED["kp"], MED["radius"])
+    lam, wt = fine_contour(m, 3000, 120.0)
+    c = np.array([[0.35, -0.8], [-0.5, -1.4]])
+    pr = O.Problem(m, 6, c, lam, wt)
+    src = np.array([0.0, 1.0])
+    beta = pr.solve_dense(src)
+    tg = np.array([[-1.0, 1.5], [0.2, 1.5], [1.3, 0.7]])
+    u_part = pr.field_layer1(src, beta, tg, "particle")
+    direct = np.zeros(len(tg), dtype=complex)
+    n = np.arange(-6, 7)
+    for j in range(2):
+        dd = tg - c[j]
+        direct += (O.hankel(n[None, :], k * np.hypot(dd[:, 0], dd[:, 1])[:, None])
+                   * np.exp(1j * n[None, :] * np.arctan2(dd[:, 1], dd[:, 0])[:, None])) @ beta[j]
+    assert np.allclose(u_part, direct, rtol=1e-10, atol=0)
+
+
+def test_reciprocity_of_layered_scattering():
+    m = medium()
+    lam, wt = fine_contour(m, 3000, 120.0)
+    c = np.array([[0.2, -0.7], [-0.6, -1.3]])
+    pr = O.Problem(m, 6, c, lam, wt)
+    a, b = np.array([-0.7, 0.6]), np.array([0.9, 1.1])
+    u_ab = pr.field_layer1(a, pr.solve_dense(a), b[None, :], "scattered")[0]
+    u_ba = pr.field_layer1(b, pr.solve_dense(b), a[None, :], "scattered")[0]
+    assert abs(u_ab - u_ba) <= 1e-6 * abs(u_ab)
+
+
+def test_oracle_gmres_matches_lu():
+    m = medium()
+    lam, wt = O.contour(256, m.k1, m.k2, m.k3, 0.2, 141.0)
+    c = inputs.layout(6, -1.5, 1.5, 11)
+    pr = O.Problem(m, 5, c, lam, wt)
+    src = np.array([0.0, 1.0])
+    beta = pr.solve_dense(src)
+    x, it, hist = O.gmres(lambda v: pr.apply(v).ravel(), pr.rhs(src).ravel(), tol=1e-13, maxiter=200)
+    assert hist[-1] <= 1e-13
+    assert np.allclose(x.reshape(beta.shape), beta, rtol=1e-9, atol=1e-10 * np.abs(beta).max())
