@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the multiple-scattering operator y = x - S (T + R) x and its solve.
+
+Workload: 5000 dielectric discs (R = 0.25, kp = 2.4 pi) in the middle layer (d = 2) of the medium
+k = (2 pi, 3 pi, 4 pi), p = 14 (29 coefficients per disc), 1024-node Sommerfeld contour, seeded
+synthetic layout at ~20% area fraction.  A step is one operator application on one coefficient
+vector already resident in device memory.  `value` is operator applications per second of the
+mixed-precision operator (FP32 translation; the solve recovers FP64 accuracy by refinement), summed
+over all ranks; the FP64 operator's rate, the solve times and the end-to-end rate through the
+host-pointer C ABI are reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 launch with torch.distributed.run: every rank runs an independent replica (the operator
+of one layout does not shard without an exchange step), so scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "disc5000_p14_ns1024"
+METRIC = "N=5000 solve time & operator applies/s, mixed/batched vs FP64 at <=1e-8 rel err"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12    # 152 SMs x 128 FP32 lanes x FMA x max clock
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12      # 2 FP64 FMA per SM per clock on GB300
+# DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by the SHA-256 of the
+# source file it was taken on (reported as null once the source changes).
+TRAFFIC = {}
+
+
+def src_hash(path: str) -> str:
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-solve", action="store_true", help="skip the solve timings")
+    ap.add_argument("--solve-fp64", action="store_true", help="also time the FP64 solve (slow)")
+    ap.add_argument("--oracle-rows", type=int, default=8,
+                    help="target rows of the oracle's bounded sample per reference step")
+    ap.add_argument("--baseline-rows", type=int, default=40,
+                    help="target rows of the oracle's bounded sample for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing")
+    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------------
+# the oracle's bounded sample (runs in a child process with one BLAS thread)
+# ------------------------------------------------------------------------------------------------
+def oracle_sample(workload: str, rows: int) -> dict:
+    """Time the oracle on a bounded sample of one operator application: the aggregate and per-node
+    layer solves once (global), the translation and disaggregate for `rows` target discs; return
+    the extrapolated time of a full application."""
+    import numpy as np
+
+    from oracle import lsms_oracle as O
+    from paper_1407_3868_gb300 import inputs
+    w = inputs.WORKLOADS[workload]
+    m = w.medium
+    c = w.centres()
+    lam, wt = O.contour(w.n_nodes, m["k1"], m["k2"], m["k3"], w.b, w.t_max)
+    pr = O.Problem(O.Medium(m["k1"], m["k2"], m["k3"], m["d"], m["kp"], m["radius"]), w.p, c, lam, wt)
+    x = inputs.random_coefficients(w.n, w.p, 1, 0)[0] / O.order_scale(w.p, m["k2"], m["radius"])
+    sel = list(np.linspace(0, w.n - 1, rows).astype(int))
+    t0 = time.perf_counter()
+    pp, qm = pr.aggregate(x)
+    sig = pr.layer_densities(None, pp, qm)
+    t1 = time.perf_counter()
+    alpha = pr.translation(x, sel) + pr.disaggregate(sig[:, 1], sig[:, 2], sel)
+    _ = x[sel] - pr.S[None, :] * alpha
+    t2 = time.perf_counter()
+    full = (t1 - t0) + (t2 - t1) * w.n / rows
+    return {"global_s": t1 - t0, "rows": rows, "rows_s": t2 - t1, "full_apply_s": full}
+
+
+def run_oracle_child(workload: str, rows: int) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", "--workload",
+                          workload, "--oracle-rows", str(rows)], capture_output=True, text=True,
+                         env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError("oracle sample failed:\n" + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_entry(s: dict) -> dict:
+    return {"value": 1.0 / s["full_apply_s"], "unit": "applies/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 NumPy/SciPy oracle, one BLAS thread: global aggregate + layer solves "
+                       f"({s['global_s']:.2f} s) and {s['rows']} of 5000 target rows "
+                       f"({s['rows_s']:.2f} s), extrapolated to a full application "
+                       f"({s['full_apply_s']:.1f} s)")}
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:6]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# our implementation
+# ------------------------------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1407_3868_gb300 import inputs, lsms
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = inputs.WORKLOADS[args.workload]
+    n, P = w.n, 2 * w.p + 1
+    centres = w.centres()
+    ctx = lsms.context_for(w, lsms.LSMS_MIXED)
+    ctx.set_particles(centres)
+    ctx.set_timing(True)
+    b = torch.from_numpy(inputs.random_coefficients(n, w.p, 1, 100 + rank)).to(dev)
+    y = torch.empty_like(b)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(flags, steps):
+        e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        t_tr, launches = [], 0
+        for i in range(steps):
+            flush.fill_(float(i))
+            e0[i].record(stream)
+            ctx.apply_dev(b, y, flags, stream)
+            e1[i].record(stream)
+            ttr, _, launches = ctx.last_timing()       # waits for this step's events
+            t_tr.append(ttr)
+        torch.cuda.synchronize()
+        ms = sum(e0[i].elapsed_time(e1[i]) for i in range(steps))
+        return ms, t_tr, launches
+
+    flags_mixed = lsms.APPLY_SCALED | lsms.APPLY_MIXED
+    flags_fp64 = lsms.APPLY_SCALED
+    for _ in range(args.warmup):
+        ctx.apply_dev(b, y, flags_mixed, stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    ms_mixed, t_tr_mixed, launches = timed(flags_mixed, args.steps)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop() if clocks else None
+    # FP64 operator (fewer steps: ~0.2 s each)
+    k64 = max(2, min(args.steps, 5))
+    for _ in range(1):
+        ctx.apply_dev(b, y, flags_fp64, stream)
+    ms_fp64, t_tr_fp64, _ = timed(flags_fp64, k64)
+    # max over ranks
+    tot = torch.tensor([ms_mixed, ms_fp64], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    ms_mixed, ms_fp64 = float(tot[0]), float(tot[1])
+    value = world * args.steps / (ms_mixed / 1e3)
+    fp64_rate = world * k64 / (ms_fp64 / 1e3)
+
+    # end to end through the host-pointer ABI: pinned host input, host output, copies inside
+    xh = torch.from_numpy(inputs.random_coefficients(n, w.p, 1, 200 + rank)).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    xn, yn = xh.numpy(), yh.numpy()
+    lib = lsms.load()
+    import ctypes
+    dp = ctypes.POINTER(ctypes.c_double)
+    for _ in range(2):
+        lib.lsms_apply(ctx.h, 1, xn.ctypes.data_as(dp), yn.ctypes.data_as(dp))
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        rc = lib.lsms_apply(ctx.h, 1, xn.ctypes.data_as(dp), yn.ctypes.data_as(dp))
+        assert rc == 0, rc
+        _ = float(yn.real[0, 0, 0])
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = world * args.steps / float(te[0])
+
+    # roofline of the dominant kernel (the FP32 translation)
+    pairs = n * (n - 1)
+    flop = 8.0 * P * P * pairs
+    tr_ms = statistics.mean(t_tr_mixed)
+    achieved = flop / (tr_ms / 1e3) / 1e12
+    tr64_ms = statistics.mean(t_tr_fp64)
+    key = src_hash(os.path.join(ROOT, "paper_1407_3868_gb300", "csrc", "mixed.cu"))
+    traffic = TRAFFIC.get(key)
+
+    solve = None
+    if not args.no_solve:
+        solve = {}
+        ctxm = lsms.context_for(w, lsms.LSMS_MIXED)
+        ctxm.set_particles(centres)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        beta_m, info_m = ctxm.solve(w.sources, tol=1e-10, maxiter=2000)
+        solve["mixed_s"] = time.perf_counter() - t0
+        u_m = ctxm.eval_field(w.targets, 0, lsms.FIELD_SCATTERED)
+        solve["mixed_iters"] = info_m["iters"]
+        solve["mixed_refinements"] = info_m["outer_iters"]
+        solve["mixed_rel_res_fp64"] = info_m["rel_res_fp64"]
+        ctxm.close()
+        if args.solve_fp64:
+            ctxd = lsms.context_for(w, lsms.LSMS_FP64)
+            ctxd.set_particles(centres)
+            t0 = time.perf_counter()
+            beta_d, info_d = ctxd.solve(w.sources, tol=1e-10, maxiter=2000)
+            solve["fp64_s"] = time.perf_counter() - t0
+            solve["fp64_iters"] = info_d["iters"]
+            u_d = ctxd.eval_field(w.targets, 0, lsms.FIELD_SCATTERED)
+            solve["mixed_vs_fp64_field_rel_err"] = float(np.linalg.norm(u_m - u_d) / np.linalg.norm(u_d))
+            ctxd.close()
+    ctx.close()
+
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "discs": n, "p": w.p, "contour_nodes": w.n_nodes,
+                   "operator": "mixed (FP32 translation)", "nrhs": 1,
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+        "fp64": {"value": fp64_rate, "unit": "applies/s", "ms_per_step": ms_fp64 / k64, "dtype": "f64",
+                 "translate_ms": tr64_ms,
+                 "translate_frac_of_fp64_peak": (flop / (tr64_ms / 1e3) / 1e12) / FP64_PEAK_TFLOPS},
+        "speedup_mixed_vs_fp64": value / fp64_rate,
+        "solve": solve,
+        "roofline": {"kernel": "k_translate_f32", "bound": "alu", "achieved": achieved,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": traffic, "flop_per_launch": flop, "launch_ms": tr_ms,
+                     "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+        "e2e": {"value": e2e, "unit": "applies/s", "h2d_bytes_per_step": n * P * 16,
+                "d2h_bytes_per_step": n * P * 16},
+        "gpu_launches": launches * args.steps,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline_entry(run_oracle_child(w.name, args.baseline_rows))
+        except Exception as e:  # pragma: no cover
+            line["cpu_baseline"] = {"value": None, "error": str(e)[-300:]}
+    return line
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    vals = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        s = run_oracle_child(args.workload, args.oracle_rows)
+        if i >= args.warmup:
+            vals.append(s["full_apply_s"])
+            last = s
+    total = sum(vals)
+    value = len(vals) / total
+    cb = cpu_baseline_entry(last)
+    cb["value"] = value
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(vals),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "operator": "FP64 oracle"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "applies/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    if args.oracle_sample:
+        print(json.dumps(oracle_sample(args.workload, args.oracle_rows)))
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        line = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

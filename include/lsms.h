@@ -1,0 +1,207 @@
+/*
+ * lsms.h — C ABI of the GB300 layered-medium multi-particle scattering library (liblsms.so).
+ *
+ * Problem (Lai, Kobayashi, Greengard, "A fast solver for multi-particle scattering in a layered
+ * medium"): 2-D TM scattering of the field of a line source in the top layer (y > 0, wavenumber
+ * k1) of a three-layer medium by identical dielectric discs (radius R, wavenumber kp) placed in the
+ * middle layer (-d < y < 0, k2) above the bottom half-space (y < -d, k3); Sec. 1, Sec. 5.
+ *
+ * Unknowns: the outgoing (Hankel) coefficients beta^j_n, n = -p..p, of every disc j
+ * (Sec. 3.1 Eq. "out"; truncation Sec. 3.1 Remark).  P = 2p + 1.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an int status: LSMS_OK (0) or a negative lsms_status code.  Nothing
+ *     throws across the ABI.  lsms_last_error() gives a message for the last failure.
+ *   - Complex numbers are interleaved (re, im) float64 pairs: C99 double _Complex,
+ *     std::complex<double> and torch.complex128 all share this layout.
+ *   - Coefficient arrays are right-hand-side major, then disc, then order:
+ *     element (r, j, n) of a [nrhs][N][P] array sits at complex index (r*N + j)*P + (n + p).
+ *   - Host pointers are owned by the caller; the library copies inputs and writes outputs the
+ *     caller allocated.  The context owns all device memory it allocates.  `*_dev` entry points
+ *     take device pointers (e.g. torch tensors) plus a cudaStream_t passed as void*; they are
+ *     asynchronous on that stream.  All other calls are synchronous on the host.
+ *   - A context is not thread-safe: use one context per host thread.
+ *   - Time dependence exp(-i w t): H_n = H_n^(1) is outgoing.
+ */
+#ifndef LSMS_H
+#define LSMS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lsms_ctx lsms_ctx;
+
+typedef enum {
+  LSMS_OK = 0,
+  LSMS_ERR_ARG = -1,           /* invalid argument: non-finite or non-positive k, p < 0, ...   */
+  LSMS_ERR_GEOMETRY = -2,      /* discs closer than 2.2 R or not strictly inside the layer     */
+  LSMS_ERR_NOT_CONVERGED = -3, /* GMRES hit maxiter (the iterate is still returned)            */
+  LSMS_ERR_NONFINITE = -4,     /* a NaN/Inf appeared in the iteration                          */
+  LSMS_ERR_OOM = -5,           /* device allocation failed                                     */
+  LSMS_ERR_CUDA = -6,          /* a CUDA runtime call failed                                   */
+  LSMS_ERR_STATE = -7          /* call order: e.g. apply before set_particles                  */
+} lsms_status;
+
+typedef enum {
+  LSMS_FP64 = 0,   /* every step in float64                                                    */
+  LSMS_MIXED = 1   /* FP32 translation, split-BF16 tensor-core contour contractions, FP64 refinement */
+} lsms_precision;
+
+/* Discretised Sommerfeld contour (Sec. 5.1, Eq. "sommerseg"): Gamma3 = t + i b (t < 0),
+ * Gamma2 = i s (s from b to -b), Gamma1 = t - i b (t > 0), truncated at |t| = t_max.
+ * Gamma1 and Gamma3 each hold n1 = q*floor((n_nodes - q)/(2q)) Gauss-Legendre nodes in panels of
+ * order q = panel_order, graded toward the branch points k1, k2, k3 (breakpoints k_i +- b*2^j);
+ * Gamma2 holds the remaining n_nodes - 2*n1 nodes as one Gauss-Legendre rule.  Node order is
+ * Gamma3, Gamma2, Gamma1.  Zero fields take defaults: b = 0.2, t_max = max(k1,k2,k3) + 20
+ * (Sec. 6), panel_order = 16. */
+typedef struct {
+  int n_nodes;       /* N_S, required; must leave n1 >= panel_order                          */
+  double b;          /* offset of Gamma1/Gamma3 from the real axis                            */
+  double t_max;      /* truncation of Gamma1/Gamma3                                           */
+  int panel_order;   /* Gauss-Legendre order of each Gamma1/Gamma3 panel                      */
+} lsms_contour;
+
+/* Outcome of lsms_solve.  history (optional, caller-owned, history_cap doubles) receives the
+ * relative residual estimate after every inner GMRES iteration. */
+typedef struct {
+  int iters;            /* GMRES iterations (summed over refinement steps)                       */
+  int outer_iters;      /* refinement steps (1 for LSMS_FP64)                                     */
+  double rel_res;       /* final GMRES residual estimate, scaled preconditioned system            */
+  double rel_res_fp64;  /* ||rhs - A beta|| / ||rhs|| recomputed in FP64 at the end               */
+  double* history;      /* in: buffer or NULL                                                     */
+  int history_cap;      /* in: capacity of history                                               */
+  int n_history;        /* out: entries written                                                   */
+} lsms_solve_info;
+
+/* Field selector of lsms_eval_field (all in the top layer, Sec. 5 Eq. "fullrep"). */
+enum {
+  LSMS_FIELD_TOTAL = 0,      /* u1 = G_{k1}(x, x0) + u1^s                                     */
+  LSMS_FIELD_SCATTERED = 1,  /* u1^s = u1 - G (layer reflection and discs)                     */
+  LSMS_FIELD_PARTICLE = 2    /* u1 - u1(no discs): the part due to the discs                   */
+};
+
+/* Flags of lsms_apply_ex / lsms_apply_dev. */
+enum {
+  LSMS_APPLY_SCALED = 1,        /* x, y in the scaled basis b_n = |H_n(k2 R)| beta_n           */
+  LSMS_APPLY_MIXED = 2,         /* mixed-precision operator (FP32 translation, BF16x3 contour) */
+  LSMS_APPLY_NO_TRANSLATION = 4,/* drop T (free-space Graf coupling)                           */
+  LSMS_APPLY_NO_REFLECTION = 8, /* drop R (layer-reflected coupling)                           */
+  LSMS_APPLY_ALPHA = 16         /* output alpha = (T + R) x instead of x - S alpha             */
+};
+
+/* lsms_create — medium, discs and discretisation (Sec. 1; Sec. 3.1 Eq. "linear"; Sec. 5.1).
+ *   k1, k2, k3: real wavenumbers of the three layers (> 0, finite).  d: middle-layer thickness.
+ *   kp: wavenumber inside the discs.  radius: disc radius R (0 < R < d/2).  p >= 0, p <= 15.
+ *   contour: see lsms_contour (required).  precision: default precision of lsms_apply/lsms_solve.
+ *   On success *out holds a new context (free with lsms_destroy).  Errors: LSMS_ERR_ARG. */
+int lsms_create(double k1, double k2, double k3, double d, double kp, double radius, int p,
+                const lsms_contour* contour, int precision, lsms_ctx** out);
+
+/* lsms_set_particles — disc centres (Sec. 3.2; Sec. 5).  centres_xy: 2n doubles (x0,y0,x1,...).
+ *   Every disc must lie strictly inside the middle layer, with gaps >= 0.2 R between discs
+ *   (10% of the diameter: the well-separation assumption of Sec. 1); otherwise
+ *   LSMS_ERR_GEOMETRY.  Builds the per-disc contour tables on the device. n may be 0. */
+int lsms_set_particles(lsms_ctx* ctx, int n, const double* centres_xy);
+
+/* lsms_apply — y = x - S (T + R) x: the preconditioned multiple-scattering operator
+ *   (Sec. 3.2 "scattmatrix" and the remark after it; Sec. 5.4 Eq. "schur").  x, y: [nrhs][N][P]
+ *   complex, host.  T: Graf translation (Lemma 3.1); R: layer-reflected coupling (Thm 5.2 ->
+ *   Eq. "sommerfeldsys" -> Lemma 5.1).  Uses the context's precision.  x and y may alias. */
+int lsms_apply(lsms_ctx* ctx, int nrhs, const double* x, double* y);
+
+/* lsms_apply_ex — lsms_apply with LSMS_APPLY_* flags (host pointers). */
+int lsms_apply_ex(lsms_ctx* ctx, int nrhs, const double* x, double* y, int flags);
+
+/* lsms_apply_dev — lsms_apply_ex on device pointers, asynchronous on `stream` (cudaStream_t). */
+int lsms_apply_dev(lsms_ctx* ctx, int nrhs, const double* x_dev, double* y_dev, int flags,
+                   void* stream);
+
+/* lsms_translate — alpha^l = sum_{m != l} T^{lm} beta^m (Sec. 3.2 Lemma 3.1, Eq. "trans"), with
+ *   T^{lm}[nu][n] = H_{n-nu}(k2 rho) exp(i (n - nu) phi), rho = |x_l - x_m|, phi = arg(x_l - x_m).
+ *   beta, alpha: [nrhs][N][P] complex, host.  precision: LSMS_FP64 or LSMS_MIXED. */
+int lsms_translate(lsms_ctx* ctx, int nrhs, const double* beta, double* alpha, int precision);
+
+/* lsms_aggregate — multipole-to-Sommerfeld (Sec. 5.3 Theorem 5.2, Eq. "invfft"):
+ *   P+(nu) = sum_j sum_n beta^j_n c_n w-(nu)^n exp(gamma2 y_j - i lambda x_j),
+ *   Q-(nu) = sum_j sum_n beta^j_n c_n w+(nu)^n exp(-gamma2 (y_j + d) - i lambda x_j),
+ *   c_n = 4 (-i)^{n+1}, w-+ = (lambda -+ gamma2)/k2.  beta: [nrhs][N][P]; p_plus, q_minus:
+ *   [nrhs][N_S] complex, host. */
+int lsms_aggregate(lsms_ctx* ctx, int nrhs, const double* beta, double* p_plus, double* q_minus,
+                   int precision);
+
+/* lsms_reflect — per-node layer response (Sec. 2 Eq. "sommerfeldsys" with the discs' terms on
+ *   the right): sigma2+ = R_t (P + R_b e Q)/D, sigma2- = R_b (Q + R_t e P)/D, D = 1 - R_t R_b e^2,
+ *   R_t = (g2-g1)/(g2+g1), R_b = (g2-g3)/(g2+g3), e = exp(-g2 d).  Arrays [nrhs][N_S], host. */
+int lsms_reflect(lsms_ctx* ctx, int nrhs, const double* p_plus, const double* q_minus,
+                 double* sigma_plus, double* sigma_minus);
+
+/* lsms_disaggregate — Sommerfeld-to-local by Jacobi-Anger (Sec. 5.2.1 Lemma 5.1, Eq. "JA2"):
+ *   alpha^i_m = (1/4pi) sum_nu (w_nu/gamma2) i^m [sigma2+ w-^m exp(gamma2 y_i + i lambda x_i)
+ *               + sigma2- w+^m exp(-gamma2 (y_i + d) + i lambda x_i)].
+ *   sigma_*: [nrhs][N_S]; alpha: [nrhs][N][P], host. */
+int lsms_disaggregate(lsms_ctx* ctx, int nrhs, const double* sigma_plus, const double* sigma_minus,
+                      double* alpha, int precision);
+
+/* lsms_incident — local expansion a_inc on every disc of the particle-free layered field of line
+ *   sources src_xy (2 n_src doubles, y > 0): Eq. "sommerfeldsys" with the incident right-hand
+ *   side, then Lemma 5.1.  a_inc: [n_src][N][P], host.  The right-hand side of the disc system is
+ *   S a_inc (Sec. 5.4). */
+int lsms_incident(lsms_ctx* ctx, int n_src, const double* src_xy, double* a_inc);
+
+/* lsms_get_contour — the contour nodes lambda_nu and weights w_nu (d lambda included), N_S complex
+ *   each, host.  lsms_get_scattering — the disc scattering matrix diagonal S_n (P complex). */
+int lsms_get_contour(const lsms_ctx* ctx, double* nodes, double* weights);
+int lsms_get_scattering(const lsms_ctx* ctx, double* s_diag);
+int lsms_num_nodes(const lsms_ctx* ctx);
+int lsms_num_particles(const lsms_ctx* ctx);
+
+/* lsms_solve — beta for each source from (I - S(T + R)) beta = S a_inc (Sec. 3.2 GMRES,
+ *   Sec. 5.4 Eq. "schur").  GMRES runs on the device on the scaled system (b = |H_n(k2R)| beta):
+ *   x0 = 0 (or x0 if given, unscaled [n_src][N][P]), stop when the residual estimate divided by
+ *   ||rhs|| <= tol or after maxiter iterations (then LSMS_ERR_NOT_CONVERGED with the iterate in
+ *   beta_out).  LSMS_MIXED: inner GMRES on the mixed operator inside an FP64 refinement loop.
+ *   beta_out: [n_src][N][P] (may be NULL).  The solution is kept in the context for
+ *   lsms_eval_field.  info may be NULL (summary of the last source). */
+int lsms_solve(lsms_ctx* ctx, int n_src, const double* src_xy, double tol, int maxiter,
+               const double* x0, double* beta_out, lsms_solve_info* info);
+
+/* lsms_eval_field — field in the top layer at n_tgt points (2 n_tgt doubles, y > 0) for source
+ *   src_index of the last lsms_solve (Sec. 2 Eq. "layer1", Sec. 5 Eq. "fullrep"):
+ *   u1^s(x) = (1/4pi) sum_nu w_nu sigma1(nu) exp(-gamma1 y + i lambda x)/gamma1,
+ *   sigma1 = R11 I + tau21 (P+ + e sigma2-).  which: LSMS_FIELD_*.  out: n_tgt complex, host. */
+int lsms_eval_field(lsms_ctx* ctx, int src_index, int n_tgt, const double* tgt_xy, int which,
+                    double* out);
+
+/* lsms_set_timing — enable (1) or disable (0) CUDA-event timing of the operator's parts.  While
+ *   enabled, every operator application records events on its stream around the translation
+ *   (Lemma 3.1) and around the reflected coupling (Thm 5.2 -> Eq. "sommerfeldsys" -> Lemma 5.1).
+ * lsms_last_timing — waits for the last application's events and returns the two durations in
+ *   milliseconds and the number of kernels that application launched (any pointer may be NULL).
+ *   LSMS_ERR_STATE when timing is off. */
+int lsms_set_timing(lsms_ctx* ctx, int enable);
+int lsms_last_timing(lsms_ctx* ctx, double* ms_translate, double* ms_reflect, int* launches);
+
+/* Host-only helpers: no GPU needed, no context.
+ * lsms_build_contour — the nodes and weights lsms_create would use for `contour` (see
+ *   lsms_contour; Sec. 5.1 Eq. "sommerseg"); nodes, weights: contour->n_nodes complex each.
+ * lsms_scattering_diagonal — S_n, n = -p..p, of a dielectric disc (Sec. 3.1 Eq. "linear").
+ * lsms_check_geometry — LSMS_OK when n discs of radius R (centres_xy, 2n doubles) lie strictly
+ *   inside the layer -d < y < 0 with gaps >= 0.2 R (10% of the diameter, the well-separation
+ *   assumption of Sec. 1), else LSMS_ERR_GEOMETRY (or LSMS_ERR_ARG for non-finite input). */
+int lsms_build_contour(const lsms_contour* contour, double k1, double k2, double k3, double* nodes,
+                       double* weights);
+int lsms_scattering_diagonal(int p, double k2, double kp, double radius, double* s_diag);
+int lsms_check_geometry(double d, double radius, int n, const double* centres_xy);
+
+/* lsms_last_error — message of the last failure on ctx (or of lsms_create when ctx is NULL).
+ *   The string is owned by the library and valid until the next call on ctx. */
+const char* lsms_last_error(const lsms_ctx* ctx);
+
+/* lsms_destroy — free the context and all its device memory.  NULL is ignored. */
+void lsms_destroy(lsms_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSMS_H */

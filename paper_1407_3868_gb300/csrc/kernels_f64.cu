@@ -1,0 +1,430 @@
+// FP64 kernels of the multiple-scattering operator y = x - S (T + R) x.
+//
+//   translation (Sec. 3.2 Lemma 3.1): tiled all pairs, one warp per target disc, lanes over the
+//     output order nu; each lane of the warp generates the Hankel sequence of one source disc
+//     (warp-cooperative: 32 pair sequences at once) into shared memory, then the warp contracts
+//     the Toeplitz block against the staged source coefficients.
+//   aggregate / disaggregate (Sec. 5.3 Thm 5.2; Sec. 5.2.1 Lemma 5.1): complex GEMMs against the
+//     precomputed plane-wave tables, then per-node order-factor dots.
+//   per-node reflection (Sec. 2 Eq. "sommerfeldsys"): closed-form 2x2 response per node.
+#include <cmath>
+
+#include "lsms_internal.h"
+
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {   // c + a b
+  c.x = fma(a.x, b.x, c.x);
+  c.x = fma(-a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y);
+  c.y = fma(a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cexp_(double re, double im) {
+  double s, c;
+  sincos(im, &s, &c);
+  const double m = exp(re);
+  return make_double2(m * c, m * s);
+}
+__device__ __forceinline__ double2 warp_sum(double2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------------------------
+// xs = scale[n] * x
+// ---------------------------------------------------------------------------------------------
+__global__ void k_scale_in(const double2* __restrict__ x, const double* __restrict__ scale,
+                           double2* __restrict__ xs, long long total, int P) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double s = scale[i % P];
+    const double2 v = x[i];
+    xs[i] = make_double2(v.x * s, v.y * s);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Translation, FP64
+// ---------------------------------------------------------------------------------------------
+constexpr int TW = 4;    // target discs (warps) per CTA
+constexpr int CH = 32;   // source discs per staged chunk (one per lane for the Hankel sequences)
+constexpr int HS = 65;   // length of a pair's sequence h_s, s = -2p..2p (4p + 1 <= 61); odd stride avoids bank conflicts
+
+// h[s + 2p] = H_s(k rho) exp(i s phi), s = -2p..2p, for the pair offset (dx, dy) = x_l - x_m.
+// H_0, H_1 from the CUDA math library; H_{q+1} = (2q/z) H_q - H_{q-1} forward (stable normwise
+// because the Y part dominates for q > z); H_{-q} = (-1)^q H_q.
+__device__ void hankel_sequence_f64(double dx, double dy, double k, int p, double2* h) {
+  const double rho = hypot(dx, dy);
+  const double z = k * rho;
+  const double2 e1 = make_double2(dx / rho, dy / rho);
+  const int c0 = 2 * p;
+  double2 hm = make_double2(j0(z), y0(z));
+  double2 hq = make_double2(j1(z), y1(z));
+  h[c0] = hm;
+  double2 eq = e1;
+  const double iz = 1.0 / z;
+  for (int q = 1; q <= 2 * p; ++q) {
+    const double2 v = cmul(hq, eq);
+    h[c0 + q] = v;
+    const double2 u = cmul(hq, make_double2(eq.x, -eq.y));
+    h[c0 - q] = (q & 1) ? make_double2(-u.x, -u.y) : u;
+    if (q < 2 * p) {
+      const double f = 2.0 * q * iz;
+      const double2 hn = make_double2(f * hq.x - hm.x, f * hq.y - hm.y);
+      hm = hq;
+      hq = hn;
+      eq = cmul(eq, e1);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(TW * 32)
+k_translate_f64(const double* __restrict__ cx, const double* __restrict__ cy, int n, int p,
+                double k, const double2* __restrict__ xs, double2* __restrict__ alpha) {
+  extern __shared__ double2 smem[];
+  double2* sb = smem;                  // [CH][32] staged source coefficients
+  double2* sh = smem + CH * 32;        // [TW][CH][HS] pair sequences
+  __shared__ double scx[CH], scy[CH];
+  const int P = 2 * p + 1;
+  const int r = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int l = blockIdx.x * TW + warp;
+  const bool lvalid = l < n;
+  const double xl = lvalid ? cx[l] : 0.0, yl = lvalid ? cy[l] : 0.0;
+  const double2* xr = xs + (size_t)r * n * P;
+  double2* hw = sh + (size_t)warp * CH * HS;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int j0c = 0; j0c < n; j0c += CH) {
+    const int cnt = min(CH, n - j0c);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt * P; i += blockDim.x) {
+      const int s = i / P, q = i - s * P;
+      sb[s * 32 + q] = xr[(size_t)(j0c + s) * P + q];
+    }
+    if (threadIdx.x < cnt) {
+      scx[threadIdx.x] = cx[j0c + threadIdx.x];
+      scy[threadIdx.x] = cy[j0c + threadIdx.x];
+    }
+    __syncthreads();
+    if (lane < cnt) {
+      double2* h = hw + lane * HS;
+      if (lvalid && j0c + lane != l) {
+        hankel_sequence_f64(xl - scx[lane], yl - scy[lane], k, p, h);
+      } else {
+        for (int q = 0; q <= 4 * p; ++q) h[q] = make_double2(0.0, 0.0);
+      }
+    }
+    __syncwarp();
+    if (lvalid && lane < P) {
+      for (int s = 0; s < cnt; ++s) {
+        const double2* hs = hw + s * HS + 2 * p - lane;   // hs[q] = h_{n - nu}, n = q - p
+        const double2* bs = sb + s * 32;
+        for (int q = 0; q < P; ++q) acc = cfma(hs[q], bs[q], acc);
+      }
+    }
+  }
+  if (lvalid && lane < P) alpha[(size_t)r * n * P + (size_t)l * P + lane] = acc;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Plane-wave tables of the discs (Thm 5.2 / Lemma 5.1 factors that depend on the disc position)
+// ---------------------------------------------------------------------------------------------
+__global__ void k_etables(const double* __restrict__ cx, const double* __restrict__ cy, int n,
+                          const double2* __restrict__ lam, const double2* __restrict__ g2, int ns,
+                          double d, double2* __restrict__ eagg, double2* __restrict__ edis) {
+  const long long total = (long long)ns * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(i / n), j = (int)(i - (long long)v * n);
+    const double2 L = lam[v], g = g2[v];
+    const double x = cx[j], y = cy[j], yd = y + d;
+    // -i lambda x = (lam.y x) + i (-lam.x x)
+    const double ax = L.y * x, ay = -L.x * x;
+    eagg[(size_t)v * n + j] = cexp_(g.x * y + ax, g.y * y + ay);               // exp(g2 y - i l x)
+    eagg[(size_t)(ns + v) * n + j] = cexp_(-g.x * yd + ax, -g.y * yd + ay);   // exp(-g2(y+d) - i l x)
+    edis[(size_t)j * 2 * ns + v] = cexp_(g.x * y - ax, g.y * y - ay);         // exp(g2 y + i l x)
+    edis[(size_t)j * 2 * ns + ns + v] = cexp_(-g.x * yd - ax, -g.y * yd - ay);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// C[r][m][n] += sum_k A[m][k] B[r][k][n]  (complex FP64, split-K with atomics)
+// ---------------------------------------------------------------------------------------------
+constexpr int GT = 32;
+
+__global__ void __launch_bounds__(256)
+k_zgemm_rows(const double2* __restrict__ A, int M, int K, const double2* __restrict__ B,
+             double2* __restrict__ C, int P, int kchunk) {
+  __shared__ double2 As[GT][GT + 1];
+  __shared__ double2 Bs[GT][GT + 1];
+  const int r = blockIdx.y;
+  const int m0 = blockIdx.x * GT;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const double2* Br = B + (size_t)r * K * P;
+  double2 acc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q] = make_double2(0.0, 0.0);
+  for (int k0 = kbeg; k0 < kend; k0 += GT) {
+    for (int e = threadIdx.x; e < GT * GT; e += blockDim.x) {
+      const int i = e >> 5, kk = e & 31;
+      const int m = m0 + i, kx = k0 + kk;
+      As[i][kk] = (m < M && kx < kend) ? A[(size_t)m * K + kx] : make_double2(0.0, 0.0);
+      const int nn = kk;   // reuse e for B: row i is k, column kk is n
+      Bs[i][nn] = (k0 + i < kend && nn < P) ? Br[(size_t)(k0 + i) * P + nn] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GT; ++kk) {
+      const double2 b = Bs[kk][tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = cfma(As[ty + 8 * q][kk], b, acc[q]);
+    }
+    __syncthreads();
+  }
+  if (tx < P) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int m = m0 + ty + 8 * q;
+      if (m < M) {
+        double2* c = C + ((size_t)r * M + m) * P + tx;
+        atomicAdd(&c->x, acc[q].x);
+        atomicAdd(&c->y, acc[q].y);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Per-node stage: order dots (aggregate epilogue), reflection (Eq. "sommerfeldsys" closed form),
+// and the disaggregate's right operand V = U * sigma.
+// G, V: [r][2ns][P]; pq, sig: [r][2][ns].
+// ---------------------------------------------------------------------------------------------
+__global__ void k_node_stage(int ns, int P, int nrhs, const double2* __restrict__ G,
+                             const double2* __restrict__ fagg, const double2* __restrict__ pq_in,
+                             const double2* __restrict__ refl, const double2* __restrict__ udis,
+                             double2* __restrict__ pq_out, double2* __restrict__ sig_out,
+                             double2* __restrict__ V) {
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= ns * nrhs) return;
+  const int r = gw / ns, v = gw - r * ns;
+  double2 Pp, Qm;
+  if (G) {
+    double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+    if (lane < P) {
+      a = cmul(fagg[(size_t)v * P + lane], G[((size_t)r * 2 * ns + v) * P + lane]);
+      b = cmul(fagg[(size_t)(ns + v) * P + lane], G[((size_t)r * 2 * ns + ns + v) * P + lane]);
+    }
+    Pp = warp_sum(a);
+    Qm = warp_sum(b);
+  } else {
+    Pp = pq_in[(size_t)r * 2 * ns + v];
+    Qm = pq_in[(size_t)r * 2 * ns + ns + v];
+  }
+  if (pq_out && lane == 0) {
+    pq_out[(size_t)r * 2 * ns + v] = Pp;
+    pq_out[(size_t)r * 2 * ns + ns + v] = Qm;
+  }
+  if (!refl) return;
+  const double2 a11 = refl[4 * v], a12 = refl[4 * v + 1], a21 = refl[4 * v + 2], a22 = refl[4 * v + 3];
+  const double2 sp = cadd(cmul(a11, Pp), cmul(a12, Qm));
+  const double2 sm = cadd(cmul(a21, Pp), cmul(a22, Qm));
+  if (sig_out && lane == 0) {
+    sig_out[(size_t)r * 2 * ns + v] = sp;
+    sig_out[(size_t)r * 2 * ns + ns + v] = sm;
+  }
+  if (V && lane < P) {
+    V[((size_t)r * 2 * ns + v) * P + lane] = cmul(udis[(size_t)v * P + lane], sp);
+    V[((size_t)r * 2 * ns + ns + v) * P + lane] = cmul(udis[(size_t)(ns + v) * P + lane], sm);
+  }
+}
+
+__global__ void k_sigma_to_v(int ns, int P, int nrhs, const double2* __restrict__ sig,
+                             const double2* __restrict__ udis, double2* __restrict__ V) {
+  const long long total = (long long)nrhs * 2 * ns * P;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(i % P);
+    const long long rv = i / P;            // r * 2ns + row
+    const int row = (int)(rv % (2 * ns));
+    V[i] = cmul(udis[(size_t)row * P + q], sig[rv]);
+  }
+}
+
+// sigma2+- of the particle-free layered field of each line source (Eq. "sommerfeldsys"):
+// I = exp(-g1 y0 - i lambda (x0 - xc)); sigma2+ = t1 I, sigma2- = t2 I.   sig: [src][2][ns]
+__global__ void k_incident_sigma(int ns, int nsrc, const double* __restrict__ src, double xc,
+                                 const double2* __restrict__ lam, const double2* __restrict__ g1,
+                                 const double2* __restrict__ inc, double2* __restrict__ sig) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ns * nsrc) return;
+  const int s = i / ns, v = i - s * ns;
+  const double sx0 = src[2 * s] - xc, sy0 = src[2 * s + 1];
+  const double2 L = lam[v], g = g1[v];
+  const double2 I = cexp_(-g.x * sy0 + L.y * sx0, -g.y * sy0 - L.x * sx0);
+  sig[(size_t)s * 2 * ns + v] = cmul(inc[2 * v], I);
+  sig[(size_t)s * 2 * ns + ns + v] = cmul(inc[2 * v + 1], I);
+}
+
+__global__ void k_combine(const double2* __restrict__ x, const double2* __restrict__ alpha,
+                          const double2* __restrict__ s_out, double2* __restrict__ y,
+                          long long total, int P, int alpha_only) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 a = alpha[i];
+    if (alpha_only) {
+      y[i] = a;
+    } else {
+      const double2 sa = cmul(s_out[i % P], a);
+      const double2 xv = x[i];
+      y[i] = make_double2(xv.x - sa.x, xv.y - sa.y);
+    }
+  }
+}
+
+// Field in layer 1 (Eq. "layer1"): one warp per target; sigma1 per node from the particle sums
+// P+, Q- (pq, [2][ns]) and the incident density.
+__global__ void k_field(int ns, int ntgt, const double* __restrict__ tgt, double xc,
+                        const double2* __restrict__ lam, const double2* __restrict__ g1,
+                        const double2* __restrict__ ft, const double2* __restrict__ inc,
+                        const double2* __restrict__ refl, const double2* __restrict__ pq,
+                        const double* __restrict__ src, double k1, int which,
+                        double2* __restrict__ out) {
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= ntgt) return;
+  const double xt = tgt[2 * t] - xc, yt = tgt[2 * t + 1];
+  const double sx0 = src[0] - xc, sy0 = src[1];
+  double2 acc = make_double2(0.0, 0.0);
+  for (int v = lane; v < ns; v += 32) {
+    const double2 L = lam[v], g = g1[v];
+    const double2 I = cexp_(-g.x * sy0 + L.y * sx0, -g.y * sy0 - L.x * sx0);
+    const double2 Pp = pq ? pq[v] : make_double2(0.0, 0.0);
+    const double2 Qm = pq ? pq[ns + v] : make_double2(0.0, 0.0);
+    const double2 r11 = ft[4 * v], t21 = ft[4 * v + 1], e = ft[4 * v + 2], q1 = ft[4 * v + 3];
+    double2 sm = cadd(cmul(refl[4 * v + 2], Pp), cmul(refl[4 * v + 3], Qm));   // particle part
+    double2 s1;
+    if (which == LSMS_FIELD_PARTICLE) {
+      s1 = cmul(t21, cadd(Pp, cmul(e, sm)));
+    } else {
+      sm = cadd(sm, cmul(inc[2 * v + 1], I));
+      s1 = cadd(cmul(r11, I), cmul(t21, cadd(Pp, cmul(e, sm))));
+    }
+    const double2 ex = cexp_(-g.x * yt - L.y * xt, -g.y * yt + L.x * xt);   // exp(-g1 y + i l x)
+    acc = cfma(cmul(q1, s1), ex, acc);
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    if (which == LSMS_FIELD_TOTAL) {
+      const double z = k1 * hypot(tgt[2 * t] - src[0], tgt[2 * t + 1] - src[1]);
+      acc.x += -0.25 * y0(z);      // (i/4)(J0 + i Y0)
+      acc.y += 0.25 * j0(z);
+    }
+    out[t] = acc;
+  }
+}
+
+inline int grid_for(long long total, int block) {
+  long long g = (total + block - 1) / block;
+  if (g > 152LL * 32) g = 152LL * 32;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------------
+void launch_scale_in(const double2* x, const double* scale, double2* xs, int nrhs, int n, int P,
+                     cudaStream_t st) {
+  const long long total = (long long)nrhs * n * P;
+  if (total == 0) return;
+  k_scale_in<<<grid_for(total, 256), 256, 0, st>>>(x, scale, xs, total, P);
+}
+
+void launch_translate_f64(const double* cx, const double* cy, int n, int p, double k,
+                          const double2* xs, double2* alpha, int nrhs, cudaStream_t st) {
+  if (n == 0 || nrhs == 0) return;
+  const size_t smem = (size_t)(CH * 32 + TW * CH * HS) * sizeof(double2);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_translate_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  dim3 grid((n + TW - 1) / TW, nrhs);
+  k_translate_f64<<<grid, TW * 32, smem, st>>>(cx, cy, n, p, k, xs, alpha);
+}
+
+void launch_etables(const double* cx, const double* cy, int n, const double2* lam,
+                    const double2* g2, int ns, double d, double2* eagg, double2* edis,
+                    cudaStream_t st) {
+  const long long total = (long long)ns * n;
+  if (total == 0) return;
+  k_etables<<<grid_for(total, 256), 256, 0, st>>>(cx, cy, n, lam, g2, ns, d, eagg, edis);
+}
+
+void launch_zgemm_rows(const double2* A, int M, int K, const double2* B, double2* C, int P,
+                       int nrhs, cudaStream_t st) {
+  if (M == 0 || K == 0 || nrhs == 0) return;
+  const int mt = (M + GT - 1) / GT;
+  const int kt = (K + GT - 1) / GT;
+  int split = (152 * 4 + mt * nrhs - 1) / (mt * nrhs);
+  if (split > kt) split = kt;
+  if (split < 1) split = 1;
+  const int kchunk = ((kt + split - 1) / split) * GT;
+  split = (K + kchunk - 1) / kchunk;
+  dim3 grid(mt, nrhs, split);
+  k_zgemm_rows<<<grid, 256, 0, st>>>(A, M, K, B, C, P, kchunk);
+}
+
+void launch_node_stage(int ns, int P, int nrhs, const double2* G, const double2* fagg,
+                       const double2* pq_in, const double2* refl, const double2* udis,
+                       double2* pq_out, double2* sig_out, double2* V, cudaStream_t st) {
+  const long long threads = (long long)ns * nrhs * 32;
+  if (threads == 0) return;
+  k_node_stage<<<(int)((threads + 255) / 256), 256, 0, st>>>(ns, P, nrhs, G, fagg, pq_in, refl,
+                                                             udis, pq_out, sig_out, V);
+}
+
+void launch_sigma_to_v(int ns, int P, int nrhs, const double2* sig, const double2* udis,
+                       double2* V, cudaStream_t st) {
+  const long long total = (long long)nrhs * 2 * ns * P;
+  if (total == 0) return;
+  k_sigma_to_v<<<grid_for(total, 256), 256, 0, st>>>(ns, P, nrhs, sig, udis, V);
+}
+
+void launch_incident_sigma(int ns, int nsrc, const double* src, double xc, const double2* lam,
+                           const double2* g1, const double2* inc, double2* sig, cudaStream_t st) {
+  const int total = ns * nsrc;
+  if (total == 0) return;
+  k_incident_sigma<<<(total + 255) / 256, 256, 0, st>>>(ns, nsrc, src, xc, lam, g1, inc, sig);
+}
+
+void launch_combine(const double2* x, const double2* alpha, const double2* s_out, double2* y,
+                    int nrhs, int n, int P, int alpha_only, cudaStream_t st) {
+  const long long total = (long long)nrhs * n * P;
+  if (total == 0) return;
+  k_combine<<<grid_for(total, 256), 256, 0, st>>>(x, alpha, s_out, y, total, P, alpha_only);
+}
+
+void launch_field(int ns, int ntgt, const double* tgt, double xc, const double2* lam,
+                  const double2* g1, const double2* fieldtab, const double2* inc,
+                  const double2* refl, const double2* pq, const double* src, double k1,
+                  int which, double2* out, cudaStream_t st) {
+  if (ntgt == 0) return;
+  const long long threads = (long long)ntgt * 32;
+  k_field<<<(int)((threads + 127) / 128), 128, 0, st>>>(ns, ntgt, tgt, xc, lam, g1, fieldtab, inc,
+                                                        refl, pq, src, k1, which, out);
+}

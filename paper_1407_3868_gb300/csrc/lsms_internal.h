@@ -1,0 +1,139 @@
+// Internal declarations of liblsms: the context, host-side setup and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "lsms.h"
+
+using cplx = std::complex<double>;
+
+#define LSMS_MAX_P 15          // P = 2p + 1 <= 31 fits one warp of lanes over orders
+
+// ------------------------------------------------------------------------------------------
+// Device buffer owned by a context (grown on demand, never shrunk).
+// ------------------------------------------------------------------------------------------
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+// Per-node constants of the contour, FP64 (Sec. 2 Eq. "sommerfeldsys", Sec. 5.1).
+struct NodeTables {
+  std::vector<cplx> lam, wt;        // nodes and weights
+  std::vector<cplx> g1, g2, g3;     // gamma_i(lambda)
+  std::vector<cplx> refl;           // [ns][4]: a11 a12 a21 a22 of sigma2 = a * (P, Q)
+  std::vector<cplx> inc;            // [ns][2]: sigma2+ = t1 I, sigma2- = t2 I (particle free)
+  std::vector<cplx> field;          // [ns][4]: R11, tau21, e, w/(4 pi gamma1)
+  std::vector<cplx> fagg;           // [2 ns][P]: c_n w-^n (rows < ns), c_n w+^n (rows >= ns)
+  std::vector<cplx> udis;           // [2 ns][P]: w/(4 pi g2) i^m w-^m, ... w+^m
+};
+
+struct lsms_ctx {
+  // medium and discretisation
+  double k1 = 0, k2 = 0, k3 = 0, d = 0, kp = 0, R = 0;
+  int p = 0, P = 0, precision = 0;
+  lsms_contour contour{};
+  int ns = 0;
+  NodeTables nodes;
+  std::vector<cplx> S;              // Mie diagonal, P
+  std::vector<double> hscale;       // |H_n(k2 R)|, P
+
+  // discs
+  int n = -1;                       // -1: set_particles not called yet
+  double xc = 0.0;                  // x shift applied on the device (layout midpoint)
+  std::vector<double> cx, cy;       // centres as given
+
+  // device copies of the constant tables
+  double2* d_lam = nullptr;         // [ns]
+  double2* d_g1 = nullptr;          // [ns]
+  double2* d_g2 = nullptr;          // [ns]
+  double2* d_refl = nullptr;        // [ns][4]
+  double2* d_inc = nullptr;         // [ns][2]
+  double2* d_field = nullptr;       // [ns][4]
+  double2* d_fagg = nullptr;        // [2ns][P]
+  double2* d_udis = nullptr;        // [2ns][P]
+  double* d_scale_in = nullptr;     // [2][P]: 1 (unscaled), 1/|H_n| (scaled)
+  double* d_hscale = nullptr;       // [P]: |H_n(k2 R)|
+  double2* d_scale_out = nullptr;   // [2][P]: S_n, |H_n| S_n
+
+  // per-layout device data
+  double* d_cx = nullptr;           // centred x, [n]
+  double* d_cy = nullptr;           // [n]
+  double2* d_eagg = nullptr;        // [2ns][n]: exp(g2 y - i l x) rows, then exp(-g2 (y+d) - i l x)
+  double2* d_edis = nullptr;        // [n][2ns]: exp(g2 y + i l x), then exp(-g2 (y+d) + i l x)
+  // low-precision copies for the mixed path (split BF16 hi/lo planes, see mixed.cu)
+  void* d_eagg_lp = nullptr;
+  void* d_edis_lp = nullptr;
+  void* d_lp_misc = nullptr;
+  DevBuf ws_lp;
+
+  // workspaces
+  DevBuf ws_x, ws_y, ws_xs, ws_alpha, ws_g, ws_v, ws_pq, ws_sig, ws_aux;
+  DevBuf gm_v, gm_h, gm_small, gm_x, gm_r, gm_w;
+  double* h_pinned = nullptr;       // small pinned host scratch for residual polling
+
+  cudaStream_t stream = nullptr;    // internal stream of the host-pointer entry points
+
+  // optional timing of the operator's parts (CUDA events on the launching stream)
+  int timing = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  int last_launches = 0;            // kernels launched by the last operator application
+
+  // solution of the last lsms_solve (device, unscaled beta), per source
+  int n_src = 0;
+  std::vector<double> src_xy;
+  DevBuf sol;
+
+  std::string err;
+};
+
+// ------------------------------------------------------------------------------------------
+// Host setup (host_setup.cpp)
+// ------------------------------------------------------------------------------------------
+int build_contour(const lsms_contour& c, double k1, double k2, double k3, std::vector<cplx>& lam,
+                  std::vector<cplx>& wt, std::string& err);
+std::vector<double> contour_panel_breaks(int n_panels, const double* ks, int nk, double b,
+                                         double t_max);
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+std::vector<cplx> mie_diagonal(int p, double k2, double kp, double R);
+std::vector<double> hankel_scale(int p, double k2, double R);
+cplx gamma_of(cplx lam, double k);
+void build_node_tables(lsms_ctx* c);
+int validate_geometry(const lsms_ctx* c, int n, const double* xy, std::string& err);
+
+// ------------------------------------------------------------------------------------------
+// Kernel launchers (kernels_f64.cu).  All arrays are device pointers; all launches are
+// asynchronous on `st`.  Coefficient arrays are [nrhs][N][P] (complex as double2).
+// ------------------------------------------------------------------------------------------
+void launch_scale_in(const double2* x, const double* scale, double2* xs, int nrhs, int n, int P,
+                     cudaStream_t st);
+void launch_translate_f64(const double* cx, const double* cy, int n, int p, double k,
+                          const double2* xs, double2* alpha, int nrhs, cudaStream_t st);
+void launch_etables(const double* cx, const double* cy, int n, const double2* lam,
+                    const double2* g2, int ns, double d, double2* eagg, double2* edis,
+                    cudaStream_t st);
+// C[r][m][n] += sum_k A[m][k] B[r][k][n];  C must be pre-zeroed (split-K uses atomics)
+void launch_zgemm_rows(const double2* A, int M, int K, const double2* B, double2* C, int P,
+                       int nrhs, cudaStream_t st);
+// per node: P,Q from G (if G) else from pq_in; optional outputs pq_out, sig_out, V
+void launch_node_stage(int ns, int P, int nrhs, const double2* G, const double2* fagg,
+                       const double2* pq_in, const double2* refl, const double2* udis,
+                       double2* pq_out, double2* sig_out, double2* V, cudaStream_t st);
+// per node: sigma from given sigma arrays -> V (for lsms_disaggregate)
+void launch_sigma_to_v(int ns, int P, int nrhs, const double2* sig, const double2* udis,
+                       double2* V, cudaStream_t st);
+// incident densities of line sources: sig [nsrc][2][ns]
+void launch_incident_sigma(int ns, int nsrc, const double* src, double xc, const double2* lam,
+                           const double2* g1, const double2* inc, double2* sig, cudaStream_t st);
+// y = x - s_out * alpha   (or y = alpha if alpha_only)
+void launch_combine(const double2* x, const double2* alpha, const double2* s_out, double2* y,
+                    int nrhs, int n, int P, int alpha_only, cudaStream_t st);
+// field in layer 1 at targets
+void launch_field(int ns, int ntgt, const double* tgt, double xc, const double2* lam,
+                  const double2* g1, const double2* fieldtab, const double2* inc,
+                  const double2* refl, const double2* pq, const double* src, double k1,
+                  int which, double2* out, cudaStream_t st);

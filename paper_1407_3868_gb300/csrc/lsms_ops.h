@@ -1,0 +1,33 @@
+// Operations shared by the translation units of liblsms (abi.cu, gmres.cu, mixed.cu).
+#pragma once
+
+#include <string>
+
+#include "lsms_internal.h"
+
+int ctx_fail(lsms_ctx* c, int code, const std::string& msg);
+int ensure(lsms_ctx* c, DevBuf& b, size_t bytes);
+int check_cuda(lsms_ctx* c, const char* where);
+int need_particles(lsms_ctx* c);
+int validate_sources(lsms_ctx* c, int nsrc, const double* xy);
+
+// y = x - s_out (T + R)(s_in x) on device buffers, flags LSMS_APPLY_*.
+int apply_device(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags, cudaStream_t st);
+// reflected coupling alpha += R xs, FP64
+int reflection_f64(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st);
+// a_inc for nsrc line sources (device source array), out [nsrc][N][P]
+int incident_device(lsms_ctx* c, int nsrc, const double* d_src, double2* out, cudaStream_t st);
+
+// mixed-precision contour contractions (mixed.cu)
+int build_lowp_tables(lsms_ctx* c);
+// alpha = T xs in FP32 arithmetic (sums of the per-split FP32 partials accumulated in FP64)
+int translate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st);
+int aggregate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* G, cudaStream_t st);
+int disaggregate_mixed(lsms_ctx* c, int nrhs, const double2* V, double2* alpha, cudaStream_t st);
+int reflection_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st);
+
+// small device helpers (gmres.cu)
+void launch_diag_mul(const double2* x, const double2* s, double2* y, long long total, int P,
+                     cudaStream_t st);
+void launch_diag_scale(const double2* x, const double* s, double2* y, long long total, int P,
+                       cudaStream_t st);

@@ -1,0 +1,337 @@
+// Mixed-precision pieces of the operator: FP32 Graf translation (Sec. 3.2 Lemma 3.1) and the
+// low-precision layout tables used by the mixed contour contractions.
+//
+// Translation in FP32.  Per pair the phase k2 rho is formed in float-float arithmetic from
+// float-float centres (about 44 significant bits, so the phase of pairs thousands of wavelengths
+// apart is still exact to ~1e-10 rad), reduced modulo 2 pi, and H_0, H_1 are evaluated from
+// Hankel's asymptotic expansion (Abramowitz & Stegun 9.2.5-9.2.10, four terms, error < 3e-8 for
+// z >= 25).  Pairs closer than z = 25 (a few per disc) use the FP64 library J0/Y0/J1/Y1.  Higher
+// orders follow from the forward recurrence in FP32.  The contraction is a register-blocked
+// Toeplitz product: a lane owns VB consecutive output orders of one target disc and slides a window
+// of 2 VB - 1 sequence values over the source orders, so each staged value feeds VB complex FMAs.
+#include <cmath>
+
+#include "lsms_internal.h"
+#include "lsms_ops.h"
+
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// float-float arithmetic (Dekker / Knuth error-free transformations)
+// ---------------------------------------------------------------------------------------------
+struct ffl {
+  float hi, lo;
+};
+__device__ __forceinline__ ffl two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+__device__ __forceinline__ ffl fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ ffl ff_add(ffl a, ffl b) {
+  ffl s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ ffl ff_sub(ffl a, ffl b) { return ff_add(a, {-b.hi, -b.lo}); }
+__device__ __forceinline__ ffl ff_mul(ffl a, ffl b) {
+  const float p = a.hi * b.hi;
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ffl ff_mul_f(ffl a, float b) {
+  const float p = a.hi * b;
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ffl ff_sqrt(ffl a) {   // Karp: s + (a - s^2) / (2 s)
+  const float s = sqrtf(a.hi);
+  const float p = s * s;
+  const float e = __fmaf_rn(s, s, -p);
+  const ffl r = ff_sub(a, {p, e});
+  return fast_two_sum(s, r.hi / (2.0f * s));
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+constexpr float kTwoPiHi = 6.28318548202514648f;      // float(2 pi)
+constexpr float kTwoPiLo = -1.74845553146951427e-07f;  // 2 pi - float(2 pi)
+constexpr float kInvTwoPi = 0.159154943091895336f;
+constexpr float kZAsym = 25.0f;
+
+// H_0(z), H_1(z) for z >= 25 from Hankel's expansion with the phase theta = z mod 2 pi:
+// H_nu(z) ~ sqrt(2/(pi z)) exp(i (z - nu pi/2 - pi/4)) sum_k i^k a_k(nu) z^-k,
+// a_k(nu) = prod_{j<=k} (4 nu^2 - (2j-1)^2) / (k! 8^k).
+__device__ __forceinline__ void hankel01_asym(float zf, float theta, float2& h0, float2& h1) {
+  float s, c;
+  sincosf(theta, &s, &c);
+  const float iz = 1.0f / zf, iz2 = iz * iz;
+  const float amp = sqrtf(0.636619772367581343f * iz) * 0.707106781186547524f;
+  // nu = 0: a1 = -1/8, a2 = 9/128, a3 = -225/3072, a4 = 11025/98304
+  const float p0 = 1.0f + iz2 * (-0.0703125f + iz2 * 0.112152099609375f);
+  const float q0 = iz * (-0.125f + iz2 * 0.0732421875f);
+  // nu = 1: a1 = 3/8, a2 = -15/128, a3 = 315/3072, a4 = -14175/98304
+  const float p1 = 1.0f + iz2 * (0.1171875f + iz2 * -0.144195556640625f);
+  const float q1 = iz * (0.375f + iz2 * -0.1025390625f);
+  // exp(i(z - pi/4)) = (c + s + i (s - c)) / sqrt2 ; exp(i(z - 3pi/4)) = (s - c - i (s + c)) / sqrt2
+  const float2 e0 = make_float2((c + s) * amp, (s - c) * amp);
+  const float2 e1 = make_float2((s - c) * amp, -(s + c) * amp);
+  h0 = cmulf(e0, make_float2(p0, q0));
+  h1 = cmulf(e1, make_float2(p1, q1));
+}
+
+// Sequence h[HOFF + s + 2p] = H_s(k rho) exp(i s phi), s = -2p..2p, for centres a (target) and
+// b (source) given as float-float (x_hi, x_lo, y_hi, y_lo).
+constexpr int HOFF = 32;
+constexpr int MHS = 97;   // > HOFF + 4p + 1 (<= 93); odd so the 32 lanes' slots fall in distinct banks
+
+__device__ void hankel_sequence_f32(float4 a, float4 b, ffl k, int p, float2* h) {
+  const ffl dx = ff_sub({a.x, a.y}, {b.x, b.y});
+  const ffl dy = ff_sub({a.z, a.w}, {b.z, b.w});
+  const ffl r2 = ff_add(ff_mul(dx, dx), ff_mul(dy, dy));
+  const ffl rho = ff_sqrt(r2);
+  const ffl z = ff_mul(rho, k);
+  const float zf = z.hi + z.lo;
+  const float irho = 1.0f / rho.hi;
+  const float2 e1 = make_float2((dx.hi + dx.lo) * irho, (dy.hi + dy.lo) * irho);
+  float2 h0, h1;
+  if (zf >= kZAsym) {
+    const float nq = rintf(z.hi * kInvTwoPi);
+    const ffl t = ff_sub(z, ff_add(ff_mul_f({kTwoPiHi, 0.0f}, nq), ff_mul_f({kTwoPiLo, 0.0f}, nq)));
+    hankel01_asym(zf, t.hi + t.lo, h0, h1);
+  } else {
+    const double zd = (double)z.hi + (double)z.lo;
+    h0 = make_float2((float)j0(zd), (float)y0(zd));
+    h1 = make_float2((float)j1(zd), (float)y1(zd));
+  }
+  const int c0 = HOFF + 2 * p;
+  h[c0] = h0;
+  float2 hm = h0, hq = h1, eq = e1;
+  const float iz = 1.0f / zf;
+  for (int q = 1; q <= 2 * p; ++q) {
+    const float2 v = cmulf(hq, eq);
+    h[c0 + q] = v;
+    const float2 u = cmulf(hq, make_float2(eq.x, -eq.y));
+    h[c0 - q] = (q & 1) ? make_float2(-u.x, -u.y) : u;
+    if (q < 2 * p) {
+      const float f = 2.0f * q * iz;
+      const float2 hn = make_float2(f * hq.x - hm.x, f * hq.y - hm.y);
+      hm = hq;
+      hq = hn;
+      eq = cmulf(eq, e1);
+    }
+  }
+}
+
+constexpr int MW = 4;    // warps per CTA
+constexpr int MT = 8;    // target discs per warp (4 lanes each)
+constexpr int MCH = 32;  // sources staged per chunk
+
+// part[split][r][l][nu] = sum over the split's sources m != l of T^{lm} xs^m   (FP32)
+template <int VB>
+__global__ void __launch_bounds__(MW * 32)
+k_translate_f32(const float4* __restrict__ cff, int n, int p, float k_hi, float k_lo,
+                const double2* __restrict__ xs, float2* __restrict__ part, int src_per_split,
+                int nrhs) {
+  __shared__ float2 sb[MCH][33];
+  __shared__ float4 sc[MCH];
+  extern __shared__ float2 sh[];       // [MW][32 pair slots][MHS]
+  const int P = 2 * p + 1;
+  const int PB = ((P + VB - 1) / VB) * VB;   // orders padded to whole blocks
+  const int r = blockIdx.z;
+  const int split = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = lane >> 2, vb = lane & 3;
+  const int l = (blockIdx.x * MW + warp) * MT + t;
+  const bool lvalid = l < n;
+  const float4 ct = lvalid ? cff[l] : make_float4(0.f, 0.f, 0.f, 0.f);
+  float2* hw = sh + (size_t)warp * 32 * MHS;
+  // zero the pair slots once: the generator only writes [HOFF, HOFF + 4p]
+  for (int i = lane; i < 32 * MHS; i += 32) hw[i] = make_float2(0.f, 0.f);
+  __syncwarp();
+  float2 acc[VB];
+#pragma unroll
+  for (int i = 0; i < VB; ++i) acc[i] = make_float2(0.f, 0.f);
+  const int jbeg = split * src_per_split;
+  const int jend = min(n, jbeg + src_per_split);
+  const double2* xr = xs + (size_t)r * n * P;
+  const ffl kf = {k_hi, k_lo};
+  for (int j0c = jbeg; j0c < jend; j0c += MCH) {
+    const int cnt = min(MCH, jend - j0c);
+    __syncthreads();
+    for (int i = threadIdx.x; i < MCH * 32; i += blockDim.x) {
+      const int s = i >> 5, q = i & 31;
+      float2 v = make_float2(0.f, 0.f);
+      if (s < cnt && q < P) {
+        const double2 d = xr[(size_t)(j0c + s) * P + q];
+        v = make_float2((float)d.x, (float)d.y);
+      }
+      sb[s][q] = v;
+    }
+    if (threadIdx.x < cnt) sc[threadIdx.x] = cff[j0c + threadIdx.x];
+    __syncthreads();
+    for (int s0 = 0; s0 < cnt; s0 += 4) {
+      // generation: lane (t, s4) -> pair (l, j0c + s0 + s4)
+      {
+        const int js = s0 + vb;
+        float2* h = hw + lane * MHS;
+        if (js < cnt && lvalid && j0c + js != l) {
+          hankel_sequence_f32(ct, sc[js], kf, p, h);
+        } else {
+          for (int q = 0; q <= 4 * p; ++q) h[HOFF + q] = make_float2(0.f, 0.f);
+        }
+      }
+      __syncwarp();
+      // contraction: lane (t, vb) owns outputs nu = VB*vb + i
+      const int nq4 = min(4, cnt - s0);
+      for (int q4 = 0; q4 < nq4; ++q4) {
+        // hb[j] = h_{n - nu} with n = j - (VB - 1) + nb ... see below
+        const float2* hs = hw + (t * 4 + q4) * MHS + HOFF + 2 * p - VB * vb;   // hs[n - i] = h_{n - (VB vb + i)}
+        const float2* bs = sb[s0 + q4];
+        float2 win[2 * VB - 1];
+        // window for block nb: win[j] = hs[nb + j - (VB - 1)], j = 0 .. 2VB-2
+#pragma unroll
+        for (int j = 0; j < VB - 1; ++j) win[j] = hs[j - (VB - 1)];
+        for (int nb = 0; nb < PB; nb += VB) {
+#pragma unroll
+          for (int j = 0; j < VB; ++j) win[VB - 1 + j] = hs[nb + j];
+#pragma unroll
+          for (int u = 0; u < VB; ++u) {
+            const float2 b = bs[nb + u];
+#pragma unroll
+            for (int i = 0; i < VB; ++i) {
+              const float2 hv = win[VB - 1 + u - i];
+              acc[i].x = __fmaf_rn(hv.x, b.x, acc[i].x);
+              acc[i].x = __fmaf_rn(-hv.y, b.y, acc[i].x);
+              acc[i].y = __fmaf_rn(hv.x, b.y, acc[i].y);
+              acc[i].y = __fmaf_rn(hv.y, b.x, acc[i].y);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < VB - 1; ++j) win[j] = win[VB + j];
+        }
+      }
+      __syncwarp();
+    }
+  }
+  if (lvalid) {
+    float2* out = part + (((size_t)split * nrhs + r) * n + l) * P;
+#pragma unroll
+    for (int i = 0; i < VB; ++i) {
+      const int nu = VB * vb + i;
+      if (nu < P) out[nu] = acc[i];
+    }
+  }
+}
+
+// alpha[r][l][nu] = sum_split part[split][r][l][nu]   (double accumulation)
+__global__ void k_reduce_parts(const float2* __restrict__ part, int nsplit, long long len,
+                               double2* __restrict__ alpha) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    double ax = 0.0, ay = 0.0;
+    for (int s = 0; s < nsplit; ++s) {
+      const float2 v = part[(size_t)s * len + i];
+      ax += v.x;
+      ay += v.y;
+    }
+    alpha[i] = make_double2(ax, ay);
+  }
+}
+
+__global__ void k_centres_ff(const double* __restrict__ cx, const double* __restrict__ cy, int n,
+                             float4* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const float xh = (float)cx[j], yh = (float)cy[j];
+  out[j] = make_float4(xh, (float)(cx[j] - (double)xh), yh, (float)(cy[j] - (double)yh));
+}
+
+template <int VB>
+void launch_vb(dim3 grid, size_t smem, cudaStream_t st, const float4* cff, int n, int p, float kh,
+               float kl, const double2* xs, float2* part, int sps, int nrhs) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_translate_f32<VB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_translate_f32<VB><<<grid, MW * 32, smem, st>>>(cff, n, p, kh, kl, xs, part, sps, nrhs);
+}
+
+}  // namespace
+
+int build_lowp_tables(lsms_ctx* c) {
+  if (c->d_lp_misc) cudaFree(c->d_lp_misc);
+  c->d_lp_misc = nullptr;
+  if (cudaMalloc(&c->d_lp_misc, (size_t)(c->n > 0 ? c->n : 1) * sizeof(float4)) != cudaSuccess) {
+    cudaGetLastError();
+    return ctx_fail(c, LSMS_ERR_OOM, "cudaMalloc failed for the float-float centres");
+  }
+  if (c->n > 0)
+    k_centres_ff<<<(c->n + 255) / 256, 256, 0, c->stream>>>(c->d_cx, c->d_cy, c->n, (float4*)c->d_lp_misc);
+  cudaStreamSynchronize(c->stream);
+  return check_cuda(c, "build_lowp_tables");
+}
+
+// Splits of the source range so that the grid covers the GPU several times.
+static int translate_splits(int n, int nrhs) {
+  const int tiles = (n + MW * MT - 1) / (MW * MT);
+  int s = (152 * 3 * 4 + tiles * nrhs - 1) / (tiles * nrhs);
+  const int max_s = (n + MCH - 1) / MCH;
+  if (s > max_s) s = max_s;
+  if (s < 1) s = 1;
+  return s;
+}
+
+int translate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st) {
+  const int n = c->n, p = c->p, P = c->P;
+  if (n == 0 || nrhs == 0) return LSMS_OK;
+  int splits = translate_splits(n, nrhs);
+  int sps = (n + splits - 1) / splits;
+  sps = ((sps + MCH - 1) / MCH) * MCH;
+  splits = (n + sps - 1) / sps;
+  const long long len = (long long)nrhs * n * P;
+  int rc;
+  if ((rc = ensure(c, c->ws_lp, (size_t)splits * len * sizeof(float2)))) return rc;
+  float2* part = (float2*)c->ws_lp.ptr;
+  const float kh = (float)c->k2, kl = (float)(c->k2 - (double)kh);
+  dim3 grid((n + MW * MT - 1) / (MW * MT), splits, nrhs);
+  const size_t smem = (size_t)MW * 32 * MHS * sizeof(float2);
+  const float4* cff = (const float4*)c->d_lp_misc;
+  const int vb = (P + 3) / 4;
+  switch (vb) {
+    case 1: launch_vb<1>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 2: launch_vb<2>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 3: launch_vb<3>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 4: launch_vb<4>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 5: launch_vb<5>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 6: launch_vb<6>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 7: launch_vb<7>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    default: launch_vb<8>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+  }
+  long long g = (len + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  k_reduce_parts<<<(int)g, 256, 0, st>>>(part, splits, len, alpha);
+  return check_cuda(c, "translate_mixed");
+}
+
+int aggregate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* G, cudaStream_t st) {
+  launch_zgemm_rows(c->d_eagg, 2 * c->ns, c->n, xs, G, c->P, nrhs, st);
+  return LSMS_OK;
+}
+
+int disaggregate_mixed(lsms_ctx* c, int nrhs, const double2* V, double2* alpha, cudaStream_t st) {
+  launch_zgemm_rows(c->d_edis, c->n, 2 * c->ns, V, alpha, c->P, nrhs, st);
+  return LSMS_OK;
+}
+
+int reflection_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st) {
+  return reflection_f64(c, nrhs, xs, alpha, st);
+}

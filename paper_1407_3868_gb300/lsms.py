@@ -1,0 +1,292 @@
+"""ctypes binding of liblsms (include/lsms.h): argument marshalling only.
+
+Every computation happens in the CUDA library.  If the library is missing this module raises: there
+is no CPU fallback.  Host arrays are NumPy complex128 (interleaved, the layout the ABI expects);
+device entry points take torch tensors (complex128, CUDA) and a stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "liblsms.so")
+
+LSMS_FP64, LSMS_MIXED = 0, 1
+APPLY_SCALED, APPLY_MIXED, APPLY_NO_TRANSLATION, APPLY_NO_REFLECTION, APPLY_ALPHA = 1, 2, 4, 8, 16
+FIELD_TOTAL, FIELD_SCATTERED, FIELD_PARTICLE = 0, 1, 2
+STATUS = {0: "OK", -1: "ARG", -2: "GEOMETRY", -3: "NOT_CONVERGED", -4: "NONFINITE", -5: "OOM",
+          -6: "CUDA", -7: "STATE"}
+EXPORTS = ["lsms_create", "lsms_set_particles", "lsms_apply", "lsms_apply_ex", "lsms_apply_dev",
+           "lsms_translate", "lsms_aggregate", "lsms_reflect", "lsms_disaggregate", "lsms_incident",
+           "lsms_get_contour", "lsms_get_scattering", "lsms_num_nodes", "lsms_num_particles",
+           "lsms_solve", "lsms_eval_field", "lsms_last_error", "lsms_destroy",
+           "lsms_build_contour", "lsms_scattering_diagonal", "lsms_check_geometry",
+           "lsms_set_timing", "lsms_last_timing"]
+
+
+class LsmsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"lsms error {code} ({STATUS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class Contour(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int), ("b", ctypes.c_double), ("t_max", ctypes.c_double),
+                ("panel_order", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("rel_res_fp64", ctypes.c_double), ("history", ctypes.POINTER(ctypes.c_double)),
+                ("history_cap", ctypes.c_int), ("n_history", ctypes.c_int)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load liblsms.so (built by paper_1407_3868_gb300.build).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"liblsms.so not found at {path}: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    i, d = ctypes.c_int, ctypes.c_double
+    sig = {
+        "lsms_create": (i, [d, d, d, d, d, d, i, ctypes.POINTER(Contour), i, ctypes.POINTER(_P)]),
+        "lsms_set_particles": (i, [_P, i, _D]),
+        "lsms_apply": (i, [_P, i, _D, _D]),
+        "lsms_apply_ex": (i, [_P, i, _D, _D, i]),
+        "lsms_apply_dev": (i, [_P, i, _P, _P, i, _P]),
+        "lsms_translate": (i, [_P, i, _D, _D, i]),
+        "lsms_aggregate": (i, [_P, i, _D, _D, _D, i]),
+        "lsms_reflect": (i, [_P, i, _D, _D, _D, _D]),
+        "lsms_disaggregate": (i, [_P, i, _D, _D, _D, i]),
+        "lsms_incident": (i, [_P, i, _D, _D]),
+        "lsms_get_contour": (i, [_P, _D, _D]),
+        "lsms_get_scattering": (i, [_P, _D]),
+        "lsms_num_nodes": (i, [_P]),
+        "lsms_num_particles": (i, [_P]),
+        "lsms_solve": (i, [_P, i, _D, d, i, _D, _D, ctypes.POINTER(SolveInfo)]),
+        "lsms_eval_field": (i, [_P, i, i, _D, i, _D]),
+        "lsms_last_error": (ctypes.c_char_p, [_P]),
+        "lsms_destroy": (None, [_P]),
+        "lsms_build_contour": (i, [ctypes.POINTER(Contour), d, d, d, _D, _D]),
+        "lsms_scattering_diagonal": (i, [i, d, d, d, _D]),
+        "lsms_check_geometry": (i, [d, d, i, _D]),
+        "lsms_set_timing": (i, [_P, i]),
+        "lsms_last_timing": (i, [_P, _D, _D, ctypes.POINTER(ctypes.c_int)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_D)
+
+
+def _c128(a, shape=None) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+class Context:
+    """One lsms context (lsms_create ... lsms_destroy)."""
+
+    def __init__(self, k1, k2, k3, d, kp, radius, p, n_nodes, b=0.0, t_max=0.0, panel_order=0,
+                 precision=LSMS_FP64):
+        self.lib = load()
+        self.p = p
+        self.P = 2 * p + 1
+        c = Contour(n_nodes, b, t_max, panel_order)
+        h = _P()
+        rc = self.lib.lsms_create(k1, k2, k3, d, kp, radius, p, ctypes.byref(c), precision,
+                                  ctypes.byref(h))
+        if rc != 0:
+            raise LsmsError(rc, self.lib.lsms_last_error(None).decode())
+        self.h = h
+        self.n = -1
+        self.ns = self.lib.lsms_num_nodes(h)
+
+    # -- lifetime ------------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lsms_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc):
+        if rc != 0:
+            raise LsmsError(rc, self.lib.lsms_last_error(self.h).decode())
+        return rc
+
+    # -- setup -----------------------------------------------------------------------------------
+    def set_particles(self, centres):
+        c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 2)
+        self._check(self.lib.lsms_set_particles(self.h, c.shape[0], _dptr(c)))
+        self.n = c.shape[0]
+
+    def contour(self):
+        lam = np.zeros(self.ns, dtype=np.complex128)
+        wt = np.zeros(self.ns, dtype=np.complex128)
+        self._check(self.lib.lsms_get_contour(self.h, _dptr(lam), _dptr(wt)))
+        return lam, wt
+
+    def scattering(self):
+        s = np.zeros(self.P, dtype=np.complex128)
+        self._check(self.lib.lsms_get_scattering(self.h, _dptr(s)))
+        return s
+
+    # -- operator and its steps ------------------------------------------------------------------
+    def _coeffs(self, x):
+        x = _c128(x)
+        nrhs = x.size // (self.n * self.P) if self.n > 0 else (x.shape[0] if x.ndim == 3 else 1)
+        return _c128(x, (nrhs, self.n, self.P)), nrhs
+
+    def apply(self, x, flags=0):
+        x, nrhs = self._coeffs(x)
+        y = np.zeros_like(x)
+        self._check(self.lib.lsms_apply_ex(self.h, nrhs, _dptr(x), _dptr(y), flags))
+        return y
+
+    def apply_default(self, x):
+        x, nrhs = self._coeffs(x)
+        y = np.zeros_like(x)
+        self._check(self.lib.lsms_apply(self.h, nrhs, _dptr(x), _dptr(y)))
+        return y
+
+    def apply_dev(self, x, y, flags=0, stream=None):
+        """x, y: CUDA complex128 torch tensors of shape (nrhs, N, P); asynchronous on `stream`."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        nrhs = x.numel() // (self.n * self.P)
+        self._check(self.lib.lsms_apply_dev(self.h, nrhs, ctypes.c_void_p(x.data_ptr()),
+                                            ctypes.c_void_p(y.data_ptr()), flags,
+                                            ctypes.c_void_p(stream.cuda_stream)))
+
+    def translate(self, beta, precision=LSMS_FP64):
+        x, nrhs = self._coeffs(beta)
+        a = np.zeros_like(x)
+        self._check(self.lib.lsms_translate(self.h, nrhs, _dptr(x), _dptr(a), precision))
+        return a
+
+    def aggregate(self, beta, precision=LSMS_FP64):
+        x, nrhs = self._coeffs(beta)
+        pp = np.zeros((nrhs, self.ns), dtype=np.complex128)
+        qm = np.zeros_like(pp)
+        self._check(self.lib.lsms_aggregate(self.h, nrhs, _dptr(x), _dptr(pp), _dptr(qm), precision))
+        return pp, qm
+
+    def reflect(self, p_plus, q_minus):
+        pp = _c128(p_plus).reshape(-1, self.ns)
+        qm = _c128(q_minus).reshape(-1, self.ns)
+        sp, sm = np.zeros_like(pp), np.zeros_like(qm)
+        self._check(self.lib.lsms_reflect(self.h, pp.shape[0], _dptr(pp), _dptr(qm), _dptr(sp), _dptr(sm)))
+        return sp, sm
+
+    def disaggregate(self, s_plus, s_minus, precision=LSMS_FP64):
+        sp = _c128(s_plus).reshape(-1, self.ns)
+        sm = _c128(s_minus).reshape(-1, self.ns)
+        a = np.zeros((sp.shape[0], self.n, self.P), dtype=np.complex128)
+        self._check(self.lib.lsms_disaggregate(self.h, sp.shape[0], _dptr(sp), _dptr(sm), _dptr(a), precision))
+        return a
+
+    def incident(self, sources):
+        s = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 2)
+        a = np.zeros((s.shape[0], self.n, self.P), dtype=np.complex128)
+        self._check(self.lib.lsms_incident(self.h, s.shape[0], _dptr(s), _dptr(a)))
+        return a
+
+    def set_timing(self, enable=True):
+        self._check(self.lib.lsms_set_timing(self.h, 1 if enable else 0))
+
+    def last_timing(self):
+        """(ms of the translation, ms of the reflected coupling, kernels launched) of the last apply."""
+        a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        self._check(self.lib.lsms_last_timing(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
+        return a.value, b.value, n.value
+
+    # -- solve and fields --------------------------------------------------------------------------
+    def solve(self, sources, tol=1e-10, maxiter=500, x0=None, history=0, raise_on_error=True):
+        s = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 2)
+        beta = np.zeros((s.shape[0], self.n, self.P), dtype=np.complex128)
+        info = SolveInfo()
+        hist = np.zeros(max(history, 1))
+        info.history = hist.ctypes.data_as(_D)
+        info.history_cap = history
+        x0a = None if x0 is None else _c128(x0, beta.shape)
+        rc = self.lib.lsms_solve(self.h, s.shape[0], _dptr(s), tol, maxiter, _dptr(x0a), _dptr(beta),
+                                 ctypes.byref(info))
+        if raise_on_error:
+            self._check(rc)
+        out = dict(status=rc, iters=info.iters, outer_iters=info.outer_iters, rel_res=info.rel_res,
+                   rel_res_fp64=info.rel_res_fp64, history=hist[:info.n_history].copy())
+        return beta, out
+
+    def eval_field(self, targets, src_index=0, which=FIELD_TOTAL):
+        t = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 2)
+        u = np.zeros(t.shape[0], dtype=np.complex128)
+        self._check(self.lib.lsms_eval_field(self.h, src_index, t.shape[0], _dptr(t), which, _dptr(u)))
+        return u
+
+
+def build_contour(n_nodes, k1, k2, k3, b=0.0, t_max=0.0, panel_order=0):
+    """Host-only: the library's contour nodes and weights (no GPU needed)."""
+    lib = load()
+    lam = np.zeros(n_nodes, dtype=np.complex128)
+    wt = np.zeros(n_nodes, dtype=np.complex128)
+    c = Contour(n_nodes, b, t_max, panel_order)
+    rc = lib.lsms_build_contour(ctypes.byref(c), k1, k2, k3, _dptr(lam), _dptr(wt))
+    if rc != 0:
+        raise LsmsError(rc, lib.lsms_last_error(None).decode())
+    return lam, wt
+
+
+def scattering_diagonal(p, k2, kp, radius):
+    """Host-only: the library's disc scattering matrix diagonal S_n, n = -p..p."""
+    lib = load()
+    s = np.zeros(2 * p + 1, dtype=np.complex128)
+    rc = lib.lsms_scattering_diagonal(p, k2, kp, radius, _dptr(s))
+    if rc != 0:
+        raise LsmsError(rc, lib.lsms_last_error(None).decode())
+    return s
+
+
+def check_geometry(d, radius, centres) -> int:
+    """Host-only: LSMS_OK (0) or a negative status for a disc layout."""
+    c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 2)
+    return load().lsms_check_geometry(d, radius, c.shape[0], _dptr(c))
+
+
+def context_for(workload, precision=LSMS_FP64) -> Context:
+    """A context for one of paper_1407_3868_gb300.inputs.WORKLOADS (medium, p, contour)."""
+    m = workload.medium
+    return Context(m["k1"], m["k2"], m["k3"], m["d"], m["kp"], m["radius"], workload.p,
+                   workload.n_nodes, b=workload.b, t_max=workload.t_max, panel_order=16,
+                   precision=precision)

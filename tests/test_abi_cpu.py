@@ -1,0 +1,111 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports every symbol the
+header declares, and its host logic (contour, disc scattering matrix, geometry validation) agrees
+with the oracle and with the stated rules."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import lsms_oracle as O
+from paper_1407_3868_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1407_3868_gb300 import build as b
+    b.build()
+    from paper_1407_3868_gb300 import lsms
+    return lsms
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lsms.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lsms_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for name in names:
+        assert hasattr(so, name), name
+    assert set(lib.EXPORTS) == set(names)
+
+
+@pytest.mark.parametrize("name", ["disc16_p10_ns256", "disc1000_p12_ns512", "disc5000_p14_ns1024",
+                                  "disc2000_p12_ns768_src64"])
+def test_library_contour_equals_oracle_contour(lib, name):
+    w = inputs.WORKLOADS[name]
+    m = w.medium
+    lam, wt = lib.build_contour(w.n_nodes, m["k1"], m["k2"], m["k3"], w.b, w.t_max, 16)
+    lam_o, wt_o = O.contour(w.n_nodes, m["k1"], m["k2"], m["k3"], w.b, w.t_max)
+    assert np.max(np.abs(lam - lam_o)) <= 1e-12 * w.t_max
+    assert np.max(np.abs(wt - wt_o)) <= 1e-14 * w.t_max
+
+
+def test_contour_defaults_follow_the_paper(lib):
+    # b = 0.2, t_max = max k + 20, 16-point panels (Sec. 6)
+    lam, wt = lib.build_contour(500, 1.0, 3.0, 1.0)
+    assert np.isclose(lam[-1].imag, -0.2) and lam[-1].real < 23.0
+    lam_o, wt_o = O.contour(500, 1.0, 3.0, 1.0, 0.2, 23.0)
+    assert np.allclose(lam, lam_o, atol=1e-13) and np.allclose(wt, wt_o, atol=1e-14)
+
+
+def test_contour_rejects_too_few_nodes(lib):
+    with pytest.raises(lib.LsmsError) as e:
+        lib.build_contour(40, 1.0, 3.0, 1.0, 0.2, 20.0, 16)
+    assert e.value.code == -1
+
+
+@pytest.mark.parametrize("p", [0, 5, 10, 14, 15])
+def test_library_scattering_matrix_equals_oracle(lib, p):
+    m = inputs.MEDIUM
+    s = lib.scattering_diagonal(p, m["k2"], m["kp"], m["radius"])
+    s_o = O.mie_coefficients(p, m["k2"], m["kp"], m["radius"])
+    assert np.allclose(s, s_o, rtol=1e-11, atol=0)
+
+
+def test_geometry_rules(lib):
+    d, R = 2.0, 0.25
+    ok = np.array([[0.0, -1.0], [0.6, -1.0], [0.3, -0.3]])
+    assert lib.check_geometry(d, R, ok) == 0
+    # gap below 0.2 R
+    assert lib.check_geometry(d, R, [[0.0, -1.0], [0.54, -1.0]]) == -2
+    # touching the top interface
+    assert lib.check_geometry(d, R, [[0.0, -0.25]]) == -2
+    # crossing the bottom interface
+    assert lib.check_geometry(d, R, [[0.0, -1.8]]) == -2
+    # non-finite
+    assert lib.check_geometry(d, R, [[math.nan, -1.0]]) == -1
+    assert lib.check_geometry(d, R, np.zeros((0, 2))) == 0
+    # every generated workload layout is valid
+    assert lib.check_geometry(d, R, inputs.WORKLOADS["disc1000_p12_ns512"].centres()) == 0
+
+
+def test_create_without_a_gpu_reports_an_error(lib):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    with pytest.raises(lib.LsmsError) as e:
+        lib.Context(1.0, 3.0, 1.0, 2.0, 2.0, 0.25, 5, 128)
+    assert e.value.code == -6
+
+
+def test_seeded_layouts_respect_the_geometry():
+    c = inputs.layout(200, -50.0, 50.0, 9)
+    assert c.shape == (200, 2)
+    assert np.all(c[:, 1] >= -1.7) and np.all(c[:, 1] <= -0.3)
+    dd = np.hypot(c[:, None, 0] - c[None, :, 0], c[:, None, 1] - c[None, :, 1]) + np.eye(200) * 9
+    assert dd.min() >= 0.6
+    assert np.array_equal(c, inputs.layout(200, -50.0, 50.0, 9))
+    assert len(inputs.sweep_sizes()) == 128
+    assert min(inputs.sweep_sizes()) >= 200 and max(inputs.sweep_sizes()) <= 4000
