@@ -30,7 +30,8 @@ __device__ __forceinline__ double2 warp_sum(double2 v) {
 
 struct GmState {
   double beta0;   // ||r0||
-  double res;     // |g_{k+1}| / beta0
+  double ref;     // ||rhs||: residuals are reported relative to it
+  double res;     // |g_{k+1}| / ||rhs||
   double hn;      // ||w|| of the last Arnoldi step
   double inv;     // scale for the next basis vector
   int flag;       // 1: non-finite value seen
@@ -136,13 +137,15 @@ __global__ void k_diag_scale(const double2* __restrict__ x, const double* __rest
   }
 }
 
-__global__ void k_gm_start(const double2* __restrict__ nrm2, GmState* __restrict__ st,
-                           double2* __restrict__ g) {
+__global__ void k_gm_start(const double2* __restrict__ nrm2, const double2* __restrict__ nrm2_rhs,
+                           GmState* __restrict__ st, double2* __restrict__ g) {
   const double b = sqrt(nrm2[0].x);
+  const double ref = sqrt(nrm2_rhs[0].x);
   st->beta0 = b;
+  st->ref = ref > 0.0 ? ref : 1.0;
   st->inv = b > 0.0 ? 1.0 / b : 0.0;
-  st->res = b > 0.0 ? 1.0 : 0.0;
-  st->flag = isfinite(b) ? 0 : 1;
+  st->res = b / st->ref;
+  st->flag = (isfinite(b) && isfinite(ref)) ? 0 : 1;
   g[0] = make_double2(b, 0.0);
 }
 
@@ -185,7 +188,7 @@ __global__ void k_gm_column(int k, const double2* __restrict__ h1, const double2
   const double2 gk = g[k];
   g[k] = cjmul(c, gk);
   g[k + 1] = make_double2(-cmul(s, gk).x, -cmul(s, gk).y);
-  const double res = hypot(g[k + 1].x, g[k + 1].y) / st->beta0;
+  const double res = hypot(g[k + 1].x, g[k + 1].y) / st->ref;
   st->res = res;
   if (!isfinite(res) || !isfinite(hn)) st->flag = 1;
 }
@@ -293,14 +296,15 @@ int gmres_device(lsms_ctx* c, const double2* rhs, double2* x, bool x_nonzero, do
     cudaMemcpyAsync(g.V, rhs, L * sizeof(double2), cudaMemcpyDeviceToDevice, stream);
   }
   mdot(g.V, L, 1, g.V, L, g.nrm, stream);
-  k_gm_start<<<1, 1, 0, stream>>>(g.nrm, g.st, g.g);
+  mdot(rhs, L, 1, rhs, L, g.nrm + 1, stream);
+  k_gm_start<<<1, 1, 0, stream>>>(g.nrm, g.nrm + 1, g.st, g.g);
   k_scale_by<<<grid_for(L, 256), 256, 0, stream>>>(g.V, g.V, g.st, L);
   cudaMemcpyAsync((void*)hs, g.st, sizeof(GmState), cudaMemcpyDeviceToHost, stream);
   cudaStreamSynchronize(stream);
   if ((rc = check_cuda(c, "gmres start"))) return rc;
   if (hs->flag) return ctx_fail(c, LSMS_ERR_NONFINITE, "non-finite right-hand side");
-  if (hs->beta0 == 0.0) {
-    *res_out = 0.0;
+  if (hs->beta0 == 0.0 || hs->res <= tol) {
+    *res_out = hs->res;
     return LSMS_OK;
   }
   int k = 0;
