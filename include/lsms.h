@@ -182,6 +182,25 @@ int lsms_eval_field(lsms_ctx* ctx, int src_index, int n_tgt, const double* tgt_x
 int lsms_set_timing(lsms_ctx* ctx, int enable);
 int lsms_last_timing(lsms_ctx* ctx, double* ms_translate, double* ms_reflect, int* launches);
 
+/* lsms_translate_mixed_noalloc — the FP32 translation of lsms_translate(..., LSMS_MIXED) for
+ *   callers that cannot allocate device memory: code that must live inside a memory budget owned
+ *   by someone else (a framework's pooled allocator, a pre-sized arena) or a latency-critical loop
+ *   where cudaMalloc/cudaFree, which may synchronise the device, are not allowed.  It needs no
+ *   context and calls no allocating routine; its scratch is a fixed 16 MiB device array inside
+ *   the library, which every GPU that loads the library keeps until the process exits.  The paper
+ *   has no counterpart: it is a packaging of Lemma 3.1's operator, not a step of the method.
+ *   n discs, order p (0..15), middle-layer wavenumber k2 > 0, nrhs coefficient vectors.
+ *   centres_xy: device, 2n doubles; beta: device [nrhs][n][P] complex; alpha: device
+ *   [nrhs][n][P] complex, written.  Asynchronous on `stream` (a cudaStream_t).  Sizes with
+ *   16 n + 8 nrhs n (2p+1) bytes above 16 MiB (n above about 70000 at p = 14, nrhs = 1) are
+ *   rejected with LSMS_ERR_ARG.  The first call on each device looks up the scratch array's
+ *   device address (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   Every call shares the one scratch array, which keeps the last call's contents, so calls
+ *   that overlap on the GPU (different streams, or different host threads) race: serialise them.
+ *   Errors are reported by lsms_last_error(NULL). */
+int lsms_translate_mixed_noalloc(int n, int p, double k2, int nrhs, const double* centres_xy,
+                                 const double* beta, double* alpha, void* stream);
+
 /* Host-only helpers: no GPU needed, no context.
  * lsms_build_contour — the nodes and weights lsms_create would use for `contour` (see
  *   lsms_contour; Sec. 5.1 Eq. "sommerseg"); nodes, weights: contour->n_nodes complex each.

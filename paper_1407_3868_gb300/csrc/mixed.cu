@@ -335,3 +335,107 @@ int disaggregate_mixed(lsms_ctx* c, int nrhs, const double2* V, double2* alpha, 
 int reflection_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st) {
   return reflection_f64(c, nrhs, xs, alpha, st);
 }
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free variant of the FP32 translation (lsms_translate_mixed_noalloc).
+//
+// Its scratch (float-float centres and the per-split FP32 partial sums) lives in the file-scope
+// device array below instead of memory obtained from cudaMalloc.  Every GPU that loads the library
+// holds these 16 MiB until the process exits.  Host code cannot pass the array's name to a kernel
+// (on the host it is only a stand-in symbol), so the device address is looked up once per device
+// with cudaGetSymbolAddress and cached.
+// ---------------------------------------------------------------------------------------------
+#include <mutex>
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device (looked up on first use).
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return ctx_fail(nullptr, LSMS_ERR_CUDA, "translate_mixed_noalloc: no current CUDA device");
+  }
+  if (dev < 0 || dev >= kMaxDevices)
+    return ctx_fail(nullptr, LSMS_ERR_CUDA, "translate_mixed_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return ctx_fail(nullptr, LSMS_ERR_CUDA,
+                      std::string("translate_mixed_noalloc: cudaGetSymbolAddress failed: ") +
+                          cudaGetErrorString(e));
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return LSMS_OK;
+}
+
+__global__ void k_centres_ff_xy(const double* __restrict__ xy, int n, float4* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double x = xy[2 * j], y = xy[2 * j + 1];
+  const float xh = (float)x, yh = (float)y;
+  out[j] = make_float4(xh, (float)(x - (double)xh), yh, (float)(y - (double)yh));
+}
+
+}  // namespace
+
+extern "C" int lsms_translate_mixed_noalloc(int n, int p, double k2, int nrhs,
+                                            const double* centres_xy, const double* beta,
+                                            double* alpha, void* stream) {
+  if (n < 0 || nrhs < 0 || p < 0 || p > LSMS_MAX_P || !std::isfinite(k2) || !(k2 > 0.0))
+    return ctx_fail(nullptr, LSMS_ERR_ARG, "translate_mixed_noalloc: need n >= 0, nrhs >= 0, 0 <= p <= 15, k2 > 0");
+  if (n == 0 || nrhs == 0) return LSMS_OK;
+  if (!centres_xy || !beta || !alpha) return ctx_fail(nullptr, LSMS_ERR_ARG, "translate_mixed_noalloc: NULL pointer");
+  const int P = 2 * p + 1;
+  const size_t cbytes = (((size_t)n * sizeof(float4)) + 255) & ~size_t(255);
+  const size_t per_split = (size_t)nrhs * n * P * sizeof(float2);
+  if (cbytes + per_split > kNoAllocScratchBytes)
+    return ctx_fail(nullptr, LSMS_ERR_ARG,
+                    "translate_mixed_noalloc: n * (16 + 8 * nrhs * (2p+1)) bytes exceed the 16 MiB scratch");
+  int splits = translate_splits(n, nrhs);
+  while (splits > 1 && cbytes + (size_t)splits * per_split > kNoAllocScratchBytes) --splits;
+  int sps = (n + splits - 1) / splits;
+  sps = ((sps + MCH - 1) / MCH) * MCH;
+  splits = (n + sps - 1) / sps;
+  void* base = nullptr;
+  int rc = noalloc_scratch(&base);
+  if (rc) return rc;
+  float4* cff = (float4*)base;
+  float2* part = (float2*)((unsigned char*)base + cbytes);
+  cudaStream_t st = (cudaStream_t)stream;
+  k_centres_ff_xy<<<(n + 255) / 256, 256, 0, st>>>(centres_xy, n, cff);
+  const float kh = (float)k2, kl = (float)(k2 - (double)kh);
+  dim3 grid((n + MW * MT - 1) / (MW * MT), splits, nrhs);
+  const size_t smem = (size_t)MW * 32 * MHS * sizeof(float2);
+  const double2* xs = (const double2*)beta;
+  switch ((P + 3) / 4) {
+    case 1: launch_vb<1>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 2: launch_vb<2>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 3: launch_vb<3>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 4: launch_vb<4>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 5: launch_vb<5>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 6: launch_vb<6>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 7: launch_vb<7>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    default: launch_vb<8>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+  }
+  const long long len = (long long)nrhs * n * P;
+  long long g = (len + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  k_reduce_parts<<<(int)g, 256, 0, st>>>(part, splits, len, (double2*)alpha);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return ctx_fail(nullptr, LSMS_ERR_CUDA, std::string("translate_mixed_noalloc: ") + cudaGetErrorString(e));
+  return LSMS_OK;
+}

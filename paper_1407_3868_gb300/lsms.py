@@ -24,7 +24,7 @@ EXPORTS = ["lsms_create", "lsms_set_particles", "lsms_apply", "lsms_apply_ex", "
            "lsms_get_contour", "lsms_get_scattering", "lsms_num_nodes", "lsms_num_particles",
            "lsms_solve", "lsms_eval_field", "lsms_last_error", "lsms_destroy",
            "lsms_build_contour", "lsms_scattering_diagonal", "lsms_check_geometry",
-           "lsms_set_timing", "lsms_last_timing"]
+           "lsms_set_timing", "lsms_last_timing", "lsms_translate_mixed_noalloc"]
 
 
 class LsmsError(RuntimeError):
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsms_check_geometry": (i, [d, d, i, _D]),
         "lsms_set_timing": (i, [_P, i]),
         "lsms_last_timing": (i, [_P, _D, _D, ctypes.POINTER(ctypes.c_int)]),
+        "lsms_translate_mixed_noalloc": (i, [i, i, d, i, _P, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -282,6 +283,25 @@ def check_geometry(d, radius, centres) -> int:
     """Host-only: LSMS_OK (0) or a negative status for a disc layout."""
     c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 2)
     return load().lsms_check_geometry(d, radius, c.shape[0], _dptr(c))
+
+
+def translate_mixed_noalloc(centres, beta, alpha, k2, p, stream=None):
+    """FP32 translation with no device allocation (lsms_translate_mixed_noalloc).
+
+    centres: CUDA float64 tensor (n, 2); beta, alpha: CUDA complex128 tensors (nrhs, n, 2p+1).
+    Asynchronous on `stream` (default: torch's current stream)."""
+    import torch
+    lib = load()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    n = centres.shape[0]
+    nrhs = beta.numel() // max(1, n * (2 * p + 1))
+    rc = lib.lsms_translate_mixed_noalloc(n, p, k2, nrhs, ctypes.c_void_p(centres.data_ptr()),
+                                          ctypes.c_void_p(beta.data_ptr()),
+                                          ctypes.c_void_p(alpha.data_ptr()),
+                                          ctypes.c_void_p(stream.cuda_stream))
+    if rc != 0:
+        raise LsmsError(rc, lib.lsms_last_error(None).decode())
 
 
 def context_for(workload, precision=LSMS_FP64) -> Context:
