@@ -192,7 +192,7 @@ int lsms_last_timing(lsms_ctx* ctx, double* ms_translate, double* ms_reflect, in
  *   n discs, order p (0..15), middle-layer wavenumber k2 > 0, nrhs coefficient vectors.
  *   centres_xy: device, 2n doubles; beta: device [nrhs][n][P] complex; alpha: device
  *   [nrhs][n][P] complex, written.  Asynchronous on `stream` (a cudaStream_t).  Sizes with
- *   16 n + 8 nrhs n (2p+1) bytes above 16 MiB (n above about 70000 at p = 14, nrhs = 1) are
+ *   16 n + 16 nrhs n (2p+1) bytes above 16 MiB (n above about 35000 at p = 14, nrhs = 1) are
  *   rejected with LSMS_ERR_ARG.  The first call on each device looks up the scratch array's
  *   device address (cudaGetSymbolAddress); make that first call before any stream capture.
  *   Every call shares the one scratch array, which keeps the last call's contents, so calls

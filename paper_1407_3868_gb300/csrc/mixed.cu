@@ -66,12 +66,13 @@ constexpr float kTwoPiLo = -1.74845553146951427e-07f;  // 2 pi - float(2 pi)
 constexpr float kInvTwoPi = 0.159154943091895336f;
 constexpr float kZAsym = 25.0f;
 
-// H_0(z), H_1(z) for z >= 25 from Hankel's expansion with the phase theta = z mod 2 pi:
-// H_nu(z) ~ sqrt(2/(pi z)) exp(i (z - nu pi/2 - pi/4)) sum_k i^k a_k(nu) z^-k,
-// a_k(nu) = prod_{j<=k} (4 nu^2 - (2j-1)^2) / (k! 8^k).
+// H_0(z), H_1(z) for z >= 25 from Hankel's expansion with the phase theta = z mod 2 pi in
+// [-pi, pi]:  H_nu(z) ~ sqrt(2/(pi z)) exp(i (z - nu pi/2 - pi/4)) sum_k i^k a_k(nu) z^-k,
+// a_k(nu) = prod_{j<=k} (4 nu^2 - (2j-1)^2) / (k! 8^k).  The hardware sine/cosine is used on the
+// reduced phase (absolute error below 4e-7 there).
 __device__ __forceinline__ void hankel01_asym(float zf, float theta, float2& h0, float2& h1) {
   float s, c;
-  sincosf(theta, &s, &c);
+  __sincosf(theta, &s, &c);
   const float iz = 1.0f / zf, iz2 = iz * iz;
   const float amp = sqrtf(0.636619772367581343f * iz) * 0.707106781186547524f;
   // nu = 0: a1 = -1/8, a2 = 9/128, a3 = -225/3072, a4 = 11025/98304
@@ -87,11 +88,15 @@ __device__ __forceinline__ void hankel01_asym(float zf, float theta, float2& h0,
   h1 = cmulf(e1, make_float2(p1, q1));
 }
 
-// Sequence h[HOFF + s + 2p] = H_s(k rho) exp(i s phi), s = -2p..2p, for centres a (target) and
-// b (source) given as float-float (x_hi, x_lo, y_hi, y_lo).
-constexpr int HOFF = 32;
-constexpr int MHS = 97;   // > HOFF + 4p + 1 (<= 93); odd so the 32 lanes' slots fall in distinct banks
+// Near pairs (z < 25, a handful per disc): FP64 library J0, Y0, J1, Y1.  Out of line so that the
+// hot loop's instruction footprint stays small.
+__device__ __noinline__ void hankel01_near(double z, float2* h0, float2* h1) {
+  *h0 = make_float2((float)j0(z), (float)y0(z));
+  *h1 = make_float2((float)j1(z), (float)y1(z));
+}
 
+// Pair sequence h[s + 2p] = H_s(k rho) exp(i s phi), s = -2p..2p, for centres a (target) and b
+// (source) given as float-float (x_hi, x_lo, y_hi, y_lo).
 __device__ void hankel_sequence_f32(float4 a, float4 b, ffl k, int p, float2* h) {
   const ffl dx = ff_sub({a.x, a.y}, {b.x, b.y});
   const ffl dy = ff_sub({a.z, a.w}, {b.z, b.w});
@@ -107,11 +112,9 @@ __device__ void hankel_sequence_f32(float4 a, float4 b, ffl k, int p, float2* h)
     const ffl t = ff_sub(z, ff_add(ff_mul_f({kTwoPiHi, 0.0f}, nq), ff_mul_f({kTwoPiLo, 0.0f}, nq)));
     hankel01_asym(zf, t.hi + t.lo, h0, h1);
   } else {
-    const double zd = (double)z.hi + (double)z.lo;
-    h0 = make_float2((float)j0(zd), (float)y0(zd));
-    h1 = make_float2((float)j1(zd), (float)y1(zd));
+    hankel01_near((double)z.hi + (double)z.lo, &h0, &h1);
   }
-  const int c0 = HOFF + 2 * p;
+  const int c0 = 2 * p;
   h[c0] = h0;
   float2 hm = h0, hq = h1, eq = e1;
   const float iz = 1.0f / zf;
@@ -130,92 +133,103 @@ __device__ void hankel_sequence_f32(float4 a, float4 b, ffl k, int p, float2* h)
   }
 }
 
-constexpr int MW = 4;    // warps per CTA
-constexpr int MT = 8;    // target discs per warp (4 lanes each)
-constexpr int MCH = 32;  // sources staged per chunk
+constexpr int MW = 4;      // warps per CTA
+constexpr int MT = 8;      // target discs per warp
+constexpr int MCH = 32;    // sources staged per chunk
+// Pair slots: 32 per warp (8 targets x 4 sources), stride MHS float2.  A slot holds the 4p + 1
+// values of one pair; windows of the contraction reach at most 3 entries before and 3 after them,
+// into the zero margin of the neighbouring slot or the guard.  MHS = 65 = 1 (mod 16): the 32 lanes'
+// window reads (offsets 2t - 16vb words) and the generator's stores hit distinct banks.
+constexpr int MHS = 65;
+constexpr int GUARD = 8;
+constexpr size_t TRANSLATE_F32_SMEM = (size_t)(2 * GUARD + MW * 32 * MHS) * sizeof(float2);
 
 // part[split][r][l][nu] = sum over the split's sources m != l of T^{lm} xs^m   (FP32)
-template <int VB>
-__global__ void __launch_bounds__(MW * 32)
+// Lane roles.  Generation: lane = 8 s4 + t computes the pair (target t, source s4) into slot lane.
+// Contraction: lane = 8 vb + t owns outputs nu = VB vb .. VB vb + VB - 1 of target t; for each
+// staged source it slides a window of 2 VB - 1 sequence values over NB blocks of VB source orders.
+// Complex products use three real FMAs (Gauss): A += hr br, B += hi bi, C += (hr+hi)(br+bi);
+// re = A - B, im = C - A - B.
+template <int VB, int NB>
+__global__ void __launch_bounds__(MW * 32, 3)
 k_translate_f32(const float4* __restrict__ cff, int n, int p, float k_hi, float k_lo,
-                const double2* __restrict__ xs, float2* __restrict__ part, int src_per_split,
+                const float2* __restrict__ xs, float2* __restrict__ part, int src_per_split,
                 int nrhs) {
-  __shared__ float2 sb[MCH][33];
+  __shared__ float2 sb[MCH][VB * NB + 1];
   __shared__ float4 sc[MCH];
-  extern __shared__ float2 sh[];       // [MW][32 pair slots][MHS]
+  extern __shared__ float2 sh[];
   const int P = 2 * p + 1;
-  const int PB = ((P + VB - 1) / VB) * VB;   // orders padded to whole blocks
   const int r = blockIdx.z;
   const int split = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = lane >> 2, vb = lane & 3;
+  const int t = lane & 7, hi8 = lane >> 3;       // hi8 = vb (contraction) = s4 (generation)
   const int l = (blockIdx.x * MW + warp) * MT + t;
   const bool lvalid = l < n;
   const float4 ct = lvalid ? cff[l] : make_float4(0.f, 0.f, 0.f, 0.f);
-  float2* hw = sh + (size_t)warp * 32 * MHS;
-  // zero the pair slots once: the generator only writes [HOFF, HOFF + 4p]
-  for (int i = lane; i < 32 * MHS; i += 32) hw[i] = make_float2(0.f, 0.f);
-  __syncwarp();
-  float2 acc[VB];
+  for (int i = threadIdx.x; i < 2 * GUARD + MW * 32 * MHS; i += blockDim.x) sh[i] = make_float2(0.f, 0.f);
+  float2* hw = sh + GUARD + warp * 32 * MHS;
+  float A[VB], B[VB], C[VB];
 #pragma unroll
-  for (int i = 0; i < VB; ++i) acc[i] = make_float2(0.f, 0.f);
+  for (int i = 0; i < VB; ++i) A[i] = B[i] = C[i] = 0.f;
   const int jbeg = split * src_per_split;
   const int jend = min(n, jbeg + src_per_split);
-  const double2* xr = xs + (size_t)r * n * P;
+  const float2* xr = xs + (size_t)r * n * P;
   const ffl kf = {k_hi, k_lo};
   for (int j0c = jbeg; j0c < jend; j0c += MCH) {
     const int cnt = min(MCH, jend - j0c);
     __syncthreads();
-    for (int i = threadIdx.x; i < MCH * 32; i += blockDim.x) {
-      const int s = i >> 5, q = i & 31;
-      float2 v = make_float2(0.f, 0.f);
-      if (s < cnt && q < P) {
-        const double2 d = xr[(size_t)(j0c + s) * P + q];
-        v = make_float2((float)d.x, (float)d.y);
-      }
-      sb[s][q] = v;
+    for (int i = threadIdx.x; i < MCH * VB * NB; i += blockDim.x) {
+      const int s = i / (VB * NB), q = i - s * (VB * NB);
+      sb[s][q] = (s < cnt && q < P) ? xr[(size_t)(j0c + s) * P + q] : make_float2(0.f, 0.f);
     }
     if (threadIdx.x < cnt) sc[threadIdx.x] = cff[j0c + threadIdx.x];
     __syncthreads();
     for (int s0 = 0; s0 < cnt; s0 += 4) {
-      // generation: lane (t, s4) -> pair (l, j0c + s0 + s4)
       {
-        const int js = s0 + vb;
+        const int js = s0 + hi8;
         float2* h = hw + lane * MHS;
         if (js < cnt && lvalid && j0c + js != l) {
           hankel_sequence_f32(ct, sc[js], kf, p, h);
         } else {
-          for (int q = 0; q <= 4 * p; ++q) h[HOFF + q] = make_float2(0.f, 0.f);
+          for (int q = 0; q <= 4 * p; ++q) h[q] = make_float2(0.f, 0.f);
         }
       }
       __syncwarp();
-      // contraction: lane (t, vb) owns outputs nu = VB*vb + i
       const int nq4 = min(4, cnt - s0);
       for (int q4 = 0; q4 < nq4; ++q4) {
-        // hb[j] = h_{n - nu} with n = j - (VB - 1) + nb ... see below
-        const float2* hs = hw + (t * 4 + q4) * MHS + HOFF + 2 * p - VB * vb;   // hs[n - i] = h_{n - (VB vb + i)}
+        const float2* hs = hw + (q4 * 8 + t) * MHS + 2 * p - VB * hi8;   // hs[n - i]: output VB vb + i
         const float2* bs = sb[s0 + q4];
         float2 win[2 * VB - 1];
-        // window for block nb: win[j] = hs[nb + j - (VB - 1)], j = 0 .. 2VB-2
+        float wsum[2 * VB - 1];
 #pragma unroll
-        for (int j = 0; j < VB - 1; ++j) win[j] = hs[j - (VB - 1)];
-        for (int nb = 0; nb < PB; nb += VB) {
+        for (int j = 0; j < VB - 1; ++j) {
+          win[j] = hs[j - (VB - 1)];
+          wsum[j] = win[j].x + win[j].y;
+        }
 #pragma unroll
-          for (int j = 0; j < VB; ++j) win[VB - 1 + j] = hs[nb + j];
+        for (int nb = 0; nb < NB; ++nb) {
+#pragma unroll
+          for (int j = 0; j < VB; ++j) {
+            win[VB - 1 + j] = hs[nb * VB + j];
+            wsum[VB - 1 + j] = win[VB - 1 + j].x + win[VB - 1 + j].y;
+          }
 #pragma unroll
           for (int u = 0; u < VB; ++u) {
-            const float2 b = bs[nb + u];
+            const float2 b = bs[nb * VB + u];
+            const float bsum = b.x + b.y;
 #pragma unroll
             for (int i = 0; i < VB; ++i) {
               const float2 hv = win[VB - 1 + u - i];
-              acc[i].x = __fmaf_rn(hv.x, b.x, acc[i].x);
-              acc[i].x = __fmaf_rn(-hv.y, b.y, acc[i].x);
-              acc[i].y = __fmaf_rn(hv.x, b.y, acc[i].y);
-              acc[i].y = __fmaf_rn(hv.y, b.x, acc[i].y);
+              A[i] = __fmaf_rn(hv.x, b.x, A[i]);
+              B[i] = __fmaf_rn(hv.y, b.y, B[i]);
+              C[i] = __fmaf_rn(wsum[VB - 1 + u - i], bsum, C[i]);
             }
           }
 #pragma unroll
-          for (int j = 0; j < VB - 1; ++j) win[j] = win[VB + j];
+          for (int j = 0; j < VB - 1; ++j) {
+            win[j] = win[VB + j];
+            wsum[j] = wsum[VB + j];
+          }
         }
       }
       __syncwarp();
@@ -225,8 +239,8 @@ k_translate_f32(const float4* __restrict__ cff, int n, int p, float k_hi, float 
     float2* out = part + (((size_t)split * nrhs + r) * n + l) * P;
 #pragma unroll
     for (int i = 0; i < VB; ++i) {
-      const int nu = VB * vb + i;
-      if (nu < P) out[nu] = acc[i];
+      const int nu = VB * hi8 + i;
+      if (nu < P) out[nu] = make_float2(A[i] - B[i], C[i] - A[i] - B[i]);
     }
   }
 }
@@ -246,6 +260,12 @@ __global__ void k_reduce_parts(const float2* __restrict__ part, int nsplit, long
   }
 }
 
+__global__ void k_to_float(const double2* __restrict__ x, float2* __restrict__ y, long long len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = make_float2((float)x[i].x, (float)x[i].y);
+}
+
 __global__ void k_centres_ff(const double* __restrict__ cx, const double* __restrict__ cy, int n,
                              float4* __restrict__ out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -254,15 +274,34 @@ __global__ void k_centres_ff(const double* __restrict__ cx, const double* __rest
   out[j] = make_float4(xh, (float)(cx[j] - (double)xh), yh, (float)(cy[j] - (double)yh));
 }
 
-template <int VB>
-void launch_vb(dim3 grid, size_t smem, cudaStream_t st, const float4* cff, int n, int p, float kh,
-               float kl, const double2* xs, float2* part, int sps, int nrhs) {
+template <int VB, int NB>
+void launch_vbnb(dim3 grid, cudaStream_t st, const float4* cff, int n, int p, float kh, float kl,
+                 const float2* xs, float2* part, int sps, int nrhs) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_translate_f32<VB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_translate_f32<VB, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)TRANSLATE_F32_SMEM);
     attr = true;
   }
-  k_translate_f32<VB><<<grid, MW * 32, smem, st>>>(cff, n, p, kh, kl, xs, part, sps, nrhs);
+  k_translate_f32<VB, NB><<<grid, MW * 32, TRANSLATE_F32_SMEM, st>>>(cff, n, p, kh, kl, xs, part, sps, nrhs);
+}
+
+// Order blocking for P = 2p + 1: VB = ceil(P/4) outputs per lane, NB = ceil(P/VB) source blocks.
+void launch_translate_kernel(dim3 grid, cudaStream_t st, const float4* cff, int n, int p, float kh,
+                             float kl, const float2* xs, float2* part, int sps, int nrhs) {
+  switch (p) {
+    case 0: launch_vbnb<1, 1>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 1: launch_vbnb<1, 3>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 2: launch_vbnb<2, 3>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 3: launch_vbnb<2, 4>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 4: launch_vbnb<3, 3>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 5: launch_vbnb<3, 4>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 6: case 7: launch_vbnb<4, 4>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 8: case 9: launch_vbnb<5, 4>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 10: case 11: launch_vbnb<6, 4>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 12: case 13: launch_vbnb<7, 4>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    default: launch_vbnb<8, 4>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+  }
 }
 
 }  // namespace
@@ -298,26 +337,17 @@ int translate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cu
   sps = ((sps + MCH - 1) / MCH) * MCH;
   splits = (n + sps - 1) / sps;
   const long long len = (long long)nrhs * n * P;
+  const size_t b32 = (((size_t)len * sizeof(float2)) + 255) & ~size_t(255);
   int rc;
-  if ((rc = ensure(c, c->ws_lp, (size_t)splits * len * sizeof(float2)))) return rc;
-  float2* part = (float2*)c->ws_lp.ptr;
-  const float kh = (float)c->k2, kl = (float)(c->k2 - (double)kh);
-  dim3 grid((n + MW * MT - 1) / (MW * MT), splits, nrhs);
-  const size_t smem = (size_t)MW * 32 * MHS * sizeof(float2);
-  const float4* cff = (const float4*)c->d_lp_misc;
-  const int vb = (P + 3) / 4;
-  switch (vb) {
-    case 1: launch_vb<1>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 2: launch_vb<2>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 3: launch_vb<3>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 4: launch_vb<4>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 5: launch_vb<5>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 6: launch_vb<6>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 7: launch_vb<7>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    default: launch_vb<8>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-  }
+  if ((rc = ensure(c, c->ws_lp, b32 + (size_t)splits * len * sizeof(float2)))) return rc;
+  float2* xs32 = (float2*)c->ws_lp.ptr;
+  float2* part = (float2*)((unsigned char*)c->ws_lp.ptr + b32);
   long long g = (len + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
+  k_to_float<<<(int)g, 256, 0, st>>>(xs, xs32, len);
+  const float kh = (float)c->k2, kl = (float)(c->k2 - (double)kh);
+  dim3 grid((n + MW * MT - 1) / (MW * MT), splits, nrhs);
+  launch_translate_kernel(grid, st, (const float4*)c->d_lp_misc, n, p, kh, kl, xs32, part, sps, nrhs);
   k_reduce_parts<<<(int)g, 256, 0, st>>>(part, splits, len, alpha);
   return check_cuda(c, "translate_mixed");
 }
@@ -399,13 +429,15 @@ extern "C" int lsms_translate_mixed_noalloc(int n, int p, double k2, int nrhs,
   if (n == 0 || nrhs == 0) return LSMS_OK;
   if (!centres_xy || !beta || !alpha) return ctx_fail(nullptr, LSMS_ERR_ARG, "translate_mixed_noalloc: NULL pointer");
   const int P = 2 * p + 1;
+  const long long len = (long long)nrhs * n * P;
   const size_t cbytes = (((size_t)n * sizeof(float4)) + 255) & ~size_t(255);
-  const size_t per_split = (size_t)nrhs * n * P * sizeof(float2);
-  if (cbytes + per_split > kNoAllocScratchBytes)
+  const size_t b32 = (((size_t)len * sizeof(float2)) + 255) & ~size_t(255);
+  const size_t per_split = (size_t)len * sizeof(float2);
+  if (cbytes + b32 + per_split > kNoAllocScratchBytes)
     return ctx_fail(nullptr, LSMS_ERR_ARG,
-                    "translate_mixed_noalloc: n * (16 + 8 * nrhs * (2p+1)) bytes exceed the 16 MiB scratch");
+                    "translate_mixed_noalloc: n * (16 + 16 * nrhs * (2p+1)) bytes exceed the 16 MiB scratch");
   int splits = translate_splits(n, nrhs);
-  while (splits > 1 && cbytes + (size_t)splits * per_split > kNoAllocScratchBytes) --splits;
+  while (splits > 1 && cbytes + b32 + (size_t)splits * per_split > kNoAllocScratchBytes) --splits;
   int sps = (n + splits - 1) / splits;
   sps = ((sps + MCH - 1) / MCH) * MCH;
   splits = (n + sps - 1) / sps;
@@ -413,26 +445,16 @@ extern "C" int lsms_translate_mixed_noalloc(int n, int p, double k2, int nrhs,
   int rc = noalloc_scratch(&base);
   if (rc) return rc;
   float4* cff = (float4*)base;
-  float2* part = (float2*)((unsigned char*)base + cbytes);
+  float2* xs32 = (float2*)((unsigned char*)base + cbytes);
+  float2* part = (float2*)((unsigned char*)base + cbytes + b32);
   cudaStream_t st = (cudaStream_t)stream;
   k_centres_ff_xy<<<(n + 255) / 256, 256, 0, st>>>(centres_xy, n, cff);
-  const float kh = (float)k2, kl = (float)(k2 - (double)kh);
-  dim3 grid((n + MW * MT - 1) / (MW * MT), splits, nrhs);
-  const size_t smem = (size_t)MW * 32 * MHS * sizeof(float2);
-  const double2* xs = (const double2*)beta;
-  switch ((P + 3) / 4) {
-    case 1: launch_vb<1>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 2: launch_vb<2>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 3: launch_vb<3>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 4: launch_vb<4>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 5: launch_vb<5>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 6: launch_vb<6>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 7: launch_vb<7>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    default: launch_vb<8>(grid, smem, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-  }
-  const long long len = (long long)nrhs * n * P;
   long long g = (len + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
+  k_to_float<<<(int)g, 256, 0, st>>>((const double2*)beta, xs32, len);
+  const float kh = (float)k2, kl = (float)(k2 - (double)kh);
+  dim3 grid((n + MW * MT - 1) / (MW * MT), splits, nrhs);
+  launch_translate_kernel(grid, st, cff, n, p, kh, kl, xs32, part, sps, nrhs);
   k_reduce_parts<<<(int)g, 256, 0, st>>>(part, splits, len, (double2*)alpha);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess)

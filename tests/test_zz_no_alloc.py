@@ -53,7 +53,7 @@ def test_noalloc_translation_rejects_sizes_beyond_its_scratch():
 
     from paper_1407_3868_gb300 import lsms
 
-    n, p = 80000, 14                      # 16 n + 8 n (2p+1) bytes > 16 MiB
+    n, p = 40000, 14                      # 16 n + 16 n (2p+1) bytes > 16 MiB
     c = torch.zeros((n, 2), dtype=torch.float64, device="cuda")
     b = torch.zeros((1, n, 2 * p + 1), dtype=torch.complex128, device="cuda")
     with pytest.raises(lsms.LsmsError) as e:
