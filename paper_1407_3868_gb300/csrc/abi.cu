@@ -211,6 +211,7 @@ extern "C" void lsms_destroy(lsms_ctx* c) {
                     &c->gm_w, &c->sol, &c->ws_lp};
   for (DevBuf* b : bufs)
     if (b->ptr) cudaFree(b->ptr);
+  tc_free(c);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   for (cudaEvent_t e : c->ev)
     if (e) cudaEventDestroy(e);
@@ -237,6 +238,7 @@ extern "C" int lsms_set_particles(lsms_ctx* c, int n, const double* xy) {
   c->xc = n > 0 ? 0.5 * (xmin + xmax) : 0.0;
   std::vector<double> xs(n);
   for (int j = 0; j < n; ++j) xs[j] = c->cx[j] - c->xc;
+  tc_free(c);
   void* old[] = {c->d_cx, c->d_cy, c->d_eagg, c->d_edis, c->d_eagg_lp, c->d_edis_lp, c->d_lp_misc};
   for (void* q : old)
     if (q) cudaFree(q);
@@ -291,7 +293,8 @@ extern "C" int lsms_apply_ex(lsms_ctx* c, int nrhs, const double* x, double* y, 
   if ((rc = copy_in(c, c->ws_x, x, len))) return rc;
   if ((rc = ensure(c, c->ws_y, len * sizeof(double2)))) return rc;
   if ((rc = apply_device(c, nrhs, (const double2*)c->ws_x.ptr, (double2*)c->ws_y.ptr, flags, c->stream))) return rc;
-  return copy_out(c, y, c->ws_y.ptr, len);
+  if ((rc = copy_out(c, y, c->ws_y.ptr, len))) return rc;
+  return (flags & LSMS_APPLY_MIXED) ? mixed_check(c) : LSMS_OK;
 }
 
 extern "C" int lsms_apply(lsms_ctx* c, int nrhs, const double* x, double* y) {
@@ -345,6 +348,7 @@ extern "C" int lsms_aggregate(lsms_ctx* c, int nrhs, const double* beta, double*
   if ((rc = check_cuda(c, "aggregate"))) return rc;
   std::vector<cplx> pq((size_t)nrhs * 2 * ns);
   if ((rc = copy_out(c, (double*)pq.data(), c->ws_pq.ptr, pq.size()))) return rc;
+  if (precision == LSMS_MIXED && (rc = mixed_check(c))) return rc;
   // the device works in x - xc; densities in absolute x carry exp(-i lambda xc)
   const std::vector<cplx> ph = shift_phase(c, -1.0);
   cplx* pp = reinterpret_cast<cplx*>(p_plus);
@@ -409,7 +413,8 @@ extern "C" int lsms_disaggregate(lsms_ctx* c, int nrhs, const double* s_plus, co
     launch_zgemm_rows(c->d_edis, c->n, 2 * ns, (const double2*)c->ws_v.ptr, (double2*)c->ws_alpha.ptr, P, nrhs, c->stream);
   }
   if ((rc = check_cuda(c, "disaggregate"))) return rc;
-  return copy_out(c, alpha, c->ws_alpha.ptr, len);
+  if ((rc = copy_out(c, alpha, c->ws_alpha.ptr, len))) return rc;
+  return precision == LSMS_MIXED ? mixed_check(c) : LSMS_OK;
 }
 
 // a_inc of line sources on the device: [nsrc][N][P] into `out`.

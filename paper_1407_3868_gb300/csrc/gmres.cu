@@ -323,6 +323,7 @@ int gmres_device(lsms_ctx* c, const double2* rhs, double2* x, bool x_nonzero, do
     cudaMemcpyAsync((void*)hs, g.st, sizeof(GmState), cudaMemcpyDeviceToHost, stream);
     cudaStreamSynchronize(stream);
     if ((rc = check_cuda(c, "gmres iteration"))) return rc;
+    if ((flags & LSMS_APPLY_MIXED) && (rc = mixed_check(c))) return rc;
     ++k;
     res = hs->res;
     if (hist && n_hist && *n_hist < hist_cap) hist[(*n_hist)++] = res;

@@ -70,6 +70,7 @@ struct lsms_ctx {
   void* d_edis_lp = nullptr;
   void* d_lp_misc = nullptr;
   DevBuf ws_lp;
+  void* tc = nullptr;               // tensor-core path state (contour_tc.cu)
 
   // workspaces
   DevBuf ws_x, ws_y, ws_xs, ws_alpha, ws_g, ws_v, ws_pq, ws_sig, ws_aux;

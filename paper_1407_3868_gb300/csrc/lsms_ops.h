@@ -18,7 +18,10 @@ int reflection_f64(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cud
 // a_inc for nsrc line sources (device source array), out [nsrc][N][P]
 int incident_device(lsms_ctx* c, int nsrc, const double* d_src, double2* out, cudaStream_t st);
 
-// mixed-precision contour contractions (mixed.cu)
+// mixed-precision contour contractions on the tensor cores (contour_tc.cu)
+int tc_setup(lsms_ctx* c);            // BF16 planes of the layout's tables (after set_particles)
+void tc_free(lsms_ctx* c);
+int mixed_check(lsms_ctx* c);         // reads and clears the device error flag of the TC kernels
 int build_lowp_tables(lsms_ctx* c);
 // alpha = T xs in FP32 arithmetic (sums of the per-split FP32 partials accumulated in FP64)
 int translate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st);

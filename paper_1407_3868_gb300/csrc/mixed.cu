@@ -316,7 +316,9 @@ int build_lowp_tables(lsms_ctx* c) {
   if (c->n > 0)
     k_centres_ff<<<(c->n + 255) / 256, 256, 0, c->stream>>>(c->d_cx, c->d_cy, c->n, (float4*)c->d_lp_misc);
   cudaStreamSynchronize(c->stream);
-  return check_cuda(c, "build_lowp_tables");
+  int rc = check_cuda(c, "build_lowp_tables");
+  if (rc) return rc;
+  return tc_setup(c);
 }
 
 // Splits of the source range so that the grid covers the GPU several times.
@@ -350,20 +352,6 @@ int translate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cu
   launch_translate_kernel(grid, st, (const float4*)c->d_lp_misc, n, p, kh, kl, xs32, part, sps, nrhs);
   k_reduce_parts<<<(int)g, 256, 0, st>>>(part, splits, len, alpha);
   return check_cuda(c, "translate_mixed");
-}
-
-int aggregate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* G, cudaStream_t st) {
-  launch_zgemm_rows(c->d_eagg, 2 * c->ns, c->n, xs, G, c->P, nrhs, st);
-  return LSMS_OK;
-}
-
-int disaggregate_mixed(lsms_ctx* c, int nrhs, const double2* V, double2* alpha, cudaStream_t st) {
-  launch_zgemm_rows(c->d_edis, c->n, 2 * c->ns, V, alpha, c->P, nrhs, st);
-  return LSMS_OK;
-}
-
-int reflection_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st) {
-  return reflection_f64(c, nrhs, xs, alpha, st);
 }
 
 // ---------------------------------------------------------------------------------------------

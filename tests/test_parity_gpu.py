@@ -126,6 +126,24 @@ def test_aggregate_reflect_disaggregate(which, small, ragged):
     assert rel(a, a_o, case.ws) < TOL64
 
 
+@pytest.mark.parametrize("which", ["small", "ragged"])
+def test_tensor_core_aggregate_and_disaggregate(which, small, ragged, L):
+    # split-BF16 (3 planes, 6 products) tcgen05 contractions are FP32-accurate
+    case = small if which == "small" else ragged
+    beta = case.rand_beta(13, nrhs=2)
+    pp, qm = case.ctx.aggregate(beta, precision=L.LSMS_MIXED)
+    for r in range(2):
+        pp_o, qm_o = case.pr.aggregate(beta[r])
+        assert rel(pp[r], pp_o) < 1e-6 and rel(qm[r], qm_o) < 1e-6
+    pp_o, qm_o = case.pr.aggregate(beta[0])
+    sig_o = case.pr.layer_densities(None, pp_o, qm_o)
+    a = case.ctx.disaggregate(sig_o[:, 1], sig_o[:, 2], precision=L.LSMS_MIXED)[0]
+    assert rel(a, case.pr.disaggregate(sig_o[:, 1], sig_o[:, 2]), case.ws) < 1e-6
+    # the reflected coupling composes both contractions with an FP32 intermediate (P+, Q-)
+    aR = case.ctx.apply(beta[:1], L.APPLY_ALPHA | L.APPLY_NO_TRANSLATION | L.APPLY_MIXED)[0]
+    assert rel(aR, case.pr.reflection(beta[0]), case.ws) < 4e-6
+
+
 def test_incident_local_expansion(small):
     src = np.array([[0.0, 1.0], [0.7, 0.4]])
     a = small.ctx.incident(src)
