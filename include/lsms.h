@@ -159,8 +159,9 @@ int lsms_num_particles(const lsms_ctx* ctx);
 /* lsms_solve — beta for each source from (I - S(T + R)) beta = S a_inc (Sec. 3.2 GMRES,
  *   Sec. 5.4 Eq. "schur").  GMRES runs on the device on the scaled system (b = |H_n(k2R)| beta):
  *   x0 = 0 (or x0 if given, unscaled [n_src][N][P]), stop when the residual estimate divided by
- *   ||rhs|| <= tol or after maxiter iterations (then LSMS_ERR_NOT_CONVERGED with the iterate in
- *   beta_out).  LSMS_MIXED: inner GMRES on the mixed operator inside an FP64 refinement loop.
+ *   ||rhs|| <= tol or after maxiter iterations, 0 < maxiter <= 4096 (then LSMS_ERR_NOT_CONVERGED
+ *   with the iterate in beta_out).  GMRES is not restarted: its basis holds maxiter + 1 vectors
+ *   of N P complex numbers in device memory.  LSMS_MIXED: inner GMRES on the mixed operator inside an FP64 refinement loop.
  *   beta_out: [n_src][N][P] (may be NULL).  The solution is kept in the context for
  *   lsms_eval_field.  info may be NULL (summary of the last source). */
 int lsms_solve(lsms_ctx* ctx, int n_src, const double* src_xy, double tol, int maxiter,

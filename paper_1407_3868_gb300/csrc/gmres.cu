@@ -37,9 +37,11 @@ struct GmState {
   int flag;       // 1: non-finite value seen
 };
 
-constexpr int DOT_T = 2048;
+constexpr int DOT_T = 1024;    // elements per CTA
+constexpr int DOT_V = 32;      // vectors per CTA (4 per warp)
 
-// out[i] += sum_t conj(V[i][t]) w[t] for i < nv (out pre-zeroed).
+// out[i] += sum_t conj(V[i][t]) w[t] for i < nv (out pre-zeroed).  Grid: (element chunks, vector
+// groups), so that the whole GPU works even for short Krylov bases.
 __global__ void __launch_bounds__(256)
 k_mdot(const double2* __restrict__ V, long long ldv, int nv, const double2* __restrict__ w,
        long long L, double2* __restrict__ out) {
@@ -49,7 +51,8 @@ k_mdot(const double2* __restrict__ V, long long ldv, int nv, const double2* __re
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) ws[i] = w[t0 + i];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = warp; i < nv; i += nw) {
+  const int i1 = min(nv, (int)(blockIdx.y + 1) * DOT_V);
+  for (int i = blockIdx.y * DOT_V + warp; i < i1; i += nw) {
     const double2* vi = V + (long long)i * ldv + t0;
     double2 acc = make_double2(0.0, 0.0);
     for (int t = lane; t < cnt; t += 32) {
@@ -150,47 +153,64 @@ __global__ void k_gm_start(const double2* __restrict__ nrm2, const double2* __re
 }
 
 // Column k of the Hessenberg matrix: H[0..k][k] = h1 + h2, H[k+1][k] = ||w||; apply the previous
-// Givens rotations, form the new one, update g and the residual estimate |g_{k+1}| / beta0.
-__global__ void k_gm_column(int k, const double2* __restrict__ h1, const double2* __restrict__ h2,
-                            const double2* __restrict__ nrm2, double2* __restrict__ H, int ldh,
-                            double2* __restrict__ cs, double2* __restrict__ sn,
-                            double2* __restrict__ g, GmState* __restrict__ st) {
-  double2* col = H + (long long)k * ldh;
-  for (int i = 0; i <= k; ++i) col[i] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
-  const double hn = sqrt(nrm2[0].x);
-  st->hn = hn;
-  st->inv = hn > 0.0 ? 1.0 / hn : 0.0;
-  col[k + 1] = make_double2(hn, 0.0);
-  for (int i = 0; i < k; ++i) {
-    const double2 a = col[i], b = col[i + 1];
-    // [conj(c) conj(s); -s c] [a; b]
-    const double2 t = make_double2(cjmul(cs[i], a).x + cjmul(sn[i], b).x,
-                                   cjmul(cs[i], a).y + cjmul(sn[i], b).y);
-    const double2 u = make_double2(-cmul(sn[i], a).x + cmul(cs[i], b).x,
-                                   -cmul(sn[i], a).y + cmul(cs[i], b).y);
-    col[i] = t;
-    col[i + 1] = u;
+// Givens rotations, form the new one, update g and the residual estimate |g_{k+1}| / ||rhs||.
+// One warp: the lanes stage the column and the rotations in shared memory, lane 0 sweeps them.
+constexpr int GIVENS_MAX = 4096;
+
+__global__ void __launch_bounds__(32)
+k_gm_column(int k, const double2* __restrict__ h1, const double2* __restrict__ h2,
+            const double2* __restrict__ nrm2, double2* __restrict__ H, int ldh,
+            double2* __restrict__ cs, double2* __restrict__ sn, double2* __restrict__ g,
+            GmState* __restrict__ st) {
+  extern __shared__ double2 sm[];
+  double2* col = sm;                    // [k + 2]
+  double2* c_s = sm + (k + 2);          // [k]
+  double2* s_s = c_s + k;               // [k]
+  const int lane = threadIdx.x;
+  for (int i = lane; i <= k; i += 32) col[i] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
+  for (int i = lane; i < k; i += 32) {
+    c_s[i] = cs[i];
+    s_s[i] = sn[i];
   }
-  const double2 a = col[k];
-  const double r = hypot(hypot(a.x, a.y), hn);
-  double2 c, s;
-  if (r > 0.0) {
-    c = make_double2(a.x / r, a.y / r);
-    s = make_double2(hn / r, 0.0);
-  } else {
-    c = make_double2(1.0, 0.0);
-    s = make_double2(0.0, 0.0);
+  __syncwarp();
+  if (lane == 0) {
+    const double hn = sqrt(nrm2[0].x);
+    st->hn = hn;
+    st->inv = hn > 0.0 ? 1.0 / hn : 0.0;
+    col[k + 1] = make_double2(hn, 0.0);
+    for (int i = 0; i < k; ++i) {
+      const double2 a = col[i], b = col[i + 1];
+      const double2 ci = c_s[i], si = s_s[i];
+      // [conj(c) conj(s); -s c] [a; b]
+      const double2 t = make_double2(cjmul(ci, a).x + cjmul(si, b).x, cjmul(ci, a).y + cjmul(si, b).y);
+      const double2 u = make_double2(-cmul(si, a).x + cmul(ci, b).x, -cmul(si, a).y + cmul(ci, b).y);
+      col[i] = t;
+      col[i + 1] = u;
+    }
+    const double2 a = col[k];
+    const double r = hypot(hypot(a.x, a.y), hn);
+    double2 c, s;
+    if (r > 0.0) {
+      c = make_double2(a.x / r, a.y / r);
+      s = make_double2(hn / r, 0.0);
+    } else {
+      c = make_double2(1.0, 0.0);
+      s = make_double2(0.0, 0.0);
+    }
+    cs[k] = c;
+    sn[k] = s;
+    col[k] = make_double2(r, 0.0);
+    col[k + 1] = make_double2(0.0, 0.0);
+    const double2 gk = g[k];
+    g[k] = cjmul(c, gk);
+    g[k + 1] = make_double2(-cmul(s, gk).x, -cmul(s, gk).y);
+    const double res = hypot(g[k + 1].x, g[k + 1].y) / st->ref;
+    st->res = res;
+    if (!isfinite(res) || !isfinite(hn)) st->flag = 1;
   }
-  cs[k] = c;
-  sn[k] = s;
-  col[k] = make_double2(r, 0.0);
-  col[k + 1] = make_double2(0.0, 0.0);
-  const double2 gk = g[k];
-  g[k] = cjmul(c, gk);
-  g[k + 1] = make_double2(-cmul(s, gk).x, -cmul(s, gk).y);
-  const double res = hypot(g[k + 1].x, g[k + 1].y) / st->ref;
-  st->res = res;
-  if (!isfinite(res) || !isfinite(hn)) st->flag = 1;
+  __syncwarp();
+  double2* Hc = H + (long long)k * ldh;
+  for (int i = lane; i <= k + 1; i += 32) Hc[i] = col[i];
 }
 
 // Back substitution H[0..k)[0..k) y = g, one warp (lanes over the column index).
@@ -225,8 +245,8 @@ inline int grid_for(long long total, int block) {
 void mdot(const double2* V, long long ldv, int nv, const double2* w, long long L, double2* out,
           cudaStream_t st) {
   cudaMemsetAsync(out, 0, (size_t)nv * sizeof(double2), st);
-  const int blocks = (int)((L + DOT_T - 1) / DOT_T);
-  k_mdot<<<blocks, 256, 0, st>>>(V, ldv, nv, w, L, out);
+  dim3 grid((unsigned)((L + DOT_T - 1) / DOT_T), (unsigned)((nv + DOT_V - 1) / DOT_V));
+  k_mdot<<<grid, 256, 0, st>>>(V, ldv, nv, w, L, out);
 }
 
 void maxpy(const double2* V, long long ldv, int nv, const double2* h, double2* w, long long L,
@@ -287,6 +307,12 @@ int gmres_device(lsms_ctx* c, const double2* rhs, double2* x, bool x_nonzero, do
   if ((rc = gm_alloc(c, L, maxiter, g))) return rc;
   volatile GmState* hs = (volatile GmState*)c->h_pinned;
   *iters = 0;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gm_column, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)((3 * GIVENS_MAX + 2) * sizeof(double2)));
+    attr = true;
+  }
   // r0 = rhs - A x
   if (x_nonzero) {
     if ((rc = apply_device(c, 1, x, g.w, flags, stream))) return rc;
@@ -318,7 +344,8 @@ int gmres_device(lsms_ctx* c, const double2* rhs, double2* x, bool x_nonzero, do
     mdot(g.V, L, k + 1, g.w, L, g.h2, stream);
     maxpy(g.V, L, k + 1, g.h2, g.w, L, -1.0, stream);
     mdot(g.w, L, 1, g.w, L, g.nrm, stream);
-    k_gm_column<<<1, 1, 0, stream>>>(k, g.h1, g.h2, g.nrm, g.H, g.ldh, g.cs, g.sn, g.g, g.st);
+    k_gm_column<<<1, 32, (size_t)(3 * k + 2) * sizeof(double2), stream>>>(k, g.h1, g.h2, g.nrm, g.H, g.ldh,
+                                                                        g.cs, g.sn, g.g, g.st);
     k_scale_by<<<grid_for(L, 256), 256, 0, stream>>>(g.V + (long long)(k + 1) * L, g.w, g.st, L);
     cudaMemcpyAsync((void*)hs, g.st, sizeof(GmState), cudaMemcpyDeviceToHost, stream);
     cudaStreamSynchronize(stream);
@@ -353,7 +380,8 @@ extern "C" int lsms_solve(lsms_ctx* c, int nsrc, const double* src_xy, double to
   int rc;
   if ((rc = need_particles(c))) return rc;
   if ((rc = validate_sources(c, nsrc, src_xy))) return rc;
-  if (!(tol > 0.0) || maxiter <= 0) return ctx_fail(c, LSMS_ERR_ARG, "tol must be > 0 and maxiter > 0");
+  if (!(tol > 0.0) || maxiter <= 0 || maxiter > GIVENS_MAX)
+    return ctx_fail(c, LSMS_ERR_ARG, "tol must be > 0 and 0 < maxiter <= 4096");
   const long long L = (long long)c->n * c->P;
   cudaStream_t st = c->stream;
   if (info) { info->iters = 0; info->outer_iters = 0; info->rel_res = 0; info->rel_res_fp64 = 0; info->n_history = 0; }
@@ -385,7 +413,7 @@ extern "C" int lsms_solve(lsms_ctx* c, int nsrc, const double* src_xy, double to
       nonzero = true;
     }
     int it = 0, outer = 0, nh = 0;
-    double r_est = 0.0;
+    double r_est = 0.0, true_res = -1.0;
     int rc_s = LSMS_OK;
     double* hist = info ? info->history : nullptr;
     const int hcap = info ? info->history_cap : 0;
@@ -395,15 +423,24 @@ extern "C" int lsms_solve(lsms_ctx* c, int nsrc, const double* src_xy, double to
     } else {
       // FP64 refinement: r = rhs - A x (FP64 operator); inner GMRES on the mixed operator.
       const double rhs_norm = norm_device(c, rhs, L, tmp, st);
+      const double inv_norm = rhs_norm > 0 ? 1.0 / rhs_norm : 1.0;
       if (!nonzero) cudaMemsetAsync(xs, 0, L * sizeof(double2), st);
       const int max_outer = 20;
       const double inner_tol = 1e-5;
       rc_s = LSMS_ERR_NOT_CONVERGED;
       for (outer = 0; outer < max_outer && it < maxiter; ++outer) {
-        if ((rc = apply_device(c, 1, xs, tmp, LSMS_APPLY_SCALED, st))) return rc;
-        k_sub<<<grid_for(L, 256), 256, 0, st>>>(res, rhs, tmp, L);
-        const double rn = norm_device(c, res, L, tmp, st) / (rhs_norm > 0 ? rhs_norm : 1.0);
+        double rn;
+        if (outer == 0 && !nonzero) {
+          // x = 0: the residual is the right-hand side itself
+          cudaMemcpyAsync(res, rhs, L * sizeof(double2), cudaMemcpyDeviceToDevice, st);
+          rn = 1.0;
+        } else {
+          if ((rc = apply_device(c, 1, xs, tmp, LSMS_APPLY_SCALED, st))) return rc;
+          k_sub<<<grid_for(L, 256), 256, 0, st>>>(res, rhs, tmp, L);
+          rn = norm_device(c, res, L, tmp, st) * inv_norm;
+        }
         r_est = rn;
+        true_res = rn;
         if (!std::isfinite(rn)) { rc_s = ctx_fail(c, LSMS_ERR_NONFINITE, "non-finite refinement residual"); break; }
         if (rn <= tol) { rc_s = LSMS_OK; break; }
         int it_in = 0;
@@ -414,19 +451,25 @@ extern "C" int lsms_solve(lsms_ctx* c, int nsrc, const double* src_xy, double to
         it += it_in;
         if (rci != LSMS_OK && rci != LSMS_ERR_NOT_CONVERGED) { rc_s = rci; break; }
         k_add<<<grid_for(L, 256), 256, 0, st>>>(xs, dx, L);              // x += dx
+        true_res = -1.0;
       }
     }
-    // true FP64 residual of the final iterate
-    if ((rc = apply_device(c, 1, xs, tmp, LSMS_APPLY_SCALED, st))) return rc;
-    k_sub<<<grid_for(L, 256), 256, 0, st>>>(res, rhs, tmp, L);
-    const double rn = norm_device(c, res, L, tmp, st);
-    const double bn = norm_device(c, rhs, L, tmp, st);
+    // true FP64 residual of the final iterate (the refinement loop already has it when it stopped
+    // on a fresh residual)
+    double rel_fp64 = true_res;
+    if (rel_fp64 < 0.0) {
+      if ((rc = apply_device(c, 1, xs, tmp, LSMS_APPLY_SCALED, st))) return rc;
+      k_sub<<<grid_for(L, 256), 256, 0, st>>>(res, rhs, tmp, L);
+      const double rn = norm_device(c, res, L, tmp, st);
+      const double bn = norm_device(c, rhs, L, tmp, st);
+      rel_fp64 = bn > 0 ? rn / bn : 0.0;
+    }
     launch_diag_scale(xs, c->d_scale_in + c->P, beta, L, c->P, st);   // beta = D^{-1} b
     if (info) {
       info->iters += it;
       info->outer_iters += outer;
       info->rel_res = r_est;
-      info->rel_res_fp64 = bn > 0 ? rn / bn : 0.0;
+      info->rel_res_fp64 = rel_fp64;
       info->n_history = nh;
     }
     if (rc_s != LSMS_OK && status == LSMS_OK) status = rc_s;

@@ -59,10 +59,10 @@ constexpr int TW = 4;    // target discs (warps) per CTA
 constexpr int CH = 32;   // source discs per staged chunk (one per lane for the Hankel sequences)
 constexpr int HS = 65;   // length of a pair's sequence h_s, s = -2p..2p (4p + 1 <= 61); odd stride avoids bank conflicts
 
-// h[s + 2p] = H_s(k rho) exp(i s phi), s = -2p..2p, for the pair offset (dx, dy) = x_l - x_m.
-// H_0, H_1 from the CUDA math library; H_{q+1} = (2q/z) H_q - H_{q-1} forward (stable normwise
-// because the Y part dominates for q > z); H_{-q} = (-1)^q H_q.
-__device__ void hankel_sequence_f64(double dx, double dy, double k, int p, double2* h) {
+// h[s + 2p] = H_s(k rho) exp(i s phi) and hsum[s + 2p] = Re h + Im h, s = -2p..2p, for the pair
+// offset (dx, dy) = x_l - x_m.  H_0, H_1 from the CUDA math library; H_{q+1} = (2q/z) H_q - H_{q-1}
+// forward (stable normwise because the Y part dominates for q > z); H_{-q} = (-1)^q H_q.
+__device__ void hankel_sequence_f64(double dx, double dy, double k, int p, double2* h, double* hsum) {
   const double rho = hypot(dx, dy);
   const double z = k * rho;
   const double2 e1 = make_double2(dx / rho, dy / rho);
@@ -70,13 +70,17 @@ __device__ void hankel_sequence_f64(double dx, double dy, double k, int p, doubl
   double2 hm = make_double2(j0(z), y0(z));
   double2 hq = make_double2(j1(z), y1(z));
   h[c0] = hm;
+  hsum[c0] = hm.x + hm.y;
   double2 eq = e1;
   const double iz = 1.0 / z;
   for (int q = 1; q <= 2 * p; ++q) {
     const double2 v = cmul(hq, eq);
     h[c0 + q] = v;
-    const double2 u = cmul(hq, make_double2(eq.x, -eq.y));
-    h[c0 - q] = (q & 1) ? make_double2(-u.x, -u.y) : u;
+    hsum[c0 + q] = v.x + v.y;
+    double2 u = cmul(hq, make_double2(eq.x, -eq.y));
+    if (q & 1) u = make_double2(-u.x, -u.y);
+    h[c0 - q] = u;
+    hsum[c0 - q] = u.x + u.y;
     if (q < 2 * p) {
       const double f = 2.0 * q * iz;
       const double2 hn = make_double2(f * hq.x - hm.x, f * hq.y - hm.y);
@@ -87,12 +91,18 @@ __device__ void hankel_sequence_f64(double dx, double dy, double k, int p, doubl
   }
 }
 
-__global__ void __launch_bounds__(TW * 32)
+// alpha^l_nu = sum_{m != l} sum_n h^{lm}_{n - nu} xs^m_n.  One warp per target disc, lane = nu.
+// Complex products use three real FMAs (Gauss): A += hr br, B += hi bi, C += (hr+hi)(br+bi);
+// alpha = (A - B) + i (C - A - B).  The sums hr+hi and br+bi are formed once, when the sequence is
+// generated and when the source coefficients are staged.
+__global__ void __launch_bounds__(TW * 32, 1)
 k_translate_f64(const double* __restrict__ cx, const double* __restrict__ cy, int n, int p,
                 double k, const double2* __restrict__ xs, double2* __restrict__ alpha) {
   extern __shared__ double2 smem[];
-  double2* sb = smem;                  // [CH][32] staged source coefficients
-  double2* sh = smem + CH * 32;        // [TW][CH][HS] pair sequences
+  double2* sb = smem;                                   // [CH][32] staged source coefficients
+  double* sbs = (double*)(sb + CH * 32);                // [CH][32] their re + im
+  double2* sh = (double2*)(sbs + CH * 32);              // [TW][CH][HS] pair sequences
+  double* shs = (double*)(sh + TW * CH * HS);           // [TW][CH][HS] their re + im
   __shared__ double scx[CH], scy[CH];
   const int P = 2 * p + 1;
   const int r = blockIdx.y;
@@ -102,13 +112,16 @@ k_translate_f64(const double* __restrict__ cx, const double* __restrict__ cy, in
   const double xl = lvalid ? cx[l] : 0.0, yl = lvalid ? cy[l] : 0.0;
   const double2* xr = xs + (size_t)r * n * P;
   double2* hw = sh + (size_t)warp * CH * HS;
-  double2 acc = make_double2(0.0, 0.0);
+  double* hsw = shs + (size_t)warp * CH * HS;
+  double A = 0.0, B = 0.0, C = 0.0;
   for (int j0c = 0; j0c < n; j0c += CH) {
     const int cnt = min(CH, n - j0c);
     __syncthreads();
     for (int i = threadIdx.x; i < cnt * P; i += blockDim.x) {
       const int s = i / P, q = i - s * P;
-      sb[s * 32 + q] = xr[(size_t)(j0c + s) * P + q];
+      const double2 v = xr[(size_t)(j0c + s) * P + q];
+      sb[s * 32 + q] = v;
+      sbs[s * 32 + q] = v.x + v.y;
     }
     if (threadIdx.x < cnt) {
       scx[threadIdx.x] = cx[j0c + threadIdx.x];
@@ -117,22 +130,33 @@ k_translate_f64(const double* __restrict__ cx, const double* __restrict__ cy, in
     __syncthreads();
     if (lane < cnt) {
       double2* h = hw + lane * HS;
+      double* hsm = hsw + lane * HS;
       if (lvalid && j0c + lane != l) {
-        hankel_sequence_f64(xl - scx[lane], yl - scy[lane], k, p, h);
+        hankel_sequence_f64(xl - scx[lane], yl - scy[lane], k, p, h, hsm);
       } else {
-        for (int q = 0; q <= 4 * p; ++q) h[q] = make_double2(0.0, 0.0);
+        for (int q = 0; q <= 4 * p; ++q) {
+          h[q] = make_double2(0.0, 0.0);
+          hsm[q] = 0.0;
+        }
       }
     }
     __syncwarp();
     if (lvalid && lane < P) {
       for (int s = 0; s < cnt; ++s) {
         const double2* hs = hw + s * HS + 2 * p - lane;   // hs[q] = h_{n - nu}, n = q - p
+        const double* hss = hsw + s * HS + 2 * p - lane;
         const double2* bs = sb + s * 32;
-        for (int q = 0; q < P; ++q) acc = cfma(hs[q], bs[q], acc);
+        const double* bss = sbs + s * 32;
+        for (int q = 0; q < P; ++q) {
+          const double2 hv = hs[q], bv = bs[q];
+          A = fma(hv.x, bv.x, A);
+          B = fma(hv.y, bv.y, B);
+          C = fma(hss[q], bss[q], C);
+        }
       }
     }
   }
-  if (lvalid && lane < P) alpha[(size_t)r * n * P + (size_t)l * P + lane] = acc;
+  if (lvalid && lane < P) alpha[(size_t)r * n * P + (size_t)l * P + lane] = make_double2(A - B, C - A - B);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -357,7 +381,7 @@ void launch_scale_in(const double2* x, const double* scale, double2* xs, int nrh
 void launch_translate_f64(const double* cx, const double* cy, int n, int p, double k,
                           const double2* xs, double2* alpha, int nrhs, cudaStream_t st) {
   if (n == 0 || nrhs == 0) return;
-  const size_t smem = (size_t)(CH * 32 + TW * CH * HS) * sizeof(double2);
+  const size_t smem = (size_t)(CH * 32 + TW * CH * HS) * (sizeof(double2) + sizeof(double));
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_translate_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
