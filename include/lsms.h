@@ -163,7 +163,10 @@ int lsms_num_particles(const lsms_ctx* ctx);
  *   with the iterate in beta_out).  GMRES is not restarted: its basis holds maxiter + 1 vectors
  *   of N P complex numbers in device memory.  LSMS_MIXED: inner GMRES on the mixed operator inside an FP64 refinement loop.
  *   beta_out: [n_src][N][P] (may be NULL).  The solution is kept in the context for
- *   lsms_eval_field.  info may be NULL (summary of the last source). */
+ *   lsms_eval_field.  Several sources are solved together: one batched GMRES per source in
+ *   lockstep, each step one multi-right-hand-side application of the operator.  info may be NULL;
+ *   it reports the most iterations any source needed, the worst residuals and, for one source,
+ *   the residual history. */
 int lsms_solve(lsms_ctx* ctx, int n_src, const double* src_xy, double tol, int maxiter,
                const double* x0, double* beta_out, lsms_solve_info* info);
 

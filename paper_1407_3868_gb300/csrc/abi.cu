@@ -203,7 +203,7 @@ extern "C" void lsms_destroy(lsms_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   void* ptrs[] = {c->d_lam, c->d_g1, c->d_g2, c->d_refl, c->d_inc, c->d_field, c->d_fagg, c->d_udis,
                   c->d_scale_in, c->d_hscale, c->d_scale_out, c->d_cx, c->d_cy, c->d_eagg, c->d_edis,
-                  c->d_eagg_lp, c->d_edis_lp, c->d_lp_misc};
+                  c->d_eagg_lp, c->d_edis_lp, c->d_lp_misc, c->d_near_ptr, c->d_near_idx, c->d_near_h};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   DevBuf* bufs[] = {&c->ws_x, &c->ws_y, &c->ws_xs, &c->ws_alpha, &c->ws_g, &c->ws_v, &c->ws_pq,
@@ -213,7 +213,10 @@ extern "C" void lsms_destroy(lsms_ctx* c) {
     if (b->ptr) cudaFree(b->ptr);
   tc_free(c);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  if (c->gm_ring) cudaFreeHost(c->gm_ring);
   for (cudaEvent_t e : c->ev)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->gm_ev)
     if (e) cudaEventDestroy(e);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;

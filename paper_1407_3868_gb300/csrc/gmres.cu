@@ -1,12 +1,19 @@
 // Device-resident GMRES (Saad-Schultz, cited in Sec. 3.2 of the paper) on the scaled,
-// preconditioned disc system (I - D S (T + R) D^{-1}) b = D S a_inc, D = diag |H_n(k2 R)|, and the
-// FP64 iterative-refinement loop of the mixed-precision solve.
+// preconditioned disc system (I - D S (T + R) D^{-1}) b = D S a_inc, D = diag |H_n(k2 R)|, for one
+// or many right-hand sides at once, and the FP64 iterative-refinement loop of the mixed solve.
 //
-// Arnoldi uses classical Gram-Schmidt applied twice (CGS2); the Hessenberg matrix, the Givens
-// rotations and the residual estimate stay on the device.  The host only launches kernels and reads
-// one double (the residual estimate) per iteration to decide when to stop.
+// Several systems (one per line source) iterate in lockstep: the Krylov basis is laid out
+// [iteration][system][N P], so every Arnoldi step is one multi-right-hand-side application of the
+// operator.  Each system keeps its own Hessenberg matrix, Givens rotations and residual estimate on
+// the device; classical Gram-Schmidt takes a second pass only when the first one cancels much of the
+// new vector.  The host reads the per-system residual estimates two iterations late (pinned ring +
+// events), so the next Arnoldi steps are always queued, and records for each system the iteration at
+// which it met its tolerance; later iterations are discarded by solving its least-squares problem on
+// that many columns only.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "lsms_internal.h"
 #include "lsms_ops.h"
@@ -35,16 +42,24 @@ struct GmState {
   double hn;      // ||w|| of the last Arnoldi step
   double inv;     // scale for the next basis vector
   int flag;       // 1: non-finite value seen
+  int reorth;     // 1: the current Arnoldi step needs a second Gram-Schmidt pass
 };
 
 constexpr int DOT_T = 1024;    // elements per CTA
 constexpr int DOT_V = 32;      // vectors per CTA (4 per warp)
+constexpr int GIVENS_MAX = 4096;
 
-// out[i] += sum_t conj(V[i][t]) w[t] for i < nv (out pre-zeroed).  Grid: (element chunks, vector
-// groups), so that the whole GPU works even for short Krylov bases.
+// System b = blockIdx.z:  out[b][i] += sum_t conj(V[i][b][t]) w[b][t] for i < nv (out pre-zeroed).
+// V slots are ldv apart, system b sits at b L inside a slot.  With a gate the kernel does nothing
+// unless system b's state asks for a second Gram-Schmidt pass.
 __global__ void __launch_bounds__(256)
 k_mdot(const double2* __restrict__ V, long long ldv, int nv, const double2* __restrict__ w,
-       long long L, double2* __restrict__ out) {
+       long long L, double2* __restrict__ out, int out_stride, const GmState* __restrict__ gate) {
+  const int b = blockIdx.z;
+  if (gate && !gate[b].reorth) return;
+  V += (long long)b * L;
+  w += (long long)b * L;
+  out += (long long)b * out_stride;
   __shared__ double2 ws[DOT_T];
   const long long t0 = blockIdx.x * (long long)DOT_T;
   const int cnt = (int)min((long long)DOT_T, L - t0);
@@ -54,13 +69,19 @@ k_mdot(const double2* __restrict__ V, long long ldv, int nv, const double2* __re
   const int i1 = min(nv, (int)(blockIdx.y + 1) * DOT_V);
   for (int i = blockIdx.y * DOT_V + warp; i < i1; i += nw) {
     const double2* vi = V + (long long)i * ldv + t0;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int t = lane; t < cnt; t += 32) {
-      const double2 c = cjmul(vi[t], ws[t]);
-      acc.x += c.x;
-      acc.y += c.y;
+    double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
+    int t = lane;
+    for (; t + 32 < cnt; t += 64) {
+      const double2 c0 = cjmul(vi[t], ws[t]);
+      const double2 c1 = cjmul(vi[t + 32], ws[t + 32]);
+      a0.x += c0.x; a0.y += c0.y;
+      a1.x += c1.x; a1.y += c1.y;
     }
-    acc = warp_sum(acc);
+    if (t < cnt) {
+      const double2 c0 = cjmul(vi[t], ws[t]);
+      a0.x += c0.x; a0.y += c0.y;
+    }
+    const double2 acc = warp_sum(make_double2(a0.x + a1.x, a0.y + a1.y));
     if (lane == 0) {
       atomicAdd(&out[i].x, acc.x);
       atomicAdd(&out[i].y, acc.y);
@@ -68,42 +89,198 @@ k_mdot(const double2* __restrict__ V, long long ldv, int nv, const double2* __re
   }
 }
 
-// w[t] += sign sum_i V[i][t] h[i]
+// System b = blockIdx.y:  w[b][t] += sign sum_{i < nv_b} V[i][b][t] h[b][i].  nv_b = nv, or
+// nv_arr[b] when given; with a gate only when system b needs a second pass.
 __global__ void __launch_bounds__(256)
-k_maxpy(const double2* __restrict__ V, long long ldv, int nv, const double2* __restrict__ h,
-        double2* __restrict__ w, long long L, double sign) {
+k_maxpy(const double2* __restrict__ V, long long ldv, int nv, const int* __restrict__ nv_arr,
+        const double2* __restrict__ h, int h_stride, double2* __restrict__ w, long long L,
+        double sign, const GmState* __restrict__ gate) {
+  const int b = blockIdx.y;
+  if (gate && !gate[b].reorth) return;
+  if (nv_arr) nv = nv_arr[b];
+  V += (long long)b * L;
+  w += (long long)b * L;
+  h += (long long)b * h_stride;
   __shared__ double2 hs[256];
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double2 acc = make_double2(0.0, 0.0);
+  double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
   for (int i0 = 0; i0 < nv; i0 += 256) {
     const int c = min(256, nv - i0);
     __syncthreads();
     if (threadIdx.x < c) hs[threadIdx.x] = h[i0 + threadIdx.x];
     __syncthreads();
     if (t < L) {
-      for (int i = 0; i < c; ++i) {
-        const double2 v = V[(long long)(i0 + i) * ldv + t];
-        const double2 hh = hs[i];
-        acc.x = fma(v.x, hh.x, fma(-v.y, hh.y, acc.x));
-        acc.y = fma(v.x, hh.y, fma(v.y, hh.x, acc.y));
+      int i = 0;
+      for (; i + 1 < c; i += 2) {
+        const double2 v0 = V[(long long)(i0 + i) * ldv + t];
+        const double2 v1 = V[(long long)(i0 + i + 1) * ldv + t];
+        const double2 h0 = hs[i], h1 = hs[i + 1];
+        a0.x = fma(v0.x, h0.x, fma(-v0.y, h0.y, a0.x));
+        a0.y = fma(v0.x, h0.y, fma(v0.y, h0.x, a0.y));
+        a1.x = fma(v1.x, h1.x, fma(-v1.y, h1.y, a1.x));
+        a1.y = fma(v1.x, h1.y, fma(v1.y, h1.x, a1.y));
+      }
+      if (i < c) {
+        const double2 v0 = V[(long long)(i0 + i) * ldv + t];
+        const double2 h0 = hs[i];
+        a0.x = fma(v0.x, h0.x, fma(-v0.y, h0.y, a0.x));
+        a0.y = fma(v0.x, h0.y, fma(v0.y, h0.x, a0.y));
       }
     }
   }
   if (t < L) {
-    w[t].x += sign * acc.x;
-    w[t].y += sign * acc.y;
+    w[t].x += sign * (a0.x + a1.x);
+    w[t].y += sign * (a0.y + a1.y);
   }
 }
 
-// dst = src * (*scale)
+// After the first Gram-Schmidt pass of system b = blockIdx.x: h1[0..k] = V^H w, h1[k+1] = ||w||^2.
+// The first pass removes ||h1||^2 from ||w||^2; if more than about half of it goes
+// (||w'|| < 0.7 ||w||), cancellation may have left w' not orthogonal enough and a second pass runs.
+__global__ void __launch_bounds__(32) k_gm_prep(int k, const double2* __restrict__ h1, int stride,
+                                                GmState* __restrict__ st) {
+  h1 += (long long)blockIdx.x * stride;
+  double s = 0.0;
+  for (int i = threadIdx.x; i <= k; i += 32) s += h1[i].x * h1[i].x + h1[i].y * h1[i].y;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) {
+    const double a = h1[k + 1].x;
+    st[blockIdx.x].reorth = (a - s < 0.49 * a) ? 1 : 0;
+  }
+}
+
+// Column k of system b = blockIdx.x: H[0..k][k] = h1 + h2, H[k+1][k] = ||w_final||; apply the
+// previous Givens rotations, form the new one, update g and the residual estimate.  The lanes
+// stage the column and the rotations in shared memory, lane 0 sweeps them.
+__global__ void __launch_bounds__(32)
+k_gm_column(int k, const double2* __restrict__ h1, const double2* __restrict__ h2, int stride,
+            double2* __restrict__ H, long long hstride, int ldh, double2* __restrict__ cs,
+            double2* __restrict__ sn, double2* __restrict__ g, GmState* __restrict__ st) {
+  extern __shared__ double2 sm[];
+  const int b = blockIdx.x;
+  h1 += (long long)b * stride;
+  h2 += (long long)b * stride;
+  cs += (long long)b * stride;
+  sn += (long long)b * stride;
+  g += (long long)b * stride;
+  H += (long long)b * hstride;
+  GmState* s = st + b;
+  double2* col = sm;                    // [k + 2]
+  double2* c_s = sm + (k + 2);          // [k]
+  double2* s_s = c_s + k;               // [k]
+  const int lane = threadIdx.x;
+  for (int i = lane; i <= k; i += 32) col[i] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
+  for (int i = lane; i < k; i += 32) {
+    c_s[i] = cs[i];
+    s_s[i] = sn[i];
+  }
+  // ||w_final||^2 = (second pass ? ||w'||^2 - ||h2||^2 : ||w||^2 - ||h1||^2)
+  const double2* hl = s->reorth ? h2 : h1;
+  double s2 = 0.0;
+  for (int i = lane; i <= k; i += 32) s2 += hl[i].x * hl[i].x + hl[i].y * hl[i].y;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  __syncwarp();
+  if (lane == 0) {
+    const double hn = sqrt(fmax(hl[k + 1].x - s2, 0.0));
+    s->hn = hn;
+    s->inv = hn > 0.0 ? 1.0 / hn : 0.0;
+    col[k + 1] = make_double2(hn, 0.0);
+    for (int i = 0; i < k; ++i) {
+      const double2 a = col[i], bb = col[i + 1];
+      const double2 ci = c_s[i], si = s_s[i];
+      // [conj(c) conj(s); -s c] [a; b]
+      const double2 t = make_double2(cjmul(ci, a).x + cjmul(si, bb).x, cjmul(ci, a).y + cjmul(si, bb).y);
+      const double2 u = make_double2(-cmul(si, a).x + cmul(ci, bb).x, -cmul(si, a).y + cmul(ci, bb).y);
+      col[i] = t;
+      col[i + 1] = u;
+    }
+    const double2 a = col[k];
+    const double r = hypot(hypot(a.x, a.y), hn);
+    double2 c, sg;
+    if (r > 0.0) {
+      c = make_double2(a.x / r, a.y / r);
+      sg = make_double2(hn / r, 0.0);
+    } else {
+      c = make_double2(1.0, 0.0);
+      sg = make_double2(0.0, 0.0);
+    }
+    cs[k] = c;
+    sn[k] = sg;
+    col[k] = make_double2(r, 0.0);
+    col[k + 1] = make_double2(0.0, 0.0);
+    const double2 gk = g[k];
+    g[k] = cjmul(c, gk);
+    g[k + 1] = make_double2(-cmul(sg, gk).x, -cmul(sg, gk).y);
+    const double res = hypot(g[k + 1].x, g[k + 1].y) / s->ref;
+    s->res = res;
+    if (!isfinite(res) || !isfinite(hn)) s->flag = 1;
+  }
+  __syncwarp();
+  double2* Hc = H + (long long)k * ldh;
+  for (int i = lane; i <= k + 1; i += 32) Hc[i] = col[i];
+}
+
+// Back substitution of system b = blockIdx.x: H[0..k_b)[0..k_b) y = g, one warp.
+__global__ void k_gm_backsolve(const int* __restrict__ kk, const double2* __restrict__ H,
+                               long long hstride, int ldh, const double2* __restrict__ g, int stride,
+                               double2* __restrict__ y) {
+  const int b = blockIdx.x;
+  const int k = kk[b];
+  H += (long long)b * hstride;
+  g += (long long)b * stride;
+  y += (long long)b * stride;
+  const int lane = threadIdx.x;
+  for (int i = k - 1; i >= 0; --i) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int j = i + 1 + lane; j < k; j += 32) {
+      const double2 c = cmul(H[(long long)j * ldh + i], y[j]);
+      s.x += c.x;
+      s.y += c.y;
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+      const double2 num = make_double2(g[i].x - s.x, g[i].y - s.y);
+      const double2 d = H[(long long)i * ldh + i];
+      const double dd = d.x * d.x + d.y * d.y;
+      y[i] = dd > 0.0 ? make_double2((num.x * d.x + num.y * d.y) / dd, (num.y * d.x - num.x * d.y) / dd)
+                      : make_double2(0.0, 0.0);
+    }
+    __syncwarp();
+  }
+}
+
+// System b = blockIdx.y: dst[b] = src[b] * st[b].inv
 __global__ void k_scale_by(double2* __restrict__ dst, const double2* __restrict__ src,
                            const GmState* __restrict__ st, long long L) {
-  const double s = st->inv;
+  const int b = blockIdx.y;
+  const double s = st[b].inv;
+  dst += (long long)b * L;
+  src += (long long)b * L;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L;
        t += (long long)gridDim.x * blockDim.x) {
     const double2 v = src[t];
     dst[t] = make_double2(v.x * s, v.y * s);
   }
+}
+
+// Start of system b = blockIdx.x: beta0 = ||r0||, ref = ||rhs|| (nrm[2b], nrm[2b + 1] hold their
+// squares), g = (beta0, 0, ...).
+__global__ void k_gm_start(const double2* __restrict__ nrm, GmState* __restrict__ st,
+                           double2* __restrict__ g, int stride) {
+  const int b = blockIdx.x;
+  const double bt = sqrt(nrm[2 * b].x);
+  const double ref = sqrt(nrm[2 * b + 1].x);
+  GmState* s = st + b;
+  s->beta0 = bt;
+  s->ref = ref > 0.0 ? ref : 1.0;
+  s->inv = bt > 0.0 ? 1.0 / bt : 0.0;
+  s->res = bt / s->ref;
+  s->flag = (isfinite(bt) && isfinite(ref)) ? 0 : 1;
+  s->reorth = 0;
+  s->hn = 0.0;
+  g[(long long)b * stride] = make_double2(bt, 0.0);
 }
 
 // dst = a - b
@@ -125,6 +302,15 @@ __global__ void k_add(double2* __restrict__ x, const double2* __restrict__ d, lo
   }
 }
 
+// Zero the vectors of the systems whose mask is 0: v[b][0..L)
+__global__ void k_mask_zero(double2* __restrict__ v, const int* __restrict__ mask, long long L) {
+  const int b = blockIdx.y;
+  if (mask[b]) return;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L;
+       t += (long long)gridDim.x * blockDim.x)
+    v[(long long)b * L + t] = make_double2(0.0, 0.0);
+}
+
 __global__ void k_diag_mul(const double2* __restrict__ x, const double2* __restrict__ s,
                            double2* __restrict__ y, long long total, int P) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -140,101 +326,6 @@ __global__ void k_diag_scale(const double2* __restrict__ x, const double* __rest
   }
 }
 
-__global__ void k_gm_start(const double2* __restrict__ nrm2, const double2* __restrict__ nrm2_rhs,
-                           GmState* __restrict__ st, double2* __restrict__ g) {
-  const double b = sqrt(nrm2[0].x);
-  const double ref = sqrt(nrm2_rhs[0].x);
-  st->beta0 = b;
-  st->ref = ref > 0.0 ? ref : 1.0;
-  st->inv = b > 0.0 ? 1.0 / b : 0.0;
-  st->res = b / st->ref;
-  st->flag = (isfinite(b) && isfinite(ref)) ? 0 : 1;
-  g[0] = make_double2(b, 0.0);
-}
-
-// Column k of the Hessenberg matrix: H[0..k][k] = h1 + h2, H[k+1][k] = ||w||; apply the previous
-// Givens rotations, form the new one, update g and the residual estimate |g_{k+1}| / ||rhs||.
-// One warp: the lanes stage the column and the rotations in shared memory, lane 0 sweeps them.
-constexpr int GIVENS_MAX = 4096;
-
-__global__ void __launch_bounds__(32)
-k_gm_column(int k, const double2* __restrict__ h1, const double2* __restrict__ h2,
-            const double2* __restrict__ nrm2, double2* __restrict__ H, int ldh,
-            double2* __restrict__ cs, double2* __restrict__ sn, double2* __restrict__ g,
-            GmState* __restrict__ st) {
-  extern __shared__ double2 sm[];
-  double2* col = sm;                    // [k + 2]
-  double2* c_s = sm + (k + 2);          // [k]
-  double2* s_s = c_s + k;               // [k]
-  const int lane = threadIdx.x;
-  for (int i = lane; i <= k; i += 32) col[i] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
-  for (int i = lane; i < k; i += 32) {
-    c_s[i] = cs[i];
-    s_s[i] = sn[i];
-  }
-  __syncwarp();
-  if (lane == 0) {
-    const double hn = sqrt(nrm2[0].x);
-    st->hn = hn;
-    st->inv = hn > 0.0 ? 1.0 / hn : 0.0;
-    col[k + 1] = make_double2(hn, 0.0);
-    for (int i = 0; i < k; ++i) {
-      const double2 a = col[i], b = col[i + 1];
-      const double2 ci = c_s[i], si = s_s[i];
-      // [conj(c) conj(s); -s c] [a; b]
-      const double2 t = make_double2(cjmul(ci, a).x + cjmul(si, b).x, cjmul(ci, a).y + cjmul(si, b).y);
-      const double2 u = make_double2(-cmul(si, a).x + cmul(ci, b).x, -cmul(si, a).y + cmul(ci, b).y);
-      col[i] = t;
-      col[i + 1] = u;
-    }
-    const double2 a = col[k];
-    const double r = hypot(hypot(a.x, a.y), hn);
-    double2 c, s;
-    if (r > 0.0) {
-      c = make_double2(a.x / r, a.y / r);
-      s = make_double2(hn / r, 0.0);
-    } else {
-      c = make_double2(1.0, 0.0);
-      s = make_double2(0.0, 0.0);
-    }
-    cs[k] = c;
-    sn[k] = s;
-    col[k] = make_double2(r, 0.0);
-    col[k + 1] = make_double2(0.0, 0.0);
-    const double2 gk = g[k];
-    g[k] = cjmul(c, gk);
-    g[k + 1] = make_double2(-cmul(s, gk).x, -cmul(s, gk).y);
-    const double res = hypot(g[k + 1].x, g[k + 1].y) / st->ref;
-    st->res = res;
-    if (!isfinite(res) || !isfinite(hn)) st->flag = 1;
-  }
-  __syncwarp();
-  double2* Hc = H + (long long)k * ldh;
-  for (int i = lane; i <= k + 1; i += 32) Hc[i] = col[i];
-}
-
-// Back substitution H[0..k)[0..k) y = g, one warp (lanes over the column index).
-__global__ void k_gm_backsolve(int k, const double2* __restrict__ H, int ldh,
-                               const double2* __restrict__ g, double2* __restrict__ y) {
-  const int lane = threadIdx.x;
-  for (int i = k - 1; i >= 0; --i) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int j = i + 1 + lane; j < k; j += 32) {
-      const double2 c = cmul(H[(long long)j * ldh + i], y[j]);
-      s.x += c.x;
-      s.y += c.y;
-    }
-    s = warp_sum(s);
-    if (lane == 0) {
-      const double2 num = make_double2(g[i].x - s.x, g[i].y - s.y);
-      const double2 d = H[(long long)i * ldh + i];
-      const double dd = d.x * d.x + d.y * d.y;
-      y[i] = make_double2((num.x * d.x + num.y * d.y) / dd, (num.y * d.x - num.x * d.y) / dd);
-    }
-    __syncwarp();
-  }
-}
-
 inline int grid_for(long long total, int block) {
   long long g = (total + block - 1) / block;
   if (g > 152LL * 32) g = 152LL * 32;
@@ -242,46 +333,75 @@ inline int grid_for(long long total, int block) {
   return (int)g;
 }
 
+// out[b * out_stride + i] = V_b[i]^H w_b, i < nv, for nb systems
 void mdot(const double2* V, long long ldv, int nv, const double2* w, long long L, double2* out,
-          cudaStream_t st) {
-  cudaMemsetAsync(out, 0, (size_t)nv * sizeof(double2), st);
-  dim3 grid((unsigned)((L + DOT_T - 1) / DOT_T), (unsigned)((nv + DOT_V - 1) / DOT_V));
-  k_mdot<<<grid, 256, 0, st>>>(V, ldv, nv, w, L, out);
+          int out_stride, int nb, cudaStream_t st, const GmState* gate = nullptr) {
+  for (int b = 0; b < nb; ++b)
+    cudaMemsetAsync(out + (long long)b * out_stride, 0, (size_t)nv * sizeof(double2), st);
+  dim3 grid((unsigned)((L + DOT_T - 1) / DOT_T), (unsigned)((nv + DOT_V - 1) / DOT_V), (unsigned)nb);
+  k_mdot<<<grid, 256, 0, st>>>(V, ldv, nv, w, L, out, out_stride, gate);
 }
 
-void maxpy(const double2* V, long long ldv, int nv, const double2* h, double2* w, long long L,
-           double sign, cudaStream_t st) {
-  k_maxpy<<<(int)((L + 255) / 256), 256, 0, st>>>(V, ldv, nv, h, w, L, sign);
+void maxpy(const double2* V, long long ldv, int nv, const int* nv_arr, const double2* h, int h_stride,
+           double2* w, long long L, double sign, int nb, cudaStream_t st, const GmState* gate = nullptr) {
+  dim3 grid((unsigned)((L + 255) / 256), (unsigned)nb);
+  k_maxpy<<<grid, 256, 0, st>>>(V, ldv, nv, nv_arr, h, h_stride, w, L, sign, gate);
 }
 
-// Small device scratch of one GMRES run.
+// Device scratch of one batched GMRES run.
 struct GmPtrs {
   double2 *V, *H, *h1, *h2, *g, *cs, *sn, *y, *nrm;
   GmState* st;
-  double2* w;
-  int ldh;
+  int* kk;
+  int ldh, stride;
+  long long hstride;
 };
 
-int gm_alloc(lsms_ctx* c, long long L, int maxiter, GmPtrs& p) {
+int gm_alloc(lsms_ctx* c, long long L, int nb, int maxiter, GmPtrs& p) {
   int rc;
-  if ((rc = ensure(c, c->gm_v, (size_t)(maxiter + 1) * L * sizeof(double2)))) return rc;
-  if ((rc = ensure(c, c->gm_h, (size_t)(maxiter + 1) * maxiter * sizeof(double2)))) return rc;
-  const size_t small = (size_t)(7 * (maxiter + 2) + 8) * sizeof(double2) + sizeof(GmState) + 64;
+  p.ldh = maxiter + 1;
+  p.stride = maxiter + 2;
+  p.hstride = (long long)maxiter * p.ldh;
+  if ((rc = ensure(c, c->gm_v, (size_t)(maxiter + 1) * nb * L * sizeof(double2)))) return rc;
+  if ((rc = ensure(c, c->gm_h, (size_t)nb * p.hstride * sizeof(double2)))) return rc;
+  const size_t small = (size_t)nb * (7 * (size_t)p.stride + 2) * sizeof(double2) + nb * sizeof(GmState) +
+                       nb * sizeof(int) + 256;
   if ((rc = ensure(c, c->gm_small, small))) return rc;
-  if ((rc = ensure(c, c->gm_w, (size_t)L * sizeof(double2)))) return rc;
   p.V = (double2*)c->gm_v.ptr;
   p.H = (double2*)c->gm_h.ptr;
-  p.ldh = maxiter + 1;
   double2* s = (double2*)c->gm_small.ptr;
-  p.h1 = s; s += maxiter + 2;
-  p.h2 = s; s += maxiter + 2;
-  p.g = s; s += maxiter + 2;
-  p.cs = s; s += maxiter + 2;
-  p.sn = s; s += maxiter + 2;
-  p.y = s; s += maxiter + 2;
-  p.nrm = s; s += maxiter + 2;
+  const long long bs = (long long)nb * p.stride;
+  p.h1 = s; s += bs;
+  p.h2 = s; s += bs;
+  p.g = s; s += bs;
+  p.cs = s; s += bs;
+  p.sn = s; s += bs;
+  p.y = s; s += bs;
+  p.nrm = s; s += 2 * (long long)nb;
   p.st = (GmState*)s;
-  p.w = (double2*)c->gm_w.ptr;
+  p.kk = (int*)(p.st + nb);
+  return LSMS_OK;
+}
+
+// pinned ring of per-system states: RING slots of nb states, read LAG iterations late
+constexpr int LAG = 2, RING = 8;
+
+int ensure_ring(lsms_ctx* c, int nb) {
+  const size_t need = (size_t)RING * nb * sizeof(GmState);
+  if (c->gm_ring_bytes < need) {
+    if (c->gm_ring) cudaFreeHost(c->gm_ring);
+    c->gm_ring = nullptr;
+    c->gm_ring_bytes = 0;
+    if (cudaMallocHost(&c->gm_ring, need) != cudaSuccess) {
+      cudaGetLastError();
+      return ctx_fail(c, LSMS_ERR_OOM, "cudaMallocHost failed for the GMRES state ring");
+    }
+    c->gm_ring_bytes = need;
+  }
+  if (!c->gm_ev[0])
+    for (int i = 0; i < RING; ++i)
+      if (cudaEventCreateWithFlags(&c->gm_ev[i], cudaEventDisableTiming) != cudaSuccess)
+        return check_cuda(c, "cudaEventCreate");
   return LSMS_OK;
 }
 
@@ -296,83 +416,118 @@ void launch_diag_scale(const double2* x, const double* s, double2* y, long long 
   if (total) k_diag_scale<<<grid_for(total, 256), 256, 0, st>>>(x, s, y, total, P);
 }
 
-// GMRES for A x = rhs with A = apply_device(flags), x (in: initial guess if x_nonzero, out:
-// solution).  Returns LSMS_OK, LSMS_ERR_NOT_CONVERGED or LSMS_ERR_NONFINITE.
-int gmres_device(lsms_ctx* c, const double2* rhs, double2* x, bool x_nonzero, double tol,
-                 int maxiter, int flags, int* iters, double* res_out, double* hist, int hist_cap,
-                 int* n_hist, cudaStream_t stream) {
+// Batched GMRES for A x_b = rhs_b, b < nb (rhs, x: [nb][L]); A = apply_device(flags) with nrhs = nb.
+// x: initial guesses if x_nonzero, solutions on return.  tol[b]: relative tolerance per system.
+// iters[b], res[b]: iterations used and final residual estimate.  Returns LSMS_OK when every system
+// converged, LSMS_ERR_NOT_CONVERGED or LSMS_ERR_NONFINITE otherwise.
+int gmres_batch(lsms_ctx* c, const double2* rhs, double2* x, bool x_nonzero, int nb, const double* tol,
+                int maxiter, int flags, int* iters, double* res, double* hist, int hist_cap,
+                int* n_hist, cudaStream_t stream) {
   const long long L = (long long)c->n * c->P;
   GmPtrs g;
   int rc;
-  if ((rc = gm_alloc(c, L, maxiter, g))) return rc;
-  volatile GmState* hs = (volatile GmState*)c->h_pinned;
-  *iters = 0;
+  if ((rc = gm_alloc(c, L, nb, maxiter, g))) return rc;
+  if ((rc = ensure_ring(c, nb))) return rc;
+  GmState* ring = (GmState*)c->gm_ring;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_gm_column, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)((3 * GIVENS_MAX + 2) * sizeof(double2)));
     attr = true;
   }
-  // r0 = rhs - A x
+  const long long slot = (long long)nb * L;              // distance between basis slots
+  // r0 = rhs - A x into basis slot 0 (slot 1 as scratch)
   if (x_nonzero) {
-    if ((rc = apply_device(c, 1, x, g.w, flags, stream))) return rc;
-    k_sub<<<grid_for(L, 256), 256, 0, stream>>>(g.V, rhs, g.w, L);
+    if ((rc = apply_device(c, nb, x, g.V + slot, flags, stream))) return rc;
+    k_sub<<<grid_for(slot, 256), 256, 0, stream>>>(g.V, rhs, g.V + slot, slot);
   } else {
-    cudaMemsetAsync(x, 0, L * sizeof(double2), stream);
-    cudaMemcpyAsync(g.V, rhs, L * sizeof(double2), cudaMemcpyDeviceToDevice, stream);
+    cudaMemsetAsync(x, 0, slot * sizeof(double2), stream);
+    cudaMemcpyAsync(g.V, rhs, slot * sizeof(double2), cudaMemcpyDeviceToDevice, stream);
   }
-  mdot(g.V, L, 1, g.V, L, g.nrm, stream);
-  mdot(rhs, L, 1, rhs, L, g.nrm + 1, stream);
-  k_gm_start<<<1, 1, 0, stream>>>(g.nrm, g.nrm + 1, g.st, g.g);
-  k_scale_by<<<grid_for(L, 256), 256, 0, stream>>>(g.V, g.V, g.st, L);
-  cudaMemcpyAsync((void*)hs, g.st, sizeof(GmState), cudaMemcpyDeviceToHost, stream);
+  mdot(g.V, slot, 1, g.V, L, g.nrm, 2, nb, stream);          // ||r0||^2 at nrm[2b]
+  mdot(rhs, slot, 1, rhs, L, g.nrm + 1, 2, nb, stream);      // ||rhs||^2 at nrm[2b + 1]
+  k_gm_start<<<nb, 1, 0, stream>>>(g.nrm, g.st, g.g, g.stride);
+  k_scale_by<<<dim3(grid_for(L, 256), nb), 256, 0, stream>>>(g.V, g.V, g.st, L);
+  cudaMemcpyAsync(ring, g.st, nb * sizeof(GmState), cudaMemcpyDeviceToHost, stream);
   cudaStreamSynchronize(stream);
   if ((rc = check_cuda(c, "gmres start"))) return rc;
-  if (hs->flag) return ctx_fail(c, LSMS_ERR_NONFINITE, "non-finite right-hand side");
-  if (hs->beta0 == 0.0 || hs->res <= tol) {
-    *res_out = hs->res;
-    return LSMS_OK;
+  std::vector<int> kdone(nb, -1);        // -1: still iterating; else iterations kept
+  bool nonfinite = false;
+  int active = 0;
+  for (int b = 0; b < nb; ++b) {
+    iters[b] = 0;
+    res[b] = ring[b].res;
+    if (ring[b].flag) nonfinite = true;
+    if (ring[b].beta0 == 0.0 || ring[b].res <= tol[b]) kdone[b] = 0;
+    else ++active;
   }
-  int k = 0;
-  double res = 1.0;
-  bool converged = false, nonfinite = false;
-  while (k < maxiter) {
-    double2* vk = g.V + (long long)k * L;
-    if ((rc = apply_device(c, 1, vk, g.w, flags, stream))) return rc;
-    mdot(g.V, L, k + 1, g.w, L, g.h1, stream);
-    maxpy(g.V, L, k + 1, g.h1, g.w, L, -1.0, stream);
-    mdot(g.V, L, k + 1, g.w, L, g.h2, stream);
-    maxpy(g.V, L, k + 1, g.h2, g.w, L, -1.0, stream);
-    mdot(g.w, L, 1, g.w, L, g.nrm, stream);
-    k_gm_column<<<1, 32, (size_t)(3 * k + 2) * sizeof(double2), stream>>>(k, g.h1, g.h2, g.nrm, g.H, g.ldh,
-                                                                        g.cs, g.sn, g.g, g.st);
-    k_scale_by<<<grid_for(L, 256), 256, 0, stream>>>(g.V + (long long)(k + 1) * L, g.w, g.st, L);
-    cudaMemcpyAsync((void*)hs, g.st, sizeof(GmState), cudaMemcpyDeviceToHost, stream);
-    cudaStreamSynchronize(stream);
+  if (nonfinite) return ctx_fail(c, LSMS_ERR_NONFINITE, "non-finite right-hand side");
+  int k = 0, checked = 0;
+  auto check = [&](int j) {              // consume the states after iteration j
+    cudaEventSynchronize(c->gm_ev[j % RING]);
+    const GmState* sj = ring + (size_t)(j % RING) * nb;
+    for (int b = 0; b < nb; ++b) {
+      if (kdone[b] >= 0) continue;
+      res[b] = sj[b].res;
+      if (nb == 1 && hist && n_hist && *n_hist < hist_cap) hist[(*n_hist)++] = res[b];
+      if (sj[b].flag) nonfinite = true;
+      if (sj[b].flag || res[b] <= tol[b] || sj[b].hn == 0.0) {
+        kdone[b] = j + 1;
+        --active;
+      }
+    }
+    checked = j + 1;
+  };
+  while (k < maxiter && active > 0 && !nonfinite) {
+    const double2* vk = g.V + (long long)k * slot;
+    double2* w = g.V + (long long)(k + 1) * slot;       // the new vectors are built in their slot
+    if ((rc = apply_device(c, nb, vk, w, flags, stream))) return rc;
+    mdot(g.V, slot, k + 2, w, L, g.h1, g.stride, nb, stream);          // V^H w and ||w||^2
+    k_gm_prep<<<nb, 32, 0, stream>>>(k, g.h1, g.stride, g.st);
+    maxpy(g.V, slot, k + 1, nullptr, g.h1, g.stride, w, L, -1.0, nb, stream);
+    mdot(g.V, slot, k + 2, w, L, g.h2, g.stride, nb, stream, g.st);   // zeros unless needed
+    maxpy(g.V, slot, k + 1, nullptr, g.h2, g.stride, w, L, -1.0, nb, stream, g.st);
+    k_gm_column<<<nb, 32, (size_t)(3 * k + 2) * sizeof(double2), stream>>>(
+        k, g.h1, g.h2, g.stride, g.H, g.hstride, g.ldh, g.cs, g.sn, g.g, g.st);
+    k_scale_by<<<dim3(grid_for(L, 256), nb), 256, 0, stream>>>(w, w, g.st, L);
+    cudaMemcpyAsync(ring + (size_t)(k % RING) * nb, g.st, nb * sizeof(GmState), cudaMemcpyDeviceToHost, stream);
+    cudaEventRecord(c->gm_ev[k % RING], stream);
     if ((rc = check_cuda(c, "gmres iteration"))) return rc;
-    if ((flags & LSMS_APPLY_MIXED) && (rc = mixed_check(c))) return rc;
+    if (k - LAG >= checked) check(k - LAG);
     ++k;
-    res = hs->res;
-    if (hist && n_hist && *n_hist < hist_cap) hist[(*n_hist)++] = res;
-    if (hs->flag) { nonfinite = true; break; }
-    if (res <= tol || hs->hn == 0.0) { converged = true; break; }
   }
-  *iters = k;
-  *res_out = res;
+  while (active > 0 && !nonfinite && checked < k) check(checked);   // drain
+  cudaStreamSynchronize(stream);
+  if ((flags & LSMS_APPLY_MIXED) && (rc = mixed_check(c))) return rc;
   if (nonfinite) return ctx_fail(c, LSMS_ERR_NONFINITE, "non-finite value in GMRES");
-  k_gm_backsolve<<<1, 32, 0, stream>>>(k, g.H, g.ldh, g.g, g.y);
-  maxpy(g.V, L, k, g.y, x, L, 1.0, stream);
+  bool all = true;
+  for (int b = 0; b < nb; ++b) {
+    if (kdone[b] < 0) {
+      kdone[b] = checked;
+      all = false;
+    }
+    iters[b] = kdone[b];
+  }
+  cudaMemcpyAsync(g.kk, kdone.data(), nb * sizeof(int), cudaMemcpyHostToDevice, stream);
+  k_gm_backsolve<<<nb, 32, 0, stream>>>(g.kk, g.H, g.hstride, g.ldh, g.g, g.stride, g.y);
+  int kmax = 0;
+  for (int b = 0; b < nb; ++b) kmax = std::max(kmax, kdone[b]);
+  if (kmax > 0) maxpy(g.V, slot, kmax, g.kk, g.y, g.stride, x, L, 1.0, nb, stream);
+  cudaStreamSynchronize(stream);
   if ((rc = check_cuda(c, "gmres update"))) return rc;
-  return converged ? LSMS_OK : LSMS_ERR_NOT_CONVERGED;
+  return all ? LSMS_OK : LSMS_ERR_NOT_CONVERGED;
 }
 
-// ||v||_2 on the device (read back synchronously)
-static double norm_device(lsms_ctx* c, const double2* v, long long L, double2* tmp, cudaStream_t st) {
-  mdot(v, L, 1, v, L, tmp, st);
-  double2 h;
-  cudaMemcpyAsync(&h, tmp, sizeof(double2), cudaMemcpyDeviceToHost, st);
+// ||v_b||_2 for nb vectors of length L (read back synchronously)
+static void norms_device(lsms_ctx* c, const double2* v, long long L, int nb, double2* tmp,
+                         cudaStream_t st, std::vector<double>& out) {
+  (void)c;
+  mdot(v, (long long)nb * L, 1, v, L, tmp, 1, nb, st);
+  std::vector<double2> h(nb);
+  cudaMemcpyAsync(h.data(), tmp, nb * sizeof(double2), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
-  return std::sqrt(h.x);
+  out.resize(nb);
+  for (int b = 0; b < nb; ++b) out[b] = std::sqrt(std::max(h[b].x, 0.0));
 }
 
 extern "C" int lsms_solve(lsms_ctx* c, int nsrc, const double* src_xy, double tol, int maxiter,
@@ -383,102 +538,127 @@ extern "C" int lsms_solve(lsms_ctx* c, int nsrc, const double* src_xy, double to
   if (!(tol > 0.0) || maxiter <= 0 || maxiter > GIVENS_MAX)
     return ctx_fail(c, LSMS_ERR_ARG, "tol must be > 0 and 0 < maxiter <= 4096");
   const long long L = (long long)c->n * c->P;
+  const long long LT = (long long)nsrc * L;
   cudaStream_t st = c->stream;
   if (info) { info->iters = 0; info->outer_iters = 0; info->rel_res = 0; info->rel_res_fp64 = 0; info->n_history = 0; }
   c->n_src = 0;
   c->src_xy.assign(src_xy, src_xy + 2 * nsrc);
-  if ((rc = ensure(c, c->sol, (size_t)(nsrc > 0 ? nsrc : 1) * (L > 0 ? L : 1) * sizeof(double2)))) return rc;
+  if ((rc = ensure(c, c->sol, (size_t)(LT > 0 ? LT : 1) * sizeof(double2)))) return rc;
   if (nsrc == 0) return LSMS_OK;
   if (L == 0) { c->n_src = nsrc; return LSMS_OK; }
-  if ((rc = ensure(c, c->gm_r, (size_t)3 * L * sizeof(double2) + 64))) return rc;
-  if ((rc = ensure(c, c->gm_x, (size_t)2 * L * sizeof(double2)))) return rc;
-  if ((rc = ensure(c, c->ws_aux, (size_t)2 * nsrc * sizeof(double)))) return rc;
-  cudaMemcpyAsync(c->ws_aux.ptr, src_xy, (size_t)2 * nsrc * sizeof(double), cudaMemcpyHostToDevice, st);
-  double2* ainc = (double2*)c->sol.ptr;                 // a_inc for every source, replaced by beta
-  if ((rc = incident_device(c, nsrc, (const double*)c->ws_aux.ptr, ainc, st))) return rc;
-  double2* rhs = (double2*)c->gm_r.ptr;
-  double2* res = rhs + L;
-  double2* tmp = res + L;
-  double2* xs = (double2*)c->gm_x.ptr;                  // scaled iterate
-  double2* dx = xs + L;
-  const bool mixed = c->precision == LSMS_MIXED;
-  int status = LSMS_OK;
-  for (int s = 0; s < nsrc; ++s) {
-    double2* beta = ainc + (long long)s * L;
-    launch_diag_mul(beta, c->d_scale_out + c->P, rhs, L, c->P, st);   // D S a_inc
-    bool nonzero = false;
-    if (x0) {
-      cudaMemcpyAsync(dx, x0 + (size_t)2 * s * L, L * sizeof(double2), cudaMemcpyHostToDevice, st);
-      launch_diag_scale(dx, c->d_hscale, xs, L, c->P, st);
-      nonzero = true;
-    }
-    int it = 0, outer = 0, nh = 0;
-    double r_est = 0.0, true_res = -1.0;
-    int rc_s = LSMS_OK;
-    double* hist = info ? info->history : nullptr;
-    const int hcap = info ? info->history_cap : 0;
-    if (!mixed) {
-      rc_s = gmres_device(c, rhs, xs, nonzero, tol, maxiter, LSMS_APPLY_SCALED, &it, &r_est, hist, hcap, &nh, st);
-      outer = 1;
-    } else {
-      // FP64 refinement: r = rhs - A x (FP64 operator); inner GMRES on the mixed operator.
-      const double rhs_norm = norm_device(c, rhs, L, tmp, st);
-      const double inv_norm = rhs_norm > 0 ? 1.0 / rhs_norm : 1.0;
-      if (!nonzero) cudaMemsetAsync(xs, 0, L * sizeof(double2), st);
-      const int max_outer = 20;
-      const double inner_tol = 1e-5;
-      rc_s = LSMS_ERR_NOT_CONVERGED;
-      for (outer = 0; outer < max_outer && it < maxiter; ++outer) {
-        double rn;
-        if (outer == 0 && !nonzero) {
-          // x = 0: the residual is the right-hand side itself
-          cudaMemcpyAsync(res, rhs, L * sizeof(double2), cudaMemcpyDeviceToDevice, st);
-          rn = 1.0;
-        } else {
-          if ((rc = apply_device(c, 1, xs, tmp, LSMS_APPLY_SCALED, st))) return rc;
-          k_sub<<<grid_for(L, 256), 256, 0, st>>>(res, rhs, tmp, L);
-          rn = norm_device(c, res, L, tmp, st) * inv_norm;
-        }
-        r_est = rn;
-        true_res = rn;
-        if (!std::isfinite(rn)) { rc_s = ctx_fail(c, LSMS_ERR_NONFINITE, "non-finite refinement residual"); break; }
-        if (rn <= tol) { rc_s = LSMS_OK; break; }
-        int it_in = 0;
-        double r_in = 0.0;
-        const double tol_in = std::max(inner_tol, 0.5 * tol / rn);
-        int rci = gmres_device(c, res, dx, false, tol_in, maxiter - it, LSMS_APPLY_SCALED | LSMS_APPLY_MIXED,
-                               &it_in, &r_in, hist, hcap, &nh, st);
-        it += it_in;
-        if (rci != LSMS_OK && rci != LSMS_ERR_NOT_CONVERGED) { rc_s = rci; break; }
-        k_add<<<grid_for(L, 256), 256, 0, st>>>(xs, dx, L);              // x += dx
-        true_res = -1.0;
-      }
-    }
-    // true FP64 residual of the final iterate (the refinement loop already has it when it stopped
-    // on a fresh residual)
-    double rel_fp64 = true_res;
-    if (rel_fp64 < 0.0) {
-      if ((rc = apply_device(c, 1, xs, tmp, LSMS_APPLY_SCALED, st))) return rc;
-      k_sub<<<grid_for(L, 256), 256, 0, st>>>(res, rhs, tmp, L);
-      const double rn = norm_device(c, res, L, tmp, st);
-      const double bn = norm_device(c, rhs, L, tmp, st);
-      rel_fp64 = bn > 0 ? rn / bn : 0.0;
-    }
-    launch_diag_scale(xs, c->d_scale_in + c->P, beta, L, c->P, st);   // beta = D^{-1} b
-    if (info) {
-      info->iters += it;
-      info->outer_iters += outer;
-      info->rel_res = r_est;
-      info->rel_res_fp64 = rel_fp64;
-      info->n_history = nh;
-    }
-    if (rc_s != LSMS_OK && status == LSMS_OK) status = rc_s;
-    if (rc_s == LSMS_ERR_NONFINITE) break;
+  if ((rc = ensure(c, c->gm_r, (size_t)3 * LT * sizeof(double2) + 64))) return rc;
+  if ((rc = ensure(c, c->gm_x, (size_t)2 * LT * sizeof(double2)))) return rc;
+  if ((rc = ensure(c, c->ws_aux, (size_t)2 * nsrc * sizeof(double) + (size_t)nsrc * sizeof(int) + 64))) return rc;
+  double* d_src = (double*)c->ws_aux.ptr;
+  int* d_mask = (int*)(d_src + 2 * nsrc);
+  cudaMemcpyAsync(d_src, src_xy, (size_t)2 * nsrc * sizeof(double), cudaMemcpyHostToDevice, st);
+  double2* beta = (double2*)c->sol.ptr;                 // a_inc for every source, replaced by beta
+  if ((rc = incident_device(c, nsrc, d_src, beta, st))) return rc;
+  double2* rhs = (double2*)c->gm_r.ptr;                 // [nsrc][L]
+  double2* resv = rhs + LT;
+  double2* tmp = resv + LT;
+  double2* xs = (double2*)c->gm_x.ptr;                  // scaled iterates
+  double2* dx = xs + LT;
+  launch_diag_mul(beta, c->d_scale_out + c->P, rhs, LT, c->P, st);   // D S a_inc
+  bool nonzero = false;
+  if (x0) {
+    cudaMemcpyAsync(dx, x0, LT * sizeof(double2), cudaMemcpyHostToDevice, st);
+    launch_diag_scale(dx, c->d_hscale, xs, LT, c->P, st);
+    nonzero = true;
   }
+  std::vector<int> it(nsrc, 0);
+  std::vector<double> rest(nsrc, 0.0), rel64(nsrc, -1.0);
+  double* hist = info ? info->history : nullptr;
+  const int hcap = info ? info->history_cap : 0;
+  int nh = 0, outer = 0, status = LSMS_OK;
+  if (c->precision != LSMS_MIXED) {
+    std::vector<double> tv(nsrc, tol);
+    status = gmres_batch(c, rhs, xs, nonzero, nsrc, tv.data(), maxiter, LSMS_APPLY_SCALED, it.data(),
+                         rest.data(), hist, hcap, &nh, st);
+    if (status != LSMS_OK && status != LSMS_ERR_NOT_CONVERGED) return status;
+    outer = 1;
+  } else {
+    // FP64 refinement: r = rhs - A x with the FP64 operator; batched inner GMRES on the mixed
+    // operator for the systems not yet converged (the others get a zero right-hand side).
+    std::vector<double> bn;
+    norms_device(c, rhs, L, nsrc, tmp, st, bn);
+    if (!nonzero) cudaMemsetAsync(xs, 0, LT * sizeof(double2), st);
+    const int max_outer = 20;
+    const double inner_tol = 1e-5;
+    status = LSMS_ERR_NOT_CONVERGED;
+    std::vector<int> mask(nsrc, 1), it_in(nsrc, 0);
+    std::vector<double> rn(nsrc, 1.0), tol_in(nsrc), r_in(nsrc);
+    int used = 0;
+    for (outer = 0; outer < max_outer && used < maxiter; ++outer) {
+      if (outer == 0 && !nonzero) {
+        cudaMemcpyAsync(resv, rhs, LT * sizeof(double2), cudaMemcpyDeviceToDevice, st);
+        std::fill(rn.begin(), rn.end(), 1.0);
+      } else {
+        if ((rc = apply_device(c, nsrc, xs, tmp, LSMS_APPLY_SCALED, st))) return rc;
+        k_sub<<<grid_for(LT, 256), 256, 0, st>>>(resv, rhs, tmp, LT);
+        std::vector<double> r;
+        norms_device(c, resv, L, nsrc, tmp, st, r);
+        for (int b = 0; b < nsrc; ++b) rn[b] = bn[b] > 0 ? r[b] / bn[b] : 0.0;
+      }
+      bool all = true, bad = false;
+      for (int b = 0; b < nsrc; ++b) {
+        rel64[b] = rn[b];
+        rest[b] = rn[b];
+        if (!std::isfinite(rn[b])) bad = true;
+        mask[b] = rn[b] > tol ? 1 : 0;
+        if (mask[b]) all = false;
+        tol_in[b] = std::max(inner_tol, 0.5 * tol / std::max(rn[b], 1e-300));
+      }
+      if (bad) { status = ctx_fail(c, LSMS_ERR_NONFINITE, "non-finite refinement residual"); break; }
+      if (all) { status = LSMS_OK; break; }
+      cudaMemcpyAsync(d_mask, mask.data(), nsrc * sizeof(int), cudaMemcpyHostToDevice, st);
+      k_mask_zero<<<dim3(grid_for(L, 256), nsrc), 256, 0, st>>>(resv, d_mask, L);
+      const int rci = gmres_batch(c, resv, dx, false, nsrc, tol_in.data(), maxiter - used,
+                                  LSMS_APPLY_SCALED | LSMS_APPLY_MIXED, it_in.data(), r_in.data(),
+                                  hist, hcap, &nh, st);
+      int mx = 0;
+      for (int b = 0; b < nsrc; ++b) {
+        it[b] += it_in[b];
+        mx = std::max(mx, it_in[b]);
+      }
+      used += mx;
+      if (rci != LSMS_OK && rci != LSMS_ERR_NOT_CONVERGED) { status = rci; break; }
+      k_add<<<grid_for(LT, 256), 256, 0, st>>>(xs, dx, LT);              // x += dx
+      std::fill(rel64.begin(), rel64.end(), -1.0);
+    }
+    if (status == LSMS_ERR_NONFINITE) return status;
+  }
+  // true FP64 residuals of the final iterates (the refinement loop has them when it stopped on a
+  // fresh residual)
+  bool need = false;
+  for (int b = 0; b < nsrc; ++b) need = need || rel64[b] < 0.0;
+  if (need) {
+    if ((rc = apply_device(c, nsrc, xs, tmp, LSMS_APPLY_SCALED, st))) return rc;
+    k_sub<<<grid_for(LT, 256), 256, 0, st>>>(resv, rhs, tmp, LT);
+    std::vector<double> r, b2;
+    norms_device(c, resv, L, nsrc, tmp, st, r);
+    norms_device(c, rhs, L, nsrc, tmp, st, b2);
+    for (int b = 0; b < nsrc; ++b) rel64[b] = b2[b] > 0 ? r[b] / b2[b] : 0.0;
+  }
+  launch_diag_scale(xs, c->d_scale_in + c->P, beta, LT, c->P, st);   // beta = D^{-1} b
   if ((rc = check_cuda(c, "solve"))) return rc;
+  if (info) {
+    int mi = 0;
+    double mr = 0.0, m64 = 0.0;
+    for (int b = 0; b < nsrc; ++b) {
+      mi = std::max(mi, it[b]);
+      mr = std::max(mr, rest[b]);
+      m64 = std::max(m64, rel64[b]);
+    }
+    info->iters = mi;                 // the most iterations any source needed
+    info->outer_iters = outer;
+    info->rel_res = mr;               // the worst source
+    info->rel_res_fp64 = m64;
+    info->n_history = nh;
+  }
   c->n_src = nsrc;
   if (beta_out) {
-    cudaMemcpyAsync(beta_out, c->sol.ptr, (size_t)nsrc * L * sizeof(double2), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(beta_out, c->sol.ptr, (size_t)LT * sizeof(double2), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
     if ((rc = check_cuda(c, "solve copy"))) return rc;
   }

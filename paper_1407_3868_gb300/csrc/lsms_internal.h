@@ -71,11 +71,20 @@ struct lsms_ctx {
   void* d_lp_misc = nullptr;
   DevBuf ws_lp;
   void* tc = nullptr;               // tensor-core path state (contour_tc.cu)
+  // near pairs (k2 rho < 25) of the mixed translation: CSR by target, FP64-accurate sequences
+  int near_nnz = 0;
+  double near_r2 = 0.0;             // squared distance threshold
+  int* d_near_ptr = nullptr;        // [n + 1]
+  int* d_near_idx = nullptr;        // [nnz]
+  void* d_near_h = nullptr;         // float2 [nnz][4p + 1]
 
   // workspaces
   DevBuf ws_x, ws_y, ws_xs, ws_alpha, ws_g, ws_v, ws_pq, ws_sig, ws_aux;
   DevBuf gm_v, gm_h, gm_small, gm_x, gm_r, gm_w;
   double* h_pinned = nullptr;       // small pinned host scratch for residual polling
+  cudaEvent_t gm_ev[8] = {};        // events of the GMRES residual ring
+  void* gm_ring = nullptr;          // pinned ring of per-system GMRES states
+  size_t gm_ring_bytes = 0;
 
   cudaStream_t stream = nullptr;    // internal stream of the host-pointer entry points
 

@@ -9,7 +9,10 @@
 // orders follow from the forward recurrence in FP32.  The contraction is a register-blocked
 // Toeplitz product: a lane owns VB consecutive output orders of one target disc and slides a window
 // of 2 VB - 1 sequence values over the source orders, so each staged value feeds VB complex FMAs.
+#include <algorithm>
 #include <cmath>
+#include <unordered_map>
+#include <vector>
 
 #include "lsms_internal.h"
 #include "lsms_ops.h"
@@ -97,10 +100,16 @@ __device__ __noinline__ void hankel01_near(double z, float2* h0, float2* h1) {
 
 // Pair sequence h[s + 2p] = H_s(k rho) exp(i s phi), s = -2p..2p, for centres a (target) and b
 // (source) given as float-float (x_hi, x_lo, y_hi, y_lo).
-__device__ void hankel_sequence_f32(float4 a, float4 b, ffl k, int p, float2* h) {
+// near_r2: squared distance (float-float) below which the pair is left to the near-pair kernel and
+// its sequence is zero here; near_r2.hi <= 0 computes every pair here.
+__device__ void hankel_sequence_f32(float4 a, float4 b, ffl k, int p, ffl near_r2, float2* h) {
   const ffl dx = ff_sub({a.x, a.y}, {b.x, b.y});
   const ffl dy = ff_sub({a.z, a.w}, {b.z, b.w});
   const ffl r2 = ff_add(ff_mul(dx, dx), ff_mul(dy, dy));
+  if (near_r2.hi > 0.0f && (r2.hi < near_r2.hi || (r2.hi == near_r2.hi && r2.lo < near_r2.lo))) {
+    for (int q = 0; q <= 4 * p; ++q) h[q] = make_float2(0.f, 0.f);
+    return;
+  }
   const ffl rho = ff_sqrt(r2);
   const ffl z = ff_mul(rho, k);
   const float zf = z.hi + z.lo;
@@ -150,16 +159,17 @@ constexpr size_t TRANSLATE_F32_SMEM = (size_t)(2 * GUARD + MW * 32 * MHS) * size
 // staged source it slides a window of 2 VB - 1 sequence values over NB blocks of VB source orders.
 // Complex products use three real FMAs (Gauss): A += hr br, B += hi bi, C += (hr+hi)(br+bi);
 // re = A - B, im = C - A - B.
-template <int VB, int NB>
-__global__ void __launch_bounds__(MW * 32, 3)
+// RB coefficient vectors (right-hand sides r0 .. r0 + RB - 1) share every generated sequence.
+template <int VB, int NB, int RB>
+__global__ void __launch_bounds__(MW * 32, RB == 1 ? 3 : 2)
 k_translate_f32(const float4* __restrict__ cff, int n, int p, float k_hi, float k_lo,
                 const float2* __restrict__ xs, float2* __restrict__ part, int src_per_split,
-                int nrhs) {
-  __shared__ float2 sb[MCH][VB * NB + 1];
+                int nrhs, float near_hi, float near_lo) {
+  __shared__ float2 sb[RB][MCH][VB * NB + 1];
   __shared__ float4 sc[MCH];
   extern __shared__ float2 sh[];
   const int P = 2 * p + 1;
-  const int r = blockIdx.z;
+  const int r0 = blockIdx.z * RB;
   const int split = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = lane & 7, hi8 = lane >> 3;       // hi8 = vb (contraction) = s4 (generation)
@@ -168,19 +178,22 @@ k_translate_f32(const float4* __restrict__ cff, int n, int p, float k_hi, float 
   const float4 ct = lvalid ? cff[l] : make_float4(0.f, 0.f, 0.f, 0.f);
   for (int i = threadIdx.x; i < 2 * GUARD + MW * 32 * MHS; i += blockDim.x) sh[i] = make_float2(0.f, 0.f);
   float2* hw = sh + GUARD + warp * 32 * MHS;
-  float A[VB], B[VB], C[VB];
+  float A[RB][VB], B[RB][VB], C[RB][VB];
 #pragma unroll
-  for (int i = 0; i < VB; ++i) A[i] = B[i] = C[i] = 0.f;
+  for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+    for (int i = 0; i < VB; ++i) A[rr][i] = B[rr][i] = C[rr][i] = 0.f;
   const int jbeg = split * src_per_split;
   const int jend = min(n, jbeg + src_per_split);
-  const float2* xr = xs + (size_t)r * n * P;
   const ffl kf = {k_hi, k_lo};
   for (int j0c = jbeg; j0c < jend; j0c += MCH) {
     const int cnt = min(MCH, jend - j0c);
     __syncthreads();
-    for (int i = threadIdx.x; i < MCH * VB * NB; i += blockDim.x) {
-      const int s = i / (VB * NB), q = i - s * (VB * NB);
-      sb[s][q] = (s < cnt && q < P) ? xr[(size_t)(j0c + s) * P + q] : make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < RB * MCH * VB * NB; i += blockDim.x) {
+      const int rr = i / (MCH * VB * NB), rem = i - rr * (MCH * VB * NB);
+      const int s = rem / (VB * NB), q = rem - s * (VB * NB);
+      sb[rr][s][q] = (s < cnt && q < P && r0 + rr < nrhs)
+                         ? xs[((size_t)(r0 + rr) * n + j0c + s) * P + q] : make_float2(0.f, 0.f);
     }
     if (threadIdx.x < cnt) sc[threadIdx.x] = cff[j0c + threadIdx.x];
     __syncthreads();
@@ -189,7 +202,7 @@ k_translate_f32(const float4* __restrict__ cff, int n, int p, float k_hi, float 
         const int js = s0 + hi8;
         float2* h = hw + lane * MHS;
         if (js < cnt && lvalid && j0c + js != l) {
-          hankel_sequence_f32(ct, sc[js], kf, p, h);
+          hankel_sequence_f32(ct, sc[js], kf, p, {near_hi, near_lo}, h);
         } else {
           for (int q = 0; q <= 4 * p; ++q) h[q] = make_float2(0.f, 0.f);
         }
@@ -198,7 +211,6 @@ k_translate_f32(const float4* __restrict__ cff, int n, int p, float k_hi, float 
       const int nq4 = min(4, cnt - s0);
       for (int q4 = 0; q4 < nq4; ++q4) {
         const float2* hs = hw + (q4 * 8 + t) * MHS + 2 * p - VB * hi8;   // hs[n - i]: output VB vb + i
-        const float2* bs = sb[s0 + q4];
         float2 win[2 * VB - 1];
         float wsum[2 * VB - 1];
 #pragma unroll
@@ -215,14 +227,17 @@ k_translate_f32(const float4* __restrict__ cff, int n, int p, float k_hi, float 
           }
 #pragma unroll
           for (int u = 0; u < VB; ++u) {
-            const float2 b = bs[nb * VB + u];
-            const float bsum = b.x + b.y;
 #pragma unroll
-            for (int i = 0; i < VB; ++i) {
-              const float2 hv = win[VB - 1 + u - i];
-              A[i] = __fmaf_rn(hv.x, b.x, A[i]);
-              B[i] = __fmaf_rn(hv.y, b.y, B[i]);
-              C[i] = __fmaf_rn(wsum[VB - 1 + u - i], bsum, C[i]);
+            for (int rr = 0; rr < RB; ++rr) {
+              const float2 b = sb[rr][s0 + q4][nb * VB + u];
+              const float bsum = b.x + b.y;
+#pragma unroll
+              for (int i = 0; i < VB; ++i) {
+                const float2 hv = win[VB - 1 + u - i];
+                A[rr][i] = __fmaf_rn(hv.x, b.x, A[rr][i]);
+                B[rr][i] = __fmaf_rn(hv.y, b.y, B[rr][i]);
+                C[rr][i] = __fmaf_rn(wsum[VB - 1 + u - i], bsum, C[rr][i]);
+              }
             }
           }
 #pragma unroll
@@ -236,13 +251,82 @@ k_translate_f32(const float4* __restrict__ cff, int n, int p, float k_hi, float 
     }
   }
   if (lvalid) {
-    float2* out = part + (((size_t)split * nrhs + r) * n + l) * P;
 #pragma unroll
-    for (int i = 0; i < VB; ++i) {
-      const int nu = VB * hi8 + i;
-      if (nu < P) out[nu] = make_float2(A[i] - B[i], C[i] - A[i] - B[i]);
+    for (int rr = 0; rr < RB; ++rr) {
+      if (r0 + rr >= nrhs) break;
+      float2* out = part + (((size_t)split * nrhs + r0 + rr) * n + l) * P;
+#pragma unroll
+      for (int i = 0; i < VB; ++i) {
+        const int nu = VB * hi8 + i;
+        if (nu < P) out[nu] = make_float2(A[rr][i] - B[rr][i], C[rr][i] - A[rr][i] - B[rr][i]);
+      }
     }
   }
+}
+
+// Near pairs (k2 rho < 25, a few per disc): their Hankel sequences are computed once per layout in
+// FP64 (CUDA J0, Y0, J1, Y1 and the forward recurrence) and stored in FP32; the main FP32 kernel
+// leaves these pairs out and k_translate_near adds them.
+__device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__global__ void k_near_sequences(const double* __restrict__ cx, const double* __restrict__ cy,
+                                 const int* __restrict__ ptr, const int* __restrict__ idx, int n,
+                                 int p, double k, float2* __restrict__ table) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n) return;
+  const int S = 4 * p + 1, c0 = 2 * p;
+  for (int e = ptr[l]; e < ptr[l + 1]; ++e) {
+    const int m = idx[e];
+    const double dx = cx[l] - cx[m], dy = cy[l] - cy[m];
+    const double rho = hypot(dx, dy), z = k * rho;
+    const double2 e1 = make_double2(dx / rho, dy / rho);
+    float2* h = table + (size_t)e * S;
+    double2 hm = make_double2(j0(z), y0(z)), hq = make_double2(j1(z), y1(z)), eq = e1;
+    h[c0] = make_float2((float)hm.x, (float)hm.y);
+    for (int q = 1; q <= 2 * p; ++q) {
+      const double2 v = cmul_d(hq, eq);
+      const double2 u = cmul_d(hq, make_double2(eq.x, -eq.y));
+      const double sg = (q & 1) ? -1.0 : 1.0;
+      h[c0 + q] = make_float2((float)v.x, (float)v.y);
+      h[c0 - q] = make_float2((float)(sg * u.x), (float)(sg * u.y));
+      if (q < 2 * p) {
+        const double f = 2.0 * q / z;
+        const double2 hn = make_double2(f * hq.x - hm.x, f * hq.y - hm.y);
+        hm = hq;
+        hq = hn;
+        eq = cmul_d(eq, e1);
+      }
+    }
+  }
+}
+
+// alpha[r][l][nu] += sum over near sources m of sum_n h^{lm}_{n - nu} xs^m_n; one warp per target.
+__global__ void k_translate_near(const int* __restrict__ ptr, const int* __restrict__ idx,
+                                 const float2* __restrict__ table, int n, int p,
+                                 const float2* __restrict__ xs, double2* __restrict__ alpha) {
+  const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.y;
+  const int P = 2 * p + 1, S = 4 * p + 1;
+  if (l >= n || lane >= P) return;
+  const float2* xr = xs + (size_t)r * n * P;
+  float ar = 0.f, ai = 0.f;
+  for (int e = ptr[l]; e < ptr[l + 1]; ++e) {
+    const float2* hs = table + (size_t)e * S + 2 * p - lane;   // hs[q] = h_{n - nu}
+    const float2* b = xr + (size_t)idx[e] * P;
+    for (int q = 0; q < P; ++q) {
+      const float2 hv = hs[q], bv = b[q];
+      ar = __fmaf_rn(hv.x, bv.x, ar);
+      ar = __fmaf_rn(-hv.y, bv.y, ar);
+      ai = __fmaf_rn(hv.x, bv.y, ai);
+      ai = __fmaf_rn(hv.y, bv.x, ai);
+    }
+  }
+  double2* o = alpha + ((size_t)r * n + l) * P + lane;
+  o->x += ar;
+  o->y += ai;
 }
 
 // alpha[r][l][nu] = sum_split part[split][r][l][nu]   (double accumulation)
@@ -274,37 +358,99 @@ __global__ void k_centres_ff(const double* __restrict__ cx, const double* __rest
   out[j] = make_float4(xh, (float)(cx[j] - (double)xh), yh, (float)(cy[j] - (double)yh));
 }
 
-template <int VB, int NB>
+template <int VB, int NB, int RB>
 void launch_vbnb(dim3 grid, cudaStream_t st, const float4* cff, int n, int p, float kh, float kl,
-                 const float2* xs, float2* part, int sps, int nrhs) {
+                 const float2* xs, float2* part, int sps, int nrhs, float nh, float nl) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_translate_f32<VB, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_translate_f32<VB, NB, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)TRANSLATE_F32_SMEM);
     attr = true;
   }
-  k_translate_f32<VB, NB><<<grid, MW * 32, TRANSLATE_F32_SMEM, st>>>(cff, n, p, kh, kl, xs, part, sps, nrhs);
+  grid.z = (nrhs + RB - 1) / RB;
+  k_translate_f32<VB, NB, RB><<<grid, MW * 32, TRANSLATE_F32_SMEM, st>>>(cff, n, p, kh, kl, xs, part, sps,
+                                                                        nrhs, nh, nl);
 }
 
 // Order blocking for P = 2p + 1: VB = ceil(P/4) outputs per lane, NB = ceil(P/VB) source blocks.
+// Four or more right-hand sides are contracted four at a time against each generated sequence.
 void launch_translate_kernel(dim3 grid, cudaStream_t st, const float4* cff, int n, int p, float kh,
-                             float kl, const float2* xs, float2* part, int sps, int nrhs) {
+                             float kl, const float2* xs, float2* part, int sps, int nrhs,
+                             float nh = 0.f, float nl = 0.f) {
+  const bool blk = nrhs >= 4;
+#define LSMS_TR(VB, NB)                                                                         \
+  (blk ? launch_vbnb<VB, NB, 4>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs, nh, nl)       \
+       : launch_vbnb<VB, NB, 1>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs, nh, nl))
   switch (p) {
-    case 0: launch_vbnb<1, 1>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 1: launch_vbnb<1, 3>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 2: launch_vbnb<2, 3>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 3: launch_vbnb<2, 4>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 4: launch_vbnb<3, 3>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 5: launch_vbnb<3, 4>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 6: case 7: launch_vbnb<4, 4>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 8: case 9: launch_vbnb<5, 4>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 10: case 11: launch_vbnb<6, 4>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    case 12: case 13: launch_vbnb<7, 4>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
-    default: launch_vbnb<8, 4>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs); break;
+    case 0: launch_vbnb<1, 1, 1>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs, nh, nl); break;
+    case 1: launch_vbnb<1, 3, 1>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs, nh, nl); break;
+    case 2: launch_vbnb<2, 3, 1>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs, nh, nl); break;
+    case 3: launch_vbnb<2, 4, 1>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs, nh, nl); break;
+    case 4: launch_vbnb<3, 3, 1>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs, nh, nl); break;
+    case 5: launch_vbnb<3, 4, 1>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs, nh, nl); break;
+    case 6: case 7: LSMS_TR(4, 4); break;
+    case 8: case 9: LSMS_TR(5, 4); break;
+    case 10: case 11: LSMS_TR(6, 4); break;
+    case 12: case 13: LSMS_TR(7, 4); break;
+    default: LSMS_TR(8, 4); break;
   }
+#undef LSMS_TR
 }
 
 }  // namespace
+
+// CSR list of near pairs (k2 rho < 25) by target, from a cell grid, and their FP64 sequences.
+static int build_near_pairs(lsms_ctx* c) {
+  void* old[] = {c->d_near_ptr, c->d_near_idx, c->d_near_h};
+  for (void* q : old)
+    if (q) cudaFree(q);
+  c->d_near_ptr = nullptr;
+  c->d_near_idx = nullptr;
+  c->d_near_h = nullptr;
+  c->near_nnz = 0;
+  const int n = c->n;
+  const double rn = (double)kZAsym / c->k2;
+  c->near_r2 = rn * rn;
+  std::vector<int> ptr(n + 1, 0), idx;
+  std::unordered_map<long long, std::vector<int>> grid;
+  auto key = [](long long i, long long k) { return (i << 32) ^ (k & 0xffffffffLL); };
+  std::vector<double> xs(n);
+  for (int j = 0; j < n; ++j) xs[j] = c->cx[j] - c->xc;
+  for (int j = 0; j < n; ++j)
+    grid[key((long long)std::floor(xs[j] / rn), (long long)std::floor(c->cy[j] / rn))].push_back(j);
+  for (int l = 0; l < n; ++l) {
+    const long long ix = (long long)std::floor(xs[l] / rn), iy = (long long)std::floor(c->cy[l] / rn);
+    std::vector<int> row;
+    for (long long a = ix - 1; a <= ix + 1; ++a)
+      for (long long b = iy - 1; b <= iy + 1; ++b) {
+        auto it = grid.find(key(a, b));
+        if (it == grid.end()) continue;
+        for (int m : it->second) {
+          if (m == l) continue;
+          const double dx = xs[l] - xs[m], dy = c->cy[l] - c->cy[m];
+          if (dx * dx + dy * dy < c->near_r2) row.push_back(m);
+        }
+      }
+    std::sort(row.begin(), row.end());
+    idx.insert(idx.end(), row.begin(), row.end());
+    ptr[l + 1] = (int)idx.size();
+  }
+  c->near_nnz = (int)idx.size();
+  const size_t hb = (size_t)(c->near_nnz > 0 ? c->near_nnz : 1) * (4 * c->p + 1) * sizeof(float2);
+  if (cudaMalloc((void**)&c->d_near_ptr, (n + 1) * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&c->d_near_idx, (idx.empty() ? 1 : idx.size()) * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&c->d_near_h, hb) != cudaSuccess) {
+    cudaGetLastError();
+    return ctx_fail(c, LSMS_ERR_OOM, "cudaMalloc failed for the near-pair tables");
+  }
+  cudaMemcpy(c->d_near_ptr, ptr.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice);
+  if (!idx.empty()) cudaMemcpy(c->d_near_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (n > 0 && c->near_nnz > 0)
+    k_near_sequences<<<(n + 127) / 128, 128, 0, c->stream>>>(c->d_cx, c->d_cy, c->d_near_ptr, c->d_near_idx,
+                                                            n, c->p, c->k2, (float2*)c->d_near_h);
+  cudaStreamSynchronize(c->stream);
+  return check_cuda(c, "build_near_pairs");
+}
 
 int build_lowp_tables(lsms_ctx* c) {
   if (c->d_lp_misc) cudaFree(c->d_lp_misc);
@@ -318,13 +464,17 @@ int build_lowp_tables(lsms_ctx* c) {
   cudaStreamSynchronize(c->stream);
   int rc = check_cuda(c, "build_lowp_tables");
   if (rc) return rc;
+  if ((rc = build_near_pairs(c))) return rc;
   return tc_setup(c);
 }
 
-// Splits of the source range so that the grid covers the GPU several times.
+// Splits of the source range so that the grid covers the GPU several times (3 CTAs per SM for one
+// right-hand side per CTA, 2 for four).
 static int translate_splits(int n, int nrhs) {
   const int tiles = (n + MW * MT - 1) / (MW * MT);
-  int s = (152 * 3 * 4 + tiles * nrhs - 1) / (tiles * nrhs);
+  const int zb = nrhs >= 4 ? (nrhs + 3) / 4 : nrhs;
+  const int per_sm = nrhs >= 4 ? 2 : 3;
+  int s = (152 * per_sm * 4 + tiles * zb - 1) / (tiles * zb);
   const int max_s = (n + MCH - 1) / MCH;
   if (s > max_s) s = max_s;
   if (s < 1) s = 1;
@@ -349,8 +499,13 @@ int translate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cu
   k_to_float<<<(int)g, 256, 0, st>>>(xs, xs32, len);
   const float kh = (float)c->k2, kl = (float)(c->k2 - (double)kh);
   dim3 grid((n + MW * MT - 1) / (MW * MT), splits, nrhs);
-  launch_translate_kernel(grid, st, (const float4*)c->d_lp_misc, n, p, kh, kl, xs32, part, sps, nrhs);
+  const float nh = (float)c->near_r2, nl = (float)(c->near_r2 - (double)nh);
+  launch_translate_kernel(grid, st, (const float4*)c->d_lp_misc, n, p, kh, kl, xs32, part, sps, nrhs, nh, nl);
   k_reduce_parts<<<(int)g, 256, 0, st>>>(part, splits, len, alpha);
+  if (c->near_nnz > 0) {
+    dim3 gn((unsigned)((n * 32 + 127) / 128), (unsigned)nrhs);
+    k_translate_near<<<gn, 128, 0, st>>>(c->d_near_ptr, c->d_near_idx, (const float2*)c->d_near_h, n, p, xs32, alpha);
+  }
   return check_cuda(c, "translate_mixed");
 }
 

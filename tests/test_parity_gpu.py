@@ -225,6 +225,38 @@ def test_solve_mixed_with_refinement(L, small, small_solution):
     ctx.close()
 
 
+SOURCES3 = np.array([[0.0, 1.0], [-1.3, 0.6], [1.7, 1.4]])
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOL_MIXED)])
+def test_solve_several_sources_in_lockstep(L, small, precision, tol):
+    w = small.w
+    ctx = L.context_for(w, precision)
+    ctx.set_particles(small.c)
+    beta, info = ctx.solve(SOURCES3, tol=1e-13 if precision == 0 else 1e-11, maxiter=300)
+    assert info["status"] == 0
+    for s in range(3):
+        b_o = small.pr.solve_dense(SOURCES3[s])
+        assert rel(beta[s], b_o, small.hs) < tol
+        u = ctx.eval_field(w.targets, s, L.FIELD_SCATTERED)
+        assert rel(u, small.pr.field_layer1(SOURCES3[s], b_o, w.targets, "scattered")) < tol
+    ctx.close()
+
+
+@pytest.mark.parametrize("nrhs", [4, 6])
+def test_translation_mixed_block_of_right_hand_sides(L, small, nrhs):
+    # four right-hand sides share each generated Hankel sequence; 6 = 4 + a partial block of 2
+    beta = small.rand_beta(21, nrhs=nrhs)
+    a = small.ctx.translate(beta, precision=L.LSMS_MIXED)
+    a1 = small.ctx.translate(beta[:1], precision=L.LSMS_MIXED)[0]
+    for r in range(nrhs):
+        assert rel(a[r], small.pr.translation(beta[r]), small.ws) < TOL_MIXED_OP
+    assert rel(a[0], a1, small.ws) < 1e-6
+    y = small.ctx.apply(beta, L.APPLY_MIXED)
+    for r in range(nrhs):
+        assert rel(y[r], small.pr.apply(beta[r]), small.hs) < TOL_MIXED_OP
+
+
 def test_solve_with_initial_guess_and_maxiter_cap(small, small_solution, L):
     # warm start at the solution converges at once; a cap of 2 iterations reports NOT_CONVERGED
     beta, info = small.ctx.solve(small.w.sources, tol=1e-12, maxiter=50, x0=small_solution[None])
