@@ -177,6 +177,26 @@ int lsms_solve(lsms_ctx* ctx, int n_src, const double* src_xy, double tol, int m
 int lsms_eval_field(lsms_ctx* ctx, int src_index, int n_tgt, const double* tgt_xy, int which,
                     double* out);
 
+/* lsms_set_layouts — a batch of independent layouts (a design sweep over particle
+ *   configurations; Sec. 1: the solver serves "a sequence of configurations as part of a design or
+ *   optimization process").  counts[l] discs for layout l; centres_xy holds every layout's centres
+ *   one after the other (2 sum counts doubles), each checked as in lsms_set_particles.  After this
+ *   call the context is a batch: coefficient arrays are the layouts' [N_l][P] arrays one after the
+ *   other (one right-hand side per layout); lsms_apply / lsms_apply_dev apply every layout's
+ *   operator, as one CUDA graph launch after the first call with the same buffers and flags;
+ *   lsms_solve takes one source, or one per layout, and solves every layout (concurrently);
+ *   lsms_eval_field's src_index selects the layout.  The per-step entry points (lsms_translate,
+ *   ...) return LSMS_ERR_ARG on a batch.  lsms_set_particles turns the batch back into one layout.
+ * lsms_num_layouts — layouts of the context (1 unless it is a batch). */
+int lsms_set_layouts(lsms_ctx* ctx, int n_layouts, const int* counts, const double* centres_xy);
+int lsms_num_layouts(const lsms_ctx* ctx);
+
+/* lsms_autotune — time candidate source-split factors of the FP32 translation on the current
+ *   layout (or on the largest layout of every power-of-two size bucket of a batch) and keep the
+ *   fastest; *split_mult (may be NULL) receives it.  No counterpart in the paper: a tuning step of
+ *   this implementation. */
+int lsms_autotune(lsms_ctx* ctx, double* split_mult);
+
 /* lsms_set_timing — enable (1) or disable (0) CUDA-event timing of the operator's parts.  While
  *   enabled, every operator application records events on its stream around the translation
  *   (Lemma 3.1) and around the reflected coupling (Thm 5.2 -> Eq. "sommerfeldsys" -> Lemma 5.1).

@@ -91,6 +91,7 @@ int reflection_f64(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cud
 int apply_device(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags, cudaStream_t st) {
   int rc;
   if ((rc = need_particles(c))) return rc;
+  if (is_batch(c)) return batch_apply(c, nrhs, x, y, flags, st);
   if (nrhs < 0) return fail(c, LSMS_ERR_ARG, "nrhs must be >= 0");
   const int n = c->n, P = c->P;
   const size_t len = (size_t)nrhs * n * P;
@@ -201,6 +202,7 @@ extern "C" int lsms_create(double k1, double k2, double k3, double d, double kp,
 extern "C" void lsms_destroy(lsms_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  batch_free(c);
   void* ptrs[] = {c->d_lam, c->d_g1, c->d_g2, c->d_refl, c->d_inc, c->d_field, c->d_fagg, c->d_udis,
                   c->d_scale_in, c->d_hscale, c->d_scale_out, c->d_cx, c->d_cy, c->d_eagg, c->d_edis,
                   c->d_eagg_lp, c->d_edis_lp, c->d_lp_misc, c->d_near_ptr, c->d_near_idx, c->d_near_h};
@@ -229,6 +231,7 @@ extern "C" int lsms_set_particles(lsms_ctx* c, int n, const double* xy) {
   int rc = validate_geometry(c, n, xy, err);
   if (rc) return fail(c, rc, err);
   cudaStreamSynchronize(c->stream);
+  batch_free(c);
   c->cx.assign(n, 0.0);
   c->cy.assign(n, 0.0);
   double xmin = 0.0, xmax = 0.0;
@@ -297,7 +300,8 @@ extern "C" int lsms_apply_ex(lsms_ctx* c, int nrhs, const double* x, double* y, 
   if ((rc = ensure(c, c->ws_y, len * sizeof(double2)))) return rc;
   if ((rc = apply_device(c, nrhs, (const double2*)c->ws_x.ptr, (double2*)c->ws_y.ptr, flags, c->stream))) return rc;
   if ((rc = copy_out(c, y, c->ws_y.ptr, len))) return rc;
-  return (flags & LSMS_APPLY_MIXED) ? mixed_check(c) : LSMS_OK;
+  if (!(flags & LSMS_APPLY_MIXED)) return LSMS_OK;
+  return is_batch(c) ? batch_mixed_check(c) : mixed_check(c);
 }
 
 extern "C" int lsms_apply(lsms_ctx* c, int nrhs, const double* x, double* y) {
@@ -315,6 +319,7 @@ extern "C" int lsms_apply_dev(lsms_ctx* c, int nrhs, const double* x, double* y,
 extern "C" int lsms_translate(lsms_ctx* c, int nrhs, const double* beta, double* alpha, int precision) {
   int rc;
   if ((rc = need_particles(c))) return rc;
+  if (is_batch(c)) return fail(c, LSMS_ERR_ARG, "not available on a layout batch");
   const size_t len = (size_t)nrhs * c->n * c->P;
   if (nrhs < 0) return fail(c, LSMS_ERR_ARG, "nrhs must be >= 0");
   if (len == 0) return LSMS_OK;
@@ -332,6 +337,7 @@ extern "C" int lsms_aggregate(lsms_ctx* c, int nrhs, const double* beta, double*
                               double* q_minus, int precision) {
   int rc;
   if ((rc = need_particles(c))) return rc;
+  if (is_batch(c)) return fail(c, LSMS_ERR_ARG, "not available on a layout batch");
   if (nrhs < 0) return fail(c, LSMS_ERR_ARG, "nrhs must be >= 0");
   const int ns = c->ns, P = c->P;
   const size_t len = (size_t)nrhs * c->n * P;
@@ -392,6 +398,7 @@ extern "C" int lsms_disaggregate(lsms_ctx* c, int nrhs, const double* s_plus, co
                                  double* alpha, int precision) {
   int rc;
   if ((rc = need_particles(c))) return rc;
+  if (is_batch(c)) return fail(c, LSMS_ERR_ARG, "not available on a layout batch");
   if (nrhs < 0) return fail(c, LSMS_ERR_ARG, "nrhs must be >= 0");
   const int ns = c->ns, P = c->P;
   const size_t len = (size_t)nrhs * c->n * P;
@@ -444,6 +451,7 @@ int validate_sources(lsms_ctx* c, int nsrc, const double* xy) {
 extern "C" int lsms_incident(lsms_ctx* c, int nsrc, const double* src_xy, double* a_inc) {
   int rc;
   if ((rc = need_particles(c))) return rc;
+  if (is_batch(c)) return fail(c, LSMS_ERR_ARG, "not available on a layout batch");
   if ((rc = validate_sources(c, nsrc, src_xy))) return rc;
   const size_t len = (size_t)nsrc * c->n * c->P;
   if (len == 0) return LSMS_OK;
@@ -461,6 +469,7 @@ extern "C" int lsms_eval_field(lsms_ctx* c, int src_index, int ntgt, const doubl
                                double* out) {
   int rc;
   if ((rc = need_particles(c))) return rc;
+  if (is_batch(c)) return batch_eval_field(c, src_index, ntgt, tgt, which, out);
   if (src_index < 0 || src_index >= c->n_src) return fail(c, LSMS_ERR_STATE, "no solution for that source: call lsms_solve first");
   if (which < LSMS_FIELD_TOTAL || which > LSMS_FIELD_PARTICLE) return fail(c, LSMS_ERR_ARG, "bad field selector");
   if (ntgt < 0 || (ntgt > 0 && (!tgt || !out))) return fail(c, LSMS_ERR_ARG, "bad target array");

@@ -1,0 +1,272 @@
+// Batches of independent layouts (a design sweep over particle configurations, Sec. 1 and Sec. 6 of
+// the paper: the solver is meant to run for "a sequence of configurations as part of a design or
+// optimization process").
+//
+// lsms_set_layouts turns a context into a batch: one child context per layout, sharing the medium,
+// the discretisation and the precision.  A batched operator application is one CUDA graph: a fork
+// from the caller's stream into one branch per layout (each child's kernels on its own stream) and
+// a join; the graph is captured on the first application with a given (x, y, flags) and replayed
+// afterwards.  A batched solve runs the layouts' solves (each a graph-captured device GMRES) from a
+// small host thread pool, largest layout first, so that the GPU works on many layouts at once.
+// lsms_autotune picks the FP32 translation's source-split factor by timing candidates.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <thread>
+#include <vector>
+
+#include "lsms_internal.h"
+#include "lsms_ops.h"
+
+bool is_batch(const lsms_ctx* c) { return c && !c->kids.empty(); }
+
+void batch_free(lsms_ctx* c) {
+  for (auto& g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+  for (cudaEvent_t e : c->kid_ev)
+    if (e) cudaEventDestroy(e);
+  c->kid_ev.clear();
+  for (lsms_ctx* k : c->kids) lsms_destroy(k);
+  c->kids.clear();
+  c->kid_off.clear();
+}
+
+extern "C" int lsms_set_layouts(lsms_ctx* c, int n_layouts, const int* counts, const double* xy) {
+  if (!c) return LSMS_ERR_ARG;
+  if (n_layouts < 1 || !counts) return ctx_fail(c, LSMS_ERR_ARG, "set_layouts: need n_layouts >= 1 and counts");
+  long long total = 0;
+  for (int l = 0; l < n_layouts; ++l) {
+    if (counts[l] < 0) return ctx_fail(c, LSMS_ERR_ARG, "set_layouts: negative disc count");
+    total += counts[l];
+  }
+  if (total > 0 && !xy) return ctx_fail(c, LSMS_ERR_ARG, "set_layouts: centres are NULL");
+  cudaStreamSynchronize(c->stream);
+  batch_free(c);
+  c->n = -1;
+  c->n_src = 0;
+  long long off = 0;
+  for (int l = 0; l < n_layouts; ++l) {
+    lsms_ctx* k = nullptr;
+    int rc = lsms_create(c->k1, c->k2, c->k3, c->d, c->kp, c->R, c->p, &c->contour, c->precision, &k);
+    if (rc) {
+      const std::string m = lsms_last_error(nullptr);
+      batch_free(c);
+      return ctx_fail(c, rc, "set_layouts: layout " + std::to_string(l) + ": " + m);
+    }
+    k->use_graphs = c->use_graphs;
+    k->split_mult = c->split_mult;
+    c->kids.push_back(k);
+    c->kid_off.push_back(off);
+    rc = lsms_set_particles(k, counts[l], xy + 2 * off);
+    if (rc) {
+      const std::string m = k->err;
+      batch_free(c);
+      return ctx_fail(c, rc, "set_layouts: layout " + std::to_string(l) + ": " + m);
+    }
+    off += counts[l];
+  }
+  c->kid_off.push_back(off);
+  c->kid_ev.assign(n_layouts + 1, nullptr);
+  for (auto& e : c->kid_ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      batch_free(c);
+      return check_cuda(c, "set_layouts events");
+    }
+  c->n = (int)total;
+  return LSMS_OK;
+}
+
+extern "C" int lsms_num_layouts(const lsms_ctx* c) {
+  if (!c) return LSMS_ERR_ARG;
+  return is_batch(c) ? (int)c->kids.size() : 1;
+}
+
+// Fork from st into every layout's stream, apply, join back into st.
+static int fork_join_apply(lsms_ctx* c, const double2* x, double2* y, int flags, cudaStream_t st) {
+  const int nl = (int)c->kids.size();
+  cudaEvent_t fork = c->kid_ev[nl];
+  cudaEventRecord(fork, st);
+  for (int l = 0; l < nl; ++l) {
+    lsms_ctx* k = c->kids[l];
+    const long long o = c->kid_off[l] * c->P;
+    cudaStreamWaitEvent(k->stream, fork, 0);
+    const int timing = k->timing;
+    k->timing = 0;
+    const int rc = apply_device(k, 1, x + o, y + o, flags, k->stream);
+    k->timing = timing;
+    if (rc) return ctx_fail(c, rc, "layout " + std::to_string(l) + ": " + k->err);
+    cudaEventRecord(c->kid_ev[l], k->stream);
+    cudaStreamWaitEvent(st, c->kid_ev[l], 0);
+  }
+  return LSMS_OK;
+}
+
+// y = x - S (T + R) x for every layout (x, y: [sum N_l][P] on the device), one graph launch.
+int batch_apply(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags, cudaStream_t st) {
+  if (nrhs != 1) return ctx_fail(c, LSMS_ERR_ARG, "a layout batch takes one coefficient vector per layout");
+  for (auto& g : c->graphs)
+    if (g.x == x && g.y == y && g.flags == flags) {
+      if (cudaGraphLaunch(g.exec, st) != cudaSuccess) return check_cuda(c, "batched apply graph");
+      return LSMS_OK;
+    }
+  // first application with these buffers: run it directly (this also sizes every workspace), then
+  // capture the same fork/join for the next calls
+  int rc = fork_join_apply(c, x, y, flags, st);
+  if (rc) return rc;
+  if (!c->use_graphs || c->graphs.size() >= 16) return check_cuda(c, "batched apply");
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    const int crc = fork_join_apply(c, x, y, flags, st);
+    const cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (crc == LSMS_OK && e == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+      exec = nullptr;
+    if (graph) cudaGraphDestroy(graph);
+  }
+  cudaGetLastError();
+  c->err.clear();
+  if (exec) c->graphs.push_back({x, y, flags, exec});
+  return LSMS_OK;
+}
+
+int batch_mixed_check(lsms_ctx* c) {
+  for (lsms_ctx* k : c->kids) {
+    const int rc = mixed_check(k);
+    if (rc) return ctx_fail(c, rc, k->err);
+  }
+  return LSMS_OK;
+}
+
+// Every layout's solve (source l, or the one source for all), concurrently from a thread pool.
+int batch_solve(lsms_ctx* c, int nsrc, const double* src_xy, double tol, int maxiter, const double* x0,
+                double* beta_out, lsms_solve_info* info) {
+  const int nl = (int)c->kids.size();
+  if (nsrc != 1 && nsrc != nl)
+    return ctx_fail(c, LSMS_ERR_ARG, "a layout batch takes one source, or one source per layout");
+  if ((c->n_src = 0), validate_sources(c, nsrc, src_xy)) return LSMS_ERR_ARG;
+  std::vector<int> order(nl), rc(nl, LSMS_OK);
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return c->kids[a]->n > c->kids[b]->n; });
+  std::vector<lsms_solve_info> inf(nl);
+  for (auto& i : inf) std::memset(&i, 0, sizeof(i));
+  std::atomic<int> next{0};
+  const int P = c->P;
+  auto work = [&]() {
+    for (;;) {
+      const int t = next.fetch_add(1);
+      if (t >= nl) break;
+      const int l = order[t];
+      lsms_ctx* k = c->kids[l];
+      const double* s = nsrc == 1 ? src_xy : src_xy + 2 * l;
+      const long long o = c->kid_off[l] * P * 2;
+      rc[l] = lsms_solve(k, 1, s, tol, maxiter, x0 ? x0 + o : nullptr, beta_out ? beta_out + o : nullptr, &inf[l]);
+    }
+  };
+  unsigned hw = std::thread::hardware_concurrency();
+  const int nt = std::max(1, std::min(nl, (int)std::min(hw ? hw : 4u, 16u)));
+  std::vector<std::thread> pool;
+  for (int i = 1; i < nt; ++i) pool.emplace_back(work);
+  work();
+  for (auto& th : pool) th.join();
+  int status = LSMS_OK;
+  for (int l = 0; l < nl; ++l) {
+    if (rc[l] == LSMS_OK) continue;
+    if (status == LSMS_OK || (status == LSMS_ERR_NOT_CONVERGED && rc[l] != LSMS_ERR_NOT_CONVERGED)) {
+      status = rc[l];
+      ctx_fail(c, rc[l], "layout " + std::to_string(l) + ": " + c->kids[l]->err);
+    }
+  }
+  if (info) {
+    info->iters = info->outer_iters = 0;
+    info->rel_res = info->rel_res_fp64 = 0.0;
+    info->n_history = 0;
+    for (int l = 0; l < nl; ++l) {
+      info->iters = std::max(info->iters, inf[l].iters);
+      info->outer_iters = std::max(info->outer_iters, inf[l].outer_iters);
+      info->rel_res = std::max(info->rel_res, inf[l].rel_res);
+      info->rel_res_fp64 = std::max(info->rel_res_fp64, inf[l].rel_res_fp64);
+    }
+  }
+  if (status == LSMS_OK || status == LSMS_ERR_NOT_CONVERGED) c->n_src = nl;
+  return status;
+}
+
+int batch_eval_field(lsms_ctx* c, int layout, int ntgt, const double* tgt, int which, double* out) {
+  if (layout < 0 || layout >= (int)c->kids.size() || c->n_src == 0)
+    return ctx_fail(c, LSMS_ERR_STATE, "no solution for that layout: call lsms_solve first");
+  const int rc = lsms_eval_field(c->kids[layout], 0, ntgt, tgt, which, out);
+  if (rc) return ctx_fail(c, rc, c->kids[layout]->err);
+  return LSMS_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// autotuning of the FP32 translation's source splits
+// ---------------------------------------------------------------------------------------------
+static int autotune_one(lsms_ctx* c, double* best_mult) {
+  *best_mult = c->split_mult;
+  if (c->n <= 0) return LSMS_OK;
+  const size_t len = (size_t)c->n * c->P;
+  int rc;
+  if ((rc = ensure(c, c->ws_xs, len * sizeof(double2)))) return rc;
+  if ((rc = ensure(c, c->ws_alpha, len * sizeof(double2)))) return rc;
+  cudaMemsetAsync(c->ws_xs.ptr, 0, len * sizeof(double2), c->stream);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const double cand[] = {0.5, 1.0, 1.5, 2.0, 3.0};
+  float best = 1e30f;
+  for (double m : cand) {
+    c->split_mult = m;
+    if ((rc = translate_mixed(c, 1, (const double2*)c->ws_xs.ptr, (double2*)c->ws_alpha.ptr, c->stream))) break;
+    cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < 3; ++r)
+      if ((rc = translate_mixed(c, 1, (const double2*)c->ws_xs.ptr, (double2*)c->ws_alpha.ptr, c->stream))) break;
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      *best_mult = m;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->split_mult = *best_mult;
+  if (rc) return rc;
+  return check_cuda(c, "autotune");
+}
+
+extern "C" int lsms_autotune(lsms_ctx* c, double* split_mult) {
+  if (!c) return LSMS_ERR_ARG;
+  if (c->n < 0) return ctx_fail(c, LSMS_ERR_STATE, "call lsms_set_particles or lsms_set_layouts first");
+  double m = c->split_mult;
+  if (!is_batch(c)) {
+    const int rc = autotune_one(c, &m);
+    if (split_mult) *split_mult = m;
+    return rc;
+  }
+  // one measurement per size bucket (powers of two), on the bucket's largest layout
+  std::vector<int> bucket(c->kids.size());
+  for (size_t l = 0; l < c->kids.size(); ++l)
+    bucket[l] = c->kids[l]->n > 0 ? (int)std::ceil(std::log2((double)c->kids[l]->n)) : -1;
+  std::vector<int> done;
+  for (size_t l = 0; l < c->kids.size(); ++l) {
+    const int b = bucket[l];
+    if (b < 0 || std::find(done.begin(), done.end(), b) != done.end()) continue;
+    size_t big = l;
+    for (size_t j = l; j < c->kids.size(); ++j)
+      if (bucket[j] == b && c->kids[j]->n > c->kids[big]->n) big = j;
+    double mb = 1.0;
+    const int rc = autotune_one(c->kids[big], &mb);
+    if (rc) return ctx_fail(c, rc, c->kids[big]->err);
+    for (size_t j = 0; j < c->kids.size(); ++j)
+      if (bucket[j] == b) c->kids[j]->split_mult = mb;
+    done.push_back(b);
+    if (split_mult) *split_mult = mb;   // the last bucket's factor
+  }
+  return LSMS_OK;
+}

@@ -22,6 +22,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "lsms_internal.h"
 #include "lsms_ops.h"
@@ -372,8 +373,10 @@ inline int grid_for(long long total, int block) {
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::mutex g_encode_mu;
 
 int get_encoder(lsms_ctx* c) {
+  std::lock_guard<std::mutex> lock(g_encode_mu);
   if (g_encode) return LSMS_OK;
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q;
@@ -457,12 +460,10 @@ int tc_setup(lsms_ctx* c) {
   if ((rc = check_cuda(c, "tc_setup"))) return rc;
   if ((rc = make_map(c, &t->map_a_agg, t->a_agg, t->kpad_agg, 2 * c->ns, BM))) return rc;
   if ((rc = make_map(c, &t->map_a_dis, t->a_dis, t->kpad_dis, c->n, BM))) return rc;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_gemm_bf16x6, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM) != cudaSuccess)
-      return check_cuda(c, "cudaFuncSetAttribute");
-    attr = true;
-  }
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_gemm_bf16x6, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+  });
   return LSMS_OK;
 }
 

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "lsms_internal.h"
@@ -49,14 +50,19 @@ constexpr int DOT_T = 1024;    // elements per CTA
 constexpr int DOT_V = 32;      // vectors per CTA (4 per warp)
 constexpr int GIVENS_MAX = 4096;
 
-// System b = blockIdx.z:  out[b][i] += sum_t conj(V[i][b][t]) w[b][t] for i < nv (out pre-zeroed).
-// V slots are ldv apart, system b sits at b L inside a slot.  With a gate the kernel does nothing
-// unless system b's state asks for a second Gram-Schmidt pass.
+// System b = blockIdx.z:  out[b][i] += sum_t conj(V[i][b][t]) w[b][t] for i < nv, and, with
+// self_norm, out[b][nv] += ||w_b||^2 (out pre-zeroed).  nv = nv0 (+ *kp when kp is given, so that a
+// captured graph follows the Arnoldi step).  V slots are ldv apart, system b sits at b L inside a
+// slot.  With a gate the kernel does nothing unless system b needs a second Gram-Schmidt pass.
 __global__ void __launch_bounds__(256)
-k_mdot(const double2* __restrict__ V, long long ldv, int nv, const double2* __restrict__ w,
-       long long L, double2* __restrict__ out, int out_stride, const GmState* __restrict__ gate) {
+k_mdot(const double2* __restrict__ V, long long ldv, int nv0, const int* __restrict__ kp,
+       int self_norm, const double2* __restrict__ w, long long L, double2* __restrict__ out,
+       int out_stride, const GmState* __restrict__ gate) {
   const int b = blockIdx.z;
   if (gate && !gate[b].reorth) return;
+  const int nv = nv0 + (kp ? *kp : 0);
+  const int ntot = nv + (self_norm ? 1 : 0);
+  if ((int)blockIdx.y * DOT_V >= ntot) return;
   V += (long long)b * L;
   w += (long long)b * L;
   out += (long long)b * out_stride;
@@ -66,9 +72,9 @@ k_mdot(const double2* __restrict__ V, long long ldv, int nv, const double2* __re
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) ws[i] = w[t0 + i];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int i1 = min(nv, (int)(blockIdx.y + 1) * DOT_V);
+  const int i1 = min(ntot, (int)(blockIdx.y + 1) * DOT_V);
   for (int i = blockIdx.y * DOT_V + warp; i < i1; i += nw) {
-    const double2* vi = V + (long long)i * ldv + t0;
+    const double2* vi = (i < nv ? V + (long long)i * ldv : w) + t0;
     double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
     int t = lane;
     for (; t + 32 < cnt; t += 64) {
@@ -93,11 +99,12 @@ k_mdot(const double2* __restrict__ V, long long ldv, int nv, const double2* __re
 // nv_arr[b] when given; with a gate only when system b needs a second pass.
 __global__ void __launch_bounds__(256)
 k_maxpy(const double2* __restrict__ V, long long ldv, int nv, const int* __restrict__ nv_arr,
-        const double2* __restrict__ h, int h_stride, double2* __restrict__ w, long long L,
-        double sign, const GmState* __restrict__ gate) {
+        const int* __restrict__ kp, const double2* __restrict__ h, int h_stride,
+        double2* __restrict__ w, long long L, double sign, const GmState* __restrict__ gate) {
   const int b = blockIdx.y;
   if (gate && !gate[b].reorth) return;
   if (nv_arr) nv = nv_arr[b];
+  if (kp) nv += *kp;
   V += (long long)b * L;
   w += (long long)b * L;
   h += (long long)b * h_stride;
@@ -137,8 +144,9 @@ k_maxpy(const double2* __restrict__ V, long long ldv, int nv, const int* __restr
 // After the first Gram-Schmidt pass of system b = blockIdx.x: h1[0..k] = V^H w, h1[k+1] = ||w||^2.
 // The first pass removes ||h1||^2 from ||w||^2; if more than about half of it goes
 // (||w'|| < 0.7 ||w||), cancellation may have left w' not orthogonal enough and a second pass runs.
-__global__ void __launch_bounds__(32) k_gm_prep(int k, const double2* __restrict__ h1, int stride,
-                                                GmState* __restrict__ st) {
+__global__ void __launch_bounds__(32) k_gm_prep(const int* __restrict__ kp, const double2* __restrict__ h1,
+                                                int stride, GmState* __restrict__ st) {
+  const int k = *kp;
   h1 += (long long)blockIdx.x * stride;
   double s = 0.0;
   for (int i = threadIdx.x; i <= k; i += 32) s += h1[i].x * h1[i].x + h1[i].y * h1[i].y;
@@ -154,10 +162,11 @@ __global__ void __launch_bounds__(32) k_gm_prep(int k, const double2* __restrict
 // previous Givens rotations, form the new one, update g and the residual estimate.  The lanes
 // stage the column and the rotations in shared memory, lane 0 sweeps them.
 __global__ void __launch_bounds__(32)
-k_gm_column(int k, const double2* __restrict__ h1, const double2* __restrict__ h2, int stride,
-            double2* __restrict__ H, long long hstride, int ldh, double2* __restrict__ cs,
+k_gm_column(const int* __restrict__ kp, const double2* __restrict__ h1, const double2* __restrict__ h2,
+            int stride, double2* __restrict__ H, long long hstride, int ldh, double2* __restrict__ cs,
             double2* __restrict__ sn, double2* __restrict__ g, GmState* __restrict__ st) {
   extern __shared__ double2 sm[];
+  const int k = *kp;
   const int b = blockIdx.x;
   h1 += (long long)b * stride;
   h2 += (long long)b * stride;
@@ -265,6 +274,39 @@ __global__ void k_scale_by(double2* __restrict__ dst, const double2* __restrict_
   }
 }
 
+// X[b] = V[k][b] (the operator's fixed input buffer)
+__global__ void k_copy_slot(double2* __restrict__ X, const double2* __restrict__ V, long long slot,
+                            const int* __restrict__ kp) {
+  const double2* src = V + (long long)(*kp) * slot;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < slot;
+       t += (long long)gridDim.x * blockDim.x)
+    X[t] = src[t];
+}
+
+// V[k + 1][b] = W[b] * st[b].inv   (system b = blockIdx.y)
+__global__ void k_scale_into_slot(double2* __restrict__ V, long long slot, const double2* __restrict__ W,
+                                  const GmState* __restrict__ st, long long L, const int* __restrict__ kp) {
+  const int b = blockIdx.y;
+  const double s = st[b].inv;
+  double2* dst = V + (long long)(*kp + 1) * slot + (long long)b * L;
+  const double2* src = W + (long long)b * L;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double2 v = src[t];
+    dst[t] = make_double2(v.x * s, v.y * s);
+  }
+}
+
+// ring[k mod ring_slots][b] = st[b] (host-mapped memory), then k += 1.  One block.
+__global__ void k_gm_snapshot(const GmState* __restrict__ st, int nb, GmState* __restrict__ ring,
+                              int ring_slots, int* __restrict__ kp) {
+  const int k = *kp;
+  GmState* dst = ring + (size_t)(k % ring_slots) * nb;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) dst[b] = st[b];
+  __syncthreads();
+  if (threadIdx.x == 0) *kp = k + 1;
+}
+
 // Start of system b = blockIdx.x: beta0 = ||r0||, ref = ||rhs|| (nrm[2b], nrm[2b + 1] hold their
 // squares), g = (beta0, 0, ...).
 __global__ void k_gm_start(const double2* __restrict__ nrm, GmState* __restrict__ st,
@@ -333,26 +375,28 @@ inline int grid_for(long long total, int block) {
   return (int)g;
 }
 
-// out[b * out_stride + i] = V_b[i]^H w_b, i < nv, for nb systems
+// out[b * out_stride + i] = V_b[i]^H w_b, i < nv, for nb systems (fixed count)
 void mdot(const double2* V, long long ldv, int nv, const double2* w, long long L, double2* out,
-          int out_stride, int nb, cudaStream_t st, const GmState* gate = nullptr) {
+          int out_stride, int nb, cudaStream_t st) {
   for (int b = 0; b < nb; ++b)
     cudaMemsetAsync(out + (long long)b * out_stride, 0, (size_t)nv * sizeof(double2), st);
   dim3 grid((unsigned)((L + DOT_T - 1) / DOT_T), (unsigned)((nv + DOT_V - 1) / DOT_V), (unsigned)nb);
-  k_mdot<<<grid, 256, 0, st>>>(V, ldv, nv, w, L, out, out_stride, gate);
+  k_mdot<<<grid, 256, 0, st>>>(V, ldv, nv, nullptr, 0, w, L, out, out_stride, nullptr);
 }
 
 void maxpy(const double2* V, long long ldv, int nv, const int* nv_arr, const double2* h, int h_stride,
-           double2* w, long long L, double sign, int nb, cudaStream_t st, const GmState* gate = nullptr) {
+           double2* w, long long L, double sign, int nb, cudaStream_t st) {
   dim3 grid((unsigned)((L + 255) / 256), (unsigned)nb);
-  k_maxpy<<<grid, 256, 0, st>>>(V, ldv, nv, nv_arr, h, h_stride, w, L, sign, gate);
+  k_maxpy<<<grid, 256, 0, st>>>(V, ldv, nv, nv_arr, nullptr, h, h_stride, w, L, sign, nullptr);
 }
 
 // Device scratch of one batched GMRES run.
 struct GmPtrs {
   double2 *V, *H, *h1, *h2, *g, *cs, *sn, *y, *nrm;
+  double2 *X, *W;          // the operator's fixed input and output buffers, [nb][L]
   GmState* st;
-  int* kk;
+  int* kk;                 // iterations kept per system (back substitution)
+  int* dk;                 // the Arnoldi step counter on the device
   int ldh, stride;
   long long hstride;
 };
@@ -364,11 +408,14 @@ int gm_alloc(lsms_ctx* c, long long L, int nb, int maxiter, GmPtrs& p) {
   p.hstride = (long long)maxiter * p.ldh;
   if ((rc = ensure(c, c->gm_v, (size_t)(maxiter + 1) * nb * L * sizeof(double2)))) return rc;
   if ((rc = ensure(c, c->gm_h, (size_t)nb * p.hstride * sizeof(double2)))) return rc;
+  if ((rc = ensure(c, c->gm_w, (size_t)2 * nb * L * sizeof(double2)))) return rc;
   const size_t small = (size_t)nb * (7 * (size_t)p.stride + 2) * sizeof(double2) + nb * sizeof(GmState) +
-                       nb * sizeof(int) + 256;
+                       nb * sizeof(int) + 512;
   if ((rc = ensure(c, c->gm_small, small))) return rc;
   p.V = (double2*)c->gm_v.ptr;
   p.H = (double2*)c->gm_h.ptr;
+  p.X = (double2*)c->gm_w.ptr;
+  p.W = p.X + (long long)nb * L;
   double2* s = (double2*)c->gm_small.ptr;
   const long long bs = (long long)nb * p.stride;
   p.h1 = s; s += bs;
@@ -380,10 +427,11 @@ int gm_alloc(lsms_ctx* c, long long L, int nb, int maxiter, GmPtrs& p) {
   p.nrm = s; s += 2 * (long long)nb;
   p.st = (GmState*)s;
   p.kk = (int*)(p.st + nb);
+  p.dk = p.kk + nb;
   return LSMS_OK;
 }
 
-// pinned ring of per-system states: RING slots of nb states, read LAG iterations late
+// host-mapped ring of per-system states: RING slots of nb states, read LAG iterations late
 constexpr int LAG = 2, RING = 8;
 
 int ensure_ring(lsms_ctx* c, int nb) {
@@ -391,10 +439,12 @@ int ensure_ring(lsms_ctx* c, int nb) {
   if (c->gm_ring_bytes < need) {
     if (c->gm_ring) cudaFreeHost(c->gm_ring);
     c->gm_ring = nullptr;
+    c->gm_ring_dev = nullptr;
     c->gm_ring_bytes = 0;
-    if (cudaMallocHost(&c->gm_ring, need) != cudaSuccess) {
+    if (cudaHostAlloc(&c->gm_ring, need, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(&c->gm_ring_dev, c->gm_ring, 0) != cudaSuccess) {
       cudaGetLastError();
-      return ctx_fail(c, LSMS_ERR_OOM, "cudaMallocHost failed for the GMRES state ring");
+      return ctx_fail(c, LSMS_ERR_OOM, "cudaHostAlloc failed for the GMRES state ring");
     }
     c->gm_ring_bytes = need;
   }
@@ -403,6 +453,30 @@ int ensure_ring(lsms_ctx* c, int nb) {
       if (cudaEventCreateWithFlags(&c->gm_ev[i], cudaEventDisableTiming) != cudaSuccess)
         return check_cuda(c, "cudaEventCreate");
   return LSMS_OK;
+}
+
+// One Arnoldi step of every system, with the step index read on the device (capturable).
+int enqueue_iteration(lsms_ctx* c, const GmPtrs& g, int nb, long long L, int maxiter, int flags,
+                      cudaStream_t st) {
+  const long long slot = (long long)nb * L;
+  int rc;
+  k_copy_slot<<<grid_for(slot, 256), 256, 0, st>>>(g.X, g.V, slot, g.dk);
+  if ((rc = apply_device(c, nb, g.X, g.W, flags, st))) return rc;
+  const dim3 gd((unsigned)((L + DOT_T - 1) / DOT_T), (unsigned)((maxiter + 2 + DOT_V - 1) / DOT_V), (unsigned)nb);
+  const dim3 ga((unsigned)((L + 255) / 256), (unsigned)nb);
+  // classical Gram-Schmidt; the second pass runs only when the first cancels much of w
+  cudaMemsetAsync(g.h1, 0, (size_t)nb * g.stride * sizeof(double2), st);
+  k_mdot<<<gd, 256, 0, st>>>(g.V, slot, 1, g.dk, 1, g.W, L, g.h1, g.stride, nullptr);   // V^H w, ||w||^2
+  k_gm_prep<<<nb, 32, 0, st>>>(g.dk, g.h1, g.stride, g.st);
+  k_maxpy<<<ga, 256, 0, st>>>(g.V, slot, 1, nullptr, g.dk, g.h1, g.stride, g.W, L, -1.0, nullptr);
+  cudaMemsetAsync(g.h2, 0, (size_t)nb * g.stride * sizeof(double2), st);
+  k_mdot<<<gd, 256, 0, st>>>(g.V, slot, 1, g.dk, 1, g.W, L, g.h2, g.stride, g.st);
+  k_maxpy<<<ga, 256, 0, st>>>(g.V, slot, 1, nullptr, g.dk, g.h2, g.stride, g.W, L, -1.0, g.st);
+  k_gm_column<<<nb, 32, (size_t)(3 * maxiter + 2) * sizeof(double2), st>>>(
+      g.dk, g.h1, g.h2, g.stride, g.H, g.hstride, g.ldh, g.cs, g.sn, g.g, g.st);
+  k_scale_into_slot<<<dim3(grid_for(L, 256), nb), 256, 0, st>>>(g.V, slot, g.W, g.st, L, g.dk);
+  k_gm_snapshot<<<1, 256, 0, st>>>(g.st, nb, (GmState*)c->gm_ring_dev, RING, g.dk);
+  return check_cuda(c, "gmres iteration");
 }
 
 }  // namespace
@@ -429,17 +503,16 @@ int gmres_batch(lsms_ctx* c, const double2* rhs, double2* x, bool x_nonzero, int
   if ((rc = gm_alloc(c, L, nb, maxiter, g))) return rc;
   if ((rc = ensure_ring(c, nb))) return rc;
   GmState* ring = (GmState*)c->gm_ring;
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;
+  std::call_once(attr, [] {
     cudaFuncSetAttribute(k_gm_column, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)((3 * GIVENS_MAX + 2) * sizeof(double2)));
-    attr = true;
-  }
+  });
   const long long slot = (long long)nb * L;              // distance between basis slots
-  // r0 = rhs - A x into basis slot 0 (slot 1 as scratch)
+  // r0 = rhs - A x into basis slot 0
   if (x_nonzero) {
-    if ((rc = apply_device(c, nb, x, g.V + slot, flags, stream))) return rc;
-    k_sub<<<grid_for(slot, 256), 256, 0, stream>>>(g.V, rhs, g.V + slot, slot);
+    if ((rc = apply_device(c, nb, x, g.W, flags, stream))) return rc;
+    k_sub<<<grid_for(slot, 256), 256, 0, stream>>>(g.V, rhs, g.W, slot);
   } else {
     cudaMemsetAsync(x, 0, slot * sizeof(double2), stream);
     cudaMemcpyAsync(g.V, rhs, slot * sizeof(double2), cudaMemcpyDeviceToDevice, stream);
@@ -448,20 +521,42 @@ int gmres_batch(lsms_ctx* c, const double2* rhs, double2* x, bool x_nonzero, int
   mdot(rhs, slot, 1, rhs, L, g.nrm + 1, 2, nb, stream);      // ||rhs||^2 at nrm[2b + 1]
   k_gm_start<<<nb, 1, 0, stream>>>(g.nrm, g.st, g.g, g.stride);
   k_scale_by<<<dim3(grid_for(L, 256), nb), 256, 0, stream>>>(g.V, g.V, g.st, L);
-  cudaMemcpyAsync(ring, g.st, nb * sizeof(GmState), cudaMemcpyDeviceToHost, stream);
+  cudaMemsetAsync(g.dk, 0, sizeof(int), stream);
   cudaStreamSynchronize(stream);
   if ((rc = check_cuda(c, "gmres start"))) return rc;
+  std::vector<GmState> s0(nb);
+  cudaMemcpy(s0.data(), g.st, nb * sizeof(GmState), cudaMemcpyDeviceToHost);
   std::vector<int> kdone(nb, -1);        // -1: still iterating; else iterations kept
   bool nonfinite = false;
   int active = 0;
   for (int b = 0; b < nb; ++b) {
     iters[b] = 0;
-    res[b] = ring[b].res;
-    if (ring[b].flag) nonfinite = true;
-    if (ring[b].beta0 == 0.0 || ring[b].res <= tol[b]) kdone[b] = 0;
+    res[b] = s0[b].res;
+    if (s0[b].flag) nonfinite = true;
+    if (s0[b].beta0 == 0.0 || s0[b].res <= tol[b]) kdone[b] = 0;
     else ++active;
   }
   if (nonfinite) return ctx_fail(c, LSMS_ERR_NONFINITE, "non-finite right-hand side");
+  // Capture one Arnoldi step of all systems as a CUDA graph (after one uncaptured application, so
+  // that every workspace the operator needs exists); launch it once per step.
+  cudaGraphExec_t exec = nullptr;
+  if (active > 0 && c->use_graphs) {
+    if ((rc = apply_device(c, nb, g.X, g.W, flags, stream))) return rc;
+    const int timing = c->timing;
+    c->timing = 0;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int erc = enqueue_iteration(c, g, nb, L, maxiter, flags, stream);
+      const cudaError_t e = cudaStreamEndCapture(stream, &graph);
+      if (erc == LSMS_OK && e == cudaSuccess && graph &&
+          cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+        exec = nullptr;
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();
+    c->timing = timing;
+    c->err.clear();
+  }
   int k = 0, checked = 0;
   auto check = [&](int j) {              // consume the states after iteration j
     cudaEventSynchronize(c->gm_ev[j % RING]);
@@ -479,24 +574,20 @@ int gmres_batch(lsms_ctx* c, const double2* rhs, double2* x, bool x_nonzero, int
     checked = j + 1;
   };
   while (k < maxiter && active > 0 && !nonfinite) {
-    const double2* vk = g.V + (long long)k * slot;
-    double2* w = g.V + (long long)(k + 1) * slot;       // the new vectors are built in their slot
-    if ((rc = apply_device(c, nb, vk, w, flags, stream))) return rc;
-    mdot(g.V, slot, k + 2, w, L, g.h1, g.stride, nb, stream);          // V^H w and ||w||^2
-    k_gm_prep<<<nb, 32, 0, stream>>>(k, g.h1, g.stride, g.st);
-    maxpy(g.V, slot, k + 1, nullptr, g.h1, g.stride, w, L, -1.0, nb, stream);
-    mdot(g.V, slot, k + 2, w, L, g.h2, g.stride, nb, stream, g.st);   // zeros unless needed
-    maxpy(g.V, slot, k + 1, nullptr, g.h2, g.stride, w, L, -1.0, nb, stream, g.st);
-    k_gm_column<<<nb, 32, (size_t)(3 * k + 2) * sizeof(double2), stream>>>(
-        k, g.h1, g.h2, g.stride, g.H, g.hstride, g.ldh, g.cs, g.sn, g.g, g.st);
-    k_scale_by<<<dim3(grid_for(L, 256), nb), 256, 0, stream>>>(w, w, g.st, L);
-    cudaMemcpyAsync(ring + (size_t)(k % RING) * nb, g.st, nb * sizeof(GmState), cudaMemcpyDeviceToHost, stream);
+    if (exec) {
+      if (cudaGraphLaunch(exec, stream) != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        return check_cuda(c, "cudaGraphLaunch");
+      }
+    } else if ((rc = enqueue_iteration(c, g, nb, L, maxiter, flags, stream))) {
+      return rc;
+    }
     cudaEventRecord(c->gm_ev[k % RING], stream);
-    if ((rc = check_cuda(c, "gmres iteration"))) return rc;
     if (k - LAG >= checked) check(k - LAG);
     ++k;
   }
   while (active > 0 && !nonfinite && checked < k) check(checked);   // drain
+  if (exec) cudaGraphExecDestroy(exec);
   cudaStreamSynchronize(stream);
   if ((flags & LSMS_APPLY_MIXED) && (rc = mixed_check(c))) return rc;
   if (nonfinite) return ctx_fail(c, LSMS_ERR_NONFINITE, "non-finite value in GMRES");
@@ -537,6 +628,7 @@ extern "C" int lsms_solve(lsms_ctx* c, int nsrc, const double* src_xy, double to
   if ((rc = validate_sources(c, nsrc, src_xy))) return rc;
   if (!(tol > 0.0) || maxiter <= 0 || maxiter > GIVENS_MAX)
     return ctx_fail(c, LSMS_ERR_ARG, "tol must be > 0 and 0 < maxiter <= 4096");
+  if (is_batch(c)) return batch_solve(c, nsrc, src_xy, tol, maxiter, x0, beta_out, info);
   const long long L = (long long)c->n * c->P;
   const long long LT = (long long)nsrc * L;
   cudaStream_t st = c->stream;

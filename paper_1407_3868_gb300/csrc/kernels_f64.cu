@@ -8,6 +8,7 @@
 //     precomputed plane-wave tables, then per-node order-factor dots.
 //   per-node reflection (Sec. 2 Eq. "sommerfeldsys"): closed-form 2x2 response per node.
 #include <cmath>
+#include <mutex>
 
 #include "lsms_internal.h"
 
@@ -382,11 +383,10 @@ void launch_translate_f64(const double* cx, const double* cy, int n, int p, doub
                           const double2* xs, double2* alpha, int nrhs, cudaStream_t st) {
   if (n == 0 || nrhs == 0) return;
   const size_t smem = (size_t)(CH * 32 + TW * CH * HS) * (sizeof(double2) + sizeof(double));
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;
+  std::call_once(attr, [smem] {
     cudaFuncSetAttribute(k_translate_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  });
   dim3 grid((n + TW - 1) / TW, nrhs);
   k_translate_f64<<<grid, TW * 32, smem, st>>>(cx, cy, n, p, k, xs, alpha);
 }

@@ -83,8 +83,23 @@ struct lsms_ctx {
   DevBuf gm_v, gm_h, gm_small, gm_x, gm_r, gm_w;
   double* h_pinned = nullptr;       // small pinned host scratch for residual polling
   cudaEvent_t gm_ev[8] = {};        // events of the GMRES residual ring
-  void* gm_ring = nullptr;          // pinned ring of per-system GMRES states
+  void* gm_ring = nullptr;          // host-mapped ring of per-system GMRES states
+  void* gm_ring_dev = nullptr;      // its device address
   size_t gm_ring_bytes = 0;
+  int use_graphs = 1;               // capture each GMRES step as a CUDA graph
+  double split_mult = 1.0;          // source splits of the FP32 translation (autotuned)
+
+  // a batch of independent layouts (lsms_set_layouts): one child context per layout
+  std::vector<lsms_ctx*> kids;
+  std::vector<long long> kid_off;   // first disc of every layout, and the total at the end
+  struct GraphEntry {
+    const void* x;
+    void* y;
+    int flags;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;   // captured batched applications
+  std::vector<cudaEvent_t> kid_ev;  // join events (one per layout) and a fork event at the end
 
   cudaStream_t stream = nullptr;    // internal stream of the host-pointer entry points
 

@@ -29,6 +29,15 @@ int aggregate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* G, cudaSt
 int disaggregate_mixed(lsms_ctx* c, int nrhs, const double2* V, double2* alpha, cudaStream_t st);
 int reflection_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st);
 
+// batches of independent layouts (batch.cu)
+bool is_batch(const lsms_ctx* c);
+void batch_free(lsms_ctx* c);
+int batch_apply(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags, cudaStream_t st);
+int batch_solve(lsms_ctx* c, int nsrc, const double* src_xy, double tol, int maxiter, const double* x0,
+                double* beta_out, lsms_solve_info* info);
+int batch_eval_field(lsms_ctx* c, int layout, int ntgt, const double* tgt, int which, double* out);
+int batch_mixed_check(lsms_ctx* c);
+
 // small device helpers (gmres.cu)
 void launch_diag_mul(const double2* x, const double2* s, double2* y, long long total, int P,
                      cudaStream_t st);

@@ -11,6 +11,7 @@
 // of 2 VB - 1 sequence values over the source orders, so each staged value feeds VB complex FMAs.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <unordered_map>
 #include <vector>
 
@@ -361,12 +362,11 @@ __global__ void k_centres_ff(const double* __restrict__ cx, const double* __rest
 template <int VB, int NB, int RB>
 void launch_vbnb(dim3 grid, cudaStream_t st, const float4* cff, int n, int p, float kh, float kl,
                  const float2* xs, float2* part, int sps, int nrhs, float nh, float nl) {
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;
+  std::call_once(attr, [] {
     cudaFuncSetAttribute(k_translate_f32<VB, NB, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)TRANSLATE_F32_SMEM);
-    attr = true;
-  }
+  });
   grid.z = (nrhs + RB - 1) / RB;
   k_translate_f32<VB, NB, RB><<<grid, MW * 32, TRANSLATE_F32_SMEM, st>>>(cff, n, p, kh, kl, xs, part, sps,
                                                                         nrhs, nh, nl);
@@ -470,11 +470,11 @@ int build_lowp_tables(lsms_ctx* c) {
 
 // Splits of the source range so that the grid covers the GPU several times (3 CTAs per SM for one
 // right-hand side per CTA, 2 for four).
-static int translate_splits(int n, int nrhs) {
+static int translate_splits(int n, int nrhs, double mult = 1.0) {
   const int tiles = (n + MW * MT - 1) / (MW * MT);
   const int zb = nrhs >= 4 ? (nrhs + 3) / 4 : nrhs;
   const int per_sm = nrhs >= 4 ? 2 : 3;
-  int s = (152 * per_sm * 4 + tiles * zb - 1) / (tiles * zb);
+  int s = (int)std::ceil(mult * (152 * per_sm * 4) / (double)(tiles * zb));
   const int max_s = (n + MCH - 1) / MCH;
   if (s > max_s) s = max_s;
   if (s < 1) s = 1;
@@ -484,7 +484,7 @@ static int translate_splits(int n, int nrhs) {
 int translate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st) {
   const int n = c->n, p = c->p, P = c->P;
   if (n == 0 || nrhs == 0) return LSMS_OK;
-  int splits = translate_splits(n, nrhs);
+  int splits = translate_splits(n, nrhs, c->split_mult);
   int sps = (n + splits - 1) / splits;
   sps = ((sps + MCH - 1) / MCH) * MCH;
   splits = (n + sps - 1) / sps;

@@ -24,7 +24,8 @@ EXPORTS = ["lsms_create", "lsms_set_particles", "lsms_apply", "lsms_apply_ex", "
            "lsms_get_contour", "lsms_get_scattering", "lsms_num_nodes", "lsms_num_particles",
            "lsms_solve", "lsms_eval_field", "lsms_last_error", "lsms_destroy",
            "lsms_build_contour", "lsms_scattering_diagonal", "lsms_check_geometry",
-           "lsms_set_timing", "lsms_last_timing", "lsms_translate_mixed_noalloc"]
+           "lsms_set_timing", "lsms_last_timing", "lsms_translate_mixed_noalloc",
+           "lsms_set_layouts", "lsms_num_layouts", "lsms_autotune"]
 
 
 class LsmsError(RuntimeError):
@@ -83,6 +84,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsms_set_timing": (i, [_P, i]),
         "lsms_last_timing": (i, [_P, _D, _D, ctypes.POINTER(ctypes.c_int)]),
         "lsms_translate_mixed_noalloc": (i, [i, i, d, i, _P, _P, _P, _P]),
+        "lsms_set_layouts": (i, [_P, i, ctypes.POINTER(ctypes.c_int), _D]),
+        "lsms_num_layouts": (i, [_P]),
+        "lsms_autotune": (i, [_P, _D]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -151,6 +155,23 @@ class Context:
         c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 2)
         self._check(self.lib.lsms_set_particles(self.h, c.shape[0], _dptr(c)))
         self.n = c.shape[0]
+        self.layout_counts = None
+
+    def set_layouts(self, layouts):
+        """A batch of independent layouts: `layouts` is a list of (N_l, 2) centre arrays."""
+        counts = np.array([len(c) for c in layouts], dtype=np.int32)
+        xy = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.float64).reshape(-1, 2)
+                                                  for c in layouts]) if len(layouts) else
+                                  np.zeros((0, 2)))
+        self._check(self.lib.lsms_set_layouts(self.h, len(layouts), counts.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_int)), _dptr(xy)))
+        self.n = int(counts.sum())
+        self.layout_counts = counts
+
+    def autotune(self):
+        m = ctypes.c_double()
+        self._check(self.lib.lsms_autotune(self.h, ctypes.byref(m)))
+        return m.value
 
     def contour(self):
         lam = np.zeros(self.ns, dtype=np.complex128)
@@ -236,12 +257,17 @@ class Context:
     # -- solve and fields --------------------------------------------------------------------------
     def solve(self, sources, tol=1e-10, maxiter=500, x0=None, history=0, raise_on_error=True):
         s = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 2)
-        beta = np.zeros((s.shape[0], self.n, self.P), dtype=np.complex128)
+        if getattr(self, "layout_counts", None) is not None:
+            beta = np.zeros((self.n, self.P), dtype=np.complex128)    # one array per layout, joined
+        else:
+            beta = np.zeros((s.shape[0], self.n, self.P), dtype=np.complex128)
         info = SolveInfo()
         hist = np.zeros(max(history, 1))
         info.history = hist.ctypes.data_as(_D)
         info.history_cap = history
         x0a = None if x0 is None else _c128(x0, beta.shape)
+        if getattr(self, "layout_counts", None) is not None and x0 is not None:
+            x0a = _c128(x0, beta.shape)
         rc = self.lib.lsms_solve(self.h, s.shape[0], _dptr(s), tol, maxiter, _dptr(x0a), _dptr(beta),
                                  ctypes.byref(info))
         if raise_on_error:
