@@ -51,7 +51,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-solve", action="store_true", help="skip the solve timings")
-    ap.add_argument("--solve-fp64", action="store_true", help="also time the FP64 solve (slow)")
+    ap.add_argument("--no-fp64-solve", action="store_true", help="skip the FP64 solve (about 70 s)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the block and sweep measurements")
+    ap.add_argument("--full", action="store_true",
+                    help="also solve the 64-source block and the 128-layout sweep (mixed, a few minutes)")
     ap.add_argument("--oracle-rows", type=int, default=8,
                     help="target rows of the oracle's bounded sample per reference step")
     ap.add_argument("--baseline-rows", type=int, default=40,
@@ -265,7 +268,7 @@ def run_ours(args, rank, world, local_rank):
         solve["mixed_refinements"] = info_m["outer_iters"]
         solve["mixed_rel_res_fp64"] = info_m["rel_res_fp64"]
         ctxm.close()
-        if args.solve_fp64:
+        if not args.no_fp64_solve:
             ctxd = lsms.context_for(w, lsms.LSMS_FP64)
             ctxd.set_particles(centres)
             t0 = time.perf_counter()
@@ -274,8 +277,12 @@ def run_ours(args, rank, world, local_rank):
             solve["fp64_iters"] = info_d["iters"]
             u_d = ctxd.eval_field(w.targets, 0, lsms.FIELD_SCATTERED)
             solve["mixed_vs_fp64_field_rel_err"] = float(np.linalg.norm(u_m - u_d) / np.linalg.norm(u_d))
+            solve["speedup_mixed_vs_fp64"] = solve["fp64_s"] / solve["mixed_s"]
             ctxd.close()
     ctx.close()
+    batched = None
+    if world == 1 and not args.no_batched:
+        batched = run_batched(args, dev, flush)
 
     if rank != 0:
         return None
@@ -291,6 +298,7 @@ def run_ours(args, rank, world, local_rank):
                  "translate_frac_of_fp64_peak": (flop / (tr64_ms / 1e3) / 1e12) / FP64_PEAK_TFLOPS},
         "speedup_mixed_vs_fp64": value / fp64_rate,
         "solve": solve,
+        "batched": batched,
         "roofline": {"kernel": "k_translate_f32", "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": traffic, "flop_per_launch": flop, "launch_ms": tr_ms,
@@ -306,6 +314,92 @@ def run_ours(args, rank, world, local_rank):
         except Exception as e:  # pragma: no cover
             line["cpu_baseline"] = {"value": None, "error": str(e)[-300:]}
     return line
+
+
+def time_device(fn, steps, flush=None):
+    import torch
+    ms = 0.0
+    for i in range(steps):
+        if flush is not None:
+            flush.fill_(float(i))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    return ms / steps
+
+
+def run_batched(args, dev, flush):
+    """Batched forms: 64 sources on one 2000-disc layout (block of right-hand sides) and a design
+    sweep of 128 layouts (log-uniform N in [200, 4000]) applied as one graph launch."""
+    import numpy as np
+    import torch
+
+    from paper_1407_3868_gb300 import inputs, lsms
+    out = {}
+    # block of right-hand sides
+    w = inputs.WORKLOADS["disc2000_p12_ns768_src64"]
+    ctx = lsms.context_for(w, lsms.LSMS_MIXED)
+    ctx.set_particles(w.centres())
+    nrhs = len(w.sources)
+    x = torch.from_numpy(inputs.random_coefficients(w.n, w.p, nrhs, 0)).to(dev)
+    y = torch.empty_like(x)
+    fl_m = lsms.APPLY_SCALED | lsms.APPLY_MIXED
+    ctx.apply_dev(x, y, fl_m)
+    torch.cuda.synchronize()
+    ms_m = time_device(lambda: ctx.apply_dev(x, y, fl_m), 5, flush)
+    ctx.apply_dev(x, y, lsms.APPLY_SCALED)
+    torch.cuda.synchronize()
+    ms_d = time_device(lambda: ctx.apply_dev(x, y, lsms.APPLY_SCALED), 1, flush)
+    blk = {"workload": w.name, "discs": w.n, "p": w.p, "contour_nodes": w.n_nodes, "rhs": nrhs,
+           "mixed": {"ms_per_block_apply": ms_m, "rhs_applies_per_s": nrhs * 1e3 / ms_m},
+           "fp64": {"ms_per_block_apply": ms_d, "rhs_applies_per_s": nrhs * 1e3 / ms_d}}
+    blk["speedup_mixed_vs_fp64"] = ms_d / ms_m
+    if args.full:
+        t0 = time.perf_counter()
+        _, info = ctx.solve(w.sources, tol=1e-10, maxiter=1000)
+        blk["mixed_solve_s"] = time.perf_counter() - t0
+        blk["mixed_solve_iters"] = info["iters"]
+        blk["mixed_solve_rel_res_fp64"] = info["rel_res_fp64"]
+    ctx.close()
+    out["block_rhs"] = blk
+    # design sweep over 128 layouts
+    lay = inputs.sweep_layouts()
+    h = inputs.widened_half_width(max(len(c) for c in lay))
+    ws = inputs.Workload("sweep128_p12_ns512", 0, 12, 512, 152.0, -h, h, 0, np.array([[0.0, 1.0]]),
+                         inputs.observation_points(-h, h, 64, 1.5), 1e-10)
+    b = lsms.context_for(ws, lsms.LSMS_MIXED)
+    b.set_layouts(lay)
+    mult = b.autotune()
+    ntot = sum(len(c) for c in lay)
+    x = torch.from_numpy(inputs.random_coefficients(ntot, ws.p, 1, 0)[0]).to(dev)
+    y = torch.empty_like(x)
+    for _ in range(2):
+        b.apply_dev(x, y, fl_m)
+    torch.cuda.synchronize()
+    ms_m = time_device(lambda: b.apply_dev(x, y, fl_m), 5, flush)
+    for _ in range(2):
+        b.apply_dev(x, y, lsms.APPLY_SCALED)
+    torch.cuda.synchronize()
+    ms_d = time_device(lambda: b.apply_dev(x, y, lsms.APPLY_SCALED), 1, flush)
+    sw = {"workload": ws.name, "layouts": len(lay), "discs": ntot, "p": ws.p, "contour_nodes": ws.n_nodes,
+          "split_mult_autotuned": mult,
+          "mixed": {"ms_per_sweep_apply": ms_m, "layout_applies_per_s": len(lay) * 1e3 / ms_m,
+                    "launch": "one CUDA graph (128 branches)"},
+          "fp64": {"ms_per_sweep_apply": ms_d, "layout_applies_per_s": len(lay) * 1e3 / ms_d}}
+    sw["speedup_mixed_vs_fp64"] = ms_d / ms_m
+    if args.full:
+        t0 = time.perf_counter()
+        _, info = b.solve(ws.sources, tol=1e-10, maxiter=1000)
+        sw["mixed_solve_s"] = time.perf_counter() - t0
+        sw["mixed_solve_iters_max"] = info["iters"]
+        sw["mixed_solve_rel_res_fp64_max"] = info["rel_res_fp64"]
+    b.close()
+    out["sweep"] = sw
+    return out
 
 
 def run_reference(args, rank):
