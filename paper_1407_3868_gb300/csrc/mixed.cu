@@ -161,15 +161,20 @@ constexpr size_t TRANSLATE_F32_SMEM = (size_t)(2 * GUARD + MW * 32 * MHS) * size
 // Complex products use three real FMAs (Gauss): A += hr br, B += hi bi, C += (hr+hi)(br+bi);
 // re = A - B, im = C - A - B.
 // RB coefficient vectors (right-hand sides r0 .. r0 + RB - 1) share every generated sequence.
-template <int VB, int NB, int RB>
+// The order p is a template parameter: P = 2p + 1, VB = ceil(P/4) outputs per lane, NB = ceil(P/VB)
+// blocks of source orders, and the padded tail of the last block is dropped at compile time.
+template <int PT, int RB>
 __global__ void __launch_bounds__(MW * 32, RB == 1 ? 3 : 2)
-k_translate_f32(const float4* __restrict__ cff, int n, int p, float k_hi, float k_lo,
+k_translate_f32(const float4* __restrict__ cff, int n, float k_hi, float k_lo,
                 const float2* __restrict__ xs, float2* __restrict__ part, int src_per_split,
                 int nrhs, float near_hi, float near_lo) {
+  constexpr int p = PT;
+  constexpr int P = 2 * PT + 1;
+  constexpr int VB = (P + 3) / 4;
+  constexpr int NB = (P + VB - 1) / VB;
   __shared__ float2 sb[RB][MCH][VB * NB + 1];
   __shared__ float4 sc[MCH];
   extern __shared__ float2 sh[];
-  const int P = 2 * p + 1;
   const int r0 = blockIdx.z * RB;
   const int split = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -228,6 +233,7 @@ k_translate_f32(const float4* __restrict__ cff, int n, int p, float k_hi, float 
           }
 #pragma unroll
           for (int u = 0; u < VB; ++u) {
+            if (nb * VB + u >= P) break;            // padded source orders (compile time)
 #pragma unroll
             for (int rr = 0; rr < RB; ++rr) {
               const float2 b = sb[rr][s0 + q4][nb * VB + u];
@@ -359,42 +365,46 @@ __global__ void k_centres_ff(const double* __restrict__ cx, const double* __rest
   out[j] = make_float4(xh, (float)(cx[j] - (double)xh), yh, (float)(cy[j] - (double)yh));
 }
 
-template <int VB, int NB, int RB>
-void launch_vbnb(dim3 grid, cudaStream_t st, const float4* cff, int n, int p, float kh, float kl,
-                 const float2* xs, float2* part, int sps, int nrhs, float nh, float nl) {
+template <int PT, int RB>
+void launch_pt(dim3 grid, cudaStream_t st, const float4* cff, int n, float kh, float kl,
+               const float2* xs, float2* part, int sps, int nrhs, float nh, float nl) {
   static std::once_flag attr;
   std::call_once(attr, [] {
-    cudaFuncSetAttribute(k_translate_f32<VB, NB, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_translate_f32<PT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)TRANSLATE_F32_SMEM);
   });
   grid.z = (nrhs + RB - 1) / RB;
-  k_translate_f32<VB, NB, RB><<<grid, MW * 32, TRANSLATE_F32_SMEM, st>>>(cff, n, p, kh, kl, xs, part, sps,
-                                                                        nrhs, nh, nl);
+  k_translate_f32<PT, RB><<<grid, MW * 32, TRANSLATE_F32_SMEM, st>>>(cff, n, kh, kl, xs, part, sps, nrhs, nh, nl);
 }
 
-// Order blocking for P = 2p + 1: VB = ceil(P/4) outputs per lane, NB = ceil(P/VB) source blocks.
-// Four or more right-hand sides are contracted four at a time against each generated sequence.
+// Four or more right-hand sides are contracted four at a time against each generated sequence
+// (orders p >= 6; smaller orders take one at a time).
 void launch_translate_kernel(dim3 grid, cudaStream_t st, const float4* cff, int n, int p, float kh,
                              float kl, const float2* xs, float2* part, int sps, int nrhs,
                              float nh = 0.f, float nl = 0.f) {
   const bool blk = nrhs >= 4;
-#define LSMS_TR(VB, NB)                                                                         \
-  (blk ? launch_vbnb<VB, NB, 4>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs, nh, nl)       \
-       : launch_vbnb<VB, NB, 1>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs, nh, nl))
+#define LSMS_T1(PT) launch_pt<PT, 1>(grid, st, cff, n, kh, kl, xs, part, sps, nrhs, nh, nl)
+#define LSMS_TB(PT) (blk ? launch_pt<PT, 4>(grid, st, cff, n, kh, kl, xs, part, sps, nrhs, nh, nl) : LSMS_T1(PT))
   switch (p) {
-    case 0: launch_vbnb<1, 1, 1>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs, nh, nl); break;
-    case 1: launch_vbnb<1, 3, 1>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs, nh, nl); break;
-    case 2: launch_vbnb<2, 3, 1>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs, nh, nl); break;
-    case 3: launch_vbnb<2, 4, 1>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs, nh, nl); break;
-    case 4: launch_vbnb<3, 3, 1>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs, nh, nl); break;
-    case 5: launch_vbnb<3, 4, 1>(grid, st, cff, n, p, kh, kl, xs, part, sps, nrhs, nh, nl); break;
-    case 6: case 7: LSMS_TR(4, 4); break;
-    case 8: case 9: LSMS_TR(5, 4); break;
-    case 10: case 11: LSMS_TR(6, 4); break;
-    case 12: case 13: LSMS_TR(7, 4); break;
-    default: LSMS_TR(8, 4); break;
+    case 0: LSMS_T1(0); break;
+    case 1: LSMS_T1(1); break;
+    case 2: LSMS_T1(2); break;
+    case 3: LSMS_T1(3); break;
+    case 4: LSMS_T1(4); break;
+    case 5: LSMS_T1(5); break;
+    case 6: LSMS_TB(6); break;
+    case 7: LSMS_TB(7); break;
+    case 8: LSMS_TB(8); break;
+    case 9: LSMS_TB(9); break;
+    case 10: LSMS_TB(10); break;
+    case 11: LSMS_TB(11); break;
+    case 12: LSMS_TB(12); break;
+    case 13: LSMS_TB(13); break;
+    case 14: LSMS_TB(14); break;
+    default: LSMS_TB(15); break;
   }
-#undef LSMS_TR
+#undef LSMS_T1
+#undef LSMS_TB
 }
 
 }  // namespace
