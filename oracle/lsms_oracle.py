@@ -547,6 +547,47 @@ class Problem:
         ex = np.exp(g3[None, :] * (pts[:, 1:2] + d) + 1j * self.lam[None, :] * pts[:, 0:1])
         return ex @ (self.wt * sig / g3) / FOUR_PI
 
+    # --- radiated power (lossless media; a check of the whole solution, not a step of it) -------
+    def outgoing_power(self, src, beta, tol=1e-13):
+        """Time-averaged power leaving through y = +inf (layer 1) and y = -inf (layer 3).
+
+        Above the source, u_1 = (1/4pi) int U exp(-gamma_1 y + i lambda x) / gamma_1 with
+        U = sigma_1 + exp(gamma_1 y0 - i lambda x0) (the direct wave written in the same form, as in
+        Eq. "sommer"); below y = -d, u_3 = (1/4pi) int sigma_3 exp(gamma_3 (y + d) + i lambda x) /
+        gamma_3.  Parseval turns the flux Im int conj(u) du/dn dx into (1/8pi) int |U|^2 / s_1 over
+        |lambda| < k_1 (s_i = sqrt(k_i^2 - lambda^2); evanescent waves carry no power), and likewise
+        (1/8pi) int |sigma_3|^2 / s_3 over |lambda| < k_3.  With lambda = k cos(theta) the weight
+        1/s becomes d theta; the layer-3 interval is split where lambda crosses +-k_1, +-k_2
+        (square-root branch points of the densities), each piece is mapped by
+        theta = a + (b - a)(1 - cos phi)/2, which makes the endpoint square roots smooth in phi, and
+        integrated by adaptive Gauss-Kronrod (QUADPACK): between k_1 and k_2 the layer acts as a
+        leaky waveguide and the densities peak near its modes.  The densities are evaluated exactly
+        on the real axis from beta.
+        """
+        from scipy import integrate
+
+        k1, k2, k3 = self.m.k1, self.m.k2, self.m.k3
+
+        def density(lam_real, layer):
+            lam = np.array([lam_real], dtype=complex)
+            pr = Problem(self.m, self.p, self.c, lam, np.zeros_like(lam))
+            sig = pr.densities(src, beta)[0]
+            if layer == 1:
+                return sig[0] + np.exp(gamma(lam, k1)[0] * src[1] - 1j * lam[0] * src[0])
+            return sig[3]
+
+        def piece(k, layer, a, b):
+            def f(phi):
+                th = a + (b - a) * 0.5 * (1.0 - math.cos(phi))
+                return abs(density(k * math.cos(th), layer)) ** 2 * (b - a) * 0.5 * math.sin(phi)
+            return integrate.quad(f, 0.0, math.pi, epsabs=tol, epsrel=tol, limit=4000)[0]
+
+        up = piece(k1, 1, 0.0, math.pi) / (2.0 * FOUR_PI)
+        inner = sorted(math.acos(kk / k3) for kk in (k1, k2) if kk < k3)
+        breaks = [0.0] + inner + [math.pi - t for t in reversed(inner)] + [math.pi]
+        down = sum(piece(k3, 3, a, b) for a, b in zip(breaks[:-1], breaks[1:])) / (2.0 * FOUR_PI)
+        return up, down
+
 
 def gmres(matvec, b, tol=1e-12, maxiter=500):
     """Unrestarted GMRES (Saad and Schultz, cited in Sec. 3.2) with modified Gram-Schmidt.

@@ -343,6 +343,28 @@ def test_reciprocity_of_layered_scattering():
     assert abs(u_ab - u_ba) <= 1e-6 * abs(u_ab)
 
 
+def test_energy_flux_balance_for_lossless_media():
+    # Lossless layers and discs: the power leaving through y = +-inf equals what the line source
+    # emits, 1/4 + Im u^s(x0) (Green's identity around the source; the discs absorb nothing).
+    # The fluxes come from the densities on the real axis, Im u^s(x0) from the contour, so the
+    # two sides agree to the contour's accuracy only if translation, reflection, the scattering
+    # matrix and the solve are all right (a mirrored translation angle or a dropped sigma_2^-
+    # term breaks the balance at the 1e-4 level).
+    src = np.array([0.3, 1.0])
+    m = medium(3 * math.pi, 3 * math.pi, 3 * math.pi)
+    lam, wt = O.contour(512, m.k1, m.k2, m.k3, 0.2, 120.0)
+    up, down = O.Problem(m, 4, np.zeros((0, 2)), lam, wt).outgoing_power(src, None)
+    assert up == pytest.approx(0.125, abs=1e-12) and down == pytest.approx(0.125, abs=1e-12)
+    m = medium()
+    lam, wt = O.contour(1024, m.k1, m.k2, m.k3, 0.2, 120.0)
+    c = np.array([[0.2, -0.7], [-0.6, -1.3], [0.9, -1.0]])
+    pr = O.Problem(m, 4, c, lam, wt)
+    beta = pr.solve_dense(src)
+    up, down = pr.outgoing_power(src, beta)
+    u_s = pr.field_layer1(src, beta, src[None, :], "scattered")[0]
+    assert abs(up + down - (0.25 + u_s.imag)) < 1e-9 * 0.25
+
+
 def test_oracle_gmres_matches_lu():
     m = medium()
     lam, wt = O.contour(256, m.k1, m.k2, m.k3, 0.2, 141.0)
