@@ -93,7 +93,7 @@ def oracle_sample(workload: str, rows: int) -> dict:
     _ = x[sel] - pr.S[None, :] * alpha
     t2 = time.perf_counter()
     full = (t1 - t0) + (t2 - t1) * w.n / rows
-    return {"global_s": t1 - t0, "rows": rows, "rows_s": t2 - t1, "full_apply_s": full}
+    return {"global_s": t1 - t0, "rows": rows, "n": w.n, "rows_s": t2 - t1, "full_apply_s": full}
 
 
 def run_oracle_child(workload: str, rows: int) -> dict:
@@ -109,7 +109,7 @@ def run_oracle_child(workload: str, rows: int) -> dict:
 def cpu_baseline_entry(s: dict) -> dict:
     return {"value": 1.0 / s["full_apply_s"], "unit": "applies/s", "cores": 1, "kind": "oracle",
             "sample": (f"FP64 NumPy/SciPy oracle, one BLAS thread: global aggregate + layer solves "
-                       f"({s['global_s']:.2f} s) and {s['rows']} of 5000 target rows "
+                       f"({s['global_s']:.2f} s) and {s['rows']} of {s['n']} target rows "
                        f"({s['rows_s']:.2f} s), extrapolated to a full application "
                        f"({s['full_apply_s']:.1f} s)")}
 
@@ -259,27 +259,33 @@ def run_ours(args, rank, world, local_rank):
 
     solve = None
     if not args.no_solve:
-        solve = {}
-        ctxm = lsms.context_for(w, lsms.LSMS_MIXED)
-        ctxm.set_particles(centres)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        beta_m, info_m = ctxm.solve(w.sources, tol=1e-10, maxiter=2000)
-        solve["mixed_s"] = time.perf_counter() - t0
-        u_m = ctxm.eval_field(w.targets, 0, lsms.FIELD_SCATTERED)
-        solve["mixed_iters"] = info_m["iters"]
-        solve["mixed_refinements"] = info_m["outer_iters"]
-        solve["mixed_rel_res_fp64"] = info_m["rel_res_fp64"]
-        ctxm.close()
+        # the mixed solve refines to 1e-8 (the refinement target of the mixed 5000-disc case) and,
+        # for comparison, to 1e-10 (the FP64 solve's tolerance); fields are compared at the targets
+        solve = {"mixed_tol": 1e-8, "fp64_tol": 1e-10}
+        u_m = {}
+        for tol, key in ((1e-8, "mixed"), (1e-10, "mixed_tol1e-10")):
+            ctxm = lsms.context_for(w, lsms.LSMS_MIXED)
+            ctxm.set_particles(centres)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, info_m = ctxm.solve(w.sources, tol=tol, maxiter=2000)
+            solve[key + "_s"] = time.perf_counter() - t0
+            u_m[key] = ctxm.eval_field(w.targets, 0, lsms.FIELD_SCATTERED)
+            solve[key + "_iters"] = info_m["iters"]
+            solve[key + "_refinements"] = info_m["outer_iters"]
+            solve[key + "_rel_res_fp64"] = info_m["rel_res_fp64"]
+            ctxm.close()
         if not args.no_fp64_solve:
             ctxd = lsms.context_for(w, lsms.LSMS_FP64)
             ctxd.set_particles(centres)
             t0 = time.perf_counter()
-            beta_d, info_d = ctxd.solve(w.sources, tol=1e-10, maxiter=2000)
+            _, info_d = ctxd.solve(w.sources, tol=1e-10, maxiter=2000)
             solve["fp64_s"] = time.perf_counter() - t0
             solve["fp64_iters"] = info_d["iters"]
+            solve["fp64_rel_res"] = info_d["rel_res_fp64"]
             u_d = ctxd.eval_field(w.targets, 0, lsms.FIELD_SCATTERED)
-            solve["mixed_vs_fp64_field_rel_err"] = float(np.linalg.norm(u_m - u_d) / np.linalg.norm(u_d))
+            for key in u_m:
+                solve[key + "_vs_fp64_field_rel_err"] = float(np.linalg.norm(u_m[key] - u_d) / np.linalg.norm(u_d))
             solve["speedup_mixed_vs_fp64"] = solve["fp64_s"] / solve["mixed_s"]
             ctxd.close()
     ctx.close()
