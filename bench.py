@@ -33,17 +33,31 @@ WORKLOAD = "disc5000_p14_ns1024"
 METRIC = "N=5000 solve time & operator applies/s, mixed/batched vs FP64 at <=1e-8 rel err"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12    # 152 SMs x 128 FP32 lanes x FMA x max clock
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12      # 2 FP64 FMA per SM per clock on GB300
+
+
+def _measured_peaks():
+    """Measured copy bandwidth and cuBLAS BF16 throughput of this GPU pool, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, 6800.0, "fallback"
+
+
+BF16_PEAK_TFLOPS, HBM_PEAK_GBS, PEAK_SOURCE = _measured_peaks()
 # DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by the SHA-256 of the
-# source file it was taken on (reported as null once the source changes).
-TRAFFIC = {
-    # k_translate_f32<14,1>, 5000 discs: dram__bytes_read.sum 1.307 MB + dram__bytes_write.sum 0.164 MB
-    "04aedfd580a02b3a": 1.470720e6,
-}
+# source files it was built from (reported as null once they change).
+TRAFFIC = {}
+KERNEL_SOURCES = ("mixed.cu", "ff_hankel.cuh")
 
 
-def src_hash(path: str) -> str:
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def src_hash(paths) -> str:
+    h = hashlib.sha256()
+    for path in paths:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -254,7 +268,7 @@ def run_ours(args, rank, world, local_rank):
     tr_ms = statistics.mean(t_tr_mixed)
     achieved = flop / (tr_ms / 1e3) / 1e12
     tr64_ms = statistics.mean(t_tr_fp64)
-    key = src_hash(os.path.join(ROOT, "paper_1407_3868_gb300", "csrc", "mixed.cu"))
+    key = src_hash([os.path.join(ROOT, "paper_1407_3868_gb300", "csrc", f) for f in KERNEL_SOURCES])
     traffic = TRAFFIC.get(key)
 
     solve = None
@@ -357,22 +371,49 @@ def run_batched(args, dev, flush):
     x = torch.from_numpy(inputs.random_coefficients(w.n, w.p, nrhs, 0)).to(dev)
     y = torch.empty_like(x)
     fl_m = lsms.APPLY_SCALED | lsms.APPLY_MIXED
-    ctx.apply_dev(x, y, fl_m)
-    torch.cuda.synchronize()
-    ms_m = time_device(lambda: ctx.apply_dev(x, y, fl_m), 5, flush)
+    P = 2 * w.p + 1
+    flop = 8.0 * P * P * w.n * (w.n - 1) * nrhs
+    blk = {"workload": w.name, "discs": w.n, "p": w.p, "contour_nodes": w.n_nodes, "rhs": nrhs}
+    for tcmin, key in ((48, "mixed"), (0, "mixed_cuda_cores")):
+        ctx.set_tc_translation(tcmin)
+        ctx.apply_dev(x, y, fl_m)
+        torch.cuda.synchronize()
+        ms_m = time_device(lambda: ctx.apply_dev(x, y, fl_m), 5, flush)
+        ctx.set_timing(1)
+        tr = []
+        for _ in range(3):
+            ctx.apply_dev(x, y, fl_m)
+            tr.append(ctx.last_timing()[0])
+        ctx.set_timing(0)
+        tr_ms = statistics.mean(tr)
+        blk[key] = {"ms_per_block_apply": ms_m, "rhs_applies_per_s": nrhs * 1e3 / ms_m,
+                    "translate_ms": tr_ms, "translate_tflops_algorithmic": flop / (tr_ms / 1e3) / 1e12,
+                    "translation": "tensor cores (split-BF16 tcgen05)" if tcmin else "FP32 CUDA cores"}
+    ctx.set_tc_translation(48)
     ctx.apply_dev(x, y, lsms.APPLY_SCALED)
     torch.cuda.synchronize()
     ms_d = time_device(lambda: ctx.apply_dev(x, y, lsms.APPLY_SCALED), 1, flush)
-    blk = {"workload": w.name, "discs": w.n, "p": w.p, "contour_nodes": w.n_nodes, "rhs": nrhs,
-           "mixed": {"ms_per_block_apply": ms_m, "rhs_applies_per_s": nrhs * 1e3 / ms_m},
-           "fp64": {"ms_per_block_apply": ms_d, "rhs_applies_per_s": nrhs * 1e3 / ms_d}}
-    blk["speedup_mixed_vs_fp64"] = ms_d / ms_m
-    if args.full:
-        t0 = time.perf_counter()
-        _, info = ctx.solve(w.sources, tol=1e-10, maxiter=1000)
-        blk["mixed_solve_s"] = time.perf_counter() - t0
-        blk["mixed_solve_iters"] = info["iters"]
-        blk["mixed_solve_rel_res_fp64"] = info["rel_res_fp64"]
+    blk["fp64"] = {"ms_per_block_apply": ms_d, "rhs_applies_per_s": nrhs * 1e3 / ms_d}
+    blk["speedup_mixed_vs_fp64"] = ms_d / blk["mixed"]["ms_per_block_apply"]
+    # the tensor-core translation: algorithmic flops against the measured BF16 peak, and the MMA
+    # work it issues (six BF16 plane products on the real embedding, padded to 128 x 64 x 64 tiles)
+    ngroups = (w.n + 15) // 16
+    issued = 2.0 * 6 * 128 * 64 * 64 * 8 * ngroups * w.n * ((nrhs + 63) // 64)
+    tms = blk["mixed"]["translate_ms"]
+    blk["roofline"] = {"kernel": "k_translate_tc", "bound": "tensor", "achieved": flop / (tms / 1e3) / 1e12,
+                       "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "frac": flop / (tms / 1e3) / 1e12 / BF16_PEAK_TFLOPS,
+                       "issued_tensor_tflops": issued / (tms / 1e3) / 1e12,
+                       "issued_frac": issued / (tms / 1e3) / 1e12 / BF16_PEAK_TFLOPS,
+                       "peak_note": f"{PEAK_SOURCE} cuBLAS BF16 burst"}
+    if not args.no_solve:
+        for tol, key in ((1e-8, "mixed_solve"), (1e-10, "mixed_solve_tol1e-10")):
+            if tol < 1e-8 and not args.full:
+                continue
+            t0 = time.perf_counter()
+            _, info = ctx.solve(w.sources, tol=tol, maxiter=1000)
+            blk[key] = {"tol": tol, "s": time.perf_counter() - t0, "iters": info["iters"],
+                        "refinements": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"]}
     ctx.close()
     out["block_rhs"] = blk
     # design sweep over 128 layouts
@@ -400,12 +441,12 @@ def run_batched(args, dev, flush):
                     "launch": "one CUDA graph (128 branches)"},
           "fp64": {"ms_per_sweep_apply": ms_d, "layout_applies_per_s": len(lay) * 1e3 / ms_d}}
     sw["speedup_mixed_vs_fp64"] = ms_d / ms_m
-    if args.full:
+    if not args.no_solve:
         t0 = time.perf_counter()
-        _, info = b.solve(ws.sources, tol=1e-10, maxiter=1000)
-        sw["mixed_solve_s"] = time.perf_counter() - t0
-        sw["mixed_solve_iters_max"] = info["iters"]
-        sw["mixed_solve_rel_res_fp64_max"] = info["rel_res_fp64"]
+        _, info = b.solve(ws.sources, tol=1e-8, maxiter=1000)
+        sw["mixed_solve"] = {"tol": 1e-8, "s": time.perf_counter() - t0, "iters_max": info["iters"],
+                             "refinements_max": info["outer_iters"],
+                             "rel_res_fp64_max": info["rel_res_fp64"]}
     b.close()
     out["sweep"] = sw
     return out

@@ -197,6 +197,16 @@ int lsms_num_layouts(const lsms_ctx* ctx);
  *   this implementation. */
 int lsms_autotune(lsms_ctx* ctx, double* split_mult);
 
+/* lsms_set_tc_translation — mixed-precision translations of at least min_rhs right-hand sides at
+ *   once (a block of sources, Sec. 3.2 Lemma 3.1 applied to every column) run on the tensor cores:
+ *   per disc pair the (P x P) Toeplitz block times the (P x R) coefficient block as split-BF16
+ *   tcgen05 MMAs accumulated in FP32 in tensor memory, drained into the FP64 result every `flush`
+ *   source discs (fewer discs per FP32 accumulation: closer to the FP32 CUDA-core path's accuracy,
+ *   more drains).  min_rhs = 0: never (the default is 48); flush = 0 keeps the current value (the
+ *   default is 32).  Orders p < 6 always use the CUDA-core path.  Applies to the layouts of a batch
+ *   too.  LSMS_ERR_ARG for negative arguments.  No counterpart in the paper. */
+int lsms_set_tc_translation(lsms_ctx* ctx, int min_rhs, int flush);
+
 /* lsms_set_timing — enable (1) or disable (0) CUDA-event timing of the operator's parts.  While
  *   enabled, every operator application records events on its stream around the translation
  *   (Lemma 3.1) and around the reflected coupling (Thm 5.2 -> Eq. "sommerfeldsys" -> Lemma 5.1).

@@ -26,6 +26,7 @@
 
 #include "lsms_internal.h"
 #include "lsms_ops.h"
+#include "tc_ptx.cuh"
 
 namespace {
 
@@ -35,82 +36,9 @@ constexpr int B_TILE = BN * BK * 2;                         // bytes of one B pl
 constexpr int STAGE_BYTES = NPL * (A_TILE + B_TILE);        // 73728
 constexpr int GEMM_SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint32_t TMEM_COLS = 64;
-constexpr long long WAIT_CYCLES = 4000000000LL;   // about 2 s at the maximum SM clock
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
-      " selp.b32 %0, 1, 0, P1;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > WAIT_CYCLES) return false;
-  return true;
-}
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
-                                            int c0, int c1, int c2) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
-      : "memory");
-}
-// Shared-memory matrix descriptor: K-major tile of 128-byte rows, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (the layout TMA writes with CU_TENSOR_MAP_SWIZZLE_128B).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;              // leading byte offset (not used by swizzled K-major): 16 B
-  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset: 8 rows x 128 B
-  d |= (uint64_t)1 << 46;              // descriptor version
-  d |= (uint64_t)2 << 61;              // 128-byte swizzle
-  return d;
-}
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N = 64, M = 128.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(IDESC), "r"(acc));
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-        "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
+// Instruction descriptor: M = 128, N = 64.
+constexpr uint32_t IDESC = idesc_bf16(BM, BN);
 
 // Plane products: (A plane, B plane) pairs of hi (0), mid (1), lo (2).
 __constant__ int kPairA[6] = {0, 0, 1, 0, 2, 1};
@@ -142,10 +70,7 @@ k_gemm_bf16x6(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CU
   }
   __syncwarp();
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
   }
   tc_fence_before();
   __syncthreads();
@@ -187,7 +112,7 @@ k_gemm_bf16x6(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CU
         const uint32_t b = st + NPL * A_TILE + kPairB[q] * B_TILE;
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk)
-          mma_bf16(tmem, sw128_desc(a + kk * 32), sw128_desc(b + kk * 32), (i | q | kk) != 0);
+          mma_bf16(tmem, sw128_desc(a + kk * 32), sw128_desc(b + kk * 32), IDESC, (i | q | kk) != 0);
       }
       mma_commit(empty0 + 8 * s);
     }
@@ -220,19 +145,10 @@ k_gemm_bf16x6(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CU
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
-                 : "memory");
+    tmem_dealloc(tmem, TMEM_COLS);
   }
 }
 
-// x = hi + mid + lo, each the BF16 rounding of what is left.
-__device__ __forceinline__ void split3(double x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
-  h = __double2bfloat16(x);
-  const double r1 = x - (double)__bfloat162float(h);
-  m = __double2bfloat16(r1);
-  const double r2 = r1 - (double)__bfloat162float(m);
-  l = __double2bfloat16(r2);
-}
 
 // A planes from a complex row-major matrix src[rows][K]: plane[pl][row][2k + e] = part e of
 // src[row][k]; row pitch kpad (zero padding beyond 2K is left untouched).
@@ -505,6 +421,11 @@ static void launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int
   split = (kb + kchunk - 1) / kchunk;
   dim3 grid(mt, nt, split);
   k_gemm_bf16x6<<<grid, 128, GEMM_SMEM, st>>>(ta, tb, M, ncols, kb, kchunk, C, ncols_pad, err);
+}
+
+int* tc_err_flag(lsms_ctx* c) {
+  TcState* t = (TcState*)c->tc;
+  return t ? t->d_err : nullptr;
 }
 
 int mixed_check(lsms_ctx* c) {

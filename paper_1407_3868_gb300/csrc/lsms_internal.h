@@ -88,6 +88,10 @@ struct lsms_ctx {
   size_t gm_ring_bytes = 0;
   int use_graphs = 1;               // capture each GMRES step as a CUDA graph
   double split_mult = 1.0;          // source splits of the FP32 translation (autotuned)
+  int tc_min_rhs = 48;              // mixed translations of >= this many right-hand sides (p >= 6)
+                                    // run on the tensor cores; 0 = never
+  int tc_flush = 32;                // source discs summed per FP32 tensor-memory accumulation
+  DevBuf ws_tcb;                    // BF16 coefficient images of the tensor-core translation
 
   // a batch of independent layouts (lsms_set_layouts): one child context per layout
   std::vector<lsms_ctx*> kids;

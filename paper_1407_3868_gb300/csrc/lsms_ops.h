@@ -22,9 +22,14 @@ int incident_device(lsms_ctx* c, int nsrc, const double* d_src, double2* out, cu
 int tc_setup(lsms_ctx* c);            // BF16 planes of the layout's tables (after set_particles)
 void tc_free(lsms_ctx* c);
 int mixed_check(lsms_ctx* c);         // reads and clears the device error flag of the TC kernels
+int* tc_err_flag(lsms_ctx* c);        // that flag (device), or null before tc_setup
 int build_lowp_tables(lsms_ctx* c);
 // alpha = T xs in FP32 arithmetic (sums of the per-split FP32 partials accumulated in FP64)
 int translate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st);
+// the same for blocks of right-hand sides on the tensor cores, near pairs excluded (translate_tc.cu)
+int translate_mixed_tc(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st);
+// alpha += near-pair terms of T xs32 (FP64-accurate sequences, FP32 coefficients)
+void launch_translate_near(lsms_ctx* c, int nrhs, const float2* xs32, double2* alpha, cudaStream_t st);
 int aggregate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* G, cudaStream_t st);
 int disaggregate_mixed(lsms_ctx* c, int nrhs, const double2* V, double2* alpha, cudaStream_t st);
 int reflection_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st);

@@ -25,7 +25,7 @@ EXPORTS = ["lsms_create", "lsms_set_particles", "lsms_apply", "lsms_apply_ex", "
            "lsms_solve", "lsms_eval_field", "lsms_last_error", "lsms_destroy",
            "lsms_build_contour", "lsms_scattering_diagonal", "lsms_check_geometry",
            "lsms_set_timing", "lsms_last_timing", "lsms_translate_mixed_noalloc",
-           "lsms_set_layouts", "lsms_num_layouts", "lsms_autotune"]
+           "lsms_set_layouts", "lsms_num_layouts", "lsms_autotune", "lsms_set_tc_translation"]
 
 
 class LsmsError(RuntimeError):
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsms_set_layouts": (i, [_P, i, ctypes.POINTER(ctypes.c_int), _D]),
         "lsms_num_layouts": (i, [_P]),
         "lsms_autotune": (i, [_P, _D]),
+        "lsms_set_tc_translation": (i, [_P, i, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -172,6 +173,11 @@ class Context:
         m = ctypes.c_double()
         self._check(self.lib.lsms_autotune(self.h, ctypes.byref(m)))
         return m.value
+
+    def set_tc_translation(self, min_rhs: int, flush: int = 0):
+        """Blocks of at least min_rhs right-hand sides: mixed translation on the tensor cores (0 = never);
+        flush: source discs per FP32 accumulation before draining into FP64 (0 = keep)."""
+        self._check(self.lib.lsms_set_tc_translation(self.h, int(min_rhs), int(flush)))
 
     def contour(self):
         lam = np.zeros(self.ns, dtype=np.complex128)
