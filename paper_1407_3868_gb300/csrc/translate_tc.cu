@@ -8,23 +8,26 @@
 //
 //   D (128 rows: 2 targets x 64, 64 columns: right-hand sides) += A (128 x 64) . B (64 x 64)^T
 //
-// A is the real embedding of two targets' Toeplitz blocks for one source disc: row nu holds
-// Re alpha_nu, row P + nu holds Im alpha_nu; column n multiplies Re beta_n, column P + n Im beta_n;
-// the entries are (Tr, -Ti) and (Ti, Tr).  B holds the source's coefficients for 64 right-hand
+// A is the real embedding of two targets' Toeplitz blocks for one source disc: a row per Re alpha_nu
+// and per Im alpha_nu (64 rows per target, in the order of the operand stage below); column n
+// multiplies Re beta_n, column P + n Im beta_n; the entries are (Tr, -Ti) and (Ti, Tr).  B holds the source's coefficients for 64 right-hand
 // sides in the same K order.  Both are split into three BF16 planes x = hi + mid + lo and the six
-// plane products with terms down to 2^-16 relative are accumulated, so the contraction is as
-// accurate as FP32 (as in the contour contractions).  The Hankel sequences are the FP32 ones of the
-// CUDA-core path; near pairs (k2 rho < 25) and the self pair are left to k_translate_near.
+// plane products with terms down to 2^-16 relative are accumulated.  The Hankel sequences are the
+// FP32 ones of the CUDA-core path; near pairs (k2 rho < 25) and the self pair are left to
+// k_translate_near.
 //
-// A persistent CTA (one per SM) owns a contiguous range of steps (right-hand-side block, group of 16
-// target discs, source disc) and keeps the 8 accumulators of its current group in the 512 columns of
-// tensor memory.  Per step: warp 0 lane 0 copies the source's B planes (24 KB, prepared once per
-// application in the swizzled shared-memory image) with a bulk copy into a 2-stage ring; warps 2-5
-// generate the chunk's pair sequences and write the eight A tiles (48 KB each) into a 2-stage ring;
-// warp 1 lane 0 issues 24 tcgen05.mma per tile.  When the group changes, warps 2-5 read the
-// accumulators (tcgen05.ld) and add them into the FP64 output with atomics.  Every mbarrier wait is
-// bounded; on a timeout the CTA records an error, waits for its copies in flight, frees its tensor
-// memory and returns.
+// A persistent CTA (one per SM) owns a contiguous range of steps (right-hand-side block, group of 8
+// target discs, source disc).  Per step: warp 0 lane 0 copies the source's B planes (24 KB,
+// prepared once per application in the 128-byte-swizzled shared-memory image) with a bulk copy into
+// a 3-stage ring; warps 2-5 generate the pair sequences of a chunk of 8 sources once, split them into
+// BF16 planes (two copies shifted by one element, so that every Toeplitz row is a run of aligned
+// 32-bit pairs), and write the four A tiles of the step straight into tensor memory (tcgen05.st,
+// each thread one row, 2-stage ring); warp 1 lane 0 issues 24 tcgen05.mma per tile with A from
+// tensor memory and B from shared memory into 4 accumulators (256 columns).  Every `flush` source
+// discs, warps 2-5 read the accumulators (tcgen05.ld) and add them into the FP64 output with
+// atomics: the tensor cores sum in FP32 with less than round-to-nearest accuracy, so the error grows
+// with the number of MMAs summed in one accumulator.  Every mbarrier wait is bounded; on a timeout
+// the CTA records an error, waits for its copies in flight, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -37,21 +40,29 @@
 
 namespace {
 
-constexpr int TG = 16;                  // target discs per group
+constexpr int TG = 8;                   // target discs per group
 constexpr int NTILE = TG / 2;           // accumulator tiles per group (two targets each)
 constexpr int RBLK = 64;                // right-hand sides per block (MMA N)
-constexpr int A_PLANE = 128 * 128;      // bytes: 128 rows x 64 BF16
-constexpr int A_STAGE = 3 * A_PLANE;    // 49152
 constexpr int B_PLANE = RBLK * 128;     // bytes: 64 rows x 64 BF16
 constexpr int B_STAGE = 3 * B_PLANE;    // 24576
-constexpr int NA = 2, NBS = 2;          // ring depths
-constexpr int CHS = 4;                  // source discs per sequence chunk
-constexpr int SEQ = 64;                 // float2 slots per pair sequence (>= 4p + 1)
+constexpr int NA = 2, NBS = 2;          // ring depths (A in tensor memory, B in shared memory)
+constexpr int CHS = 8;                  // source discs per sequence chunk
+constexpr int SEQ = 64;                 // elements per pair sequence (>= 4p + 2)
 constexpr int NTHR = 192;               // warp 0: copies, warp 1: MMA, warps 2-5: operands, epilogue
-constexpr int SEQ_BYTES = CHS * TG * SEQ * 8;
+// split sequence of one pair: 12 arrays [plane 3][Re, Im][parity 2] of SEQ BF16 (40 words each: the
+// Re and Im arrays of a plane and parity start 16 banks apart); parity 1 is shifted by one element so that a
+// window starting at any index is read as aligned 32-bit pairs.  Pair strides are odd in words (no
+// bank conflicts between the generating threads).
+constexpr int AW = SEQ / 2 + 8;                                  // words per array (Re/Im 80 apart)
+constexpr int PW = 12 * AW + 1;                                  // words per pair (481, odd)
+constexpr int RAWS = SEQ + 1;                                    // float2 per raw pair sequence
+constexpr int SPLIT_BYTES = CHS * TG * PW * 4;                   // 123136
+constexpr int RAW_BYTES = CHS * TG * RAWS * 8;                   // 33280
 constexpr int BAR_BYTES = 256;
-constexpr size_t TC_SMEM = 1024 + (size_t)NA * A_STAGE + (size_t)NBS * B_STAGE + SEQ_BYTES + BAR_BYTES;
+constexpr size_t TC_SMEM = 1024 + (size_t)NBS * B_STAGE + SPLIT_BYTES + RAW_BYTES + BAR_BYTES;
 constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t ACC_COLS = NTILE * RBLK;                       // 256
+constexpr uint32_t A_COLS = 3 * 32;                               // one A tile: 3 planes x 32 columns
 constexpr uint32_t IDESC_T = idesc_bf16(128, RBLK);
 // plane products (A plane, B plane): hi.hi, hi.mid, mid.hi, hi.lo, lo.hi, mid.mid
 __host__ __device__ constexpr int plane_a(int q) { return q == 2 || q == 5 ? 1 : (q == 4 ? 2 : 0); }
@@ -99,14 +110,12 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
                float near_lo, const unsigned char* __restrict__ bimg, int nrhs, long long nsteps,
                int flush, double2* __restrict__ alpha, int* __restrict__ err) {
   constexpr int p = PT, P = 2 * PT + 1;
-  constexpr int K2 = 2 * P;                        // real K in use (<= 62)
-  constexpr int NCH = (K2 + 7) / 8;                // 16-byte chunks written per A row
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = smem;
-  unsigned char* sB = sA + NA * A_STAGE;
-  float2* seq = (float2*)(sB + NBS * B_STAGE);
-  uint64_t* bars = (uint64_t*)((unsigned char*)seq + SEQ_BYTES);
+  unsigned char* sB = smem;
+  uint32_t* split = (uint32_t*)(sB + NBS * B_STAGE);
+  float2* raw = (float2*)((unsigned char*)split + SPLIT_BYTES);
+  uint64_t* bars = (uint64_t*)((unsigned char*)raw + RAW_BYTES);
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * NA + 2 * NBS + 3);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   volatile int* bcast = abort_flag + 1;
@@ -123,9 +132,6 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
   const long long s0 = nsteps * blockIdx.x / gridDim.x;
   const long long s1 = nsteps * (blockIdx.x + 1) / gridDim.x;
 
-  // A ring zeroed once: rows and columns past 2P are never written and stay zero
-  for (int i = threadIdx.x; i < NA * A_STAGE / 16; i += NTHR) ((uint4*)sA)[i] = make_uint4(0u, 0u, 0u, 0u);
-  fence_proxy_async_smem();                       // the zeros are read by the tensor cores
   if (threadIdx.x == 0) {
     for (int s = 0; s < NA; ++s) {
       mbar_init(a_full + 8 * s, 1);
@@ -170,7 +176,7 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
     for (int bs = 0; bs < NBS; ++bs)
       if (i > bs) mbar_wait(b_full + 8 * bs, (uint32_t)(((i - 1 - bs) / NBS) & 1));
   } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer ----
+    // ---- MMA issuer: A from tensor memory, B from shared memory ----
     long long i = 0, t = 0, key_prev = -1;
     int grp = 0;
     bool first = true, ok = true;
@@ -205,13 +211,13 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
           break;
         }
         tc_fence_after();
-        const uint32_t a0 = smem_u32(sA + as * A_STAGE);
+        const uint32_t a0 = tmem + ACC_COLS + as * A_COLS;
 #pragma unroll
         for (int q = 0; q < 6; ++q)
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
-            mma_bf16(tmem + tt * RBLK, sw128_desc(a0 + plane_a(q) * A_PLANE + kk * 32),
-                     sw128_desc(b0 + plane_b(q) * B_PLANE + kk * 32), IDESC_T, (!first || q || kk) ? 1u : 0u);
+            mma_bf16_ta(tmem + tt * RBLK, a0 + plane_a(q) * 32 + kk * 8,
+                        sw128_desc(b0 + plane_b(q) * B_PLANE + kk * 32), IDESC_T, (!first || q || kk) ? 1u : 0u);
         mma_commit(a_empty + 8 * as);
       }
       if (!ok) break;
@@ -227,8 +233,22 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
     mma_commit(done);
     mbar_wait(done, 0);
   } else if (warp >= 2) {
-    // ---- operands (pair sequences, A tiles) and epilogue: 128 threads, named barrier 1 ----
+    // ---- operands and epilogue: 128 threads, named barrier 1.  Thread (warp, lane) owns row
+    // 32 (warp mod 4) + lane of every A tile and accumulator (its tensor-memory lane quarter).
+    // Row order inside a target's 64 rows: lane quarter e = q4 mod 2 holds the orders nu of parity
+    // e, Re alpha_nu on lanes 0-15 (nu = 2 lane + e) and Im alpha_nu on lanes 16-31; the other lanes
+    // are zero rows.  All lanes of a warp then read one parity, the Re and Im halves 16 banks
+    // apart: the window reads are free of bank conflicts.
     const int b = threadIdx.x - 64;
+    const int q4 = warp & 3;
+    const int half = q4 >> 1;                     // which of the tile's two targets
+    const int e = q4 & 1;
+    const bool im = lane >= 16;
+    const int nu = 2 * (lane & 15) + e;
+    const bool valid = nu < P;
+    const int w0 = 2 * p - nu;                    // window start: h_{n - nu} = h[w0 + n]
+    const int par = e;                            // = w0 mod 2
+    const uint32_t lane_addr = (uint32_t)(32 * q4) << 16;
     const ffl kf = {k_hi, k_lo}, nr = {near_hi, near_lo};
     long long t = 0, s = s0;
     int grp = 0;
@@ -237,14 +257,34 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
       const int g = (int)(gkey % ngroups);
       const int m0 = (int)(s - gkey * n);
       const int cnt = (int)min((long long)min(CHS, flush - m0 % flush), min(s1 - s, (long long)(n - m0)));
+      // the chunk's pair sequences, FP32, then split into BF16 planes with both parities
       if (b < TG * cnt) {
         const int i = b % TG, j = b / TG;
         const int l = g * TG + i, m = m0 + j;
-        float2* h = seq + (j * TG + i) * SEQ;
+        float2* h = raw + b * RAWS;
         if (l < n && l != m) {
           hankel_sequence_f32(cff[l], cff[m], kf, p, nr, h);
         } else {
           for (int q = 0; q <= 4 * p; ++q) h[q] = make_float2(0.f, 0.f);
+        }
+        // word k of (plane pl, part c): parity 0 holds elements (2k, 2k + 1), parity 1 (2k - 1, 2k)
+        uint32_t* sp = split + b * PW;
+        uint32_t prev[3][2] = {{0u, 0u}, {0u, 0u}, {0u, 0u}};
+        for (int k = 0; k < SEQ / 2; ++k) {
+          const float2 e0 = 2 * k <= 4 * p ? h[2 * k] : make_float2(0.f, 0.f);
+          const float2 e1 = 2 * k + 1 <= 4 * p ? h[2 * k + 1] : make_float2(0.f, 0.f);
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            unsigned short u0[3], u1[3];
+            split3f(c ? e0.y : e0.x, u0);
+            split3f(c ? e1.y : e1.x, u1);
+#pragma unroll
+            for (int pl = 0; pl < 3; ++pl) {
+              sp[((pl * 2 + c) * 2 + 0) * AW + k] = (uint32_t)u0[pl] | ((uint32_t)u1[pl] << 16);
+              sp[((pl * 2 + c) * 2 + 1) * AW + k] = prev[pl][c] | ((uint32_t)u0[pl] << 16);
+              prev[pl][c] = u1[pl];
+            }
+          }
         }
       }
       named_bar_sync(1, 128);
@@ -266,35 +306,36 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
             ok = false;
             break;
           }
-          const int i = 2 * tt + (b >> 6), rl = b & 63;
-          if (rl < K2) {
-            const bool im = rl >= P;
-            const int nu = im ? rl - P : rl;
-            const float2* hs = seq + (j * TG + i) * SEQ + 2 * p - nu;   // hs[n] = h_{n - nu}
-            float2 wv[P];
+          tc_fence_after();
+          // row of the real embedding: K words (2 elements each); first half from A1 (Re for a
+          // Re row, Im for an Im row), second half from A2 (-Im, resp. Re), zero from K = 2P
+          const int i = 2 * tt + half;
+          const uint32_t* base = split + (j * TG + i) * PW;
+          const uint32_t taddr = tmem + lane_addr + ACC_COLS + as * A_COLS;
 #pragma unroll
-            for (int q = 0; q < P; ++q) wv[q] = hs[q];
-            unsigned char* row = sA + as * A_STAGE + b * 128;
+          for (int pl = 0; pl < 3; ++pl) {
+            uint32_t v[32];
+            if (valid) {
+              const uint32_t* a1 = base + ((pl * 2 + (im ? 1 : 0)) * 2 + par) * AW + (w0 + par) / 2;
+              const uint32_t* a2e = base + ((pl * 2 + (im ? 0 : 1)) * 2 + par) * AW + (w0 + par) / 2;
+              const uint32_t* a2o = base + ((pl * 2 + (im ? 0 : 1)) * 2 + (par ^ 1)) * AW + (w0 + 1 + (par ^ 1)) / 2;
+              const uint32_t neg = im ? 0u : 0x80008000u;
 #pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-              float v[8];
+              for (int jw = 0; jw < p; ++jw) v[jw] = a1[jw];
+              v[p] = (a1[p] & 0xFFFFu) | (((a2e[0] ^ neg) & 0xFFFFu) << 16);
+              // words j > p hold A2[w0 + 2j - P], A2[w0 + 2j + 1 - P]: start parity is par ^ 1
 #pragma unroll
-              for (int e = 0; e < 8; ++e) {
-                const int kk = 8 * c + e;
-                float x = 0.f;
-                if (kk < P) x = im ? wv[kk].y : wv[kk].x;
-                else if (kk < K2) x = im ? wv[kk - P].x : -wv[kk - P].y;
-                v[e] = x;
-              }
-              uint4 hi, mid, lo;
-              split3x8(v, hi, mid, lo);
-              const int pos = (c ^ (b & 7)) * 16;
-              *(uint4*)(row + pos) = hi;
-              *(uint4*)(row + A_PLANE + pos) = mid;
-              *(uint4*)(row + 2 * A_PLANE + pos) = lo;
+              for (int jw = p + 1; jw < P; ++jw) v[jw] = a2o[jw - p - 1] ^ neg;
+#pragma unroll
+              for (int jw = P; jw < 32; ++jw) v[jw] = 0u;
+            } else {
+#pragma unroll
+              for (int jw = 0; jw < 32; ++jw) v[jw] = 0u;
             }
+            tmem_st32(taddr + pl * 32, v);
           }
-          fence_proxy_async_smem();
+          tmem_wait_st();
+          tc_fence_before();
           named_bar_sync(1, 128);
           if (b == 0) mbar_arrive(a_full + 8 * as);
         }
@@ -302,7 +343,7 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
       if (!ok) break;
       s += cnt;
       if (s == s1 || segkey(s) != key) {
-        // group done: read the accumulators and add them into alpha
+        // segment done: read the accumulators and add them into alpha
         if (b == 0) {
           bool w = !*abort_flag && mbar_wait(acc_full, (uint32_t)(grp & 1));
           if (!w && !*abort_flag) {
@@ -314,20 +355,16 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
         named_bar_sync(1, 128);
         if (!*bcast) break;
         tc_fence_after();
-        const int q4 = warp & 3;                   // tensor-memory lane quarter of this warp
-        const int row = 32 * q4 + lane;
         const int rb = (int)(gkey / ngroups);
-        const int rl = row & 63;
-        const int nu = rl < P ? rl : rl - P;
 #pragma unroll 1
         for (int tt = 0; tt < NTILE; ++tt) {
-          const int l = g * TG + 2 * tt + (row >> 6);
-          const bool use = l < n && rl < K2;
-          double* o = (double*)(alpha + (size_t)l * P + nu) + (rl < P ? 0 : 1);
+          const int l = g * TG + 2 * tt + half;
+          const bool use = l < n && valid;
+          double* o = (double*)(alpha + (size_t)l * P + (valid ? nu : 0)) + (im ? 1 : 0);
 #pragma unroll 1
           for (int cb = 0; cb < RBLK; cb += 16) {
             uint32_t v[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + tt * RBLK + cb, v);
+            tmem_ld16(tmem + lane_addr + tt * RBLK + cb, v);
             if (use) {
 #pragma unroll
               for (int e = 0; e < 16; ++e) {
