@@ -52,6 +52,21 @@ TRAFFIC = {}
 KERNEL_SOURCES = ("mixed.cu", "ff_hankel.cuh")
 
 
+def max_over_ranks(vals, world, device):
+    """Element-wise maximum of per-rank timings: the slowest replica sets the job's time."""
+    import torch
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: every rank processed units_per_rank in at most ms milliseconds."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def src_hash(paths) -> str:
     h = hashlib.sha256()
     for path in paths:
@@ -190,7 +205,11 @@ def run_ours(args, rank, world, local_rank):
     n, P = w.n, 2 * w.p + 1
     centres = w.centres()
     ctx = lsms.context_for(w, lsms.LSMS_MIXED)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter()
     ctx.set_particles(centres)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
     ctx.set_timing(True)
     b = torch.from_numpy(inputs.random_coefficients(n, w.p, 1, 100 + rank)).to(dev)
     y = torch.empty_like(b)
@@ -233,13 +252,9 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(1):
         ctx.apply_dev(b, y, flags_fp64, stream)
     ms_fp64, t_tr_fp64, _ = timed(flags_fp64, k64)
-    # max over ranks
-    tot = torch.tensor([ms_mixed, ms_fp64], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-    ms_mixed, ms_fp64 = float(tot[0]), float(tot[1])
-    value = world * args.steps / (ms_mixed / 1e3)
-    fp64_rate = world * k64 / (ms_fp64 / 1e3)
+    ms_mixed, ms_fp64 = max_over_ranks([ms_mixed, ms_fp64], world, dev)
+    value = job_rate(args.steps, world, ms_mixed)
+    fp64_rate = job_rate(k64, world, ms_fp64)
 
     # end to end through the host-pointer ABI: pinned host input, host output, copies inside
     xh = torch.from_numpy(inputs.random_coefficients(n, w.p, 1, 200 + rank)).pin_memory()
@@ -257,10 +272,7 @@ def run_ours(args, rank, world, local_rank):
         assert rc == 0, rc
         _ = float(yn.real[0, 0, 0])
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e = world * args.steps / float(te[0])
+    e2e = job_rate(args.steps, world, 1e3 * max_over_ranks([e2e_s], world, dev)[0])
 
     # roofline of the dominant kernel (the FP32 translation)
     pairs = n * (n - 1)
@@ -275,15 +287,24 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_solve:
         # the mixed solve refines to 1e-8 (the refinement target of the mixed 5000-disc case) and,
         # for comparison, to 1e-10 (the FP64 solve's tolerance); fields are compared at the targets
-        solve = {"mixed_tol": 1e-8, "fp64_tol": 1e-10}
+        solve = {"mixed_tol": 1e-8, "fp64_tol": 1e-10, "set_particles_s": t_setup,
+                 "timing": "wall clock around lsms_solve (create and set_particles excluded); mixed "
+                           "at 1e-8: median of 3 after one warm-up solve"}
         u_m = {}
-        for tol, key in ((1e-8, "mixed"), (1e-10, "mixed_tol1e-10")):
+        for tol, key, reps in ((1e-8, "mixed", 3), (1e-10, "mixed_tol1e-10", 1)):
             ctxm = lsms.context_for(w, lsms.LSMS_MIXED)
             ctxm.set_particles(centres)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            _, info_m = ctxm.solve(w.sources, tol=tol, maxiter=2000)
-            solve[key + "_s"] = time.perf_counter() - t0
+            if reps > 1:
+                ctxm.solve(w.sources, tol=tol, maxiter=2000)
+            times = []
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, info_m = ctxm.solve(w.sources, tol=tol, maxiter=2000)
+                times.append(time.perf_counter() - t0)
+            solve[key + "_s"] = statistics.median(times)
+            if reps > 1:
+                solve[key + "_s_all"] = times
             u_m[key] = ctxm.eval_field(w.targets, 0, lsms.FIELD_SCATTERED)
             solve[key + "_iters"] = info_m["iters"]
             solve[key + "_refinements"] = info_m["outer_iters"]
