@@ -46,14 +46,17 @@ struct GmState {
   int reorth;     // 1: the current Arnoldi step needs a second Gram-Schmidt pass
 };
 
-constexpr int DOT_T = 1024;    // elements per CTA
-constexpr int DOT_V = 32;      // vectors per CTA (4 per warp)
+constexpr int DOT_T = 2048;    // elements per CTA (8 per thread)
+constexpr int DOT_V = 8;       // vectors per CTA, accumulated side by side
+constexpr int DOT_E = DOT_T / 256;
 constexpr int GIVENS_MAX = 4096;
 
 // System b = blockIdx.z:  out[b][i] += sum_t conj(V[i][b][t]) w[b][t] for i < nv, and, with
 // self_norm, out[b][nv] += ||w_b||^2 (out pre-zeroed).  nv = nv0 (+ *kp when kp is given, so that a
 // captured graph follows the Arnoldi step).  V slots are ldv apart, system b sits at b L inside a
 // slot.  With a gate the kernel does nothing unless system b needs a second Gram-Schmidt pass.
+// Each thread keeps 8 elements of w in registers and reads the matching elements of 8 vectors, so
+// 64 independent loads are in flight per thread (the multi-dot is bound by HBM bandwidth).
 __global__ void __launch_bounds__(256)
 k_mdot(const double2* __restrict__ V, long long ldv, int nv0, const int* __restrict__ kp,
        int self_norm, const double2* __restrict__ w, long long L, double2* __restrict__ out,
@@ -62,36 +65,53 @@ k_mdot(const double2* __restrict__ V, long long ldv, int nv0, const int* __restr
   if (gate && !gate[b].reorth) return;
   const int nv = nv0 + (kp ? *kp : 0);
   const int ntot = nv + (self_norm ? 1 : 0);
-  if ((int)blockIdx.y * DOT_V >= ntot) return;
+  const int i0 = blockIdx.y * DOT_V;
+  if (i0 >= ntot) return;
   V += (long long)b * L;
   w += (long long)b * L;
   out += (long long)b * out_stride;
-  __shared__ double2 ws[DOT_T];
-  const long long t0 = blockIdx.x * (long long)DOT_T;
-  const int cnt = (int)min((long long)DOT_T, L - t0);
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) ws[i] = w[t0 + i];
+  const long long t0 = blockIdx.x * (long long)DOT_T + threadIdx.x;
+  double2 wr[DOT_E];
+#pragma unroll
+  for (int e = 0; e < DOT_E; ++e) {
+    const long long t = t0 + e * 256;
+    wr[e] = t < L ? w[t] : make_double2(0.0, 0.0);
+  }
+  double2 acc[DOT_V];
+#pragma unroll
+  for (int v = 0; v < DOT_V; ++v) {
+    acc[v] = make_double2(0.0, 0.0);
+    const int i = i0 + v;
+    if (i < ntot) {
+      const double2* vi = i < nv ? V + (long long)i * ldv : w;
+#pragma unroll
+      for (int e = 0; e < DOT_E; ++e) {
+        const long long t = t0 + e * 256;
+        if (t < L) {
+          const double2 c = cjmul(vi[t], wr[e]);
+          acc[v].x += c.x;
+          acc[v].y += c.y;
+        }
+      }
+    }
+  }
+  __shared__ double2 red[8][DOT_V];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int v = 0; v < DOT_V; ++v) {
+    const double2 a = warp_sum(acc[v]);
+    if (lane == 0) red[warp][v] = a;
+  }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int i1 = min(ntot, (int)(blockIdx.y + 1) * DOT_V);
-  for (int i = blockIdx.y * DOT_V + warp; i < i1; i += nw) {
-    const double2* vi = (i < nv ? V + (long long)i * ldv : w) + t0;
-    double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
-    int t = lane;
-    for (; t + 32 < cnt; t += 64) {
-      const double2 c0 = cjmul(vi[t], ws[t]);
-      const double2 c1 = cjmul(vi[t + 32], ws[t + 32]);
-      a0.x += c0.x; a0.y += c0.y;
-      a1.x += c1.x; a1.y += c1.y;
+  if (threadIdx.x < DOT_V && i0 + (int)threadIdx.x < ntot) {
+    double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      s.x += red[q][threadIdx.x].x;
+      s.y += red[q][threadIdx.x].y;
     }
-    if (t < cnt) {
-      const double2 c0 = cjmul(vi[t], ws[t]);
-      a0.x += c0.x; a0.y += c0.y;
-    }
-    const double2 acc = warp_sum(make_double2(a0.x + a1.x, a0.y + a1.y));
-    if (lane == 0) {
-      atomicAdd(&out[i].x, acc.x);
-      atomicAdd(&out[i].y, acc.y);
-    }
+    atomicAdd(&out[i0 + threadIdx.x].x, s.x);
+    atomicAdd(&out[i0 + threadIdx.x].y, s.y);
   }
 }
 
@@ -118,16 +138,22 @@ k_maxpy(const double2* __restrict__ V, long long ldv, int nv, const int* __restr
     __syncthreads();
     if (t < L) {
       int i = 0;
-      for (; i + 1 < c; i += 2) {
+      for (; i + 3 < c; i += 4) {
         const double2 v0 = V[(long long)(i0 + i) * ldv + t];
         const double2 v1 = V[(long long)(i0 + i + 1) * ldv + t];
-        const double2 h0 = hs[i], h1 = hs[i + 1];
+        const double2 v2 = V[(long long)(i0 + i + 2) * ldv + t];
+        const double2 v3 = V[(long long)(i0 + i + 3) * ldv + t];
+        const double2 h0 = hs[i], h1 = hs[i + 1], h2 = hs[i + 2], h3 = hs[i + 3];
         a0.x = fma(v0.x, h0.x, fma(-v0.y, h0.y, a0.x));
         a0.y = fma(v0.x, h0.y, fma(v0.y, h0.x, a0.y));
         a1.x = fma(v1.x, h1.x, fma(-v1.y, h1.y, a1.x));
         a1.y = fma(v1.x, h1.y, fma(v1.y, h1.x, a1.y));
+        a0.x = fma(v2.x, h2.x, fma(-v2.y, h2.y, a0.x));
+        a0.y = fma(v2.x, h2.y, fma(v2.y, h2.x, a0.y));
+        a1.x = fma(v3.x, h3.x, fma(-v3.y, h3.y, a1.x));
+        a1.y = fma(v3.x, h3.y, fma(v3.y, h3.x, a1.y));
       }
-      if (i < c) {
+      for (; i < c; ++i) {
         const double2 v0 = V[(long long)(i0 + i) * ldv + t];
         const double2 h0 = hs[i];
         a0.x = fma(v0.x, h0.x, fma(-v0.y, h0.y, a0.x));
