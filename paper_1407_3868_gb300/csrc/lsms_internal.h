@@ -80,7 +80,7 @@ struct lsms_ctx {
 
   // workspaces
   DevBuf ws_x, ws_y, ws_xs, ws_alpha, ws_g, ws_v, ws_pq, ws_sig, ws_aux;
-  DevBuf gm_v, gm_h, gm_small, gm_x, gm_r, gm_w;
+  DevBuf gm_v, gm_h, gm_small, gm_x, gm_r, gm_w, gm_b, gm_mask, gm_off;
   double* h_pinned = nullptr;       // small pinned host scratch for residual polling
   cudaEvent_t gm_ev[8] = {};        // events of the GMRES residual ring
   void* gm_ring = nullptr;          // host-mapped ring of per-system GMRES states

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <string>
+#include <vector>
 
 #include "lsms_internal.h"
 
@@ -42,6 +43,23 @@ int batch_solve(lsms_ctx* c, int nsrc, const double* src_xy, double tol, int max
                 double* beta_out, lsms_solve_info* info);
 int batch_eval_field(lsms_ctx* c, int layout, int ntgt, const double* tgt, int which, double* out);
 int batch_mixed_check(lsms_ctx* c);
+
+// The systems one GMRES run iterates in lockstep (gmres.cu): nb vectors packed in one slot of
+// length `slot`, system b at elements off[b] .. off[b + 1] (device copy d_off).  The operator is
+// applied to a whole slot with apply_nrhs right-hand sides: nb for the sources of one layout (equal
+// lengths), 1 for the layouts of a batch (the batch operator covers every layout at once).
+struct GmSys {
+  int nb = 0;
+  long long slot = 0, maxlen = 0;
+  const long long* d_off = nullptr;
+  int apply_nrhs = 0;
+};
+// Solve the scaled systems of s (rhs = D S a_inc; xs scaled unknowns, initial guesses if nonzero):
+// FP64 GMRES, or FP64 refinement around mixed inner GMRES for a mixed context.  Per system: it
+// iterations, rest residual estimate, rel64 FP64 relative residual; outer refinement steps.
+int solve_systems(lsms_ctx* c, const GmSys& s, const double2* rhs, double2* xs, bool nonzero, double tol,
+                  int maxiter, std::vector<int>& it, std::vector<double>& rest, std::vector<double>& rel64,
+                  int* outer_out, double* hist, int hcap, int* nh, cudaStream_t st);
 
 // small device helpers (gmres.cu)
 void launch_diag_mul(const double2* x, const double2* s, double2* y, long long total, int P,
