@@ -107,7 +107,9 @@ int apply_device(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags,
   ++launches;
   if (c->timing) cudaEventRecord(c->ev[0], st);
   if (!(flags & LSMS_APPLY_NO_TRANSLATION)) {
-    launches += mixed ? 2 : 1;
+    // FP64: one kernel; mixed: FP32 copy of xs, the translation (+ the partial-sum reduction, or
+    // the packing of the tensor-core operands) and the near pairs
+    launches += mixed ? 3 + (c->near_nnz > 0 ? 1 : 0) : 1;
     if (mixed) {
       if ((rc = translate_mixed(c, nrhs, xs, alpha, st))) return rc;
     } else {
@@ -123,7 +125,7 @@ int apply_device(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags,
     } else {
       if ((rc = reflection_f64(c, nrhs, xs, alpha, st))) return rc;
     }
-    launches += 3;
+    launches += mixed ? 5 : 3;   // split, GEMM, per-node stage, GEMM, add / GEMM, stage, GEMM
   }
   if (c->timing) cudaEventRecord(c->ev[2], st);
   launch_combine(x, alpha, c->d_scale_out + mode * P, y, nrhs, n, P,

@@ -36,6 +36,26 @@ __device__ __forceinline__ double2 warp_sum(double2 v) {
   return v;
 }
 
+// Krylov basis arithmetic: FP64 (double2 basis) for FP64 solves; FP32 storage and FP32 products
+// (float2 basis) for the inner solves of the mixed refinement, whose tolerances are >= 1e-5.  The
+// FP64 pipe of this GPU is narrow enough that FP64 Gram-Schmidt products are arithmetic-bound near
+// 1-2 TB/s; in FP32 they are bound by the (halved) memory traffic.  Reductions across threads and
+// CTAs, the Hessenberg matrix, the rotations and the iterate stay FP64.
+template <typename T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+template <typename T> using vec2 = typename Vec2<T>::type;
+template <typename T> __device__ __forceinline__ vec2<T> mk2(double x, double y);
+template <> __device__ __forceinline__ double2 mk2<double>(double x, double y) { return make_double2(x, y); }
+template <> __device__ __forceinline__ float2 mk2<float>(double x, double y) { return make_float2((float)x, (float)y); }
+template <typename V2> __device__ __forceinline__ double2 to_d2(V2 v) { return make_double2(v.x, v.y); }
+template <typename V2> __device__ __forceinline__ V2 cjmul_t(V2 a, V2 b) {   // conj(a) b
+  V2 r;
+  r.x = a.x * b.x + a.y * b.y;
+  r.y = a.x * b.y - a.y * b.x;
+  return r;
+}
+
 struct GmState {
   double beta0;   // ||r0||
   double ref;     // ||rhs||: residuals are reported relative to it
@@ -59,10 +79,12 @@ constexpr int GIVENS_MAX = 4096;
 // gate the kernel does nothing unless system b needs a second Gram-Schmidt pass.
 // Each thread keeps 8 elements of w in registers and reads the matching elements of 8 vectors, so
 // 64 independent loads are in flight per thread (the multi-dot is bound by HBM bandwidth).
+template <typename T>
 __global__ void __launch_bounds__(256)
-k_mdot(const double2* __restrict__ V, long long ldv, int nv0, const int* __restrict__ kp,
+k_mdot(const vec2<T>* __restrict__ V, long long ldv, int nv0, const int* __restrict__ kp,
        int self_norm, const double2* __restrict__ w, const long long* __restrict__ off,
        double2* __restrict__ out, int out_stride, const GmState* __restrict__ gate) {
+  using V2 = vec2<T>;
   const int b = blockIdx.z;
   if (gate && !gate[b].reorth) return;
   const int nv = nv0 + (kp ? *kp : 0);
@@ -73,28 +95,29 @@ k_mdot(const double2* __restrict__ V, long long ldv, int nv0, const int* __restr
   w += off[b];
   out += (long long)b * out_stride;
   const long long t0 = blockIdx.x * (long long)DOT_T + threadIdx.x;
-  double2 wr[DOT_E];
+  V2 wr[DOT_E];
 #pragma unroll
   for (int e = 0; e < DOT_E; ++e) {
     const long long t = t0 + e * 256;
-    wr[e] = t < L ? w[t] : make_double2(0.0, 0.0);
+    const double2 u = t < L ? w[t] : make_double2(0.0, 0.0);
+    wr[e] = mk2<T>(u.x, u.y);
   }
   __shared__ double2 red[8][DOT_V];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // vector groups blockIdx.y, blockIdx.y + gridDim.y, ... (the grid does not grow with the basis)
   for (int i0 = blockIdx.y * DOT_V; i0 < ntot; i0 += gridDim.y * DOT_V) {
-    double2 acc[DOT_V];
+    V2 acc[DOT_V];
 #pragma unroll
     for (int v = 0; v < DOT_V; ++v) {
-      acc[v] = make_double2(0.0, 0.0);
+      acc[v] = mk2<T>(0.0, 0.0);
       const int i = i0 + v;
       if (i < nv) {
-        const double2* vi = V + (long long)i * ldv;
+        const V2* vi = V + (long long)i * ldv;
 #pragma unroll
         for (int e = 0; e < DOT_E; ++e) {
           const long long t = t0 + e * 256;
           if (t < L) {
-            const double2 c = cjmul(vi[t], wr[e]);
+            const V2 c = cjmul_t(vi[t], wr[e]);
             acc[v].x += c.x;
             acc[v].y += c.y;
           }
@@ -107,7 +130,7 @@ k_mdot(const double2* __restrict__ V, long long ldv, int nv0, const int* __restr
     __syncthreads();                               // red is reused across groups
 #pragma unroll
     for (int v = 0; v < DOT_V; ++v) {
-      const double2 a = warp_sum(acc[v]);
+      const double2 a = warp_sum(to_d2(acc[v]));
       if (lane == 0) red[warp][v] = a;
     }
     __syncthreads();
@@ -127,11 +150,13 @@ k_mdot(const double2* __restrict__ V, long long ldv, int nv0, const int* __restr
 // System b = blockIdx.y:  w[b][t] += sign sum_{i < nv_b} V[i][b][t] h[b][i] over the system's
 // elements off[b] .. off[b + 1].  nv_b = nv, or nv_arr[b] when given; with a gate only when system b
 // needs a second pass.
+template <typename T>
 __global__ void __launch_bounds__(256)
-k_maxpy(const double2* __restrict__ V, long long ldv, int nv, const int* __restrict__ nv_arr,
+k_maxpy(const vec2<T>* __restrict__ V, long long ldv, int nv, const int* __restrict__ nv_arr,
         const int* __restrict__ kp, const double2* __restrict__ h, int h_stride,
         double2* __restrict__ w, const long long* __restrict__ off, double sign,
         const GmState* __restrict__ gate) {
+  using V2 = vec2<T>;
   const int b = blockIdx.y;
   if (gate && !gate[b].reorth) return;
   const long long L = off[b + 1] - off[b];
@@ -141,22 +166,25 @@ k_maxpy(const double2* __restrict__ V, long long ldv, int nv, const int* __restr
   V += off[b];
   w += off[b];
   h += (long long)b * h_stride;
-  __shared__ double2 hs[256];
+  __shared__ V2 hs[256];
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
+  V2 a0 = mk2<T>(0.0, 0.0), a1 = mk2<T>(0.0, 0.0);
   for (int i0 = 0; i0 < nv; i0 += 256) {
     const int c = min(256, nv - i0);
     __syncthreads();
-    if (threadIdx.x < c) hs[threadIdx.x] = h[i0 + threadIdx.x];
+    if (threadIdx.x < c) {
+      const double2 u = h[i0 + threadIdx.x];
+      hs[threadIdx.x] = mk2<T>(u.x, u.y);
+    }
     __syncthreads();
     if (t < L) {
       int i = 0;
       for (; i + 3 < c; i += 4) {
-        const double2 v0 = V[(long long)(i0 + i) * ldv + t];
-        const double2 v1 = V[(long long)(i0 + i + 1) * ldv + t];
-        const double2 v2 = V[(long long)(i0 + i + 2) * ldv + t];
-        const double2 v3 = V[(long long)(i0 + i + 3) * ldv + t];
-        const double2 h0 = hs[i], h1 = hs[i + 1], h2 = hs[i + 2], h3 = hs[i + 3];
+        const V2 v0 = V[(long long)(i0 + i) * ldv + t];
+        const V2 v1 = V[(long long)(i0 + i + 1) * ldv + t];
+        const V2 v2 = V[(long long)(i0 + i + 2) * ldv + t];
+        const V2 v3 = V[(long long)(i0 + i + 3) * ldv + t];
+        const V2 h0 = hs[i], h1 = hs[i + 1], h2 = hs[i + 2], h3 = hs[i + 3];
         a0.x = fma(v0.x, h0.x, fma(-v0.y, h0.y, a0.x));
         a0.y = fma(v0.x, h0.y, fma(v0.y, h0.x, a0.y));
         a1.x = fma(v1.x, h1.x, fma(-v1.y, h1.y, a1.x));
@@ -167,16 +195,16 @@ k_maxpy(const double2* __restrict__ V, long long ldv, int nv, const int* __restr
         a1.y = fma(v3.x, h3.y, fma(v3.y, h3.x, a1.y));
       }
       for (; i < c; ++i) {
-        const double2 v0 = V[(long long)(i0 + i) * ldv + t];
-        const double2 h0 = hs[i];
+        const V2 v0 = V[(long long)(i0 + i) * ldv + t];
+        const V2 h0 = hs[i];
         a0.x = fma(v0.x, h0.x, fma(-v0.y, h0.y, a0.x));
         a0.y = fma(v0.x, h0.y, fma(v0.y, h0.x, a0.y));
       }
     }
   }
   if (t < L) {
-    w[t].x += sign * (a0.x + a1.x);
-    w[t].y += sign * (a0.y + a1.y);
+    w[t].x += sign * ((double)a0.x + (double)a1.x);
+    w[t].y += sign * ((double)a0.y + (double)a1.y);
   }
 }
 
@@ -300,7 +328,8 @@ __global__ void k_gm_backsolve(const int* __restrict__ kk, const double2* __rest
 }
 
 // System b = blockIdx.y: dst[b] = src[b] * st[b].inv
-__global__ void k_scale_by(double2* __restrict__ dst, const double2* __restrict__ src,
+template <typename T>
+__global__ void k_scale_by(vec2<T>* __restrict__ dst, const double2* __restrict__ src,
                            const GmState* __restrict__ st, const long long* __restrict__ off) {
   const int b = blockIdx.y;
   const double s = st[b].inv;
@@ -310,32 +339,34 @@ __global__ void k_scale_by(double2* __restrict__ dst, const double2* __restrict_
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L;
        t += (long long)gridDim.x * blockDim.x) {
     const double2 v = src[t];
-    dst[t] = make_double2(v.x * s, v.y * s);
+    dst[t] = mk2<T>(v.x * s, v.y * s);
   }
 }
 
 // X[b] = V[k][b] (the operator's fixed input buffer)
-__global__ void k_copy_slot(double2* __restrict__ X, const double2* __restrict__ V, long long slot,
+template <typename T>
+__global__ void k_copy_slot(double2* __restrict__ X, const vec2<T>* __restrict__ V, long long slot,
                             const int* __restrict__ kp) {
-  const double2* src = V + (long long)(*kp) * slot;
+  const vec2<T>* src = V + (long long)(*kp) * slot;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < slot;
        t += (long long)gridDim.x * blockDim.x)
-    X[t] = src[t];
+    X[t] = to_d2(src[t]);
 }
 
 // V[k + 1][b] = W[b] * st[b].inv   (system b = blockIdx.y)
-__global__ void k_scale_into_slot(double2* __restrict__ V, long long slot, const double2* __restrict__ W,
+template <typename T>
+__global__ void k_scale_into_slot(vec2<T>* __restrict__ V, long long slot, const double2* __restrict__ W,
                                   const GmState* __restrict__ st, const long long* __restrict__ off,
                                   const int* __restrict__ kp) {
   const int b = blockIdx.y;
   const double s = st[b].inv;
   const long long L = off[b + 1] - off[b];
-  double2* dst = V + (long long)(*kp + 1) * slot + off[b];
+  vec2<T>* dst = V + (long long)(*kp + 1) * slot + off[b];
   const double2* src = W + off[b];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L;
        t += (long long)gridDim.x * blockDim.x) {
     const double2 v = src[t];
-    dst[t] = make_double2(v.x * s, v.y * s);
+    dst[t] = mk2<T>(v.x * s, v.y * s);
   }
 }
 
@@ -420,24 +451,27 @@ inline int grid_for(long long total, int block) {
 }
 
 // out[b * out_stride + i] = V_b[i]^H w_b, i < nv, for the systems of s
-void mdot(const double2* V, long long ldv, int nv, const double2* w, const GmSys& s, double2* out,
+template <typename T>
+void mdot(const vec2<T>* V, long long ldv, int nv, const double2* w, const GmSys& s, double2* out,
           int out_stride, cudaStream_t st) {
   for (int b = 0; b < s.nb; ++b)
     cudaMemsetAsync(out + (long long)b * out_stride, 0, (size_t)nv * sizeof(double2), st);
   dim3 grid((unsigned)((s.maxlen + DOT_T - 1) / DOT_T), (unsigned)std::min(DOT_GY, (nv + DOT_V - 1) / DOT_V),
             (unsigned)s.nb);
-  k_mdot<<<grid, 256, 0, st>>>(V, ldv, nv, nullptr, 0, w, s.d_off, out, out_stride, nullptr);
+  k_mdot<T><<<grid, 256, 0, st>>>(V, ldv, nv, nullptr, 0, w, s.d_off, out, out_stride, nullptr);
 }
 
-void maxpy(const double2* V, long long ldv, int nv, const int* nv_arr, const double2* h, int h_stride,
+template <typename T>
+void maxpy(const vec2<T>* V, long long ldv, int nv, const int* nv_arr, const double2* h, int h_stride,
            double2* w, const GmSys& s, double sign, cudaStream_t st) {
   dim3 grid((unsigned)((s.maxlen + 255) / 256), (unsigned)s.nb);
-  k_maxpy<<<grid, 256, 0, st>>>(V, ldv, nv, nv_arr, nullptr, h, h_stride, w, s.d_off, sign, nullptr);
+  k_maxpy<T><<<grid, 256, 0, st>>>(V, ldv, nv, nv_arr, nullptr, h, h_stride, w, s.d_off, sign, nullptr);
 }
 
 // Device scratch of one batched GMRES run.
 struct GmPtrs {
-  double2 *V, *H, *h1, *h2, *g, *cs, *sn, *y, *nrm;
+  void* V;                 // basis [maxiter + 1][slot] of double2 or float2
+  double2 *H, *h1, *h2, *g, *cs, *sn, *y, *nrm;
   double2 *X, *W;          // the operator's fixed input and output buffers, [nb][L]
   GmState* st;
   int* kk;                 // iterations kept per system (back substitution)
@@ -446,19 +480,19 @@ struct GmPtrs {
   long long hstride;
 };
 
-int gm_alloc(lsms_ctx* c, const GmSys& sys, int maxiter, GmPtrs& p) {
+int gm_alloc(lsms_ctx* c, const GmSys& sys, int maxiter, size_t basis_elem, GmPtrs& p) {
   int rc;
   const int nb = sys.nb;
   p.ldh = maxiter + 1;
   p.stride = maxiter + 2;
   p.hstride = (long long)maxiter * p.ldh;
-  if ((rc = ensure(c, c->gm_v, (size_t)(maxiter + 1) * sys.slot * sizeof(double2)))) return rc;
+  if ((rc = ensure(c, c->gm_v, (size_t)(maxiter + 1) * sys.slot * basis_elem))) return rc;
   if ((rc = ensure(c, c->gm_h, (size_t)nb * p.hstride * sizeof(double2)))) return rc;
   if ((rc = ensure(c, c->gm_w, (size_t)2 * sys.slot * sizeof(double2)))) return rc;
   const size_t small = (size_t)nb * (7 * (size_t)p.stride + 2) * sizeof(double2) + nb * sizeof(GmState) +
                        nb * sizeof(int) + 512;
   if ((rc = ensure(c, c->gm_small, small))) return rc;
-  p.V = (double2*)c->gm_v.ptr;
+  p.V = c->gm_v.ptr;
   p.H = (double2*)c->gm_h.ptr;
   p.X = (double2*)c->gm_w.ptr;
   p.W = p.X + sys.slot;
@@ -502,27 +536,29 @@ int ensure_ring(lsms_ctx* c, int nb) {
 }
 
 // One Arnoldi step of every system, with the step index read on the device (capturable).
+template <typename T>
 int enqueue_iteration(lsms_ctx* c, const GmPtrs& g, const GmSys& s, int maxiter, int flags,
                       cudaStream_t st) {
   const long long slot = s.slot;
   const int nb = s.nb;
+  vec2<T>* V = (vec2<T>*)g.V;
   int rc;
-  k_copy_slot<<<grid_for(slot, 256), 256, 0, st>>>(g.X, g.V, slot, g.dk);
+  k_copy_slot<T><<<grid_for(slot, 256), 256, 0, st>>>(g.X, V, slot, g.dk);
   if ((rc = apply_device(c, s.apply_nrhs, g.X, g.W, flags, st))) return rc;
   const dim3 gd((unsigned)((s.maxlen + DOT_T - 1) / DOT_T), (unsigned)std::min(DOT_GY, (maxiter + 2 + DOT_V - 1) / DOT_V),
                 (unsigned)nb);
   const dim3 ga((unsigned)((s.maxlen + 255) / 256), (unsigned)nb);
   // classical Gram-Schmidt; the second pass runs only when the first cancels much of w
   cudaMemsetAsync(g.h1, 0, (size_t)nb * g.stride * sizeof(double2), st);
-  k_mdot<<<gd, 256, 0, st>>>(g.V, slot, 1, g.dk, 1, g.W, s.d_off, g.h1, g.stride, nullptr);   // V^H w, ||w||^2
+  k_mdot<T><<<gd, 256, 0, st>>>(V, slot, 1, g.dk, 1, g.W, s.d_off, g.h1, g.stride, nullptr);   // V^H w, ||w||^2
   k_gm_prep<<<nb, 32, 0, st>>>(g.dk, g.h1, g.stride, g.st);
-  k_maxpy<<<ga, 256, 0, st>>>(g.V, slot, 1, nullptr, g.dk, g.h1, g.stride, g.W, s.d_off, -1.0, nullptr);
+  k_maxpy<T><<<ga, 256, 0, st>>>(V, slot, 1, nullptr, g.dk, g.h1, g.stride, g.W, s.d_off, -1.0, nullptr);
   cudaMemsetAsync(g.h2, 0, (size_t)nb * g.stride * sizeof(double2), st);
-  k_mdot<<<gd, 256, 0, st>>>(g.V, slot, 1, g.dk, 1, g.W, s.d_off, g.h2, g.stride, g.st);
-  k_maxpy<<<ga, 256, 0, st>>>(g.V, slot, 1, nullptr, g.dk, g.h2, g.stride, g.W, s.d_off, -1.0, g.st);
+  k_mdot<T><<<gd, 256, 0, st>>>(V, slot, 1, g.dk, 1, g.W, s.d_off, g.h2, g.stride, g.st);
+  k_maxpy<T><<<ga, 256, 0, st>>>(V, slot, 1, nullptr, g.dk, g.h2, g.stride, g.W, s.d_off, -1.0, g.st);
   k_gm_column<<<nb, 32, (size_t)(3 * maxiter + 2) * sizeof(double2), st>>>(
       g.dk, g.h1, g.h2, g.stride, g.H, g.hstride, g.ldh, g.cs, g.sn, g.g, g.st);
-  k_scale_into_slot<<<dim3(grid_for(s.maxlen, 256), nb), 256, 0, st>>>(g.V, slot, g.W, g.st, s.d_off, g.dk);
+  k_scale_into_slot<T><<<dim3(grid_for(s.maxlen, 256), nb), 256, 0, st>>>(V, slot, g.W, g.st, s.d_off, g.dk);
   k_gm_snapshot<<<1, 256, 0, st>>>(g.st, nb, (GmState*)c->gm_ring_dev, RING, g.dk);
   return check_cuda(c, "gmres iteration");
 }
@@ -542,13 +578,15 @@ void launch_diag_scale(const double2* x, const double* s, double2* y, long long 
 // x_nonzero, solutions on return.  tol[b]: relative tolerance per system.  iters[b], res[b]:
 // iterations used and final residual estimate.  Returns LSMS_OK when every system converged,
 // LSMS_ERR_NOT_CONVERGED or LSMS_ERR_NONFINITE otherwise.
-int gmres_batch(lsms_ctx* c, const GmSys& s, const double2* rhs, double2* x, bool x_nonzero, const double* tol,
-                int maxiter, int flags, int* iters, double* res, double* hist, int hist_cap,
-                int* n_hist, cudaStream_t stream) {
+template <typename T>
+int gmres_batch_t(lsms_ctx* c, const GmSys& s, const double2* rhs, double2* x, bool x_nonzero, const double* tol,
+                  int maxiter, int flags, int* iters, double* res, double* hist, int hist_cap,
+                  int* n_hist, cudaStream_t stream) {
   const int nb = s.nb;
   GmPtrs g;
   int rc;
-  if ((rc = gm_alloc(c, s, maxiter, g))) return rc;
+  if ((rc = gm_alloc(c, s, maxiter, sizeof(vec2<T>), g))) return rc;
+  vec2<T>* V = (vec2<T>*)g.V;
   if ((rc = ensure_ring(c, nb))) return rc;
   GmState* ring = (GmState*)c->gm_ring;
   static std::once_flag attr;
@@ -557,18 +595,19 @@ int gmres_batch(lsms_ctx* c, const GmSys& s, const double2* rhs, double2* x, boo
                          (int)((3 * GIVENS_MAX + 2) * sizeof(double2)));
   });
   const long long slot = s.slot;                         // distance between basis slots
-  // r0 = rhs - A x into basis slot 0
+  // r0 = rhs - A x (in the operator's input buffer X when x is given); basis slot 0 = r0 / ||r0||
+  const double2* r0 = rhs;
   if (x_nonzero) {
     if ((rc = apply_device(c, s.apply_nrhs, x, g.W, flags, stream))) return rc;
-    k_sub<<<grid_for(slot, 256), 256, 0, stream>>>(g.V, rhs, g.W, slot);
+    k_sub<<<grid_for(slot, 256), 256, 0, stream>>>(g.X, rhs, g.W, slot);
+    r0 = g.X;
   } else {
     cudaMemsetAsync(x, 0, slot * sizeof(double2), stream);
-    cudaMemcpyAsync(g.V, rhs, slot * sizeof(double2), cudaMemcpyDeviceToDevice, stream);
   }
-  mdot(g.V, slot, 1, g.V, s, g.nrm, 2, stream);          // ||r0||^2 at nrm[2b]
-  mdot(rhs, slot, 1, rhs, s, g.nrm + 1, 2, stream);      // ||rhs||^2 at nrm[2b + 1]
+  mdot<double>(r0, slot, 1, r0, s, g.nrm, 2, stream);        // ||r0||^2 at nrm[2b]
+  mdot<double>(rhs, slot, 1, rhs, s, g.nrm + 1, 2, stream);  // ||rhs||^2 at nrm[2b + 1]
   k_gm_start<<<nb, 1, 0, stream>>>(g.nrm, g.st, g.g, g.stride);
-  k_scale_by<<<dim3(grid_for(s.maxlen, 256), nb), 256, 0, stream>>>(g.V, g.V, g.st, s.d_off);
+  k_scale_by<T><<<dim3(grid_for(s.maxlen, 256), nb), 256, 0, stream>>>(V, r0, g.st, s.d_off);
   cudaMemsetAsync(g.dk, 0, sizeof(int), stream);
   cudaStreamSynchronize(stream);
   if ((rc = check_cuda(c, "gmres start"))) return rc;
@@ -594,7 +633,7 @@ int gmres_batch(lsms_ctx* c, const GmSys& s, const double2* rhs, double2* x, boo
     c->timing = 0;
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      const int erc = enqueue_iteration(c, g, s, maxiter, flags, stream);
+      const int erc = enqueue_iteration<T>(c, g, s, maxiter, flags, stream);
       const cudaError_t e = cudaStreamEndCapture(stream, &graph);
       if (erc == LSMS_OK && e == cudaSuccess && graph &&
           cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
@@ -627,7 +666,7 @@ int gmres_batch(lsms_ctx* c, const GmSys& s, const double2* rhs, double2* x, boo
         cudaGraphExecDestroy(exec);
         return check_cuda(c, "cudaGraphLaunch");
       }
-    } else if ((rc = enqueue_iteration(c, g, s, maxiter, flags, stream))) {
+    } else if ((rc = enqueue_iteration<T>(c, g, s, maxiter, flags, stream))) {
       return rc;
     }
     cudaEventRecord(c->gm_ev[k % RING], stream);
@@ -651,16 +690,30 @@ int gmres_batch(lsms_ctx* c, const GmSys& s, const double2* rhs, double2* x, boo
   k_gm_backsolve<<<nb, 32, 0, stream>>>(g.kk, g.H, g.hstride, g.ldh, g.g, g.stride, g.y);
   int kmax = 0;
   for (int b = 0; b < nb; ++b) kmax = std::max(kmax, kdone[b]);
-  if (kmax > 0) maxpy(g.V, slot, kmax, g.kk, g.y, g.stride, x, s, 1.0, stream);
+  if (kmax > 0) maxpy<T>(V, slot, kmax, g.kk, g.y, g.stride, x, s, 1.0, stream);
   cudaStreamSynchronize(stream);
   if ((rc = check_cuda(c, "gmres update"))) return rc;
   return all ? LSMS_OK : LSMS_ERR_NOT_CONVERGED;
 }
 
+// Batched GMRES for A x_b = rhs_b over the systems of s: the inner solves of the mixed refinement
+// (every tolerance >= 1e-5) keep and multiply their Krylov basis in FP32, FP64 solves in FP64.
+int gmres_batch(lsms_ctx* c, const GmSys& s, const double2* rhs, double2* x, bool x_nonzero, const double* tol,
+                int maxiter, int flags, int* iters, double* res, double* hist, int hist_cap,
+                int* n_hist, cudaStream_t stream) {
+  bool f32 = (flags & LSMS_APPLY_MIXED) != 0;
+  for (int b = 0; b < s.nb && f32; ++b) f32 = tol[b] >= 1e-5;
+  if (f32)
+    return gmres_batch_t<float>(c, s, rhs, x, x_nonzero, tol, maxiter, flags, iters, res, hist, hist_cap, n_hist,
+                                stream);
+  return gmres_batch_t<double>(c, s, rhs, x, x_nonzero, tol, maxiter, flags, iters, res, hist, hist_cap, n_hist,
+                               stream);
+}
+
 // ||v_b||_2 for the systems of s (read back synchronously)
 static void norms_device(const double2* v, const GmSys& s, double2* tmp, cudaStream_t st,
                          std::vector<double>& out) {
-  mdot(v, s.slot, 1, v, s, tmp, 1, st);
+  mdot<double>(v, s.slot, 1, v, s, tmp, 1, st);
   std::vector<double2> h(s.nb);
   cudaMemcpyAsync(h.data(), tmp, s.nb * sizeof(double2), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
