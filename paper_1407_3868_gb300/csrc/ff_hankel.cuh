@@ -91,11 +91,15 @@ __device__ __noinline__ void hankel01_near(double z, float2* h0, float2* h1) {
 // (source) given as float-float (x_hi, x_lo, y_hi, y_lo).
 // near_r2: squared distance (float-float) below which the pair is left to the near-pair kernel and
 // its sequence is zero here; near_r2.hi <= 0 computes every pair here.
-__device__ void hankel_sequence_f32(float4 a, float4 b, ffl k, int p, ffl near_r2, float2* h) {
+// The order p is a template parameter, so the recurrence is unrolled.
+template <int PT>
+__device__ __forceinline__ void hankel_sequence_f32(float4 a, float4 b, ffl k, ffl near_r2, float2* h) {
+  constexpr int p = PT;
   const ffl dx = ff_sub({a.x, a.y}, {b.x, b.y});
   const ffl dy = ff_sub({a.z, a.w}, {b.z, b.w});
   const ffl r2 = ff_add(ff_mul(dx, dx), ff_mul(dy, dy));
   if (near_r2.hi > 0.0f && (r2.hi < near_r2.hi || (r2.hi == near_r2.hi && r2.lo < near_r2.lo))) {
+#pragma unroll
     for (int q = 0; q <= 4 * p; ++q) h[q] = make_float2(0.f, 0.f);
     return;
   }
@@ -116,6 +120,7 @@ __device__ void hankel_sequence_f32(float4 a, float4 b, ffl k, int p, ffl near_r
   h[c0] = h0;
   float2 hm = h0, hq = h1, eq = e1;
   const float iz = 1.0f / zf;
+#pragma unroll
   for (int q = 1; q <= 2 * p; ++q) {
     const float2 v = cmulf(hq, eq);
     h[c0 + q] = v;

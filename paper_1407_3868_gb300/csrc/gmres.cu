@@ -66,10 +66,8 @@ struct GmState {
   int reorth;     // 1: the current Arnoldi step needs a second Gram-Schmidt pass
 };
 
-constexpr int DOT_T = 2048;    // elements per CTA (8 per thread)
-constexpr int DOT_V = 8;       // vectors per CTA, accumulated side by side
-constexpr int DOT_E = DOT_T / 256;
-constexpr int DOT_GY = 8;      // vector groups in the grid; a CTA loops over every DOT_GY-th group
+constexpr int DOT_T = 2048;    // elements of w staged per CTA
+constexpr int DOT_GY = 8;      // groups of 8 vectors in the grid; a CTA loops over every 8th group
 constexpr int GIVENS_MAX = 4096;
 
 // System b = blockIdx.z:  out[b][i] += sum_t conj(V[i][b][t]) w[b][t] for i < nv, and, with
@@ -77,72 +75,64 @@ constexpr int GIVENS_MAX = 4096;
 // captured graph follows the Arnoldi step).  V slots are ldv apart; system b occupies elements
 // off[b] .. off[b + 1] of a slot (systems may differ in length: the layouts of a batch).  With a
 // gate the kernel does nothing unless system b needs a second Gram-Schmidt pass.
-// Each thread keeps 8 elements of w in registers and reads the matching elements of 8 vectors, so
-// 64 independent loads are in flight per thread (the multi-dot is bound by HBM bandwidth).
+// A CTA stages a chunk of DOT_T elements of w in shared memory; each warp takes one basis vector
+// at a time (vectors blockIdx.y * 8 + warp, stepping gridDim.y * 8) with 8 loads in flight per lane
+// and reduces it with shuffles only, so the multi-dot streams the basis at memory speed.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_mdot(const vec2<T>* __restrict__ V, long long ldv, int nv0, const int* __restrict__ kp,
        int self_norm, const double2* __restrict__ w, const long long* __restrict__ off,
        double2* __restrict__ out, int out_stride, const GmState* __restrict__ gate) {
   using V2 = vec2<T>;
+  constexpr int U = 8;
   const int b = blockIdx.z;
   if (gate && !gate[b].reorth) return;
   const int nv = nv0 + (kp ? *kp : 0);
   const int ntot = nv + (self_norm ? 1 : 0);
   const long long L = off[b + 1] - off[b];
-  if (blockIdx.x * (long long)DOT_T >= L || (int)blockIdx.y * DOT_V >= ntot) return;
-  V += off[b];
-  w += off[b];
+  const long long c0 = blockIdx.x * (long long)DOT_T;
+  if (c0 >= L || (int)blockIdx.y * 8 >= ntot) return;
+  const int cnt = (int)min((long long)DOT_T, L - c0);
+  V += off[b] + c0;
+  w += off[b] + c0;
   out += (long long)b * out_stride;
-  const long long t0 = blockIdx.x * (long long)DOT_T + threadIdx.x;
-  V2 wr[DOT_E];
-#pragma unroll
-  for (int e = 0; e < DOT_E; ++e) {
-    const long long t = t0 + e * 256;
-    const double2 u = t < L ? w[t] : make_double2(0.0, 0.0);
-    wr[e] = mk2<T>(u.x, u.y);
+  __shared__ V2 ws[DOT_T];
+  for (int i = threadIdx.x; i < DOT_T; i += blockDim.x) {
+    const double2 u = i < cnt ? w[i] : make_double2(0.0, 0.0);
+    ws[i] = mk2<T>(u.x, u.y);
   }
-  __shared__ double2 red[8][DOT_V];
+  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // vector groups blockIdx.y, blockIdx.y + gridDim.y, ... (the grid does not grow with the basis)
-  for (int i0 = blockIdx.y * DOT_V; i0 < ntot; i0 += gridDim.y * DOT_V) {
-    V2 acc[DOT_V];
+  for (int i = blockIdx.y * 8 + warp; i < ntot; i += gridDim.y * 8) {
+    T ax = 0, ay = 0, bx = 0, by = 0;
+    if (i < nv) {
+      const V2* vi = V + (long long)i * ldv;
+      for (int t = lane; t < DOT_T; t += 32 * U) {
+        V2 v[U];
 #pragma unroll
-    for (int v = 0; v < DOT_V; ++v) {
-      acc[v] = mk2<T>(0.0, 0.0);
-      const int i = i0 + v;
-      if (i < nv) {
-        const V2* vi = V + (long long)i * ldv;
+        for (int u = 0; u < U; ++u) {
+          const int tt = t + 32 * u;
+          v[u] = tt < cnt ? vi[tt] : mk2<T>(0.0, 0.0);
+        }
 #pragma unroll
-        for (int e = 0; e < DOT_E; ++e) {
-          const long long t = t0 + e * 256;
-          if (t < L) {
-            const V2 c = cjmul_t(vi[t], wr[e]);
-            acc[v].x += c.x;
-            acc[v].y += c.y;
+        for (int u = 0; u < U; ++u) {
+          const V2 c = cjmul_t(v[u], ws[t + 32 * u]);
+          if (u & 1) {
+            bx += c.x;
+            by += c.y;
+          } else {
+            ax += c.x;
+            ay += c.y;
           }
         }
-      } else if (i < ntot) {                       // ||w||^2
-#pragma unroll
-        for (int e = 0; e < DOT_E; ++e) acc[v].x += wr[e].x * wr[e].x + wr[e].y * wr[e].y;
       }
+    } else {                                        // ||w||^2
+      for (int t = lane; t < cnt; t += 32) ax += ws[t].x * ws[t].x + ws[t].y * ws[t].y;
     }
-    __syncthreads();                               // red is reused across groups
-#pragma unroll
-    for (int v = 0; v < DOT_V; ++v) {
-      const double2 a = warp_sum(to_d2(acc[v]));
-      if (lane == 0) red[warp][v] = a;
-    }
-    __syncthreads();
-    if (threadIdx.x < DOT_V && i0 + (int)threadIdx.x < ntot) {
-      double2 s = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        s.x += red[q][threadIdx.x].x;
-        s.y += red[q][threadIdx.x].y;
-      }
-      atomicAdd(&out[i0 + threadIdx.x].x, s.x);
-      atomicAdd(&out[i0 + threadIdx.x].y, s.y);
+    const double2 s = warp_sum(make_double2((double)ax + (double)bx, (double)ay + (double)by));
+    if (lane == 0) {
+      atomicAdd(&out[i].x, s.x);
+      atomicAdd(&out[i].y, s.y);
     }
   }
 }
@@ -456,8 +446,7 @@ void mdot(const vec2<T>* V, long long ldv, int nv, const double2* w, const GmSys
           int out_stride, cudaStream_t st) {
   for (int b = 0; b < s.nb; ++b)
     cudaMemsetAsync(out + (long long)b * out_stride, 0, (size_t)nv * sizeof(double2), st);
-  dim3 grid((unsigned)((s.maxlen + DOT_T - 1) / DOT_T), (unsigned)std::min(DOT_GY, (nv + DOT_V - 1) / DOT_V),
-            (unsigned)s.nb);
+  dim3 grid((unsigned)((s.maxlen + DOT_T - 1) / DOT_T), (unsigned)std::min(DOT_GY, (nv + 7) / 8), (unsigned)s.nb);
   k_mdot<T><<<grid, 256, 0, st>>>(V, ldv, nv, nullptr, 0, w, s.d_off, out, out_stride, nullptr);
 }
 
@@ -545,7 +534,7 @@ int enqueue_iteration(lsms_ctx* c, const GmPtrs& g, const GmSys& s, int maxiter,
   int rc;
   k_copy_slot<T><<<grid_for(slot, 256), 256, 0, st>>>(g.X, V, slot, g.dk);
   if ((rc = apply_device(c, s.apply_nrhs, g.X, g.W, flags, st))) return rc;
-  const dim3 gd((unsigned)((s.maxlen + DOT_T - 1) / DOT_T), (unsigned)std::min(DOT_GY, (maxiter + 2 + DOT_V - 1) / DOT_V),
+  const dim3 gd((unsigned)((s.maxlen + DOT_T - 1) / DOT_T), (unsigned)std::min(DOT_GY, (maxiter + 2 + 7) / 8),
                 (unsigned)nb);
   const dim3 ga((unsigned)((s.maxlen + 255) / 256), (unsigned)nb);
   // classical Gram-Schmidt; the second pass runs only when the first cancels much of w

@@ -86,7 +86,7 @@ k_translate_f32(const float4* __restrict__ cff, int n, float k_hi, float k_lo,
         const int js = s0 + hi8;
         float2* h = hw + lane * MHS;
         if (js < cnt && lvalid && j0c + js != l) {
-          hankel_sequence_f32(ct, sc[js], kf, p, {near_hi, near_lo}, h);
+          hankel_sequence_f32<PT>(ct, sc[js], kf, {near_hi, near_lo}, h);
         } else {
           for (int q = 0; q <= 4 * p; ++q) h[q] = make_float2(0.f, 0.f);
         }

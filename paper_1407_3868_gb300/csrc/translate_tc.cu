@@ -263,7 +263,7 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
         const int l = g * TG + i, m = m0 + j;
         float2* h = raw + b * RAWS;
         if (l < n && l != m) {
-          hankel_sequence_f32(cff[l], cff[m], kf, p, nr, h);
+          hankel_sequence_f32<PT>(cff[l], cff[m], kf, nr, h);
         } else {
           for (int q = 0; q <= 4 * p; ++q) h[q] = make_float2(0.f, 0.f);
         }
