@@ -121,7 +121,7 @@ def contour_panel_breaks(n_panels: int, branch_points, b: float, t_max: float) -
 
 
 def contour(n_nodes: int, k1: float, k2: float, k3: float, b: float, t_max: float,
-            panel_order: int = 16):
+            panel_order: int = 16, branch_points=None):
     """Nodes lambda_nu and weights w_nu (d lambda included) of the discretised contour.
 
     Gamma1 (t - i b, 0 < t < t_max) and Gamma3 (its mirror t + i b, -t_max < t < 0) each carry
@@ -134,7 +134,8 @@ def contour(n_nodes: int, k1: float, k2: float, k3: float, b: float, t_max: floa
     n2 = n_nodes - 2 * n1
     if n1 <= 0 or n2 <= 0:
         raise ValueError("contour: too few nodes for the panel order")
-    breaks = contour_panel_breaks(n1 // q, (k1, k2, k3), b, t_max)
+    breaks = contour_panel_breaks(n1 // q, (k1, k2, k3) if branch_points is None else branch_points,
+                                  b, t_max)
     x, w = np.polynomial.legendre.leggauss(q)
     t1, w1 = [], []
     for a, c in zip(breaks[:-1], breaks[1:]):
@@ -288,6 +289,86 @@ class Medium:
         a = self.a_lambda(lam)
         r = self.rhs(lam, inc, p_plus, q_minus)
         return np.linalg.solve(a, r[..., None])[..., 0]
+
+
+class Stack:
+    """Any number of layers (the generalisation the paper's introduction names): wavenumbers
+    k_1 (top, y > 0) .. k_L (bottom), interior layers 2..L-1 of thicknesses d_2..d_{L-1}, discs in
+    layer m (2 <= m <= L-1).  The interfaces are at z_1 = 0, z_i = z_{i-1} - d_i.
+
+    Each interior layer j carries (1/4pi) int [s_j^+ exp(gamma_j (y - z_{j-1})) +
+    s_j^- exp(-gamma_j (y - z_j))] / gamma_j exp(i lambda x) d lambda (a wave leaving its top and one
+    leaving its bottom interface), layer 1 sigma_1 exp(-gamma_1 y) / gamma_1 and layer L
+    sigma_L exp(gamma_L (y - z_{L-1})) / gamma_L, as in the three-layer representation (Sec. 2).
+    [u] = [du/dy] = 0 at every interface gives 2(L - 1) equations per node, solved by LAPACK LU.
+    The discs' spectral densities enter at the two interfaces of layer m in the particle layer's own
+    frame (its top interface at y = 0): the Problem class is used unchanged with disc centres given
+    in that frame (y + depth), and solve_layers returns (sigma_1, s_m^+, s_m^-, sigma_L).
+    """
+
+    def __init__(self, ks, ds, m, kp, radius):
+        self.ks, self.ds, self.mi = [float(k) for k in ks], [float(d) for d in ds], int(m)
+        self.L = len(self.ks)
+        if self.L < 3 or len(self.ds) != self.L - 2 or not 2 <= self.mi <= self.L - 1:
+            raise ValueError("Stack: need L >= 3 layers, L - 2 thicknesses and 2 <= m <= L - 1")
+        self.k1, self.k2, self.k3 = self.ks[0], self.ks[self.mi - 1], self.ks[-1]
+        self.d = self.ds[self.mi - 2]
+        self.depth = sum(self.ds[: self.mi - 2])        # from y = 0 down to the top of layer m
+        self.kp, self.radius = kp, radius
+
+    def incident_density(self, lam, src) -> np.ndarray:
+        return np.exp(-gamma(lam, self.k1) * src[1] - 1j * lam * src[0])
+
+    def solve_layers(self, lam, inc=None, p_plus=None, q_minus=None) -> np.ndarray:
+        lam = np.atleast_1d(np.asarray(lam, dtype=complex))
+        L, m = self.L, self.mi
+        n = 2 * L - 2
+        g = [gamma(lam, k) for k in self.ks]                    # g[j - 1] for layer j
+        E = {j: np.exp(-g[j - 1] * self.ds[j - 2]) for j in range(2, L)}
+
+        def col(j, sign):                                        # unknown index of layer j
+            if j == 1:
+                return 0
+            if j == L:
+                return n - 1
+            return 1 + 2 * (j - 2) + (0 if sign > 0 else 1)
+
+        out = np.zeros((lam.size, 4), dtype=complex)
+        for v in range(lam.size):
+            a = np.zeros((n, n), dtype=complex)
+            r = np.zeros(n, dtype=complex)
+            for i in range(1, L):                                # interface i: layer i above, i + 1 below
+                rv, rd = 2 * (i - 1), 2 * (i - 1) + 1
+                gi, gb = g[i - 1][v], g[i][v]
+                if i == 1:                                       # layer above: value, derivative
+                    a[rv, col(1, 1)] += 1.0 / gi
+                    a[rd, col(1, 1)] += -1.0
+                else:
+                    a[rv, col(i, 1)] += E[i][v] / gi
+                    a[rv, col(i, -1)] += 1.0 / gi
+                    a[rd, col(i, 1)] += E[i][v]
+                    a[rd, col(i, -1)] += -1.0
+                if i + 1 == L:                                   # layer below (subtracted)
+                    a[rv, col(L, 1)] -= 1.0 / gb
+                    a[rd, col(L, 1)] -= 1.0
+                else:
+                    a[rv, col(i + 1, 1)] -= 1.0 / gb
+                    a[rv, col(i + 1, -1)] -= E[i + 1][v] / gb
+                    a[rd, col(i + 1, 1)] -= 1.0
+                    a[rd, col(i + 1, -1)] -= -E[i + 1][v]
+                # known fields: rhs = (below) - (above)
+                if i == 1 and inc is not None:                   # incident wave in layer 1
+                    r[rv] -= inc[v] / gi
+                    r[rd] -= inc[v]
+                if i == m - 1 and p_plus is not None:            # discs, below this interface
+                    r[rv] += p_plus[v] / gb
+                    r[rd] += -p_plus[v]
+                if i == m and q_minus is not None:               # discs, above this interface
+                    r[rv] -= q_minus[v] / gi
+                    r[rd] -= q_minus[v]
+            s = np.linalg.solve(a, r)
+            out[v] = (s[0], s[col(m, 1)], s[col(m, -1)], s[n - 1])
+        return out
 
 
 # ----------------------------------------------------------------------------------------------
@@ -557,8 +638,8 @@ class Problem:
         gamma_3.  Parseval turns the flux Im int conj(u) du/dn dx into (1/8pi) int |U|^2 / s_1 over
         |lambda| < k_1 (s_i = sqrt(k_i^2 - lambda^2); evanescent waves carry no power), and likewise
         (1/8pi) int |sigma_3|^2 / s_3 over |lambda| < k_3.  With lambda = k cos(theta) the weight
-        1/s becomes d theta; the layer-3 interval is split where lambda crosses +-k_1, +-k_2
-        (square-root branch points of the densities), each piece is mapped by
+        1/s becomes d theta; each interval is split where lambda crosses the other layers'
+        wavenumbers (square-root branch points of the densities), each piece is mapped by
         theta = a + (b - a)(1 - cos phi)/2, which makes the endpoint square roots smooth in phi, and
         integrated by adaptive Gauss-Kronrod (QUADPACK): between k_1 and k_2 the layer acts as a
         leaky waveguide and the densities peak near its modes.  The densities are evaluated exactly
@@ -582,11 +663,14 @@ class Problem:
                 return abs(density(k * math.cos(th), layer)) ** 2 * (b - a) * 0.5 * math.sin(phi)
             return integrate.quad(f, 0.0, math.pi, epsabs=tol, epsrel=tol, limit=4000)[0]
 
-        up = piece(k1, 1, 0.0, math.pi) / (2.0 * FOUR_PI)
-        inner = sorted(math.acos(kk / k3) for kk in (k1, k2) if kk < k3)
-        breaks = [0.0] + inner + [math.pi - t for t in reversed(inner)] + [math.pi]
-        down = sum(piece(k3, 3, a, b) for a, b in zip(breaks[:-1], breaks[1:])) / (2.0 * FOUR_PI)
-        return up, down
+        branch = getattr(self.m, "ks", (k1, k2, k3))          # every layer's wavenumber
+
+        def pieces(k, layer):
+            inner = sorted(set(math.acos(kk / k) for kk in branch if kk < k))
+            breaks = [0.0] + inner + [math.pi - t for t in reversed(inner)] + [math.pi]
+            return sum(piece(k, layer, a, b) for a, b in zip(breaks[:-1], breaks[1:])) / (2.0 * FOUR_PI)
+
+        return pieces(k1, 1), pieces(k3, 3)
 
 
 def gmres(matvec, b, tol=1e-12, maxiter=500):

@@ -365,6 +365,47 @@ def test_energy_flux_balance_for_lossless_media():
     assert abs(up + down - (0.25 + u_s.imag)) < 1e-9 * 0.25
 
 
+def test_layer_stack_reduces_to_three_layers():
+    # Stack (any number of layers) against the pinned three-layer medium: an interface between two
+    # layers of equal wavenumber must be invisible.  (a) the disc layer split below the discs;
+    # (b) a layer of k_1 inserted above the disc layer (all absolute heights shift by its thickness).
+    m = medium()
+    p, src = 5, np.array([0.3, 1.0])
+    c = np.array([[0.2, -0.7], [-0.6, -1.3], [0.9, -1.0]])          # disc-layer frame
+    tg = np.array([[-1.0, 1.5], [0.5, 1.2], [1.5, 2.0]])
+    lam, wt = O.contour(512, m.k1, m.k2, m.k3, 0.2, 120.0)
+    ref = O.Problem(m, p, c, lam, wt)
+    b_ref = ref.solve_dense(src)
+    u_ref = ref.field_layer1(src, b_ref, tg, "scattered")
+    st = O.Stack([m.k1, m.k2, m.k2, m.k3], [1.6, m.d - 1.6], 2, m.kp, m.radius)
+    pa = O.Problem(st, p, c, lam, wt)
+    b = pa.solve_dense(src)
+    assert np.allclose(b, b_ref, rtol=0, atol=1e-12 * np.abs(b_ref).max())
+    assert np.allclose(pa.field_layer1(src, b, tg, "scattered"), u_ref, rtol=0, atol=1e-12 * np.abs(u_ref).max())
+    h = 0.8
+    st = O.Stack([m.k1, m.k1, m.k2, m.k3], [h, m.d], 3, m.kp, m.radius)
+    assert st.depth == h
+    pb = O.Problem(st, p, c, lam, wt)
+    b = pb.solve_dense(src)
+    b2 = ref.solve_dense(src + [0.0, h])
+    assert np.allclose(b, b2, rtol=0, atol=1e-12 * np.abs(b2).max())
+    u2 = ref.field_layer1(src + [0.0, h], b2, tg + [0.0, h], "scattered")
+    assert np.allclose(pb.field_layer1(src, b, tg, "scattered"), u2, rtol=0, atol=1e-12 * np.abs(u2).max())
+
+
+def test_layer_stack_energy_balance():
+    # five lossless layers, discs in the third: the radiated power balance of the energy pin
+    ks = [2 * math.pi, 2.6 * math.pi, 3 * math.pi, 3.4 * math.pi, 4 * math.pi]
+    st = O.Stack(ks, [0.5, 2.0, 0.7], 3, MED["kp"], MED["radius"])
+    lam, wt = O.contour(2048, ks[0], ks[2], ks[-1], 0.2, 120.0, branch_points=ks)
+    src = np.array([0.3, 1.0])
+    pr = O.Problem(st, 5, np.array([[0.2, -0.7], [-0.6, -1.3], [0.9, -1.0]]), lam, wt)
+    beta = pr.solve_dense(src)
+    up, down = pr.outgoing_power(src, beta)
+    u_s = pr.field_layer1(src, beta, src[None, :], "scattered")[0]
+    assert abs(up + down - (0.25 + u_s.imag)) < 1e-9 * 0.25
+
+
 def test_oracle_gmres_matches_lu():
     m = medium()
     lam, wt = O.contour(256, m.k1, m.k2, m.k3, 0.2, 141.0)
