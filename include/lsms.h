@@ -98,6 +98,21 @@ enum {
 int lsms_create(double k1, double k2, double k3, double d, double kp, double radius, int p,
                 const lsms_contour* contour, int precision, lsms_ctx** out);
 
+/* lsms_create_stack — lsms_create for any number of layers (the generalisation named in Sec. 1;
+ *   the interface conditions of Sec. 2 at every interface, Sec. 5.2 "sommerfeldsys" extended).
+ *   k[n_layers]: wavenumbers top (layer 1, y > 0) to bottom (layer n_layers), > 0, finite.
+ *   thickness[n_layers - 2]: thicknesses of the interior layers 2 .. n_layers - 1 (> 0); the
+ *   interfaces are at y = 0, -thickness[0], -thickness[0] - thickness[1], ...
+ *   particle_layer: the interior layer m (2 <= m <= n_layers - 1) holding the discs, radius < half
+ *   its thickness.  Centres passed to lsms_set_particles are in the same global frame (layer 1 is
+ *   y > 0); sources and field targets too.  lsms_aggregate / lsms_reflect / lsms_disaggregate
+ *   densities refer to layer m (P+ at its top interface, Q- at its bottom one).  The contour is
+ *   graded to every k_j.  lsms_create(k1, k2, k3, d, ...) is this call with n_layers = 3, m = 2.
+ *   Errors: LSMS_ERR_ARG (*out = NULL). */
+int lsms_create_stack(int n_layers, const double* k, const double* thickness, int particle_layer,
+                      double kp, double radius, int p, const lsms_contour* contour, int precision,
+                      lsms_ctx** out);
+
 /* lsms_set_particles — disc centres (Sec. 3.2; Sec. 5).  centres_xy: 2n doubles (x0,y0,x1,...).
  *   Every disc must lie strictly inside the middle layer, with gaps >= 0.2 R between discs
  *   (10% of the diameter: the well-separation assumption of Sec. 1); otherwise

@@ -138,25 +138,37 @@ int apply_device(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags,
 // ---------------------------------------------------------------------------------------------
 // create / destroy / particles
 // ---------------------------------------------------------------------------------------------
-extern "C" int lsms_create(double k1, double k2, double k3, double d, double kp, double radius,
-                           int p, const lsms_contour* contour, int precision, lsms_ctx** out) {
+int create_stack(const std::vector<double>& ks, const std::vector<double>& ds, int layer, double kp,
+                 double radius, int p, const lsms_contour* contour, int precision, lsms_ctx** out) {
   if (!out) return fail(nullptr, LSMS_ERR_ARG, "out is NULL");
   *out = nullptr;
-  const double vals[6] = {k1, k2, k3, d, kp, radius};
-  for (double v : vals)
-    if (!std::isfinite(v) || !(v > 0.0))
-      return fail(nullptr, LSMS_ERR_ARG, "k1, k2, k3, d, kp, radius must be finite and > 0");
-  if (!(radius < 0.5 * d)) return fail(nullptr, LSMS_ERR_ARG, "radius must be < d/2");
+  const int L = (int)ks.size();
+  if (L < 3 || (int)ds.size() != L - 2 || layer < 2 || layer > L - 1)
+    return fail(nullptr, LSMS_ERR_ARG, "need n_layers >= 3, n_layers - 2 thicknesses and 2 <= particle_layer <= n_layers - 1");
+  for (double v : ks)
+    if (!std::isfinite(v) || !(v > 0.0)) return fail(nullptr, LSMS_ERR_ARG, "wavenumbers must be finite and > 0");
+  for (double v : ds)
+    if (!std::isfinite(v) || !(v > 0.0)) return fail(nullptr, LSMS_ERR_ARG, "thicknesses must be finite and > 0");
+  if (!std::isfinite(kp) || !(kp > 0.0) || !std::isfinite(radius) || !(radius > 0.0))
+    return fail(nullptr, LSMS_ERR_ARG, "kp and radius must be finite and > 0");
+  const double d = ds[layer - 2];
+  if (!(radius < 0.5 * d)) return fail(nullptr, LSMS_ERR_ARG, "radius must be < half the disc layer's thickness");
   if (p < 0 || p > LSMS_MAX_P) return fail(nullptr, LSMS_ERR_ARG, "p must be in [0, 15]");
   if (!contour) return fail(nullptr, LSMS_ERR_ARG, "contour is NULL");
   if (precision != LSMS_FP64 && precision != LSMS_MIXED)
     return fail(nullptr, LSMS_ERR_ARG, "precision must be LSMS_FP64 or LSMS_MIXED");
   lsms_ctx* c = new (std::nothrow) lsms_ctx();
   if (!c) return fail(nullptr, LSMS_ERR_OOM, "host allocation failed");
-  c->k1 = k1; c->k2 = k2; c->k3 = k3; c->d = d; c->kp = kp; c->R = radius;
+  c->ks = ks;
+  c->ds = ds;
+  c->layer = layer;
+  c->depth = 0.0;
+  for (int j = 2; j < layer; ++j) c->depth += ds[j - 2];
+  c->k1 = ks[0]; c->k2 = ks[layer - 1]; c->k3 = ks[L - 1]; c->d = d; c->kp = kp; c->R = radius;
   c->p = p; c->P = 2 * p + 1; c->precision = precision; c->contour = *contour;
+  const double k2 = c->k2;
   std::string err;
-  int rc = build_contour(*contour, k1, k2, k3, c->nodes.lam, c->nodes.wt, err);
+  int rc = build_contour(*contour, ks, c->nodes.lam, c->nodes.wt, err);
   if (rc) { delete c; return fail(nullptr, rc, err); }
   c->ns = (int)c->nodes.lam.size();
   c->S = mie_diagonal(p, k2, kp, radius);
@@ -201,6 +213,22 @@ extern "C" int lsms_create(double k1, double k2, double k3, double d, double kp,
   return LSMS_OK;
 }
 
+extern "C" int lsms_create(double k1, double k2, double k3, double d, double kp, double radius,
+                           int p, const lsms_contour* contour, int precision, lsms_ctx** out) {
+  return create_stack({k1, k2, k3}, {d}, 2, kp, radius, p, contour, precision, out);
+}
+
+extern "C" int lsms_create_stack(int n_layers, const double* k, const double* thickness, int particle_layer,
+                                 double kp, double radius, int p, const lsms_contour* contour,
+                                 int precision, lsms_ctx** out) {
+  if (n_layers < 3 || !k || !thickness) {
+    if (out) *out = nullptr;
+    return fail(nullptr, LSMS_ERR_ARG, "need n_layers >= 3 and non-NULL k and thickness arrays");
+  }
+  return create_stack(std::vector<double>(k, k + n_layers), std::vector<double>(thickness, thickness + n_layers - 2),
+                      particle_layer, kp, radius, p, contour, precision, out);
+}
+
 extern "C" void lsms_destroy(lsms_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
@@ -239,7 +267,7 @@ extern "C" int lsms_set_particles(lsms_ctx* c, int n, const double* xy) {
   double xmin = 0.0, xmax = 0.0;
   for (int j = 0; j < n; ++j) {
     c->cx[j] = xy[2 * j];
-    c->cy[j] = xy[2 * j + 1];
+    c->cy[j] = xy[2 * j + 1] + c->depth;       // the disc layer's frame: its top interface at y = 0
     if (j == 0 || xy[2 * j] < xmin) xmin = xy[2 * j];
     if (j == 0 || xy[2 * j] > xmax) xmax = xy[2 * j];
   }
@@ -498,8 +526,8 @@ extern "C" int lsms_eval_field(lsms_ctx* c, int src_index, int ntgt, const doubl
                       nullptr, nullptr, c->stream);
     pq = (const double2*)c->ws_pq.ptr;
   }
-  launch_field(ns, ntgt, d_tgt, c->xc, c->d_lam, c->d_g1, c->d_field, c->d_inc, c->d_refl, pq,
-               d_src, c->k1, which, d_out, c->stream);
+  launch_field(ns, ntgt, d_tgt, c->xc, c->d_lam, c->d_g1, c->d_field, pq, d_src, c->k1, which, d_out,
+               c->stream);
   if ((rc = check_cuda(c, "eval_field"))) return rc;
   return copy_out(c, out, d_out, ntgt);
 }
@@ -550,7 +578,7 @@ extern "C" int lsms_build_contour(const lsms_contour* contour, double k1, double
   if (!contour || !nodes || !weights) return fail(nullptr, LSMS_ERR_ARG, "NULL argument");
   std::vector<cplx> lam, wt;
   std::string err;
-  const int rc = build_contour(*contour, k1, k2, k3, lam, wt, err);
+  const int rc = build_contour(*contour, {k1, k2, k3}, lam, wt, err);
   if (rc) return fail(nullptr, rc, err);
   std::memcpy(nodes, lam.data(), lam.size() * sizeof(cplx));
   std::memcpy(weights, wt.data(), wt.size() * sizeof(cplx));

@@ -91,11 +91,11 @@ std::vector<double> contour_panel_breaks(int n_panels, const double* ks, int nk,
   return pts;
 }
 
-int build_contour(const lsms_contour& c, double k1, double k2, double k3, std::vector<cplx>& lam,
+int build_contour(const lsms_contour& c, const std::vector<double>& ks, std::vector<cplx>& lam,
                   std::vector<cplx>& wt, std::string& err) {
   const int q = c.panel_order > 0 ? c.panel_order : 16;
   const double b = c.b > 0.0 ? c.b : 0.2;
-  const double t_max = c.t_max > 0.0 ? c.t_max : std::max(k1, std::max(k2, k3)) + 20.0;
+  const double t_max = c.t_max > 0.0 ? c.t_max : *std::max_element(ks.begin(), ks.end()) + 20.0;
   const int ns = c.n_nodes;
   if (ns <= 0 || q <= 0 || !std::isfinite(b) || !std::isfinite(t_max)) {
     err = "contour: n_nodes, panel_order, b and t_max must be positive and finite";
@@ -107,8 +107,7 @@ int build_contour(const lsms_contour& c, double k1, double k2, double k3, std::v
     err = "contour: n_nodes too small for the panel order";
     return LSMS_ERR_ARG;
   }
-  const double ks[3] = {k1, k2, k3};
-  std::vector<double> br = contour_panel_breaks(n1 / q, ks, 3, b, t_max);
+  std::vector<double> br = contour_panel_breaks(n1 / q, ks.data(), (int)ks.size(), b, t_max);
   std::vector<double> gx, gw;
   gauss_legendre(q, gx, gw);
   std::vector<double> t1, w1;
@@ -187,54 +186,133 @@ static cplx ipow(int n) {   // i^n for any integer n
   return t[((n % 4) + 4) % 4];
 }
 
+// Gaussian elimination with partial pivoting: a (n x n, row-major) x = b (n x nrhs, row-major),
+// solution in b.  False for a singular matrix.
+static bool solve_small(std::vector<cplx>& a, int n, std::vector<cplx>& b, int nrhs) {
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::abs(a[(size_t)i * n + k]) > std::abs(a[(size_t)piv * n + k])) piv = i;
+    if (std::abs(a[(size_t)piv * n + k]) == 0.0) return false;
+    if (piv != k) {
+      for (int j = 0; j < n; ++j) std::swap(a[(size_t)k * n + j], a[(size_t)piv * n + j]);
+      for (int j = 0; j < nrhs; ++j) std::swap(b[(size_t)k * nrhs + j], b[(size_t)piv * nrhs + j]);
+    }
+    for (int i = k + 1; i < n; ++i) {
+      const cplx f = a[(size_t)i * n + k] / a[(size_t)k * n + k];
+      if (f == cplx(0, 0)) continue;
+      for (int j = k; j < n; ++j) a[(size_t)i * n + j] -= f * a[(size_t)k * n + j];
+      for (int j = 0; j < nrhs; ++j) b[(size_t)i * nrhs + j] -= f * b[(size_t)k * nrhs + j];
+    }
+  }
+  for (int k = n - 1; k >= 0; --k)
+    for (int j = 0; j < nrhs; ++j) {
+      cplx s = b[(size_t)k * nrhs + j];
+      for (int i = k + 1; i < n; ++i) s -= a[(size_t)k * n + i] * b[(size_t)i * nrhs + j];
+      b[(size_t)k * nrhs + j] = s / a[(size_t)k * n + k];
+    }
+  return true;
+}
+
+// Per-node constants.  The layer response (Sec. 2 Eq. "sommerfeldsys", generalised to any number of
+// layers): interior layer j carries s_j^+ exp(g_j (y - z_{j-1})) + s_j^- exp(-g_j (y - z_j)) (over
+// g_j, times exp(i lambda x)), layer 1 sigma_1 exp(-g_1 y), the bottom layer sigma_L exp(g_L (y -
+// z_{L-1})); [u] = [du/dy] = 0 at the L - 1 interfaces.  The system is solved for a unit incident
+// density I (line source in layer 1), a unit upgoing particle density P at the top of the disc layer
+// and a unit downgoing one Q at its bottom; the tables are the linear maps (P, Q) -> (s_m^+, s_m^-),
+// I -> (s_m^+, s_m^-) and (I, P, Q) -> sigma_1.
 void build_node_tables(lsms_ctx* c) {
   NodeTables& t = c->nodes;
   const int ns = c->ns, p = c->p, P = c->P;
+  const int L = (int)c->ks.size(), m = c->layer, n = 2 * L - 2;
   t.g1.resize(ns); t.g2.resize(ns); t.g3.resize(ns);
   t.refl.resize(4 * ns); t.inc.resize(2 * ns); t.field.resize(4 * ns);
   t.fagg.assign(2 * (size_t)ns * P, cplx(0, 0));
   t.udis.assign(2 * (size_t)ns * P, cplx(0, 0));
+  auto col = [&](int j, int sign) {             // unknown of layer j (1-based)
+    if (j == 1) return 0;
+    if (j == L) return n - 1;
+    return 1 + 2 * (j - 2) + (sign > 0 ? 0 : 1);
+  };
+  std::vector<cplx> g(L), E(L + 1), a, b;
   for (int v = 0; v < ns; ++v) {
     const cplx lam = t.lam[v], w = t.wt[v];
-    const cplx g1 = gamma_of(lam, c->k1), g2 = gamma_of(lam, c->k2), g3 = gamma_of(lam, c->k3);
-    t.g1[v] = g1; t.g2[v] = g2; t.g3[v] = g3;
-    const cplx e = std::exp(-g2 * c->d);
-    const cplx rt = (g2 - g1) / (g2 + g1), rb = (g2 - g3) / (g2 + g3);
-    const cplx den = 1.0 - rt * rb * e * e;
-    t.refl[4 * v + 0] = rt / den;
-    t.refl[4 * v + 1] = rt * rb * e / den;
-    t.refl[4 * v + 2] = rb * rt * e / den;
-    t.refl[4 * v + 3] = rb / den;
-    const cplx tau = 2.0 * g2 / (g1 + g2);
-    t.inc[2 * v + 0] = tau / den;
-    t.inc[2 * v + 1] = rb * e * tau / den;
-    t.field[4 * v + 0] = (g1 - g2) / (g1 + g2);
-    t.field[4 * v + 1] = 2.0 * g1 / (g1 + g2);
-    t.field[4 * v + 2] = e;
+    for (int j = 1; j <= L; ++j) g[j - 1] = gamma_of(lam, c->ks[j - 1]);
+    for (int j = 2; j < L; ++j) E[j] = std::exp(-g[j - 1] * c->ds[j - 2]);
+    const cplx g1 = g[0], g2 = g[m - 1];
+    t.g1[v] = g1; t.g2[v] = g2; t.g3[v] = g[L - 1];
+    a.assign((size_t)n * n, cplx(0, 0));
+    b.assign((size_t)n * 3, cplx(0, 0));       // right-hand sides: unit I, P, Q
+    for (int i = 1; i < L; ++i) {               // interface i: layer i above, i + 1 below
+      const int rv = 2 * (i - 1), rd = rv + 1;
+      const cplx gi = g[i - 1], gb = g[i];
+      if (i == 1) {
+        a[(size_t)rv * n + col(1, 1)] += 1.0 / gi;
+        a[(size_t)rd * n + col(1, 1)] += -1.0;
+      } else {
+        a[(size_t)rv * n + col(i, 1)] += E[i] / gi;
+        a[(size_t)rv * n + col(i, -1)] += 1.0 / gi;
+        a[(size_t)rd * n + col(i, 1)] += E[i];
+        a[(size_t)rd * n + col(i, -1)] += -1.0;
+      }
+      if (i + 1 == L) {
+        a[(size_t)rv * n + col(L, 1)] -= 1.0 / gb;
+        a[(size_t)rd * n + col(L, 1)] -= 1.0;
+      } else {
+        a[(size_t)rv * n + col(i + 1, 1)] -= 1.0 / gb;
+        a[(size_t)rv * n + col(i + 1, -1)] -= E[i + 1] / gb;
+        a[(size_t)rd * n + col(i + 1, 1)] -= 1.0;
+        a[(size_t)rd * n + col(i + 1, -1)] += E[i + 1];
+      }
+      if (i == 1) {                             // incident wave, above interface 1
+        b[(size_t)rv * 3 + 0] -= 1.0 / gi;
+        b[(size_t)rd * 3 + 0] -= 1.0;
+      }
+      if (i == m - 1) {                         // discs' upgoing density, below this interface
+        b[(size_t)rv * 3 + 1] += 1.0 / gb;
+        b[(size_t)rd * 3 + 1] += -1.0;
+      }
+      if (i == m) {                             // discs' downgoing density, above this interface
+        b[(size_t)rv * 3 + 2] -= 1.0 / gi;
+        b[(size_t)rd * 3 + 2] -= 1.0;
+      }
+    }
+    if (!solve_small(a, n, b, 3)) b.assign((size_t)n * 3, cplx(NAN, NAN));
+    const int up = col(m, 1), dn = col(m, -1);
+    t.refl[4 * v + 0] = b[(size_t)up * 3 + 1];
+    t.refl[4 * v + 1] = b[(size_t)up * 3 + 2];
+    t.refl[4 * v + 2] = b[(size_t)dn * 3 + 1];
+    t.refl[4 * v + 3] = b[(size_t)dn * 3 + 2];
+    t.inc[2 * v + 0] = b[(size_t)up * 3 + 0];
+    t.inc[2 * v + 1] = b[(size_t)dn * 3 + 0];
+    t.field[4 * v + 0] = b[0];
+    t.field[4 * v + 1] = b[1];
+    t.field[4 * v + 2] = b[2];
     t.field[4 * v + 3] = w / (4.0 * kPi * g1);
     const cplx wm = (lam - g2) / c->k2, wp = (lam + g2) / c->k2;
     const cplx q = w / (4.0 * kPi * g2);
     // powers w^n, n = -p..p, by repeated multiplication (w-^{-n} = w+^n since w- w+ = 1)
     std::vector<cplx> pm(P), pp(P);
     pm[p] = pp[p] = cplx(1, 0);
-    for (int n = 1; n <= p; ++n) {
-      pm[p + n] = pm[p + n - 1] * wm;
-      pm[p - n] = pm[p - n + 1] * wp;
-      pp[p + n] = pp[p + n - 1] * wp;
-      pp[p - n] = pp[p - n + 1] * wm;
+    for (int k = 1; k <= p; ++k) {
+      pm[p + k] = pm[p + k - 1] * wm;
+      pm[p - k] = pm[p - k + 1] * wp;
+      pp[p + k] = pp[p + k - 1] * wp;
+      pp[p - k] = pp[p - k + 1] * wm;
     }
-    for (int n = -p; n <= p; ++n) {
-      const cplx cn = 4.0 * ipow(-(n + 1)) ;   // 4 (-i)^{n+1} = 4 i^{-(n+1)}
-      t.fagg[(size_t)v * P + n + p] = cn * pm[p + n];
-      t.fagg[(size_t)(ns + v) * P + n + p] = cn * pp[p + n];
-      t.udis[(size_t)v * P + n + p] = q * ipow(n) * pm[p + n];
-      t.udis[(size_t)(ns + v) * P + n + p] = q * ipow(n) * pp[p + n];
+    for (int k = -p; k <= p; ++k) {
+      const cplx cn = 4.0 * ipow(-(k + 1)) ;   // 4 (-i)^{n+1} = 4 i^{-(n+1)}
+      t.fagg[(size_t)v * P + k + p] = cn * pm[p + k];
+      t.fagg[(size_t)(ns + v) * P + k + p] = cn * pp[p + k];
+      t.udis[(size_t)v * P + k + p] = q * ipow(k) * pm[p + k];
+      t.udis[(size_t)(ns + v) * P + k + p] = q * ipow(k) * pp[p + k];
     }
   }
 }
 
-// Discs must lie strictly inside the middle layer and be separated by at least 10% of their
-// diameter (the well-separation assumption of Sec. 1).
+// Discs must lie strictly inside the disc layer (centres given in absolute coordinates; the layer's
+// top interface is `depth` below y = 0) and be separated by at least 10% of their diameter (the
+// well-separation assumption of Sec. 1).
 int validate_geometry(const lsms_ctx* c, int n, const double* xy, std::string& err) {
   const double R = c->R, gap = 0.2 * R, dmin = 2.0 * R + gap;
   for (int j = 0; j < n; ++j) {
@@ -243,8 +321,8 @@ int validate_geometry(const lsms_ctx* c, int n, const double* xy, std::string& e
       err = "set_particles: non-finite centre " + std::to_string(j);
       return LSMS_ERR_ARG;
     }
-    if (!(y + R < 0.0) || !(y - R > -c->d)) {
-      err = "set_particles: disc " + std::to_string(j) + " is not strictly inside the middle layer";
+    if (!(y + c->depth + R < 0.0) || !(y + c->depth - R > -c->d)) {
+      err = "set_particles: disc " + std::to_string(j) + " is not strictly inside the disc layer";
       return LSMS_ERR_GEOMETRY;
     }
   }

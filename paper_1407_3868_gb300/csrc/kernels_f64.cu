@@ -322,8 +322,7 @@ __global__ void k_combine(const double2* __restrict__ x, const double2* __restri
 // P+, Q- (pq, [2][ns]) and the incident density.
 __global__ void k_field(int ns, int ntgt, const double* __restrict__ tgt, double xc,
                         const double2* __restrict__ lam, const double2* __restrict__ g1,
-                        const double2* __restrict__ ft, const double2* __restrict__ inc,
-                        const double2* __restrict__ refl, const double2* __restrict__ pq,
+                        const double2* __restrict__ ft, const double2* __restrict__ pq,
                         const double* __restrict__ src, double k1, int which,
                         double2* __restrict__ out) {
   const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -337,17 +336,11 @@ __global__ void k_field(int ns, int ntgt, const double* __restrict__ tgt, double
     const double2 I = cexp_(-g.x * sy0 + L.y * sx0, -g.y * sy0 - L.x * sx0);
     const double2 Pp = pq ? pq[v] : make_double2(0.0, 0.0);
     const double2 Qm = pq ? pq[ns + v] : make_double2(0.0, 0.0);
-    const double2 r11 = ft[4 * v], t21 = ft[4 * v + 1], e = ft[4 * v + 2], q1 = ft[4 * v + 3];
-    double2 sm = cadd(cmul(refl[4 * v + 2], Pp), cmul(refl[4 * v + 3], Qm));   // particle part
-    double2 s1;
-    if (which == LSMS_FIELD_PARTICLE) {
-      s1 = cmul(t21, cadd(Pp, cmul(e, sm)));
-    } else {
-      sm = cadd(sm, cmul(inc[2 * v + 1], I));
-      s1 = cadd(cmul(r11, I), cmul(t21, cadd(Pp, cmul(e, sm))));
-    }
+    // sigma_1 = f_I I + f_P P + f_Q Q (the layer response of every interface, per node)
+    double2 s1 = cadd(cmul(ft[4 * v + 1], Pp), cmul(ft[4 * v + 2], Qm));
+    if (which != LSMS_FIELD_PARTICLE) s1 = cadd(s1, cmul(ft[4 * v], I));
     const double2 ex = cexp_(-g.x * yt - L.y * xt, -g.y * yt + L.x * xt);   // exp(-g1 y + i l x)
-    acc = cfma(cmul(q1, s1), ex, acc);
+    acc = cfma(cmul(ft[4 * v + 3], s1), ex, acc);
   }
   acc = warp_sum(acc);
   if (lane == 0) {
@@ -444,11 +437,10 @@ void launch_combine(const double2* x, const double2* alpha, const double2* s_out
 }
 
 void launch_field(int ns, int ntgt, const double* tgt, double xc, const double2* lam,
-                  const double2* g1, const double2* fieldtab, const double2* inc,
-                  const double2* refl, const double2* pq, const double* src, double k1,
-                  int which, double2* out, cudaStream_t st) {
+                  const double2* g1, const double2* fieldtab, const double2* pq, const double* src,
+                  double k1, int which, double2* out, cudaStream_t st) {
   if (ntgt == 0) return;
   const long long threads = (long long)ntgt * 32;
-  k_field<<<(int)((threads + 127) / 128), 128, 0, st>>>(ns, ntgt, tgt, xc, lam, g1, fieldtab, inc,
-                                                        refl, pq, src, k1, which, out);
+  k_field<<<(int)((threads + 127) / 128), 128, 0, st>>>(ns, ntgt, tgt, xc, lam, g1, fieldtab, pq, src,
+                                                        k1, which, out);
 }

@@ -27,13 +27,19 @@ struct NodeTables {
   std::vector<cplx> g1, g2, g3;     // gamma_i(lambda)
   std::vector<cplx> refl;           // [ns][4]: a11 a12 a21 a22 of sigma2 = a * (P, Q)
   std::vector<cplx> inc;            // [ns][2]: sigma2+ = t1 I, sigma2- = t2 I (particle free)
-  std::vector<cplx> field;          // [ns][4]: R11, tau21, e, w/(4 pi gamma1)
+  std::vector<cplx> field;          // [ns][4]: sigma_1 per unit I, P, Q; w/(4 pi gamma1)
   std::vector<cplx> fagg;           // [2 ns][P]: c_n w-^n (rows < ns), c_n w+^n (rows >= ns)
   std::vector<cplx> udis;           // [2 ns][P]: w/(4 pi g2) i^m w-^m, ... w+^m
 };
 
 struct lsms_ctx {
-  // medium and discretisation
+  // medium and discretisation: layers ks[0] (top) .. ks[L-1] (bottom), interior thicknesses
+  // ds[0..L-3]; the discs lie in layer `layer` (1-based, 2 <= layer <= L-1), whose top interface is
+  // `depth` below y = 0.  k1 = ks[0], k2 = ks[layer-1] (the disc layer), k3 = ks[L-1], d = its
+  // thickness.  Disc centres are kept in the disc layer's own frame (top interface at y = 0).
+  std::vector<double> ks, ds;
+  int layer = 2;
+  double depth = 0.0;
   double k1 = 0, k2 = 0, k3 = 0, d = 0, kp = 0, R = 0;
   int p = 0, P = 0, precision = 0;
   lsms_contour contour{};
@@ -123,7 +129,7 @@ struct lsms_ctx {
 // ------------------------------------------------------------------------------------------
 // Host setup (host_setup.cpp)
 // ------------------------------------------------------------------------------------------
-int build_contour(const lsms_contour& c, double k1, double k2, double k3, std::vector<cplx>& lam,
+int build_contour(const lsms_contour& c, const std::vector<double>& ks, std::vector<cplx>& lam,
                   std::vector<cplx>& wt, std::string& err);
 std::vector<double> contour_panel_breaks(int n_panels, const double* ks, int nk, double b,
                                          double t_max);
@@ -163,6 +169,5 @@ void launch_combine(const double2* x, const double2* alpha, const double2* s_out
                     int nrhs, int n, int P, int alpha_only, cudaStream_t st);
 // field in layer 1 at targets
 void launch_field(int ns, int ntgt, const double* tgt, double xc, const double2* lam,
-                  const double2* g1, const double2* fieldtab, const double2* inc,
-                  const double2* refl, const double2* pq, const double* src, double k1,
-                  int which, double2* out, cudaStream_t st);
+                  const double2* g1, const double2* fieldtab, const double2* pq, const double* src,
+                  double k1, int which, double2* out, cudaStream_t st);

@@ -7,6 +7,9 @@
 #include "lsms_internal.h"
 
 int ctx_fail(lsms_ctx* c, int code, const std::string& msg);
+// context for a stack of layers (ks top to bottom, interior thicknesses ds, discs in `layer`)
+int create_stack(const std::vector<double>& ks, const std::vector<double>& ds, int layer, double kp,
+                 double radius, int p, const lsms_contour* contour, int precision, lsms_ctx** out);
 int ensure(lsms_ctx* c, DevBuf& b, size_t bytes);
 int check_cuda(lsms_ctx* c, const char* where);
 int need_particles(lsms_ctx* c);

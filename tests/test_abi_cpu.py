@@ -109,3 +109,30 @@ def test_seeded_layouts_respect_the_geometry():
     assert np.array_equal(c, inputs.layout(200, -50.0, 50.0, 9))
     assert len(inputs.sweep_sizes()) == 128
     assert min(inputs.sweep_sizes()) >= 200 and max(inputs.sweep_sizes()) <= 4000
+
+
+def test_layer_stack_arguments_are_validated_before_any_device_work(lib):
+    two_pi = 2 * math.pi
+    ks, ds = [two_pi, 2.6 * math.pi, 3 * math.pi, 3.4 * math.pi, 4 * math.pi], [0.5, 2.0, 0.7]
+    bad = [
+        (ks[:2], [], 2),                 # fewer than three layers
+        (ks, ds, 1),                     # discs in the top half-space
+        (ks, ds, 5),                     # discs in the bottom half-space
+        (ks, [0.5, -2.0, 0.7], 3),       # negative thickness
+        (ks, [0.5, 0.4, 0.7], 3),        # radius 0.25 not below half the disc layer (0.2)
+        ([two_pi, -1.0] + ks[2:], ds, 3),
+        (ks, ds[:2], 3),                 # wrong number of thicknesses
+    ]
+    for stack in bad:
+        with pytest.raises(lib.LsmsError) as e:
+            lib.Context(0, 0, 0, 0, 2.4 * math.pi, 0.25, 6, 128, stack=stack)
+        assert e.value.code == -1, stack
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return
+    except ImportError:
+        pass
+    with pytest.raises(lib.LsmsError) as e:         # valid: fails only for want of a GPU
+        lib.Context(0, 0, 0, 0, 2.4 * math.pi, 0.25, 6, 128, stack=(ks, ds, 3))
+    assert e.value.code == -6
