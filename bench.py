@@ -327,9 +327,10 @@ def run_ours(args, rank, world, local_rank):
             solve["speedup_mixed_vs_fp64"] = solve["fp64_s"] / solve["mixed_s"]
             ctxd.close()
     ctx.close()
-    batched = None
+    batched = stack = None
     if world == 1 and not args.no_batched:
         batched = run_batched(args, dev, flush)
+        stack = run_stack(args, w, dev, flush)
 
     if rank != 0:
         return None
@@ -346,6 +347,7 @@ def run_ours(args, rank, world, local_rank):
         "speedup_mixed_vs_fp64": value / fp64_rate,
         "solve": solve,
         "batched": batched,
+        "stack": stack,
         "roofline": {"kernel": "k_translate_f32", "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": traffic, "flop_per_launch": flop, "launch_ms": tr_ms,
@@ -473,6 +475,36 @@ def run_batched(args, dev, flush):
                              "rel_res_fp64_max": info["rel_res_fp64"]}
     b.close()
     out["sweep"] = sw
+    return out
+
+
+def run_stack(args, w, dev, flush):
+    """The bench layout in a five-layer medium (discs in layer 3): mixed operator applications and
+    the mixed solve at 1e-8.  Only the per-node layer response differs from the three-layer run."""
+    import numpy as np
+    import torch
+
+    from paper_1407_3868_gb300 import inputs, lsms
+    st, m = inputs.STACK5, w.medium
+    ctx = lsms.Context(0, 0, 0, 0, m["kp"], m["radius"], w.p, w.n_nodes, b=w.b, t_max=w.t_max,
+                       panel_order=16, precision=lsms.LSMS_MIXED, stack=(st["ks"], st["ds"], st["layer"]))
+    centres = w.centres() - np.array([0.0, inputs.STACK5_DEPTH])
+    ctx.set_particles(centres)
+    x = torch.from_numpy(inputs.random_coefficients(w.n, w.p, 1, 300)).to(dev)
+    y = torch.empty_like(x)
+    fl_m = lsms.APPLY_SCALED | lsms.APPLY_MIXED
+    for _ in range(3):
+        ctx.apply_dev(x, y, fl_m)
+    torch.cuda.synchronize()
+    ms = time_device(lambda: ctx.apply_dev(x, y, fl_m), max(args.steps, 3), flush)
+    out = {"workload": w.name + "_stack5", "wavenumbers": st["ks"], "thicknesses": st["ds"],
+           "particle_layer": st["layer"], "mixed": {"ms_per_apply": ms, "applies_per_s": 1e3 / ms}}
+    if not args.no_solve:
+        t0 = time.perf_counter()
+        _, info = ctx.solve(w.sources, tol=1e-8, maxiter=2000)      # sources stay in layer 1
+        out["mixed_solve"] = {"tol": 1e-8, "s": time.perf_counter() - t0, "iters": info["iters"],
+                              "refinements": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"]}
+    ctx.close()
     return out
 
 

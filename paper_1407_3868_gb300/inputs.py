@@ -21,6 +21,12 @@ import numpy as np
 # Medium shared by every workload: k1 = 2 pi, k2 = 3 pi, k3 = 4 pi, d = 2, discs kp = 2.4 pi, R = 0.25.
 MEDIUM = dict(k1=2.0 * math.pi, k2=3.0 * math.pi, k3=4.0 * math.pi, d=2.0,
               kp=2.4 * math.pi, radius=0.25)
+# Five layers (top to bottom): the three-layer medium's k1 and k3 at the ends, two extra layers
+# (k = 2.6 pi above, 3.4 pi below) around the disc layer (k2, thickness d); discs in layer 3, whose
+# top interface lies 0.5 below y = 0, so layout centres move down by STACK5_DEPTH.
+STACK5 = dict(ks=[2.0 * math.pi, 2.6 * math.pi, 3.0 * math.pi, 3.4 * math.pi, 4.0 * math.pi],
+              ds=[0.5, 2.0, 0.7], layer=3)
+STACK5_DEPTH = 0.5
 GAP = 0.1            # minimum edge-to-edge gap between discs
 CLEARANCE = 0.05     # minimum distance from a disc edge to either interface
 AREA_FRACTION = 0.2  # area fraction used to widen the large layouts

@@ -21,10 +21,10 @@ TOL64 = 1e-10
 TOL_MIXED_OP = 2e-5
 TOL_MIXED = 1e-8
 
-KS = [2 * math.pi, 2.6 * math.pi, 3 * math.pi, 3.4 * math.pi, 4 * math.pi]
-DS = [0.5, 2.0, 0.7]
-LAYER = 3
-DEPTH = 0.5
+KS = inputs.STACK5["ks"]
+DS = inputs.STACK5["ds"]
+LAYER = inputs.STACK5["layer"]
+DEPTH = inputs.STACK5_DEPTH
 KP, RADIUS = 2.4 * math.pi, 0.25
 
 
