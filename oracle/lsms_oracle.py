@@ -12,6 +12,9 @@ for multi-particle scattering in a layered medium"):
   "layer21", "layer22", "layer3") and the 4x4 mode-by-mode interface system A_lambda
   (Eq. "sommerfeldsys");
 * the scattering matrix of a dielectric disc from its 2x2 mode system (Sec. 3.1, Eq. "linear");
+* the scattering matrix of an inclusion of any smooth shape from Muller's second-kind system
+  (Sec. 4, Eqs. "intg1", "intg2"), discretised by Nystrom with Kress's product rule for the
+  logarithmic singularities, and its rotated copies (Sec. 4.1);
 * Graf's multipole-to-local translation (Sec. 3.2, Lemma 3.1 / Eq. "trans");
 * the multipole-to-Sommerfeld map (Sec. 5.3, Theorem 5.2) and the Sommerfeld-to-local map by
   Jacobi-Anger (Sec. 5.2.1, Lemma 5.1, Eq. "JA2");
@@ -178,6 +181,174 @@ def order_scale(p: int, k2: float, radius: float) -> np.ndarray:
     """|H_n(k2 R)|, n = -p..p: the diagonal that makes every order O(1) on the disc boundary."""
     n = np.arange(-p, p + 1)
     return np.abs(hankel(n, k2 * radius))
+
+
+# ----------------------------------------------------------------------------------------------
+# Inclusions of any smooth shape (Sec. 4: Eqs. "rep1", "rep2", "intg1", "intg2"; Sec. 4.1)
+# ----------------------------------------------------------------------------------------------
+EULER_GAMMA = 0.57721566490153286061
+
+
+def kress_log_weights(n_pts: int) -> np.ndarray:
+    """Weights R_j of the product rule  int_0^2pi ln(4 sin^2((t_i - tau)/2)) f(tau) d tau
+    ~ sum_j R_{(i - j) mod n_pts} f(t_j),  t_j = 2 pi j / n_pts  (exact for trigonometric
+    polynomials of degree < n_pts / 2: Kress's quadrature for logarithmic singularities, used here
+    in place of Alpert's hybrid Gauss-trapezoidal rule; reading of Sec. 4's remark).
+
+    With n = n_pts / 2:  R_j = -(2 pi / n) sum_{m=1}^{n-1} cos(m t_j) / m - (pi / n^2) cos(n t_j).
+    """
+    if n_pts < 4 or n_pts % 2:
+        raise ValueError("kress_log_weights: need an even number of points >= 4")
+    n = n_pts // 2
+    tj = 2.0 * np.pi * np.arange(n_pts) / n_pts
+    m = np.arange(1, n)
+    return (-(2.0 * np.pi / n) * (np.cos(np.outer(tj, m)) / m[None, :]).sum(axis=1)
+            - (np.pi / n ** 2) * np.cos(n * tj))
+
+
+def _kernels(curve, k: float):
+    """Parametrised kernels of the four boundary operators for wavenumber k, split as
+    M(t, tau) = M1(t, tau) ln(4 sin^2((t - tau)/2)) + M2(t, tau), off the diagonal.
+
+    G = (i/4) H_0(k r);  S: G;  D (at the boundary, principal value): dG/dn_y;  N: dG/dn_x;
+    T: d^2 G / dn_x dn_y.  ds_y = |x'(tau)| d tau is folded in.  M1 is the coefficient of ln r
+    halved (ln r = ln(4 sin^2)/2 + smooth), taken from the J_0, J_1 parts of H_0 = J_0 (1 +
+    (2i/pi) ln(k r / 2)) + ..., H_1 = J_1 (1 + (2i/pi) ln(k r / 2)) - 2i/(pi k r) + ....
+    Returns dicts of (n_pts, n_pts) arrays with the diagonal left at zero.
+    """
+    x, dx, ddx = curve
+    n_pts = x.shape[0]
+    d = x[:, None, :] - x[None, :, :]                  # x(t_i) - x(t_j)
+    r = np.hypot(d[..., 0], d[..., 1])
+    off = ~np.eye(n_pts, dtype=bool)
+    r_safe = np.where(off, r, 1.0)
+    sp = np.hypot(dx[:, 0], dx[:, 1])                  # |x'|
+    nu = np.stack([dx[:, 1], -dx[:, 0]], axis=1)       # |x'| n (outward for counterclockwise)
+    nx = nu / sp[:, None]
+    nx_d = np.einsum("ik,ijk->ij", nx, d)              # n(t_i) . (x_i - x_j)
+    nuy_d = np.einsum("jk,ijk->ij", nu, d)             # |x'_j| n(t_j) . (x_i - x_j)
+    nx_nuy = nx @ nu.T                                 # n(t_i) . |x'_j| n(t_j)
+    z = k * r_safe
+    h0, h1 = special.hankel1(0, z), special.hankel1(1, z)
+    j0, j1 = special.jv(0, z), special.jv(1, z)
+    sp_j = sp[None, :]
+    out = {}
+    out["S"] = (0.25j * h0 * sp_j, -(1.0 / FOUR_PI) * j0 * sp_j)
+    out["D"] = (0.25j * k * h1 * nuy_d / r_safe, -(k / FOUR_PI) * j1 * nuy_d / r_safe)
+    out["N"] = (-0.25j * k * h1 * nx_d / r_safe * sp_j, (k / FOUR_PI) * j1 * nx_d / r_safe * sp_j)
+    a_full = k * k * h0 / r_safe ** 2 - 2.0 * k * h1 / r_safe ** 3
+    a_reg = k * k * j0 / r_safe ** 2 - 2.0 * k * j1 / r_safe ** 3
+    out["T"] = (0.25j * (a_full * nx_d * nuy_d + k * h1 / r_safe * nx_nuy),
+                -(1.0 / FOUR_PI) * (a_reg * nx_d * nuy_d + k * j1 / r_safe * nx_nuy))
+    res = {}
+    for key, (m, m1) in out.items():
+        m = np.where(off, m, 0.0)
+        m1 = np.where(off, m1, 0.0)
+        res[key] = (m, m1)
+    return res, sp
+
+
+def muller_matrix(curve, k2: float, kp: float) -> np.ndarray:
+    """Nystrom matrix of Eqs. "intg1", "intg2" in the unknowns [mu; sigma] (2 n_pts):
+
+        mu + (S^{k2} - S^{kp}) sigma + (D^{k2} - D^{kp}) mu            = -u_inc
+        -sigma + (N^{k2} - N^{kp}) sigma + (T^{k2} - T^{kp}) mu         = -du_inc/dn
+
+    Each difference kernel is at most logarithmically singular; it is integrated with the weights
+    R_j against its log part M1 and with the trapezoidal rule (2 pi / n_pts) against M2 = M - M1 L.
+    Diagonal limits of the differences (C = Euler's constant, s = |x'(t)|):
+      S: M1 = -(s / 4 pi)(J_0 terms cancel to 0 in the difference), M2 = -(s / 2 pi) ln(k2 / kp);
+      D, N: M1 = M2 = 0;
+      T: M1 = -(k2^2 - kp^2) s / (8 pi),
+         M2 = s [ (i/8 + (1 - 2C)/(8 pi)) (k2^2 - kp^2) - (k2^2 ln(k2 s / 2) - kp^2 ln(kp s / 2)) / (4 pi) ].
+    """
+    x = curve[0]
+    n_pts = x.shape[0]
+    kw = kress_log_weights(n_pts)
+    idx = (np.arange(n_pts)[:, None] - np.arange(n_pts)[None, :]) % n_pts
+    Rw = kw[idx]
+    tt = 2.0 * np.pi * np.arange(n_pts) / n_pts
+    L = np.log(np.where(np.eye(n_pts, dtype=bool), 1.0, 4.0 * np.sin((tt[:, None] - tt[None, :]) / 2) ** 2))
+    ka, sp = _kernels(curve, k2)
+    kb, _ = _kernels(curve, kp)
+    h = 2.0 * np.pi / n_pts
+    diag = np.arange(n_pts)
+    mats = {}
+    dk2 = k2 * k2 - kp * kp
+    for key in ("S", "D", "N", "T"):
+        m = ka[key][0] - kb[key][0]
+        m1 = ka[key][1] - kb[key][1]
+        m2 = m - m1 * L
+        if key == "S":
+            m1[diag, diag] = 0.0
+            m2[diag, diag] = -(sp / (2.0 * np.pi)) * np.log(k2 / kp)
+        elif key == "T":
+            m1[diag, diag] = -dk2 * sp / (8.0 * np.pi)
+            m2[diag, diag] = sp * ((0.125j + (1.0 - 2.0 * EULER_GAMMA) / (8.0 * np.pi)) * dk2
+                                   - (k2 * k2 * np.log(k2 * sp / 2.0) - kp * kp * np.log(kp * sp / 2.0))
+                                   / FOUR_PI)
+        else:
+            m1[diag, diag] = 0.0
+            m2[diag, diag] = 0.0
+        mats[key] = Rw * m1 + h * m2
+    eye = np.eye(n_pts)
+    return np.block([[eye + mats["D"], mats["S"]], [mats["T"], -eye + mats["N"]]])
+
+
+def regular_wave_traces(curve, k: float, n: int):
+    """J_n(k rho) e^{i n theta} and its normal derivative at the curve points (polar coordinates
+    about the enclosing disc's centre, the origin)."""
+    x, dx, _ = curve
+    rho = np.hypot(x[:, 0], x[:, 1])
+    th = np.arctan2(x[:, 1], x[:, 0])
+    sp = np.hypot(dx[:, 0], dx[:, 1])
+    nrm = np.stack([dx[:, 1], -dx[:, 0]], axis=1) / sp[:, None]
+    n_rho = (nrm[:, 0] * np.cos(th) + nrm[:, 1] * np.sin(th))
+    n_th = (-nrm[:, 0] * np.sin(th) + nrm[:, 1] * np.cos(th))
+    e = np.exp(1j * n * th)
+    u = bessel(n, k * rho) * e
+    du = (k * bessel_p(n, k * rho) * n_rho + 1j * n / rho * bessel(n, k * rho) * n_th) * e
+    return u, du
+
+
+def outgoing_from_densities(curve, k2: float, sigma, mu, p: int) -> np.ndarray:
+    """beta_l, l = -p..p, of u^s = S^{k2} sigma + D^{k2} mu outside the enclosing disc (Sec. 4.1):
+    beta_l = (i/4) int [J_l(k2 |y|) e^{-i l theta_y} sigma + n_y . grad(J_l(k2 |y|) e^{-i l theta_y}) mu] ds_y
+    (Graf's addition theorem for G = (i/4) H_0), by the trapezoidal rule."""
+    x, dx, _ = curve
+    n_pts = x.shape[0]
+    h = 2.0 * np.pi / n_pts
+    sp = np.hypot(dx[:, 0], dx[:, 1])
+    out = np.zeros(2 * p + 1, dtype=complex)
+    for l in range(-p, p + 1):
+        u, du = regular_wave_traces(curve, k2, -l)        # J_{-l} e^{-i l theta} = (-1)^l J_l e^{-i l theta}
+        sgn = (-1.0) ** l
+        out[l + p] = 0.25j * h * np.sum(sgn * (u * sigma + du * mu) * sp)
+    return out
+
+
+def inclusion_scattering_matrix(curve, p: int, k2: float, kp: float) -> np.ndarray:
+    """S[l + p, n + p] = beta^n_l: outgoing coefficients of the inclusion for the incoming wave
+    J_n(k2 r) e^{i n theta} (Sec. 4.1), by one LU of the Muller matrix and 2p + 1 solves."""
+    a = muller_matrix(curve, k2, kp)
+    n_pts = curve[0].shape[0]
+    S = np.zeros((2 * p + 1, 2 * p + 1), dtype=complex)
+    lu = __import__("scipy.linalg", fromlist=["lu_factor"])
+    fac = lu.lu_factor(a)
+    for n in range(-p, p + 1):
+        u, du = regular_wave_traces(curve, k2, n)
+        sol = lu.lu_solve(fac, np.concatenate([-u, -du]))
+        mu, sigma = sol[:n_pts], sol[n_pts:]
+        S[:, n + p] = outgoing_from_densities(curve, k2, sigma, mu, p)
+    return S
+
+
+def rotate_scattering_matrix(S: np.ndarray, theta: float) -> np.ndarray:
+    """Scattering matrix of the prototype turned by theta about its centre (Sec. 4.1):
+    S_theta[l, n] = e^{-i l theta} S[l, n] e^{i n theta}."""
+    p = (S.shape[0] - 1) // 2
+    e = np.exp(1j * np.arange(-p, p + 1) * theta)
+    return np.conj(e)[:, None] * S * e[None, :]
 
 
 # ----------------------------------------------------------------------------------------------
@@ -409,7 +580,7 @@ class Problem:
     (1/4pi) sum_nu w_nu (...) over the same nodes.
     """
 
-    def __init__(self, medium: Medium, p: int, centres: np.ndarray, lam, wt):
+    def __init__(self, medium: Medium, p: int, centres: np.ndarray, lam, wt, smat=None, theta=None):
         self.m = medium
         self.p = p
         self.P = 2 * p + 1
@@ -419,6 +590,21 @@ class Problem:
         self.wt = np.asarray(wt, dtype=complex)
         self.S = mie_coefficients(p, medium.k2, medium.kp, medium.radius)
         self.orders = np.arange(-p, p + 1)
+        # inclusions of another shape (Sec. 4.1): one scattering matrix per particle, the
+        # prototype's turned by that particle's angle
+        self.smats = None
+        if smat is not None:
+            th = np.zeros(self.N) if theta is None else np.asarray(theta, dtype=float)
+            self.smats = np.stack([rotate_scattering_matrix(np.asarray(smat), a) for a in th]) \
+                if self.N else np.zeros((0, self.P, self.P), dtype=complex)
+
+    def scatter(self, alpha, rows=None):
+        """S_j alpha^j for every particle j (or the listed rows)."""
+        alpha = np.asarray(alpha)
+        if self.smats is None:
+            return self.S[None, :] * alpha
+        sm = self.smats if rows is None else self.smats[list(rows)]
+        return np.einsum("jln,jn->jl", sm, alpha)
 
     # --- (a2) free-space translation --------------------------------------------------------
     def translation(self, beta, rows=None):
@@ -481,7 +667,7 @@ class Problem:
         if "R" in parts:
             alpha += self.reflection(x, rows)
         xr = x if rows is None else x[list(rows)]
-        return xr - self.S[None, :] * alpha
+        return xr - self.scatter(alpha, rows)
 
     # --- (a8) incident local expansions ---------------------------------------------------------
     def incident_local(self, src, rows=None):
@@ -491,7 +677,7 @@ class Problem:
         return self.disaggregate(sig[:, 1], sig[:, 2], rows)
 
     def rhs(self, src):
-        return self.S[None, :] * self.incident_local(src)
+        return self.scatter(self.incident_local(src))
 
     # --- dense assembly and solves (Eq. "finalsys", Eq. "schur") ----------------------------------
     def dense_operator(self):
@@ -546,15 +732,22 @@ class Problem:
             ct = np.exp(g2 * yj + 1j * lam * xj)
             cb = np.exp(-g2 * (yj + d) + 1j * lam * xj)
             rows = slice(j * P, (j + 1) * P)
-            C[rows, 1::4] = (self.S[:, None] * (q * ct)[None, :] * l_top.T)
-            C[rows, 2::4] = (self.S[:, None] * (q * cb)[None, :] * l_bot.T)
+            sj = np.diag(self.S) if self.smats is None else self.smats[j]
+            C[rows, 1::4] = sj @ ((q * ct)[None, :] * l_top.T)
+            C[rows, 2::4] = sj @ ((q * cb)[None, :] * l_bot.T)
         T = np.zeros((N * P, N * P), dtype=complex)
         for l in range(N):
             for m in range(N):
                 if l != m:
                     T[l * P:(l + 1) * P, m * P:(m + 1) * P] = translation_matrix(
                         self.c[l], self.c[m], k2, self.p, self.p)
-        D = np.tile(self.S, N)[:, None] * T - np.eye(N * P)
+        if self.smats is None:
+            D = np.tile(self.S, N)[:, None] * T - np.eye(N * P)
+        else:
+            sblk = np.zeros((N * P, N * P), dtype=complex)
+            for j in range(N):
+                sblk[j * P:(j + 1) * P, j * P:(j + 1) * P] = self.smats[j]
+            D = sblk @ T - np.eye(N * P)
         inc = self.m.incident_density(lam, src)
         b = self.m.rhs(lam, inc=inc).ravel()
         return A, B, C, D, b

@@ -169,3 +169,31 @@ def random_coefficients(n: int, p: int, nrhs: int = 1, seed: int = 0) -> np.ndar
 def observation_points(x_lo: float, x_hi: float, n: int, y: float) -> np.ndarray:
     """n points evenly spaced on the horizontal line at height y, endpoints included."""
     return _targets(x_lo, x_hi, n, y)
+
+
+# ------------------------------------------------------------------------------------------------
+# Inclusion shapes (the star-shaped family of Sec. 6, Eq. "par1") and orientations
+# ------------------------------------------------------------------------------------------------
+# The pentagon-like inclusion used with the bench layout: radius 0.15 +- 0.05 (inside the
+# enclosing disc of radius 0.25), five lobes, 256 boundary points.
+STAR5 = dict(a1=0.15, a2=0.05, a3=5, n_pts=256)
+
+
+def star_curve(a1: float, a2: float, a3: int, n_pts: int, rotation: float = 0.0,
+               centre=(0.0, 0.0)):
+    """Points, first and second derivatives of x(t) = c + (a1 + a2 cos(a3 t)) (cos(t + rot),
+    sin(t + rot)) at t_j = 2 pi j / n_pts (counterclockwise).  Returns three (n_pts, 2) arrays."""
+    t = 2.0 * np.pi * np.arange(n_pts) / n_pts
+    r = a1 + a2 * np.cos(a3 * t)
+    dr = -a2 * a3 * np.sin(a3 * t)
+    ddr = -a2 * a3 * a3 * np.cos(a3 * t)
+    ct, st = np.cos(t + rotation), np.sin(t + rotation)
+    x = np.stack([centre[0] + r * ct, centre[1] + r * st], axis=1)
+    dx = np.stack([dr * ct - r * st, dr * st + r * ct], axis=1)
+    ddx = np.stack([ddr * ct - 2.0 * dr * st - r * ct, ddr * st + 2.0 * dr * ct - r * st], axis=1)
+    return x, dx, ddx
+
+
+def orientations(n: int, seed: int) -> np.ndarray:
+    """n rotation angles, uniform on [0, 2 pi) (NumPy PCG64, default_rng(seed))."""
+    return np.random.default_rng(seed).uniform(0.0, 2.0 * np.pi, n)

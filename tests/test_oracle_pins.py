@@ -416,3 +416,137 @@ def test_oracle_gmres_matches_lu():
     x, it, hist = O.gmres(lambda v: pr.apply(v).ravel(), pr.rhs(src).ravel(), tol=1e-13, maxiter=200)
     assert hist[-1] <= 1e-13
     assert np.allclose(x.reshape(beta.shape), beta, rtol=1e-9, atol=1e-10 * np.abs(beta).max())
+
+
+# ---------------------------------------------------------------------------------------------
+# Inclusions of any smooth shape (Sec. 4): Muller's system, Kress's log quadrature, S matrix
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.filterwarnings("ignore::scipy.integrate.IntegrationWarning")
+def test_kress_log_weights_integrate_the_log_kernel():
+    # int_0^2pi ln(4 sin^2((t - tau)/2)) cos(m tau) d tau = -(2 pi / m) cos(m t) (m >= 1), 0 (m = 0)
+    n_pts = 32
+    w = O.kress_log_weights(n_pts)
+    tj = 2 * np.pi * np.arange(n_pts) / n_pts
+    for i in (0, 5):
+        for m in (0, 1, 4, 15):
+            got = np.sum(w[(i - np.arange(n_pts)) % n_pts] * np.cos(m * tj))
+            want = 0.0 if m == 0 else -(2 * np.pi / m) * np.cos(m * tj[i])
+            assert abs(got - want) < 1e-12, (i, m)
+    # a smooth non-polynomial density against adaptive quadrature of the singular integral
+    f = lambda s: np.exp(np.cos(s)) * (1 + 0.3 * np.sin(2 * s))
+    n_pts = 64
+    w = O.kress_log_weights(n_pts)
+    tj = 2 * np.pi * np.arange(n_pts) / n_pts
+    t0 = tj[3]
+    # ln(4 sin^2(u/2)) = 2 ln|u| + ln(4 sin^2(u/2) / u^2), the second smooth for |u| < 2 pi;
+    # the log part by QUADPACK's algebraic-logarithmic weights on either side of t0
+    q = dict(limit=200, epsabs=1e-14, epsrel=1e-14)
+    ref = 2 * (integrate.quad(f, 0, t0, weight="alg-logb", wvar=(0, 0), **q)[0]
+               + integrate.quad(f, t0, 2 * np.pi, weight="alg-loga", wvar=(0, 0), **q)[0])
+    smooth = lambda s: np.log(4 * np.sin((t0 - s) / 2) ** 2 / (t0 - s) ** 2) if s != t0 else 0.0
+    ref += integrate.quad(lambda s: smooth(s) * f(s), 0, 2 * np.pi, points=[t0], **q)[0]
+    got = np.sum(w[(3 - np.arange(n_pts)) % n_pts] * f(tj))
+    assert abs(got - ref) < 1e-12
+
+
+@pytest.mark.parametrize("radius,kp", [(0.2, 2.4 * math.pi), (0.25, 1.5 * math.pi), (0.1, 5.0 * math.pi)])
+def test_inclusion_matrix_of_a_centred_circle_is_the_mie_diagonal(radius, kp):
+    k2, p = MED["k2"], 10
+    S = O.inclusion_scattering_matrix(inputs.star_curve(radius, 0.0, 0, 128), p, k2, kp)
+    mie = O.mie_coefficients(p, k2, kp, radius)
+    assert np.abs(np.diag(S) - mie).max() < 1e-13
+    assert np.abs(S - np.diag(np.diag(S))).max() < 1e-13
+
+
+def test_inclusion_matrix_of_an_off_centre_circle_is_the_translated_mie_matrix():
+    # a circle of radius a centred at c: regular waves re-expanded about c, Mie there, outgoing
+    # waves re-expanded about the origin (Graf), both addition theorems checked here first
+    k2, kp, p, a = MED["k2"], 2.4 * math.pi, 8, 0.12
+    c = np.array([0.05, 0.03])
+    rc, pc = np.hypot(*c), math.atan2(c[1], c[0])
+    x = np.array([0.31, -0.22])
+    xr, xth = np.hypot(*x), math.atan2(x[1], x[0])
+    xp = x - c
+    xpr, xpth = np.hypot(*xp), math.atan2(xp[1], xp[0])
+    mm = np.arange(-40, 41)
+    for n in (-3, 0, 2):
+        lhs = O.bessel(n, k2 * xr) * np.exp(1j * n * xth)
+        rhs = np.sum(O.bessel(n - mm, k2 * rc) * np.exp(1j * (n - mm) * pc) * O.bessel(mm, k2 * xpr)
+                     * np.exp(1j * mm * xpth))
+        assert abs(lhs - rhs) < 1e-13
+        lhs = O.hankel(n, k2 * xpr) * np.exp(1j * n * xpth)
+        rhs = np.sum(O.bessel(mm - n, k2 * rc) * np.exp(-1j * (mm - n) * pc) * O.hankel(mm, k2 * xr)
+                     * np.exp(1j * mm * xth))
+        assert abs(lhs - rhs) < 1e-12
+    q = 24
+    mie = O.mie_coefficients(q, k2, kp, a)
+    m = np.arange(-q, q + 1)
+    ords = np.arange(-p, p + 1)
+    Jin = O.bessel(ords[None, :] - m[:, None], k2 * rc) * np.exp(1j * (ords[None, :] - m[:, None]) * pc)
+    Jout = O.bessel(ords[:, None] - m[None, :], k2 * rc) * np.exp(-1j * (ords[:, None] - m[None, :]) * pc)
+    want = Jout @ (mie[:, None] * Jin)
+    S = O.inclusion_scattering_matrix(inputs.star_curve(a, 0.0, 0, 128, centre=c), p, k2, kp)
+    assert np.abs(S - want).max() < 1e-12 * np.abs(want).max()
+
+
+@pytest.fixture(scope="module")
+def star5_matrix():
+    k2, kp, p = MED["k2"], MED["kp"], 10
+    s = inputs.STAR5
+    return O.inclusion_scattering_matrix(inputs.star_curve(s["a1"], s["a2"], s["a3"], 256), p, k2, kp)
+
+
+def test_inclusion_matrix_symmetries_and_energy(star5_matrix):
+    S = star5_matrix
+    p = (S.shape[0] - 1) // 2
+    l = np.arange(-p, p + 1)
+    sg = (-1.0) ** (l[:, None] + l[None, :])
+    big = np.abs(S).max()
+    # five-fold rotational symmetry: S[l, n] = 0 unless l = n mod 5
+    assert np.abs(S[((l[:, None] - l[None, :]) % 5) != 0]).max() < 1e-13 * big
+    assert np.abs(S[((l[:, None] - l[None, :]) % 5) == 0]).min() >= 0.0
+    # mirror symmetry about the x-axis: S[l, n] = (-1)^(l+n) S[-l, -n]
+    assert np.abs(S - sg * S[::-1, ::-1]).max() < 1e-13 * big
+    # reciprocity: S[l, n] = (-1)^(l+n) S[-n, -l]
+    assert np.abs(S - sg * S[::-1, ::-1].T).max() < 1e-13 * big
+    # lossless media: I + 2 S is unitary (outgoing power = incoming power, mode by mode)
+    U = np.eye(S.shape[0]) + 2 * S
+    assert np.abs(U.conj().T @ U - np.eye(S.shape[0])).max() < 1e-12
+    # a genuinely non-circular inclusion couples orders 5 apart
+    allowed = (((l[:, None] - l[None, :]) % 5) == 0) & (l[:, None] != l[None, :])
+    assert np.abs(S[allowed]).max() > 1e-3 * big
+
+
+def test_inclusion_matrix_converges_and_rotates(star5_matrix):
+    k2, kp, p = MED["k2"], MED["kp"], 10
+    s = inputs.STAR5
+    S512 = O.inclusion_scattering_matrix(inputs.star_curve(s["a1"], s["a2"], s["a3"], 512), p, k2, kp)
+    assert np.abs(S512 - star5_matrix).max() < 1e-12
+    th = 0.37
+    Sr = O.inclusion_scattering_matrix(inputs.star_curve(s["a1"], s["a2"], s["a3"], 256, rotation=th),
+                                       p, k2, kp)
+    assert np.abs(Sr - O.rotate_scattering_matrix(star5_matrix, th)).max() < 1e-12
+    # a wrong sign in the rotation would be caught: the matrix is not rotation invariant
+    assert np.abs(Sr - O.rotate_scattering_matrix(star5_matrix, -th)).max() > 1e-3
+
+
+def test_problem_with_inclusion_matrices():
+    # (i) circles as dense matrices reproduce the disc problem; (ii) rotated star inclusions: the
+    # preconditioned system and the block system of Eq. "finalsys" give the same solution
+    m = O.Medium(MED["k1"], MED["k2"], MED["k3"], MED["d"], MED["kp"], MED["radius"])
+    p, src = 6, np.array([0.1, 1.0])
+    c = inputs.layout(5, -1.5, 1.5, 3)
+    lam, wt = O.contour(128, m.k1, m.k2, m.k3, 0.2, 80.0)
+    disc = O.Problem(m, p, c, lam, wt)
+    circ = O.Problem(m, p, c, lam, wt, smat=np.diag(disc.S), theta=inputs.orientations(5, 1))
+    x = inputs.random_coefficients(5, p, 1, 2)[0]
+    assert np.allclose(circ.apply(x), disc.apply(x), rtol=0, atol=1e-14 * np.abs(x).max())
+    s = inputs.STAR5
+    S = O.inclusion_scattering_matrix(inputs.star_curve(s["a1"], s["a2"], s["a3"], 128), p, m.k2, m.kp)
+    pr = O.Problem(m, p, c, lam, wt, smat=S, theta=inputs.orientations(5, 1))
+    b1 = pr.solve_dense(src)
+    _, b2 = pr.solve_block(src)
+    b3 = pr.solve_schur(src)
+    assert np.allclose(b1, b2, rtol=0, atol=1e-11 * np.abs(b1).max())
+    assert np.allclose(b1, b3, rtol=0, atol=1e-11 * np.abs(b1).max())
+    assert np.abs(b1 - disc.solve_dense(src)).max() > 1e-3 * np.abs(b1).max()
