@@ -250,6 +250,44 @@ int lsms_last_timing(lsms_ctx* ctx, double* ms_translate, double* ms_reflect, in
 int lsms_translate_mixed_noalloc(int n, int p, double k2, int nrhs, const double* centres_xy,
                                  const double* beta, double* alpha, void* stream);
 
+/* Inclusions of any smooth shape (Sec. 4; Sec. 4.1 "The scattering matrix").
+ *
+ * lsms_set_scattering_matrix — replace the disc's Mie diagonal by a dense prototype matrix:
+ *   s: [P][P] complex (row l = outgoing order, column n = incoming order, orders -p..p), the
+ *   outgoing coefficients beta_l of the prototype for the incoming wave J_n(k2 r) e^{i n theta}
+ *   (e.g. from lsms_inclusion_scattering_matrix).  Every particle j then scatters with
+ *   S_j[l][n] = e^{-i l theta_j} S[l][n] e^{i n theta_j} (theta_j from lsms_set_orientations, else 0)
+ *   in lsms_apply*, lsms_solve and the batched forms.  The radius given at creation is the
+ *   enclosing disc's: each inclusion must lie inside it, and the geometry rules of
+ *   lsms_set_particles apply to the enclosing discs.  s = NULL restores the Mie diagonal.
+ *   Copied; may be called before or after lsms_set_particles / lsms_set_layouts.
+ *   Errors: LSMS_ERR_ARG (non-finite entry), LSMS_ERR_OOM.
+ * lsms_set_orientations — rotation angles theta_j (radians, counterclockwise) of the n particles
+ *   (n = lsms_num_particles; for a batch of layouts, all layouts' particles in order).  NULL: all
+ *   zero.  lsms_set_particles / lsms_set_layouts reset them to zero.  Errors: LSMS_ERR_ARG (n or a
+ *   non-finite angle), LSMS_ERR_STATE (no particles yet).
+ * lsms_get_scattering_matrix — the prototype matrix in use ([P][P] complex; the Mie diagonal as a
+ *   diagonal matrix unless one was set).  lsms_get_scattering returns its diagonal. */
+int lsms_set_scattering_matrix(lsms_ctx* ctx, const double* s);
+int lsms_set_orientations(lsms_ctx* ctx, int n, const double* theta);
+int lsms_get_scattering_matrix(const lsms_ctx* ctx, double* s);
+
+/* lsms_inclusion_scattering_matrix — host only, no context.  The scattering matrix of a homogeneous
+ *   inclusion (wavenumber kp) in the layer of wavenumber k2 (Sec. 4): Muller's second-kind system
+ *   (Eqs. "intg1", "intg2") for the unknowns mu, sigma of u^s = S^{k2} sigma + D^{k2} mu outside,
+ *   u = S^{kp} sigma + D^{kp} mu inside, solved by Nystrom discretisation with Kress's product rule
+ *   for the logarithmic singularities of the difference kernels (spectrally accurate for smooth
+ *   boundaries; the paper uses Alpert's hybrid Gauss-trapezoidal rule) for the 2p+1 incoming waves
+ *   J_n(k2 r) e^{i n theta}; beta_l from Graf's theorem (Sec. 4.1).
+ *   curve: [n_pts][6] doubles x, y, x', y', x'', y'' at t_j = 2 pi j / n_pts of a smooth closed
+ *   curve run counterclockwise, coordinates relative to the enclosing disc's centre; n_pts even,
+ *   8 <= n_pts <= 4096 (about 256 gives 1e-13 for the shapes of Sec. 6); radius: the enclosing
+ *   disc's.  s_out: [P][P] complex as for lsms_set_scattering_matrix.  O(n_pts^3) host work.
+ *   Errors: LSMS_ERR_ARG (arguments, a clockwise or degenerate curve, a singular system),
+ *   LSMS_ERR_GEOMETRY (a point outside the enclosing disc or at its centre). */
+int lsms_inclusion_scattering_matrix(int p, double k2, double kp, double radius, int n_pts,
+                                     const double* curve, double* s_out);
+
 /* Host-only helpers: no GPU needed, no context.
  * lsms_build_contour — the nodes and weights lsms_create would use for `contour` (see
  *   lsms_contour; Sec. 5.1 Eq. "sommerseg"); nodes, weights: contour->n_nodes complex each.

@@ -128,8 +128,11 @@ int apply_device(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags,
     launches += mixed ? 5 : 3;   // split, GEMM, per-node stage, GEMM, add / GEMM, stage, GEMM
   }
   if (c->timing) cudaEventRecord(c->ev[2], st);
-  launch_combine(x, alpha, c->d_scale_out + mode * P, y, nrhs, n, P,
-                 (flags & LSMS_APPLY_ALPHA) ? 1 : 0, st);
+  if (c->dense && !(flags & LSMS_APPLY_ALPHA))
+    launch_scatter_dense(x, alpha, c->d_smt + (size_t)mode * P * P,
+                         c->has_theta ? (const double*)c->theta_buf.ptr : nullptr, nrhs, n, P, y, st);
+  else
+    launch_combine(x, alpha, c->d_scale_out + mode * P, y, nrhs, n, P, (flags & LSMS_APPLY_ALPHA) ? 1 : 0, st);
   ++launches;
   c->last_launches = launches;
   return check_cuda(c, "apply");
@@ -235,12 +238,13 @@ extern "C" void lsms_destroy(lsms_ctx* c) {
   batch_free(c);
   void* ptrs[] = {c->d_lam, c->d_g1, c->d_g2, c->d_refl, c->d_inc, c->d_field, c->d_fagg, c->d_udis,
                   c->d_scale_in, c->d_hscale, c->d_scale_out, c->d_cx, c->d_cy, c->d_eagg, c->d_edis,
-                  c->d_eagg_lp, c->d_edis_lp, c->d_lp_misc, c->d_near_ptr, c->d_near_idx, c->d_near_h};
+                  c->d_eagg_lp, c->d_edis_lp, c->d_lp_misc, c->d_near_ptr, c->d_near_idx, c->d_near_h,
+                  c->d_smt};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   DevBuf* bufs[] = {&c->ws_x, &c->ws_y, &c->ws_xs, &c->ws_alpha, &c->ws_g, &c->ws_v, &c->ws_pq,
                     &c->ws_sig, &c->ws_aux, &c->gm_v, &c->gm_h, &c->gm_small, &c->gm_x, &c->gm_r,
-                    &c->gm_w, &c->sol, &c->ws_lp, &c->ws_tcb, &c->gm_b, &c->gm_mask, &c->gm_off};
+                    &c->gm_w, &c->sol, &c->ws_lp, &c->ws_tcb, &c->gm_b, &c->gm_mask, &c->gm_off, &c->theta_buf};
   for (DevBuf* b : bufs)
     if (b->ptr) cudaFree(b->ptr);
   tc_free(c);
@@ -284,6 +288,7 @@ extern "C" int lsms_set_particles(lsms_ctx* c, int n, const double* xy) {
   c->d_lp_misc = nullptr;
   c->n = n;
   c->n_src = 0;
+  c->has_theta = false;                      // orientations refer to the previous particles
   const size_t nb = (size_t)(n > 0 ? n : 1) * sizeof(double);
   const size_t eb = (size_t)2 * c->ns * (n > 0 ? n : 1) * sizeof(double2);
   if (cudaMalloc((void**)&c->d_cx, nb) != cudaSuccess || cudaMalloc((void**)&c->d_cy, nb) != cudaSuccess ||
@@ -543,7 +548,11 @@ extern "C" int lsms_get_contour(const lsms_ctx* c, double* nodes, double* weight
 }
 extern "C" int lsms_get_scattering(const lsms_ctx* c, double* s) {
   if (!c || !s) return LSMS_ERR_ARG;
-  std::memcpy(s, c->S.data(), c->P * sizeof(cplx));
+  if (c->dense) {
+    for (int q = 0; q < c->P; ++q) std::memcpy(s + 2 * q, &c->smat[(size_t)q * c->P + q], sizeof(cplx));
+  } else {
+    std::memcpy(s, c->S.data(), c->P * sizeof(cplx));
+  }
   return LSMS_OK;
 }
 extern "C" int lsms_num_nodes(const lsms_ctx* c) { return c ? c->ns : LSMS_ERR_ARG; }

@@ -22,10 +22,14 @@
 
 bool is_batch(const lsms_ctx* c) { return c && !c->kids.empty(); }
 
-void batch_free(lsms_ctx* c) {
+void batch_clear_graphs(lsms_ctx* c) {
   for (auto& g : c->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   c->graphs.clear();
+}
+
+void batch_free(lsms_ctx* c) {
+  batch_clear_graphs(c);
   for (cudaEvent_t e : c->kid_ev)
     if (e) cudaEventDestroy(e);
   c->kid_ev.clear();
@@ -59,6 +63,11 @@ extern "C" int lsms_set_layouts(lsms_ctx* c, int n_layouts, const int* counts, c
     k->use_graphs = c->use_graphs;
     k->split_mult = c->split_mult;
     c->kids.push_back(k);
+    if (c->dense && (rc = lsms_set_scattering_matrix(k, reinterpret_cast<const double*>(c->smat.data())))) {
+      const std::string m = k->err;
+      batch_free(c);
+      return ctx_fail(c, rc, "set_layouts: layout " + std::to_string(l) + ": " + m);
+    }
     c->kid_off.push_back(off);
     rc = lsms_set_particles(k, counts[l], xy + 2 * off);
     if (rc) {

@@ -845,7 +845,11 @@ extern "C" int lsms_solve(lsms_ctx* c, int nsrc, const double* src_xy, double to
   if ((rc = incident_device(c, nsrc, d_src, beta, st))) return rc;
   double2* rhs = (double2*)c->gm_b.ptr;                 // [nsrc][L]
   double2* xs = rhs + LT;                               // scaled iterates
-  launch_diag_mul(beta, c->d_scale_out + c->P, rhs, LT, c->P, st);   // D S a_inc
+  if (c->dense)                                          // D S_j a_inc (rotated dense matrices)
+    launch_scatter_dense(nullptr, beta, c->d_smt + (size_t)c->P * c->P,
+                         c->has_theta ? (const double*)c->theta_buf.ptr : nullptr, nsrc, c->n, c->P, rhs, st);
+  else
+    launch_diag_mul(beta, c->d_scale_out + c->P, rhs, LT, c->P, st);   // D S a_inc
   bool nonzero = false;
   if (x0) {
     cudaMemcpyAsync(beta, x0, LT * sizeof(double2), cudaMemcpyHostToDevice, st);

@@ -6,6 +6,7 @@
 #include <unordered_map>
 
 #include "lsms_internal.h"
+#include "lsms_ops.h"
 
 static const double kPi = 3.14159265358979323846;
 
@@ -188,7 +189,7 @@ static cplx ipow(int n) {   // i^n for any integer n
 
 // Gaussian elimination with partial pivoting: a (n x n, row-major) x = b (n x nrhs, row-major),
 // solution in b.  False for a singular matrix.
-static bool solve_small(std::vector<cplx>& a, int n, std::vector<cplx>& b, int nrhs) {
+bool solve_small(std::vector<cplx>& a, int n, std::vector<cplx>& b, int nrhs) {
   for (int k = 0; k < n; ++k) {
     int piv = k;
     for (int i = k + 1; i < n; ++i)

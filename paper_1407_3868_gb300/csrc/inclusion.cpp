@@ -1,0 +1,273 @@
+// Inclusions of any smooth shape (Sec. 4 of the paper): the scattering matrix of a prototype
+// inclusion from Muller's second-kind boundary integral equations (Eqs. "intg1", "intg2"), and
+// the per-particle rotated copies S_j = D(-theta_j) S D(theta_j), D(theta) = diag(e^{i n theta})
+// (Sec. 4.1), that replace the disc's Mie diagonal in the operator x - S (T + R) x.
+//
+// Discretisation: Nystrom on the 2 pi-periodic parametrisation x(t), with Kress's product rule for
+// the logarithmic singularities.  Every difference kernel of Eqs. "intg1", "intg2" is split as
+// M(t, tau) = M1(t, tau) ln(4 sin^2((t - tau)/2)) + M2(t, tau) with M1, M2 smooth; M1 integrates
+// against the weights R_j (exact for trigonometric polynomials of degree < n_pts/2), M2 with the
+// trapezoidal rule.  M1 comes from the J_0, J_1 parts of H_0 = J_0 + (2i/pi) ln(z/2) J_0 + ... and
+// H_1 = J_1 + (2i/pi) ln(z/2) J_1 - 2i/(pi z) + ...; the diagonal limits follow from the small-z
+// expansions of H_0, H_1 (C = Euler's constant, s = |x'(t)|):
+//   S^{k2} - S^{kp}: M1 = 0, M2 = -(s / 2 pi) ln(k2 / kp);   D, N differences: M1 = M2 = 0;
+//   T^{k2} - T^{kp}: M1 = -(k2^2 - kp^2) s / 8 pi,
+//     M2 = s [(i/8 + (1 - 2C)/8 pi)(k2^2 - kp^2) - (k2^2 ln(k2 s/2) - kp^2 ln(kp s/2)) / 4 pi].
+// The outgoing coefficients follow from Graf's theorem for G = (i/4) H_0:
+//   beta_l = (i/4) int [J_l(k2 |y|) e^{-i l theta_y} sigma + n_y . grad(J_l e^{-i l theta}) mu] ds_y.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lsms_internal.h"
+#include "lsms_ops.h"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kEuler = 0.57721566490153286061;
+
+// J_n(z) for any integer n (J_{-n} = (-1)^n J_n), z >= 0.
+double bessel_jn(int n, double z) {
+  const double v = std::cyl_bessel_j((double)std::abs(n), z);
+  return (n < 0 && (std::abs(n) & 1)) ? -v : v;
+}
+
+struct Kernels {        // the four kernels for one wavenumber and one (i, j) pair: full and log part
+  cplx s, d, nn, t;
+  double s1, d1, n1, t1;
+};
+
+// Kernels at x_i (normal nx, unit) and x_j (nu_j = |x'_j| n_j), ds_y = |x'_j| d tau folded in.
+Kernels kernels(double k, const double dxy[2], double r, const double nx[2], const double nuj[2],
+                double spj) {
+  const double z = k * r;
+  const double j0 = std::cyl_bessel_j(0.0, z), j1 = std::cyl_bessel_j(1.0, z);
+  const cplx h0(j0, std::cyl_neumann(0.0, z)), h1(j1, std::cyl_neumann(1.0, z));
+  const double nxd = nx[0] * dxy[0] + nx[1] * dxy[1];
+  const double nuyd = nuj[0] * dxy[0] + nuj[1] * dxy[1];
+  const double nxnuy = nx[0] * nuj[0] + nx[1] * nuj[1];
+  const cplx iq(0.0, 0.25);
+  const double c4 = 1.0 / (4.0 * kPi);
+  Kernels o;
+  o.s = iq * h0 * spj;
+  o.s1 = -c4 * j0 * spj;
+  o.d = iq * k * h1 * nuyd / r;
+  o.d1 = -c4 * k * j1 * nuyd / r;
+  o.nn = -iq * k * h1 * nxd / r * spj;
+  o.n1 = c4 * k * j1 * nxd / r * spj;
+  const cplx a = k * k * h0 / (r * r) - 2.0 * k * h1 / (r * r * r);
+  const double areg = k * k * j0 / (r * r) - 2.0 * k * j1 / (r * r * r);
+  o.t = iq * (a * nxd * nuyd + k * h1 / r * nxnuy);
+  o.t1 = -c4 * (areg * nxd * nuyd + k * j1 / r * nxnuy);
+  return o;
+}
+
+}  // namespace
+
+// S[l][n] (row-major, orders -p..p) of the inclusion bounded by `curve` ([n_pts][6]: x, y, x', y',
+// x'', y'' at t_j = 2 pi j / n_pts, counterclockwise, about the enclosing disc's centre).
+int inclusion_matrix(int p, double k2, double kp, double radius, int n_pts, const double* curve,
+                     std::vector<cplx>& S, std::string& err) {
+  const int P = 2 * p + 1, n = n_pts;
+  std::vector<double> x(n), y(n), sp(n), rho(n), th(n);
+  std::vector<double> nux(n), nuy(n);                  // |x'| n (outward)
+  double area = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const double* c = curve + 6 * j;
+    for (int q = 0; q < 6; ++q)
+      if (!std::isfinite(c[q])) { err = "non-finite curve data"; return LSMS_ERR_ARG; }
+    x[j] = c[0]; y[j] = c[1];
+    sp[j] = std::hypot(c[2], c[3]);
+    if (!(sp[j] > 0.0)) { err = "curve has a zero derivative"; return LSMS_ERR_ARG; }
+    nux[j] = c[3]; nuy[j] = -c[2];
+    rho[j] = std::hypot(x[j], y[j]);
+    th[j] = std::atan2(y[j], x[j]);
+    if (!(rho[j] > 1e-12 * radius)) { err = "curve passes through the enclosing disc's centre"; return LSMS_ERR_GEOMETRY; }
+    if (!(rho[j] < radius)) { err = "inclusion is not inside the enclosing disc"; return LSMS_ERR_GEOMETRY; }
+    area += 0.5 * (x[j] * c[3] - y[j] * c[2]);
+  }
+  if (!(area > 0.0)) { err = "curve must run counterclockwise"; return LSMS_ERR_ARG; }
+  const double h = 2.0 * kPi / n;
+  // Kress weights R_m, m = (i - j) mod n:  -(2 pi/h2) sum_{m'=1}^{h2-1} cos(m' t_m)/m' - (pi/h2^2) cos(h2 t_m)
+  const int h2 = n / 2;
+  std::vector<double> Rw(n);
+  for (int m = 0; m < n; ++m) {
+    const double tm = h * m;
+    double s = 0.0;
+    for (int q = 1; q < h2; ++q) s += std::cos(q * tm) / q;
+    Rw[m] = -(2.0 * kPi / h2) * s - (kPi / ((double)h2 * h2)) * std::cos(h2 * tm);
+  }
+  // Muller matrix in the unknowns [mu; sigma]
+  const int N2 = 2 * n;
+  std::vector<cplx> A((size_t)N2 * N2, cplx(0, 0));
+  const double dk2 = k2 * k2 - kp * kp;
+  for (int i = 0; i < n; ++i) {
+    const double nx[2] = {nux[i] / sp[i], nuy[i] / sp[i]};
+    for (int j = 0; j < n; ++j) {
+      cplx ms, md, mn, mt;
+      double m1s, m1d, m1n, m1t;
+      double L = 0.0;
+      if (i == j) {
+        m1s = m1d = m1n = 0.0;
+        m1t = -dk2 * sp[i] / (8.0 * kPi);
+        ms = cplx(-(sp[i] / (2.0 * kPi)) * std::log(k2 / kp), 0.0);
+        md = mn = cplx(0, 0);
+        mt = sp[i] * (cplx((1.0 - 2.0 * kEuler) / (8.0 * kPi), 0.125) * dk2 -
+                      (k2 * k2 * std::log(k2 * sp[i] / 2.0) - kp * kp * std::log(kp * sp[i] / 2.0)) /
+                          (4.0 * kPi));
+      } else {
+        const double dxy[2] = {x[i] - x[j], y[i] - y[j]};
+        const double r = std::hypot(dxy[0], dxy[1]);
+        const double nuj[2] = {nux[j], nuy[j]};
+        const Kernels a = kernels(k2, dxy, r, nx, nuj, sp[j]);
+        const Kernels b = kernels(kp, dxy, r, nx, nuj, sp[j]);
+        const double sn = std::sin(0.5 * h * (i - j));
+        L = std::log(4.0 * sn * sn);
+        m1s = a.s1 - b.s1; m1d = a.d1 - b.d1; m1n = a.n1 - b.n1; m1t = a.t1 - b.t1;
+        ms = (a.s - b.s) - m1s * L;
+        md = (a.d - b.d) - m1d * L;
+        mn = (a.nn - b.nn) - m1n * L;
+        mt = (a.t - b.t) - m1t * L;
+      }
+      const double rw = Rw[((i - j) % n + n) % n];
+      A[(size_t)i * N2 + j] = rw * m1d + h * md + (i == j ? 1.0 : 0.0);
+      A[(size_t)i * N2 + n + j] = rw * m1s + h * ms;
+      A[(size_t)(n + i) * N2 + j] = rw * m1t + h * mt;
+      A[(size_t)(n + i) * N2 + n + j] = rw * m1n + h * mn - (i == j ? 1.0 : 0.0);
+    }
+  }
+  // right-hand sides: -u_inc, -du_inc/dn for u_inc = J_m(k2 rho) e^{i m theta}, m = -p..p
+  std::vector<cplx> B((size_t)N2 * P);
+  for (int i = 0; i < n; ++i) {
+    const double nr = (nux[i] * std::cos(th[i]) + nuy[i] * std::sin(th[i])) / sp[i];
+    const double nt = (-nux[i] * std::sin(th[i]) + nuy[i] * std::cos(th[i])) / sp[i];
+    const double z = k2 * rho[i];
+    for (int m = -p; m <= p; ++m) {
+      const cplx e = std::polar(1.0, m * th[i]);
+      const double jm = bessel_jn(m, z);
+      const double jmp = 0.5 * (bessel_jn(m - 1, z) - bessel_jn(m + 1, z));
+      B[(size_t)i * P + m + p] = -jm * e;
+      B[(size_t)(n + i) * P + m + p] = -(k2 * jmp * nr * e + cplx(0.0, m / rho[i]) * jm * nt * e);
+    }
+  }
+  if (!solve_small(A, N2, B, P)) { err = "singular Muller system"; return LSMS_ERR_ARG; }
+  // beta^m_l = (i/4) h sum_j [J_l e^{-i l theta} sigma |x'| + nu . grad(J_l e^{-i l theta}) mu]
+  S.assign((size_t)P * P, cplx(0, 0));
+  for (int j = 0; j < n; ++j) {
+    const double z = k2 * rho[j];
+    const double nr = nux[j] * std::cos(th[j]) + nuy[j] * std::sin(th[j]);    // |x'| n . e_rho
+    const double nt = -nux[j] * std::sin(th[j]) + nuy[j] * std::cos(th[j]);   // |x'| n . e_theta
+    for (int l = -p; l <= p; ++l) {
+      const cplx e = std::polar(1.0, -l * th[j]);
+      const double jl = bessel_jn(l, z);
+      const double jlp = 0.5 * (bessel_jn(l - 1, z) - bessel_jn(l + 1, z));
+      const cplx fs = jl * e * sp[j];
+      const cplx fm = e * (k2 * jlp * nr - cplx(0.0, l / rho[j]) * jl * nt);
+      for (int m = 0; m < P; ++m) {
+        const cplx mu = B[(size_t)j * P + m], sigma = B[(size_t)(n + j) * P + m];
+        S[(size_t)(l + p) * P + m] += cplx(0.0, 0.25 * h) * (fs * sigma + fm * mu);
+      }
+    }
+  }
+  for (const cplx& v : S)
+    if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) { err = "non-finite scattering matrix"; return LSMS_ERR_ARG; }
+  return LSMS_OK;
+}
+
+extern "C" int lsms_inclusion_scattering_matrix(int p, double k2, double kp, double radius, int n_pts,
+                                                const double* curve, double* s_out) {
+  if (p < 0 || p > LSMS_MAX_P || !std::isfinite(k2) || !(k2 > 0.0) || !std::isfinite(kp) || !(kp > 0.0) ||
+      !std::isfinite(radius) || !(radius > 0.0) || n_pts < 8 || n_pts > 4096 || (n_pts & 1) || !curve || !s_out)
+    return ctx_fail(nullptr, LSMS_ERR_ARG,
+                    "inclusion_scattering_matrix: need 0 <= p <= 15, k2, kp, radius > 0, an even n_pts in "
+                    "[8, 4096], curve and output");
+  std::vector<cplx> S;
+  std::string err;
+  const int rc = inclusion_matrix(p, k2, kp, radius, n_pts, curve, S, err);
+  if (rc) return ctx_fail(nullptr, rc, "inclusion_scattering_matrix: " + err);
+  std::memcpy(s_out, S.data(), S.size() * sizeof(cplx));
+  return LSMS_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// The context's scattering matrices
+// ---------------------------------------------------------------------------------------------
+extern "C" int lsms_set_scattering_matrix(lsms_ctx* c, const double* s) {
+  if (!c) return LSMS_ERR_ARG;
+  const int P = c->P;
+  cudaStreamSynchronize(c->stream);
+  batch_clear_graphs(c);
+  if (!s) {
+    c->dense = false;
+    c->smat.clear();
+  } else {
+    std::vector<cplx> m((size_t)P * P);
+    std::memcpy(m.data(), s, m.size() * sizeof(cplx));
+    for (const cplx& v : m)
+      if (!std::isfinite(v.real()) || !std::isfinite(v.imag()))
+        return ctx_fail(c, LSMS_ERR_ARG, "set_scattering_matrix: non-finite entry");
+    // device tables, transposed ([n][l]) for the two output scalings: S and diag(|H_l(k2 R)|) S
+    std::vector<cplx> t((size_t)2 * P * P);
+    for (int l = 0; l < P; ++l)
+      for (int q = 0; q < P; ++q) {
+        t[(size_t)q * P + l] = m[(size_t)l * P + q];
+        t[(size_t)P * P + (size_t)q * P + l] = c->hscale[l] * m[(size_t)l * P + q];
+      }
+    if (!c->d_smt && cudaMalloc((void**)&c->d_smt, t.size() * sizeof(cplx)) != cudaSuccess) {
+      cudaGetLastError();
+      c->d_smt = nullptr;
+      return ctx_fail(c, LSMS_ERR_OOM, "set_scattering_matrix: cudaMalloc failed");
+    }
+    if (cudaMemcpy(c->d_smt, t.data(), t.size() * sizeof(cplx), cudaMemcpyHostToDevice) != cudaSuccess)
+      return check_cuda(c, "set_scattering_matrix");
+    c->smat = m;
+    c->dense = true;
+  }
+  for (lsms_ctx* k : c->kids) {
+    const int rc = lsms_set_scattering_matrix(k, s);
+    if (rc) return ctx_fail(c, rc, std::string("set_scattering_matrix: ") + k->err);
+  }
+  return LSMS_OK;
+}
+
+extern "C" int lsms_set_orientations(lsms_ctx* c, int n, const double* theta) {
+  if (!c) return LSMS_ERR_ARG;
+  if (c->n < 0) return ctx_fail(c, LSMS_ERR_STATE, "call lsms_set_particles or lsms_set_layouts first");
+  if (n != c->n) return ctx_fail(c, LSMS_ERR_ARG, "set_orientations: n must equal the number of particles");
+  cudaStreamSynchronize(c->stream);
+  batch_clear_graphs(c);
+  if (!c->kids.empty()) {
+    for (size_t l = 0; l < c->kids.size(); ++l) {
+      lsms_ctx* k = c->kids[l];
+      const int rc = lsms_set_orientations(k, k->n, theta ? theta + c->kid_off[l] : nullptr);
+      if (rc) return ctx_fail(c, rc, "set_orientations: layout " + std::to_string(l) + ": " + k->err);
+    }
+    return LSMS_OK;
+  }
+  if (!theta || n == 0) {
+    c->has_theta = false;
+    return LSMS_OK;
+  }
+  for (int j = 0; j < n; ++j)
+    if (!std::isfinite(theta[j])) return ctx_fail(c, LSMS_ERR_ARG, "set_orientations: non-finite angle");
+  int rc;
+  if ((rc = ensure(c, c->theta_buf, (size_t)n * sizeof(double)))) return rc;
+  if (cudaMemcpy(c->theta_buf.ptr, theta, (size_t)n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return check_cuda(c, "set_orientations");
+  c->has_theta = true;
+  return LSMS_OK;
+}
+
+extern "C" int lsms_get_scattering_matrix(const lsms_ctx* c, double* s) {
+  if (!c || !s) return LSMS_ERR_ARG;
+  const int P = c->P;
+  std::vector<cplx> m((size_t)P * P, cplx(0, 0));
+  if (c->dense)
+    m = c->smat;
+  else
+    for (int q = 0; q < P; ++q) m[(size_t)q * P + q] = c->S[q];
+  std::memcpy(s, m.data(), m.size() * sizeof(cplx));
+  return LSMS_OK;
+}

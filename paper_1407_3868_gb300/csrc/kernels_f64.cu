@@ -422,6 +422,49 @@ void launch_sigma_to_v(int ns, int P, int nrhs, const double2* sig, const double
   k_sigma_to_v<<<grid_for(total, 256), 256, 0, st>>>(ns, P, nrhs, sig, udis, V);
 }
 
+// y = x - D(-theta_j) M D(theta_j) alpha for every (right-hand side, particle): one warp per pair,
+// lane = order (alpha_n e^{i n theta} broadcast by shuffles, M^T staged in shared memory so that a
+// warp reads one contiguous row per source order).
+__global__ void k_scatter_dense(const double2* __restrict__ x, const double2* __restrict__ alpha,
+                                const double2* __restrict__ mt, const double* __restrict__ theta,
+                                long long units, int n, int P, double2* __restrict__ y) {
+  extern __shared__ double2 s_mt[];
+  for (int i = threadIdx.x; i < P * P; i += blockDim.x) s_mt[i] = mt[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int p = (P - 1) / 2;
+  const long long stride = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units; u += stride) {
+    double sn = 0.0, cs = 1.0;
+    if (theta) sincos((double)(lane - p) * theta[u % n], &sn, &cs);
+    double2 a = make_double2(0.0, 0.0);
+    if (lane < P) a = cmul(alpha[u * P + lane], make_double2(cs, sn));
+    double2 acc = make_double2(0.0, 0.0);
+    for (int q = 0; q < P; ++q) {
+      const double2 b = make_double2(__shfl_sync(0xffffffffu, a.x, q), __shfl_sync(0xffffffffu, a.y, q));
+      if (lane < P) acc = cfma(s_mt[q * P + lane], b, acc);
+    }
+    if (lane < P) {
+      const double2 v = cmul(acc, make_double2(cs, -sn));
+      if (x) {
+        const double2 xv = x[u * P + lane];
+        y[u * P + lane] = make_double2(xv.x - v.x, xv.y - v.y);
+      } else {
+        y[u * P + lane] = v;
+      }
+    }
+  }
+}
+
+void launch_scatter_dense(const double2* x, const double2* alpha, const double2* mt, const double* theta,
+                          int nrhs, int n, int P, double2* y, cudaStream_t st) {
+  const long long units = (long long)nrhs * n;
+  if (units == 0) return;
+  long long blocks = (units + 7) / 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_scatter_dense<<<(int)blocks, 256, (size_t)P * P * sizeof(double2), st>>>(x, alpha, mt, theta, units, n, P, y);
+}
+
 void launch_incident_sigma(int ns, int nsrc, const double* src, double xc, const double2* lam,
                            const double2* g1, const double2* inc, double2* sig, cudaStream_t st) {
   const int total = ns * nsrc;

@@ -46,6 +46,12 @@ struct lsms_ctx {
   int ns = 0;
   NodeTables nodes;
   std::vector<cplx> S;              // Mie diagonal, P
+  // inclusions of another shape (Sec. 4.1): a dense prototype matrix S[l][n] and per-particle angles
+  bool dense = false;
+  std::vector<cplx> smat;           // [P][P]
+  double2* d_smt = nullptr;         // [2][P][P] transposed ([n][l]): S, diag(|H_l(k2 R)|) S
+  DevBuf theta_buf;                 // [N] rotation angles (valid when has_theta)
+  bool has_theta = false;
   std::vector<double> hscale;       // |H_n(k2 R)|, P
 
   // discs
@@ -165,6 +171,10 @@ void launch_sigma_to_v(int ns, int P, int nrhs, const double2* sig, const double
 void launch_incident_sigma(int ns, int nsrc, const double* src, double xc, const double2* lam,
                            const double2* g1, const double2* inc, double2* sig, cudaStream_t st);
 // y = x - s_out * alpha   (or y = alpha if alpha_only)
+// y = x - D(-theta_j) M D(theta_j) alpha per particle (x == nullptr: y = D(-theta) M D(theta) alpha);
+// mt: [P][P] transposed, theta: [n] or nullptr (all zero); nrhs blocks of n particles.
+void launch_scatter_dense(const double2* x, const double2* alpha, const double2* mt, const double* theta,
+                          int nrhs, int n, int P, double2* y, cudaStream_t st);
 void launch_combine(const double2* x, const double2* alpha, const double2* s_out, double2* y,
                     int nrhs, int n, int P, int alpha_only, cudaStream_t st);
 // field in layer 1 at targets

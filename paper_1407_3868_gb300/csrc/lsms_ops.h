@@ -11,6 +11,10 @@ int ctx_fail(lsms_ctx* c, int code, const std::string& msg);
 int create_stack(const std::vector<double>& ks, const std::vector<double>& ds, int layer, double kp,
                  double radius, int p, const lsms_contour* contour, int precision, lsms_ctx** out);
 int ensure(lsms_ctx* c, DevBuf& b, size_t bytes);
+// Gaussian elimination with partial pivoting, a (n x n) x = b (n x nrhs), row-major; false if singular
+bool solve_small(std::vector<cplx>& a, int n, std::vector<cplx>& b, int nrhs);
+// drop the captured batched applications (their kernels depend on the context's settings)
+void batch_clear_graphs(lsms_ctx* c);
 int check_cuda(lsms_ctx* c, const char* where);
 int need_particles(lsms_ctx* c);
 int validate_sources(lsms_ctx* c, int nsrc, const double* xy);

@@ -19,7 +19,8 @@ APPLY_SCALED, APPLY_MIXED, APPLY_NO_TRANSLATION, APPLY_NO_REFLECTION, APPLY_ALPH
 FIELD_TOTAL, FIELD_SCATTERED, FIELD_PARTICLE = 0, 1, 2
 STATUS = {0: "OK", -1: "ARG", -2: "GEOMETRY", -3: "NOT_CONVERGED", -4: "NONFINITE", -5: "OOM",
           -6: "CUDA", -7: "STATE"}
-EXPORTS = ["lsms_create", "lsms_create_stack", "lsms_set_particles", "lsms_apply", "lsms_apply_ex", "lsms_apply_dev",
+EXPORTS = ["lsms_create", "lsms_create_stack", "lsms_set_scattering_matrix", "lsms_set_orientations",
+           "lsms_get_scattering_matrix", "lsms_inclusion_scattering_matrix", "lsms_set_particles", "lsms_apply", "lsms_apply_ex", "lsms_apply_dev",
            "lsms_translate", "lsms_aggregate", "lsms_reflect", "lsms_disaggregate", "lsms_incident",
            "lsms_get_contour", "lsms_get_scattering", "lsms_num_nodes", "lsms_num_particles",
            "lsms_solve", "lsms_eval_field", "lsms_last_error", "lsms_destroy",
@@ -63,6 +64,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsms_create": (i, [d, d, d, d, d, d, i, ctypes.POINTER(Contour), i, ctypes.POINTER(_P)]),
         "lsms_create_stack": (i, [i, _D, _D, i, d, d, i, ctypes.POINTER(Contour), i, ctypes.POINTER(_P)]),
         "lsms_set_particles": (i, [_P, i, _D]),
+        "lsms_set_scattering_matrix": (i, [_P, _D]),
+        "lsms_set_orientations": (i, [_P, i, _D]),
+        "lsms_get_scattering_matrix": (i, [_P, _D]),
+        "lsms_inclusion_scattering_matrix": (i, [i, d, d, d, i, _D, _D]),
         "lsms_apply": (i, [_P, i, _D, _D]),
         "lsms_apply_ex": (i, [_P, i, _D, _D, i]),
         "lsms_apply_dev": (i, [_P, i, _P, _P, i, _P]),
@@ -184,6 +189,25 @@ class Context:
         m = ctypes.c_double()
         self._check(self.lib.lsms_autotune(self.h, ctypes.byref(m)))
         return m.value
+
+    def set_scattering_matrix(self, smat=None):
+        """Dense prototype scattering matrix [P][P] (None: the disc's Mie diagonal)."""
+        if smat is None:
+            self._check(self.lib.lsms_set_scattering_matrix(self.h, None))
+            return
+        s = _c128(smat, (self.P, self.P))
+        self._check(self.lib.lsms_set_scattering_matrix(self.h, _dptr(s)))
+
+    def set_orientations(self, theta=None):
+        """Rotation angles of the particles (None: all zero)."""
+        th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float64)
+        n = self.n if th is None else th.size
+        self._check(self.lib.lsms_set_orientations(self.h, int(n), _dptr(th)))
+
+    def scattering_matrix(self):
+        s = np.zeros((self.P, self.P), dtype=np.complex128)
+        self._check(self.lib.lsms_get_scattering_matrix(self.h, _dptr(s)))
+        return s
 
     def set_tc_translation(self, min_rhs: int, flush: int = 0):
         """Blocks of at least min_rhs right-hand sides: mixed translation on the tensor cores (0 = never);
@@ -345,6 +369,19 @@ def translate_mixed_noalloc(centres, beta, alpha, k2, p, stream=None):
                                           ctypes.c_void_p(stream.cuda_stream))
     if rc != 0:
         raise LsmsError(rc, lib.lsms_last_error(None).decode())
+
+
+def inclusion_scattering_matrix(p, k2, kp, radius, curve) -> np.ndarray:
+    """lsms_inclusion_scattering_matrix: curve = (x, x', x'') as three (n_pts, 2) arrays."""
+    lib = load()
+    x, dx, ddx = (np.asarray(a, dtype=np.float64).reshape(-1, 2) for a in curve)
+    c = np.ascontiguousarray(np.concatenate([x, dx, ddx], axis=1))
+    s = np.zeros((2 * p + 1, 2 * p + 1), dtype=np.complex128)
+    rc = lib.lsms_inclusion_scattering_matrix(int(p), float(k2), float(kp), float(radius), c.shape[0],
+                                              _dptr(c), _dptr(s))
+    if rc != 0:
+        raise LsmsError(rc, lib.lsms_last_error(None).decode())
+    return s
 
 
 def context_for(workload, precision=LSMS_FP64) -> Context:

@@ -136,3 +136,32 @@ def test_layer_stack_arguments_are_validated_before_any_device_work(lib):
     with pytest.raises(lib.LsmsError) as e:         # valid: fails only for want of a GPU
         lib.Context(0, 0, 0, 0, 2.4 * math.pi, 0.25, 6, 128, stack=(ks, ds, 3))
     assert e.value.code == -6
+
+
+@pytest.mark.parametrize("p,n_pts,shape,kp", [(10, 256, (0.15, 0.05, 5), 2.4 * math.pi),
+                                              (14, 128, (0.2, 0.0, 0), 2.4 * math.pi),
+                                              (8, 96, (0.12, 0.04, 3), 2.0 * math.pi)])
+def test_library_inclusion_matrix_equals_oracle(lib, p, n_pts, shape, kp):
+    # host-only helper (Sec. 4): the library's Nystrom solve against the oracle's
+    from oracle import lsms_oracle as O
+    k2 = inputs.MEDIUM["k2"]
+    cur = inputs.star_curve(*shape, n_pts, rotation=0.3)
+    s_lib = lib.inclusion_scattering_matrix(p, k2, kp, 0.25, cur)
+    s_o = O.inclusion_scattering_matrix(cur, p, k2, kp)
+    assert np.abs(s_lib - s_o).max() < 1e-13 * np.abs(s_o).max()
+
+
+def test_library_inclusion_matrix_rejects_bad_curves(lib):
+    k2, kp = inputs.MEDIUM["k2"], inputs.MEDIUM["kp"]
+    x, dx, ddx = inputs.star_curve(0.15, 0.05, 5, 64)
+    cases = [((x, dx, ddx), 0.15, -2),                      # outside the enclosing disc
+             ((x[::-1], -dx[::-1], ddx[::-1]), 0.25, -1),   # clockwise
+             ((x[:63], dx[:63], ddx[:63]), 0.25, -1),       # odd number of points
+             ((x * np.nan, dx, ddx), 0.25, -1)]
+    for cur, radius, code in cases:
+        with pytest.raises(lib.LsmsError) as e:
+            lib.inclusion_scattering_matrix(10, k2, kp, radius, cur)
+        assert e.value.code == code
+    with pytest.raises(lib.LsmsError) as e:
+        lib.inclusion_scattering_matrix(16, k2, kp, 0.25, (x, dx, ddx))
+    assert e.value.code == -1
