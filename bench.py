@@ -327,10 +327,11 @@ def run_ours(args, rank, world, local_rank):
             solve["speedup_mixed_vs_fp64"] = solve["fp64_s"] / solve["mixed_s"]
             ctxd.close()
     ctx.close()
-    batched = stack = None
+    batched = stack = inclusions = None
     if world == 1 and not args.no_batched:
         batched = run_batched(args, dev, flush)
         stack = run_stack(args, w, dev, flush)
+        inclusions = run_inclusions(args, w, dev, flush)
 
     if rank != 0:
         return None
@@ -348,6 +349,7 @@ def run_ours(args, rank, world, local_rank):
         "solve": solve,
         "batched": batched,
         "stack": stack,
+        "inclusions": inclusions,
         "roofline": {"kernel": "k_translate_f32", "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": traffic, "flop_per_launch": flop, "launch_ms": tr_ms,
@@ -502,6 +504,41 @@ def run_stack(args, w, dev, flush):
     if not args.no_solve:
         t0 = time.perf_counter()
         _, info = ctx.solve(w.sources, tol=1e-8, maxiter=2000)      # sources stay in layer 1
+        out["mixed_solve"] = {"tol": 1e-8, "s": time.perf_counter() - t0, "iters": info["iters"],
+                              "refinements": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"]}
+    ctx.close()
+    return out
+
+
+def run_inclusions(args, w, dev, flush):
+    """The bench layout with five-lobed star inclusions (Sec. 4; Sec. 6 Eq. "par1"), each turned
+    by a seeded angle: the prototype's scattering matrix from the host Nystrom solve, then mixed
+    operator applications and the mixed solve at 1e-8 with the rotated dense matrices."""
+    import numpy as np
+    import torch
+
+    from paper_1407_3868_gb300 import inputs, lsms
+    s, m = inputs.STAR5, w.medium
+    t0 = time.perf_counter()
+    smat = lsms.inclusion_scattering_matrix(w.p, m["k2"], m["kp"], m["radius"],
+                                            inputs.star_curve(s["a1"], s["a2"], s["a3"], s["n_pts"]))
+    t_matrix = time.perf_counter() - t0
+    ctx = lsms.context_for(w, lsms.LSMS_MIXED)
+    ctx.set_particles(w.centres())
+    ctx.set_scattering_matrix(smat)
+    ctx.set_orientations(inputs.orientations(w.n, 7))
+    x = torch.from_numpy(inputs.random_coefficients(w.n, w.p, 1, 400)).to(dev)
+    y = torch.empty_like(x)
+    fl_m = lsms.APPLY_SCALED | lsms.APPLY_MIXED
+    for _ in range(3):
+        ctx.apply_dev(x, y, fl_m)
+    torch.cuda.synchronize()
+    ms = time_device(lambda: ctx.apply_dev(x, y, fl_m), max(args.steps, 3), flush)
+    out = {"workload": w.name + "_star5", "shape": dict(s), "matrix_setup_s": t_matrix,
+           "mixed": {"ms_per_apply": ms, "applies_per_s": 1e3 / ms}}
+    if not args.no_solve:
+        t0 = time.perf_counter()
+        _, info = ctx.solve(w.sources, tol=1e-8, maxiter=2000)
         out["mixed_solve"] = {"tol": 1e-8, "s": time.perf_counter() - t0, "iters": info["iters"],
                               "refinements": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"]}
     ctx.close()
