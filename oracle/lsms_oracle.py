@@ -90,15 +90,57 @@ def gamma(lam, k):
 # ----------------------------------------------------------------------------------------------
 # Sommerfeld contour (Sec. 5.1, Eq. "sommerseg")
 # ----------------------------------------------------------------------------------------------
-def contour_panel_breaks(n_panels: int, branch_points, b: float, t_max: float) -> np.ndarray:
+def guided_band(branch_points):
+    """(lo, hi): the real lambda where the layer response can have poles (guided modes), i.e.
+    evanescent in both half-spaces (lambda > max(k_top, k_bottom)) yet propagating in an interior
+    layer (lambda < the largest interior k); None when that interval is empty.  branch_points are
+    the layers' wavenumbers from top to bottom."""
+    ks = [float(k) for k in branch_points]
+    if len(ks) < 3:
+        return None
+    lo, hi = max(ks[0], ks[-1]), max(ks[1:-1])
+    return (lo, hi) if hi > lo else None
+
+
+def contour_panel_breaks(n_panels: int, branch_points, b: float, t_max: float, band=None) -> np.ndarray:
     """Panel breakpoints of Gamma1 on t in [0, t_max].
 
-    Breakpoints sit at 0, t_max and every branch point k_i < t_max, and are graded geometrically
-    toward each branch point (k_i +- b 2^j, j < L) with the largest L that keeps the panel count
-    at most n_panels.  Remaining panels are made by halving the longest panel (first one on ties).
-    If even the ungraded set has too many panels, the branch points are dropped.
+    Without a guided-mode band: breakpoints sit at 0, t_max and every branch point k_i < t_max,
+    and are graded geometrically toward each branch point (k_i +- b 2^j, j < L) with the largest L
+    that keeps the panel count at most n_panels.  Remaining panels are made by halving the longest
+    panel (first one on ties).  If even the ungraded set has too many panels, the branch points
+    are dropped.
+
+    With a guided-mode band (lo, hi) (poles of the layer response on the real axis, a distance b
+    from Gamma1): start from 0, t_max and the branch points, then repeatedly halve the panel with
+    the largest length / (b + distance to the nearest branch point) (distance 0 for a panel that
+    meets the band; first one on ties) until there are n_panels: the length of a Gauss-Legendre
+    panel relative to the distance of its nearest singularity sets its error.
     """
     ks = sorted(set(float(k) for k in branch_points if 0.0 < k < t_max))
+    if band is not None:
+        lo, hi = float(band[0]), float(band[1])
+        pts = sorted(set([0.0, float(t_max)] + ks))
+        if len(pts) - 1 > n_panels:
+            raise ValueError(f"contour: {len(pts) - 1} panels of Gamma1 needed, {n_panels} available")
+
+        def score(a, e):
+            if e > lo and a < hi:
+                dist = 0.0
+            else:
+                dist = t_max
+                for s in ks:
+                    dist = min(dist, 0.0 if a <= s <= e else min(abs(a - s), abs(e - s)))
+            return (e - a) / (b + dist)
+
+        while len(pts) - 1 < n_panels:
+            best, bs = 0, -1.0
+            for i in range(len(pts) - 1):
+                sc = score(pts[i], pts[i + 1])
+                if sc > bs:
+                    best, bs = i, sc
+            pts.insert(best + 1, 0.5 * (pts[best] + pts[best + 1]))
+        return np.array(pts)
     levels = 0
     while b * 2.0 ** levels < t_max:
         levels += 1
@@ -124,11 +166,12 @@ def contour_panel_breaks(n_panels: int, branch_points, b: float, t_max: float) -
 
 
 def contour(n_nodes: int, k1: float, k2: float, k3: float, b: float, t_max: float,
-            panel_order: int = 16, branch_points=None):
+            panel_order: int = 16, branch_points=None, guided=True):
     """Nodes lambda_nu and weights w_nu (d lambda included) of the discretised contour.
 
     Gamma1 (t - i b, 0 < t < t_max) and Gamma3 (its mirror t + i b, -t_max < t < 0) each carry
-    n1 = q * floor((N_S - q) / (2 q)) Gauss-Legendre nodes in panels of order q; Gamma2 (i s,
+    n1 = q * floor((N_S - q) / (2 q)) Gauss-Legendre nodes in panels of order q (guided-mode
+    media: see contour_panel_breaks; guided=False keeps the plain grading); Gamma2 (i s,
     s from b down to -b) carries the remaining N_S - 2 n1 nodes as one Gauss-Legendre rule.
     Returned in path order Gamma3 -> Gamma2 -> Gamma1.
     """
@@ -137,8 +180,8 @@ def contour(n_nodes: int, k1: float, k2: float, k3: float, b: float, t_max: floa
     n2 = n_nodes - 2 * n1
     if n1 <= 0 or n2 <= 0:
         raise ValueError("contour: too few nodes for the panel order")
-    breaks = contour_panel_breaks(n1 // q, (k1, k2, k3) if branch_points is None else branch_points,
-                                  b, t_max)
+    bp = (k1, k2, k3) if branch_points is None else branch_points
+    breaks = contour_panel_breaks(n1 // q, bp, b, t_max, guided_band(bp) if guided else None)
     x, w = np.polynomial.legendre.leggauss(q)
     t1, w1 = [], []
     for a, c in zip(breaks[:-1], breaks[1:]):

@@ -52,11 +52,14 @@ def test_gamma_branch():
 
 def test_contour_weights_integrate_entire_functions():
     # An entire, decaying integrand integrates to its real-axis value along the deformed path.
-    lam, wt = O.contour(512, 1.0, 3.0, 2.0, 0.2, 30.0)
+    # (k2 > k1, k3 here: first the plain grading, then the guided-mode panel rule)
+    lam, wt = O.contour(512, 1.0, 3.0, 2.0, 0.2, 30.0, guided=False)
     assert np.sum(wt * np.exp(-lam ** 2)) == pytest.approx(math.sqrt(math.pi), rel=1e-13)
     f = lambda z: np.exp(-0.5 * (z - 1.0) ** 2 + 2j * z)
     ref = math.sqrt(2 * math.pi) * np.exp(2j - 2.0)        # Fourier transform of a Gaussian
     assert abs(np.sum(wt * f(lam)) - ref) < 1e-13
+    lam_g, wt_g = O.contour(512, 1.0, 3.0, 2.0, 0.2, 30.0)
+    assert abs(np.sum(wt_g * f(lam_g)) - ref) < 1e-13
     # reversing Gamma2's orientation (a plausible sign slip) changes the value
     n1 = 16 * ((512 - 16) // 32)
     wt_bad = wt.copy()
@@ -550,3 +553,39 @@ def test_problem_with_inclusion_matrices():
     assert np.allclose(b1, b2, rtol=0, atol=1e-11 * np.abs(b1).max())
     assert np.allclose(b1, b3, rtol=0, atol=1e-11 * np.abs(b1).max())
     assert np.abs(b1 - disc.solve_dense(src)).max() > 1e-3 * np.abs(b1).max()
+
+
+# ---------------------------------------------------------------------------------------------
+# Guided-mode media (k2 > k1, k3): poles of the layer response next to the contour
+# ---------------------------------------------------------------------------------------------
+def _guided_fields(n_nodes, b, guided=True):
+    k1, k2, k3, d, kp, R = 1.0, 6.0, 1.0, 3.0, 2.0, 0.25
+    m = O.Medium(k1, k2, k3, d, kp, R)
+    c = inputs.layout(8, -2.0, 2.0, 5, radius=R, d=d, clearance=0.3)
+    src = np.array([0.2, 1.0])
+    tg = inputs.observation_points(-3.0, 3.0, 16, 1.5)
+    lam, wt = O.contour(n_nodes, k1, k2, k3, b, 40.0, guided=guided)
+    pr = O.Problem(m, 6, c, lam, wt)
+    beta = pr.solve_dense(src)
+    return pr.field_layer1(src, beta, tg, "scattered"), pr.field_layer1(src, beta, tg, "particle")
+
+
+def test_guided_medium_fields_do_not_depend_on_the_contour():
+    # Cauchy: moving Gamma (b, node count) without crossing a pole or branch point leaves every
+    # Sommerfeld integral unchanged, so the solved fields must agree between contours; with the
+    # poles of the guided modes a distance b below Gamma1 this checks the panel rule as well as
+    # the layer response, the coupling and the fields
+    ref = _guided_fields(1536, 0.15)
+    for n_nodes, b in ((640, 0.3), (768, 0.25), (1024, 0.2)):
+        for u, r in zip(_guided_fields(n_nodes, b), ref):
+            assert np.linalg.norm(u - r) / np.linalg.norm(r) < 1e-11, (n_nodes, b)
+    # the plain grading (no guided-mode refinement) misses at the same node count
+    u, r = _guided_fields(1024, 0.2, guided=False)[0], ref[0]
+    assert np.linalg.norm(u - r) / np.linalg.norm(r) > 1e-8
+
+
+def test_guided_band():
+    assert O.guided_band((1.0, 6.0, 1.0)) == (1.0, 6.0)
+    assert O.guided_band((1.0, 6.0, 2.0)) == (2.0, 6.0)
+    assert O.guided_band((MED["k1"], MED["k2"], MED["k3"])) is None     # k2 < k3: energy leaks down
+    assert O.guided_band((1.0, 2.0, 5.0, 3.0, 1.5)) == (1.5, 5.0)
