@@ -56,10 +56,40 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
 // geometrically toward each branch point (k +- b 2^j, j < L) with the largest L that keeps at most
 // n_panels panels; then the longest panel is halved (first one on ties) until there are n_panels.
 std::vector<double> contour_panel_breaks(int n_panels, const double* ks, int nk, double b,
-                                         double t_max) {
+                                         double t_max, double band_lo, double band_hi) {
   std::set<double> branch;
   for (int i = 0; i < nk; ++i)
     if (ks[i] > 0.0 && ks[i] < t_max) branch.insert(ks[i]);
+  if (band_hi > band_lo) {
+    // guided-mode medium: poles of the layer response on the real axis in (band_lo, band_hi), a
+    // distance b below Gamma1.  Halve the panel with the largest length / (b + distance to the
+    // nearest branch point) (distance 0 for a panel meeting the band; first one on ties).
+    std::set<double> s0 = branch;
+    s0.insert(0.0);
+    s0.insert(t_max);
+    std::vector<double> pts(s0.begin(), s0.end());
+    if ((int)pts.size() - 1 > n_panels) return {};
+    auto score = [&](double a, double e) {
+      double dist;
+      if (e > band_lo && a < band_hi) {
+        dist = 0.0;
+      } else {
+        dist = t_max;
+        for (double s : branch) dist = std::min(dist, (a <= s && s <= e) ? 0.0 : std::min(std::abs(a - s), std::abs(e - s)));
+      }
+      return (e - a) / (b + dist);
+    };
+    while ((int)pts.size() - 1 < n_panels) {
+      int best = 0;
+      double bs = -1.0;
+      for (size_t i = 0; i + 1 < pts.size(); ++i) {
+        const double sc = score(pts[i], pts[i + 1]);
+        if (sc > bs) { bs = sc; best = (int)i; }
+      }
+      pts.insert(pts.begin() + best + 1, 0.5 * (pts[best] + pts[best + 1]));
+    }
+    return pts;
+  }
   int levels = 0;
   while (b * std::ldexp(1.0, levels) < t_max) ++levels;
   std::vector<double> pts;
@@ -108,7 +138,15 @@ int build_contour(const lsms_contour& c, const std::vector<double>& ks, std::vec
     err = "contour: n_nodes too small for the panel order";
     return LSMS_ERR_ARG;
   }
-  std::vector<double> br = contour_panel_breaks(n1 / q, ks.data(), (int)ks.size(), b, t_max);
+  // guided modes: evanescent in both half-spaces (lambda > max(k_top, k_bottom)) and propagating in
+  // an interior layer (lambda < its k) -> poles of the layer response on the real axis
+  double band_lo = std::max(ks.front(), ks.back()), band_hi = 0.0;
+  for (size_t i = 1; i + 1 < ks.size(); ++i) band_hi = std::max(band_hi, ks[i]);
+  std::vector<double> br = contour_panel_breaks(n1 / q, ks.data(), (int)ks.size(), b, t_max, band_lo, band_hi);
+  if (br.empty()) {
+    err = "contour: too few nodes for the panels a guided-mode medium needs (one per branch point)";
+    return LSMS_ERR_ARG;
+  }
   std::vector<double> gx, gw;
   gauss_legendre(q, gx, gw);
   std::vector<double> t1, w1;

@@ -137,8 +137,9 @@ struct lsms_ctx {
 // ------------------------------------------------------------------------------------------
 int build_contour(const lsms_contour& c, const std::vector<double>& ks, std::vector<cplx>& lam,
                   std::vector<cplx>& wt, std::string& err);
+// Gamma1 panel breakpoints; band_hi > band_lo marks a guided-mode band (empty result: too few panels)
 std::vector<double> contour_panel_breaks(int n_panels, const double* ks, int nk, double b,
-                                         double t_max);
+                                         double t_max, double band_lo, double band_hi);
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 std::vector<cplx> mie_diagonal(int p, double k2, double kp, double R);
 std::vector<double> hankel_scale(int p, double k2, double R);

@@ -49,6 +49,19 @@ def test_library_contour_equals_oracle_contour(lib, name):
     assert np.max(np.abs(wt - wt_o)) <= 1e-14 * w.t_max
 
 
+@pytest.mark.parametrize("ks,b,n_nodes,t_max", [((1.0, 6.0, 1.0), 0.2, 1024, 40.0),
+                                              ((1.0, 20.0, 1.0), 0.19, 2048, 40.0),
+                                              ((2.0, 3.0, 2.5), 0.05, 768, 25.0)])
+def test_library_contour_equals_oracle_contour_in_guided_media(lib, ks, b, n_nodes, t_max):
+    lam, wt = lib.build_contour(n_nodes, *ks, b, t_max, 16)
+    lam_o, wt_o = O.contour(n_nodes, *ks, b, t_max)
+    assert np.max(np.abs(lam - lam_o)) <= 1e-12 * t_max
+    assert np.max(np.abs(wt - wt_o)) <= 1e-14 * t_max
+    # the guided-mode rule is active: the plain grading gives other nodes
+    lam_p, _ = O.contour(n_nodes, *ks, b, t_max, guided=False)
+    assert np.max(np.abs(lam - lam_p)) > 1e-3
+
+
 def test_contour_defaults_follow_the_paper(lib):
     # b = 0.2, t_max = max k + 20, 16-point panels (Sec. 6)
     lam, wt = lib.build_contour(500, 1.0, 3.0, 1.0)
