@@ -327,11 +327,12 @@ def run_ours(args, rank, world, local_rank):
             solve["speedup_mixed_vs_fp64"] = solve["fp64_s"] / solve["mixed_s"]
             ctxd.close()
     ctx.close()
-    batched = stack = inclusions = None
+    batched = stack = inclusions = contrast = None
     if world == 1 and not args.no_batched:
         batched = run_batched(args, dev, flush)
         stack = run_stack(args, w, dev, flush)
         inclusions = run_inclusions(args, w, dev, flush)
+        contrast = run_contrast(args)
 
     if rank != 0:
         return None
@@ -350,6 +351,7 @@ def run_ours(args, rank, world, local_rank):
         "batched": batched,
         "stack": stack,
         "inclusions": inclusions,
+        "contrast_sweep": contrast,
         "roofline": {"kernel": "k_translate_f32", "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": traffic, "flop_per_launch": flop, "launch_ms": tr_ms,
@@ -543,6 +545,44 @@ def run_inclusions(args, w, dev, flush):
                               "refinements": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"]}
     ctx.close()
     return out
+
+
+def run_contrast(args):
+    """Contrast sweep (Sec. 6, Example 2): 200 rotated three-lobed inclusions in a layer of
+    thickness 12 between half-spaces of k = 1, the layer's k2 from 1 to 20 (guided-mode media for
+    k2 > 1), FP64 GMRES to 1e-6 for each k2.  Per k2: context and layout setup, the inclusion's
+    scattering matrix (host), the solve; the sweep total."""
+    import torch
+
+    from paper_1407_3868_gb300 import inputs, lsms
+    cfg = inputs.CONTRAST
+    sh = cfg["shape"]
+    centres = inputs.contrast_layout()
+    theta = inputs.orientations(cfg["n"], 22)
+    curve = inputs.star_curve(sh["a1"], sh["a2"], sh["a3"], sh["n_pts"])
+    b = inputs.contour_b(cfg["x_hi"] - cfg["x_lo"])
+    rows = []
+    t_all = time.perf_counter()
+    for k2 in cfg["k2_values"]:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = lsms.Context(cfg["k1"], k2, cfg["k3"], cfg["d"], cfg["kp"], cfg["radius"], cfg["p"],
+                           cfg["n_nodes"], b=b, t_max=inputs.contrast_t_max(k2), panel_order=16,
+                           precision=lsms.LSMS_FP64)
+        ctx.set_particles(centres)
+        t1 = time.perf_counter()
+        smat = lsms.inclusion_scattering_matrix(cfg["p"], k2, cfg["kp"], cfg["radius"], curve)
+        ctx.set_scattering_matrix(smat)
+        ctx.set_orientations(theta)
+        t2 = time.perf_counter()
+        _, info = ctx.solve([[0.0, 1.0]], tol=cfg["tol"], maxiter=3000, raise_on_error=False)
+        t3 = time.perf_counter()
+        ctx.close()
+        rows.append({"k2": k2, "setup_s": t1 - t0, "matrix_s": t2 - t1, "solve_s": t3 - t2,
+                     "iters": info["iters"], "rel_res": info["rel_res_fp64"], "status": info["status"]})
+    return {"workload": "contrast200_p10_ns2048", "inclusions": cfg["n"], "p": cfg["p"],
+            "contour_nodes": cfg["n_nodes"], "tol": cfg["tol"], "precision": "fp64",
+            "total_s": time.perf_counter() - t_all, "per_k2": rows}
 
 
 def run_reference(args, rank):

@@ -197,3 +197,28 @@ def star_curve(a1: float, a2: float, a3: int, n_pts: int, rotation: float = 0.0,
 def orientations(n: int, seed: int) -> np.ndarray:
     """n rotation angles, uniform on [0, 2 pi) (NumPy PCG64, default_rng(seed))."""
     return np.random.default_rng(seed).uniform(0.0, 2.0 * np.pi, n)
+
+
+# ------------------------------------------------------------------------------------------------
+# Contrast sweep (Sec. 6, Example 2): 200 three-lobed inclusions (Eq. "par1" with a1 = 0.12,
+# a2 = 0.04, a3 = 3; enclosing radius 0.17) with kp = 2 in a layer of thickness 12 between two
+# half-spaces of k = 1, the layer's k2 swept from 1 to 20 (k2 > 1: a guided-mode layer); p = 10,
+# GMRES to 1e-6.  The layout (20 wide, centres at least 1 from the interfaces) stands in for the
+# paper's random placement.
+# ------------------------------------------------------------------------------------------------
+CONTRAST = dict(k1=1.0, k3=1.0, d=12.0, kp=2.0, radius=0.17, n=200, p=10, n_nodes=2048,
+                x_lo=-10.0, x_hi=10.0, clearance=1.0, seed=21, tol=1e-6,
+                shape=dict(a1=0.12, a2=0.04, a3=3, n_pts=256),
+                k2_values=[1.0, 2.0, 4.0, 6.0, 8.0, 10.0, 12.0, 14.0, 16.0, 18.0, 20.0])
+
+
+def contrast_layout(n: int = CONTRAST["n"], x_lo: float = CONTRAST["x_lo"], x_hi: float = CONTRAST["x_hi"],
+                    seed: int = CONTRAST["seed"]) -> np.ndarray:
+    c = CONTRAST
+    return layout(n, x_lo, x_hi, seed, radius=c["radius"], d=c["d"], clearance=c["clearance"])
+
+
+def contrast_t_max(k2: float) -> float:
+    """Gamma1 length for the contrast sweep: the integrands decay like exp(-2 t) beyond k2 (centres
+    at least 1.17 from the interfaces), so 30 past the largest wavenumber."""
+    return max(CONTRAST["k1"], k2) + 30.0

@@ -1,0 +1,89 @@
+"""GPU parity in a guided-mode medium (k2 above both half-spaces: poles of the layer response a
+distance b below the contour), with rotated three-lobed inclusions: the contrast medium of Sec. 6
+Example 2 (k1 = k3 = 1, d = 12, kp = 2) at k2 = 10, 24 inclusions, p = 10, against the oracle on the
+same contour.  FP64 1e-10, mixed operator 2e-5, mixed solve 1e-8."""
+import numpy as np
+import pytest
+
+from oracle import lsms_oracle as O
+from paper_1407_3868_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL_MIXED_OP = 2e-5
+TOL_MIXED = 1e-8
+K2 = 10.0
+
+
+@pytest.fixture(scope="module")
+def L():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1407_3868_gb300 import lsms
+    return lsms
+
+
+def rel(a, b, w=None):
+    a, b = np.asarray(a), np.asarray(b)
+    if w is not None:
+        a, b = a * w, b * w
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def case(L):
+    cfg = inputs.CONTRAST
+    sh = cfg["shape"]
+    c = inputs.contrast_layout(24, -4.0, 4.0, 5)
+    p, n_nodes, b, t_max = cfg["p"], 1024, inputs.contour_b(8.0), inputs.contrast_t_max(K2)
+    curve = inputs.star_curve(sh["a1"], sh["a2"], sh["a3"], sh["n_pts"])
+    S = O.inclusion_scattering_matrix(curve, p, K2, cfg["kp"])
+    th = inputs.orientations(24, 6)
+    med = O.Medium(cfg["k1"], K2, cfg["k3"], cfg["d"], cfg["kp"], cfg["radius"])
+    lam, wt = O.contour(n_nodes, cfg["k1"], K2, cfg["k3"], b, t_max)
+    pr = O.Problem(med, p, c, lam, wt, smat=S, theta=th)
+
+    def make(precision):
+        ctx = L.Context(cfg["k1"], K2, cfg["k3"], cfg["d"], cfg["kp"], cfg["radius"], p, n_nodes, b=b,
+                        t_max=t_max, panel_order=16, precision=precision)
+        ctx.set_particles(c)
+        ctx.set_scattering_matrix(L.inclusion_scattering_matrix(p, K2, cfg["kp"], cfg["radius"], curve))
+        ctx.set_orientations(th)
+        return ctx
+    src = np.array([[0.3, 1.0], [-2.0, 0.5]])
+    tg = inputs.observation_points(-5.0, 5.0, 16, 1.5)
+    hs = O.order_scale(p, K2, cfg["radius"])
+    return dict(make=make, pr=pr, lam=lam, wt=wt, src=src, tg=tg, hs=hs, n=24, p=p)
+
+
+def test_guided_contour_matches_the_oracle(case, L):
+    ctx = case["make"](0)
+    lam, wt = ctx.contour()
+    ctx.close()
+    assert np.abs(lam - case["lam"]).max() < 1e-12 and np.abs(wt - case["wt"]).max() < 1e-13
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOL_MIXED_OP)])
+def test_guided_apply(case, L, precision, tol):
+    x = inputs.random_coefficients(case["n"], case["p"], 2, 3) / case["hs"][None, None, :]
+    ctx = case["make"](precision)
+    y = ctx.apply(x)
+    ctx.close()
+    for r in range(2):
+        assert rel(y[r], case["pr"].apply(x[r]), case["hs"]) < tol, r
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOL_MIXED)])
+def test_guided_solve_and_fields(case, L, precision, tol):
+    ctx = case["make"](precision)
+    beta, info = ctx.solve(case["src"], tol=1e-12 if precision == 0 else 1e-11, maxiter=600)
+    assert info["status"] == 0
+    pr = case["pr"]
+    for s in range(2):
+        b_o = pr.solve_dense(case["src"][s])
+        assert rel(beta[s], b_o, case["hs"][None, :]) < tol, s
+        for which, name in ((L.FIELD_SCATTERED, "scattered"), (L.FIELD_PARTICLE, "particle")):
+            u = ctx.eval_field(case["tg"], s, which)
+            assert rel(u, pr.field_layer1(case["src"][s], b_o, case["tg"], name)) < tol, (s, name)
+    ctx.close()
