@@ -113,6 +113,15 @@ int lsms_create_stack(int n_layers, const double* k, const double* thickness, in
                       double kp, double radius, int p, const lsms_contour* contour, int precision,
                       lsms_ctx** out);
 
+/* lsms_create_stack_c — lsms_create_stack with complex wavenumbers k[n_layers] (interleaved re, im):
+ *   Im k > 0 makes a layer absorbing (a lossy substrate or film; gamma = -i sqrt(k^2 - lambda^2)
+ *   keeps Re gamma >= 0 on the contour).  Re k > 0 and Im k >= 0 everywhere; layer 1 (sources,
+ *   targets) and the particle layer must be lossless (Im k = 0).  The contour is graded to Re k.
+ *   Errors as lsms_create_stack. */
+int lsms_create_stack_c(int n_layers, const double* k, const double* thickness, int particle_layer,
+                        double kp, double radius, int p, const lsms_contour* contour, int precision,
+                        lsms_ctx** out);
+
 /* lsms_set_particles — disc centres (Sec. 3.2; Sec. 5).  centres_xy: 2n doubles (x0,y0,x1,...).
  *   Every disc must lie strictly inside the middle layer, with gaps >= 0.2 R between discs
  *   (10% of the diameter: the well-separation assumption of Sec. 1); otherwise

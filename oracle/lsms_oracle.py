@@ -102,30 +102,31 @@ def guided_band(branch_points):
     return (lo, hi) if hi > lo else None
 
 
-def contour_panel_breaks(n_panels: int, branch_points, b: float, t_max: float, band=None) -> np.ndarray:
+def contour_panel_breaks(n_panels: int, branch_points, b: float, t_max: float, band=None,
+                         graded: bool = False) -> np.ndarray:
     """Panel breakpoints of Gamma1 on t in [0, t_max].
 
-    Without a guided-mode band: breakpoints sit at 0, t_max and every branch point k_i < t_max,
-    and are graded geometrically toward each branch point (k_i +- b 2^j, j < L) with the largest L
-    that keeps the panel count at most n_panels.  Remaining panels are made by halving the longest
-    panel (first one on ties).  If even the ungraded set has too many panels, the branch points
-    are dropped.
+    Start from 0, t_max and the branch points k_i < t_max, then repeatedly halve the panel with
+    the largest length / (b + distance to the nearest branch point) (first one on ties) until there
+    are n_panels: a Gauss-Legendre panel's error is set by its length relative to the distance of
+    its nearest singularity, and every singularity lies at least b from Gamma1 (with fewer panels
+    than branch points, start from 0 and t_max alone).  With a
+    guided-mode band (lo, hi) the poles of the layer response lie on the real axis in between,
+    so a panel that meets the band counts as distance 0.
 
-    With a guided-mode band (lo, hi) (poles of the layer response on the real axis, a distance b
-    from Gamma1): start from 0, t_max and the branch points, then repeatedly halve the panel with
-    the largest length / (b + distance to the nearest branch point) (distance 0 for a panel that
-    meets the band; first one on ties) until there are n_panels: the length of a Gauss-Legendre
-    panel relative to the distance of its nearest singularity sets its error.
+    graded=True keeps the earlier rule, for comparison only: breakpoints graded geometrically
+    toward each branch point (k_i +- b 2^j, j < L) with the largest L that keeps the panel count at
+    most n_panels, then the longest panel halved until there are n_panels.
     """
     ks = sorted(set(float(k) for k in branch_points if 0.0 < k < t_max))
-    if band is not None:
-        lo, hi = float(band[0]), float(band[1])
+    if not graded:
+        lo, hi = (float(band[0]), float(band[1])) if band is not None else (0.0, -1.0)
         pts = sorted(set([0.0, float(t_max)] + ks))
-        if len(pts) - 1 > n_panels:
-            raise ValueError(f"contour: {len(pts) - 1} panels of Gamma1 needed, {n_panels} available")
+        if len(pts) - 1 > n_panels:                  # too few panels: no breakpoints at branch points
+            pts = [0.0, float(t_max)]
 
         def score(a, e):
-            if e > lo and a < hi:
+            if band is not None and e > lo and a < hi:
                 dist = 0.0
             else:
                 dist = t_max
@@ -141,6 +142,8 @@ def contour_panel_breaks(n_panels: int, branch_points, b: float, t_max: float, b
                     best, bs = i, sc
             pts.insert(best + 1, 0.5 * (pts[best] + pts[best + 1]))
         return np.array(pts)
+    if band is not None:
+        raise ValueError("contour_panel_breaks: the graded rule takes no guided-mode band")
     levels = 0
     while b * 2.0 ** levels < t_max:
         levels += 1
@@ -166,12 +169,13 @@ def contour_panel_breaks(n_panels: int, branch_points, b: float, t_max: float, b
 
 
 def contour(n_nodes: int, k1: float, k2: float, k3: float, b: float, t_max: float,
-            panel_order: int = 16, branch_points=None, guided=True):
+            panel_order: int = 16, branch_points=None, guided=True, graded=False):
     """Nodes lambda_nu and weights w_nu (d lambda included) of the discretised contour.
 
     Gamma1 (t - i b, 0 < t < t_max) and Gamma3 (its mirror t + i b, -t_max < t < 0) each carry
-    n1 = q * floor((N_S - q) / (2 q)) Gauss-Legendre nodes in panels of order q (guided-mode
-    media: see contour_panel_breaks; guided=False keeps the plain grading); Gamma2 (i s,
+    n1 = q * floor((N_S - q) / (2 q)) Gauss-Legendre nodes in panels of order q placed by
+    contour_panel_breaks (guided=False ignores a guided-mode band, graded=True takes the earlier
+    geometric grading; both for comparison only); Gamma2 (i s,
     s from b down to -b) carries the remaining N_S - 2 n1 nodes as one Gauss-Legendre rule.
     Returned in path order Gamma3 -> Gamma2 -> Gamma1.
     """
@@ -181,7 +185,8 @@ def contour(n_nodes: int, k1: float, k2: float, k3: float, b: float, t_max: floa
     if n1 <= 0 or n2 <= 0:
         raise ValueError("contour: too few nodes for the panel order")
     bp = (k1, k2, k3) if branch_points is None else branch_points
-    breaks = contour_panel_breaks(n1 // q, bp, b, t_max, guided_band(bp) if guided else None)
+    breaks = contour_panel_breaks(n1 // q, bp, b, t_max,
+                                  guided_band(bp) if guided and not graded else None, graded)
     x, w = np.polynomial.legendre.leggauss(q)
     t1, w1 = [], []
     for a, c in zip(breaks[:-1], breaks[1:]):
@@ -521,7 +526,9 @@ class Stack:
     """
 
     def __init__(self, ks, ds, m, kp, radius):
-        self.ks, self.ds, self.mi = [float(k) for k in ks], [float(d) for d in ds], int(m)
+        # complex k (Im k > 0) makes a layer absorbing; gamma's principal branch keeps Re >= 0
+        self.ks = [complex(k) if np.iscomplexobj(k) and complex(k).imag != 0.0 else float(np.real(k)) for k in ks]
+        self.ds, self.mi = [float(d) for d in ds], int(m)
         self.L = len(self.ks)
         if self.L < 3 or len(self.ds) != self.L - 2 or not 2 <= self.mi <= self.L - 1:
             raise ValueError("Stack: need L >= 3 layers, L - 2 thicknesses and 2 <= m <= L - 1")

@@ -141,15 +141,20 @@ int apply_device(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags,
 // ---------------------------------------------------------------------------------------------
 // create / destroy / particles
 // ---------------------------------------------------------------------------------------------
-int create_stack(const std::vector<double>& ks, const std::vector<double>& ds, int layer, double kp,
+int create_stack(const std::vector<cplx>& kc, const std::vector<double>& ds, int layer, double kp,
                  double radius, int p, const lsms_contour* contour, int precision, lsms_ctx** out) {
   if (!out) return fail(nullptr, LSMS_ERR_ARG, "out is NULL");
   *out = nullptr;
-  const int L = (int)ks.size();
+  const int L = (int)kc.size();
   if (L < 3 || (int)ds.size() != L - 2 || layer < 2 || layer > L - 1)
     return fail(nullptr, LSMS_ERR_ARG, "need n_layers >= 3, n_layers - 2 thicknesses and 2 <= particle_layer <= n_layers - 1");
-  for (double v : ks)
-    if (!std::isfinite(v) || !(v > 0.0)) return fail(nullptr, LSMS_ERR_ARG, "wavenumbers must be finite and > 0");
+  for (const cplx& v : kc)
+    if (!std::isfinite(v.real()) || !std::isfinite(v.imag()) || !(v.real() > 0.0) || !(v.imag() >= 0.0))
+      return fail(nullptr, LSMS_ERR_ARG, "wavenumbers must be finite with Re k > 0 and Im k >= 0");
+  if (kc[0].imag() != 0.0 || kc[layer - 1].imag() != 0.0)
+    return fail(nullptr, LSMS_ERR_ARG, "the source half-space (layer 1) and the particle layer must be lossless");
+  std::vector<double> ks(L);
+  for (int j = 0; j < L; ++j) ks[j] = kc[j].real();
   for (double v : ds)
     if (!std::isfinite(v) || !(v > 0.0)) return fail(nullptr, LSMS_ERR_ARG, "thicknesses must be finite and > 0");
   if (!std::isfinite(kp) || !(kp > 0.0) || !std::isfinite(radius) || !(radius > 0.0))
@@ -163,6 +168,7 @@ int create_stack(const std::vector<double>& ks, const std::vector<double>& ds, i
   lsms_ctx* c = new (std::nothrow) lsms_ctx();
   if (!c) return fail(nullptr, LSMS_ERR_OOM, "host allocation failed");
   c->ks = ks;
+  c->kc = kc;
   c->ds = ds;
   c->layer = layer;
   c->depth = 0.0;
@@ -218,7 +224,7 @@ int create_stack(const std::vector<double>& ks, const std::vector<double>& ds, i
 
 extern "C" int lsms_create(double k1, double k2, double k3, double d, double kp, double radius,
                            int p, const lsms_contour* contour, int precision, lsms_ctx** out) {
-  return create_stack({k1, k2, k3}, {d}, 2, kp, radius, p, contour, precision, out);
+  return create_stack({cplx(k1, 0.0), cplx(k2, 0.0), cplx(k3, 0.0)}, {d}, 2, kp, radius, p, contour, precision, out);
 }
 
 extern "C" int lsms_create_stack(int n_layers, const double* k, const double* thickness, int particle_layer,
@@ -228,8 +234,23 @@ extern "C" int lsms_create_stack(int n_layers, const double* k, const double* th
     if (out) *out = nullptr;
     return fail(nullptr, LSMS_ERR_ARG, "need n_layers >= 3 and non-NULL k and thickness arrays");
   }
-  return create_stack(std::vector<double>(k, k + n_layers), std::vector<double>(thickness, thickness + n_layers - 2),
-                      particle_layer, kp, radius, p, contour, precision, out);
+  std::vector<cplx> kc(n_layers);
+  for (int j = 0; j < n_layers; ++j) kc[j] = cplx(k[j], 0.0);
+  return create_stack(kc, std::vector<double>(thickness, thickness + n_layers - 2), particle_layer, kp, radius, p,
+                      contour, precision, out);
+}
+
+extern "C" int lsms_create_stack_c(int n_layers, const double* k, const double* thickness, int particle_layer,
+                                   double kp, double radius, int p, const lsms_contour* contour,
+                                   int precision, lsms_ctx** out) {
+  if (n_layers < 3 || !k || !thickness) {
+    if (out) *out = nullptr;
+    return fail(nullptr, LSMS_ERR_ARG, "need n_layers >= 3 and non-NULL k and thickness arrays");
+  }
+  std::vector<cplx> kc(n_layers);
+  for (int j = 0; j < n_layers; ++j) kc[j] = cplx(k[2 * j], k[2 * j + 1]);
+  return create_stack(kc, std::vector<double>(thickness, thickness + n_layers - 2), particle_layer, kp, radius, p,
+                      contour, precision, out);
 }
 
 extern "C" void lsms_destroy(lsms_ctx* c) {

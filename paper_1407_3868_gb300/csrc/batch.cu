@@ -54,7 +54,7 @@ extern "C" int lsms_set_layouts(lsms_ctx* c, int n_layouts, const int* counts, c
   long long off = 0;
   for (int l = 0; l < n_layouts; ++l) {
     lsms_ctx* k = nullptr;
-    int rc = create_stack(c->ks, c->ds, c->layer, c->kp, c->R, c->p, &c->contour, c->precision, &k);
+    int rc = create_stack(c->kc, c->ds, c->layer, c->kp, c->R, c->p, &c->contour, c->precision, &k);
     if (rc) {
       const std::string m = lsms_last_error(nullptr);
       batch_free(c);

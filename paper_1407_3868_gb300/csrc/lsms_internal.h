@@ -37,7 +37,8 @@ struct lsms_ctx {
   // ds[0..L-3]; the discs lie in layer `layer` (1-based, 2 <= layer <= L-1), whose top interface is
   // `depth` below y = 0.  k1 = ks[0], k2 = ks[layer-1] (the disc layer), k3 = ks[L-1], d = its
   // thickness.  Disc centres are kept in the disc layer's own frame (top interface at y = 0).
-  std::vector<double> ks, ds;
+  std::vector<double> ks, ds;       // ks: real parts of kc (the contour's branch points)
+  std::vector<cplx> kc;             // wavenumbers (Im k > 0: an absorbing layer)
   int layer = 2;
   double depth = 0.0;
   double k1 = 0, k2 = 0, k3 = 0, d = 0, kp = 0, R = 0;
@@ -137,13 +138,14 @@ struct lsms_ctx {
 // ------------------------------------------------------------------------------------------
 int build_contour(const lsms_contour& c, const std::vector<double>& ks, std::vector<cplx>& lam,
                   std::vector<cplx>& wt, std::string& err);
-// Gamma1 panel breakpoints; band_hi > band_lo marks a guided-mode band (empty result: too few panels)
+// Gamma1 panel breakpoints; band_hi > band_lo marks a guided-mode band
 std::vector<double> contour_panel_breaks(int n_panels, const double* ks, int nk, double b,
                                          double t_max, double band_lo, double band_hi);
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 std::vector<cplx> mie_diagonal(int p, double k2, double kp, double R);
 std::vector<double> hankel_scale(int p, double k2, double R);
 cplx gamma_of(cplx lam, double k);
+cplx gamma_of(cplx lam, cplx k);
 void build_node_tables(lsms_ctx* c);
 int validate_geometry(const lsms_ctx* c, int n, const double* xy, std::string& err);
 

@@ -7,8 +7,9 @@
 #include "lsms_internal.h"
 
 int ctx_fail(lsms_ctx* c, int code, const std::string& msg);
-// context for a stack of layers (ks top to bottom, interior thicknesses ds, discs in `layer`)
-int create_stack(const std::vector<double>& ks, const std::vector<double>& ds, int layer, double kp,
+// context for a stack of layers (kc top to bottom, Im k >= 0 and real in layer 1 and the particle
+// layer; interior thicknesses ds; discs in `layer`)
+int create_stack(const std::vector<cplx>& kc, const std::vector<double>& ds, int layer, double kp,
                  double radius, int p, const lsms_contour* contour, int precision, lsms_ctx** out);
 int ensure(lsms_ctx* c, DevBuf& b, size_t bytes);
 // Gaussian elimination with partial pivoting, a (n x n) x = b (n x nrhs), row-major; false if singular

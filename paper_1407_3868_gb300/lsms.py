@@ -19,7 +19,7 @@ APPLY_SCALED, APPLY_MIXED, APPLY_NO_TRANSLATION, APPLY_NO_REFLECTION, APPLY_ALPH
 FIELD_TOTAL, FIELD_SCATTERED, FIELD_PARTICLE = 0, 1, 2
 STATUS = {0: "OK", -1: "ARG", -2: "GEOMETRY", -3: "NOT_CONVERGED", -4: "NONFINITE", -5: "OOM",
           -6: "CUDA", -7: "STATE"}
-EXPORTS = ["lsms_create", "lsms_create_stack", "lsms_set_scattering_matrix", "lsms_set_orientations",
+EXPORTS = ["lsms_create", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
            "lsms_get_scattering_matrix", "lsms_inclusion_scattering_matrix", "lsms_set_particles", "lsms_apply", "lsms_apply_ex", "lsms_apply_dev",
            "lsms_translate", "lsms_aggregate", "lsms_reflect", "lsms_disaggregate", "lsms_incident",
            "lsms_get_contour", "lsms_get_scattering", "lsms_num_nodes", "lsms_num_particles",
@@ -63,6 +63,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     sig = {
         "lsms_create": (i, [d, d, d, d, d, d, i, ctypes.POINTER(Contour), i, ctypes.POINTER(_P)]),
         "lsms_create_stack": (i, [i, _D, _D, i, d, d, i, ctypes.POINTER(Contour), i, ctypes.POINTER(_P)]),
+        "lsms_create_stack_c": (i, [i, _D, _D, i, d, d, i, ctypes.POINTER(Contour), i, ctypes.POINTER(_P)]),
         "lsms_set_particles": (i, [_P, i, _D]),
         "lsms_set_scattering_matrix": (i, [_P, _D]),
         "lsms_set_orientations": (i, [_P, i, _D]),
@@ -122,7 +123,8 @@ class Context:
     def __init__(self, k1, k2, k3, d, kp, radius, p, n_nodes, b=0.0, t_max=0.0, panel_order=0,
                  precision=LSMS_FP64, stack=None):
         """Three layers (k1, k2, k3; middle thickness d), or with stack=(ks, thicknesses, m) any
-        number of layers (k1, k2, k3 and d are then ignored; lsms_create_stack)."""
+        number of layers (k1, k2, k3 and d are then ignored; lsms_create_stack, or with complex ks
+        — absorbing layers — lsms_create_stack_c)."""
         self.lib = load()
         self.p = p
         self.P = 2 * p + 1
@@ -132,12 +134,14 @@ class Context:
             rc = self.lib.lsms_create(k1, k2, k3, d, kp, radius, p, ctypes.byref(c), precision,
                                       ctypes.byref(h))
         else:
-            ks = np.ascontiguousarray(stack[0], dtype=np.float64)
+            lossy = np.iscomplexobj(np.asarray(stack[0]))
+            ks = np.ascontiguousarray(stack[0], dtype=np.complex128 if lossy else np.float64)
             ds = np.ascontiguousarray(stack[1], dtype=np.float64)
             if ds.size != max(ks.size - 2, 0):
                 raise LsmsError(-1, "stack: need len(ks) - 2 thicknesses")
-            rc = self.lib.lsms_create_stack(int(ks.size), _dptr(ks), _dptr(ds), int(stack[2]), kp,
-                                            radius, p, ctypes.byref(c), precision, ctypes.byref(h))
+            create = self.lib.lsms_create_stack_c if lossy else self.lib.lsms_create_stack
+            rc = create(int(ks.size), _dptr(ks), _dptr(ds), int(stack[2]), kp, radius, p, ctypes.byref(c),
+                        precision, ctypes.byref(h))
         if rc != 0:
             raise LsmsError(rc, self.lib.lsms_last_error(None).decode())
         self.h = h

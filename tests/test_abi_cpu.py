@@ -57,9 +57,10 @@ def test_library_contour_equals_oracle_contour_in_guided_media(lib, ks, b, n_nod
     lam_o, wt_o = O.contour(n_nodes, *ks, b, t_max)
     assert np.max(np.abs(lam - lam_o)) <= 1e-12 * t_max
     assert np.max(np.abs(wt - wt_o)) <= 1e-14 * t_max
-    # the guided-mode rule is active: the plain grading gives other nodes
-    lam_p, _ = O.contour(n_nodes, *ks, b, t_max, guided=False)
-    assert np.max(np.abs(lam - lam_p)) > 1e-3
+    # the band refines the panels between max(k1, k3) and k2 (where it is wider than the panels)
+    if ks[1] - max(ks[0], ks[2]) > 20 * b:
+        lam_p, _ = O.contour(n_nodes, *ks, b, t_max, guided=False)
+        assert np.max(np.abs(lam - lam_p)) > 1e-3
 
 
 def test_contour_defaults_follow_the_paper(lib):
