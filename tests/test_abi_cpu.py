@@ -179,3 +179,14 @@ def test_library_inclusion_matrix_rejects_bad_curves(lib):
     with pytest.raises(lib.LsmsError) as e:
         lib.inclusion_scattering_matrix(16, k2, kp, 0.25, (x, dx, ddx))
     assert e.value.code == -1
+
+
+def test_lossy_stack_arguments_are_validated_before_any_device_work(lib):
+    kp, R = 2.4 * math.pi, 0.25
+    for ks in ([2 * math.pi + 0.1j, 3 * math.pi, 4 * math.pi],      # lossy source half-space
+               [2 * math.pi, 3 * math.pi + 0.1j, 4 * math.pi],      # lossy particle layer
+               [2 * math.pi, 3 * math.pi, 4 * math.pi - 0.1j],      # gain
+               [2 * math.pi, 3 * math.pi, -4 * math.pi + 0.1j]):    # Re k <= 0
+        with pytest.raises(lib.LsmsError) as e:
+            lib.Context(0, 0, 0, 0, kp, R, 6, 128, stack=(np.array(ks), [2.0], 2))
+        assert e.value.code == -1, ks

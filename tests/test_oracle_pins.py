@@ -610,3 +610,51 @@ def test_contour_panel_rule_converges():
     err = lambda u: np.linalg.norm(u - ref) / np.linalg.norm(ref)
     assert err(field(768, 141.0, 10)) < 1e-10
     assert err(field(768, 141.0, 10, graded=True)) > 1e-7
+
+
+# ---------------------------------------------------------------------------------------------
+# Absorbing layers (complex wavenumbers)
+# ---------------------------------------------------------------------------------------------
+K3_LOSSY = MED["k3"] + 2.0j
+
+
+def test_lossy_substrate_particle_free_reflection_is_the_airy_slab():
+    st = O.Stack([MED["k1"], MED["k2"], K3_LOSSY], [MED["d"]], 2, MED["kp"], MED["radius"])
+    lam, _ = O.contour(256, MED["k1"], MED["k2"], MED["k3"], 0.2, 40.0)
+    src = np.array([0.3, 1.0])
+    inc = st.incident_density(lam, src)
+    sig = st.solve_layers(lam, inc=inc)
+    g1, g2, g3 = (O.gamma(lam, k) for k in (MED["k1"], MED["k2"], K3_LOSSY))
+    assert np.all(g3.real > 0)                                         # decays into the substrate
+    r12, r23 = (g1 - g2) / (g1 + g2), (g2 - g3) / (g2 + g3)
+    e2 = np.exp(-2 * g2 * MED["d"])
+    slab = (r12 + r23 * e2) / (1 + r12 * r23 * e2)
+    assert np.allclose(sig[:, 0] / inc, slab, rtol=1e-12, atol=1e-14)
+    # the lossless substrate gives another reflection (the loss is felt)
+    st0 = O.Stack([MED["k1"], MED["k2"], MED["k3"]], [MED["d"]], 2, MED["kp"], MED["radius"])
+    assert np.abs(st0.solve_layers(lam, inc=inc)[:, 0] - sig[:, 0]).max() > 1e-3 * np.abs(sig[:, 0]).max()
+
+
+def _lossy_fields(n_nodes, b, ks):
+    st = O.Stack(ks, [MED["d"]] + [0.9] * (len(ks) - 3), 2, MED["kp"], MED["radius"])
+    c = inputs.layout(8, -2.0, 2.0, 5, clearance=0.3)
+    src = np.array([0.2, 1.0])
+    tg = inputs.observation_points(-3.0, 3.0, 16, 1.5)
+    lam, wt = O.contour(n_nodes, MED["k1"], MED["k2"], MED["k3"], b, 50.0,
+                        branch_points=[complex(k).real for k in ks])
+    pr = O.Problem(st, 6, c, lam, wt)
+    return pr.field_layer1(src, pr.solve_dense(src), tg, "scattered")
+
+
+def test_lossy_fields_do_not_depend_on_the_contour_and_split_layers_are_invisible():
+    ks = [MED["k1"], MED["k2"], K3_LOSSY]
+    ref = _lossy_fields(1536, 0.15, ks)
+    for n_nodes, b in ((768, 0.25), (1024, 0.3)):
+        u = _lossy_fields(n_nodes, b, ks)
+        assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < 1e-10, (n_nodes, b)
+    # an interface inside the absorbing substrate (equal complex k on both sides) changes nothing
+    u4 = _lossy_fields(768, 0.25, [MED["k1"], MED["k2"], K3_LOSSY, K3_LOSSY])
+    assert np.linalg.norm(u4 - ref) / np.linalg.norm(ref) < 1e-10
+    # and the loss matters
+    u0 = _lossy_fields(768, 0.25, [MED["k1"], MED["k2"], MED["k3"]])
+    assert np.linalg.norm(u0 - ref) / np.linalg.norm(ref) > 1e-2

@@ -137,3 +137,37 @@ def test_three_layer_stack_equals_the_three_layer_context(L):
         b.set_particles(c)
         # the same arithmetic; only the order of FP64 atomic additions may differ between runs
         assert rel(b.apply(beta), a.apply(beta)) < 1e-13
+
+
+# ---------------------------------------------------------------------------------------------
+# Absorbing layers (lsms_create_stack_c): a lossy film below the disc layer, over a substrate
+# ---------------------------------------------------------------------------------------------
+KS_LOSSY = [2 * math.pi, 3 * math.pi, 3.4 * math.pi + 0.5j, 4 * math.pi]
+DS_LOSSY = [2.0, 0.7]
+
+
+@pytest.mark.parametrize("precision,tol_op,tol_solve", [(0, TOL64, TOL64), (1, TOL_MIXED_OP, TOL_MIXED)])
+def test_lossy_film_apply_solve_and_fields(L, precision, tol_op, tol_solve):
+    n, p, n_nodes, b, t_max = 20, 8, 512, 0.2, 80.0
+    local = inputs.layout(n, -3.0, 3.0, 44)
+    src = np.array([[0.3, 1.0], [-1.0, 0.7]])
+    tg = inputs.observation_points(-3.0, 3.0, 12, 1.5)
+    lam, wt = O.contour(n_nodes, KS_LOSSY[0], KS_LOSSY[1], KS_LOSSY[3].real, b, t_max,
+                        branch_points=[complex(k).real for k in KS_LOSSY])
+    pr = O.Problem(O.Stack(KS_LOSSY, DS_LOSSY, 2, KP, RADIUS), p, local, lam, wt)
+    hs = O.order_scale(p, KS_LOSSY[1], RADIUS)
+    with L.Context(0, 0, 0, 0, KP, RADIUS, p, n_nodes, b=b, t_max=t_max, panel_order=16,
+                   precision=precision, stack=(np.array(KS_LOSSY), DS_LOSSY, 2)) as ctx:
+        ctx.set_particles(local)                 # disc layer directly below y = 0: no depth shift
+        l2, w2 = ctx.contour()
+        assert np.abs(l2 - lam).max() < 1e-12 and np.abs(w2 - wt).max() < 1e-13
+        x = inputs.random_coefficients(n, p, 1, 12) / hs[None, None, :]
+        assert rel(ctx.apply(x)[0], pr.apply(x[0]), hs) < tol_op
+        beta, info = ctx.solve(src, tol=1e-12 if precision == 0 else 1e-11, maxiter=400)
+        assert info["status"] == 0
+        for s in range(2):
+            b_o = pr.solve_dense(src[s])
+            assert rel(beta[s], b_o, hs[None, :]) < tol_solve, s
+            for which, name in ((L.FIELD_SCATTERED, "scattered"), (L.FIELD_PARTICLE, "particle")):
+                u = ctx.eval_field(tg, s, which)
+                assert rel(u, pr.field_layer1(src[s], b_o, tg, name)) < tol_solve, (s, name)
