@@ -102,31 +102,31 @@ def guided_band(branch_points):
     return (lo, hi) if hi > lo else None
 
 
-def contour_panel_breaks(n_panels: int, branch_points, b: float, t_max: float, band=None,
-                         graded: bool = False) -> np.ndarray:
+def contour_panel_breaks(n_panels: int, branch_points, b: float, t_max: float, band=None) -> np.ndarray:
     """Panel breakpoints of Gamma1 on t in [0, t_max].
 
-    Start from 0, t_max and the branch points k_i < t_max, then repeatedly halve the panel with
-    the largest length / (b + distance to the nearest branch point) (first one on ties) until there
-    are n_panels: a Gauss-Legendre panel's error is set by its length relative to the distance of
-    its nearest singularity, and every singularity lies at least b from Gamma1 (with fewer panels
-    than branch points, start from 0 and t_max alone).  With a
-    guided-mode band (lo, hi) the poles of the layer response lie on the real axis in between,
-    so a panel that meets the band counts as distance 0.
+    Without a guided-mode band: breakpoints sit at 0, t_max and every branch point k_i < t_max,
+    and are graded geometrically toward each branch point (k_i +- b 2^j, j < L) with the largest L
+    that keeps the panel count at most n_panels.  Remaining panels are made by halving the longest
+    panel (first one on ties).  If even the ungraded set has too many panels, the branch points
+    are dropped.
 
-    graded=True keeps the earlier rule, for comparison only: breakpoints graded geometrically
-    toward each branch point (k_i +- b 2^j, j < L) with the largest L that keeps the panel count at
-    most n_panels, then the longest panel halved until there are n_panels.
+    With a guided-mode band (lo, hi) (poles of the layer response on the real axis, a distance b
+    from Gamma1): start from 0, t_max and the branch points (0 and t_max alone if there are fewer
+    panels than that), then repeatedly halve the panel with the largest length / (b + distance to
+    the nearest branch point) (distance 0 for a panel that meets the band; first one on ties) until
+    there are n_panels: the length of a Gauss-Legendre panel relative to the distance of its
+    nearest singularity sets its error.
     """
     ks = sorted(set(float(k) for k in branch_points if 0.0 < k < t_max))
-    if not graded:
-        lo, hi = (float(band[0]), float(band[1])) if band is not None else (0.0, -1.0)
+    if band is not None:
+        lo, hi = float(band[0]), float(band[1])
         pts = sorted(set([0.0, float(t_max)] + ks))
-        if len(pts) - 1 > n_panels:                  # too few panels: no breakpoints at branch points
+        if len(pts) - 1 > n_panels:
             pts = [0.0, float(t_max)]
 
         def score(a, e):
-            if band is not None and e > lo and a < hi:
+            if e > lo and a < hi:
                 dist = 0.0
             else:
                 dist = t_max
@@ -142,8 +142,6 @@ def contour_panel_breaks(n_panels: int, branch_points, b: float, t_max: float, b
                     best, bs = i, sc
             pts.insert(best + 1, 0.5 * (pts[best] + pts[best + 1]))
         return np.array(pts)
-    if band is not None:
-        raise ValueError("contour_panel_breaks: the graded rule takes no guided-mode band")
     levels = 0
     while b * 2.0 ** levels < t_max:
         levels += 1
@@ -174,8 +172,8 @@ def contour(n_nodes: int, k1: float, k2: float, k3: float, b: float, t_max: floa
 
     Gamma1 (t - i b, 0 < t < t_max) and Gamma3 (its mirror t + i b, -t_max < t < 0) each carry
     n1 = q * floor((N_S - q) / (2 q)) Gauss-Legendre nodes in panels of order q placed by
-    contour_panel_breaks (guided=False ignores a guided-mode band, graded=True takes the earlier
-    geometric grading; both for comparison only); Gamma2 (i s,
+    contour_panel_breaks (guided=False or graded=True: the geometric grading even in a
+    guided-mode medium, for comparison only); Gamma2 (i s,
     s from b down to -b) carries the remaining N_S - 2 n1 nodes as one Gauss-Legendre rule.
     Returned in path order Gamma3 -> Gamma2 -> Gamma1.
     """
@@ -185,8 +183,7 @@ def contour(n_nodes: int, k1: float, k2: float, k3: float, b: float, t_max: floa
     if n1 <= 0 or n2 <= 0:
         raise ValueError("contour: too few nodes for the panel order")
     bp = (k1, k2, k3) if branch_points is None else branch_points
-    breaks = contour_panel_breaks(n1 // q, bp, b, t_max,
-                                  guided_band(bp) if guided and not graded else None, graded)
+    breaks = contour_panel_breaks(n1 // q, bp, b, t_max, guided_band(bp) if guided and not graded else None)
     x, w = np.polynomial.legendre.leggauss(q)
     t1, w1 = [], []
     for a, c in zip(breaks[:-1], breaks[1:]):

@@ -57,37 +57,65 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
 // n_panels panels; then the longest panel is halved (first one on ties) until there are n_panels.
 std::vector<double> contour_panel_breaks(int n_panels, const double* ks, int nk, double b,
                                          double t_max, double band_lo, double band_hi) {
-  // Start from 0, t_max and the branch points, then halve the panel with the largest
-  // length / (b + distance to the nearest branch point) until there are n_panels (first one on
-  // ties): a Gauss-Legendre panel's error is set by its length relative to the distance of its
-  // nearest singularity.  In a guided-mode medium (band_hi > band_lo) the layer response has poles
-  // on the real axis in (band_lo, band_hi), a distance b below Gamma1: panels meeting that band
-  // count as distance 0.  With fewer panels than branch points, start from 0 and t_max alone.
   std::set<double> branch;
   for (int i = 0; i < nk; ++i)
     if (ks[i] > 0.0 && ks[i] < t_max) branch.insert(ks[i]);
-  const bool guided = band_hi > band_lo;
-  std::set<double> s0 = branch;
-  s0.insert(0.0);
-  s0.insert(t_max);
-  std::vector<double> pts(s0.begin(), s0.end());
-  if ((int)pts.size() - 1 > n_panels) pts = {0.0, t_max};     // too few panels for every branch point
-  auto score = [&](double a, double e) {
-    double dist;
-    if (guided && e > band_lo && a < band_hi) {
-      dist = 0.0;
-    } else {
-      dist = t_max;
-      for (double s : branch) dist = std::min(dist, (a <= s && s <= e) ? 0.0 : std::min(std::abs(a - s), std::abs(e - s)));
+  if (band_hi > band_lo) {
+    // guided-mode medium: poles of the layer response on the real axis in (band_lo, band_hi), a
+    // distance b below Gamma1.  Halve the panel with the largest length / (b + distance to the
+    // nearest branch point) (distance 0 for a panel meeting the band; first one on ties).
+    std::set<double> s0 = branch;
+    s0.insert(0.0);
+    s0.insert(t_max);
+    std::vector<double> pts(s0.begin(), s0.end());
+    if ((int)pts.size() - 1 > n_panels) pts = {0.0, t_max};   // too few panels for every branch point
+    auto score = [&](double a, double e) {
+      double dist;
+      if (e > band_lo && a < band_hi) {
+        dist = 0.0;
+      } else {
+        dist = t_max;
+        for (double s : branch) dist = std::min(dist, (a <= s && s <= e) ? 0.0 : std::min(std::abs(a - s), std::abs(e - s)));
+      }
+      return (e - a) / (b + dist);
+    };
+    while ((int)pts.size() - 1 < n_panels) {
+      int best = 0;
+      double bs = -1.0;
+      for (size_t i = 0; i + 1 < pts.size(); ++i) {
+        const double sc = score(pts[i], pts[i + 1]);
+        if (sc > bs) { bs = sc; best = (int)i; }
+      }
+      pts.insert(pts.begin() + best + 1, 0.5 * (pts[best] + pts[best + 1]));
     }
-    return (e - a) / (b + dist);
-  };
+    return pts;
+  }
+  int levels = 0;
+  while (b * std::ldexp(1.0, levels) < t_max) ++levels;
+  std::vector<double> pts;
+  for (int lev = levels; lev >= 0; --lev) {
+    std::set<double> cand = {0.0, t_max};
+    for (double k : branch) {
+      cand.insert(k);
+      for (int j = 0; j < lev; ++j) {
+        double off = b * std::ldexp(1.0, j);
+        double lo = k - off, hi = k + off;
+        if (lo > 0.0 && lo < t_max) cand.insert(lo);
+        if (hi > 0.0 && hi < t_max) cand.insert(hi);
+      }
+    }
+    if ((int)cand.size() - 1 <= n_panels) {
+      pts.assign(cand.begin(), cand.end());
+      break;
+    }
+  }
+  if (pts.empty()) pts = {0.0, t_max};
   while ((int)pts.size() - 1 < n_panels) {
     int best = 0;
-    double bs = -1.0;
+    double len = -1.0;
     for (size_t i = 0; i + 1 < pts.size(); ++i) {
-      const double sc = score(pts[i], pts[i + 1]);
-      if (sc > bs) { bs = sc; best = (int)i; }
+      double l = pts[i + 1] - pts[i];
+      if (l > len) { len = l; best = (int)i; }
     }
     pts.insert(pts.begin() + best + 1, 0.5 * (pts[best] + pts[best + 1]));
   }
