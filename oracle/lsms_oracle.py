@@ -443,6 +443,47 @@ def translate(centres: np.ndarray, beta: np.ndarray, k2: float, p: int, rows=Non
 # ----------------------------------------------------------------------------------------------
 # Layered medium: the 4x4 mode system (Sec. 2, Eq. "sommerfeldsys")
 # ----------------------------------------------------------------------------------------------
+def box_translate(centres: np.ndarray, beta: np.ndarray, k2: float, p: int, box_width: float,
+                  order: int, y_centre: float) -> np.ndarray:
+    """The translation of Lemma 3.1 with the far field compressed by boxes (the FMM remark of
+    Sec. 3.2 and the multipole shifts of Sec. 5.3), plainly: discs are grouped into boxes of width
+    box_width along x with centres C_i at height y_centre; pairs in the same or adjacent boxes are
+    translated directly; for boxes at least two apart the discs' H-expansions are shifted to their
+    box centre (Graf: B_q = sum_m sum_n J_{q-n}(k |x_m - C|) e^{-i (q - n) phi_m} beta^m_n),
+    translated box to box by Lemma 3.1 truncated at |q|, |nu| <= order, and shifted to each target
+    (Graf: alpha_nu = sum_q J_{q - nu}(k |x_l - C|) e^{i (q - nu) phi_l} A_q)."""
+    c = np.asarray(centres, dtype=float).reshape(-1, 2)
+    n_d = c.shape[0]
+    P = 2 * p + 1
+    x0 = c[:, 0].min()
+    box = np.floor((c[:, 0] - x0) / box_width).astype(int)
+    nb = int(box.max()) + 1 if n_d else 0
+    C = np.stack([x0 + (np.arange(nb) + 0.5) * box_width, np.full(nb, float(y_centre))], axis=1)
+    nn = np.arange(-p, p + 1)
+    qq = np.arange(-order, order + 1)
+    B = np.zeros((nb, 2 * order + 1), dtype=complex)
+    for m in range(n_d):
+        d = c[m] - C[box[m]]
+        r, ph = math.hypot(d[0], d[1]), math.atan2(d[1], d[0])
+        s = qq[:, None] - nn[None, :]
+        B[box[m]] += (bessel(s, k2 * r) * np.exp(-1j * s * ph)) @ beta[m]
+    A = np.zeros_like(B)
+    for i in range(nb):
+        for j in range(nb):
+            if abs(i - j) >= 2:
+                A[i] += translation_matrix(C[i], C[j], k2, order, order) @ B[j]
+    alpha = np.zeros((n_d, P), dtype=complex)
+    for l in range(n_d):
+        d = c[l] - C[box[l]]
+        r, ph = math.hypot(d[0], d[1]), math.atan2(d[1], d[0])
+        s = qq[None, :] - nn[:, None]
+        alpha[l] = (bessel(s, k2 * r) * np.exp(1j * s * ph)) @ A[box[l]]
+        for m in np.nonzero(np.abs(box - box[l]) <= 1)[0]:
+            if m != l:
+                alpha[l] += translation_matrix(c[l], c[m], k2, p, p) @ beta[m]
+    return alpha
+
+
 class Medium:
     """Three layers: k1 (y > 0), k2 (-d < y < 0), k3 (y < -d); discs kp, radius R."""
 

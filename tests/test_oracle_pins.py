@@ -637,3 +637,21 @@ def test_lossy_fields_do_not_depend_on_the_contour_and_split_layers_are_invisibl
     # and the loss matters
     u0 = _lossy_fields(1536, 0.25, [MED["k1"], MED["k2"], MED["k3"]])
     assert np.linalg.norm(u0 - ref) / np.linalg.norm(ref) > 1e-2
+
+
+def test_box_translation_converges_to_the_dense_translation():
+    # the far field through box expansions (Graf shifts + Lemma 3.1 between boxes two or more
+    # apart) against the all-pairs sum: the error falls geometrically with the box order once it
+    # passes k times the box radius (boxes of width 8 and height 2: k r = 38.9)
+    k2, p = MED["k2"], 8
+    n = 120
+    h = inputs.widened_half_width(n)
+    c = inputs.layout(n, -h, h, 7)
+    hs = O.order_scale(p, k2, MED["radius"])
+    beta = inputs.random_coefficients(n, p, 1, 3)[0] / hs[None, :]
+    ref = O.translate(c, beta, k2, p)
+    ws = hs * np.abs(O.mie_coefficients(p, k2, MED["kp"], MED["radius"]))
+    err = lambda a: np.linalg.norm((a - ref) * ws) / np.linalg.norm(ref * ws)
+    e50 = err(O.box_translate(c, beta, k2, p, 8.0, 50, -MED["d"] / 2))
+    e70 = err(O.box_translate(c, beta, k2, p, 8.0, 70, -MED["d"] / 2))
+    assert e70 < 1e-12 < 1e-6 < e50
