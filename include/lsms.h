@@ -297,6 +297,22 @@ int lsms_get_scattering_matrix(const lsms_ctx* ctx, double* s);
 int lsms_inclusion_scattering_matrix(int p, double k2, double kp, double radius, int n_pts,
                                      const double* curve, double* s_out);
 
+/* lsms_set_fmm — translate through boxes for long layouts of many discs (the FMM acceleration named
+ *   in Sec. 3.2; the multipole shifts of Sec. 5.3).  Discs are grouped into boxes of width
+ *   box_width along x (centres at the disc layer's mid-height); pairs in the same or adjacent boxes
+ *   are translated directly; farther pairs through box expansions of order `order`: Graf shifts
+ *   disc -> box (H -> H) and box -> disc (J -> J), and Lemma 3.1 between boxes two or more apart,
+ *   evaluated for all boxes at once as a convolution over (box offset, order difference) with
+ *   cuFFT.  FP64 throughout; used by lsms_apply*, lsms_translate and lsms_solve in both precisions.
+ *   order = 0: ceil(k2 r_box) + 32 with r_box = hypot(box_width, d) / 2 (about 1e-12 relative
+ *   in the scaled norm).  box_width <= 0 turns it off (all-pairs translation).  box_width must be
+ *   at least the disc layer's thickness d (boxes two apart are then well separated); order in
+ *   [p, 400].  The tables follow each lsms_set_particles / lsms_set_layouts (one set per layout).
+ *   Errors: LSMS_ERR_ARG, LSMS_ERR_OOM, LSMS_ERR_CUDA (cuFFT).
+ * lsms_get_fmm — number of boxes and the order in use (0, 0 when off or before particles). */
+int lsms_set_fmm(lsms_ctx* ctx, double box_width, int order);
+int lsms_get_fmm(const lsms_ctx* ctx, int* n_boxes, int* order);
+
 /* Host-only helpers: no GPU needed, no context.
  * lsms_build_contour — the nodes and weights lsms_create would use for `contour` (see
  *   lsms_contour; Sec. 5.1 Eq. "sommerseg"); nodes, weights: contour->n_nodes complex each.

@@ -107,12 +107,17 @@ int apply_device(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags,
   ++launches;
   if (c->timing) cudaEventRecord(c->ev[0], st);
   if (!(flags & LSMS_APPLY_NO_TRANSLATION)) {
-    // FP64: one kernel; mixed: FP32 copy of xs, the translation (+ the partial-sum reduction, or
-    // the packing of the tensor-core operands) and the near pairs
-    launches += mixed ? 3 + (c->near_nnz > 0 ? 1 : 0) : 1;
-    if (mixed) {
+    // box method (FP64, either precision): see fmm.cu; FP64: one kernel; mixed: FP32 copy of xs,
+    // the translation (+ the partial-sum reduction, or the packing of the tensor-core operands)
+    // and the near pairs
+    if (c->fmm.ready) {
+      launches += 3 * nrhs + 1;
+      if ((rc = fmm_translate(c, nrhs, xs, alpha, st))) return rc;
+    } else if (mixed) {
+      launches += 3 + (c->near_nnz > 0 ? 1 : 0);
       if ((rc = translate_mixed(c, nrhs, xs, alpha, st))) return rc;
     } else {
+      launches += 1;
       launch_translate_f64(c->d_cx, c->d_cy, n, c->p, c->k2, xs, alpha, nrhs, st);
     }
   } else {
@@ -269,6 +274,7 @@ extern "C" void lsms_destroy(lsms_ctx* c) {
   for (DevBuf* b : bufs)
     if (b->ptr) cudaFree(b->ptr);
   tc_free(c);
+  fmm_free(c);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   if (c->gm_ring) cudaFreeHost(c->gm_ring);
   for (cudaEvent_t e : c->ev)
@@ -326,6 +332,8 @@ extern "C" int lsms_set_particles(lsms_ctx* c, int n, const double* xy) {
     if ((rc = check_cuda(c, "set_particles"))) return rc;
     if ((rc = build_lowp_tables(c))) return rc;
   }
+  if (c->fmm.box_width > 0.0) return fmm_setup(c);
+  fmm_free(c);
   return LSMS_OK;
 }
 
@@ -381,7 +389,9 @@ extern "C" int lsms_translate(lsms_ctx* c, int nrhs, const double* beta, double*
   if (len == 0) return LSMS_OK;
   if ((rc = copy_in(c, c->ws_x, beta, len))) return rc;
   if ((rc = ensure(c, c->ws_alpha, len * sizeof(double2)))) return rc;
-  if (precision == LSMS_MIXED) {
+  if (c->fmm.ready) {
+    if ((rc = fmm_translate(c, nrhs, (const double2*)c->ws_x.ptr, (double2*)c->ws_alpha.ptr, c->stream))) return rc;
+  } else if (precision == LSMS_MIXED) {
     if ((rc = translate_mixed(c, nrhs, (const double2*)c->ws_x.ptr, (double2*)c->ws_alpha.ptr, c->stream))) return rc;
   } else
     launch_translate_f64(c->d_cx, c->d_cy, c->n, c->p, c->k2, (const double2*)c->ws_x.ptr, (double2*)c->ws_alpha.ptr, nrhs, c->stream);

@@ -62,6 +62,8 @@ extern "C" int lsms_set_layouts(lsms_ctx* c, int n_layouts, const int* counts, c
     }
     k->use_graphs = c->use_graphs;
     k->split_mult = c->split_mult;
+    k->fmm.box_width = c->fmm.box_width;
+    k->fmm.order_req = c->fmm.order_req;
     c->kids.push_back(k);
     if (c->dense && (rc = lsms_set_scattering_matrix(k, reinterpret_cast<const double*>(c->smat.data())))) {
       const std::string m = k->err;

@@ -1,0 +1,388 @@
+// Translation with the far field compressed by boxes (the FMM acceleration of Sec. 3.2; the
+// multipole shifts of Sec. 5.3), for long layouts of many discs.
+//
+// The discs are grouped into boxes of width w along x (centres C_i = (x0 + (i + 1/2) w, -d/2) in
+// the disc layer).  Pairs in the same or adjacent boxes are translated directly (Lemma 3.1, FP64,
+// as the all-pairs kernel).  For boxes two or more apart:
+//   M2M  B_i(q) = sum_{m in box i} sum_n J_{q-n}(k r_m) e^{-i (q-n) phi_m} beta^m_n     (Graf, H -> H)
+//   M2L  A_i(nu) = sum_{|i-j| >= 2} sum_q H_{q-nu}(k |i-j| w) e^{i (q-nu) phi_ij} B_j(q) (Lemma 3.1)
+//   L2L  alpha^l_nu += sum_q J_{q-nu}(k r_l) e^{i (q-nu) phi_l} A_{box(l)}(q)           (Graf, J -> J)
+// with (r_m, phi_m) the polar offset of disc m from its box centre, |q|, |nu| <= Q, and
+// phi_ij = 0 (i > j) or pi (i < j).  On the regular grid of box centres the M2L kernel depends only
+// on the box offset i - j and the order difference q - nu, so the M2L step is one two-dimensional
+// convolution (box index x order), done as a cyclic convolution with cuFFT on an n1 x n2 grid
+// (n1 >= 2 nb - 1, n2 >= 6Q + 1: no wrap-around reaches the outputs).  The Graf shift tables
+// J_s(k r_m) e^{i s phi_m}, |s| <= Q + p, and the transformed box kernel are built once per layout.
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "c64.cuh"
+#include "lsms_internal.h"
+#include "lsms_ops.h"
+
+namespace {
+
+constexpr int FW = 4;     // target discs (warps) per CTA of the near-field kernel
+constexpr int FCH = 32;   // source discs per staged chunk
+constexpr int FHS = 65;   // pair sequence stride (4p + 1 <= 61)
+
+// smallest n >= m whose prime factors are 2, 3, 5, 7 (sizes cuFFT handles fastest)
+int fft_size(int m) {
+  for (int n = std::max(m, 1);; ++n) {
+    int r = n;
+    for (int f : {2, 3, 5, 7})
+      while (r % f == 0) r /= f;
+    if (r == 1) return n;
+  }
+}
+
+// T_m[s + S] = J_s(k r_m) e^{i s phi_m}, s = -S..S, for every disc (thread per entry).
+__global__ void k_fmm_shift_table(const double* __restrict__ cx, const double* __restrict__ cy,
+                                  const int* __restrict__ dbox, int n, double x0, double w, double yc,
+                                  double k, int S, double2* __restrict__ tab) {
+  const long long W = 2LL * S + 1;
+  const long long total = (long long)n * W;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(i / W);
+    const int s = (int)(i - (long long)m * W) - S;
+    const double dx = cx[m] - (x0 + (dbox[m] + 0.5) * w), dy = cy[m] - yc;
+    const double r = hypot(dx, dy), ph = atan2(dy, dx);
+    const int as = s < 0 ? -s : s;
+    double j = (r > 0.0) ? jn(as, k * r) : (as == 0 ? 1.0 : 0.0);
+    if (s < 0 && (as & 1)) j = -j;                   // J_{-s} = (-1)^s J_s
+    double sn, cs;
+    sincos(s * ph, &sn, &cs);
+    tab[i] = make_double2(j * cs, j * sn);
+  }
+}
+
+// Box kernel on the cyclic grid: G[d mod n1][s mod n2] = H_s(k |d| w) e^{i s phi_d} for
+// 2 <= |d| <= nb - 1, |s| <= 2Q (phi_d = 0 for d > 0, pi for d < 0); zero elsewhere.  One thread
+// per offset: H_0, H_1 from the CUDA library, forward recurrence (the arguments are >= 2 k w).
+__global__ void k_fmm_box_kernel(int nb, int Q, double k, double w, int n1, int n2,
+                                 double2* __restrict__ grid) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nd = 2 * (nb - 1) + 1;
+  if (t >= nd) return;
+  const int d = t - (nb - 1);
+  const int ad = d < 0 ? -d : d;
+  if (ad < 2) return;
+  const double z = k * ad * w;
+  const int row = ((d % n1) + n1) % n1;
+  double2* g = grid + (size_t)row * n2;
+  double2 hm = make_double2(j0(z), y0(z)), hq = make_double2(j1(z), y1(z));
+  const double sg = d < 0 ? -1.0 : 1.0;              // e^{i s pi} = (-1)^s for d < 0
+  g[0] = hm;
+  for (int s = 1; s <= 2 * Q; ++s) {
+    const double f = (s & 1) ? sg : 1.0;
+    g[s] = make_double2(f * hq.x, f * hq.y);                                   // H_s e^{i s phi}
+    const double fn = (s & 1) ? -f : f;                                        // H_{-s} = (-1)^s H_s
+    g[n2 - s] = make_double2(fn * hq.x, fn * hq.y);
+    if (s < 2 * Q) {
+      const double c = 2.0 * s / z;
+      const double2 hn = make_double2(c * hq.x - hm.x, c * hq.y - hm.y);
+      hm = hq;
+      hq = hn;
+    }
+  }
+}
+
+__global__ void k_fmm_scale(double2* __restrict__ a, long long total, double s) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x)
+    a[i] = make_double2(a[i].x * s, a[i].y * s);
+}
+
+__global__ void k_fmm_mul(double2* __restrict__ a, const double2* __restrict__ b, long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x)
+    a[i] = cmul(a[i], b[i]);
+}
+
+// M2M: one CTA per box, thread t <-> box order q = t - Q; writes grid[i][(-q) mod n2].
+__global__ void k_fmm_m2m(const double2* __restrict__ xs, const int* __restrict__ perm,
+                          const int* __restrict__ bstart, const double2* __restrict__ tab, int p,
+                          int Q, int S, int n2, double2* __restrict__ grid) {
+  extern __shared__ double2 sbeta[];                 // [P] coefficients of the current disc
+  const int i = blockIdx.x, P = 2 * p + 1;
+  const int q = (int)threadIdx.x - Q;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int jj = bstart[i]; jj < bstart[i + 1]; ++jj) {
+    const int m = perm[jj];
+    __syncthreads();
+    if (threadIdx.x < P) sbeta[threadIdx.x] = xs[(size_t)m * P + threadIdx.x];
+    __syncthreads();
+    if (q >= -Q && q <= Q) {
+      const double2* t = tab + (size_t)m * (2 * S + 1) + S + q + p;    // t[-(n + p)] <-> s = q - n
+      for (int a = 0; a < P; ++a) {
+        const double2 tv = t[-a];                    // J_{q-n} e^{i (q-n) phi}, n = a - p
+        acc = cfma(make_double2(tv.x, -tv.y), sbeta[a], acc);
+      }
+    }
+  }
+  if (q >= -Q && q <= Q) grid[(size_t)i * n2 + ((-q) % n2 + n2) % n2] = acc;
+}
+
+// L2L: one warp per disc, lane <-> nu; alpha = sum_q T_l[q - nu] A_box(q), A(q) = grid[b][(-q) mod n2].
+__global__ void k_fmm_l2l(const double2* __restrict__ grid, const int* __restrict__ dbox,
+                          const double2* __restrict__ tab, int n, int p, int Q, int S, int n2,
+                          double2* __restrict__ alpha) {
+  const int l = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  const int P = 2 * p + 1;
+  if (l >= n || lane >= P) return;
+  const int nu = lane - p;
+  const double2* g = grid + (size_t)dbox[l] * n2;
+  const double2* t = tab + (size_t)l * (2 * S + 1) + S;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int q = -Q; q <= Q; ++q) acc = cfma(t[q - nu], g[((-q) % n2 + n2) % n2], acc);
+  alpha[(size_t)l * P + lane] = acc;
+}
+
+// Near field: CTA over FW consecutive targets in box order; sources from the neighbouring boxes,
+// staged in chunks; alpha += (pairs in the same or adjacent boxes), as the all-pairs FP64 kernel.
+__global__ void __launch_bounds__(FW * 32, 1)
+k_fmm_near(const double* __restrict__ scx, const double* __restrict__ scy, const int* __restrict__ perm,
+           const int* __restrict__ sbox, const int* __restrict__ bstart, int n, int nb, int p, double k,
+           const double2* __restrict__ xs, double2* __restrict__ alpha) {
+  extern __shared__ double2 smem[];
+  double2* sb = smem;                                 // [FCH][32]
+  double* sbs = (double*)(sb + FCH * 32);             // [FCH][32]
+  double2* sh = (double2*)(sbs + FCH * 32);           // [FW][FCH][FHS]
+  double* shs = (double*)(sh + FW * FCH * FHS);       // [FW][FCH][FHS]
+  __shared__ double cxs[FCH], cys[FCH];
+  __shared__ int bxs[FCH], ids[FCH];
+  const int P = 2 * p + 1;
+  const int r = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t0 = blockIdx.x * FW;
+  const int t = t0 + warp;                            // sorted target index
+  const bool tvalid = t < n;
+  const int l = tvalid ? perm[t] : -1;
+  const int bl = tvalid ? sbox[t] : 0;
+  const double xl = tvalid ? scx[t] : 0.0, yl = tvalid ? scy[t] : 0.0;
+  const int blo = sbox[t0], bhi = sbox[min(t0 + FW, n) - 1];
+  const int j_beg = bstart[max(blo - 1, 0)], j_end = bstart[min(bhi + 2, nb)];
+  const double2* xr = xs + (size_t)r * n * P;
+  double2* hw = sh + (size_t)warp * FCH * FHS;
+  double* hsw = shs + (size_t)warp * FCH * FHS;
+  double A = 0.0, B = 0.0, C = 0.0;
+  for (int j0c = j_beg; j0c < j_end; j0c += FCH) {
+    const int cnt = min(FCH, j_end - j0c);
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      cxs[threadIdx.x] = scx[j0c + threadIdx.x];
+      cys[threadIdx.x] = scy[j0c + threadIdx.x];
+      bxs[threadIdx.x] = sbox[j0c + threadIdx.x];
+      ids[threadIdx.x] = perm[j0c + threadIdx.x];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt * P; i += blockDim.x) {
+      const int s = i / P, q = i - s * P;
+      const double2 v = xr[(size_t)ids[s] * P + q];
+      sb[s * 32 + q] = v;
+      sbs[s * 32 + q] = v.x + v.y;
+    }
+    if (lane < cnt) {
+      double2* h = hw + lane * FHS;
+      double* hsm = hsw + lane * FHS;
+      const int db = bxs[lane] - bl;
+      if (tvalid && ids[lane] != l && db >= -1 && db <= 1) {
+        hankel_sequence_f64(xl - cxs[lane], yl - cys[lane], k, p, h, hsm);
+      } else {
+        for (int q = 0; q <= 4 * p; ++q) {
+          h[q] = make_double2(0.0, 0.0);
+          hsm[q] = 0.0;
+        }
+      }
+    }
+    __syncthreads();
+    if (tvalid && lane < P) {
+      for (int s = 0; s < cnt; ++s) {
+        const double2* hs = hw + s * FHS + 2 * p - lane;
+        const double* hss = hsw + s * FHS + 2 * p - lane;
+        const double2* bs = sb + s * 32;
+        const double* bss = sbs + s * 32;
+        for (int q = 0; q < P; ++q) {
+          const double2 hv = hs[q], bv = bs[q];
+          A = fma(hv.x, bv.x, A);
+          B = fma(hv.y, bv.y, B);
+          C = fma(hss[q], bss[q], C);
+        }
+      }
+    }
+  }
+  if (tvalid && lane < P) {
+    double2* o = alpha + (size_t)r * n * P + (size_t)l * P + lane;
+    *o = make_double2(o->x + (A - B), o->y + (C - A - B));
+  }
+}
+
+inline int blocks_for(long long total, int block) {
+  long long b = (total + block - 1) / block;
+  return (int)std::min<long long>(std::max<long long>(b, 1), 152LL * 32);
+}
+
+}  // namespace
+
+void fmm_free(lsms_ctx* c) {
+  FmmState& f = c->fmm;
+  void* ptrs[] = {f.d_perm, f.d_bstart, f.d_dbox, f.d_sbox, f.d_scx, f.d_scy, f.d_tab, f.d_khat, f.d_grid};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (f.has_plan) cufftDestroy((cufftHandle)f.plan);
+  const double w = f.box_width;
+  const int order = f.order_req;
+  f = FmmState();
+  f.box_width = w;
+  f.order_req = order;
+}
+
+// Box tables of the current layout (host grouping; device shift tables and transformed kernel).
+int fmm_setup(lsms_ctx* c) {
+  FmmState& f = c->fmm;
+  fmm_free(c);
+  if (!(f.box_width > 0.0) || c->n <= 0) return LSMS_OK;
+  const int n = c->n, p = c->p;
+  const double w = f.box_width;
+  const double rb = std::hypot(0.5 * w, 0.5 * c->d);
+  f.order = f.order_req > 0 ? f.order_req : (int)std::ceil(c->k2 * rb) + 32;
+  f.S = f.order + p;
+  // the device centres are x - xc (layout midpoint) and y in the disc layer's frame
+  std::vector<double> x(n);
+  for (int j = 0; j < n; ++j) x[j] = c->cx[j] - c->xc;
+  f.x0 = *std::min_element(x.begin(), x.end());
+  std::vector<int> dbox(n);
+  int nb = 0;
+  for (int j = 0; j < n; ++j) {
+    dbox[j] = (int)std::floor((x[j] - f.x0) / w);
+    nb = std::max(nb, dbox[j] + 1);
+  }
+  f.nb = nb;
+  std::vector<int> perm(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return dbox[a] < dbox[b]; });
+  std::vector<int> bstart(nb + 1, 0), sbox(n);
+  for (int j = 0; j < n; ++j) ++bstart[dbox[j] + 1];
+  for (int i = 0; i < nb; ++i) bstart[i + 1] += bstart[i];
+  std::vector<double> scx(n), scy(n);
+  for (int t = 0; t < n; ++t) {
+    sbox[t] = dbox[perm[t]];
+    scx[t] = x[perm[t]];
+    scy[t] = c->cy[perm[t]];
+  }
+  f.n1 = fft_size(2 * nb - 1);
+  f.n2 = fft_size(6 * f.order + 1);
+  const size_t gsz = (size_t)f.n1 * f.n2;
+  const size_t tsz = (size_t)n * (2 * f.S + 1);
+  if (cudaMalloc((void**)&f.d_perm, n * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_bstart, (nb + 1) * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_dbox, n * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_sbox, n * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_scx, n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_scy, n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_tab, tsz * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_khat, gsz * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_grid, gsz * sizeof(double2)) != cudaSuccess) {
+    cudaGetLastError();
+    fmm_free(c);
+    return ctx_fail(c, LSMS_ERR_OOM, "set_fmm: cudaMalloc failed for the box tables");
+  }
+  cudaMemcpy(f.d_perm, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(f.d_bstart, bstart.data(), (nb + 1) * sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(f.d_dbox, dbox.data(), n * sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(f.d_sbox, sbox.data(), n * sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(f.d_scx, scx.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(f.d_scy, scy.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+  cufftHandle plan;
+  if (cufftPlan2d(&plan, f.n1, f.n2, CUFFT_Z2Z) != CUFFT_SUCCESS) {
+    fmm_free(c);
+    return ctx_fail(c, LSMS_ERR_CUDA, "set_fmm: cuFFT plan creation failed");
+  }
+  f.plan = (int)plan;
+  f.has_plan = true;
+  cudaStream_t st = c->stream;
+  k_fmm_shift_table<<<blocks_for((long long)tsz, 256), 256, 0, st>>>(c->d_cx, c->d_cy, f.d_dbox, n, f.x0, w,
+                                                                      -0.5 * c->d, c->k2, f.S, f.d_tab);
+  cudaMemsetAsync(f.d_khat, 0, gsz * sizeof(double2), st);
+  const int nd = 2 * (nb - 1) + 1;
+  k_fmm_box_kernel<<<(nd + 127) / 128, 128, 0, st>>>(nb, f.order, c->k2, w, f.n1, f.n2, f.d_khat);
+  cufftSetStream(plan, st);
+  if (cufftExecZ2Z(plan, (cufftDoubleComplex*)f.d_khat, (cufftDoubleComplex*)f.d_khat, CUFFT_FORWARD) !=
+      CUFFT_SUCCESS) {
+    fmm_free(c);
+    return ctx_fail(c, LSMS_ERR_CUDA, "set_fmm: cuFFT failed");
+  }
+  k_fmm_scale<<<blocks_for((long long)gsz, 256), 256, 0, st>>>(f.d_khat, (long long)gsz, 1.0 / (double)gsz);
+  cudaStreamSynchronize(st);
+  f.ready = true;
+  return check_cuda(c, "set_fmm");
+}
+
+// alpha = T xs for nrhs right-hand sides through the box method (FP64).  Launches: per right-hand
+// side M2M, the pointwise product and L2L, plus one near-field launch (cuFFT's own kernels aside).
+int fmm_translate(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st) {
+  FmmState& f = c->fmm;
+  const int n = c->n, p = c->p, P = 2 * p + 1;
+  if (!f.ready) return ctx_fail(c, LSMS_ERR_STATE, "box translation tables are not built");
+  const size_t gsz = (size_t)f.n1 * f.n2;
+  cufftHandle plan = (cufftHandle)f.plan;
+  cufftSetStream(plan, st);
+  for (int r = 0; r < nrhs; ++r) {
+    const double2* x = xs + (size_t)r * n * P;
+    double2* a = alpha + (size_t)r * n * P;
+    cudaMemsetAsync(f.d_grid, 0, gsz * sizeof(double2), st);
+    k_fmm_m2m<<<f.nb, ((2 * f.order + 1 + 31) / 32) * 32, P * sizeof(double2), st>>>(
+        x, f.d_perm, f.d_bstart, f.d_tab, p, f.order, f.S, f.n2, f.d_grid);
+    if (cufftExecZ2Z(plan, (cufftDoubleComplex*)f.d_grid, (cufftDoubleComplex*)f.d_grid, CUFFT_FORWARD) !=
+        CUFFT_SUCCESS)
+      return ctx_fail(c, LSMS_ERR_CUDA, "box translation: cuFFT failed");
+    k_fmm_mul<<<blocks_for((long long)gsz, 256), 256, 0, st>>>(f.d_grid, f.d_khat, (long long)gsz);
+    if (cufftExecZ2Z(plan, (cufftDoubleComplex*)f.d_grid, (cufftDoubleComplex*)f.d_grid, CUFFT_INVERSE) !=
+        CUFFT_SUCCESS)
+      return ctx_fail(c, LSMS_ERR_CUDA, "box translation: cuFFT failed");
+    k_fmm_l2l<<<(int)(((long long)n * 32 + 255) / 256), 256, 0, st>>>(f.d_grid, f.d_dbox, f.d_tab, n, p, f.order,
+                                                                       f.S, f.n2, a);
+  }
+  const size_t smem = (size_t)(FCH * 32 + FW * FCH * FHS) * (sizeof(double2) + sizeof(double));
+  static std::once_flag attr;
+  std::call_once(attr, [smem] {
+    cudaFuncSetAttribute(k_fmm_near, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  dim3 grid((n + FW - 1) / FW, nrhs);
+  k_fmm_near<<<grid, FW * 32, smem, st>>>(f.d_scx, f.d_scy, f.d_perm, f.d_sbox, f.d_bstart, n, f.nb, p, c->k2, xs,
+                                           alpha);
+  return LSMS_OK;
+}
+
+extern "C" int lsms_set_fmm(lsms_ctx* c, double box_width, int order) {
+  if (!c) return LSMS_ERR_ARG;
+  if (!std::isfinite(box_width) || order < 0 || order > 400)
+    return ctx_fail(c, LSMS_ERR_ARG, "set_fmm: box_width must be finite and 0 <= order <= 400");
+  if (box_width > 0.0 && !(box_width >= c->d))
+    return ctx_fail(c, LSMS_ERR_ARG, "set_fmm: box_width must be at least the disc layer's thickness");
+  if (order > 0 && order < c->p) return ctx_fail(c, LSMS_ERR_ARG, "set_fmm: order must be >= p");
+  cudaStreamSynchronize(c->stream);
+  batch_clear_graphs(c);
+  c->fmm.box_width = box_width > 0.0 ? box_width : 0.0;
+  c->fmm.order_req = order;
+  for (lsms_ctx* k : c->kids) {
+    const int rc = lsms_set_fmm(k, box_width, order);
+    if (rc) return ctx_fail(c, rc, std::string("set_fmm: ") + k->err);
+  }
+  if (c->kids.empty() && c->n >= 0) return fmm_setup(c);
+  return LSMS_OK;
+}
+
+extern "C" int lsms_get_fmm(const lsms_ctx* c, int* n_boxes, int* order) {
+  if (!c) return LSMS_ERR_ARG;
+  if (n_boxes) *n_boxes = c->fmm.ready ? c->fmm.nb : 0;
+  if (order) *order = c->fmm.ready ? c->fmm.order : 0;
+  return LSMS_OK;
+}

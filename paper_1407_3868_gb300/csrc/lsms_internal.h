@@ -32,6 +32,26 @@ struct NodeTables {
   std::vector<cplx> udis;           // [2 ns][P]: w/(4 pi g2) i^m w-^m, ... w+^m
 };
 
+// Box-compressed translation (fmm.cu): tables of the current layout.
+struct FmmState {
+  double box_width = 0.0;           // > 0: translation through boxes of this width
+  int order_req = 0;                // requested box order (0: k2 r_box + 32)
+  bool ready = false;
+  int order = 0, S = 0, nb = 0, n1 = 0, n2 = 0;
+  double x0 = 0.0;
+  int* d_perm = nullptr;            // [n] discs sorted by box
+  int* d_bstart = nullptr;          // [nb + 1]
+  int* d_dbox = nullptr;            // [n] box of each disc
+  int* d_sbox = nullptr;            // [n] box in sorted order
+  double* d_scx = nullptr;          // [n] sorted centres (device frame)
+  double* d_scy = nullptr;
+  double2* d_tab = nullptr;         // [n][2S + 1] J_s(k r) e^{i s phi}
+  double2* d_khat = nullptr;        // [n1][n2] transformed box kernel / (n1 n2)
+  double2* d_grid = nullptr;        // [n1][n2] work grid
+  int plan = 0;                     // cufftHandle
+  bool has_plan = false;
+};
+
 struct lsms_ctx {
   // medium and discretisation: layers ks[0] (top) .. ks[L-1] (bottom), interior thicknesses
   // ds[0..L-3]; the discs lie in layer `layer` (1-based, 2 <= layer <= L-1), whose top interface is
@@ -53,6 +73,7 @@ struct lsms_ctx {
   double2* d_smt = nullptr;         // [2][P][P] transposed ([n][l]): S, diag(|H_l(k2 R)|) S
   DevBuf theta_buf;                 // [N] rotation angles (valid when has_theta)
   bool has_theta = false;
+  FmmState fmm;
   std::vector<double> hscale;       // |H_n(k2 R)|, P
 
   // discs

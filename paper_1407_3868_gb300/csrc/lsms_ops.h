@@ -14,6 +14,10 @@ int create_stack(const std::vector<cplx>& kc, const std::vector<double>& ds, int
 int ensure(lsms_ctx* c, DevBuf& b, size_t bytes);
 // Gaussian elimination with partial pivoting, a (n x n) x = b (n x nrhs), row-major; false if singular
 bool solve_small(std::vector<cplx>& a, int n, std::vector<cplx>& b, int nrhs);
+// box-compressed translation (fmm.cu)
+int fmm_setup(lsms_ctx* c);
+void fmm_free(lsms_ctx* c);
+int fmm_translate(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st);
 // drop the captured batched applications (their kernels depend on the context's settings)
 void batch_clear_graphs(lsms_ctx* c);
 int check_cuda(lsms_ctx* c, const char* where);

@@ -19,7 +19,7 @@ APPLY_SCALED, APPLY_MIXED, APPLY_NO_TRANSLATION, APPLY_NO_REFLECTION, APPLY_ALPH
 FIELD_TOTAL, FIELD_SCATTERED, FIELD_PARTICLE = 0, 1, 2
 STATUS = {0: "OK", -1: "ARG", -2: "GEOMETRY", -3: "NOT_CONVERGED", -4: "NONFINITE", -5: "OOM",
           -6: "CUDA", -7: "STATE"}
-EXPORTS = ["lsms_create", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
+EXPORTS = ["lsms_create", "lsms_set_fmm", "lsms_get_fmm", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
            "lsms_get_scattering_matrix", "lsms_inclusion_scattering_matrix", "lsms_set_particles", "lsms_apply", "lsms_apply_ex", "lsms_apply_dev",
            "lsms_translate", "lsms_aggregate", "lsms_reflect", "lsms_disaggregate", "lsms_incident",
            "lsms_get_contour", "lsms_get_scattering", "lsms_num_nodes", "lsms_num_particles",
@@ -66,6 +66,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsms_create_stack_c": (i, [i, _D, _D, i, d, d, i, ctypes.POINTER(Contour), i, ctypes.POINTER(_P)]),
         "lsms_set_particles": (i, [_P, i, _D]),
         "lsms_set_scattering_matrix": (i, [_P, _D]),
+        "lsms_set_fmm": (i, [_P, d, i]),
+        "lsms_get_fmm": (i, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "lsms_set_orientations": (i, [_P, i, _D]),
         "lsms_get_scattering_matrix": (i, [_P, _D]),
         "lsms_inclusion_scattering_matrix": (i, [i, d, d, d, i, _D, _D]),
@@ -193,6 +195,15 @@ class Context:
         m = ctypes.c_double()
         self._check(self.lib.lsms_autotune(self.h, ctypes.byref(m)))
         return m.value
+
+    def set_fmm(self, box_width: float, order: int = 0):
+        """Translation through boxes of this width (0: all pairs); order 0 picks k2 r_box + 32."""
+        self._check(self.lib.lsms_set_fmm(self.h, float(box_width), int(order)))
+
+    def fmm_info(self):
+        nb, q = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.lsms_get_fmm(self.h, ctypes.byref(nb), ctypes.byref(q)))
+        return nb.value, q.value
 
     def set_scattering_matrix(self, smat=None):
         """Dense prototype scattering matrix [P][P] (None: the disc's Mie diagonal)."""

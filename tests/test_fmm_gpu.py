@@ -1,0 +1,144 @@
+"""GPU parity of the translation through boxes (lsms_set_fmm: the FMM acceleration named in Sec. 3.2,
+with the multipole shifts of Sec. 5.3) against the oracle.
+
+(a) With a low box order the library reproduces the oracle's own box translation (the same
+    approximation, the same boxes) to FP64 rounding; (b) at the default order it matches the all-pairs
+    translation of Lemma 3.1 to 1e-10 in the scaled norm (the FP64 bar), on layouts of 400 and 1000
+    discs with ragged boxes, for several right-hand sides; (c) the operator and the solves with boxes
+    agree with the all-pairs ones; (d) at 50,000 discs (10x the bench layout, 6136 boxes) sampled rows
+    match the oracle's row-by-row translation; (e) batches of layouts carry the setting."""
+import numpy as np
+import pytest
+
+from oracle import lsms_oracle as O
+from paper_1407_3868_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL_MIXED = 1e-8
+
+
+@pytest.fixture(scope="module")
+def L():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1407_3868_gb300 import lsms
+    return lsms
+
+
+def rel(a, b, w=None):
+    a, b = np.asarray(a), np.asarray(b)
+    if w is not None:
+        a, b = a * w, b * w
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def workload(n, p, seed, n_nodes=256):
+    h = inputs.widened_half_width(n)
+    return inputs.Workload(f"fmm{n}", n, p, n_nodes, 141.0, -h, h, seed, np.array([[0.0, 1.0]]),
+                           inputs.observation_points(-h, h, 16, 1.5), 1e-11)
+
+
+def weights(w):
+    m = w.medium
+    hs = O.order_scale(w.p, m["k2"], m["radius"])
+    return hs, hs * np.abs(O.mie_coefficients(w.p, m["k2"], m["kp"], m["radius"]))
+
+
+def test_box_translation_equals_the_oracles_box_translation(L):
+    w = workload(160, 8, 51)
+    c = w.centres()
+    hs, ws = weights(w)
+    beta = inputs.random_coefficients(w.n, w.p, 1, 2) / hs[None, None, :]
+    with L.context_for(w) as ctx:
+        ctx.set_particles(c)
+        ctx.set_fmm(4.0, 30)                      # deliberately low order: a visible truncation
+        nb, q = ctx.fmm_info()
+        assert q == 30 and nb >= 10
+        a = ctx.translate(beta)[0]
+    a_box = O.box_translate(c, beta[0], w.medium["k2"], w.p, 4.0, 30, -w.medium["d"] / 2)
+    a_all = O.translate(c, beta[0], w.medium["k2"], w.p)
+    assert rel(a_box, a_all, ws) > 1e-6           # the truncation is visible ...
+    assert rel(a, a_box, ws) < 1e-12              # ... and the library makes the same one
+
+
+@pytest.mark.parametrize("n,width,nrhs", [(400, 4.0, 3), (1000, 6.0, 1)])
+def test_box_translation_matches_all_pairs(L, n, width, nrhs):
+    w = workload(n, 12, 52)
+    c = w.centres()
+    hs, ws = weights(w)
+    beta = inputs.random_coefficients(w.n, w.p, nrhs, 3) / hs[None, None, :]
+    with L.context_for(w) as ctx:
+        ctx.set_particles(c)
+        dense = ctx.translate(beta)
+        ctx.set_fmm(width)
+        a = ctx.translate(beta)
+    for r in range(nrhs):
+        assert rel(a[r], dense[r], ws) < TOL64, r
+    rows = [0, 1, n // 2, n - 1]
+    a_o = O.translate(c, beta[0], w.medium["k2"], w.p, rows=rows)
+    assert rel(a[0][rows], a_o, ws) < TOL64
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOL_MIXED)])
+def test_operator_and_solve_with_boxes(L, precision, tol):
+    w = workload(600, 10, 53)
+    c = w.centres()
+    hs, _ = weights(w)
+    x = inputs.random_coefficients(w.n, w.p, 1, 4) / hs[None, None, :]
+    with L.context_for(w, precision) as ctx:
+        ctx.set_particles(c)
+        y0 = ctx.apply(x, L.APPLY_MIXED if precision else 0)
+        b0, i0 = ctx.solve(w.sources, tol=1e-11, maxiter=1500)
+        u0 = ctx.eval_field(w.targets, 0, L.FIELD_SCATTERED)
+        ctx.set_fmm(4.0)
+        y1 = ctx.apply(x, L.APPLY_MIXED if precision else 0)
+        b1, i1 = ctx.solve(w.sources, tol=1e-11, maxiter=1500)
+        u1 = ctx.eval_field(w.targets, 0, L.FIELD_SCATTERED)
+    assert i0["status"] == 0 and i1["status"] == 0
+    assert rel(y1, y0, hs) < (TOL64 if precision == 0 else 2e-5)
+    assert rel(b1, b0, hs) < tol and rel(u1, u0) < tol
+
+
+def test_fifty_thousand_discs_on_sampled_rows(L):
+    n, p = 50000, 14
+    h = inputs.widened_half_width(n)
+    w = inputs.Workload("disc50000_p14_ns1024", n, p, 1024, 163.0, -h, h, 6, np.array([[0.0, 1.0]]),
+                        inputs.observation_points(-h, h, 64, 1.5), 1e-8)
+    c = w.centres()
+    hs, ws = weights(w)
+    beta = inputs.random_coefficients(n, p, 1, 5) / hs[None, None, :]
+    with L.context_for(w) as ctx:
+        ctx.set_particles(c)
+        ctx.set_fmm(4.0)
+        nb, q = ctx.fmm_info()
+        assert nb > 6000 and q == 54
+        a = ctx.translate(beta)[0]
+    rows = [0, 1, 7, n // 3, n // 2, n - 2, n - 1]
+    a_o = O.translate(c, beta[0], w.medium["k2"], p, rows=rows)
+    assert rel(a[rows], a_o, ws) < TOL64
+
+
+def test_batch_of_layouts_with_boxes(L):
+    base = workload(300, 8, 54)
+    lay = [inputs.layout(150, -40.0, 40.0, 61), inputs.layout(260, -65.0, 65.0, 62)]
+    hs, _ = weights(base)
+    x = inputs.random_coefficients(410, base.p, 1, 6)[0] / hs[None, :]
+    with L.context_for(base) as ctx:
+        ctx.set_layouts(lay)
+        y_dense = ctx.apply(x)
+        ctx.set_fmm(4.0)
+        y_box = ctx.apply(x)
+    assert rel(y_box, y_dense, hs) < TOL64
+
+
+def test_box_settings_are_validated(L):
+    w = workload(50, 6, 55)
+    with L.context_for(w) as ctx:
+        for bw, q in ((1.0, 0), (4.0, 3), (4.0, 401), (float("nan"), 0)):
+            with pytest.raises(L.LsmsError) as e:
+                ctx.set_fmm(bw, q)
+            assert e.value.code == -1, (bw, q)
+        ctx.set_fmm(0.0)
+        assert ctx.fmm_info() == (0, 0)
