@@ -111,7 +111,7 @@ int apply_device(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags,
     // the translation (+ the partial-sum reduction, or the packing of the tensor-core operands)
     // and the near pairs
     if (c->fmm.ready) {
-      launches += 3 * nrhs + 1;
+      launches += (c->fmm.dmin > 2 ? 4 : 3) * nrhs + 1;
       if ((rc = fmm_translate(c, nrhs, xs, alpha, st))) return rc;
     } else if (mixed) {
       launches += 3 + (c->near_nnz > 0 ? 1 : 0);

@@ -11,7 +11,10 @@
 // phi_ij = 0 (i > j) or pi (i < j).  On the regular grid of box centres the M2L kernel depends only
 // on the box offset i - j and the order difference q - nu, so the M2L step is one two-dimensional
 // convolution (box index x order), done as a cyclic convolution with cuFFT on an n1 x n2 grid
-// (n1 >= 2 nb - 1, n2 >= 6Q + 1: no wrap-around reaches the outputs).  The Graf shift tables
+// (n1 >= 2 nb - 1, n2 >= 6Q + 1: no wrap-around reaches the outputs).  An FFT spreads its rounding
+// over all outputs in proportion to the largest kernel entry, and H_s(z) grows fast once |s| > z,
+// so offsets with k |d| w < 2Q + 2 (where orders up to 2Q leave the oscillatory range) are
+// translated box by box instead and left out of the FFT kernel.  The Graf shift tables
 // J_s(k r_m) e^{i s phi_m}, |s| <= Q + p, and the transformed box kernel are built once per layout.
 #include <cufft.h>
 
@@ -63,16 +66,16 @@ __global__ void k_fmm_shift_table(const double* __restrict__ cx, const double* _
 }
 
 // Box kernel on the cyclic grid: G[d mod n1][s mod n2] = H_s(k |d| w) e^{i s phi_d} for
-// 2 <= |d| <= nb - 1, |s| <= 2Q (phi_d = 0 for d > 0, pi for d < 0); zero elsewhere.  One thread
+// dmin <= |d| <= nb - 1, |s| <= 2Q (phi_d = 0 for d > 0, pi for d < 0); zero elsewhere.  One thread
 // per offset: H_0, H_1 from the CUDA library, forward recurrence (the arguments are >= 2 k w).
-__global__ void k_fmm_box_kernel(int nb, int Q, double k, double w, int n1, int n2,
+__global__ void k_fmm_box_kernel(int nb, int Q, double k, double w, int n1, int n2, int dmin,
                                  double2* __restrict__ grid) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int nd = 2 * (nb - 1) + 1;
   if (t >= nd) return;
   const int d = t - (nb - 1);
   const int ad = d < 0 ? -d : d;
-  if (ad < 2) return;
+  if (ad < dmin) return;
   const double z = k * ad * w;
   const int row = ((d % n1) + n1) % n1;
   double2* g = grid + (size_t)row * n2;
@@ -108,7 +111,7 @@ __global__ void k_fmm_mul(double2* __restrict__ a, const double2* __restrict__ b
 // M2M: one CTA per box, thread t <-> box order q = t - Q; writes grid[i][(-q) mod n2].
 __global__ void k_fmm_m2m(const double2* __restrict__ xs, const int* __restrict__ perm,
                           const int* __restrict__ bstart, const double2* __restrict__ tab, int p,
-                          int Q, int S, int n2, double2* __restrict__ grid) {
+                          int Q, int S, int n2, double2* __restrict__ grid, double2* __restrict__ bq) {
   extern __shared__ double2 sbeta[];                 // [P] coefficients of the current disc
   const int i = blockIdx.x, P = 2 * p + 1;
   const int q = (int)threadIdx.x - Q;
@@ -126,7 +129,56 @@ __global__ void k_fmm_m2m(const double2* __restrict__ xs, const int* __restrict_
       }
     }
   }
-  if (q >= -Q && q <= Q) grid[(size_t)i * n2 + ((-q) % n2 + n2) % n2] = acc;
+  if (q >= -Q && q <= Q) {
+    grid[(size_t)i * n2 + ((-q) % n2 + n2) % n2] = acc;
+    bq[(size_t)i * (2 * Q + 1) + q + Q] = acc;
+  }
+}
+
+// M2L for the offsets 2 <= |d| < dmin, box by box: grid[i][(-nu) mod n2] += sum_d sum_q
+// hd[d][q - nu] B_{i-d}(q), hd[(sign, |d| - 2)][s + 2Q] = H_s(k |d| w) e^{i s phi_d}.
+__global__ void k_fmm_m2l_direct(const double2* __restrict__ bq, const double2* __restrict__ hd, int nb,
+                                 int Q, int dmin, int n2, double2* __restrict__ grid) {
+  const int i = blockIdx.x;
+  const int nu = (int)threadIdx.x - Q;
+  if (nu < -Q || nu > Q) return;
+  const int W = 2 * Q + 1, H = 4 * Q + 1;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int ad = 2; ad < dmin; ++ad)
+    for (int sg = 0; sg < 2; ++sg) {
+      const int d = sg ? -ad : ad;
+      const int j = i - d;
+      if (j < 0 || j >= nb) continue;
+      const double2* h = hd + (size_t)(2 * (ad - 2) + sg) * H + 2 * Q - nu;   // h[q] <-> s = q - nu
+      const double2* b = bq + (size_t)j * W + Q;
+      for (int q = -Q; q <= Q; ++q) acc = cfma(h[q], b[q], acc);
+    }
+  double2* g = grid + (size_t)i * n2 + ((-nu) % n2 + n2) % n2;
+  *g = cadd(*g, acc);
+}
+
+// Direct-offset kernels hd[(sign, |d| - 2)][s + 2Q], 2 <= |d| < dmin (one thread per offset).
+__global__ void k_fmm_direct_table(int Q, double k, double w, int dmin, double2* __restrict__ hd) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * (dmin - 2)) return;
+  const int ad = 2 + t / 2, sg = t & 1;
+  const double z = k * ad * w;
+  const double sgn = sg ? -1.0 : 1.0;
+  double2* h = hd + (size_t)t * (4 * Q + 1) + 2 * Q;
+  double2 hm = make_double2(j0(z), y0(z)), hq = make_double2(j1(z), y1(z));
+  h[0] = hm;
+  for (int s = 1; s <= 2 * Q; ++s) {
+    const double f = (s & 1) ? sgn : 1.0;
+    h[s] = make_double2(f * hq.x, f * hq.y);
+    const double fn = (s & 1) ? -f : f;
+    h[-s] = make_double2(fn * hq.x, fn * hq.y);
+    if (s < 2 * Q) {
+      const double c = 2.0 * s / z;
+      const double2 hn = make_double2(c * hq.x - hm.x, c * hq.y - hm.y);
+      hm = hq;
+      hq = hn;
+    }
+  }
 }
 
 // L2L: one warp per disc, lane <-> nu; alpha = sum_q T_l[q - nu] A_box(q), A(q) = grid[b][(-q) mod n2].
@@ -233,7 +285,8 @@ inline int blocks_for(long long total, int block) {
 
 void fmm_free(lsms_ctx* c) {
   FmmState& f = c->fmm;
-  void* ptrs[] = {f.d_perm, f.d_bstart, f.d_dbox, f.d_sbox, f.d_scx, f.d_scy, f.d_tab, f.d_khat, f.d_grid};
+  void* ptrs[] = {f.d_perm, f.d_bstart, f.d_dbox, f.d_sbox, f.d_scx, f.d_scy, f.d_tab, f.d_khat, f.d_grid,
+                  f.d_bq, f.d_hd};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (f.has_plan) cufftDestroy((cufftHandle)f.plan);
@@ -277,6 +330,9 @@ int fmm_setup(lsms_ctx* c) {
     scx[t] = x[perm[t]];
     scy[t] = c->cy[perm[t]];
   }
+  // offsets below dmin go box by box (k |d| w < 2Q + 2)
+  f.dmin = 2;
+  while (c->k2 * f.dmin * w < 2.0 * f.order + 2.0) ++f.dmin;
   f.n1 = fft_size(2 * nb - 1);
   f.n2 = fft_size(6 * f.order + 1);
   const size_t gsz = (size_t)f.n1 * f.n2;
@@ -289,7 +345,10 @@ int fmm_setup(lsms_ctx* c) {
       cudaMalloc((void**)&f.d_scy, n * sizeof(double)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_tab, tsz * sizeof(double2)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_khat, gsz * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc((void**)&f.d_grid, gsz * sizeof(double2)) != cudaSuccess) {
+      cudaMalloc((void**)&f.d_grid, gsz * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_bq, (size_t)nb * (2 * f.order + 1) * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_hd, (size_t)std::max(1, 2 * (f.dmin - 2)) * (4 * f.order + 1) * sizeof(double2)) !=
+          cudaSuccess) {
     cudaGetLastError();
     fmm_free(c);
     return ctx_fail(c, LSMS_ERR_OOM, "set_fmm: cudaMalloc failed for the box tables");
@@ -312,7 +371,8 @@ int fmm_setup(lsms_ctx* c) {
                                                                       -0.5 * c->d, c->k2, f.S, f.d_tab);
   cudaMemsetAsync(f.d_khat, 0, gsz * sizeof(double2), st);
   const int nd = 2 * (nb - 1) + 1;
-  k_fmm_box_kernel<<<(nd + 127) / 128, 128, 0, st>>>(nb, f.order, c->k2, w, f.n1, f.n2, f.d_khat);
+  k_fmm_box_kernel<<<(nd + 127) / 128, 128, 0, st>>>(nb, f.order, c->k2, w, f.n1, f.n2, f.dmin, f.d_khat);
+  if (f.dmin > 2) k_fmm_direct_table<<<(2 * (f.dmin - 2) + 63) / 64, 64, 0, st>>>(f.order, c->k2, w, f.dmin, f.d_hd);
   cufftSetStream(plan, st);
   if (cufftExecZ2Z(plan, (cufftDoubleComplex*)f.d_khat, (cufftDoubleComplex*)f.d_khat, CUFFT_FORWARD) !=
       CUFFT_SUCCESS) {
@@ -338,8 +398,9 @@ int fmm_translate(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cuda
     const double2* x = xs + (size_t)r * n * P;
     double2* a = alpha + (size_t)r * n * P;
     cudaMemsetAsync(f.d_grid, 0, gsz * sizeof(double2), st);
-    k_fmm_m2m<<<f.nb, ((2 * f.order + 1 + 31) / 32) * 32, P * sizeof(double2), st>>>(
-        x, f.d_perm, f.d_bstart, f.d_tab, p, f.order, f.S, f.n2, f.d_grid);
+    const int qthreads = ((2 * f.order + 1 + 31) / 32) * 32;
+    k_fmm_m2m<<<f.nb, qthreads, P * sizeof(double2), st>>>(x, f.d_perm, f.d_bstart, f.d_tab, p, f.order, f.S,
+                                                           f.n2, f.d_grid, f.d_bq);
     if (cufftExecZ2Z(plan, (cufftDoubleComplex*)f.d_grid, (cufftDoubleComplex*)f.d_grid, CUFFT_FORWARD) !=
         CUFFT_SUCCESS)
       return ctx_fail(c, LSMS_ERR_CUDA, "box translation: cuFFT failed");
@@ -347,6 +408,8 @@ int fmm_translate(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cuda
     if (cufftExecZ2Z(plan, (cufftDoubleComplex*)f.d_grid, (cufftDoubleComplex*)f.d_grid, CUFFT_INVERSE) !=
         CUFFT_SUCCESS)
       return ctx_fail(c, LSMS_ERR_CUDA, "box translation: cuFFT failed");
+    if (f.dmin > 2)
+      k_fmm_m2l_direct<<<f.nb, qthreads, 0, st>>>(f.d_bq, f.d_hd, f.nb, f.order, f.dmin, f.n2, f.d_grid);
     k_fmm_l2l<<<(int)(((long long)n * 32 + 255) / 256), 256, 0, st>>>(f.d_grid, f.d_dbox, f.d_tab, n, p, f.order,
                                                                        f.S, f.n2, a);
   }

@@ -37,7 +37,7 @@ struct FmmState {
   double box_width = 0.0;           // > 0: translation through boxes of this width
   int order_req = 0;                // requested box order (0: k2 r_box + 32)
   bool ready = false;
-  int order = 0, S = 0, nb = 0, n1 = 0, n2 = 0;
+  int order = 0, S = 0, nb = 0, n1 = 0, n2 = 0, dmin = 2;   // dmin: smallest offset in the FFT
   double x0 = 0.0;
   int* d_perm = nullptr;            // [n] discs sorted by box
   int* d_bstart = nullptr;          // [nb + 1]
@@ -48,6 +48,8 @@ struct FmmState {
   double2* d_tab = nullptr;         // [n][2S + 1] J_s(k r) e^{i s phi}
   double2* d_khat = nullptr;        // [n1][n2] transformed box kernel / (n1 n2)
   double2* d_grid = nullptr;        // [n1][n2] work grid
+  double2* d_bq = nullptr;          // [nb][2Q + 1] box coefficients (for the direct offsets)
+  double2* d_hd = nullptr;          // [2 (dmin - 2)][4Q + 1] kernels of the direct offsets
   int plan = 0;                     // cufftHandle
   bool has_plan = false;
 };
