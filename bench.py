@@ -327,12 +327,13 @@ def run_ours(args, rank, world, local_rank):
             solve["speedup_mixed_vs_fp64"] = solve["fp64_s"] / solve["mixed_s"]
             ctxd.close()
     ctx.close()
-    batched = stack = inclusions = contrast = None
+    batched = stack = inclusions = contrast = large = None
     if world == 1 and not args.no_batched:
         batched = run_batched(args, dev, flush)
         stack = run_stack(args, w, dev, flush)
         inclusions = run_inclusions(args, w, dev, flush)
         contrast = run_contrast(args)
+        large = run_large(args, dev, flush)
 
     if rank != 0:
         return None
@@ -352,6 +353,7 @@ def run_ours(args, rank, world, local_rank):
         "stack": stack,
         "inclusions": inclusions,
         "contrast_sweep": contrast,
+        "large": large,
         "roofline": {"kernel": "k_translate_f32", "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": traffic, "flop_per_launch": flop, "launch_ms": tr_ms,
@@ -583,6 +585,64 @@ def run_contrast(args):
     return {"workload": "contrast200_p10_ns2048", "inclusions": cfg["n"], "p": cfg["p"],
             "contour_nodes": cfg["n_nodes"], "tol": cfg["tol"], "precision": "fp64",
             "total_s": time.perf_counter() - t_all, "per_k2": rows}
+
+
+def run_large(args, dev, flush):
+    """N >> 5000: 50,000 discs (the bench medium and density, p = 14, 1024 nodes, 24,544 wide).
+    Operator applications with the translation through boxes (width 4, FP64; the contour part
+    mixed) against the all-pairs FP32 translation, the box translation alone, and the mixed
+    solve at 1e-8 with boxes."""
+    import numpy as np
+    import torch
+
+    from paper_1407_3868_gb300 import inputs, lsms
+    n, p = 50000, 14
+    h = inputs.widened_half_width(n)
+    w = inputs.Workload("disc50000_p14_ns1024", n, p, 1024, 163.0, -h, h, 6, np.array([[0.0, 1.0]]),
+                        inputs.observation_points(-h, h, 64, 1.5), 1e-8)
+    ctx = lsms.context_for(w, lsms.LSMS_MIXED)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.set_particles(w.centres())
+    torch.cuda.synchronize()
+    t_particles = time.perf_counter() - t0
+    x = torch.from_numpy(inputs.random_coefficients(n, p, 1, 500)).to(dev)
+    y = torch.empty_like(x)
+    fl_m = lsms.APPLY_SCALED | lsms.APPLY_MIXED
+    out = {"workload": w.name, "discs": n, "p": p, "contour_nodes": w.n_nodes, "set_particles_s": t_particles}
+    for _ in range(2):
+        ctx.apply_dev(x, y, fl_m)
+    torch.cuda.synchronize()
+    out["all_pairs_mixed"] = {"ms_per_apply": time_device(lambda: ctx.apply_dev(x, y, fl_m), 3, flush),
+                              "translation": "FP32 all pairs"}
+    t0 = time.perf_counter()
+    ctx.set_fmm(4.0)
+    torch.cuda.synchronize()
+    nb, q = ctx.fmm_info()
+    out["boxes"] = {"box_width": 4.0, "boxes": nb, "order": q, "setup_s": time.perf_counter() - t0}
+    for _ in range(2):
+        ctx.apply_dev(x, y, fl_m)
+    torch.cuda.synchronize()
+    ms = time_device(lambda: ctx.apply_dev(x, y, fl_m), max(3, min(args.steps, 10)), flush)
+    ctx.set_timing(True)
+    tr = []
+    for _ in range(3):
+        ctx.apply_dev(x, y, fl_m)
+        tr.append(ctx.last_timing()[0])
+    ctx.set_timing(False)
+    out["boxes_mixed"] = {"ms_per_apply": ms, "translate_ms": statistics.mean(tr),
+                          "translation": "FP64 through boxes"}
+    ms64 = time_device(lambda: ctx.apply_dev(x, y, lsms.APPLY_SCALED), 3, flush)
+    out["boxes_fp64"] = {"ms_per_apply": ms64}
+    out["speedup_boxes_vs_all_pairs_mixed"] = out["all_pairs_mixed"]["ms_per_apply"] / ms
+    if not args.no_solve:
+        t0 = time.perf_counter()
+        _, info = ctx.solve(w.sources, tol=1e-8, maxiter=3000, raise_on_error=False)
+        out["mixed_solve"] = {"tol": 1e-8, "s": time.perf_counter() - t0, "iters": info["iters"],
+                              "refinements": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"],
+                              "status": info["status"]}
+    ctx.close()
+    return out
 
 
 def run_reference(args, rank):
