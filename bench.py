@@ -95,6 +95,8 @@ def parse():
     ap.add_argument("--baseline-rows", type=int, default=40,
                     help="target rows of the oracle's bounded sample for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing")
+    ap.add_argument("--section", choices=["large"], default=None,
+                    help="run one extra measurement alone and print its dict (for profiling)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -625,13 +627,27 @@ def run_large(args, dev, flush):
     torch.cuda.synchronize()
     ms = time_device(lambda: ctx.apply_dev(x, y, fl_m), max(3, min(args.steps, 10)), flush)
     ctx.set_timing(True)
-    tr = []
+    tr, near, far = [], [], []
     for _ in range(3):
+        flush.fill_(1.0)
         ctx.apply_dev(x, y, fl_m)
         tr.append(ctx.last_timing()[0])
+        pairs, f_ms, n_ms = ctx.fmm_stats()
+        far.append(f_ms)
+        near.append(n_ms)
     ctx.set_timing(False)
     out["boxes_mixed"] = {"ms_per_apply": ms, "translate_ms": statistics.mean(tr),
+                          "far_ms": statistics.mean(far), "near_ms": statistics.mean(near),
                           "translation": "FP64 through boxes"}
+    # the near field (pairs in adjacent boxes, FP64 CUDA cores) against the FP64 peak
+    P = 2 * p + 1
+    flop = 8.0 * P * P * pairs
+    near_ms = statistics.mean(near)
+    out["roofline_near"] = {"kernel": "k_fmm_near", "bound": "alu", "pairs": pairs, "flop_per_launch": flop,
+                            "launch_ms": near_ms, "achieved": flop / (near_ms / 1e3) / 1e12,
+                            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": flop / (near_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                            "peak_note": "derived FP64: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz"}
     ms64 = time_device(lambda: ctx.apply_dev(x, y, lsms.APPLY_SCALED), 3, flush)
     out["boxes_fp64"] = {"ms_per_apply": ms64}
     out["speedup_boxes_vs_all_pairs_mixed"] = out["all_pairs_mixed"]["ms_per_apply"] / ms
@@ -676,6 +692,16 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.section == "large":
+        import torch
+
+        import __graft_entry__
+        __graft_entry__.build()
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        print(json.dumps({"section": "large", "large": run_large(args, dev, flush)}))
+        return
     if args.impl == "reference":
         line = run_reference(args, rank)
     else:

@@ -309,9 +309,13 @@ int lsms_inclusion_scattering_matrix(int p, double k2, double kp, double radius,
  *   at least the disc layer's thickness d (boxes two apart are then well separated); order in
  *   [p, 400].  The tables follow each lsms_set_particles / lsms_set_layouts (one set per layout).
  *   Errors: LSMS_ERR_ARG, LSMS_ERR_OOM, LSMS_ERR_CUDA (cuFFT).
- * lsms_get_fmm — number of boxes and the order in use (0, 0 when off or before particles). */
+ * lsms_get_fmm — number of boxes and the order in use (0, 0 when off or before particles).
+ * lsms_fmm_stats — ordered disc pairs translated directly (adjacent boxes), and, when timing is on
+ *   (lsms_set_timing), the device milliseconds of the last box translation's far part (shifts,
+ *   FFT convolution) and near part; waits for that translation.  NULL outputs are skipped. */
 int lsms_set_fmm(lsms_ctx* ctx, double box_width, int order);
 int lsms_get_fmm(const lsms_ctx* ctx, int* n_boxes, int* order);
+int lsms_fmm_stats(lsms_ctx* ctx, long long* near_pairs, double* far_ms, double* near_ms);
 
 /* Host-only helpers: no GPU needed, no context.
  * lsms_build_contour — the nodes and weights lsms_create would use for `contour` (see

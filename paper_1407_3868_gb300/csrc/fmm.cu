@@ -290,6 +290,8 @@ void fmm_free(lsms_ctx* c) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (f.has_plan) cufftDestroy((cufftHandle)f.plan);
+  for (cudaEvent_t e : f.ev)
+    if (e) cudaEventDestroy(e);
   const double w = f.box_width;
   const int order = f.order_req;
   f = FmmState();
@@ -324,6 +326,12 @@ int fmm_setup(lsms_ctx* c) {
   std::vector<int> bstart(nb + 1, 0), sbox(n);
   for (int j = 0; j < n; ++j) ++bstart[dbox[j] + 1];
   for (int i = 0; i < nb; ++i) bstart[i + 1] += bstart[i];
+  f.near_pairs = 0;
+  for (int b = 0; b < nb; ++b) {
+    const long long own = bstart[b + 1] - bstart[b];
+    const long long nbr = bstart[std::min(b + 2, nb)] - bstart[std::max(b - 1, 0)];
+    f.near_pairs += own * (nbr - 1);
+  }
   std::vector<double> scx(n), scy(n);
   for (int t = 0; t < n; ++t) {
     sbox[t] = dbox[perm[t]];
@@ -394,6 +402,10 @@ int fmm_translate(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cuda
   const size_t gsz = (size_t)f.n1 * f.n2;
   cufftHandle plan = (cufftHandle)f.plan;
   cufftSetStream(plan, st);
+  const bool timed = c->timing && !c->kids.size();
+  if (timed && !f.ev[0])
+    for (cudaEvent_t& e : f.ev) cudaEventCreate(&e);
+  if (timed) cudaEventRecord(f.ev[0], st);
   for (int r = 0; r < nrhs; ++r) {
     const double2* x = xs + (size_t)r * n * P;
     double2* a = alpha + (size_t)r * n * P;
@@ -419,8 +431,11 @@ int fmm_translate(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cuda
     cudaFuncSetAttribute(k_fmm_near, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   dim3 grid((n + FW - 1) / FW, nrhs);
+  if (timed) cudaEventRecord(f.ev[1], st);
   k_fmm_near<<<grid, FW * 32, smem, st>>>(f.d_scx, f.d_scy, f.d_perm, f.d_sbox, f.d_bstart, n, f.nb, p, c->k2, xs,
                                            alpha);
+  if (timed) cudaEventRecord(f.ev[2], st);
+  f.timed = timed;
   return LSMS_OK;
 }
 
@@ -440,6 +455,21 @@ extern "C" int lsms_set_fmm(lsms_ctx* c, double box_width, int order) {
     if (rc) return ctx_fail(c, rc, std::string("set_fmm: ") + k->err);
   }
   if (c->kids.empty() && c->n >= 0) return fmm_setup(c);
+  return LSMS_OK;
+}
+
+extern "C" int lsms_fmm_stats(lsms_ctx* c, long long* near_pairs, double* far_ms, double* near_ms) {
+  if (!c) return LSMS_ERR_ARG;
+  FmmState& f = c->fmm;
+  if (near_pairs) *near_pairs = f.ready ? f.near_pairs : 0;
+  float a = 0.0f, b = 0.0f;
+  if (f.timed && f.ev[2]) {
+    if (cudaEventSynchronize(f.ev[2]) != cudaSuccess || cudaEventElapsedTime(&a, f.ev[0], f.ev[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&b, f.ev[1], f.ev[2]) != cudaSuccess)
+      return check_cuda(c, "fmm_stats");
+  }
+  if (far_ms) *far_ms = a;
+  if (near_ms) *near_ms = b;
   return LSMS_OK;
 }
 

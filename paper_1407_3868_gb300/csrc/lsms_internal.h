@@ -52,6 +52,9 @@ struct FmmState {
   double2* d_hd = nullptr;          // [2 (dmin - 2)][4Q + 1] kernels of the direct offsets
   int plan = 0;                     // cufftHandle
   bool has_plan = false;
+  long long near_pairs = 0;         // ordered pairs translated directly
+  bool timed = false;               // the last translation recorded the events
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // far start, near start, near end (timing)
 };
 
 struct lsms_ctx {
