@@ -111,8 +111,8 @@ int apply_device(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags,
     // the translation (+ the partial-sum reduction, or the packing of the tensor-core operands)
     // and the near pairs
     if (c->fmm.ready) {
-      launches += (c->fmm.dmin > 2 ? 4 : 3) * nrhs + 1;
-      if ((rc = fmm_translate(c, nrhs, xs, alpha, st))) return rc;
+      launches += (c->fmm.dmin > 2 ? 4 : 3) * nrhs + (mixed ? 3 + (c->near_nnz > 0 ? 1 : 0) : 1);
+      if ((rc = fmm_translate(c, nrhs, xs, alpha, mixed, st))) return rc;
     } else if (mixed) {
       launches += 3 + (c->near_nnz > 0 ? 1 : 0);
       if ((rc = translate_mixed(c, nrhs, xs, alpha, st))) return rc;
@@ -390,7 +390,9 @@ extern "C" int lsms_translate(lsms_ctx* c, int nrhs, const double* beta, double*
   if ((rc = copy_in(c, c->ws_x, beta, len))) return rc;
   if ((rc = ensure(c, c->ws_alpha, len * sizeof(double2)))) return rc;
   if (c->fmm.ready) {
-    if ((rc = fmm_translate(c, nrhs, (const double2*)c->ws_x.ptr, (double2*)c->ws_alpha.ptr, c->stream))) return rc;
+    if ((rc = fmm_translate(c, nrhs, (const double2*)c->ws_x.ptr, (double2*)c->ws_alpha.ptr,
+                            precision == LSMS_MIXED, c->stream)))
+      return rc;
   } else if (precision == LSMS_MIXED) {
     if ((rc = translate_mixed(c, nrhs, (const double2*)c->ws_x.ptr, (double2*)c->ws_alpha.ptr, c->stream))) return rc;
   } else

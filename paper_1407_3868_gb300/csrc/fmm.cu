@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "c64.cuh"
+#include "ff_hankel.cuh"
 #include "lsms_internal.h"
 #include "lsms_ops.h"
 
@@ -276,6 +277,196 @@ k_fmm_near(const double* __restrict__ scx, const double* __restrict__ scy, const
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Mixed precision: the near field in FP32 (float-float phases, Hankel's asymptotic H_0, H_1 for
+// k rho >= 25, forward recurrence) with the register-blocked Toeplitz contraction of the all-pairs
+// FP32 kernel, restricted to adjacent boxes; pairs with k rho < 25 are left to the near-pair kernel
+// (FP64-accurate sequences).  Inputs and outputs in box order.
+// ---------------------------------------------------------------------------------------------
+constexpr int BW = 4;      // warps per CTA
+constexpr int BT = 8;      // target discs per warp
+constexpr int BCH = 32;    // sources staged per chunk
+constexpr int BHS = 65;    // pair slot stride (see the all-pairs FP32 kernel: conflict-free windows)
+constexpr int BGUARD = 8;
+constexpr size_t BOX_NEAR_SMEM = (size_t)(2 * BGUARD + BW * 32 * BHS) * sizeof(float2);
+
+template <int PT>
+__global__ void __launch_bounds__(BW * 32, 3)
+k_box_near_f32(const float4* __restrict__ cff, const int* __restrict__ sbox, const int* __restrict__ bstart,
+               int nb, int n, float k_hi, float k_lo, float near_hi, float near_lo,
+               const float2* __restrict__ xs, float2* __restrict__ out) {
+  constexpr int p = PT;
+  constexpr int P = 2 * PT + 1;
+  constexpr int VB = (P + 3) / 4;
+  constexpr int NB = (P + VB - 1) / VB;
+  __shared__ float2 sb[BCH][VB * NB + 1];
+  __shared__ float4 sc[BCH];
+  __shared__ int sbx[BCH];
+  extern __shared__ float2 sh[];
+  const int r = blockIdx.z;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = lane & 7, hi8 = lane >> 3;
+  const int l0 = blockIdx.x * BW * BT;
+  const int l = l0 + warp * BT + t;
+  const bool lvalid = l < n;
+  const float4 ct = lvalid ? cff[l] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const int bl = lvalid ? sbox[l] : 0;
+  const int b0 = sbox[l0], b1 = sbox[min(l0 + BW * BT, n) - 1];
+  const int jbeg = bstart[max(b0 - 1, 0)], jend = bstart[min(b1 + 2, nb)];
+  for (int i = threadIdx.x; i < 2 * BGUARD + BW * 32 * BHS; i += blockDim.x) sh[i] = make_float2(0.f, 0.f);
+  float2* hw = sh + BGUARD + warp * 32 * BHS;
+  float A[VB], B[VB], C[VB];
+#pragma unroll
+  for (int i = 0; i < VB; ++i) A[i] = B[i] = C[i] = 0.f;
+  const ffl kf = {k_hi, k_lo};
+  const float2* xr = xs + (size_t)r * n * P;
+  for (int j0c = jbeg; j0c < jend; j0c += BCH) {
+    const int cnt = min(BCH, jend - j0c);
+    __syncthreads();
+    for (int i = threadIdx.x; i < BCH * VB * NB; i += blockDim.x) {
+      const int s = i / (VB * NB), q = i - s * (VB * NB);
+      sb[s][q] = (s < cnt && q < P) ? xr[(size_t)(j0c + s) * P + q] : make_float2(0.f, 0.f);
+    }
+    if (threadIdx.x < cnt) {
+      sc[threadIdx.x] = cff[j0c + threadIdx.x];
+      sbx[threadIdx.x] = sbox[j0c + threadIdx.x];
+    }
+    __syncthreads();
+    for (int s0 = 0; s0 < cnt; s0 += 4) {
+      {
+        const int js = s0 + hi8;
+        float2* h = hw + lane * BHS;
+        const int db = js < cnt ? sbx[js] - bl : 2;
+        if (js < cnt && lvalid && j0c + js != l && db >= -1 && db <= 1) {
+          hankel_sequence_f32<PT>(ct, sc[js], kf, {near_hi, near_lo}, h);
+        } else {
+          for (int q = 0; q <= 4 * p; ++q) h[q] = make_float2(0.f, 0.f);
+        }
+      }
+      __syncwarp();
+      const int nq4 = min(4, cnt - s0);
+      for (int q4 = 0; q4 < nq4; ++q4) {
+        const float2* hs = hw + (q4 * 8 + t) * BHS + 2 * p - VB * hi8;
+        float2 win[2 * VB - 1];
+        float wsum[2 * VB - 1];
+#pragma unroll
+        for (int j = 0; j < VB - 1; ++j) {
+          win[j] = hs[j - (VB - 1)];
+          wsum[j] = win[j].x + win[j].y;
+        }
+#pragma unroll
+        for (int nbk = 0; nbk < NB; ++nbk) {
+#pragma unroll
+          for (int j = 0; j < VB; ++j) {
+            win[VB - 1 + j] = hs[nbk * VB + j];
+            wsum[VB - 1 + j] = win[VB - 1 + j].x + win[VB - 1 + j].y;
+          }
+#pragma unroll
+          for (int u = 0; u < VB; ++u) {
+            if (nbk * VB + u >= P) break;
+            const float2 bv = sb[s0 + q4][nbk * VB + u];
+            const float bsum = bv.x + bv.y;
+#pragma unroll
+            for (int i = 0; i < VB; ++i) {
+              const float2 hv = win[VB - 1 + u - i];
+              A[i] = __fmaf_rn(hv.x, bv.x, A[i]);
+              B[i] = __fmaf_rn(hv.y, bv.y, B[i]);
+              C[i] = __fmaf_rn(wsum[VB - 1 + u - i], bsum, C[i]);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < VB - 1; ++j) {
+            win[j] = win[VB + j];
+            wsum[j] = wsum[VB + j];
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  if (lvalid) {
+    float2* o = out + ((size_t)r * n + l) * P;
+#pragma unroll
+    for (int i = 0; i < VB; ++i) {
+      const int nu = VB * hi8 + i;
+      if (nu < P) o[nu] = make_float2(A[i] - B[i], C[i] - A[i] - B[i]);
+    }
+  }
+}
+
+template <int PT>
+void launch_box_near_pt(dim3 grid, cudaStream_t st, const float4* cff, const int* sbox, const int* bstart, int nb,
+                        int n, float kh, float kl, float nh, float nl, const float2* xs, float2* out) {
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_box_near_f32<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BOX_NEAR_SMEM);
+  });
+  k_box_near_f32<PT><<<grid, BW * 32, BOX_NEAR_SMEM, st>>>(cff, sbox, bstart, nb, n, kh, kl, nh, nl, xs, out);
+}
+
+void launch_box_near(int p, dim3 grid, cudaStream_t st, const float4* cff, const int* sbox, const int* bstart,
+                     int nb, int n, float kh, float kl, float nh, float nl, const float2* xs, float2* out) {
+#define LSMS_BN(PT) launch_box_near_pt<PT>(grid, st, cff, sbox, bstart, nb, n, kh, kl, nh, nl, xs, out)
+  switch (p) {
+    case 0: LSMS_BN(0); break;
+    case 1: LSMS_BN(1); break;
+    case 2: LSMS_BN(2); break;
+    case 3: LSMS_BN(3); break;
+    case 4: LSMS_BN(4); break;
+    case 5: LSMS_BN(5); break;
+    case 6: LSMS_BN(6); break;
+    case 7: LSMS_BN(7); break;
+    case 8: LSMS_BN(8); break;
+    case 9: LSMS_BN(9); break;
+    case 10: LSMS_BN(10); break;
+    case 11: LSMS_BN(11); break;
+    case 12: LSMS_BN(12); break;
+    case 13: LSMS_BN(13); break;
+    case 14: LSMS_BN(14); break;
+    default: LSMS_BN(15); break;
+  }
+#undef LSMS_BN
+}
+
+// FP32 copies of the coefficients in both orders: x32 (disc order), xs32 (box order).
+__global__ void k_fmm_to_f32(const double2* __restrict__ x, const int* __restrict__ perm, int n, int P,
+                             long long len, float2* __restrict__ x32, float2* __restrict__ xs32) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long rt = i / P;
+    const int q = (int)(i - rt * P);
+    const long long r = rt / n;
+    const int tt = (int)(rt - r * n);
+    const double2 v = x[i];
+    x32[i] = make_float2((float)v.x, (float)v.y);
+    const double2 w = x[((size_t)r * n + perm[tt]) * P + q];
+    xs32[i] = make_float2((float)w.x, (float)w.y);
+  }
+}
+
+// alpha[r][perm[t]][nu] += part[r][t][nu]
+__global__ void k_fmm_scatter_add(const float2* __restrict__ part, const int* __restrict__ perm, int n, int P,
+                                  long long len, double2* __restrict__ alpha) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long rt = i / P;
+    const int q = (int)(i - rt * P);
+    const long long r = rt / n;
+    const int tt = (int)(rt - r * n);
+    double2* o = alpha + ((size_t)r * n + perm[tt]) * P + q;
+    const float2 v = part[i];
+    *o = make_double2(o->x + v.x, o->y + v.y);
+  }
+}
+
+__global__ void k_fmm_ff_centres(const double* __restrict__ cx, const double* __restrict__ cy, int n,
+                                 float4* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const float xh = (float)cx[j], yh = (float)cy[j];
+  out[j] = make_float4(xh, (float)(cx[j] - (double)xh), yh, (float)(cy[j] - (double)yh));
+}
+
 inline int blocks_for(long long total, int block) {
   long long b = (total + block - 1) / block;
   return (int)std::min<long long>(std::max<long long>(b, 1), 152LL * 32);
@@ -286,7 +477,7 @@ inline int blocks_for(long long total, int block) {
 void fmm_free(lsms_ctx* c) {
   FmmState& f = c->fmm;
   void* ptrs[] = {f.d_perm, f.d_bstart, f.d_dbox, f.d_sbox, f.d_scx, f.d_scy, f.d_tab, f.d_khat, f.d_grid,
-                  f.d_bq, f.d_hd};
+                  f.d_bq, f.d_hd, f.d_scff, f.ws.ptr};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (f.has_plan) cufftDestroy((cufftHandle)f.plan);
@@ -355,6 +546,7 @@ int fmm_setup(lsms_ctx* c) {
       cudaMalloc((void**)&f.d_khat, gsz * sizeof(double2)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_grid, gsz * sizeof(double2)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_bq, (size_t)nb * (2 * f.order + 1) * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_scff, (size_t)n * sizeof(float4)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_hd, (size_t)std::max(1, 2 * (f.dmin - 2)) * (4 * f.order + 1) * sizeof(double2)) !=
           cudaSuccess) {
     cudaGetLastError();
@@ -375,6 +567,7 @@ int fmm_setup(lsms_ctx* c) {
   f.plan = (int)plan;
   f.has_plan = true;
   cudaStream_t st = c->stream;
+  k_fmm_ff_centres<<<(n + 255) / 256, 256, 0, st>>>(f.d_scx, f.d_scy, n, f.d_scff);
   k_fmm_shift_table<<<blocks_for((long long)tsz, 256), 256, 0, st>>>(c->d_cx, c->d_cy, f.d_dbox, n, f.x0, w,
                                                                       -0.5 * c->d, c->k2, f.S, f.d_tab);
   cudaMemsetAsync(f.d_khat, 0, gsz * sizeof(double2), st);
@@ -395,7 +588,7 @@ int fmm_setup(lsms_ctx* c) {
 
 // alpha = T xs for nrhs right-hand sides through the box method (FP64).  Launches: per right-hand
 // side M2M, the pointwise product and L2L, plus one near-field launch (cuFFT's own kernels aside).
-int fmm_translate(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st) {
+int fmm_translate(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, bool mixed, cudaStream_t st) {
   FmmState& f = c->fmm;
   const int n = c->n, p = c->p, P = 2 * p + 1;
   if (!f.ready) return ctx_fail(c, LSMS_ERR_STATE, "box translation tables are not built");
@@ -424,6 +617,27 @@ int fmm_translate(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cuda
       k_fmm_m2l_direct<<<f.nb, qthreads, 0, st>>>(f.d_bq, f.d_hd, f.nb, f.order, f.dmin, f.n2, f.d_grid);
     k_fmm_l2l<<<(int)(((long long)n * 32 + 255) / 256), 256, 0, st>>>(f.d_grid, f.d_dbox, f.d_tab, n, p, f.order,
                                                                        f.S, f.n2, a);
+  }
+  if (mixed) {
+    // near field in FP32: box-order copies, the adjacent-box kernel, scatter-add, the near pairs
+    const long long len = (long long)nrhs * n * P;
+    const size_t b = (((size_t)len * sizeof(float2)) + 255) & ~size_t(255);
+    int rc;
+    if ((rc = ensure(c, f.ws, 3 * b))) return rc;
+    float2* x32 = (float2*)f.ws.ptr;
+    float2* xs32 = (float2*)((unsigned char*)f.ws.ptr + b);
+    float2* part = (float2*)((unsigned char*)f.ws.ptr + 2 * b);
+    if (timed) cudaEventRecord(f.ev[1], st);
+    k_fmm_to_f32<<<blocks_for(len, 256), 256, 0, st>>>(xs, f.d_perm, n, P, len, x32, xs32);
+    const float kh = (float)c->k2, kl = (float)(c->k2 - (double)kh);
+    const float nh = (float)c->near_r2, nl = (float)(c->near_r2 - (double)nh);
+    dim3 grid((n + BW * BT - 1) / (BW * BT), 1, nrhs);
+    launch_box_near(p, grid, st, f.d_scff, f.d_sbox, f.d_bstart, f.nb, n, kh, kl, nh, nl, xs32, part);
+    k_fmm_scatter_add<<<blocks_for(len, 256), 256, 0, st>>>(part, f.d_perm, n, P, len, alpha);
+    launch_translate_near(c, nrhs, x32, alpha, st);
+    if (timed) cudaEventRecord(f.ev[2], st);
+    f.timed = timed;
+    return LSMS_OK;
   }
   const size_t smem = (size_t)(FCH * 32 + FW * FCH * FHS) * (sizeof(double2) + sizeof(double));
   static std::once_flag attr;

@@ -50,6 +50,8 @@ struct FmmState {
   double2* d_grid = nullptr;        // [n1][n2] work grid
   double2* d_bq = nullptr;          // [nb][2Q + 1] box coefficients (for the direct offsets)
   double2* d_hd = nullptr;          // [2 (dmin - 2)][4Q + 1] kernels of the direct offsets
+  float4* d_scff = nullptr;         // [n] sorted centres, float-float (mixed near field)
+  DevBuf ws;                        // FP32 copies and partial sums of the mixed near field
   int plan = 0;                     // cufftHandle
   bool has_plan = false;
   long long near_pairs = 0;         // ordered pairs translated directly

@@ -17,7 +17,8 @@ bool solve_small(std::vector<cplx>& a, int n, std::vector<cplx>& b, int nrhs);
 // box-compressed translation (fmm.cu)
 int fmm_setup(lsms_ctx* c);
 void fmm_free(lsms_ctx* c);
-int fmm_translate(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st);
+// mixed: the near field in FP32 (adjacent boxes) plus the FP32 near-pair kernel; else all FP64
+int fmm_translate(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, bool mixed, cudaStream_t st);
 // drop the captured batched applications (their kernels depend on the context's settings)
 void batch_clear_graphs(lsms_ctx* c);
 int check_cuda(lsms_ctx* c, const char* where);

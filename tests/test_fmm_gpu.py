@@ -83,6 +83,26 @@ def test_box_translation_matches_all_pairs(L, n, width, nrhs):
     assert rel(a[0][rows], a_o, ws) < TOL64
 
 
+@pytest.mark.parametrize("n,p", [(1000, 12), (300, 6)])
+def test_mixed_box_translation_matches_all_pairs(L, n, p):
+    # mixed precision: the adjacent-box pairs in FP32 (pairs with k rho < 25 through the FP64-accurate
+    # near-pair tables), the far field through the FP64 boxes; the mixed-operator tolerance 2e-5
+    w = workload(n, p, 56)
+    c = w.centres()
+    hs, ws = weights(w)
+    beta = inputs.random_coefficients(w.n, w.p, 2, 7) / hs[None, None, :]
+    with L.context_for(w, L.LSMS_MIXED) as ctx:
+        ctx.set_particles(c)
+        ctx.set_fmm(4.0)
+        a = ctx.translate(beta, precision=L.LSMS_MIXED)
+        a64 = ctx.translate(beta, precision=L.LSMS_FP64)
+    rows = [0, 3, n // 2, n - 1]
+    for r in range(2):
+        a_o = O.translate(c, beta[r], w.medium["k2"], w.p, rows=rows)
+        assert rel(a[r][rows], a_o, ws) < 2e-5, r
+        assert rel(a[r], a64[r], ws) < 2e-5, r
+
+
 @pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOL_MIXED)])
 def test_operator_and_solve_with_boxes(L, precision, tol):
     w = workload(600, 10, 53)
