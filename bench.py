@@ -626,28 +626,36 @@ def run_large(args, dev, flush):
         ctx.apply_dev(x, y, fl_m)
     torch.cuda.synchronize()
     ms = time_device(lambda: ctx.apply_dev(x, y, fl_m), max(3, min(args.steps, 10)), flush)
-    ctx.set_timing(True)
-    tr, near, far = [], [], []
-    for _ in range(3):
-        flush.fill_(1.0)
-        ctx.apply_dev(x, y, fl_m)
-        tr.append(ctx.last_timing()[0])
-        pairs, f_ms, n_ms = ctx.fmm_stats()
-        far.append(f_ms)
-        near.append(n_ms)
-    ctx.set_timing(False)
-    out["boxes_mixed"] = {"ms_per_apply": ms, "translate_ms": statistics.mean(tr),
-                          "far_ms": statistics.mean(far), "near_ms": statistics.mean(near),
-                          "translation": "FP64 through boxes"}
-    # the near field (pairs in adjacent boxes, FP64 CUDA cores) against the FP64 peak
+    def staged(flags):
+        ctx.set_timing(True)
+        tr, near, far = [], [], []
+        for _ in range(3):
+            flush.fill_(1.0)
+            ctx.apply_dev(x, y, flags)
+            tr.append(ctx.last_timing()[0])
+            pairs, f_ms, n_ms = ctx.fmm_stats()
+            far.append(f_ms)
+            near.append(n_ms)
+        ctx.set_timing(False)
+        return pairs, statistics.mean(tr), statistics.mean(far), statistics.mean(near)
+
+    pairs, tr_ms, far_ms, near_ms = staged(fl_m)
+    out["boxes_mixed"] = {"ms_per_apply": ms, "translate_ms": tr_ms, "far_ms": far_ms, "near_ms": near_ms,
+                          "translation": "through boxes: far field FP32 (shifts, FFT convolution), near field FP32"}
+    # the near field (ordered pairs in adjacent boxes, 8 P^2 flop each) against the peak of its precision
     P = 2 * p + 1
     flop = 8.0 * P * P * pairs
-    near_ms = statistics.mean(near)
-    out["roofline_near"] = {"kernel": "k_fmm_near", "bound": "alu", "pairs": pairs, "flop_per_launch": flop,
-                            "launch_ms": near_ms, "achieved": flop / (near_ms / 1e3) / 1e12,
-                            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": flop / (near_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
-                            "peak_note": "derived FP64: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz"}
+
+    def roof(kernel, ms_, peak, note):
+        ach = flop / (ms_ / 1e3) / 1e12
+        return {"kernel": kernel, "bound": "alu", "pairs": pairs, "flop_per_launch": flop, "launch_ms": ms_,
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "peak_note": note}
+    out["roofline_near_mixed"] = roof("k_box_near_f32 (+ FP32 copies, near pairs, scatter-add)", near_ms,
+                                      FP32_PEAK_TFLOPS, "derived FP32: 152 SMs x 128 lanes x 2 x 2070 MHz")
+    pairs, tr64, far64, near64 = staged(lsms.APPLY_SCALED)
+    out["boxes_fp64_stages"] = {"translate_ms": tr64, "far_ms": far64, "near_ms": near64}
+    out["roofline_near_fp64"] = roof("k_fmm_near", near64, FP64_PEAK_TFLOPS,
+                                     "derived FP64: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz")
     ms64 = time_device(lambda: ctx.apply_dev(x, y, lsms.APPLY_SCALED), 3, flush)
     out["boxes_fp64"] = {"ms_per_apply": ms64}
     out["speedup_boxes_vs_all_pairs_mixed"] = out["all_pairs_mixed"]["ms_per_apply"] / ms

@@ -35,6 +35,22 @@ constexpr int FW = 4;     // target discs (warps) per CTA of the near-field kern
 constexpr int FCH = 32;   // source discs per staged chunk
 constexpr int FHS = 65;   // pair sequence stride (4p + 1 <= 61)
 
+// FP32 complex helpers (the FP64 ones come from c64.cuh) and loads of either precision
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+  c.x = fmaf(a.x, b.x, c.x);
+  c.x = fmaf(-a.y, b.y, c.x);
+  c.y = fmaf(a.x, b.y, c.y);
+  c.y = fmaf(a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C cconj(C a) { C r = a; r.y = -r.y; return r; }
+template <typename C> __device__ __forceinline__ C czero() { C r; r.x = 0; r.y = 0; return r; }
+template <typename C> __device__ __forceinline__ C from_d2(double2 v) { C r; r.x = v.x; r.y = v.y; return r; }
+
 // smallest n >= m whose prime factors are 2, 3, 5, 7 (sizes cuFFT handles fastest)
 int fft_size(int m) {
   for (int n = std::max(m, 1);; ++n) {
@@ -103,31 +119,32 @@ __global__ void k_fmm_scale(double2* __restrict__ a, long long total, double s) 
     a[i] = make_double2(a[i].x * s, a[i].y * s);
 }
 
-__global__ void k_fmm_mul(double2* __restrict__ a, const double2* __restrict__ b, long long total) {
+template <typename C>
+__global__ void k_fmm_mul(C* __restrict__ a, const C* __restrict__ b, long long total) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x)
     a[i] = cmul(a[i], b[i]);
 }
 
-// M2M: one CTA per box, thread t <-> box order q = t - Q; writes grid[i][(-q) mod n2].
+// M2M: one CTA per box, thread t <-> box order q = t - Q; writes grid[i][(-q) mod n2].  C is the
+// complex type of the tables and the grid (double2, or float2 in mixed precision).
+template <typename C>
 __global__ void k_fmm_m2m(const double2* __restrict__ xs, const int* __restrict__ perm,
-                          const int* __restrict__ bstart, const double2* __restrict__ tab, int p,
-                          int Q, int S, int n2, double2* __restrict__ grid, double2* __restrict__ bq) {
-  extern __shared__ double2 sbeta[];                 // [P] coefficients of the current disc
+                          const int* __restrict__ bstart, const C* __restrict__ tab, int p,
+                          int Q, int S, int n2, C* __restrict__ grid, C* __restrict__ bq) {
+  extern __shared__ unsigned char sraw[];
+  C* sbeta = reinterpret_cast<C*>(sraw);             // [P] coefficients of the current disc
   const int i = blockIdx.x, P = 2 * p + 1;
   const int q = (int)threadIdx.x - Q;
-  double2 acc = make_double2(0.0, 0.0);
+  C acc = czero<C>();
   for (int jj = bstart[i]; jj < bstart[i + 1]; ++jj) {
     const int m = perm[jj];
     __syncthreads();
-    if (threadIdx.x < P) sbeta[threadIdx.x] = xs[(size_t)m * P + threadIdx.x];
+    if (threadIdx.x < P) sbeta[threadIdx.x] = from_d2<C>(xs[(size_t)m * P + threadIdx.x]);
     __syncthreads();
     if (q >= -Q && q <= Q) {
-      const double2* t = tab + (size_t)m * (2 * S + 1) + S + q + p;    // t[-(n + p)] <-> s = q - n
-      for (int a = 0; a < P; ++a) {
-        const double2 tv = t[-a];                    // J_{q-n} e^{i (q-n) phi}, n = a - p
-        acc = cfma(make_double2(tv.x, -tv.y), sbeta[a], acc);
-      }
+      const C* t = tab + (size_t)m * (2 * S + 1) + S + q + p;           // t[-(n + p)] <-> s = q - n
+      for (int a = 0; a < P; ++a) acc = cfma(cconj(t[-a]), sbeta[a], acc);   // J_{q-n} e^{-i (q-n) phi}
     }
   }
   if (q >= -Q && q <= Q) {
@@ -138,23 +155,24 @@ __global__ void k_fmm_m2m(const double2* __restrict__ xs, const int* __restrict_
 
 // M2L for the offsets 2 <= |d| < dmin, box by box: grid[i][(-nu) mod n2] += sum_d sum_q
 // hd[d][q - nu] B_{i-d}(q), hd[(sign, |d| - 2)][s + 2Q] = H_s(k |d| w) e^{i s phi_d}.
-__global__ void k_fmm_m2l_direct(const double2* __restrict__ bq, const double2* __restrict__ hd, int nb,
-                                 int Q, int dmin, int n2, double2* __restrict__ grid) {
+template <typename C>
+__global__ void k_fmm_m2l_direct(const C* __restrict__ bq, const C* __restrict__ hd, int nb,
+                                 int Q, int dmin, int n2, C* __restrict__ grid) {
   const int i = blockIdx.x;
   const int nu = (int)threadIdx.x - Q;
   if (nu < -Q || nu > Q) return;
   const int W = 2 * Q + 1, H = 4 * Q + 1;
-  double2 acc = make_double2(0.0, 0.0);
+  C acc = czero<C>();
   for (int ad = 2; ad < dmin; ++ad)
     for (int sg = 0; sg < 2; ++sg) {
       const int d = sg ? -ad : ad;
       const int j = i - d;
       if (j < 0 || j >= nb) continue;
-      const double2* h = hd + (size_t)(2 * (ad - 2) + sg) * H + 2 * Q - nu;   // h[q] <-> s = q - nu
-      const double2* b = bq + (size_t)j * W + Q;
+      const C* h = hd + (size_t)(2 * (ad - 2) + sg) * H + 2 * Q - nu;   // h[q] <-> s = q - nu
+      const C* b = bq + (size_t)j * W + Q;
       for (int q = -Q; q <= Q; ++q) acc = cfma(h[q], b[q], acc);
     }
-  double2* g = grid + (size_t)i * n2 + ((-nu) % n2 + n2) % n2;
+  C* g = grid + (size_t)i * n2 + ((-nu) % n2 + n2) % n2;
   *g = cadd(*g, acc);
 }
 
@@ -183,19 +201,20 @@ __global__ void k_fmm_direct_table(int Q, double k, double w, int dmin, double2*
 }
 
 // L2L: one warp per disc, lane <-> nu; alpha = sum_q T_l[q - nu] A_box(q), A(q) = grid[b][(-q) mod n2].
-__global__ void k_fmm_l2l(const double2* __restrict__ grid, const int* __restrict__ dbox,
-                          const double2* __restrict__ tab, int n, int p, int Q, int S, int n2,
+template <typename C>
+__global__ void k_fmm_l2l(const C* __restrict__ grid, const int* __restrict__ dbox,
+                          const C* __restrict__ tab, int n, int p, int Q, int S, int n2,
                           double2* __restrict__ alpha) {
   const int l = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   const int P = 2 * p + 1;
   if (l >= n || lane >= P) return;
   const int nu = lane - p;
-  const double2* g = grid + (size_t)dbox[l] * n2;
-  const double2* t = tab + (size_t)l * (2 * S + 1) + S;
-  double2 acc = make_double2(0.0, 0.0);
+  const C* g = grid + (size_t)dbox[l] * n2;
+  const C* t = tab + (size_t)l * (2 * S + 1) + S;
+  C acc = czero<C>();
   for (int q = -Q; q <= Q; ++q) acc = cfma(t[q - nu], g[((-q) % n2 + n2) % n2], acc);
-  alpha[(size_t)l * P + lane] = acc;
+  alpha[(size_t)l * P + lane] = make_double2(acc.x, acc.y);
 }
 
 // Near field: CTA over FW consecutive targets in box order; sources from the neighbouring boxes,
@@ -459,6 +478,12 @@ __global__ void k_fmm_scatter_add(const float2* __restrict__ part, const int* __
   }
 }
 
+__global__ void k_fmm_d2f(const double2* __restrict__ a, float2* __restrict__ b, long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
 __global__ void k_fmm_ff_centres(const double* __restrict__ cx, const double* __restrict__ cy, int n,
                                  float4* __restrict__ out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -477,10 +502,11 @@ inline int blocks_for(long long total, int block) {
 void fmm_free(lsms_ctx* c) {
   FmmState& f = c->fmm;
   void* ptrs[] = {f.d_perm, f.d_bstart, f.d_dbox, f.d_sbox, f.d_scx, f.d_scy, f.d_tab, f.d_khat, f.d_grid,
-                  f.d_bq, f.d_hd, f.d_scff, f.ws.ptr};
+                  f.d_bq, f.d_hd, f.d_scff, f.ws.ptr, f.d_tab32, f.d_khat32, f.d_grid32, f.d_bq32, f.d_hd32};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (f.has_plan) cufftDestroy((cufftHandle)f.plan);
+  if (f.has_plan32) cufftDestroy((cufftHandle)f.plan32);
   for (cudaEvent_t e : f.ev)
     if (e) cudaEventDestroy(e);
   const double w = f.box_width;
@@ -581,6 +607,27 @@ int fmm_setup(lsms_ctx* c) {
     return ctx_fail(c, LSMS_ERR_CUDA, "set_fmm: cuFFT failed");
   }
   k_fmm_scale<<<blocks_for((long long)gsz, 256), 256, 0, st>>>(f.d_khat, (long long)gsz, 1.0 / (double)gsz);
+  // FP32 copies for the mixed-precision far field
+  const size_t hsz = (size_t)std::max(1, 2 * (f.dmin - 2)) * (4 * f.order + 1);
+  if (cudaMalloc((void**)&f.d_tab32, tsz * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_khat32, gsz * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_grid32, gsz * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_bq32, (size_t)nb * (2 * f.order + 1) * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_hd32, hsz * sizeof(float2)) != cudaSuccess) {
+    cudaGetLastError();
+    fmm_free(c);
+    return ctx_fail(c, LSMS_ERR_OOM, "set_fmm: cudaMalloc failed for the FP32 box tables");
+  }
+  k_fmm_d2f<<<blocks_for((long long)tsz, 256), 256, 0, st>>>(f.d_tab, f.d_tab32, (long long)tsz);
+  k_fmm_d2f<<<blocks_for((long long)gsz, 256), 256, 0, st>>>(f.d_khat, f.d_khat32, (long long)gsz);
+  if (f.dmin > 2) k_fmm_d2f<<<blocks_for((long long)hsz, 256), 256, 0, st>>>(f.d_hd, f.d_hd32, (long long)hsz);
+  cufftHandle plan32;
+  if (cufftPlan2d(&plan32, f.n1, f.n2, CUFFT_C2C) != CUFFT_SUCCESS) {
+    fmm_free(c);
+    return ctx_fail(c, LSMS_ERR_CUDA, "set_fmm: cuFFT plan creation failed");
+  }
+  f.plan32 = (int)plan32;
+  f.has_plan32 = true;
   cudaStreamSynchronize(st);
   f.ready = true;
   return check_cuda(c, "set_fmm");
@@ -599,24 +646,42 @@ int fmm_translate(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, bool
   if (timed && !f.ev[0])
     for (cudaEvent_t& e : f.ev) cudaEventCreate(&e);
   if (timed) cudaEventRecord(f.ev[0], st);
+  const int qthreads = ((2 * f.order + 1 + 31) / 32) * 32;
   for (int r = 0; r < nrhs; ++r) {
     const double2* x = xs + (size_t)r * n * P;
     double2* a = alpha + (size_t)r * n * P;
+    if (mixed) {
+      cufftHandle p32 = (cufftHandle)f.plan32;
+      cufftSetStream(p32, st);
+      cudaMemsetAsync(f.d_grid32, 0, gsz * sizeof(float2), st);
+      k_fmm_m2m<float2><<<f.nb, qthreads, P * sizeof(float2), st>>>(x, f.d_perm, f.d_bstart, f.d_tab32, p, f.order,
+                                                                    f.S, f.n2, f.d_grid32, f.d_bq32);
+      if (cufftExecC2C(p32, (cufftComplex*)f.d_grid32, (cufftComplex*)f.d_grid32, CUFFT_FORWARD) != CUFFT_SUCCESS)
+        return ctx_fail(c, LSMS_ERR_CUDA, "box translation: cuFFT failed");
+      k_fmm_mul<float2><<<blocks_for((long long)gsz, 256), 256, 0, st>>>(f.d_grid32, f.d_khat32, (long long)gsz);
+      if (cufftExecC2C(p32, (cufftComplex*)f.d_grid32, (cufftComplex*)f.d_grid32, CUFFT_INVERSE) != CUFFT_SUCCESS)
+        return ctx_fail(c, LSMS_ERR_CUDA, "box translation: cuFFT failed");
+      if (f.dmin > 2)
+        k_fmm_m2l_direct<float2><<<f.nb, qthreads, 0, st>>>(f.d_bq32, f.d_hd32, f.nb, f.order, f.dmin, f.n2,
+                                                            f.d_grid32);
+      k_fmm_l2l<float2><<<(int)(((long long)n * 32 + 255) / 256), 256, 0, st>>>(f.d_grid32, f.d_dbox, f.d_tab32, n, p,
+                                                                                f.order, f.S, f.n2, a);
+      continue;
+    }
     cudaMemsetAsync(f.d_grid, 0, gsz * sizeof(double2), st);
-    const int qthreads = ((2 * f.order + 1 + 31) / 32) * 32;
-    k_fmm_m2m<<<f.nb, qthreads, P * sizeof(double2), st>>>(x, f.d_perm, f.d_bstart, f.d_tab, p, f.order, f.S,
-                                                           f.n2, f.d_grid, f.d_bq);
+    k_fmm_m2m<double2><<<f.nb, qthreads, P * sizeof(double2), st>>>(x, f.d_perm, f.d_bstart, f.d_tab, p, f.order,
+                                                                     f.S, f.n2, f.d_grid, f.d_bq);
     if (cufftExecZ2Z(plan, (cufftDoubleComplex*)f.d_grid, (cufftDoubleComplex*)f.d_grid, CUFFT_FORWARD) !=
         CUFFT_SUCCESS)
       return ctx_fail(c, LSMS_ERR_CUDA, "box translation: cuFFT failed");
-    k_fmm_mul<<<blocks_for((long long)gsz, 256), 256, 0, st>>>(f.d_grid, f.d_khat, (long long)gsz);
+    k_fmm_mul<double2><<<blocks_for((long long)gsz, 256), 256, 0, st>>>(f.d_grid, f.d_khat, (long long)gsz);
     if (cufftExecZ2Z(plan, (cufftDoubleComplex*)f.d_grid, (cufftDoubleComplex*)f.d_grid, CUFFT_INVERSE) !=
         CUFFT_SUCCESS)
       return ctx_fail(c, LSMS_ERR_CUDA, "box translation: cuFFT failed");
     if (f.dmin > 2)
-      k_fmm_m2l_direct<<<f.nb, qthreads, 0, st>>>(f.d_bq, f.d_hd, f.nb, f.order, f.dmin, f.n2, f.d_grid);
-    k_fmm_l2l<<<(int)(((long long)n * 32 + 255) / 256), 256, 0, st>>>(f.d_grid, f.d_dbox, f.d_tab, n, p, f.order,
-                                                                       f.S, f.n2, a);
+      k_fmm_m2l_direct<double2><<<f.nb, qthreads, 0, st>>>(f.d_bq, f.d_hd, f.nb, f.order, f.dmin, f.n2, f.d_grid);
+    k_fmm_l2l<double2><<<(int)(((long long)n * 32 + 255) / 256), 256, 0, st>>>(f.d_grid, f.d_dbox, f.d_tab, n, p,
+                                                                                f.order, f.S, f.n2, a);
   }
   if (mixed) {
     // near field in FP32: box-order copies, the adjacent-box kernel, scatter-add, the near pairs

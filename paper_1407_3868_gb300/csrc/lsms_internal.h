@@ -51,6 +51,13 @@ struct FmmState {
   double2* d_bq = nullptr;          // [nb][2Q + 1] box coefficients (for the direct offsets)
   double2* d_hd = nullptr;          // [2 (dmin - 2)][4Q + 1] kernels of the direct offsets
   float4* d_scff = nullptr;         // [n] sorted centres, float-float (mixed near field)
+  float2* d_tab32 = nullptr;        // FP32 copies of the shift tables, the transformed kernel, the
+  float2* d_khat32 = nullptr;       // work grid, the box coefficients and the direct-offset kernels
+  float2* d_grid32 = nullptr;       // (mixed-precision far field)
+  float2* d_bq32 = nullptr;
+  float2* d_hd32 = nullptr;
+  int plan32 = 0;                   // cufftHandle (C2C)
+  bool has_plan32 = false;
   DevBuf ws;                        // FP32 copies and partial sums of the mixed near field
   int plan = 0;                     // cufftHandle
   bool has_plan = false;
