@@ -164,3 +164,32 @@ def test_box_settings_are_validated(L):
             assert e.value.code == -1, (bw, q)
         ctx.set_fmm(0.0)
         assert ctx.fmm_info() == (0, 0)
+
+
+@pytest.mark.parametrize("case", ["gap", "one_box", "two_boxes", "single"])
+def test_box_translation_edge_layouts(L, case):
+    # empty boxes in the middle of a layout, a layout inside one or two boxes (no far field at all),
+    # a single disc: both precisions against the all-pairs translation
+    p = 8
+    if case == "gap":
+        c = np.concatenate([inputs.layout(40, -60.0, -40.0, 71), inputs.layout(40, 40.0, 60.0, 72)])
+    elif case == "one_box":
+        c = inputs.layout(6, -1.5, 1.5, 73)
+    elif case == "two_boxes":
+        c = inputs.layout(10, -3.5, 3.5, 74)
+    else:
+        c = inputs.layout(1, -1.0, 1.0, 75)
+    w = workload(len(c), p, 57)
+    hs, ws = weights(w)
+    beta = inputs.random_coefficients(len(c), p, 1, 8) / hs[None, None, :]
+    with L.context_for(w, L.LSMS_MIXED) as ctx:
+        ctx.set_particles(c)
+        dense = ctx.translate(beta, precision=L.LSMS_FP64)
+        ctx.set_fmm(4.0)
+        a64 = ctx.translate(beta, precision=L.LSMS_FP64)
+        a32 = ctx.translate(beta, precision=L.LSMS_MIXED)
+    if case == "single":
+        assert np.all(a64 == 0) and np.all(a32 == 0)
+        return
+    assert rel(a64, dense, ws) < TOL64
+    assert rel(a32, dense, ws) < 2e-5
