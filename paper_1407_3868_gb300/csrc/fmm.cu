@@ -558,7 +558,8 @@ int fmm_setup(lsms_ctx* c) {
   // offsets below dmin go box by box (k |d| w < 2Q + 2)
   f.dmin = 2;
   while (c->k2 * f.dmin * w < 2.0 * f.order + 2.0) ++f.dmin;
-  f.n1 = fft_size(2 * nb - 1);
+  f.far = nb >= 3;                 // boxes two apart exist only from three boxes on
+  f.n1 = f.far ? fft_size(2 * nb - 1) : 1;
   f.n2 = fft_size(6 * f.order + 1);
   const size_t gsz = (size_t)f.n1 * f.n2;
   const size_t tsz = (size_t)n * (2 * f.S + 1);
@@ -585,6 +586,13 @@ int fmm_setup(lsms_ctx* c) {
   cudaMemcpy(f.d_sbox, sbox.data(), n * sizeof(int), cudaMemcpyHostToDevice);
   cudaMemcpy(f.d_scx, scx.data(), n * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(f.d_scy, scy.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+  cudaStream_t st = c->stream;
+  k_fmm_ff_centres<<<(n + 255) / 256, 256, 0, st>>>(f.d_scx, f.d_scy, n, f.d_scff);
+  if (!f.far) {                    // near field only
+    cudaStreamSynchronize(st);
+    f.ready = true;
+    return check_cuda(c, "set_fmm");
+  }
   cufftHandle plan;
   if (cufftPlan2d(&plan, f.n1, f.n2, CUFFT_Z2Z) != CUFFT_SUCCESS) {
     fmm_free(c);
@@ -592,8 +600,6 @@ int fmm_setup(lsms_ctx* c) {
   }
   f.plan = (int)plan;
   f.has_plan = true;
-  cudaStream_t st = c->stream;
-  k_fmm_ff_centres<<<(n + 255) / 256, 256, 0, st>>>(f.d_scx, f.d_scy, n, f.d_scff);
   k_fmm_shift_table<<<blocks_for((long long)tsz, 256), 256, 0, st>>>(c->d_cx, c->d_cy, f.d_dbox, n, f.x0, w,
                                                                       -0.5 * c->d, c->k2, f.S, f.d_tab);
   cudaMemsetAsync(f.d_khat, 0, gsz * sizeof(double2), st);
@@ -647,7 +653,8 @@ int fmm_translate(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, bool
     for (cudaEvent_t& e : f.ev) cudaEventCreate(&e);
   if (timed) cudaEventRecord(f.ev[0], st);
   const int qthreads = ((2 * f.order + 1 + 31) / 32) * 32;
-  for (int r = 0; r < nrhs; ++r) {
+  if (!f.far) cudaMemsetAsync(alpha, 0, (size_t)nrhs * n * P * sizeof(double2), st);
+  for (int r = 0; r < nrhs && f.far; ++r) {
     const double2* x = xs + (size_t)r * n * P;
     double2* a = alpha + (size_t)r * n * P;
     if (mixed) {

@@ -37,6 +37,7 @@ struct FmmState {
   double box_width = 0.0;           // > 0: translation through boxes of this width
   int order_req = 0;                // requested box order (0: k2 r_box + 32)
   bool ready = false;
+  bool far = false;                 // at least three boxes: a far field exists
   int order = 0, S = 0, nb = 0, n1 = 0, n2 = 0, dmin = 2;   // dmin: smallest offset in the FFT
   double x0 = 0.0;
   int* d_perm = nullptr;            // [n] discs sorted by box
