@@ -303,6 +303,12 @@ int lsms_get_scattering_matrix(const lsms_ctx* ctx, double* s);
 int lsms_inclusion_scattering_matrix(int p, double k2, double kp, double radius, int n_pts,
                                      const double* curve, double* s_out);
 
+/* lsms_pec_scattering_diagonal — host only.  S_n = -J_n(k2 R) / H_n(k2 R), n = -p..p, of a perfectly
+ *   conducting disc (Sec. 3.1, remark after Definition 3.1: the total field vanishes on the
+ *   boundary); pass diag(S) to lsms_set_scattering_matrix.  s_diag: 2p + 1 complex.
+ *   Errors: LSMS_ERR_ARG. */
+int lsms_pec_scattering_diagonal(int p, double k2, double radius, double* s_diag);
+
 /* lsms_set_fmm — translate through boxes for long layouts of many discs (the FMM acceleration named
  *   in Sec. 3.2; the multipole shifts of Sec. 5.3).  Discs are grouped into boxes of width
  *   box_width along x (centres at the disc layer's mid-height); pairs in the same or adjacent boxes

@@ -222,6 +222,13 @@ def mie_coefficients(p: int, k2: float, kp: float, radius: float) -> np.ndarray:
     return out
 
 
+def pec_coefficients(p: int, k2: float, radius: float) -> np.ndarray:
+    """Scattering diagonal of a perfectly conducting disc (Sec. 3.1, remark after Definition 3.1):
+    the total field vanishes on the boundary, J_n(k2 R) alpha_n + H_n(k2 R) beta_n = 0."""
+    n = np.arange(-p, p + 1)
+    return -bessel(n, k2 * radius) / hankel(n, k2 * radius)
+
+
 def order_scale(p: int, k2: float, radius: float) -> np.ndarray:
     """|H_n(k2 R)|, n = -p..p: the diagonal that makes every order O(1) on the disc boundary."""
     n = np.arange(-p, p + 1)

@@ -191,6 +191,24 @@ extern "C" int lsms_inclusion_scattering_matrix(int p, double k2, double kp, dou
   return LSMS_OK;
 }
 
+// Perfectly conducting disc (Sec. 3.1, remark after Definition 3.1): the total field vanishes on
+// the boundary, so S_n = -J_n(k2 R) / H_n(k2 R).
+extern "C" int lsms_pec_scattering_diagonal(int p, double k2, double radius, double* s_diag) {
+  if (p < 0 || p > LSMS_MAX_P || !std::isfinite(k2) || !(k2 > 0.0) || !std::isfinite(radius) || !(radius > 0.0) ||
+      !s_diag)
+    return ctx_fail(nullptr, LSMS_ERR_ARG, "pec_scattering_diagonal: need 0 <= p <= 15, k2 > 0, radius > 0");
+  const double z = k2 * radius;
+  for (int n = -p; n <= p; ++n) {
+    const int an = std::abs(n);
+    const double sg = (n < 0 && (an & 1)) ? -1.0 : 1.0;          // Z_{-n} = (-1)^n Z_n
+    const double j = sg * std::cyl_bessel_j((double)an, z), y = sg * std::cyl_neumann((double)an, z);
+    const cplx s = -j / cplx(j, y);
+    s_diag[2 * (n + p)] = s.real();
+    s_diag[2 * (n + p) + 1] = s.imag();
+  }
+  return LSMS_OK;
+}
+
 // ---------------------------------------------------------------------------------------------
 // The context's scattering matrices
 // ---------------------------------------------------------------------------------------------

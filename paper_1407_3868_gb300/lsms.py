@@ -19,7 +19,7 @@ APPLY_SCALED, APPLY_MIXED, APPLY_NO_TRANSLATION, APPLY_NO_REFLECTION, APPLY_ALPH
 FIELD_TOTAL, FIELD_SCATTERED, FIELD_PARTICLE = 0, 1, 2
 STATUS = {0: "OK", -1: "ARG", -2: "GEOMETRY", -3: "NOT_CONVERGED", -4: "NONFINITE", -5: "OOM",
           -6: "CUDA", -7: "STATE"}
-EXPORTS = ["lsms_create", "lsms_set_fmm", "lsms_get_fmm", "lsms_fmm_stats", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
+EXPORTS = ["lsms_create", "lsms_pec_scattering_diagonal", "lsms_set_fmm", "lsms_get_fmm", "lsms_fmm_stats", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
            "lsms_get_scattering_matrix", "lsms_inclusion_scattering_matrix", "lsms_set_particles", "lsms_apply", "lsms_apply_ex", "lsms_apply_dev",
            "lsms_translate", "lsms_aggregate", "lsms_reflect", "lsms_disaggregate", "lsms_incident",
            "lsms_get_contour", "lsms_get_scattering", "lsms_num_nodes", "lsms_num_particles",
@@ -72,6 +72,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsms_set_orientations": (i, [_P, i, _D]),
         "lsms_get_scattering_matrix": (i, [_P, _D]),
         "lsms_inclusion_scattering_matrix": (i, [i, d, d, d, i, _D, _D]),
+        "lsms_pec_scattering_diagonal": (i, [i, d, d, _D]),
         "lsms_apply": (i, [_P, i, _D, _D]),
         "lsms_apply_ex": (i, [_P, i, _D, _D, i]),
         "lsms_apply_dev": (i, [_P, i, _P, _P, i, _P]),
@@ -401,6 +402,16 @@ def inclusion_scattering_matrix(p, k2, kp, radius, curve) -> np.ndarray:
     s = np.zeros((2 * p + 1, 2 * p + 1), dtype=np.complex128)
     rc = lib.lsms_inclusion_scattering_matrix(int(p), float(k2), float(kp), float(radius), c.shape[0],
                                               _dptr(c), _dptr(s))
+    if rc != 0:
+        raise LsmsError(rc, lib.lsms_last_error(None).decode())
+    return s
+
+
+def pec_scattering_diagonal(p, k2, radius) -> np.ndarray:
+    """lsms_pec_scattering_diagonal: S_n of a perfectly conducting disc, n = -p..p."""
+    lib = load()
+    s = np.zeros(2 * p + 1, dtype=np.complex128)
+    rc = lib.lsms_pec_scattering_diagonal(int(p), float(k2), float(radius), _dptr(s))
     if rc != 0:
         raise LsmsError(rc, lib.lsms_last_error(None).decode())
     return s

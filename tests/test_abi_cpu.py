@@ -190,3 +190,13 @@ def test_lossy_stack_arguments_are_validated_before_any_device_work(lib):
         with pytest.raises(lib.LsmsError) as e:
             lib.Context(0, 0, 0, 0, kp, R, 6, 128, stack=(np.array(ks), [2.0], 2))
         assert e.value.code == -1, ks
+
+
+def test_library_pec_diagonal_equals_oracle(lib):
+    from oracle import lsms_oracle as O
+    for p, k2, R in ((10, inputs.MEDIUM["k2"], 0.25), (15, 2.0, 0.17)):
+        s = lib.pec_scattering_diagonal(p, k2, R)
+        s_o = O.pec_coefficients(p, k2, R)
+        assert np.abs(s - s_o).max() < 1e-13 * np.abs(s_o).max()
+    with pytest.raises(lib.LsmsError):
+        lib.pec_scattering_diagonal(16, 2.0, 0.2)

@@ -149,3 +149,22 @@ def test_batch_of_layouts_with_rotated_inclusions(L):
             pr = O.Problem(medium_of(base), base.p, c, lam, wt, smat=S, theta=th[off:off + len(c)])
             assert rel(y[off:off + len(c)], pr.apply(x[off:off + len(c)]), hs) < TOL64, l
             off += len(c)
+
+
+def test_perfectly_conducting_discs(L, small):
+    # PEC discs (Sec. 3.1 remark): the library's diagonal through lsms_set_scattering_matrix, solved
+    # and compared with the oracle's problem with the same diagonal
+    w = small.w
+    m = w.medium
+    s_pec = L.pec_scattering_diagonal(w.p, m["k2"], m["radius"])
+    pr = O.Problem(medium_of(w), w.p, small.c, small.lam, small.wt, smat=np.diag(O.pec_coefficients(w.p, m["k2"],
+                                                                                                    m["radius"])))
+    with L.context_for(w) as ctx:
+        ctx.set_particles(small.c)
+        ctx.set_scattering_matrix(np.diag(s_pec))
+        beta, info = ctx.solve(w.sources, tol=1e-12, maxiter=400)
+        assert info["status"] == 0
+        b_o = pr.solve_dense(w.sources[0])
+        assert rel(beta[0], b_o, small.hs[None, :]) < TOL64
+        u = ctx.eval_field(w.targets, 0, L.FIELD_SCATTERED)
+        assert rel(u, pr.field_layer1(w.sources[0], b_o, w.targets, "scattered")) < TOL64

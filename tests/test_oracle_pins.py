@@ -655,3 +655,24 @@ def test_box_translation_converges_to_the_dense_translation():
     e50 = err(O.box_translate(c, beta, k2, p, 8.0, 50, -MED["d"] / 2))
     e70 = err(O.box_translate(c, beta, k2, p, 8.0, 70, -MED["d"] / 2))
     assert e70 < 1e-12 < 1e-6 < e50
+
+
+def test_pec_disc_total_field_vanishes_on_the_boundary():
+    # incoming J_n e^{i n theta} plus the scattered S_n H_n e^{i n theta} is zero at r = R for every n,
+    # checked by summing a random incoming expansion on points of the circle; the dielectric disc
+    # does not satisfy it
+    k2, R, p = MED["k2"], MED["radius"], 10
+    S = O.pec_coefficients(p, k2, R)
+    rng = np.random.default_rng(3)
+    alpha = rng.normal(size=2 * p + 1) + 1j * rng.normal(size=2 * p + 1)
+    th = np.linspace(0.0, 2 * np.pi, 37)
+    n = np.arange(-p, p + 1)
+    e = np.exp(1j * np.outer(th, n))
+    u = e @ (alpha * (O.bessel(n, k2 * R) + S * O.hankel(n, k2 * R)))
+    ref = np.abs(e @ (alpha * O.bessel(n, k2 * R))).max()
+    assert np.abs(u).max() < 1e-13 * ref
+    # a lossless scatterer: |1 + 2 S_n| = 1
+    assert np.allclose(np.abs(1 + 2 * S), 1.0, rtol=0, atol=1e-13)
+    Sd = O.mie_coefficients(p, k2, MED["kp"], R)
+    u_d = e @ (alpha * (O.bessel(n, k2 * R) + Sd * O.hankel(n, k2 * R)))
+    assert np.abs(u_d).max() > 1e-2 * ref
