@@ -289,6 +289,7 @@ def run_ours(args, rank, world, local_rank):
     traffic = TRAFFIC.get(key)
 
     solve = None
+    u_ref_fp64 = None
     if not args.no_solve:
         # the mixed solve refines to 1e-8 (the refinement target of the mixed 5000-disc case) and,
         # for comparison, to 1e-10 (the FP64 solve's tolerance); fields are compared at the targets
@@ -324,18 +325,20 @@ def run_ours(args, rank, world, local_rank):
             solve["fp64_iters"] = info_d["iters"]
             solve["fp64_rel_res"] = info_d["rel_res_fp64"]
             u_d = ctxd.eval_field(w.targets, 0, lsms.FIELD_SCATTERED)
+            u_ref_fp64 = u_d
             for key in u_m:
                 solve[key + "_vs_fp64_field_rel_err"] = float(np.linalg.norm(u_m[key] - u_d) / np.linalg.norm(u_d))
             solve["speedup_mixed_vs_fp64"] = solve["fp64_s"] / solve["mixed_s"]
             ctxd.close()
     ctx.close()
-    batched = stack = inclusions = contrast = large = None
+    batched = stack = inclusions = contrast = large = boxes = None
     if world == 1 and not args.no_batched:
         batched = run_batched(args, dev, flush)
         stack = run_stack(args, w, dev, flush)
         inclusions = run_inclusions(args, w, dev, flush)
         contrast = run_contrast(args)
         large = run_large(args, dev, flush)
+        boxes = run_boxes(args, w, dev, flush, u_ref_fp64)
 
     if rank != 0:
         return None
@@ -356,6 +359,7 @@ def run_ours(args, rank, world, local_rank):
         "inclusions": inclusions,
         "contrast_sweep": contrast,
         "large": large,
+        "boxes": boxes,
         "roofline": {"kernel": "k_translate_f32", "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": traffic, "flop_per_launch": flop, "launch_ms": tr_ms,
@@ -587,6 +591,47 @@ def run_contrast(args):
     return {"workload": "contrast200_p10_ns2048", "inclusions": cfg["n"], "p": cfg["p"],
             "contour_nodes": cfg["n_nodes"], "tol": cfg["tol"], "precision": "fp64",
             "total_s": time.perf_counter() - t_all, "per_k2": rows}
+
+
+def run_boxes(args, w, dev, flush, u_ref=None):
+    """The bench layout with the translation through boxes (width 4, 614 boxes): mixed and FP64
+    operator applications, the mixed solve at 1e-8 and the FP64 solve at 1e-10, and the scattered
+    field against the all-pairs FP64 solve (u_ref)."""
+    import numpy as np
+    import torch
+
+    from paper_1407_3868_gb300 import inputs, lsms
+    out = {"workload": w.name + "_boxes", "box_width": 4.0}
+    x = torch.from_numpy(inputs.random_coefficients(w.n, w.p, 1, 600)).to(dev)
+    y = torch.empty_like(x)
+    fl_m = lsms.APPLY_SCALED | lsms.APPLY_MIXED
+    for prec, key, flags, tol in ((lsms.LSMS_MIXED, "mixed", fl_m, 1e-8),
+                                  (lsms.LSMS_FP64, "fp64", lsms.APPLY_SCALED, 1e-10)):
+        ctx = lsms.context_for(w, prec)
+        ctx.set_particles(w.centres())
+        ctx.set_fmm(4.0)
+        out["boxes"], out["order"] = ctx.fmm_info()
+        for _ in range(3):
+            ctx.apply_dev(x, y, flags)
+        torch.cuda.synchronize()
+        ms = time_device(lambda: ctx.apply_dev(x, y, flags), max(3, min(args.steps, 10)), flush)
+        row = {"ms_per_apply": ms, "applies_per_s": 1e3 / ms}
+        if not args.no_solve:
+            if prec == lsms.LSMS_MIXED:
+                ctx.solve(w.sources, tol=tol, maxiter=2000)          # warm-up (graphs, workspaces)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, info = ctx.solve(w.sources, tol=tol, maxiter=2000, raise_on_error=False)
+            row["solve"] = {"tol": tol, "s": time.perf_counter() - t0, "iters": info["iters"],
+                            "refinements": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"],
+                            "status": info["status"]}
+            if u_ref is not None:
+                u = ctx.eval_field(w.targets, 0, lsms.FIELD_SCATTERED)
+                row["solve"]["field_rel_err_vs_all_pairs_fp64"] = float(np.linalg.norm(u - u_ref) /
+                                                                        np.linalg.norm(u_ref))
+        out[key] = row
+        ctx.close()
+    return out
 
 
 def run_large(args, dev, flush):
