@@ -193,3 +193,29 @@ def test_box_translation_edge_layouts(L, case):
         return
     assert rel(a64, dense, ws) < TOL64
     assert rel(a32, dense, ws) < 2e-5
+
+
+def test_boxes_with_a_layer_stack_and_rotated_inclusions(L):
+    # the box translation inside the five-layer medium (disc layer 0.5 below y = 0) with rotated
+    # star inclusions: the operator through boxes equals the all-pairs one, both precisions
+    st = inputs.STACK5
+    m = inputs.MEDIUM
+    n, p = 500, 10
+    h = inputs.widened_half_width(n)
+    local = inputs.layout(n, -h, h, 81)
+    glob = local - np.array([0.0, inputs.STACK5_DEPTH])
+    s = inputs.STAR5
+    smat = O.inclusion_scattering_matrix(inputs.star_curve(s["a1"], s["a2"], s["a3"], s["n_pts"]), p, m["k2"], m["kp"])
+    theta = inputs.orientations(n, 82)
+    hs = O.order_scale(p, m["k2"], m["radius"])
+    x = inputs.random_coefficients(n, p, 1, 83) / hs[None, None, :]
+    for precision, flags, tol in ((0, 0, TOL64), (1, L.APPLY_MIXED, 2e-5)):
+        with L.Context(0, 0, 0, 0, m["kp"], m["radius"], p, 512, b=inputs.contour_b(2 * h), t_max=141.0,
+                       panel_order=16, precision=precision, stack=(st["ks"], st["ds"], st["layer"])) as ctx:
+            ctx.set_particles(glob)
+            ctx.set_scattering_matrix(smat)
+            ctx.set_orientations(theta)
+            y_all = ctx.apply(x, flags)
+            ctx.set_fmm(4.0)
+            y_box = ctx.apply(x, flags)
+        assert rel(y_box, y_all, hs) < tol, precision
