@@ -95,7 +95,7 @@ def parse():
     ap.add_argument("--baseline-rows", type=int, default=40,
                     help="target rows of the oracle's bounded sample for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing")
-    ap.add_argument("--section", choices=["large"], default=None,
+    ap.add_argument("--section", choices=["large", "example1"], default=None,
                     help="run one extra measurement alone and print its dict (for profiling)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -331,7 +331,7 @@ def run_ours(args, rank, world, local_rank):
             solve["speedup_mixed_vs_fp64"] = solve["fp64_s"] / solve["mixed_s"]
             ctxd.close()
     ctx.close()
-    batched = stack = inclusions = contrast = large = boxes = None
+    batched = stack = inclusions = contrast = large = boxes = example1 = None
     if world == 1 and not args.no_batched:
         batched = run_batched(args, dev, flush)
         stack = run_stack(args, w, dev, flush)
@@ -339,6 +339,7 @@ def run_ours(args, rank, world, local_rank):
         contrast = run_contrast(args)
         large = run_large(args, dev, flush)
         boxes = run_boxes(args, w, dev, flush, u_ref_fp64)
+        example1 = run_example1(args)
 
     if rank != 0:
         return None
@@ -360,6 +361,7 @@ def run_ours(args, rank, world, local_rank):
         "contrast_sweep": contrast,
         "large": large,
         "boxes": boxes,
+        "example1": example1,
         "roofline": {"kernel": "k_translate_f32", "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": traffic, "flop_per_launch": flop, "launch_ms": tr_ms,
@@ -634,6 +636,40 @@ def run_boxes(args, w, dev, flush, u_ref=None):
     return out
 
 
+def run_example1(args):
+    """Sec. 6 Example 1's configuration: 5000 rotated three-lobed inclusions, k = (1, 3, 1), a layer 32
+    thick (a guided-mode layer), kp = 2, p = 10, 2048 contour nodes; the mixed solve to 1e-6 (the
+    paper's tolerance; its serial CPU code with FMM needed 127 s on a laptop, context only)."""
+    import torch
+
+    from paper_1407_3868_gb300 import inputs, lsms
+    e = inputs.EXAMPLE1
+    sh = e["shape"]
+    curve = inputs.star_curve(sh["a1"], sh["a2"], sh["a3"], sh["n_pts"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = lsms.Context(e["k1"], e["k2"], e["k3"], e["d"], e["kp"], e["radius"], e["p"], e["n_nodes"],
+                       b=inputs.contour_b(e["x_hi"] - e["x_lo"]), t_max=e["t_max"], panel_order=16,
+                       precision=lsms.LSMS_MIXED)
+    ctx.set_particles(inputs.example1_layout())
+    ctx.set_scattering_matrix(lsms.inclusion_scattering_matrix(e["p"], e["k2"], e["kp"], e["radius"], curve))
+    ctx.set_orientations(inputs.orientations(e["n"], 32))
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    out = {"workload": "example1_star5000_p10_ns2048", "setup_s": t_setup,
+           "paper_context": "Sec. 6 Example 1: 127 s to 6 digits on a 2.3 GHz laptop (serial, FMM)"}
+    if not args.no_solve:
+        ctx.solve([[0.0, 1.0]], tol=e["tol"], maxiter=3000, raise_on_error=False)      # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info = ctx.solve([[0.0, 1.0]], tol=e["tol"], maxiter=3000, raise_on_error=False)
+        out["mixed_solve"] = {"tol": e["tol"], "s": time.perf_counter() - t0, "iters": info["iters"],
+                              "refinements": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"],
+                              "status": info["status"]}
+    ctx.close()
+    return out
+
+
 def run_large(args, dev, flush):
     """N >> 5000: 50,000 discs (the bench medium and density, p = 14, 1024 nodes, 24,544 wide).
     Operator applications with the translation through boxes (width 4, FP64; the contour part
@@ -754,6 +790,14 @@ def main():
         torch.cuda.set_device(dev)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
         print(json.dumps({"section": "large", "large": run_large(args, dev, flush)}))
+        return
+    if args.section == "example1":
+        import torch
+
+        import __graft_entry__
+        __graft_entry__.build()
+        torch.cuda.set_device(torch.device("cuda", local_rank))
+        print(json.dumps({"section": "example1", "example1": run_example1(args)}))
         return
     if args.impl == "reference":
         line = run_reference(args, rank)

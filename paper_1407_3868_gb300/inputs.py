@@ -222,3 +222,20 @@ def contrast_t_max(k2: float) -> float:
     """Gamma1 length for the contrast sweep: the integrands decay like exp(-2 t) beyond k2 (centres
     at least 1.17 from the interfaces), so 30 past the largest wavenumber."""
     return max(CONTRAST["k1"], k2) + 30.0
+
+
+# ------------------------------------------------------------------------------------------------
+# Sec. 6, Example 1: 5000 three-lobed inclusions (a1 = 0.12, a2 = 0.04, a3 = 3; enclosing radius
+# 0.17) with kp = 2 in a layer of thickness 32 between half-spaces of k = 1, k2 = 3 (a guided-mode
+# layer); p = 10; GMRES to 1e-6.  The layout (71 wide, ~21% area fraction, centres at least 0.67
+# from the interfaces) stands in for the paper's random placement.
+# ------------------------------------------------------------------------------------------------
+EXAMPLE1 = dict(k1=1.0, k2=3.0, k3=1.0, d=32.0, kp=2.0, radius=0.17, n=5000, p=10, n_nodes=2048,
+                t_max=45.0, x_lo=-35.5, x_hi=35.5, clearance=0.5, seed=31, tol=1e-6,
+                shape=dict(a1=0.12, a2=0.04, a3=3, n_pts=256))
+
+
+def example1_layout(n: int = EXAMPLE1["n"], x_lo: float = EXAMPLE1["x_lo"], x_hi: float = EXAMPLE1["x_hi"],
+                    seed: int = EXAMPLE1["seed"]) -> np.ndarray:
+    e = EXAMPLE1
+    return layout(n, x_lo, x_hi, seed, radius=e["radius"], d=e["d"], clearance=e["clearance"])

@@ -93,3 +93,35 @@ def test_guided_solve_and_fields(case, L, precision, tol):
             u = ctx.eval_field(case["tg"], s, which)
             assert rel(u, pr.field_layer1(case["src"][s], b_o, case["tg"], name)) < tol, (s, name)
     ctx.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL64_SOLVE), (1, TOL_MIXED)])
+def test_example1_medium_small(L, precision, tol):
+    # the medium of Sec. 6 Example 1 (k = (1, 3, 1), a layer 32 thick, kp = 2, three-lobed
+    # inclusions, p = 10) with 30 inclusions, against the oracle on the same 2048-node contour
+    e = inputs.EXAMPLE1
+    sh = e["shape"]
+    c = inputs.example1_layout(30, -3.0, 3.0, 7)
+    b = inputs.contour_b(e["x_hi"] - e["x_lo"])
+    curve = inputs.star_curve(sh["a1"], sh["a2"], sh["a3"], sh["n_pts"])
+    S = O.inclusion_scattering_matrix(curve, e["p"], e["k2"], e["kp"])
+    th = inputs.orientations(30, 8)
+    med = O.Medium(e["k1"], e["k2"], e["k3"], e["d"], e["kp"], e["radius"])
+    lam, wt = O.contour(e["n_nodes"], e["k1"], e["k2"], e["k3"], b, e["t_max"])
+    pr = O.Problem(med, e["p"], c, lam, wt, smat=S, theta=th)
+    hs = O.order_scale(e["p"], e["k2"], e["radius"])
+    src = np.array([0.0, 1.0])
+    tg = inputs.observation_points(-4.0, 4.0, 12, 1.5)
+    with L.Context(e["k1"], e["k2"], e["k3"], e["d"], e["kp"], e["radius"], e["p"], e["n_nodes"], b=b,
+                   t_max=e["t_max"], panel_order=16, precision=precision) as ctx:
+        ctx.set_particles(c)
+        ctx.set_scattering_matrix(L.inclusion_scattering_matrix(e["p"], e["k2"], e["kp"], e["radius"], curve))
+        ctx.set_orientations(th)
+        x = inputs.random_coefficients(30, e["p"], 1, 9) / hs[None, None, :]
+        assert rel(ctx.apply(x)[0], pr.apply(x[0]), hs) < (TOL64 if precision == 0 else TOL_MIXED_OP)
+        beta, info = ctx.solve(src[None, :], tol=1e-12 if precision == 0 else 1e-11, maxiter=800)
+        assert info["status"] == 0
+        b_o = pr.solve_dense(src)
+        assert rel(beta[0], b_o, hs[None, :]) < tol
+        u = ctx.eval_field(tg, 0, L.FIELD_SCATTERED)
+        assert rel(u, pr.field_layer1(src, b_o, tg, "scattered")) < tol
