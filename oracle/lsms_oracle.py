@@ -787,9 +787,14 @@ class Problem:
         return out
 
     def solve_dense(self, src):
-        """beta from (I - S(T + R)) beta = S a_inc by LU."""
+        """beta from (I - S(T + R)) beta = S a_inc by LU, on the system equilibrated by the order
+        scale D = diag(|H_n(k2 R)|) (D A D^{-1} (D beta) = D rhs: the same solution; when k2 R is
+        small the plain matrix's condition number grows with |H_p(k2 R)| while the equilibrated one
+        stays near 1, and LU is only backward stable in the norm of the system it factors)."""
         a = self.dense_operator()
-        return np.linalg.solve(a, self.rhs(src).ravel()).reshape(self.N, self.P)
+        d = np.tile(order_scale(self.p, self.m.k2, self.m.radius), self.N)
+        x = np.linalg.solve(d[:, None] * a / d[None, :], d * self.rhs(src).ravel()) / d
+        return x.reshape(self.N, self.P)
 
     def block_system(self, src):
         """[A B; C D] [sigma; beta] = [b; 0] of Eq. "finalsys", assembled entry by entry.
