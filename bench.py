@@ -206,6 +206,9 @@ def run_ours(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
+    # measured FMA ceilings of this GPU, beside the derived ALU peaks
+    fma = {"fp32_tflops": lsms.fma_probe(lsms.LSMS_MIXED), "fp64_tflops": lsms.fma_probe(lsms.LSMS_FP64),
+           "probe": "lsms_fma_probe: 8 independent FMA chains per thread, 8 CTAs of 256 per SM"}
     w = inputs.WORKLOADS[args.workload]
     n, P = w.n, 2 * w.p + 1
     centres = w.centres()
@@ -365,7 +368,9 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"kernel": "k_translate_f32", "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": traffic, "flop_per_launch": flop, "launch_ms": tr_ms,
-                     "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+                     "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                     "measured_fma_peak": fma["fp32_tflops"], "frac_of_measured_fma": achieved / fma["fp32_tflops"]},
+        "fma_probe": fma,
         "e2e": {"value": e2e, "unit": "applies/s", "h2d_bytes_per_step": n * P * 16,
                 "d2h_bytes_per_step": n * P * 16},
         "gpu_launches": launches * args.steps,

@@ -303,6 +303,12 @@ int lsms_get_scattering_matrix(const lsms_ctx* ctx, double* s);
 int lsms_inclusion_scattering_matrix(int p, double k2, double kp, double radius, int n_pts,
                                      const double* curve, double* s_out);
 
+/* lsms_fma_probe — the achievable FMA rate of the current GPU (TFLOP/s, 2 flop per FMA), measured
+ *   with independent dependency chains over a grid that fills every SM (precision LSMS_FP64:
+ *   FP64; LSMS_MIXED: FP32).  A measured ceiling to set beside the derived ALU peaks.  About a
+ *   millisecond of GPU time.  Errors: LSMS_ERR_ARG, LSMS_ERR_CUDA (no device). */
+int lsms_fma_probe(int precision, double* tflops);
+
 /* lsms_pec_scattering_diagonal — host only.  S_n = -J_n(k2 R) / H_n(k2 R), n = -p..p, of a perfectly
  *   conducting disc (Sec. 3.1, remark after Definition 3.1: the total field vanishes on the
  *   boundary); pass diag(S) to lsms_set_scattering_matrix.  s_diag: 2p + 1 complex.

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblsms.so")
 SOURCES = ["abi.cu", "kernels_f64.cu", "mixed.cu", "contour_tc.cu", "translate_tc.cu", "gmres.cu", "batch.cu",
-           "host_setup.cpp", "inclusion.cpp", "fmm.cu"]
+           "host_setup.cpp", "inclusion.cpp", "fmm.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 

@@ -1,0 +1,71 @@
+// FMA-pipe probe: the achievable FP32 and FP64 FMA rates of this GPU, measured with independent
+// dependency chains per thread (enough in flight to hide the pipe latency) over a grid that fills
+// every SM.  Used to put the derived peaks (SMs x lanes x 2 x clock) of the ALU-bound kernels
+// beside a measured ceiling.
+#include <cuda_runtime.h>
+
+#include "lsms.h"
+#include "lsms_internal.h"
+#include "lsms_ops.h"
+
+namespace {
+
+constexpr int kChains = 8;
+constexpr int kIters = 4096;
+
+template <typename T>
+__global__ void k_fma_chains(T a, T b, T* out) {
+  T v[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) v[c] = (T)(threadIdx.x + c);
+  for (int i = 0; i < kIters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) v[c] = fma(v[c], a, b);
+  }
+  T s = 0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += v[c];
+  if (s == (T)-1.2345) out[0] = s;        // never true for the inputs used: keeps the chains alive
+}
+
+}  // namespace
+
+extern "C" int lsms_fma_probe(int precision, double* tflops) {
+  if (!tflops || (precision != LSMS_FP64 && precision != LSMS_MIXED))
+    return ctx_fail(nullptr, LSMS_ERR_ARG, "fma_probe: precision LSMS_FP64 or LSMS_MIXED (FP32) and an output");
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return ctx_fail(nullptr, LSMS_ERR_CUDA, "fma_probe: no CUDA device");
+  }
+  void* out = nullptr;
+  if (cudaMalloc(&out, 16) != cudaSuccess) {
+    cudaGetLastError();
+    return ctx_fail(nullptr, LSMS_ERR_OOM, "fma_probe: cudaMalloc failed");
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int threads = 256, blocks = sms * 8;
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {       // the first launch warms up; keep the fastest
+    cudaEventRecord(e0);
+    if (precision == LSMS_FP64)
+      k_fma_chains<double><<<blocks, threads>>>(0.9999999, 1e-7, (double*)out);
+    else
+      k_fma_chains<float><<<blocks, threads>>>(0.9999f, 1e-4f, (float*)out);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  const cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return ctx_fail(nullptr, LSMS_ERR_CUDA, std::string("fma_probe: ") + cudaGetErrorString(err));
+  const double flop = 2.0 * kChains * (double)kIters * threads * blocks;
+  *tflops = flop / (best / 1e3) / 1e12;
+  return LSMS_OK;
+}

@@ -19,7 +19,7 @@ APPLY_SCALED, APPLY_MIXED, APPLY_NO_TRANSLATION, APPLY_NO_REFLECTION, APPLY_ALPH
 FIELD_TOTAL, FIELD_SCATTERED, FIELD_PARTICLE = 0, 1, 2
 STATUS = {0: "OK", -1: "ARG", -2: "GEOMETRY", -3: "NOT_CONVERGED", -4: "NONFINITE", -5: "OOM",
           -6: "CUDA", -7: "STATE"}
-EXPORTS = ["lsms_create", "lsms_pec_scattering_diagonal", "lsms_set_fmm", "lsms_get_fmm", "lsms_fmm_stats", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
+EXPORTS = ["lsms_create", "lsms_fma_probe", "lsms_pec_scattering_diagonal", "lsms_set_fmm", "lsms_get_fmm", "lsms_fmm_stats", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
            "lsms_get_scattering_matrix", "lsms_inclusion_scattering_matrix", "lsms_set_particles", "lsms_apply", "lsms_apply_ex", "lsms_apply_dev",
            "lsms_translate", "lsms_aggregate", "lsms_reflect", "lsms_disaggregate", "lsms_incident",
            "lsms_get_contour", "lsms_get_scattering", "lsms_num_nodes", "lsms_num_particles",
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsms_get_scattering_matrix": (i, [_P, _D]),
         "lsms_inclusion_scattering_matrix": (i, [i, d, d, d, i, _D, _D]),
         "lsms_pec_scattering_diagonal": (i, [i, d, d, _D]),
+        "lsms_fma_probe": (i, [i, _D]),
         "lsms_apply": (i, [_P, i, _D, _D]),
         "lsms_apply_ex": (i, [_P, i, _D, _D, i]),
         "lsms_apply_dev": (i, [_P, i, _P, _P, i, _P]),
@@ -405,6 +406,16 @@ def inclusion_scattering_matrix(p, k2, kp, radius, curve) -> np.ndarray:
     if rc != 0:
         raise LsmsError(rc, lib.lsms_last_error(None).decode())
     return s
+
+
+def fma_probe(precision) -> float:
+    """lsms_fma_probe: measured FMA TFLOP/s of the GPU (LSMS_FP64 or LSMS_MIXED for FP32)."""
+    lib = load()
+    v = ctypes.c_double()
+    rc = lib.lsms_fma_probe(int(precision), ctypes.byref(v))
+    if rc != 0:
+        raise LsmsError(rc, lib.lsms_last_error(None).decode())
+    return v.value
 
 
 def pec_scattering_diagonal(p, k2, radius) -> np.ndarray:

@@ -351,3 +351,14 @@ def test_full_size_solve_satisfies_the_equations_on_sampled_rows(L):
     assert rel(beta_m[0], beta[0], case.hs) < TOL_MIXED
     ctx_m.close()
     case.ctx.close()
+
+
+def test_fma_probe_is_plausible(L):
+    # the measured FMA ceilings sit near the derived peaks (152 SMs x 128 FP32 lanes, or x 2 FP64
+    # FMA units, x 2 flop x clock): between a quarter of them and a little above
+    f32 = L.fma_probe(L.LSMS_MIXED)
+    f64 = L.fma_probe(L.LSMS_FP64)
+    assert 0.25 * 80.5 < f32 < 1.1 * 80.5, f32
+    assert 0.25 * 1.26 < f64 < 1.1 * 1.26, f64
+    with pytest.raises(L.LsmsError):
+        L.fma_probe(7)
