@@ -3,6 +3,13 @@
 Every computation happens in the CUDA library.  If the library is missing this module raises: there
 is no CPU fallback.  Host arrays are NumPy complex128 (interleaved, the layout the ABI expects);
 device entry points take torch tensors (complex128, CUDA) and a stream.
+
+Context covers the C ABI: three-layer media (Context(k1, k2, k3, d, ...)) or any stack of layers,
+absorbing ones included (stack=(ks, thicknesses, particle_layer), complex ks); particles or batches
+of layouts (set_particles, set_layouts); dense rotated scattering matrices for inclusions of any
+shape (set_scattering_matrix, set_orientations; inclusion_scattering_matrix and
+pec_scattering_diagonal build them on the host); the translation through boxes (set_fmm); the
+operator and its steps, solves and fields.  fma_probe measures the GPU's FMA ceilings.
 """
 from __future__ import annotations
 
