@@ -57,10 +57,14 @@ typedef enum {
 /* Discretised Sommerfeld contour (Sec. 5.1, Eq. "sommerseg"): Gamma3 = t + i b (t < 0),
  * Gamma2 = i s (s from b to -b), Gamma1 = t - i b (t > 0), truncated at |t| = t_max.
  * Gamma1 and Gamma3 each hold n1 = q*floor((n_nodes - q)/(2q)) Gauss-Legendre nodes in panels of
- * order q = panel_order, graded toward the branch points k1, k2, k3 (breakpoints k_i +- b*2^j);
- * Gamma2 holds the remaining n_nodes - 2*n1 nodes as one Gauss-Legendre rule.  Node order is
- * Gamma3, Gamma2, Gamma1.  Zero fields take defaults: b = 0.2, t_max = max(k1,k2,k3) + 20
- * (Sec. 6), panel_order = 16. */
+ * order q = panel_order, graded toward the branch points (every layer's Re k; breakpoints
+ * k_i +- b*2^j, the deepest grading that fits, then the longest panel halved).  In a guided-mode
+ * medium (an interior k above both half-spaces' k: poles of the layer response on the real axis
+ * between them, a distance b below Gamma1) the panels are instead placed greedily, halving the one
+ * with the largest length / (b + distance to the nearest branch point), a panel meeting the pole
+ * band counting as distance 0.  Gamma2 holds the remaining n_nodes - 2*n1 nodes as one
+ * Gauss-Legendre rule.  Node order is Gamma3, Gamma2, Gamma1.  Zero fields take defaults: b = 0.2,
+ * t_max = max k + 20 (Sec. 6), panel_order = 16. */
 typedef struct {
   int n_nodes;       /* N_S, required; must leave n1 >= panel_order                          */
   double b;          /* offset of Gamma1/Gamma3 from the real axis                            */
