@@ -106,6 +106,16 @@ int apply_device(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags,
   launch_scale_in(x, c->d_scale_in + mode * P, xs, nrhs, n, P, st);
   ++launches;
   if (c->timing) cudaEventRecord(c->ev[0], st);
+  // mixed: the reflected coupling (tensor-core contour contractions) on the side stream, beside
+  // the translation; its result is added into alpha after the join (same arithmetic, same order)
+  const bool overlap = mixed && c->side && !(flags & LSMS_APPLY_NO_TRANSLATION) &&
+                       !(flags & LSMS_APPLY_NO_REFLECTION);
+  if (overlap) {
+    cudaEventRecord(c->ev_fork, st);
+    cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    if ((rc = reflection_mixed_stage(c, nrhs, xs, c->side))) return rc;
+    cudaEventRecord(c->ev_join, c->side);
+  }
   if (!(flags & LSMS_APPLY_NO_TRANSLATION)) {
     // box method (FP64, either precision): see fmm.cu; FP64: one kernel; mixed: FP32 copy of xs,
     // the translation (+ the partial-sum reduction, or the packing of the tensor-core operands)
@@ -125,7 +135,10 @@ int apply_device(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags,
   }
   if (c->timing) cudaEventRecord(c->ev[1], st);
   if (!(flags & LSMS_APPLY_NO_REFLECTION)) {
-    if (mixed) {
+    if (overlap) {
+      cudaStreamWaitEvent(st, c->ev_join, 0);
+      reflection_mixed_add(c, nrhs, alpha, st);
+    } else if (mixed) {
       if ((rc = reflection_mixed(c, nrhs, xs, alpha, st))) return rc;
     } else {
       if ((rc = reflection_f64(c, nrhs, xs, alpha, st))) return rc;
@@ -195,6 +208,13 @@ int create_stack(const std::vector<cplx>& kc, const std::vector<double>& ds, int
     delete c;
     return fail(nullptr, LSMS_ERR_CUDA, "cudaStreamCreate failed (no CUDA device?)");
   }
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    lsms_destroy(c);
+    return fail(nullptr, LSMS_ERR_CUDA, "side stream creation failed");
+  }
   std::vector<cplx> s_out(2 * c->P);
   std::vector<double> s_in(2 * c->P);
   for (int q = 0; q < c->P; ++q) {
@@ -261,6 +281,7 @@ extern "C" int lsms_create_stack_c(int n_layers, const double* k, const double* 
 extern "C" void lsms_destroy(lsms_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->side) cudaStreamSynchronize(c->side);
   batch_free(c);
   void* ptrs[] = {c->d_lam, c->d_g1, c->d_g2, c->d_refl, c->d_inc, c->d_field, c->d_fagg, c->d_udis,
                   c->d_scale_in, c->d_hscale, c->d_scale_out, c->d_cx, c->d_cy, c->d_eagg, c->d_edis,
@@ -281,6 +302,10 @@ extern "C" void lsms_destroy(lsms_ctx* c) {
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : c->gm_ev)
     if (e) cudaEventDestroy(e);
+  if (c->side) cudaStreamSynchronize(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }

@@ -468,7 +468,8 @@ int disaggregate_mixed(lsms_ctx* c, int nrhs, const double2* V, double2* alpha, 
 }
 
 // alpha += R xs: aggregate GEMM -> per-node stage writing the second GEMM's planes -> disaggregate.
-int reflection_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st) {
+// The reflected coupling up to (excluding) the final add into alpha, on stream st.
+int reflection_mixed_stage(lsms_ctx* c, int nrhs, const double2* xs, cudaStream_t st) {
   int rc;
   const int P = c->P, ncols = nrhs * 2 * P, ns = c->ns;
   if ((rc = tc_reserve(c, ncols, st))) return rc;
@@ -481,6 +482,19 @@ int reflection_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, c
   k_node_stage_tc<<<(int)((threads + 255) / 256), 256, 0, st>>>(ns, P, nrhs, t->c_agg, t->ncols_pad, c->d_fagg,
                                                                c->d_refl, c->d_udis, t->ncols_pad, t->kpad_dis, t->b_dis);
   launch_gemm(t->map_a_dis, t->map_b_dis, c->n, ncols, t->ncols_pad, t->kpad_dis, t->c_dis, t->d_err, st);
+  return check_cuda(c, "reflection_mixed");
+}
+
+// alpha += the disaggregated reflected coupling of the last reflection_mixed_stage.
+void reflection_mixed_add(lsms_ctx* c, int nrhs, double2* alpha, cudaStream_t st) {
+  TcState* t = (TcState*)c->tc;
+  const int P = c->P;
   k_c_add_alpha<<<grid_for((long long)nrhs * c->n * P, 256), 256, 0, st>>>(t->c_dis, t->ncols_pad, c->n, P, nrhs, alpha);
+}
+
+int reflection_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st) {
+  int rc;
+  if ((rc = reflection_mixed_stage(c, nrhs, xs, st))) return rc;
+  reflection_mixed_add(c, nrhs, alpha, st);
   return check_cuda(c, "reflection_mixed");
 }

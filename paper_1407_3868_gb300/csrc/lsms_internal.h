@@ -89,6 +89,9 @@ struct lsms_ctx {
   DevBuf theta_buf;                 // [N] rotation angles (valid when has_theta)
   bool has_theta = false;
   FmmState fmm;
+  // side stream of the mixed operator: the reflected coupling runs beside the translation
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<double> hscale;       // |H_n(k2 R)|, P
 
   // discs

@@ -36,6 +36,9 @@ int incident_device(lsms_ctx* c, int nsrc, const double* d_src, double2* out, cu
 int tc_setup(lsms_ctx* c);            // BF16 planes of the layout's tables (after set_particles)
 void tc_free(lsms_ctx* c);
 int mixed_check(lsms_ctx* c);         // reads and clears the device error flag of the TC kernels
+// the mixed reflected coupling split at its final add (run the stage on a side stream, add after a join)
+int reflection_mixed_stage(lsms_ctx* c, int nrhs, const double2* xs, cudaStream_t st);
+void reflection_mixed_add(lsms_ctx* c, int nrhs, double2* alpha, cudaStream_t st);
 int* tc_err_flag(lsms_ctx* c);        // that flag (device), or null before tc_setup
 int build_lowp_tables(lsms_ctx* c);
 // alpha = T xs in FP32 arithmetic (sums of the per-split FP32 partials accumulated in FP64)
