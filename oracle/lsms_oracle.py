@@ -956,14 +956,29 @@ class Problem:
                 return abs(density(k * math.cos(th), layer)) ** 2 * (b - a) * 0.5 * math.sin(phi)
             return integrate.quad(f, 0.0, math.pi, epsabs=tol, epsrel=tol, limit=4000)[0]
 
-        branch = getattr(self.m, "ks", (k1, k2, k3))          # every layer's wavenumber
+        branch = [complex(kk).real for kk in getattr(self.m, "ks", (k1, k2, k3))]   # every layer's Re k
 
         def pieces(k, layer):
             inner = sorted(set(math.acos(kk / k) for kk in branch if kk < k))
             breaks = [0.0] + inner + [math.pi - t for t in reversed(inner)] + [math.pi]
             return sum(piece(k, layer, a, b) for a, b in zip(breaks[:-1], breaks[1:])) / (2.0 * FOUR_PI)
 
-        return pieces(k1, 1), pieces(k3, 3)
+        if complex(k3).imag == 0.0:
+            return pieces(k1, 1), pieces(complex(k3).real, 3)
+        # an absorbing bottom half-space: the power crossing into it, all of which it absorbs,
+        # -(1/8pi) int |sigma_L|^2 Im(gamma_L) / |gamma_L|^2 over the whole real axis (the same
+        # Parseval identity; for real k_L only |lambda| < k_L contributes and this is the form above)
+        kl = complex(k3)
+
+        def f(lam_real):
+            g = gamma(np.array([lam_real], dtype=complex), kl)[0]
+            return -abs(density(lam_real, 3)) ** 2 * g.imag / abs(g) ** 2
+
+        tail = max(abs(kk) for kk in branch) + 60.0
+        pts = sorted(set([-tail, tail] + [s * abs(kk) for kk in branch for s in (-1.0, 1.0)]))
+        down = sum(integrate.quad(f, a, b, epsabs=tol, epsrel=tol, limit=4000)[0]
+                   for a, b in zip(pts[:-1], pts[1:])) / (2.0 * FOUR_PI)
+        return pieces(k1, 1), down
 
 
 def gmres(matvec, b, tol=1e-12, maxiter=500):

@@ -676,3 +676,22 @@ def test_pec_disc_total_field_vanishes_on_the_boundary():
     Sd = O.mie_coefficients(p, k2, MED["kp"], R)
     u_d = e @ (alpha * (O.bessel(n, k2 * R) + Sd * O.hankel(n, k2 * R)))
     assert np.abs(u_d).max() > 1e-2 * ref
+
+
+@pytest.mark.parametrize("loss", [0.5, 2.0])
+def test_energy_balance_with_an_absorbing_substrate(loss):
+    # lossless layers 1 and 2 and discs over an absorbing half-space: the source's power
+    # 1/4 + Im u^s(x0) leaves upward through y = +inf or crosses into the substrate, where it is
+    # absorbed (flux -(1/8pi) int |sigma_3|^2 Im(gamma_3)/|gamma_3|^2 over the whole real axis)
+    k3 = MED["k3"] + 1j * loss
+    st = O.Stack([MED["k1"], MED["k2"], k3], [MED["d"]], 2, MED["kp"], MED["radius"])
+    c = np.array([[0.2, -0.7], [-0.6, -1.3], [0.9, -1.0]])
+    src = np.array([0.3, 1.0])
+    lam, wt = O.contour(1024, MED["k1"], MED["k2"], MED["k3"], 0.2, 120.0,
+                        branch_points=[MED["k1"], MED["k2"], MED["k3"]])
+    pr = O.Problem(st, 4, c, lam, wt)
+    beta = pr.solve_dense(src)
+    up, down = pr.outgoing_power(src, beta)
+    u_s = pr.field_layer1(src, beta, src[None, :], "scattered")[0]
+    assert up > 0 and down > 0
+    assert abs(up + down - (0.25 + u_s.imag)) < 1e-9 * 0.25
