@@ -348,6 +348,10 @@ int lsms_fmm_stats(lsms_ctx* ctx, long long* near_pairs, double* far_ms, double*
  *   assumption of Sec. 1), else LSMS_ERR_GEOMETRY (or LSMS_ERR_ARG for non-finite input). */
 int lsms_build_contour(const lsms_contour* contour, double k1, double k2, double k3, double* nodes,
                        double* weights);
+/* lsms_build_contour_stack — the contour lsms_create_stack / lsms_create_stack_c would use: k holds
+ *   the n_layers wavenumbers top to bottom (their real parts for an absorbing stack). */
+int lsms_build_contour_stack(const lsms_contour* contour, int n_layers, const double* k, double* nodes,
+                             double* weights);
 int lsms_scattering_diagonal(int p, double k2, double kp, double radius, double* s_diag);
 int lsms_check_geometry(double d, double radius, int n, const double* centres_xy);
 

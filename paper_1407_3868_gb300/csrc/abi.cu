@@ -652,6 +652,21 @@ extern "C" int lsms_build_contour(const lsms_contour* contour, double k1, double
   return LSMS_OK;
 }
 
+extern "C" int lsms_build_contour_stack(const lsms_contour* contour, int n_layers, const double* k,
+                                        double* nodes, double* weights) {
+  if (!contour || !k || !nodes || !weights || n_layers < 3)
+    return fail(nullptr, LSMS_ERR_ARG, "need n_layers >= 3 and non-NULL arguments");
+  for (int j = 0; j < n_layers; ++j)
+    if (!std::isfinite(k[j]) || !(k[j] > 0.0)) return fail(nullptr, LSMS_ERR_ARG, "wavenumbers must be finite and > 0");
+  std::vector<cplx> lam, wt;
+  std::string err;
+  const int rc = build_contour(*contour, std::vector<double>(k, k + n_layers), lam, wt, err);
+  if (rc) return fail(nullptr, rc, err);
+  std::memcpy(nodes, lam.data(), lam.size() * sizeof(cplx));
+  std::memcpy(weights, wt.data(), wt.size() * sizeof(cplx));
+  return LSMS_OK;
+}
+
 extern "C" int lsms_scattering_diagonal(int p, double k2, double kp, double radius, double* s) {
   if (p < 0 || p > LSMS_MAX_P || !s || !(k2 > 0) || !(kp > 0) || !(radius > 0))
     return fail(nullptr, LSMS_ERR_ARG, "bad arguments");

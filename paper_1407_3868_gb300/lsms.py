@@ -26,7 +26,7 @@ APPLY_SCALED, APPLY_MIXED, APPLY_NO_TRANSLATION, APPLY_NO_REFLECTION, APPLY_ALPH
 FIELD_TOTAL, FIELD_SCATTERED, FIELD_PARTICLE = 0, 1, 2
 STATUS = {0: "OK", -1: "ARG", -2: "GEOMETRY", -3: "NOT_CONVERGED", -4: "NONFINITE", -5: "OOM",
           -6: "CUDA", -7: "STATE"}
-EXPORTS = ["lsms_create", "lsms_fma_probe", "lsms_pec_scattering_diagonal", "lsms_set_fmm", "lsms_get_fmm", "lsms_fmm_stats", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
+EXPORTS = ["lsms_create", "lsms_build_contour_stack", "lsms_fma_probe", "lsms_pec_scattering_diagonal", "lsms_set_fmm", "lsms_get_fmm", "lsms_fmm_stats", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
            "lsms_get_scattering_matrix", "lsms_inclusion_scattering_matrix", "lsms_set_particles", "lsms_apply", "lsms_apply_ex", "lsms_apply_dev",
            "lsms_translate", "lsms_aggregate", "lsms_reflect", "lsms_disaggregate", "lsms_incident",
            "lsms_get_contour", "lsms_get_scattering", "lsms_num_nodes", "lsms_num_particles",
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsms_last_error": (ctypes.c_char_p, [_P]),
         "lsms_destroy": (None, [_P]),
         "lsms_build_contour": (i, [ctypes.POINTER(Contour), d, d, d, _D, _D]),
+        "lsms_build_contour_stack": (i, [ctypes.POINTER(Contour), i, _D, _D, _D]),
         "lsms_scattering_diagonal": (i, [i, d, d, d, _D]),
         "lsms_check_geometry": (i, [d, d, i, _D]),
         "lsms_set_timing": (i, [_P, i]),
@@ -362,6 +363,19 @@ def build_contour(n_nodes, k1, k2, k3, b=0.0, t_max=0.0, panel_order=0):
     wt = np.zeros(n_nodes, dtype=np.complex128)
     c = Contour(n_nodes, b, t_max, panel_order)
     rc = lib.lsms_build_contour(ctypes.byref(c), k1, k2, k3, _dptr(lam), _dptr(wt))
+    if rc != 0:
+        raise LsmsError(rc, lib.lsms_last_error(None).decode())
+    return lam, wt
+
+
+def build_contour_stack(n_nodes, ks, b=0.0, t_max=0.0, panel_order=0):
+    """Host-only: the library's contour for a stack of layers with wavenumbers ks (top to bottom)."""
+    lib = load()
+    k = np.ascontiguousarray(np.real(np.asarray(ks)), dtype=np.float64)
+    lam = np.zeros(n_nodes, dtype=np.complex128)
+    wt = np.zeros(n_nodes, dtype=np.complex128)
+    c = Contour(n_nodes, b, t_max, panel_order)
+    rc = lib.lsms_build_contour_stack(ctypes.byref(c), int(k.size), _dptr(k), _dptr(lam), _dptr(wt))
     if rc != 0:
         raise LsmsError(rc, lib.lsms_last_error(None).decode())
     return lam, wt

@@ -200,3 +200,19 @@ def test_library_pec_diagonal_equals_oracle(lib):
         assert np.abs(s - s_o).max() < 1e-13 * np.abs(s_o).max()
     with pytest.raises(lib.LsmsError):
         lib.pec_scattering_diagonal(16, 2.0, 0.2)
+
+
+@pytest.mark.parametrize("ks,b,n_nodes,t_max", [
+    (inputs.STACK5["ks"], 0.2, 512, 80.0),                                # five layers, no guided band
+    ([1.0, 2.5, 6.0, 3.0, 1.5], 0.2, 1024, 40.0),                          # guided band (1.5, 6)
+    ([2.0 * math.pi, 3.0 * math.pi, 3.4 * math.pi, 4.0 * math.pi], 0.1, 768, 60.0),
+    ([1.0, 1.0, 3.0, 1.0], 0.15, 2048, 45.0),                               # Example 1's medium, split
+])
+def test_library_stack_contour_equals_oracle_contour(lib, ks, b, n_nodes, t_max):
+    # the contour lsms_create_stack builds (host only) against the oracle's, node for node
+    lam, wt = lib.build_contour_stack(n_nodes, ks, b, t_max, 16)
+    lam_o, wt_o = O.contour(n_nodes, ks[0], ks[1], ks[-1], b, t_max, branch_points=ks)
+    assert np.max(np.abs(lam - lam_o)) <= 1e-12 * t_max
+    assert np.max(np.abs(wt - wt_o)) <= 1e-14 * t_max
+    with pytest.raises(lib.LsmsError):
+        lib.build_contour_stack(n_nodes, ks[:2], b, t_max, 16)
