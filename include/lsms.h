@@ -352,6 +352,14 @@ int lsms_build_contour(const lsms_contour* contour, double k1, double k2, double
  *   the n_layers wavenumbers top to bottom (their real parts for an absorbing stack). */
 int lsms_build_contour_stack(const lsms_contour* contour, int n_layers, const double* k, double* nodes,
                              double* weights);
+/* lsms_layer_response — host only.  The interface conditions of Sec. 2 at every interface of a
+ *   stack (complex k[n_layers] interleaved, thicknesses of layers 2 .. n_layers - 1, discs in
+ *   particle_layer), solved at n complex nodes lam for a unit incident density I in layer 1, a unit
+ *   upgoing particle density P at the top of the particle layer and a unit downgoing Q at its
+ *   bottom.  out: [n][4][3] complex; row u = sigma_1, s_m^+, s_m^-, sigma_L; column s = I, P, Q (the
+ *   per-node tables every context precomputes).  NaN entries where the system is singular. */
+int lsms_layer_response(int n_layers, const double* k, const double* thickness, int particle_layer, int n,
+                        const double* lam, double* out);
 int lsms_scattering_diagonal(int p, double k2, double kp, double radius, double* s_diag);
 int lsms_check_geometry(double d, double radius, int n, const double* centres_xy);
 

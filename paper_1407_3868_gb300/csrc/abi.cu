@@ -667,6 +667,38 @@ extern "C" int lsms_build_contour_stack(const lsms_contour* contour, int n_layer
   return LSMS_OK;
 }
 
+extern "C" int lsms_layer_response(int n_layers, const double* k, const double* thickness, int particle_layer,
+                                   int n, const double* lam, double* out) {
+  if (n_layers < 3 || !k || !thickness || particle_layer < 2 || particle_layer > n_layers - 1 || n < 0 ||
+      (n > 0 && (!lam || !out)))
+    return fail(nullptr, LSMS_ERR_ARG, "layer_response: need n_layers >= 3, 2 <= particle_layer <= n_layers - 1");
+  lsms_ctx tmp;
+  tmp.layer = particle_layer;
+  for (int j = 0; j < n_layers; ++j) {
+    const cplx kj(k[2 * j], k[2 * j + 1]);
+    if (!std::isfinite(kj.real()) || !std::isfinite(kj.imag()) || !(kj.real() > 0.0) || !(kj.imag() >= 0.0))
+      return fail(nullptr, LSMS_ERR_ARG, "layer_response: wavenumbers need Re k > 0, Im k >= 0");
+    tmp.kc.push_back(kj);
+    tmp.ks.push_back(kj.real());
+  }
+  for (int j = 0; j < n_layers - 2; ++j) {
+    if (!std::isfinite(thickness[j]) || !(thickness[j] > 0.0))
+      return fail(nullptr, LSMS_ERR_ARG, "layer_response: thicknesses must be finite and > 0");
+    tmp.ds.push_back(thickness[j]);
+  }
+  std::vector<cplx> g;
+  cplx r[4][3];
+  for (int v = 0; v < n; ++v) {
+    layer_response(&tmp, cplx(lam[2 * v], lam[2 * v + 1]), g, r);
+    for (int u = 0; u < 4; ++u)
+      for (int s = 0; s < 3; ++s) {
+        out[2 * ((size_t)v * 12 + u * 3 + s)] = r[u][s].real();
+        out[2 * ((size_t)v * 12 + u * 3 + s) + 1] = r[u][s].imag();
+      }
+  }
+  return LSMS_OK;
+}
+
 extern "C" int lsms_scattering_diagonal(int p, double k2, double kp, double radius, double* s) {
   if (p < 0 || p > LSMS_MAX_P || !s || !(k2 > 0) || !(kp > 0) || !(radius > 0))
     return fail(nullptr, LSMS_ERR_ARG, "bad arguments");

@@ -260,73 +260,84 @@ bool solve_small(std::vector<cplx>& a, int n, std::vector<cplx>& b, int nrhs) {
 // density I (line source in layer 1), a unit upgoing particle density P at the top of the disc layer
 // and a unit downgoing one Q at its bottom; the tables are the linear maps (P, Q) -> (s_m^+, s_m^-),
 // I -> (s_m^+, s_m^-) and (I, P, Q) -> sigma_1.
-void build_node_tables(lsms_ctx* c) {
-  NodeTables& t = c->nodes;
-  const int ns = c->ns, p = c->p, P = c->P;
+// The interface system of one node (see above) for unit I, P, Q: r[u][s] is unknown u (0: sigma_1,
+// 1: s_m^+, 2: s_m^-, 3: sigma_L) for source s (0: I, 1: P, 2: Q); g receives gamma_j(lambda) of
+// every layer.  NaN when the system is singular.
+void layer_response(const lsms_ctx* c, cplx lam, std::vector<cplx>& g, cplx r[4][3]) {
   const int L = (int)c->ks.size(), m = c->layer, n = 2 * L - 2;
-  t.g1.resize(ns); t.g2.resize(ns); t.g3.resize(ns);
-  t.refl.resize(4 * ns); t.inc.resize(2 * ns); t.field.resize(4 * ns);
-  t.fagg.assign(2 * (size_t)ns * P, cplx(0, 0));
-  t.udis.assign(2 * (size_t)ns * P, cplx(0, 0));
   auto col = [&](int j, int sign) {             // unknown of layer j (1-based)
     if (j == 1) return 0;
     if (j == L) return n - 1;
     return 1 + 2 * (j - 2) + (sign > 0 ? 0 : 1);
   };
-  std::vector<cplx> g(L), E(L + 1), a, b;
+  g.resize(L);
+  std::vector<cplx> E(L + 1), a((size_t)n * n, cplx(0, 0)), b((size_t)n * 3, cplx(0, 0));
+  for (int j = 1; j <= L; ++j) g[j - 1] = c->kc[j - 1].imag() == 0.0 ? gamma_of(lam, c->ks[j - 1]) : gamma_of(lam, c->kc[j - 1]);
+  for (int j = 2; j < L; ++j) E[j] = std::exp(-g[j - 1] * c->ds[j - 2]);
+  for (int i = 1; i < L; ++i) {                 // interface i: layer i above, i + 1 below
+    const int rv = 2 * (i - 1), rd = rv + 1;
+    const cplx gi = g[i - 1], gb = g[i];
+    if (i == 1) {
+      a[(size_t)rv * n + col(1, 1)] += 1.0 / gi;
+      a[(size_t)rd * n + col(1, 1)] += -1.0;
+    } else {
+      a[(size_t)rv * n + col(i, 1)] += E[i] / gi;
+      a[(size_t)rv * n + col(i, -1)] += 1.0 / gi;
+      a[(size_t)rd * n + col(i, 1)] += E[i];
+      a[(size_t)rd * n + col(i, -1)] += -1.0;
+    }
+    if (i + 1 == L) {
+      a[(size_t)rv * n + col(L, 1)] -= 1.0 / gb;
+      a[(size_t)rd * n + col(L, 1)] -= 1.0;
+    } else {
+      a[(size_t)rv * n + col(i + 1, 1)] -= 1.0 / gb;
+      a[(size_t)rv * n + col(i + 1, -1)] -= E[i + 1] / gb;
+      a[(size_t)rd * n + col(i + 1, 1)] -= 1.0;
+      a[(size_t)rd * n + col(i + 1, -1)] += E[i + 1];
+    }
+    if (i == 1) {                               // incident wave, above interface 1
+      b[(size_t)rv * 3 + 0] -= 1.0 / gi;
+      b[(size_t)rd * 3 + 0] -= 1.0;
+    }
+    if (i == m - 1) {                           // discs' upgoing density, below this interface
+      b[(size_t)rv * 3 + 1] += 1.0 / gb;
+      b[(size_t)rd * 3 + 1] += -1.0;
+    }
+    if (i == m) {                               // discs' downgoing density, above this interface
+      b[(size_t)rv * 3 + 2] -= 1.0 / gi;
+      b[(size_t)rd * 3 + 2] -= 1.0;
+    }
+  }
+  if (!solve_small(a, n, b, 3)) b.assign((size_t)n * 3, cplx(NAN, NAN));
+  const int rows[4] = {0, col(m, 1), col(m, -1), n - 1};
+  for (int u = 0; u < 4; ++u)
+    for (int s = 0; s < 3; ++s) r[u][s] = b[(size_t)rows[u] * 3 + s];
+}
+
+void build_node_tables(lsms_ctx* c) {
+  NodeTables& t = c->nodes;
+  const int ns = c->ns, p = c->p, P = c->P;
+  const int L = (int)c->ks.size(), m = c->layer;
+  t.g1.resize(ns); t.g2.resize(ns); t.g3.resize(ns);
+  t.refl.resize(4 * ns); t.inc.resize(2 * ns); t.field.resize(4 * ns);
+  t.fagg.assign(2 * (size_t)ns * P, cplx(0, 0));
+  t.udis.assign(2 * (size_t)ns * P, cplx(0, 0));
+  std::vector<cplx> g;
+  cplx r[4][3];
   for (int v = 0; v < ns; ++v) {
     const cplx lam = t.lam[v], w = t.wt[v];
-    for (int j = 1; j <= L; ++j) g[j - 1] = c->kc[j - 1].imag() == 0.0 ? gamma_of(lam, c->ks[j - 1]) : gamma_of(lam, c->kc[j - 1]);
-    for (int j = 2; j < L; ++j) E[j] = std::exp(-g[j - 1] * c->ds[j - 2]);
+    layer_response(c, lam, g, r);
     const cplx g1 = g[0], g2 = g[m - 1];
     t.g1[v] = g1; t.g2[v] = g2; t.g3[v] = g[L - 1];
-    a.assign((size_t)n * n, cplx(0, 0));
-    b.assign((size_t)n * 3, cplx(0, 0));       // right-hand sides: unit I, P, Q
-    for (int i = 1; i < L; ++i) {               // interface i: layer i above, i + 1 below
-      const int rv = 2 * (i - 1), rd = rv + 1;
-      const cplx gi = g[i - 1], gb = g[i];
-      if (i == 1) {
-        a[(size_t)rv * n + col(1, 1)] += 1.0 / gi;
-        a[(size_t)rd * n + col(1, 1)] += -1.0;
-      } else {
-        a[(size_t)rv * n + col(i, 1)] += E[i] / gi;
-        a[(size_t)rv * n + col(i, -1)] += 1.0 / gi;
-        a[(size_t)rd * n + col(i, 1)] += E[i];
-        a[(size_t)rd * n + col(i, -1)] += -1.0;
-      }
-      if (i + 1 == L) {
-        a[(size_t)rv * n + col(L, 1)] -= 1.0 / gb;
-        a[(size_t)rd * n + col(L, 1)] -= 1.0;
-      } else {
-        a[(size_t)rv * n + col(i + 1, 1)] -= 1.0 / gb;
-        a[(size_t)rv * n + col(i + 1, -1)] -= E[i + 1] / gb;
-        a[(size_t)rd * n + col(i + 1, 1)] -= 1.0;
-        a[(size_t)rd * n + col(i + 1, -1)] += E[i + 1];
-      }
-      if (i == 1) {                             // incident wave, above interface 1
-        b[(size_t)rv * 3 + 0] -= 1.0 / gi;
-        b[(size_t)rd * 3 + 0] -= 1.0;
-      }
-      if (i == m - 1) {                         // discs' upgoing density, below this interface
-        b[(size_t)rv * 3 + 1] += 1.0 / gb;
-        b[(size_t)rd * 3 + 1] += -1.0;
-      }
-      if (i == m) {                             // discs' downgoing density, above this interface
-        b[(size_t)rv * 3 + 2] -= 1.0 / gi;
-        b[(size_t)rd * 3 + 2] -= 1.0;
-      }
-    }
-    if (!solve_small(a, n, b, 3)) b.assign((size_t)n * 3, cplx(NAN, NAN));
-    const int up = col(m, 1), dn = col(m, -1);
-    t.refl[4 * v + 0] = b[(size_t)up * 3 + 1];
-    t.refl[4 * v + 1] = b[(size_t)up * 3 + 2];
-    t.refl[4 * v + 2] = b[(size_t)dn * 3 + 1];
-    t.refl[4 * v + 3] = b[(size_t)dn * 3 + 2];
-    t.inc[2 * v + 0] = b[(size_t)up * 3 + 0];
-    t.inc[2 * v + 1] = b[(size_t)dn * 3 + 0];
-    t.field[4 * v + 0] = b[0];
-    t.field[4 * v + 1] = b[1];
-    t.field[4 * v + 2] = b[2];
+    t.refl[4 * v + 0] = r[1][1];
+    t.refl[4 * v + 1] = r[1][2];
+    t.refl[4 * v + 2] = r[2][1];
+    t.refl[4 * v + 3] = r[2][2];
+    t.inc[2 * v + 0] = r[1][0];
+    t.inc[2 * v + 1] = r[2][0];
+    t.field[4 * v + 0] = r[0][0];
+    t.field[4 * v + 1] = r[0][1];
+    t.field[4 * v + 2] = r[0][2];
     t.field[4 * v + 3] = w / (4.0 * kPi * g1);
     const cplx wm = (lam - g2) / c->k2, wp = (lam + g2) / c->k2;
     const cplx q = w / (4.0 * kPi * g2);

@@ -186,6 +186,8 @@ std::vector<double> hankel_scale(int p, double k2, double R);
 cplx gamma_of(cplx lam, double k);
 cplx gamma_of(cplx lam, cplx k);
 void build_node_tables(lsms_ctx* c);
+// the interface system of one node for unit I, P, Q (rows sigma_1, s_m^+, s_m^-, sigma_L)
+void layer_response(const lsms_ctx* c, cplx lam, std::vector<cplx>& g, cplx r[4][3]);
 int validate_geometry(const lsms_ctx* c, int n, const double* xy, std::string& err);
 
 // ------------------------------------------------------------------------------------------

@@ -26,7 +26,7 @@ APPLY_SCALED, APPLY_MIXED, APPLY_NO_TRANSLATION, APPLY_NO_REFLECTION, APPLY_ALPH
 FIELD_TOTAL, FIELD_SCATTERED, FIELD_PARTICLE = 0, 1, 2
 STATUS = {0: "OK", -1: "ARG", -2: "GEOMETRY", -3: "NOT_CONVERGED", -4: "NONFINITE", -5: "OOM",
           -6: "CUDA", -7: "STATE"}
-EXPORTS = ["lsms_create", "lsms_build_contour_stack", "lsms_fma_probe", "lsms_pec_scattering_diagonal", "lsms_set_fmm", "lsms_get_fmm", "lsms_fmm_stats", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
+EXPORTS = ["lsms_create", "lsms_layer_response", "lsms_build_contour_stack", "lsms_fma_probe", "lsms_pec_scattering_diagonal", "lsms_set_fmm", "lsms_get_fmm", "lsms_fmm_stats", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
            "lsms_get_scattering_matrix", "lsms_inclusion_scattering_matrix", "lsms_set_particles", "lsms_apply", "lsms_apply_ex", "lsms_apply_dev",
            "lsms_translate", "lsms_aggregate", "lsms_reflect", "lsms_disaggregate", "lsms_incident",
            "lsms_get_contour", "lsms_get_scattering", "lsms_num_nodes", "lsms_num_particles",
@@ -99,6 +99,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsms_destroy": (None, [_P]),
         "lsms_build_contour": (i, [ctypes.POINTER(Contour), d, d, d, _D, _D]),
         "lsms_build_contour_stack": (i, [ctypes.POINTER(Contour), i, _D, _D, _D]),
+        "lsms_layer_response": (i, [i, _D, _D, i, i, _D, _D]),
         "lsms_scattering_diagonal": (i, [i, d, d, d, _D]),
         "lsms_check_geometry": (i, [d, d, i, _D]),
         "lsms_set_timing": (i, [_P, i]),
@@ -379,6 +380,20 @@ def build_contour_stack(n_nodes, ks, b=0.0, t_max=0.0, panel_order=0):
     if rc != 0:
         raise LsmsError(rc, lib.lsms_last_error(None).decode())
     return lam, wt
+
+
+def layer_response(ks, thicknesses, particle_layer, lam) -> np.ndarray:
+    """Host-only: (n, 4, 3) complex, rows sigma_1, s_m^+, s_m^-, sigma_L for unit I, P, Q."""
+    lib = load()
+    k = np.ascontiguousarray(np.asarray(ks, dtype=np.complex128))
+    ds = np.ascontiguousarray(thicknesses, dtype=np.float64)
+    lm = np.ascontiguousarray(np.asarray(lam, dtype=np.complex128).ravel())
+    out = np.zeros((lm.size, 4, 3), dtype=np.complex128)
+    rc = lib.lsms_layer_response(int(k.size), _dptr(k), _dptr(ds), int(particle_layer), int(lm.size), _dptr(lm),
+                                 _dptr(out))
+    if rc != 0:
+        raise LsmsError(rc, lib.lsms_last_error(None).decode())
+    return out
 
 
 def scattering_diagonal(p, k2, kp, radius):

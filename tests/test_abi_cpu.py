@@ -13,6 +13,7 @@ from oracle import lsms_oracle as O
 from paper_1407_3868_gb300 import inputs
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+MED_K = (inputs.MEDIUM["k1"], inputs.MEDIUM["k2"], inputs.MEDIUM["k3"])
 
 
 @pytest.fixture(scope="module")
@@ -216,3 +217,24 @@ def test_library_stack_contour_equals_oracle_contour(lib, ks, b, n_nodes, t_max)
     assert np.max(np.abs(wt - wt_o)) <= 1e-14 * t_max
     with pytest.raises(lib.LsmsError):
         lib.build_contour_stack(n_nodes, ks[:2], b, t_max, 16)
+
+
+@pytest.mark.parametrize("ks,ds,m", [
+    ([MED_K[0], MED_K[1], MED_K[2]], [2.0], 2),                                      # the bench medium
+    (inputs.STACK5["ks"], inputs.STACK5["ds"], 3),                                   # five layers
+    ([2 * math.pi, 3 * math.pi, 3.4 * math.pi + 0.5j, 4 * math.pi], [2.0, 0.7], 2),  # absorbing film
+    ([1.0, 3.0, 1.0], [32.0], 2),                                                    # Example 1 (guided)
+])
+def test_library_layer_response_equals_oracle(lib, ks, ds, m):
+    # the per-node interface solve every context precomputes (host only) against the oracle's Stack
+    lam, _ = O.contour(256, complex(ks[0]).real, complex(ks[m - 1]).real, complex(ks[-1]).real, 0.2, 40.0,
+                       branch_points=[complex(k).real for k in ks])
+    lam = lam[::7]
+    r = lib.layer_response(ks, ds, m, lam)
+    st = O.Stack(ks, ds, m, 2.4 * math.pi, 0.25)
+    one = np.ones(lam.size, dtype=complex)
+    zero = np.zeros(lam.size, dtype=complex)
+    for s, (inc, pp, qm) in enumerate(((one, zero, zero), (zero, one, zero), (zero, zero, one))):
+        o = st.solve_layers(lam, inc=inc, p_plus=pp, q_minus=qm)           # (sigma_1, s+, s-, sigma_L)
+        scale = np.abs(o).max(axis=1, keepdims=True) + 1e-300
+        assert np.max(np.abs(r[:, :, s] - o) / scale) < 1e-11, s
