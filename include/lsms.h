@@ -325,7 +325,9 @@ int lsms_pec_scattering_diagonal(int p, double k2, double radius, double* s_diag
  *   are translated directly; farther pairs through box expansions of order `order`: Graf shifts
  *   disc -> box (H -> H) and box -> disc (J -> J), and Lemma 3.1 between boxes two or more apart,
  *   evaluated for all boxes at once as a convolution over (box offset, order difference) with
- *   cuFFT.  FP64 throughout; used by lsms_apply*, lsms_translate and lsms_solve in both precisions.
+ *   cuFFT.  Used by lsms_apply*, lsms_translate and lsms_solve in both precisions (FP32 shifts,
+ *   convolution and near field in mixed precision, FP64 otherwise), in place of the all-pairs and
+ *   the tensor-core block translations.
  *   order = 0: ceil(k2 r_box) + 32 with r_box = hypot(box_width, d) / 2 (about 1e-12 relative
  *   in the scaled norm).  box_width <= 0 turns it off (all-pairs translation).  box_width must be
  *   at least the disc layer's thickness d (boxes two apart are then well separated); order in

@@ -153,13 +153,13 @@ def test_layer_stack_arguments_are_validated_before_any_device_work(lib):
     assert e.value.code == -6
 
 
-@pytest.mark.parametrize("p,n_pts,shape,kp", [(10, 256, (0.15, 0.05, 5), 2.4 * math.pi),
-                                              (14, 128, (0.2, 0.0, 0), 2.4 * math.pi),
-                                              (8, 96, (0.12, 0.04, 3), 2.0 * math.pi)])
-def test_library_inclusion_matrix_equals_oracle(lib, p, n_pts, shape, kp):
+@pytest.mark.parametrize("p,n_pts,shape,kp,k2", [(10, 256, (0.15, 0.05, 5), 2.4 * math.pi, MED_K[1]),
+                                                 (14, 128, (0.2, 0.0, 0), 2.4 * math.pi, MED_K[1]),
+                                                 (8, 96, (0.12, 0.04, 3), 2.0 * math.pi, MED_K[1]),
+                                                 (10, 256, (0.12, 0.04, 3), 2.0, 20.0)])   # Example 2's contrast
+def test_library_inclusion_matrix_equals_oracle(lib, p, n_pts, shape, kp, k2):
     # host-only helper (Sec. 4): the library's Nystrom solve against the oracle's
     from oracle import lsms_oracle as O
-    k2 = inputs.MEDIUM["k2"]
     cur = inputs.star_curve(*shape, n_pts, rotation=0.3)
     s_lib = lib.inclusion_scattering_matrix(p, k2, kp, 0.25, cur)
     s_o = O.inclusion_scattering_matrix(cur, p, k2, kp)
