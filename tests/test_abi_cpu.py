@@ -238,3 +238,22 @@ def test_library_layer_response_equals_oracle(lib, ks, ds, m):
         o = st.solve_layers(lam, inc=inc, p_plus=pp, q_minus=qm)           # (sigma_1, s+, s-, sigma_L)
         scale = np.abs(o).max(axis=1, keepdims=True) + 1e-300
         assert np.max(np.abs(r[:, :, s] - o) / scale) < 1e-11, s
+
+
+def test_library_contour_equals_oracle_contour_on_random_stacks(lib):
+    # both panel rules (graded; greedy in guided-mode media), random stacks of 3-5 layers, random
+    # offsets, lengths and node counts (including budgets too small for every branch point)
+    rng = np.random.default_rng(2024)
+    guided = 0
+    for _ in range(60):
+        L = int(rng.integers(3, 6))
+        ks = list(rng.uniform(0.5, 25.0, L))
+        b = float(rng.uniform(0.01, 0.4))
+        t_max = float(max(ks) + rng.uniform(5.0, 80.0))
+        n_nodes = int(rng.integers(64, 3000))
+        guided += O.guided_band(ks) is not None
+        lam, wt = lib.build_contour_stack(n_nodes, ks, b, t_max, 16)
+        lam_o, wt_o = O.contour(n_nodes, ks[0], ks[1], ks[-1], b, t_max, branch_points=ks)
+        assert np.max(np.abs(lam - lam_o)) <= 1e-12 * t_max, (ks, b, t_max, n_nodes)
+        assert np.max(np.abs(wt - wt_o)) <= 1e-14 * t_max, (ks, b, t_max, n_nodes)
+    assert 10 < guided < 60                      # both rules exercised
