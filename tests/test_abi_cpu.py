@@ -284,3 +284,20 @@ def test_library_layer_response_on_random_stacks(lib):
             # library 7.6e-15, LAPACK in the oracle 3.5e-13 — so there the check is absolute, ~1e-12
             scale = np.maximum(np.abs(o).max(axis=1, keepdims=True), 1e-2 * np.abs(o).max())
             assert np.max(np.abs(r[:, :, s] - o) / scale) < 1e-10, (ks, ds, m, s)
+
+
+def test_library_inclusion_matrix_on_random_shapes(lib):
+    # random star-shaped inclusions (lobes, amplitude, rotation, offset from the enclosing disc's
+    # centre) and contrasts: the library's Nystrom solve against the oracle's
+    rng = np.random.default_rng(11)
+    for _ in range(4):
+        a1 = float(rng.uniform(0.08, 0.15))
+        a2 = float(rng.uniform(0.0, 0.4 * a1))
+        a3 = int(rng.integers(2, 7))
+        off = rng.uniform(-0.03, 0.03, 2)
+        k2, kp = float(rng.uniform(2.0, 12.0)), float(rng.uniform(1.0, 15.0))
+        p = int(rng.integers(4, 12))
+        cur = inputs.star_curve(a1, a2, a3, 128, rotation=float(rng.uniform(0, 6.3)), centre=off)
+        s_lib = lib.inclusion_scattering_matrix(p, k2, kp, 0.25, cur)
+        s_o = O.inclusion_scattering_matrix(cur, p, k2, kp)
+        assert np.abs(s_lib - s_o).max() < 1e-12 * np.abs(s_o).max(), (a1, a2, a3, k2, kp, p)
