@@ -497,14 +497,15 @@ class Medium:
     def __init__(self, k1, k2, k3, d, kp, radius):
         self.k1, self.k2, self.k3, self.d, self.kp, self.radius = k1, k2, k3, d, kp, radius
 
-    def a_lambda(self, lam) -> np.ndarray:
+    def a_lambda(self, lam, g=None) -> np.ndarray:
         """A_lambda of Eq. "sommerfeldsys" for every node: shape (N_S, 4, 4).
 
         Unknowns (sigma_1, sigma_2^+, sigma_2^-, sigma_3); rows: [u] = 0 at y = 0, [u] = 0 at
-        y = -d, [du/dy] = 0 at y = 0, [du/dy] = 0 at y = -d (Eqs. "cont1", "cont2").
+        y = -d, [du/dy] = 0 at y = 0, [du/dy] = 0 at y = -d (Eqs. "cont1", "cont2").  g: the
+        vertical wavenumbers (gamma_1, gamma_2, gamma_3) to use instead of `gamma` (another branch).
         """
         lam = np.atleast_1d(lam)
-        g1, g2, g3 = gamma(lam, self.k1), gamma(lam, self.k2), gamma(lam, self.k3)
+        g1, g2, g3 = g if g is not None else (gamma(lam, self.k1), gamma(lam, self.k2), gamma(lam, self.k3))
         e = np.exp(-g2 * self.d)
         a = np.zeros((lam.size, 4, 4), dtype=complex)
         a[:, 0, 0] = 1.0 / g1
@@ -521,12 +522,13 @@ class Medium:
         a[:, 3, 3] = -1.0
         return a
 
-    def incident_density(self, lam, src) -> np.ndarray:
+    def incident_density(self, lam, src, g1=None) -> np.ndarray:
         """I(lambda) = exp(-gamma_1 y0 - i lambda x0): the line source's plane-wave amplitude at
         y = 0 (Eq. "sommer" with y < y0; the exp(-i lambda x0) phase is kept in the density)."""
-        return np.exp(-gamma(lam, self.k1) * src[1] - 1j * lam * src[0])
+        g1 = gamma(lam, self.k1) if g1 is None else g1
+        return np.exp(-g1 * src[1] - 1j * lam * src[0])
 
-    def rhs(self, lam, inc=None, p_plus=None, q_minus=None) -> np.ndarray:
+    def rhs(self, lam, inc=None, p_plus=None, q_minus=None, g=None) -> np.ndarray:
         """Right-hand side of A_lambda sigma for the incident density I and the particle sums.
 
         Incident: (-I/gamma_1, 0, I, 0) (Eq. "sommerfeldsys").  Particles: their field near the
@@ -535,7 +537,7 @@ class Medium:
         terms of [u] and [du/dy] to the right gives (P^+/gamma_2, -Q^-/gamma_2, P^+, -Q^-).
         """
         lam = np.atleast_1d(lam)
-        g1, g2 = gamma(lam, self.k1), gamma(lam, self.k2)
+        g1, g2 = (g[0], g[1]) if g is not None else (gamma(lam, self.k1), gamma(lam, self.k2))
         r = np.zeros((lam.size, 4), dtype=complex)
         if inc is not None:
             r[:, 0] += -inc / g1
@@ -548,11 +550,38 @@ class Medium:
             r[:, 3] += -q_minus
         return r
 
-    def solve_layers(self, lam, inc=None, p_plus=None, q_minus=None) -> np.ndarray:
+    def solve_layers(self, lam, inc=None, p_plus=None, q_minus=None, g=None) -> np.ndarray:
         """sigma = A_lambda^{-1} rhs at every node (LAPACK LU); shape (N_S, 4)."""
-        a = self.a_lambda(lam)
-        r = self.rhs(lam, inc, p_plus, q_minus)
+        a = self.a_lambda(lam, g)
+        r = self.rhs(lam, inc, p_plus, q_minus, g)
         return np.linalg.solve(a, r[..., None])[..., 0]
+
+    def guided_poles(self, n_scan: int = 40001) -> list:
+        """Real poles lambda_g of the layer response in (max(k1, k3), k2): the guided modes of a
+        lossless layer (zeros of det A_lambda; on the real axis det A = c(lambda) f(lambda) with a
+        slowly turning phase c, so sign changes of its real or imaginary part are bracketed on a
+        fine grid and refined by Brent's method, keeping those where |det A| vanishes)."""
+        from scipy import optimize
+
+        lo, hi = max(self.k1, self.k3), self.k2
+        if not hi > lo:
+            return []
+        det = lambda x: np.linalg.det(self.a_lambda(np.array([complex(x)]))[0])
+        xs = np.linspace(lo + 1e-9, hi - 1e-9, n_scan)
+        vals = np.array([det(x) for x in xs])
+        ref = np.abs(vals).mean()
+        poles = []
+        for i in range(n_scan - 1):
+            for part in (np.real, np.imag):
+                if np.sign(part(vals[i])) != np.sign(part(vals[i + 1])):
+                    r = optimize.brentq(lambda x: part(det(x)), xs[i], xs[i + 1], xtol=1e-15, rtol=1e-15)
+                    if abs(det(r)) < 1e-8 * ref:
+                        poles.append(r)
+        out = []
+        for r in sorted(poles):
+            if not out or r - out[-1] > 1e-9:
+                out.append(r)
+        return out
 
 
 class Stack:
@@ -979,6 +1008,57 @@ class Problem:
         down = sum(integrate.quad(f, a, b, epsabs=tol, epsrel=tol, limit=4000)[0]
                    for a, b in zip(pts[:-1], pts[1:])) / (2.0 * FOUR_PI)
         return pieces(k1, 1), down
+
+
+def guided_power(pr: "Problem", src, beta, n_circle: int = 128):
+    """Time-averaged power the guided modes carry to x = +inf and x = -inf (three-layer medium).
+
+    For x -> +inf the Sommerfeld integrals close upward around the poles +lambda_g (the contour
+    passes below them), so the field tends to (i/2) sum_g R_g(y) e^{i lambda_g x}, R_g the residue
+    of the integrand: sigma_1 e^{-gamma_1 y}/gamma_1 above, (sigma_2^+ e^{gamma_2 y} +
+    sigma_2^- e^{-gamma_2 (y + d)})/gamma_2 in the layer, sigma_3 e^{gamma_3 (y + d)}/gamma_3
+    below (the discs' own H-expansions have no poles); likewise -lambda_g for x -> -inf.  The flux
+    Im int conj(u) du/dx dy of a mode is (lambda_g / 4) int |R_g|^2 dy.  Residues come from the
+    trapezoidal rule on a circle around the pole, with gamma_j continued from the contour
+    (sqrt(lambda^2 - k_j^2) for k_j < lambda_g, where the principal -i sqrt(k^2 - lambda^2) has
+    its cut); the mode integrals are exact exponentials outside the layer, Gauss-Legendre inside.
+    Returns (power to +inf, power to -inf)."""
+    m = pr.m
+    poles = m.guided_poles()
+    ks = (m.k1, m.k2, m.k3)
+
+    def gcont(lam, k, lg):
+        lam = np.asarray(lam, dtype=complex)
+        return np.sqrt(lam * lam - k * k) if k < abs(lg) else gamma(lam, k)
+
+    def dens(lam, lg):
+        g = tuple(gcont(lam, k, lg) for k in ks)
+        inc = m.incident_density(lam, src, g[0])
+        if pr.N and beta is not None:
+            sub = Problem(m, pr.p, pr.c, lam, np.zeros_like(lam))
+            p_plus, q_minus = sub.aggregate(np.asarray(beta).reshape(pr.N, pr.P))
+        else:
+            p_plus = q_minus = None
+        return m.solve_layers(lam, inc, p_plus, q_minus, g)
+
+    xg, wg = np.polynomial.legendre.leggauss(64)
+    y = -m.d / 2 + m.d / 2 * xg
+    total = [0.0, 0.0]
+    for side, sgn in ((0, 1.0), (1, -1.0)):
+        for pg in poles:
+            lg = sgn * pg
+            others = [k for k in ks] + [q for q in poles if q != pg]
+            rho = min(abs(pg - q) for q in others) / 3.0
+            th = 2.0 * np.pi * np.arange(n_circle) / n_circle
+            z = lg + rho * np.exp(1j * th)
+            res = (rho / n_circle) * (dens(z, lg) * np.exp(1j * th)[:, None]).sum(axis=0)
+            l = np.array([lg], dtype=complex)
+            g1, g2, g3 = (gcont(l, k, lg)[0] for k in ks)
+            c1, c2p, c2m, c3 = res[0] / g1, res[1] / g2, res[2] / g2, res[3] / g3
+            inner = np.sum(wg * m.d / 2 * np.abs(c2p * np.exp(g2 * y) + c2m * np.exp(-g2 * (y + m.d))) ** 2)
+            integral = abs(c1) ** 2 / (2.0 * g1.real) + abs(c3) ** 2 / (2.0 * g3.real) + inner
+            total[side] += pg / 4.0 * integral
+    return total[0], total[1]
 
 
 def gmres(matvec, b, tol=1e-12, maxiter=500):

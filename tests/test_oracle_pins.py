@@ -695,3 +695,28 @@ def test_energy_balance_with_an_absorbing_substrate(loss):
     u_s = pr.field_layer1(src, beta, src[None, :], "scattered")[0]
     assert up > 0 and down > 0
     assert abs(up + down - (0.25 + u_s.imag)) < 1e-9 * 0.25
+
+
+@pytest.mark.parametrize("with_discs", [False, True])
+def test_energy_balance_in_a_guided_medium(with_discs):
+    # k2 above both half-spaces: the source's power 1/4 + Im u^s(x0) (from the contour, which passes
+    # a distance b from the guided poles) leaves through y = +-inf (real-axis densities) and along
+    # the layer in its guided modes (residues at the real poles)
+    k1, k2, k3, d = 1.0, 3.0, 1.5, 1.0
+    m = O.Medium(k1, k2, k3, d, 2.0, 0.1)
+    assert len(m.guided_poles()) == 1
+    src = np.array([0.3, 0.5])
+    c = np.array([[0.1, -0.3], [-0.5, -0.7], [0.6, -0.55]]) if with_discs else np.zeros((0, 2))
+    lam, wt = O.contour(2048, k1, k2, k3, 0.2, 33.0)
+    pr = O.Problem(m, 4, c, lam, wt)
+    beta = pr.solve_dense(src) if with_discs else None
+    up, down = pr.outgoing_power(src, beta)
+    right, left = O.guided_power(pr, src, beta)
+    u_s = pr.field_layer1(src, beta, src[None, :], "scattered")[0]
+    total = 0.25 + u_s.imag
+    assert right > 1e-4 and left > 1e-4
+    if not with_discs:
+        assert abs(right - left) < 1e-12 * right           # symmetric about the source
+    assert abs(up + down + right + left - total) < 1e-10 * total
+    # the guided modes are needed: without them the balance misses by their share
+    assert abs(up + down - total) > 1e-3 * total
