@@ -720,3 +720,18 @@ def test_energy_balance_in_a_guided_medium(with_discs):
     assert abs(up + down + right + left - total) < 1e-10 * total
     # the guided modes are needed: without them the balance misses by their share
     assert abs(up + down - total) > 1e-3 * total
+
+
+def test_energy_balance_with_many_guided_modes():
+    # Sec. 6 Example 1's medium (k = (1, 3, 1), a layer 32 thick): 29 guided modes, the last one
+    # 0.0015 below k2; radiation plus the modes' power equals the source's power
+    e = inputs.EXAMPLE1
+    m = O.Medium(e["k1"], e["k2"], e["k3"], e["d"], e["kp"], e["radius"])
+    assert len(m.guided_poles()) == 29
+    src = np.array([0.0, 1.0])
+    lam, wt = O.contour(2048, e["k1"], e["k2"], e["k3"], 0.2, 33.0)
+    pr = O.Problem(m, 4, np.zeros((0, 2)), lam, wt)
+    up, down = pr.outgoing_power(src, None)
+    right, left = O.guided_power(pr, src, None)
+    total = 0.25 + pr.field_layer1(src, None, src[None, :], "scattered")[0].imag
+    assert abs(up + down + right + left - total) < 1e-10 * total
