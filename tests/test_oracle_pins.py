@@ -735,3 +735,19 @@ def test_energy_balance_with_many_guided_modes():
     right, left = O.guided_power(pr, src, None)
     total = 0.25 + pr.field_layer1(src, None, src[None, :], "scattered")[0].imag
     assert abs(up + down + right + left - total) < 1e-10 * total
+
+
+def test_energy_balance_with_rotated_inclusions():
+    # lossless five-lobed inclusions (dense scattering matrices, each turned by its own angle) in the
+    # three-layer medium: the power through y = +-inf equals the source's power
+    s = inputs.STAR5
+    m = medium()
+    S = O.inclusion_scattering_matrix(inputs.star_curve(s["a1"], s["a2"], s["a3"], 128), 6, m.k2, m.kp)
+    c = np.array([[0.2, -0.7], [-0.6, -1.3], [0.9, -1.0]])
+    src = np.array([0.3, 1.0])
+    lam, wt = O.contour(1024, m.k1, m.k2, m.k3, 0.2, 120.0)
+    pr = O.Problem(m, 6, c, lam, wt, smat=S, theta=np.array([0.3, 1.7, 4.0]))
+    beta = pr.solve_dense(src)
+    up, down = pr.outgoing_power(src, beta)
+    u_s = pr.field_layer1(src, beta, src[None, :], "scattered")[0]
+    assert abs(up + down - (0.25 + u_s.imag)) < 1e-9 * 0.25
