@@ -558,30 +558,39 @@ class Medium:
 
     def guided_poles(self, n_scan: int = 40001) -> list:
         """Real poles lambda_g of the layer response in (max(k1, k3), k2): the guided modes of a
-        lossless layer (zeros of det A_lambda; on the real axis det A = c(lambda) f(lambda) with a
-        slowly turning phase c, so sign changes of its real or imaginary part are bracketed on a
-        fine grid and refined by Brent's method, keeping those where |det A| vanishes)."""
-        from scipy import optimize
-
-        lo, hi = max(self.k1, self.k3), self.k2
-        if not hi > lo:
+        lossless layer (zeros of det A_lambda)."""
+        band = guided_band((self.k1, self.k2, self.k3))
+        if band is None:
             return []
-        det = lambda x: np.linalg.det(self.a_lambda(np.array([complex(x)]))[0])
-        xs = np.linspace(lo + 1e-9, hi - 1e-9, n_scan)
-        vals = np.array([det(x) for x in xs])
-        ref = np.abs(vals).mean()
-        poles = []
-        for i in range(n_scan - 1):
-            for part in (np.real, np.imag):
-                if np.sign(part(vals[i])) != np.sign(part(vals[i + 1])):
-                    r = optimize.brentq(lambda x: part(det(x)), xs[i], xs[i + 1], xtol=1e-15, rtol=1e-15)
-                    if abs(det(r)) < 1e-8 * ref:
-                        poles.append(r)
-        out = []
-        for r in sorted(poles):
-            if not out or r - out[-1] > 1e-9:
-                out.append(r)
-        return out
+        return real_zeros(lambda x: np.linalg.det(self.a_lambda(np.array([complex(x)]))[0]), *band, n_scan)
+
+
+def real_zeros(det, lo: float, hi: float, n_scan: int = 40001) -> list:
+    """Zeros of det(lambda) on the open interval (lo, hi) of the real axis.  On the real axis a
+    layer system's determinant is c(lambda) f(lambda) with a slowly turning phase c, so sign changes
+    of its real or imaginary part are bracketed on a fine grid and refined by Brent's method,
+    keeping those where |det| vanishes against the grid's median (a sign change through a pole of
+    det, where an interior layer's gamma passes through 0, is dropped by that test)."""
+    from scipy import optimize
+
+    xs = np.linspace(lo + 1e-9, hi - 1e-9, n_scan)
+    vals = np.array([det(x) for x in xs])
+    ok = np.isfinite(vals)
+    ref = np.median(np.abs(vals[ok]))
+    zeros = []
+    for i in range(n_scan - 1):
+        if not (ok[i] and ok[i + 1]):
+            continue
+        for part in (np.real, np.imag):
+            if np.sign(part(vals[i])) != np.sign(part(vals[i + 1])):
+                r = optimize.brentq(lambda x: part(det(x)), xs[i], xs[i + 1], xtol=1e-15, rtol=1e-15)
+                if abs(det(r)) < 1e-8 * ref:
+                    zeros.append(r)
+    out = []
+    for r in sorted(zeros):
+        if not out or r - out[-1] > 1e-9:
+            out.append(r)
+    return out
 
 
 class Stack:
@@ -611,59 +620,94 @@ class Stack:
         self.depth = sum(self.ds[: self.mi - 2])        # from y = 0 down to the top of layer m
         self.kp, self.radius = kp, radius
 
-    def incident_density(self, lam, src) -> np.ndarray:
-        return np.exp(-gamma(lam, self.k1) * src[1] - 1j * lam * src[0])
+    def incident_density(self, lam, src, g1=None) -> np.ndarray:
+        g1 = gamma(lam, self.k1) if g1 is None else g1
+        return np.exp(-g1 * src[1] - 1j * lam * src[0])
 
-    def solve_layers(self, lam, inc=None, p_plus=None, q_minus=None) -> np.ndarray:
+    def interfaces(self):
+        """z_1 = 0, z_i = z_{i-1} - d_i: the interface heights (L - 1 values)."""
+        z = [0.0]
+        for dd in self.ds:
+            z.append(z[-1] - dd)
+        return z
+
+    def _col(self, j, sign):
+        """Unknown index of layer j (1-based): sigma_1, (s_2^+, s_2^-), ..., sigma_L."""
+        n = 2 * self.L - 2
+        if j == 1:
+            return 0
+        if j == self.L:
+            return n - 1
+        return 1 + 2 * (j - 2) + (0 if sign > 0 else 1)
+
+    def _assemble(self, gv, inc=None, p_plus=None, q_minus=None):
+        """The interface system of one node: [u] = [du/dy] = 0 at every interface, for the vertical
+        wavenumbers gv[j - 1] of layer j and the known densities (scalars or None)."""
+        L, m, col = self.L, self.mi, self._col
+        n = 2 * L - 2
+        E = {j: np.exp(-gv[j - 1] * self.ds[j - 2]) for j in range(2, L)}
+        a = np.zeros((n, n), dtype=complex)
+        r = np.zeros(n, dtype=complex)
+        for i in range(1, L):                                    # interface i: layer i above, i + 1 below
+            rv, rd = 2 * (i - 1), 2 * (i - 1) + 1
+            gi, gb = gv[i - 1], gv[i]
+            if i == 1:                                           # layer above: value, derivative
+                a[rv, col(1, 1)] += 1.0 / gi
+                a[rd, col(1, 1)] += -1.0
+            else:
+                a[rv, col(i, 1)] += E[i] / gi
+                a[rv, col(i, -1)] += 1.0 / gi
+                a[rd, col(i, 1)] += E[i]
+                a[rd, col(i, -1)] += -1.0
+            if i + 1 == L:                                       # layer below (subtracted)
+                a[rv, col(L, 1)] -= 1.0 / gb
+                a[rd, col(L, 1)] -= 1.0
+            else:
+                a[rv, col(i + 1, 1)] -= 1.0 / gb
+                a[rv, col(i + 1, -1)] -= E[i + 1] / gb
+                a[rd, col(i + 1, 1)] -= 1.0
+                a[rd, col(i + 1, -1)] -= -E[i + 1]
+            # known fields: rhs = (below) - (above)
+            if i == 1 and inc is not None:                       # incident wave in layer 1
+                r[rv] -= inc / gi
+                r[rd] -= inc
+            if i == m - 1 and p_plus is not None:                # discs, below this interface
+                r[rv] += p_plus / gb
+                r[rd] += -p_plus
+            if i == m and q_minus is not None:                   # discs, above this interface
+                r[rv] -= q_minus / gi
+                r[rd] -= q_minus
+        return a, r
+
+    def solve_layers(self, lam, inc=None, p_plus=None, q_minus=None, g=None, full=False) -> np.ndarray:
+        """(sigma_1, s_m^+, s_m^-, sigma_L) per node, or with full=True every unknown (sigma_1,
+        s_2^+, s_2^-, ..., sigma_L).  g: the vertical wavenumbers of every layer to use instead of
+        `gamma` (another branch)."""
         lam = np.atleast_1d(np.asarray(lam, dtype=complex))
         L, m = self.L, self.mi
         n = 2 * L - 2
-        g = [gamma(lam, k) for k in self.ks]                    # g[j - 1] for layer j
-        E = {j: np.exp(-g[j - 1] * self.ds[j - 2]) for j in range(2, L)}
-
-        def col(j, sign):                                        # unknown index of layer j
-            if j == 1:
-                return 0
-            if j == L:
-                return n - 1
-            return 1 + 2 * (j - 2) + (0 if sign > 0 else 1)
-
-        out = np.zeros((lam.size, 4), dtype=complex)
+        g = [gamma(lam, k) for k in self.ks] if g is None else list(g)    # g[j - 1] for layer j
+        out = np.zeros((lam.size, n if full else 4), dtype=complex)
+        pick = lambda arr, v: None if arr is None else arr[v]
         for v in range(lam.size):
-            a = np.zeros((n, n), dtype=complex)
-            r = np.zeros(n, dtype=complex)
-            for i in range(1, L):                                # interface i: layer i above, i + 1 below
-                rv, rd = 2 * (i - 1), 2 * (i - 1) + 1
-                gi, gb = g[i - 1][v], g[i][v]
-                if i == 1:                                       # layer above: value, derivative
-                    a[rv, col(1, 1)] += 1.0 / gi
-                    a[rd, col(1, 1)] += -1.0
-                else:
-                    a[rv, col(i, 1)] += E[i][v] / gi
-                    a[rv, col(i, -1)] += 1.0 / gi
-                    a[rd, col(i, 1)] += E[i][v]
-                    a[rd, col(i, -1)] += -1.0
-                if i + 1 == L:                                   # layer below (subtracted)
-                    a[rv, col(L, 1)] -= 1.0 / gb
-                    a[rd, col(L, 1)] -= 1.0
-                else:
-                    a[rv, col(i + 1, 1)] -= 1.0 / gb
-                    a[rv, col(i + 1, -1)] -= E[i + 1][v] / gb
-                    a[rd, col(i + 1, 1)] -= 1.0
-                    a[rd, col(i + 1, -1)] -= -E[i + 1][v]
-                # known fields: rhs = (below) - (above)
-                if i == 1 and inc is not None:                   # incident wave in layer 1
-                    r[rv] -= inc[v] / gi
-                    r[rd] -= inc[v]
-                if i == m - 1 and p_plus is not None:            # discs, below this interface
-                    r[rv] += p_plus[v] / gb
-                    r[rd] += -p_plus[v]
-                if i == m and q_minus is not None:               # discs, above this interface
-                    r[rv] -= q_minus[v] / gi
-                    r[rd] -= q_minus[v]
+            a, r = self._assemble([gj[v] for gj in g], pick(inc, v), pick(p_plus, v), pick(q_minus, v))
             s = np.linalg.solve(a, r)
-            out[v] = (s[0], s[col(m, 1)], s[col(m, -1)], s[n - 1])
+            out[v] = s if full else (s[0], s[self._col(m, 1)], s[self._col(m, -1)], s[n - 1])
         return out
+
+    def det(self, lam_real: float) -> complex:
+        """det of the interface system at one real node (for locating its poles)."""
+        lam = np.array([complex(lam_real)])
+        a, _ = self._assemble([gamma(lam, k)[0] for k in self.ks])
+        return np.linalg.det(a)
+
+    def guided_poles(self, n_scan: int = 40001) -> list:
+        """Real poles of the layer response in the guided band (max(k_1, k_L), max interior k),
+        lossless stacks only: zeros of det of the interface system."""
+        if any(isinstance(k, complex) for k in self.ks):
+            raise ValueError("guided_poles: lossless layers only")
+        band = guided_band(self.ks)
+        return [] if band is None else real_zeros(self.det, *band, n_scan)
 
 
 # ----------------------------------------------------------------------------------------------
@@ -1011,52 +1055,63 @@ class Problem:
 
 
 def guided_power(pr: "Problem", src, beta, n_circle: int = 128):
-    """Time-averaged power the guided modes carry to x = +inf and x = -inf (three-layer medium).
+    """Time-averaged power the guided modes carry to x = +inf and x = -inf (lossless media).
 
     For x -> +inf the Sommerfeld integrals close upward around the poles +lambda_g (the contour
     passes below them), so the field tends to (i/2) sum_g R_g(y) e^{i lambda_g x}, R_g the residue
-    of the integrand: sigma_1 e^{-gamma_1 y}/gamma_1 above, (sigma_2^+ e^{gamma_2 y} +
-    sigma_2^- e^{-gamma_2 (y + d)})/gamma_2 in the layer, sigma_3 e^{gamma_3 (y + d)}/gamma_3
-    below (the discs' own H-expansions have no poles); likewise -lambda_g for x -> -inf.  The flux
-    Im int conj(u) du/dx dy of a mode is (lambda_g / 4) int |R_g|^2 dy.  Residues come from the
-    trapezoidal rule on a circle around the pole, with gamma_j continued from the contour
-    (sqrt(lambda^2 - k_j^2) for k_j < lambda_g, where the principal -i sqrt(k^2 - lambda^2) has
-    its cut); the mode integrals are exact exponentials outside the layer, Gauss-Legendre inside.
+    of the integrand: sigma_1 e^{-gamma_1 y}/gamma_1 above, (s_j^+ e^{gamma_j (y - z_{j-1})} +
+    s_j^- e^{-gamma_j (y - z_j)})/gamma_j in interior layer j (for three layers
+    (sigma_2^+ e^{gamma_2 y} + sigma_2^- e^{-gamma_2 (y + d)})/gamma_2), sigma_L
+    e^{gamma_L (y - z_{L-1})}/gamma_L below (the discs' own H-expansions have no poles); likewise
+    -lambda_g for x -> -inf.  The flux Im int conj(u) du/dx dy of a mode is
+    (lambda_g / 4) int |R_g|^2 dy.  Residues come from the trapezoidal rule on a circle around the
+    pole, with gamma_j continued from the contour (sqrt(lambda^2 - k_j^2) for k_j < lambda_g, where
+    the principal -i sqrt(k^2 - lambda^2) has its cut); the mode integrals are exact exponentials in
+    the half-spaces, Gauss-Legendre in each interior layer.  Works for a Medium or a Stack.
     Returns (power to +inf, power to -inf)."""
     m = pr.m
     poles = m.guided_poles()
-    ks = (m.k1, m.k2, m.k3)
+    stack = isinstance(m, Stack)
+    ks = list(m.ks) if stack else [m.k1, m.k2, m.k3]
+    ds = list(m.ds) if stack else [m.d]
+    zs = m.interfaces() if stack else [0.0, -m.d]
 
     def gcont(lam, k, lg):
         lam = np.asarray(lam, dtype=complex)
         return np.sqrt(lam * lam - k * k) if k < abs(lg) else gamma(lam, k)
 
     def dens(lam, lg):
-        g = tuple(gcont(lam, k, lg) for k in ks)
+        g = [gcont(lam, k, lg) for k in ks]
         inc = m.incident_density(lam, src, g[0])
         if pr.N and beta is not None:
             sub = Problem(m, pr.p, pr.c, lam, np.zeros_like(lam))
             p_plus, q_minus = sub.aggregate(np.asarray(beta).reshape(pr.N, pr.P))
         else:
             p_plus = q_minus = None
-        return m.solve_layers(lam, inc, p_plus, q_minus, g)
+        if stack:
+            return m.solve_layers(lam, inc, p_plus, q_minus, g, full=True)
+        return m.solve_layers(lam, inc, p_plus, q_minus, g)      # (sigma_1, sigma_2^+-, sigma_3)
 
     xg, wg = np.polynomial.legendre.leggauss(64)
-    y = -m.d / 2 + m.d / 2 * xg
     total = [0.0, 0.0]
     for side, sgn in ((0, 1.0), (1, -1.0)):
         for pg in poles:
             lg = sgn * pg
-            others = [k for k in ks] + [q for q in poles if q != pg]
+            others = list(ks) + [q for q in poles if q != pg]
             rho = min(abs(pg - q) for q in others) / 3.0
             th = 2.0 * np.pi * np.arange(n_circle) / n_circle
             z = lg + rho * np.exp(1j * th)
             res = (rho / n_circle) * (dens(z, lg) * np.exp(1j * th)[:, None]).sum(axis=0)
             l = np.array([lg], dtype=complex)
-            g1, g2, g3 = (gcont(l, k, lg)[0] for k in ks)
-            c1, c2p, c2m, c3 = res[0] / g1, res[1] / g2, res[2] / g2, res[3] / g3
-            inner = np.sum(wg * m.d / 2 * np.abs(c2p * np.exp(g2 * y) + c2m * np.exp(-g2 * (y + m.d))) ** 2)
-            integral = abs(c1) ** 2 / (2.0 * g1.real) + abs(c3) ** 2 / (2.0 * g3.real) + inner
+            g = [gcont(l, k, lg)[0] for k in ks]
+            c_top, c_bot = res[0] / g[0], res[-1] / g[-1]
+            integral = abs(c_top) ** 2 / (2.0 * g[0].real) + abs(c_bot) ** 2 / (2.0 * g[-1].real)
+            for j in range(2, len(ks)):                          # interior layer j: z_j < y < z_{j-1}
+                d, top, bot = ds[j - 2], zs[j - 2], zs[j - 1]
+                cp, cm = res[1 + 2 * (j - 2)] / g[j - 1], res[2 + 2 * (j - 2)] / g[j - 1]
+                y = bot + d / 2 * (1.0 + xg)
+                u = cp * np.exp(g[j - 1] * (y - top)) + cm * np.exp(-g[j - 1] * (y - bot))
+                integral += np.sum(wg * d / 2 * np.abs(u) ** 2)
             total[side] += pg / 4.0 * integral
     return total[0], total[1]
 

@@ -737,6 +737,29 @@ def test_energy_balance_with_many_guided_modes():
     assert abs(up + down + right + left - total) < 1e-10 * total
 
 
+@pytest.mark.parametrize("with_discs", [False, True])
+def test_energy_balance_in_a_guided_stack(with_discs):
+    # four layers (k = 1, 2.5, 3, 1.5), discs in the third: two guided modes, one of them above the
+    # second layer's k (evanescent there, so that layer's gamma is continued too); radiation through
+    # y = +-inf plus the modes' power equals the source's power
+    ks, ds, mi = [1.0, 2.5, 3.0, 1.5], [0.7, 2.0], 3
+    st = O.Stack(ks, ds, mi, 2.0, 0.1)
+    poles = st.guided_poles()
+    assert len(poles) == 2 and ks[1] < poles[1] < ks[2]
+    src = np.array([0.3, 0.5])
+    c = np.array([[0.1, -0.2], [-0.5, -0.5], [0.6, -0.35]]) if with_discs else np.zeros((0, 2))
+    lam, wt = O.contour(2048, ks[0], ks[mi - 1], ks[-1], 0.2, 33.0, branch_points=ks)
+    pr = O.Problem(st, 4, c, lam, wt)
+    beta = pr.solve_dense(src) if with_discs else None
+    up, down = pr.outgoing_power(src, beta)
+    right, left = O.guided_power(pr, src, beta)
+    total = 0.25 + pr.field_layer1(src, beta, src[None, :], "scattered")[0].imag
+    if not with_discs:
+        assert abs(right - left) < 1e-12 * right
+    assert abs(up + down + right + left - total) < 1e-10 * total
+    assert abs(up + down - total) > 1e-2 * total
+
+
 def test_energy_balance_with_rotated_inclusions():
     # lossless five-lobed inclusions (dense scattering matrices, each turned by its own angle) in the
     # three-layer medium: the power through y = +-inf equals the source's power
