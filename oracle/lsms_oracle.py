@@ -1,25 +1,37 @@
-"""FP64 CPU oracle for multi-particle scattering in a three-layer medium.
+"""FP64 CPU oracle for multi-particle scattering in a layered medium.
 
 TEST INFRASTRUCTURE.  Only the test suite, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
 ``--impl reference`` legs of ``bench.py`` may import this module.  The CUDA library never calls it
 and shares no code with it: special functions come from SciPy (AMOS), Gauss-Legendre rules from
-NumPy, and the 4x4 interface systems are solved by LAPACK LU.
+NumPy, and the interface systems are solved by LAPACK LU (no FFT anywhere: every sum is written out).
 
 It computes, plainly and slowly, what the paper defines (Lai, Kobayashi, Greengard, "A fast solver
 for multi-particle scattering in a layered medium"):
 
 * the Sommerfeld representation of the fields in the three layers (Sec. 2, Eqs. "layer1",
   "layer21", "layer22", "layer3") and the 4x4 mode-by-mode interface system A_lambda
-  (Eq. "sommerfeldsys");
-* the scattering matrix of a dielectric disc from its 2x2 mode system (Sec. 3.1, Eq. "linear");
+  (Eq. "sommerfeldsys") (``Medium``); any number of layers, absorbing ones included, by the same
+  continuity conditions at every interface (``Stack``; the extension Sec. 1 names);
+* the discretised Sommerfeld contour of Sec. 5.1 (``contour``), with its panels placed around the
+  branch points and, where an interior layer guides waves, around the real poles
+  (``contour_panel_breaks``, ``guided_band``);
+* the scattering matrix of a dielectric disc from its 2x2 mode system (Sec. 3.1, Eq. "linear"),
+  and of a perfectly conducting disc (``pec_coefficients``);
 * the scattering matrix of an inclusion of any smooth shape from Muller's second-kind system
   (Sec. 4, Eqs. "intg1", "intg2"), discretised by Nystrom with Kress's product rule for the
   logarithmic singularities, and its rotated copies (Sec. 4.1);
-* Graf's multipole-to-local translation (Sec. 3.2, Lemma 3.1 / Eq. "trans");
+* Graf's multipole-to-local translation (Sec. 3.2, Lemma 3.1 / Eq. "trans"), all pairs or through
+  one level of boxes (``box_translate``: shift to box centres, box-to-box Graf translation, shift
+  back);
 * the multipole-to-Sommerfeld map (Sec. 5.3, Theorem 5.2) and the Sommerfeld-to-local map by
   Jacobi-Anger (Sec. 5.2.1, Lemma 5.1, Eq. "JA2");
 * the block system [A B; C D] (Eq. "finalsys"), its Schur complement (Eq. "schur") and the
-  preconditioned operator I - S(T + R) (Sec. 3.2, Eq. "scattmatrix" and the remark after it).
+  preconditioned operator I - S(T + R) (Sec. 3.2, Eq. "scattmatrix" and the remark after it),
+  solved densely or by GMRES;
+* the fields in every layer, and two checks that need no reference solution: the power radiated
+  through y = +-inf (``Problem.outgoing_power``, Parseval on the real axis) and the power the
+  guided modes carry along the layers (``guided_power``, residues at the real poles), which
+  together equal the power the source emits.
 
 Readings of the paper taken here (each is listed in the design notes with its reason):
 
@@ -40,6 +52,17 @@ Readings of the paper taken here (each is listed in the design notes with its re
 * the disc equations are solved in the preconditioned form (I - S(T + R)) beta = S a_inc, where
   S multiplies the incoming (local) coefficients (Sec. 3.2; Eq. "schur" with D = S T - I and C
   including S).
+* more than three layers: each interior layer carries a wave leaving its top and one leaving its
+  bottom interface, and [u] = [du/dy] = 0 at every interface gives 2(L - 1) equations per node;
+* inclusions: Kress's product rule stands in for the Alpert rule Sec. 4 names; the coefficients of
+  Sec. 4.1 carry the i/4 of the free-space Green's function and the full normal derivative of the
+  incoming wave; a copy turned by theta has S_theta[l][n] = exp(-i l theta) S[l][n] exp(i n theta);
+* guided-mode media: Gamma1's panels are placed by length over distance to the nearest
+  singularity; absorbing layers (complex k, not in the sources' or the particles' layer) keep the
+  principal branch of gamma;
+* the fast translation Sec. 3.2 leaves to a wideband FMM is one level of boxes along x: Graf shifts
+  to and from box centres and Graf translation between well-separated boxes, direct pairs
+  between neighbours.
 
 Notation: P = 2p + 1 orders n = -p..p stored at index n + p; beta has shape (N, P) (or
 (nrhs, N, P)); the contour has N_S nodes lambda_nu with weights w_nu (d lambda included).
