@@ -678,6 +678,23 @@ def test_pec_disc_total_field_vanishes_on_the_boundary():
     assert np.abs(u_d).max() > 1e-2 * ref
 
 
+def test_pec_disc_is_the_limit_of_a_good_conductor():
+    # a dielectric disc whose interior wavenumber k_p = s (1 + i) has a large imaginary part (a good
+    # conductor, skin depth 1/s) tends to the perfectly conducting disc with a gap O(1/s): the gap
+    # halves as s doubles and one Richardson step leaves O(1/s^2).  Independent of the PEC formula:
+    # the dielectric side solves the pinned 2x2 mode system with complex-argument Bessel functions.
+    k2, R, p = MED["k2"], MED["radius"], 10
+    pec = O.pec_coefficients(p, k2, R)
+    ref = np.abs(pec).max()
+    m = {s: O.mie_coefficients(p, k2, s * (1 + 1j), R) for s in (200, 400, 800, 1600)}
+    gap = {s: np.abs(m[s] - pec).max() / ref for s in m}
+    assert gap[200] < 0.05
+    for s in (200, 400, 800):
+        assert 1.95 < gap[s] / gap[2 * s] < 2.05
+    rich = {s: np.abs(2 * m[2 * s] - m[s] - pec).max() / ref for s in (400, 800)}
+    assert rich[800] < 5e-5 and 3.5 < rich[400] / rich[800] < 4.5
+
+
 @pytest.mark.parametrize("loss", [0.5, 2.0])
 def test_energy_balance_with_an_absorbing_substrate(loss):
     # lossless layers 1 and 2 and discs over an absorbing half-space: the source's power
