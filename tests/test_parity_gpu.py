@@ -7,7 +7,6 @@ coefficients beta_n weighted by |H_n(k2 R)|, incoming coefficients alpha_nu weig
 for the FP64 path, 1e-8 for the mixed path after refinement (the stated targets); the mixed operator
 itself (FP32 translation) is checked at 2e-5.
 """
-import math
 
 import numpy as np
 import pytest
