@@ -319,6 +319,16 @@ int lsms_fma_probe(int precision, double* tflops);
  *   Errors: LSMS_ERR_ARG. */
 int lsms_pec_scattering_diagonal(int p, double k2, double radius, double* s_diag);
 
+/* lsms_scattering_diagonal_c — host only.  S_n, n = -p..p, of an absorbing dielectric disc: the
+ *   mode system of Sec. 3.1 Eq. "linear" with a complex interior wavenumber kp = kp_re + i kp_im
+ *   (kp_re >= 0, kp_im >= 0: a lossy or conducting interior; the layer k2 stays real), solved
+ *   through the logarithmic derivative J_n'(kp R) / J_n(kp R), which stays finite where J_n(kp R)
+ *   overflows.  kp_im = 0 gives lsms_scattering_diagonal.  As kp_im grows the disc tends to the
+ *   perfectly conducting one (lsms_pec_scattering_diagonal).  Pass diag(S) to
+ *   lsms_set_scattering_matrix.  s_diag: 2p + 1 complex.  Errors: LSMS_ERR_ARG (also for
+ *   |kp| R > 1e5). */
+int lsms_scattering_diagonal_c(int p, double k2, double kp_re, double kp_im, double radius, double* s_diag);
+
 /* lsms_set_fmm — translate through boxes for long layouts of many discs (the FMM acceleration named
  *   in Sec. 3.2; the multipole shifts of Sec. 5.3).  Discs are grouped into boxes of width
  *   box_width along x (centres at the disc layer's mid-height); pairs in the same or adjacent boxes

@@ -16,7 +16,7 @@ for multi-particle scattering in a layered medium"):
   branch points and, where an interior layer guides waves, around the real poles
   (``contour_panel_breaks``, ``guided_band``);
 * the scattering matrix of a dielectric disc from its 2x2 mode system (Sec. 3.1, Eq. "linear"),
-  and of a perfectly conducting disc (``pec_coefficients``);
+  lossless or absorbing (complex k_p), and of a perfectly conducting disc (``pec_coefficients``);
 * the scattering matrix of an inclusion of any smooth shape from Muller's second-kind system
   (Sec. 4, Eqs. "intg1", "intg2"), discretised by Nystrom with Kress's product rule for the
   logarithmic singularities, and its rotated copies (Sec. 4.1);
@@ -31,7 +31,8 @@ for multi-particle scattering in a layered medium"):
 * the fields in every layer, and two checks that need no reference solution: the power radiated
   through y = +-inf (``Problem.outgoing_power``, Parseval on the real axis) and the power the
   guided modes carry along the layers (``guided_power``, residues at the real poles), which
-  together equal the power the source emits.
+  together with the power absorbed inside lossy particles (``Problem.absorbed_power``) equal the
+  power the source emits.
 
 Readings of the paper taken here (each is listed in the design notes with its reason):
 
@@ -869,6 +870,20 @@ class Problem:
 
     def rhs(self, src):
         return self.scatter(self.incident_local(src))
+
+    def absorbed_power(self, src, beta) -> np.ndarray:
+        """Time-averaged power absorbed inside each particle (zero for lossless ones).
+
+        Near particle j the total field is sum_n (alpha_n J_n(k2 r) + beta_n H_n(k2 r)) e^{i n theta}
+        with alpha = a_inc + (T + R) beta, its incoming coefficients.  Its flux
+        Im int conj(u) du/dr ds through a circle around the particle (inside the annulus that holds
+        no other sources) follows from the Wronskian J_n Y_n' - J_n' Y_n = 2 / (pi x):
+        4 sum_n (|beta_n|^2 + Re(conj(alpha_n) beta_n)), the same normalisation in which the line
+        source (i/4) H_0 emits 1/4.  The absorbed power is minus that flux; for a lossless particle
+        (I + 2S unitary) it vanishes."""
+        beta = np.asarray(beta, dtype=complex).reshape(self.N, self.P)
+        alpha = self.incident_local(src) + self.translation(beta) + self.reflection(beta)
+        return -4.0 * (np.abs(beta) ** 2 + (np.conj(alpha) * beta).real).sum(axis=1)
 
     # --- dense assembly and solves (Eq. "finalsys", Eq. "schur") ----------------------------------
     def dense_operator(self):

@@ -209,6 +209,60 @@ extern "C" int lsms_pec_scattering_diagonal(int p, double k2, double radius, dou
   return LSMS_OK;
 }
 
+// Absorbing disc: complex k_p with Re k_p >= 0, Im k_p > 0 (a lossy or conducting interior).  The
+// 2x2 mode system of Eq. "linear" divided by J_n(k_p R) leaves only the logarithmic derivative
+// D_n = J_n'(z) / J_n(z) at z = k_p R:
+//   S_n = (k_p D_n J_n(k2 R) - k2 J_n'(k2 R)) / (k2 H_n'(k2 R) - k_p D_n H_n(k2 R)),
+// finite where J_n(z) itself overflows (Im z of several hundred).  With r_n = J_{n+1}(z) / J_n(z),
+// D_n = n / z - r_n, and J_{n-1} + J_{n+1} = (2n / z) J_n gives r_{n-1} = 1 / (2n / z - r_n): run
+// downward from r_N = 0 at N well above max(p, |z|), it converges to the ratio of the minimal
+// solution J (Miller's backward recurrence in ratio form).  J_n has no zeros off the real axis, so
+// no step divides by zero when Im z > 0.  S_{-n} = S_n.
+static std::vector<cplx> mie_diagonal_c(int p, double k2, cplx kp, double R) {
+  auto jn = [](int n, double x) {
+    const double v = std::cyl_bessel_j((double)std::abs(n), x);
+    return (n < 0 && (std::abs(n) & 1)) ? -v : v;
+  };
+  auto yn = [](int n, double x) {
+    const double v = std::cyl_neumann((double)std::abs(n), x);
+    return (n < 0 && (std::abs(n) & 1)) ? -v : v;
+  };
+  const cplx z = kp * R;
+  const double az = std::abs(z);
+  const int top = p + (int)std::ceil(az + 12.0 * std::cbrt(az)) + 60;
+  std::vector<cplx> r(p + 1);
+  cplx rn(0.0, 0.0);                                   // r_top
+  for (int n = top; n >= 1; --n) {
+    rn = 1.0 / (2.0 * n / z - rn);                     // r_{n-1}
+    if (n - 1 <= p) r[n - 1] = rn;
+  }
+  std::vector<cplx> S(2 * p + 1);
+  const double a = k2 * R;
+  for (int n = 0; n <= p; ++n) {
+    const cplx D = (double)n / z - r[n];
+    const double j2 = jn(n, a), y2 = yn(n, a);
+    const double j2p = 0.5 * (jn(n - 1, a) - jn(n + 1, a)), y2p = 0.5 * (yn(n - 1, a) - yn(n + 1, a));
+    const cplx h(j2, y2), hp(j2p, y2p);
+    S[p + n] = (kp * D * j2 - k2 * j2p) / (k2 * hp - kp * D * h);
+    S[p - n] = S[p + n];
+  }
+  return S;
+}
+
+extern "C" int lsms_scattering_diagonal_c(int p, double k2, double kp_re, double kp_im, double radius,
+                                          double* s_diag) {
+  if (p < 0 || p > LSMS_MAX_P || !s_diag || !std::isfinite(k2) || !(k2 > 0.0) || !std::isfinite(kp_re) ||
+      !std::isfinite(kp_im) || kp_re < 0.0 || kp_im < 0.0 || !(std::hypot(kp_re, kp_im) > 0.0) ||
+      !std::isfinite(radius) || !(radius > 0.0) || std::hypot(kp_re, kp_im) * radius > 1e5)
+    return ctx_fail(nullptr, LSMS_ERR_ARG,
+                    "scattering_diagonal_c: need 0 <= p <= 15, k2 > 0, Re kp >= 0, Im kp >= 0, 0 < |kp| R <= 1e5, "
+                    "radius > 0");
+  const std::vector<cplx> S = kp_im == 0.0 ? mie_diagonal(p, k2, kp_re, radius)
+                                           : mie_diagonal_c(p, k2, cplx(kp_re, kp_im), radius);
+  std::memcpy(s_diag, S.data(), S.size() * sizeof(cplx));
+  return LSMS_OK;
+}
+
 // ---------------------------------------------------------------------------------------------
 // The context's scattering matrices
 // ---------------------------------------------------------------------------------------------

@@ -203,6 +203,34 @@ def test_library_pec_diagonal_equals_oracle(lib):
         lib.pec_scattering_diagonal(16, 2.0, 0.2)
 
 
+@pytest.mark.parametrize("kp", [7.54 + 0.5j, 7.54 + 7.54j, 40 + 1j, 0.1 + 20j, 2 + 1e-3j, 5j, 1e-3 + 0.01j,
+                                300 + 300j])
+def test_library_absorbing_disc_diagonal_equals_oracle(lib, kp):
+    # complex k_p: the library's log-derivative route against the oracle's 2x2 solve with SciPy's
+    # complex-argument Bessel functions
+    for p in (0, 5, 10, 15):
+        for k2, R in ((inputs.MEDIUM["k2"], 0.25), (1.0, 0.1), (20.0, 0.5)):
+            s = lib.scattering_diagonal(p, k2, kp, R)
+            s_o = O.mie_coefficients(p, k2, kp, R)
+            assert np.abs(s - s_o).max() < 1e-12 * np.abs(s_o).max(), (p, k2, R)
+
+
+def test_library_absorbing_disc_beyond_the_oracle_range(lib):
+    # Im(k_p R) = 800, where J_n(k_p R) overflows (the oracle's 2x2 solve gives NaN): the library's
+    # diagonal stays finite and sits at the good-conductor gap O(1/|k_p|) from the perfectly
+    # conducting disc, half the gap at half the |k_p|
+    k2, R, p = 20.0, 0.5, 12
+    pec = O.pec_coefficients(p, k2, R)
+    gap = {s: np.abs(lib.scattering_diagonal(p, k2, s * (1 + 1j), R) - pec).max() / np.abs(pec).max()
+           for s in (800.0, 1600.0)}
+    assert gap[1600.0] < 2e-2 and 1.9 < gap[800.0] / gap[1600.0] < 2.1
+    real = lib.scattering_diagonal(p, k2, 7.5, R)
+    assert np.array_equal(lib.scattering_diagonal(p, k2, 7.5 + 0j, R), real)   # Im k_p = 0: the real route
+    for bad in (7.5 - 0.1j, -1 + 1j, 0j, complex(np.nan, 1.0), 1e6 + 1e6j):
+        with pytest.raises(lib.LsmsError):
+            lib.scattering_diagonal(p, k2, bad, R)
+
+
 @pytest.mark.parametrize("ks,b,n_nodes,t_max", [
     (inputs.STACK5["ks"], 0.2, 512, 80.0),                                # five layers, no guided band
     ([1.0, 2.5, 6.0, 3.0, 1.5], 0.2, 1024, 40.0),                          # guided band (1.5, 6)

@@ -168,3 +168,25 @@ def test_perfectly_conducting_discs(L, small):
         assert rel(beta[0], b_o, small.hs[None, :]) < TOL64
         u = ctx.eval_field(w.targets, 0, L.FIELD_SCATTERED)
         assert rel(u, pr.field_layer1(w.sources[0], b_o, w.targets, "scattered")) < TOL64
+
+
+@pytest.mark.parametrize("loss", [0.5, 7.5])
+def test_absorbing_discs(L, small, loss):
+    # discs with a lossy interior (complex k_p in Sec. 3.1's mode system): the library's diagonal
+    # (lsms_scattering_diagonal_c) through lsms_set_scattering_matrix, solved and compared with the
+    # oracle's problem built on its own complex-k_p Mie coefficients
+    w = small.w
+    m = w.medium
+    kp = m["kp"] + 1j * loss
+    s_abs = L.scattering_diagonal(w.p, m["k2"], kp, m["radius"])
+    pr = O.Problem(medium_of(w), w.p, small.c, small.lam, small.wt,
+                   smat=np.diag(O.mie_coefficients(w.p, m["k2"], kp, m["radius"])))
+    with L.context_for(w) as ctx:
+        ctx.set_particles(small.c)
+        ctx.set_scattering_matrix(np.diag(s_abs))
+        beta, info = ctx.solve(w.sources, tol=1e-12, maxiter=400)
+        assert info["status"] == 0
+        b_o = pr.solve_dense(w.sources[0])
+        assert rel(beta[0], b_o, small.hs[None, :]) < TOL64
+        u = ctx.eval_field(w.targets, 0, L.FIELD_SCATTERED)
+        assert rel(u, pr.field_layer1(w.sources[0], b_o, w.targets, "scattered")) < TOL64

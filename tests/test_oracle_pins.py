@@ -695,6 +695,28 @@ def test_pec_disc_is_the_limit_of_a_good_conductor():
     assert rich[800] < 5e-5 and 3.5 < rich[400] / rich[800] < 4.5
 
 
+@pytest.mark.parametrize("kp", [MED["kp"] + 0.5j, MED["kp"] * (1 + 1j), 300 * (1 + 1j)])
+def test_energy_balance_with_absorbing_discs(kp):
+    # discs with a lossy or conducting interior (complex k_p) in the lossless three-layer medium: the
+    # source's power 1/4 + Im u^s(x0) leaves through y = +-inf or is absorbed inside the discs (the
+    # flux of each disc's own expansion, from the Wronskian); lossless discs absorb nothing
+    m = O.Medium(MED["k1"], MED["k2"], MED["k3"], MED["d"], kp, MED["radius"])
+    c = np.array([[0.1, -0.6], [-0.7, -1.2], [0.8, -1.0]])
+    src = np.array([0.3, 0.5])
+    lam, wt = O.contour(2048, m.k1, m.k2, m.k3, 0.2, 60.0)
+    pr = O.Problem(m, 8, c, lam, wt)
+    beta = pr.solve_dense(src)
+    absorbed = pr.absorbed_power(src, beta)
+    up, down = pr.outgoing_power(src, beta)
+    total = 0.25 + pr.field_layer1(src, beta, src[None, :], "scattered")[0].imag
+    assert np.all(absorbed > 1e-4)
+    assert abs(up + down + absorbed.sum() - total) < 1e-11 * total
+    assert abs(up + down - total) > 1e-2 * total
+    lossless = O.Problem(O.Medium(MED["k1"], MED["k2"], MED["k3"], MED["d"], MED["kp"], MED["radius"]), 8, c,
+                         lam, wt)
+    assert np.abs(lossless.absorbed_power(src, lossless.solve_dense(src))).max() < 1e-14
+
+
 @pytest.mark.parametrize("loss", [0.5, 2.0])
 def test_energy_balance_with_an_absorbing_substrate(loss):
     # lossless layers 1 and 2 and discs over an absorbing half-space: the source's power
