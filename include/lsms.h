@@ -306,6 +306,15 @@ int lsms_get_scattering_matrix(const lsms_ctx* ctx, double* s);
  *   LSMS_ERR_GEOMETRY (a point outside the enclosing disc or at its centre). */
 int lsms_inclusion_scattering_matrix(int p, double k2, double kp, double radius, int n_pts,
                                      const double* curve, double* s_out);
+/* lsms_inclusion_scattering_matrix_c — the same for an absorbing inclusion: complex interior
+ *   wavenumber kp = kp_re + i kp_im (kp_re >= 0, kp_im >= 0; the layer k2 stays real) in the
+ *   interior kernels of Muller's system, their J_0, J_1, Y_0, Y_1 at complex argument from
+ *   Miller's backward recurrence and Neumann's expansions.  The product rule's log part grows like
+ *   exp(Im kp r) along the curve, so accuracy falls off as about 1e-16 exp(2 Im kp R): kp_im * 2R
+ *   must be <= 12 (1e-10 or better).  kp_im = 0 is lsms_inclusion_scattering_matrix.
+ *   Errors: as above, LSMS_ERR_ARG also for a loss beyond that bound. */
+int lsms_inclusion_scattering_matrix_c(int p, double k2, double kp_re, double kp_im, double radius, int n_pts,
+                                       const double* curve, double* s_out);
 
 /* lsms_fma_probe — the achievable FMA rate of the current GPU (TFLOP/s, 2 flop per FMA), measured
  *   with independent dependency chains over a grid that fills every SM (precision LSMS_FP64:

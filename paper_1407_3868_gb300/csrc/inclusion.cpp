@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "lsms_internal.h"
@@ -34,23 +35,78 @@ double bessel_jn(int n, double z) {
   return (n < 0 && (std::abs(n) & 1)) ? -v : v;
 }
 
-struct Kernels {        // the four kernels for one wavenumber and one (i, j) pair: full and log part
+// J_0, J_1, H_0, H_1 at a real argument (libstdc++ special math).
+void bessel01(double z, double& j0, double& j1, cplx& h0, cplx& h1) {
+  j0 = std::cyl_bessel_j(0.0, z);
+  j1 = std::cyl_bessel_j(1.0, z);
+  h0 = cplx(j0, std::cyl_neumann(0.0, z));
+  h1 = cplx(j1, std::cyl_neumann(1.0, z));
+}
+
+// The same at a complex argument z (Re z >= 0, Im z >= 0, z != 0): the interior kernels of an
+// absorbing inclusion.  J_n by Miller's backward recurrence J_{n-1} = (2n/z) J_n - J_{n+1} from
+// J_{N+1} = 0 at N well above |z|, normalised with exp(-iz) = J_0 + 2 sum_{n>=1} (-i)^n J_n (the
+// generating function exp((z/2)(t - 1/t)) = sum_n J_n t^n at t = -i; |exp(-iz)| = exp(Im z) >= 1,
+// so the sum does not cancel).  Y_0 from Neumann's expansion
+//   Y_0 = (2/pi)(ln(z/2) + C) J_0 - (4/pi) sum_{k>=1} (-1)^k J_{2k} / k,
+// Y_1 = -Y_0' term by term (J_0' = -J_1, 2 J_n' = J_{n-1} - J_{n+1}):
+//   Y_1 = -(2/pi) J_0 / z + (2/pi)(ln(z/2) + C) J_1 + (2/pi) sum_{k>=1} (-1)^k (J_{2k-1} - J_{2k+1}) / k.
+// J is accurate to rounding relative to itself; H = J + iY, exponentially small when Im z is large,
+// carries an absolute error of about 1e-16 |J| ~ 1e-16 exp(Im z), hence the cap on the loss.
+void bessel01(cplx z, cplx& j0, cplx& j1, cplx& h0, cplx& h1) {
+  const double az = std::abs(z);
+  int top = (int)(az + 12.0 * std::cbrt(az)) + 40;
+  top += top & 1;
+  std::vector<cplx> J(top + 2);
+  J[top + 1] = 0.0;
+  J[top] = 1e-300;
+  const cplx iz = 1.0 / z;
+  for (int n = top; n >= 1; --n) {
+    J[n - 1] = (2.0 * n) * iz * J[n] - J[n + 1];
+    if (std::abs(J[n - 1]) > 1e250)
+      for (int q = n - 1; q <= top + 1; ++q) J[q] *= 1e-250;
+  }
+  static const cplx mi[4] = {cplx(1, 0), cplx(0, -1), cplx(-1, 0), cplx(0, 1)};   // (-i)^n
+  cplx s = J[0];
+  for (int n = 1; n <= top; ++n) s += 2.0 * mi[n & 3] * J[n];
+  const cplx scale = std::exp(cplx(0.0, -1.0) * z) / s;
+  for (cplx& v : J) v *= scale;
+  const cplx lg = std::log(0.5 * z) + kEuler;
+  cplx s0 = 0.0, s1 = 0.0;
+  for (int k = 1; 2 * k + 1 <= top; ++k) {
+    const double sg = (k & 1) ? -1.0 : 1.0;
+    s0 += sg * J[2 * k] / (double)k;
+    s1 += sg * (J[2 * k - 1] - J[2 * k + 1]) / (double)k;
+  }
+  const cplx y0 = (2.0 / kPi) * (lg * J[0]) - (4.0 / kPi) * s0;
+  const cplx y1 = -(2.0 / kPi) * J[0] * iz + (2.0 / kPi) * (lg * J[1]) + (2.0 / kPi) * s1;
+  j0 = J[0];
+  j1 = J[1];
+  h0 = j0 + cplx(0.0, 1.0) * y0;
+  h1 = j1 + cplx(0.0, 1.0) * y1;
+}
+
+// the four kernels for one wavenumber (real, or complex for an absorbing interior) and one (i, j)
+// pair: full and log part
+template <typename K>
+struct Kernels {
   cplx s, d, nn, t;
-  double s1, d1, n1, t1;
+  K s1, d1, n1, t1;
 };
 
 // Kernels at x_i (normal nx, unit) and x_j (nu_j = |x'_j| n_j), ds_y = |x'_j| d tau folded in.
-Kernels kernels(double k, const double dxy[2], double r, const double nx[2], const double nuj[2],
-                double spj) {
-  const double z = k * r;
-  const double j0 = std::cyl_bessel_j(0.0, z), j1 = std::cyl_bessel_j(1.0, z);
-  const cplx h0(j0, std::cyl_neumann(0.0, z)), h1(j1, std::cyl_neumann(1.0, z));
+template <typename K>
+Kernels<K> kernels(K k, const double dxy[2], double r, const double nx[2], const double nuj[2], double spj) {
+  const K z = k * r;
+  K j0, j1;
+  cplx h0, h1;
+  bessel01(z, j0, j1, h0, h1);
   const double nxd = nx[0] * dxy[0] + nx[1] * dxy[1];
   const double nuyd = nuj[0] * dxy[0] + nuj[1] * dxy[1];
   const double nxnuy = nx[0] * nuj[0] + nx[1] * nuj[1];
   const cplx iq(0.0, 0.25);
   const double c4 = 1.0 / (4.0 * kPi);
-  Kernels o;
+  Kernels<K> o;
   o.s = iq * h0 * spj;
   o.s1 = -c4 * j0 * spj;
   o.d = iq * k * h1 * nuyd / r;
@@ -58,7 +114,7 @@ Kernels kernels(double k, const double dxy[2], double r, const double nx[2], con
   o.nn = -iq * k * h1 * nxd / r * spj;
   o.n1 = c4 * k * j1 * nxd / r * spj;
   const cplx a = k * k * h0 / (r * r) - 2.0 * k * h1 / (r * r * r);
-  const double areg = k * k * j0 / (r * r) - 2.0 * k * j1 / (r * r * r);
+  const K areg = k * k * j0 / (r * r) - 2.0 * k * j1 / (r * r * r);
   o.t = iq * (a * nxd * nuyd + k * h1 / r * nxnuy);
   o.t1 = -c4 * (areg * nxd * nuyd + k * j1 / r * nxnuy);
   return o;
@@ -68,8 +124,9 @@ Kernels kernels(double k, const double dxy[2], double r, const double nx[2], con
 
 // S[l][n] (row-major, orders -p..p) of the inclusion bounded by `curve` ([n_pts][6]: x, y, x', y',
 // x'', y'' at t_j = 2 pi j / n_pts, counterclockwise, about the enclosing disc's centre).
-int inclusion_matrix(int p, double k2, double kp, double radius, int n_pts, const double* curve,
-                     std::vector<cplx>& S, std::string& err) {
+template <typename K>
+int inclusion_matrix_t(int p, double k2, K kp, double radius, int n_pts, const double* curve,
+                       std::vector<cplx>& S, std::string& err) {
   const int P = 2 * p + 1, n = n_pts;
   std::vector<double> x(n), y(n), sp(n), rho(n), th(n);
   std::vector<double> nux(n), nuy(n);                  // |x'| n (outward)
@@ -102,17 +159,20 @@ int inclusion_matrix(int p, double k2, double kp, double radius, int n_pts, cons
   // Muller matrix in the unknowns [mu; sigma]
   const int N2 = 2 * n;
   std::vector<cplx> A((size_t)N2 * N2, cplx(0, 0));
-  const double dk2 = k2 * k2 - kp * kp;
+  const K dk2 = k2 * k2 - kp * kp;
   for (int i = 0; i < n; ++i) {
     const double nx[2] = {nux[i] / sp[i], nuy[i] / sp[i]};
     for (int j = 0; j < n; ++j) {
       cplx ms, md, mn, mt;
-      double m1s, m1d, m1n, m1t;
+      K m1s, m1d, m1n, m1t;
       double L = 0.0;
       if (i == j) {
         m1s = m1d = m1n = 0.0;
         m1t = -dk2 * sp[i] / (8.0 * kPi);
-        ms = cplx(-(sp[i] / (2.0 * kPi)) * std::log(k2 / kp), 0.0);
+        if constexpr (std::is_same_v<K, double>)
+          ms = cplx(-(sp[i] / (2.0 * kPi)) * std::log(k2 / kp), 0.0);
+        else
+          ms = -(sp[i] / (2.0 * kPi)) * std::log(k2 / kp);
         md = mn = cplx(0, 0);
         mt = sp[i] * (cplx((1.0 - 2.0 * kEuler) / (8.0 * kPi), 0.125) * dk2 -
                       (k2 * k2 * std::log(k2 * sp[i] / 2.0) - kp * kp * std::log(kp * sp[i] / 2.0)) /
@@ -121,8 +181,8 @@ int inclusion_matrix(int p, double k2, double kp, double radius, int n_pts, cons
         const double dxy[2] = {x[i] - x[j], y[i] - y[j]};
         const double r = std::hypot(dxy[0], dxy[1]);
         const double nuj[2] = {nux[j], nuy[j]};
-        const Kernels a = kernels(k2, dxy, r, nx, nuj, sp[j]);
-        const Kernels b = kernels(kp, dxy, r, nx, nuj, sp[j]);
+        const Kernels<double> a = kernels(k2, dxy, r, nx, nuj, sp[j]);
+        const Kernels<K> b = kernels(kp, dxy, r, nx, nuj, sp[j]);
         const double sn = std::sin(0.5 * h * (i - j));
         L = std::log(4.0 * sn * sn);
         m1s = a.s1 - b.s1; m1d = a.d1 - b.d1; m1n = a.n1 - b.n1; m1t = a.t1 - b.t1;
@@ -176,17 +236,41 @@ int inclusion_matrix(int p, double k2, double kp, double radius, int n_pts, cons
   return LSMS_OK;
 }
 
+static bool inclusion_args_ok(int p, double k2, double radius, int n_pts, const double* curve, const double* s_out) {
+  return p >= 0 && p <= LSMS_MAX_P && std::isfinite(k2) && k2 > 0.0 && std::isfinite(radius) && radius > 0.0 &&
+         n_pts >= 8 && n_pts <= 4096 && !(n_pts & 1) && curve && s_out;
+}
+
 extern "C" int lsms_inclusion_scattering_matrix(int p, double k2, double kp, double radius, int n_pts,
                                                 const double* curve, double* s_out) {
-  if (p < 0 || p > LSMS_MAX_P || !std::isfinite(k2) || !(k2 > 0.0) || !std::isfinite(kp) || !(kp > 0.0) ||
-      !std::isfinite(radius) || !(radius > 0.0) || n_pts < 8 || n_pts > 4096 || (n_pts & 1) || !curve || !s_out)
+  if (!inclusion_args_ok(p, k2, radius, n_pts, curve, s_out) || !std::isfinite(kp) || !(kp > 0.0))
     return ctx_fail(nullptr, LSMS_ERR_ARG,
                     "inclusion_scattering_matrix: need 0 <= p <= 15, k2, kp, radius > 0, an even n_pts in "
                     "[8, 4096], curve and output");
   std::vector<cplx> S;
   std::string err;
-  const int rc = inclusion_matrix(p, k2, kp, radius, n_pts, curve, S, err);
+  const int rc = inclusion_matrix_t<double>(p, k2, kp, radius, n_pts, curve, S, err);
   if (rc) return ctx_fail(nullptr, rc, "inclusion_scattering_matrix: " + err);
+  std::memcpy(s_out, S.data(), S.size() * sizeof(cplx));
+  return LSMS_OK;
+}
+
+// An absorbing inclusion: complex kp (Re kp >= 0, Im kp >= 0) in the interior kernels, the same
+// Muller system and product rule; Im kp = 0 is the call above.  The log part of Kress's split is
+// J_0(kp r), J_1(kp r) over the whole curve, which grows like exp(Im kp r): the product rule and
+// H = J + iY then lose about exp(Im kp * 2R) * 1e-16, hence Im kp * 2R <= 12 (1e-10 and better).
+extern "C" int lsms_inclusion_scattering_matrix_c(int p, double k2, double kp_re, double kp_im, double radius,
+                                                  int n_pts, const double* curve, double* s_out) {
+  if (!inclusion_args_ok(p, k2, radius, n_pts, curve, s_out) || !std::isfinite(kp_re) || !std::isfinite(kp_im) ||
+      kp_re < 0.0 || kp_im < 0.0 || !(std::hypot(kp_re, kp_im) > 0.0) || kp_im * 2.0 * radius > 12.0)
+    return ctx_fail(nullptr, LSMS_ERR_ARG,
+                    "inclusion_scattering_matrix_c: need 0 <= p <= 15, k2, radius > 0, Re kp >= 0, Im kp >= 0, "
+                    "kp != 0, Im kp * 2 radius <= 12, an even n_pts in [8, 4096], curve and output");
+  if (kp_im == 0.0) return lsms_inclusion_scattering_matrix(p, k2, kp_re, radius, n_pts, curve, s_out);
+  std::vector<cplx> S;
+  std::string err;
+  const int rc = inclusion_matrix_t<cplx>(p, k2, cplx(kp_re, kp_im), radius, n_pts, curve, S, err);
+  if (rc) return ctx_fail(nullptr, rc, "inclusion_scattering_matrix_c: " + err);
   std::memcpy(s_out, S.data(), S.size() * sizeof(cplx));
   return LSMS_OK;
 }

@@ -8,8 +8,8 @@ Context covers the C ABI: three-layer media (Context(k1, k2, k3, d, ...)) or any
 absorbing ones included (stack=(ks, thicknesses, particle_layer), complex ks); particles or batches
 of layouts (set_particles, set_layouts); dense rotated scattering matrices for inclusions of any
 shape (set_scattering_matrix, set_orientations; inclusion_scattering_matrix,
-pec_scattering_diagonal and scattering_diagonal with a complex kp, for absorbing discs, build them on
-the host); the translation through boxes (set_fmm); the
+pec_scattering_diagonal and, with a complex kp for absorbing particles, scattering_diagonal and
+inclusion_scattering_matrix build them on the host); the translation through boxes (set_fmm); the
 operator and its steps, solves and fields.  fma_probe measures the GPU's FMA ceilings.
 """
 from __future__ import annotations
@@ -27,7 +27,7 @@ APPLY_SCALED, APPLY_MIXED, APPLY_NO_TRANSLATION, APPLY_NO_REFLECTION, APPLY_ALPH
 FIELD_TOTAL, FIELD_SCATTERED, FIELD_PARTICLE = 0, 1, 2
 STATUS = {0: "OK", -1: "ARG", -2: "GEOMETRY", -3: "NOT_CONVERGED", -4: "NONFINITE", -5: "OOM",
           -6: "CUDA", -7: "STATE"}
-EXPORTS = ["lsms_create", "lsms_layer_response", "lsms_build_contour_stack", "lsms_fma_probe", "lsms_pec_scattering_diagonal", "lsms_scattering_diagonal_c", "lsms_set_fmm", "lsms_get_fmm", "lsms_fmm_stats", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
+EXPORTS = ["lsms_create", "lsms_layer_response", "lsms_build_contour_stack", "lsms_fma_probe", "lsms_pec_scattering_diagonal", "lsms_scattering_diagonal_c", "lsms_inclusion_scattering_matrix_c", "lsms_set_fmm", "lsms_get_fmm", "lsms_fmm_stats", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
            "lsms_get_scattering_matrix", "lsms_inclusion_scattering_matrix", "lsms_set_particles", "lsms_apply", "lsms_apply_ex", "lsms_apply_dev",
            "lsms_translate", "lsms_aggregate", "lsms_reflect", "lsms_disaggregate", "lsms_incident",
            "lsms_get_contour", "lsms_get_scattering", "lsms_num_nodes", "lsms_num_particles",
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsms_inclusion_scattering_matrix": (i, [i, d, d, d, i, _D, _D]),
         "lsms_pec_scattering_diagonal": (i, [i, d, d, _D]),
         "lsms_scattering_diagonal_c": (i, [i, d, d, d, d, _D]),
+        "lsms_inclusion_scattering_matrix_c": (i, [i, d, d, d, d, i, _D, _D]),
         "lsms_fma_probe": (i, [i, _D]),
         "lsms_apply": (i, [_P, i, _D, _D]),
         "lsms_apply_ex": (i, [_P, i, _D, _D, i]),
@@ -439,13 +440,19 @@ def translate_mixed_noalloc(centres, beta, alpha, k2, p, stream=None):
 
 
 def inclusion_scattering_matrix(p, k2, kp, radius, curve) -> np.ndarray:
-    """lsms_inclusion_scattering_matrix: curve = (x, x', x'') as three (n_pts, 2) arrays."""
+    """lsms_inclusion_scattering_matrix: curve = (x, x', x'') as three (n_pts, 2) arrays; a complex
+    kp (an absorbing inclusion) goes to lsms_inclusion_scattering_matrix_c."""
     lib = load()
     x, dx, ddx = (np.asarray(a, dtype=np.float64).reshape(-1, 2) for a in curve)
     c = np.ascontiguousarray(np.concatenate([x, dx, ddx], axis=1))
     s = np.zeros((2 * p + 1, 2 * p + 1), dtype=np.complex128)
-    rc = lib.lsms_inclusion_scattering_matrix(int(p), float(k2), float(kp), float(radius), c.shape[0],
-                                              _dptr(c), _dptr(s))
+    if np.iscomplexobj(kp):
+        kc = complex(kp)
+        rc = lib.lsms_inclusion_scattering_matrix_c(int(p), float(k2), kc.real, kc.imag, float(radius), c.shape[0],
+                                                    _dptr(c), _dptr(s))
+    else:
+        rc = lib.lsms_inclusion_scattering_matrix(int(p), float(k2), float(kp), float(radius), c.shape[0],
+                                                  _dptr(c), _dptr(s))
     if rc != 0:
         raise LsmsError(rc, lib.lsms_last_error(None).decode())
     return s

@@ -166,6 +166,34 @@ def test_library_inclusion_matrix_equals_oracle(lib, p, n_pts, shape, kp, k2):
     assert np.abs(s_lib - s_o).max() < 1e-13 * np.abs(s_o).max()
 
 
+@pytest.mark.parametrize("kp", [7.54 + 0.5j, 7.54 + 7.54j, 20 + 10j, 3 + 23.9j, 0.5 + 5j])
+@pytest.mark.parametrize("shape", [(0.18, 0.05, 5), (0.15, 0.06, 3), (0.2, 0.0, 0)])
+def test_library_absorbing_inclusion_matrix_equals_oracle(lib, kp, shape):
+    # complex k_p (absorbing interior): the library's complex-argument J_0, J_1, Y_0, Y_1 (Miller,
+    # Neumann) against the oracle's AMOS values in the same Nystrom system, up to the loss bound
+    # Im k_p * 2R <= 12 (R = 0.25); a centred circle also equals the library's own absorbing Mie
+    # diagonal (the log-derivative route)
+    k2, p = inputs.MEDIUM["k2"], 10
+    cur = inputs.star_curve(*shape, 256, rotation=0.3)
+    s_lib = lib.inclusion_scattering_matrix(p, k2, kp, 0.25, cur)
+    s_o = O.inclusion_scattering_matrix(cur, p, k2, kp)
+    assert np.abs(s_lib - s_o).max() < 1e-12 * np.abs(s_o).max()
+    if shape[1] == 0.0:
+        mie = lib.scattering_diagonal(p, k2, kp, shape[0])
+        assert np.abs(s_lib - np.diag(mie)).max() < 1e-12 * np.abs(mie).max()
+
+
+def test_library_absorbing_inclusion_arguments(lib):
+    s = inputs.STAR5
+    cur = inputs.star_curve(s["a1"], s["a2"], s["a3"], 128)
+    k2 = inputs.MEDIUM["k2"]
+    real = lib.inclusion_scattering_matrix(6, k2, 7.5, 0.25, cur)
+    assert np.array_equal(lib.inclusion_scattering_matrix(6, k2, 7.5 + 0j, 0.25, cur), real)
+    for bad in (7.5 - 0.1j, -1 + 1j, 0j, complex(7.5, np.nan), 3 + 24.1j):      # 24.1 * 0.5 > 12
+        with pytest.raises(lib.LsmsError):
+            lib.inclusion_scattering_matrix(6, k2, bad, 0.25, cur)
+
+
 def test_library_inclusion_matrix_rejects_bad_curves(lib):
     k2, kp = inputs.MEDIUM["k2"], inputs.MEDIUM["kp"]
     x, dx, ddx = inputs.star_curve(0.15, 0.05, 5, 64)

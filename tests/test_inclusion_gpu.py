@@ -190,3 +190,27 @@ def test_absorbing_discs(L, small, loss):
         assert rel(beta[0], b_o, small.hs[None, :]) < TOL64
         u = ctx.eval_field(w.targets, 0, L.FIELD_SCATTERED)
         assert rel(u, pr.field_layer1(w.sources[0], b_o, w.targets, "scattered")) < TOL64
+
+
+def test_absorbing_rotated_inclusions(L, small):
+    # lossy five-lobed inclusions (complex k_p in Muller's system, the library's own matrix from
+    # lsms_inclusion_scattering_matrix_c), each turned by its angle: FP64 solve and fields against
+    # the oracle's problem built on its own absorbing matrix
+    w = small.w
+    m = w.medium
+    s = inputs.STAR5
+    kp = m["kp"] * (1 + 0.3j)
+    cur = inputs.star_curve(s["a1"], s["a2"], s["a3"], s["n_pts"])
+    S_lib = L.inclusion_scattering_matrix(w.p, m["k2"], kp, m["radius"], cur)
+    S_o = O.inclusion_scattering_matrix(cur, w.p, m["k2"], kp)
+    pr = O.Problem(medium_of(w), w.p, small.c, small.lam, small.wt, smat=S_o, theta=small.theta)
+    with L.context_for(w) as ctx:
+        ctx.set_particles(small.c)
+        ctx.set_scattering_matrix(S_lib)
+        ctx.set_orientations(small.theta)
+        beta, info = ctx.solve(w.sources, tol=1e-12, maxiter=400)
+        assert info["status"] == 0
+        b_o = pr.solve_dense(w.sources[0])
+        assert rel(beta[0], b_o, small.hs[None, :]) < TOL64
+        u = ctx.eval_field(w.targets, 0, L.FIELD_SCATTERED)
+        assert rel(u, pr.field_layer1(w.sources[0], b_o, w.targets, "scattered")) < TOL64

@@ -799,6 +799,52 @@ def test_energy_balance_in_a_guided_stack(with_discs):
     assert abs(up + down - total) > 1e-2 * total
 
 
+@pytest.mark.parametrize("kp", [MED["kp"] + 0.5j, MED["kp"] * (1 + 1j), 3 + 23.9j])
+def test_absorbing_inclusion_matrix(kp):
+    # complex k_p in Muller's system: a centred circle gives the absorbing disc's Mie diagonal (the
+    # 2x2 mode system, pinned by the energy balance with absorbing discs); the five-lobed star keeps
+    # its selection rule, mirror symmetry and reciprocity, converges in the number of points, and is
+    # passive: I - (I + 2S)^H (I + 2S) is positive semidefinite and not zero
+    k2, p = MED["k2"], 10
+    S = O.inclusion_scattering_matrix(inputs.star_curve(0.2, 0.0, 0, 256), p, k2, kp)
+    mie = O.mie_coefficients(p, k2, kp, 0.2)
+    assert np.abs(S - np.diag(mie)).max() < 1e-12 * np.abs(mie).max()
+    s = inputs.STAR5
+    S = O.inclusion_scattering_matrix(inputs.star_curve(s["a1"], s["a2"], s["a3"], 256), p, k2, kp)
+    S384 = O.inclusion_scattering_matrix(inputs.star_curve(s["a1"], s["a2"], s["a3"], 384), p, k2, kp)
+    big = np.abs(S).max()
+    assert np.abs(S384 - S).max() < 1e-12 * big
+    l = np.arange(-p, p + 1)
+    sg = (-1.0) ** (l[:, None] + l[None, :])
+    assert np.abs(S[((l[:, None] - l[None, :]) % 5) != 0]).max() < 1e-13 * big
+    assert np.abs(S - sg * S[::-1, ::-1]).max() < 1e-13 * big
+    assert np.abs(S - sg * S[::-1, ::-1].T).max() < 1e-13 * big
+    U = np.eye(2 * p + 1) + 2 * S
+    ev = np.linalg.eigvalsh(np.eye(2 * p + 1) - U.conj().T @ U)
+    assert ev.min() > -1e-12 and ev.max() > 1e-2
+
+
+def test_energy_balance_with_absorbing_rotated_inclusions():
+    # lossy five-lobed inclusions, each turned by its own angle, in the three-layer medium: radiation
+    # through y = +-inf plus the power each inclusion absorbs (minus the flux of its own expansion)
+    # equals the source's power
+    s = inputs.STAR5
+    m = medium()
+    kp = m.kp * (1 + 0.3j)
+    S = O.inclusion_scattering_matrix(inputs.star_curve(s["a1"], s["a2"], s["a3"], 128), 6, m.k2, kp)
+    c = np.array([[0.2, -0.7], [-0.6, -1.3], [0.9, -1.0]])
+    src = np.array([0.3, 1.0])
+    lam, wt = O.contour(1024, m.k1, m.k2, m.k3, 0.2, 120.0)
+    pr = O.Problem(m, 6, c, lam, wt, smat=S, theta=np.array([0.3, 1.7, 4.0]))
+    beta = pr.solve_dense(src)
+    up, down = pr.outgoing_power(src, beta)
+    absorbed = pr.absorbed_power(src, beta)
+    total = 0.25 + pr.field_layer1(src, beta, src[None, :], "scattered")[0].imag
+    assert np.all(absorbed > 1e-3)
+    assert abs(up + down + absorbed.sum() - total) < 1e-9 * total
+    assert abs(up + down - total) > 1e-2 * total
+
+
 def test_energy_balance_with_rotated_inclusions():
     # lossless five-lobed inclusions (dense scattering matrices, each turned by its own angle) in the
     # three-layer medium: the power through y = +-inf equals the source's power
