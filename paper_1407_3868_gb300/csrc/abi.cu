@@ -470,8 +470,8 @@ extern "C" int lsms_reflect(lsms_ctx* c, int nrhs, const double* p_plus, const d
   const int ns = c->ns;
   std::vector<cplx> pq((size_t)nrhs * 2 * ns);
   for (int r = 0; r < nrhs; ++r) {
-    std::memcpy(pq.data() + (size_t)r * 2 * ns, p_plus + (size_t)r * ns * 2, ns * sizeof(cplx));
-    std::memcpy(pq.data() + (size_t)r * 2 * ns + ns, q_minus + (size_t)r * ns * 2, ns * sizeof(cplx));
+    std::memcpy(static_cast<void*>(pq.data() + (size_t)r * 2 * ns), p_plus + (size_t)r * ns * 2, ns * sizeof(cplx));
+    std::memcpy(static_cast<void*>(pq.data() + (size_t)r * 2 * ns + ns), q_minus + (size_t)r * ns * 2, ns * sizeof(cplx));
   }
   int rc;
   if ((rc = copy_in(c, c->ws_pq, (const double*)pq.data(), pq.size()))) return rc;

@@ -360,7 +360,7 @@ extern "C" int lsms_set_scattering_matrix(lsms_ctx* c, const double* s) {
     c->smat.clear();
   } else {
     std::vector<cplx> m((size_t)P * P);
-    std::memcpy(m.data(), s, m.size() * sizeof(cplx));
+    std::memcpy(static_cast<void*>(m.data()), s, m.size() * sizeof(cplx));
     for (const cplx& v : m)
       if (!std::isfinite(v.real()) || !std::isfinite(v.imag()))
         return ctx_fail(c, LSMS_ERR_ARG, "set_scattering_matrix: non-finite entry");
