@@ -9,8 +9,10 @@
  * Generalisations built on the same operator: any number of layers with the particles in any
  * interior one (lsms_create_stack), absorbing layers (lsms_create_stack_c), inclusions of any smooth
  * shape turned per particle (Sec. 4: lsms_inclusion_scattering_matrix, lsms_set_scattering_matrix,
- * lsms_set_orientations), batches of layouts (lsms_set_layouts) and, for long layouts of many
- * discs, the translation through boxes (lsms_set_fmm).
+ * lsms_set_orientations), perfectly conducting and absorbing particles
+ * (lsms_pec_scattering_diagonal, lsms_scattering_diagonal_c, lsms_inclusion_scattering_matrix_c),
+ * batches of layouts (lsms_set_layouts) and, for long layouts of many discs, the translation
+ * through boxes (lsms_set_fmm).  The header is plain C99.
  *
  * Unknowns: the outgoing (Hankel) coefficients beta^j_n, n = -p..p, of every disc j
  * (Sec. 3.1 Eq. "out"; truncation Sec. 3.1 Remark).  P = 2p + 1.
