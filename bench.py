@@ -335,13 +335,15 @@ def run_ours(args, rank, world, local_rank):
     ctx.close()
     batched = stack = inclusions = contrast = large = boxes = example1 = None
     if world == 1 and not args.no_batched:
-        batched = run_batched(args, dev, flush)
-        stack = run_stack(args, w, dev, flush)
-        inclusions = run_inclusions(args, w, dev, flush)
-        contrast = run_contrast(args)
-        large = run_large(args, dev, flush)
-        boxes = run_boxes(args, w, dev, flush, u_ref_fp64)
-        example1 = run_example1(args)
+        # the further workloads, after the headline: a failure in one is reported in its own key
+        # (and on stderr) without losing the headline line
+        batched = guarded("batched", run_batched, args, dev, flush)
+        stack = guarded("stack", run_stack, args, w, dev, flush)
+        inclusions = guarded("inclusions", run_inclusions, args, w, dev, flush)
+        contrast = guarded("contrast_sweep", run_contrast, args)
+        large = guarded("large", run_large, args, dev, flush)
+        boxes = guarded("boxes", run_boxes, args, w, dev, flush, u_ref_fp64)
+        example1 = guarded("example1", run_example1, args)
 
     if rank != 0:
         return None
@@ -381,6 +383,16 @@ def run_ours(args, rank, world, local_rank):
         except Exception as e:  # pragma: no cover
             line["cpu_baseline"] = {"value": None, "error": str(e)[-300:]}
     return line
+
+
+def guarded(name, fn, *args):
+    """fn(*args), or {"error": ...} (also printed to stderr) if it raises."""
+    try:
+        return fn(*args)
+    except Exception as e:  # noqa: BLE001 - any failure of a further workload is reported, not raised
+        msg = f"{type(e).__name__}: {e}"
+        print(f"bench: section {name} failed: {msg}", file=sys.stderr)
+        return {"error": msg[-500:]}
 
 
 def time_device(fn, steps, flush=None):

@@ -31,3 +31,17 @@ def test_reference_arm_other_ranks_exit_quietly():
     res = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert res.returncode == 0, res.stderr[-2000:]
     assert res.stdout.strip() == ""
+
+
+def test_a_failing_further_workload_keeps_the_headline(capsys):
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.guarded("ok", lambda a, b: a + b, 2, 3) == 5
+
+    def boom():
+        raise RuntimeError("no convergence")
+    out = bench.guarded("example1", boom)
+    assert out == {"error": "RuntimeError: no convergence"}
+    assert "section example1 failed" in capsys.readouterr().err
