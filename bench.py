@@ -569,6 +569,18 @@ def run_inclusions(args, w, dev, flush):
         _, info = ctx.solve(w.sources, tol=1e-8, maxiter=2000)
         out["mixed_solve"] = {"tol": 1e-8, "s": time.perf_counter() - t0, "iters": info["iters"],
                               "refinements": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"]}
+        # the same stars with a lossy interior, k_p (1 + 0.3i) (complex k_p in Muller's system)
+        kp_abs = m["kp"] * (1 + 0.3j)
+        t0 = time.perf_counter()
+        smat_abs = lsms.inclusion_scattering_matrix(w.p, m["k2"], kp_abs, m["radius"],
+                                                    inputs.star_curve(s["a1"], s["a2"], s["a3"], s["n_pts"]))
+        t_abs = time.perf_counter() - t0
+        ctx.set_scattering_matrix(smat_abs)
+        t0 = time.perf_counter()
+        _, info = ctx.solve(w.sources, tol=1e-8, maxiter=2000)
+        out["absorbing_mixed_solve"] = {"kp": [kp_abs.real, kp_abs.imag], "matrix_setup_s": t_abs, "tol": 1e-8,
+                                        "s": time.perf_counter() - t0, "iters": info["iters"],
+                                        "refinements": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"]}
     ctx.close()
     return out
 
