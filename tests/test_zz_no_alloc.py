@@ -7,8 +7,9 @@ output must match the context entry point lsms_translate(..., LSMS_MIXED) within
 mixed-operator parity tests use, on consecutive calls (the scratch array keeps the previous call's
 contents, so a second call with other inputs checks that nothing stale leaks through).
 
-This file is collected last on purpose: a run that stops at the first failure has then already run
-every other test.
+This file is collected after the other parity files (only the order-range edges,
+test_zzz_orders_gpu.py, come later): a run that stops at the first failure has then already run
+them.
 """
 import numpy as np
 import pytest
