@@ -33,6 +33,8 @@ for multi-particle scattering in a layered medium"):
   guided modes carry along the layers (``guided_power``, residues at the real poles), which
   together with the power absorbed inside lossy particles (``Problem.absorbed_power``) equal the
   power the source emits.
+* converged mode for discretisation studies: every contour sum replaced by its adaptive integral
+  over the same truncated contour (``converged_parts``, ``converged_solution``).
 
 Readings of the paper taken here (each is listed in the design notes with its reason):
 
@@ -1152,6 +1154,109 @@ def guided_power(pr: "Problem", src, beta, n_circle: int = 128):
                 integral += np.sum(wg * d / 2 * np.abs(u) ** 2)
             total[side] += pg / 4.0 * integral
     return total[0], total[1]
+
+
+# ----------------------------------------------------------------------------------------------
+# Converged mode (discretisation studies only): the same contour, integrated adaptively
+# ----------------------------------------------------------------------------------------------
+def contour_pieces(branch_points, b: float, t_max: float) -> list:
+    """Sec. 5.1's contour Gamma3 -> Gamma2 -> Gamma1, truncated at |Re lambda| = t_max, as straight
+    pieces (lam0, direction, s0, s1): lambda(s) = lam0 + direction s, d lambda = direction ds,
+    split at the branch points (real parts) so that every piece is smooth."""
+    ks = sorted(set(float(np.real(k)) for k in branch_points if 0.0 < float(np.real(k)) < t_max))
+    g1 = [0.0] + ks + [float(t_max)]
+    back = g1[::-1]
+    pieces = [(1j * b, 1.0, -a, -e) for a, e in zip(back[:-1], back[1:])]     # Gamma3, t up to 0
+    pieces.append((1j * b, -1j, 0.0, 2.0 * b))                                 # Gamma2: i (b - s)
+    pieces += [(-1j * b, 1.0, a, e) for a, e in zip(g1[:-1], g1[1:])]          # Gamma1
+    return pieces
+
+
+def converged_parts(pr: "Problem", src, targets, lam):
+    """At nodes lam (any complex values): the integrands of the three contour sums of Problem, in
+    the scaled unknowns b = |H_n(k2 R)| beta: K(lambda) (N P x N P) with D S R D^{-1} = int K,
+    r(lambda) (N P) with D S a_inc = int r, and for the layer-1 scattered field at the targets
+    u = int (f(lambda) + H(lambda) b).  Per node the reflection is rank two (Sec. 5: aggregate,
+    layer response, disaggregate), so K = q [u_top (r_pp v_top + r_pq v_bot)^T + u_bot (r_qp v_top +
+    r_qq v_bot)^T], with the factors of Problem.aggregate / disaggregate and the layer response for
+    unit densities.  Returns (K, r, f, H) stacked over the nodes."""
+    m, k2, d = pr.m, pr.m.k2, pr.m.d
+    lam = np.atleast_1d(np.asarray(lam, dtype=complex))
+    n_s, N, P = lam.size, pr.N, pr.P
+    hs = order_scale(pr.p, k2, m.radius)
+    x, y = pr.c[:, 0], pr.c[:, 1]
+    g2 = gamma(lam, k2)[:, None]
+    lc = lam[:, None]
+    # aggregation factors (Theorem 5.2): P^+ = v_top . beta, Q^- = v_bot . beta
+    v_top = (np.exp(g2 * y[None, :] - 1j * lc * x[None, :])[:, :, None]
+             * m2s_factor(pr.orders[None, None, :], lc[:, :, None], k2, above=True)).reshape(n_s, N * P)
+    v_bot = (np.exp(-g2 * (y[None, :] + d) - 1j * lc * x[None, :])[:, :, None]
+             * m2s_factor(pr.orders[None, None, :], lc[:, :, None], k2, above=False)).reshape(n_s, N * P)
+    # disaggregation factors (Lemma 5.1), with the scattering matrices applied (S alpha)
+    u_top = (np.exp(g2 * y[None, :] + 1j * lc * x[None, :])[:, :, None]
+             * plane_wave_local_factor(pr.orders[None, None, :], lc[:, :, None], k2, downward=True))
+    u_bot = (np.exp(-g2 * (y[None, :] + d) + 1j * lc * x[None, :])[:, :, None]
+             * plane_wave_local_factor(pr.orders[None, None, :], lc[:, :, None], k2, downward=False))
+    u_top = np.stack([pr.scatter(u) for u in u_top]).reshape(n_s, N * P)
+    u_bot = np.stack([pr.scatter(u) for u in u_bot]).reshape(n_s, N * P)
+    q = 1.0 / (FOUR_PI * gamma(lam, k2))
+    one, zero = np.ones(n_s, dtype=complex), np.zeros(n_s, dtype=complex)
+    from_p = m.solve_layers(lam, None, one, zero)          # response to a unit P^+
+    from_q = m.solve_layers(lam, None, zero, one)          # response to a unit Q^-
+    inc = m.incident_density(lam, src)
+    from_i = m.solve_layers(lam, inc)
+    dsc = np.tile(hs, N)                                   # D on rows and columns
+    left_t = (q[:, None] * u_top) * dsc[None, :]
+    left_b = (q[:, None] * u_bot) * dsc[None, :]
+    right_t = v_top / dsc[None, :]
+    right_b = v_bot / dsc[None, :]
+    K = (left_t[:, :, None] * (from_p[:, 1, None] * right_t + from_q[:, 1, None] * right_b)[:, None, :]
+         + left_b[:, :, None] * (from_p[:, 2, None] * right_t + from_q[:, 2, None] * right_b)[:, None, :])
+    r = left_t * from_i[:, 1, None] + left_b * from_i[:, 2, None]
+    pts = np.atleast_2d(targets)
+    g1 = gamma(lam, m.k1)
+    ex = np.exp(-g1[:, None] * pts[None, :, 1] + 1j * lam[:, None] * pts[None, :, 0]) / (FOUR_PI * g1[:, None])
+    f = ex * from_i[:, 0, None]
+    H = ex[:, :, None] * (from_p[:, 0, None] * right_t + from_q[:, 0, None] * right_b)[:, None, :]
+    return K, r, f, H
+
+
+def converged_solution(pr: "Problem", src, targets, b: float, t_max: float, tol: float = 1e-13):
+    """The solution of the same problem with every contour sum replaced by the exact integral over
+    the same truncated contour (adaptive Gauss-Kronrod, scipy's quad_vec, to tol in the scaled
+    entries), the translation unchanged: (beta, scattered field at the targets).  Only the contour
+    quadrature differs from Problem's discrete solution, so the difference measures its error."""
+    from scipy import integrate
+
+    N, P = pr.N, pr.P
+    n_t = np.atleast_2d(targets).shape[0]
+    sizes = [(N * P) ** 2, N * P, n_t, n_t * N * P]
+
+    def fun(lam):
+        K, r, f, H = converged_parts(pr, src, targets, np.array([lam]))
+        return np.concatenate([K.ravel(), r.ravel(), f.ravel(), H.ravel()])
+
+    branch = getattr(pr.m, "ks", (pr.m.k1, pr.m.k2, pr.m.k3))
+    total = 0.0
+    for lam0, dr, s0, s1 in contour_pieces(branch, b, t_max):
+        val, _ = integrate.quad_vec(lambda s: fun(lam0 + dr * s) * dr, s0, s1, epsabs=tol, epsrel=tol,
+                                    norm="max", limit=20000)
+        total = total + val
+    o = np.cumsum([0] + sizes)
+    K = total[o[0]:o[1]].reshape(N * P, N * P)
+    r = total[o[1]:o[2]]
+    f = total[o[2]:o[3]]
+    H = total[o[3]:o[4]].reshape(n_t, N * P)
+    hs = np.tile(order_scale(pr.p, pr.m.k2, pr.m.radius), N)
+    T = np.zeros((N * P, N * P), dtype=complex)
+    for l in range(N):
+        for j in range(N):
+            if j != l:
+                T[l * P:(l + 1) * P, j * P:(j + 1) * P] = translation_matrix(pr.c[l], pr.c[j], pr.m.k2, pr.p, pr.p)
+    ST = np.concatenate([pr.scatter(T[:, c].reshape(N, P)).reshape(-1, 1) for c in range(N * P)], axis=1)
+    A = np.eye(N * P) - hs[:, None] * ST / hs[None, :] - K
+    bsol = np.linalg.solve(A, r)
+    return (bsol / hs).reshape(N, P), f + H @ bsol
 
 
 def gmres(matvec, b, tol=1e-12, maxiter=500):

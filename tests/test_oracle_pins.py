@@ -859,3 +859,38 @@ def test_energy_balance_with_rotated_inclusions():
     up, down = pr.outgoing_power(src, beta)
     u_s = pr.field_layer1(src, beta, src[None, :], "scattered")[0]
     assert abs(up + down - (0.25 + u_s.imag)) < 1e-9 * 0.25
+
+
+def test_converged_mode_reproduces_the_discrete_sums_and_is_their_limit():
+    # converged mode (discretisation studies): its per-node integrands, summed with a contour's own
+    # nodes and weights, give Problem's discrete operator, right-hand side and field (scaled); its
+    # adaptive integrals over the same truncated contour are what the discrete solutions converge to
+    m = medium()
+    c = np.array([[0.1, -0.6], [-0.7, -1.2], [0.8, -1.0]])
+    src, tg = np.array([0.3, 0.5]), np.array([[0.0, 0.8], [1.0, 1.5], [-2.0, 0.3]])
+    p, b, t_max = 3, 0.2, 60.0
+    lam, wt = O.contour(256, m.k1, m.k2, m.k3, b, t_max)
+    pr = O.Problem(m, p, c, lam, wt)
+    N, P = pr.N, pr.P
+    hs = np.tile(O.order_scale(p, m.k2, m.radius), N)
+    K, r, f, H = O.converged_parts(pr, src, tg, lam)
+    R = np.zeros((N * P, N * P), dtype=complex)
+    for col in range(N * P):
+        e = np.zeros(N * P, dtype=complex)
+        e[col] = 1.0 / hs[col]
+        R[:, col] = hs * pr.scatter(pr.reflection(e.reshape(N, P))).ravel()
+    assert np.abs(np.tensordot(wt, K, axes=1) - R).max() < 1e-14 * np.abs(R).max()
+    rhs = hs * pr.rhs(src).ravel()
+    assert np.abs(wt @ r - rhs).max() < 1e-14 * np.abs(rhs).max()
+    beta = pr.solve_dense(src)
+    u = pr.field_layer1(src, beta, tg, "scattered")
+    u_parts = wt @ f + np.tensordot(wt, H, axes=1) @ (hs * beta.ravel())
+    assert np.abs(u_parts - u).max() < 1e-14 * np.abs(u).max()
+    bc, uc = O.converged_solution(pr, src, tg, b, t_max)
+    errs = {}
+    for ns in (256, 2048):
+        lam, wt = O.contour(ns, m.k1, m.k2, m.k3, b, t_max)
+        prn = O.Problem(m, p, c, lam, wt)
+        bn = prn.solve_dense(src)
+        errs[ns] = np.linalg.norm((bn - bc).ravel() * hs) / np.linalg.norm(bc.ravel() * hs)
+    assert errs[256] > 1e-6 and errs[2048] < 1e-11
