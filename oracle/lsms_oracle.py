@@ -193,13 +193,14 @@ def contour_panel_breaks(n_panels: int, branch_points, b: float, t_max: float, b
 
 
 def contour(n_nodes: int, k1: float, k2: float, k3: float, b: float, t_max: float,
-            panel_order: int = 16, branch_points=None, guided=True, graded=False):
+            panel_order: int = 16, branch_points=None, guided=True, graded=False, greedy=False):
     """Nodes lambda_nu and weights w_nu (d lambda included) of the discretised contour.
 
     Gamma1 (t - i b, 0 < t < t_max) and Gamma3 (its mirror t + i b, -t_max < t < 0) each carry
     n1 = q * floor((N_S - q) / (2 q)) Gauss-Legendre nodes in panels of order q placed by
     contour_panel_breaks (guided=False or graded=True: the geometric grading even in a
-    guided-mode medium, for comparison only); Gamma2 (i s,
+    guided-mode medium, for comparison only; greedy=True: the length over distance rule in every
+    medium, with an empty band where there is no guided-mode band); Gamma2 (i s,
     s from b down to -b) carries the remaining N_S - 2 n1 nodes as one Gauss-Legendre rule.
     Returned in path order Gamma3 -> Gamma2 -> Gamma1.
     """
@@ -209,7 +210,10 @@ def contour(n_nodes: int, k1: float, k2: float, k3: float, b: float, t_max: floa
     if n1 <= 0 or n2 <= 0:
         raise ValueError("contour: too few nodes for the panel order")
     bp = (k1, k2, k3) if branch_points is None else branch_points
-    breaks = contour_panel_breaks(n1 // q, bp, b, t_max, guided_band(bp) if guided and not graded else None)
+    band = guided_band(bp) if guided and not graded else None
+    if greedy and band is None:
+        band = (0.0, 0.0)                                 # no panel meets an empty band
+    breaks = contour_panel_breaks(n1 // q, bp, b, t_max, band)
     x, w = np.polynomial.legendre.leggauss(q)
     t1, w1 = [], []
     for a, c in zip(breaks[:-1], breaks[1:]):

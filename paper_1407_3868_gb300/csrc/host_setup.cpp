@@ -56,14 +56,16 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
 // geometrically toward each branch point (k +- b 2^j, j < L) with the largest L that keeps at most
 // n_panels panels; then the longest panel is halved (first one on ties) until there are n_panels.
 std::vector<double> contour_panel_breaks(int n_panels, const double* ks, int nk, double b,
-                                         double t_max, double band_lo, double band_hi) {
+                                         double t_max, double band_lo, double band_hi, bool greedy) {
   std::set<double> branch;
   for (int i = 0; i < nk; ++i)
     if (ks[i] > 0.0 && ks[i] < t_max) branch.insert(ks[i]);
-  if (band_hi > band_lo) {
-    // guided-mode medium: poles of the layer response on the real axis in (band_lo, band_hi), a
-    // distance b below Gamma1.  Halve the panel with the largest length / (b + distance to the
-    // nearest branch point) (distance 0 for a panel meeting the band; first one on ties).
+  const bool has_band = band_hi > band_lo;
+  if (has_band || greedy) {
+    // guided-mode medium (poles of the layer response on the real axis in (band_lo, band_hi), a
+    // distance b below Gamma1), or the greedy rule asked for: halve the panel with the largest
+    // length / (b + distance to the nearest branch point) (distance 0 for a panel meeting the
+    // band; first one on ties).
     std::set<double> s0 = branch;
     s0.insert(0.0);
     s0.insert(t_max);
@@ -71,7 +73,7 @@ std::vector<double> contour_panel_breaks(int n_panels, const double* ks, int nk,
     if ((int)pts.size() - 1 > n_panels) pts = {0.0, t_max};   // too few panels for every branch point
     auto score = [&](double a, double e) {
       double dist;
-      if (e > band_lo && a < band_hi) {
+      if (has_band && e > band_lo && a < band_hi) {
         dist = 0.0;
       } else {
         dist = t_max;
@@ -132,6 +134,10 @@ int build_contour(const lsms_contour& c, const std::vector<double>& ks, std::vec
     err = "contour: n_nodes, panel_order, b and t_max must be positive and finite";
     return LSMS_ERR_ARG;
   }
+  if (c.panel_rule != 0 && c.panel_rule != 1) {
+    err = "contour: panel_rule must be 0 (graded) or 1 (greedy)";
+    return LSMS_ERR_ARG;
+  }
   const int n1 = q * ((ns - q) / (2 * q));
   const int n2 = ns - 2 * n1;
   if (n1 <= 0 || n2 <= 0) {
@@ -142,7 +148,8 @@ int build_contour(const lsms_contour& c, const std::vector<double>& ks, std::vec
   // an interior layer (lambda < its k) -> poles of the layer response on the real axis
   double band_lo = std::max(ks.front(), ks.back()), band_hi = 0.0;
   for (size_t i = 1; i + 1 < ks.size(); ++i) band_hi = std::max(band_hi, ks[i]);
-  std::vector<double> br = contour_panel_breaks(n1 / q, ks.data(), (int)ks.size(), b, t_max, band_lo, band_hi);
+  std::vector<double> br =
+      contour_panel_breaks(n1 / q, ks.data(), (int)ks.size(), b, t_max, band_lo, band_hi, c.panel_rule == 1);
 
   std::vector<double> gx, gw;
   gauss_legendre(q, gx, gw);

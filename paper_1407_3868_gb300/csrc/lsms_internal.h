@@ -177,9 +177,10 @@ struct lsms_ctx {
 // ------------------------------------------------------------------------------------------
 int build_contour(const lsms_contour& c, const std::vector<double>& ks, std::vector<cplx>& lam,
                   std::vector<cplx>& wt, std::string& err);
-// Gamma1 panel breakpoints; band_hi > band_lo marks a guided-mode band
+// Gamma1 panel breakpoints; band_hi > band_lo marks a guided-mode band; greedy: the length over
+// distance rule even without a band
 std::vector<double> contour_panel_breaks(int n_panels, const double* ks, int nk, double b,
-                                         double t_max, double band_lo, double band_hi);
+                                         double t_max, double band_lo, double band_hi, bool greedy);
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 std::vector<cplx> mie_diagonal(int p, double k2, double kp, double R);
 std::vector<double> hankel_scale(int p, double k2, double R);

@@ -45,7 +45,7 @@ class LsmsError(RuntimeError):
 
 class Contour(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int), ("b", ctypes.c_double), ("t_max", ctypes.c_double),
-                ("panel_order", ctypes.c_int)]
+                ("panel_order", ctypes.c_int), ("panel_rule", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -138,14 +138,14 @@ class Context:
     """One lsms context (lsms_create ... lsms_destroy)."""
 
     def __init__(self, k1, k2, k3, d, kp, radius, p, n_nodes, b=0.0, t_max=0.0, panel_order=0,
-                 precision=LSMS_FP64, stack=None):
+                 precision=LSMS_FP64, stack=None, panel_rule=0):
         """Three layers (k1, k2, k3; middle thickness d), or with stack=(ks, thicknesses, m) any
         number of layers (k1, k2, k3 and d are then ignored; lsms_create_stack, or with complex ks
-        — absorbing layers — lsms_create_stack_c)."""
+        — absorbing layers — lsms_create_stack_c).  panel_rule: lsms_contour.panel_rule."""
         self.lib = load()
         self.p = p
         self.P = 2 * p + 1
-        c = Contour(n_nodes, b, t_max, panel_order)
+        c = Contour(n_nodes, b, t_max, panel_order, panel_rule)
         h = _P()
         if stack is None:
             rc = self.lib.lsms_create(k1, k2, k3, d, kp, radius, p, ctypes.byref(c), precision,
@@ -360,25 +360,25 @@ class Context:
         return u
 
 
-def build_contour(n_nodes, k1, k2, k3, b=0.0, t_max=0.0, panel_order=0):
+def build_contour(n_nodes, k1, k2, k3, b=0.0, t_max=0.0, panel_order=0, panel_rule=0):
     """Host-only: the library's contour nodes and weights (no GPU needed)."""
     lib = load()
     lam = np.zeros(n_nodes, dtype=np.complex128)
     wt = np.zeros(n_nodes, dtype=np.complex128)
-    c = Contour(n_nodes, b, t_max, panel_order)
+    c = Contour(n_nodes, b, t_max, panel_order, panel_rule)
     rc = lib.lsms_build_contour(ctypes.byref(c), k1, k2, k3, _dptr(lam), _dptr(wt))
     if rc != 0:
         raise LsmsError(rc, lib.lsms_last_error(None).decode())
     return lam, wt
 
 
-def build_contour_stack(n_nodes, ks, b=0.0, t_max=0.0, panel_order=0):
+def build_contour_stack(n_nodes, ks, b=0.0, t_max=0.0, panel_order=0, panel_rule=0):
     """Host-only: the library's contour for a stack of layers with wavenumbers ks (top to bottom)."""
     lib = load()
     k = np.ascontiguousarray(np.real(np.asarray(ks)), dtype=np.float64)
     lam = np.zeros(n_nodes, dtype=np.complex128)
     wt = np.zeros(n_nodes, dtype=np.complex128)
-    c = Contour(n_nodes, b, t_max, panel_order)
+    c = Contour(n_nodes, b, t_max, panel_order, panel_rule)
     rc = lib.lsms_build_contour_stack(ctypes.byref(c), int(k.size), _dptr(k), _dptr(lam), _dptr(wt))
     if rc != 0:
         raise LsmsError(rc, lib.lsms_last_error(None).decode())

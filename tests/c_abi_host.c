@@ -20,7 +20,7 @@ int main(void) {
   double k1 = 2.0 * pi, k2 = 3.0 * pi, k3 = 4.0 * pi, kp = 2.4 * pi, radius = 0.25;
   int p = 6, rc, n, i;
   double s[2 * 13], nodes[2 * 256], weights[2 * 256], status[1];
-  lsms_contour contour = {256, 0.2, 40.0, 16};
+  lsms_contour contour = {256, 0.2, 40.0, 16, 0};
   lsms_ctx* ctx = NULL;
   double centres[6] = {0.0, -1.0, 0.6, -1.0, 0.3, -0.3};
   double ds[2] = {0.7, 2.0};

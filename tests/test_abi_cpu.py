@@ -64,6 +64,22 @@ def test_library_contour_equals_oracle_contour_in_guided_media(lib, ks, b, n_nod
         assert np.max(np.abs(lam - lam_p)) > 1e-3
 
 
+@pytest.mark.parametrize("ks,b,n_nodes,t_max", [(MED_K, 0.2, 256, 141.0), (MED_K, 9.4e-4, 1024, 163.0),
+                                              ((1.0, 6.0, 1.0), 0.2, 1024, 40.0)])
+def test_library_greedy_contour_equals_oracle(lib, ks, b, n_nodes, t_max):
+    # panel_rule = 1: the length / (b + distance) rule in every medium (the default in guided media)
+    lam, wt = lib.build_contour(n_nodes, *ks, b, t_max, 16, 1)
+    lam_o, wt_o = O.contour(n_nodes, *ks, b, t_max, greedy=True)
+    assert np.max(np.abs(lam - lam_o)) <= 1e-12 * t_max
+    assert np.max(np.abs(wt - wt_o)) <= 1e-14 * t_max
+    lam_d, _ = lib.build_contour(n_nodes, *ks, b, t_max, 16, 0)
+    guided = ks[1] > max(ks[0], ks[2])
+    assert (np.array_equal(lam, lam_d)) == guided
+    with pytest.raises(lib.LsmsError) as e:
+        lib.build_contour(n_nodes, *ks, b, t_max, 16, 2)
+    assert e.value.code == -1
+
+
 def test_contour_defaults_follow_the_paper(lib):
     # b = 0.2, t_max = max k + 20, 16-point panels (Sec. 6)
     lam, wt = lib.build_contour(500, 1.0, 3.0, 1.0)

@@ -894,3 +894,23 @@ def test_converged_mode_reproduces_the_discrete_sums_and_is_their_limit():
         bn = prn.solve_dense(src)
         errs[ns] = np.linalg.norm((bn - bc).ravel() * hs) / np.linalg.norm(bc.ravel() * hs)
     assert errs[256] > 1e-6 and errs[2048] < 1e-11
+
+
+def test_greedy_panel_rule_reaches_the_converged_integral_sooner():
+    # the length / (b + distance) panel rule in a medium without guided modes (greedy=True), against
+    # converged mode on a narrow three-disc layout: at 768 nodes it is at the converged integral
+    # while the geometric grading still misses by 1e-7; at 256 nodes (7 panels a side) they agree
+    m = medium()
+    c = np.array([[0.1, -0.6], [-0.7, -1.2], [0.8, -1.0]])
+    src, tg = np.array([0.3, 0.5]), np.array([[0.0, 0.8], [1.0, 1.5], [-2.0, 0.3]])
+    p, b, t_max = 3, 0.2, 60.0
+    lam, wt = O.contour(256, m.k1, m.k2, m.k3, b, t_max)
+    _, uc = O.converged_solution(O.Problem(m, p, c, lam, wt), src, tg, b, t_max)
+    err = {}
+    for ns, g in ((256, False), (256, True), (768, False), (768, True)):
+        lam, wt = O.contour(ns, m.k1, m.k2, m.k3, b, t_max, greedy=g)
+        pr = O.Problem(m, p, c, lam, wt)
+        u = pr.field_layer1(src, pr.solve_dense(src), tg, "scattered")
+        err[(ns, g)] = np.linalg.norm(u - uc) / np.linalg.norm(uc)
+    assert err[(768, True)] < 1e-10 < 1e-8 < err[(768, False)]
+    assert abs(err[(256, True)] - err[(256, False)]) < 1e-2 * err[(256, False)]

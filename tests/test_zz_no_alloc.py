@@ -7,8 +7,8 @@ output must match the context entry point lsms_translate(..., LSMS_MIXED) within
 mixed-operator parity tests use, on consecutive calls (the scratch array keeps the previous call's
 contents, so a second call with other inputs checks that nothing stale leaks through).
 
-This file is collected after the other parity files (only the order-range edges,
-test_zzz_orders_gpu.py, come later): a run that stops at the first failure has then already run
+This file is collected after the other parity files (only test_zzz_contour_rule_gpu.py and
+test_zzz_orders_gpu.py come later): a run that stops at the first failure has then already run
 them.
 """
 import numpy as np
