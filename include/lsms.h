@@ -318,7 +318,8 @@ int lsms_inclusion_scattering_matrix(int p, double k2, double kp, double radius,
  *   interior kernels of Muller's system, their J_0, J_1, Y_0, Y_1 at complex argument from
  *   Miller's backward recurrence and Neumann's expansions.  The product rule's log part grows like
  *   exp(Im kp r) along the curve, so accuracy falls off as about 1e-16 exp(2 Im kp R): kp_im * 2R
- *   must be <= 12 (1e-10 or better).  kp_im = 0 is lsms_inclusion_scattering_matrix.
+ *   must be <= 12 (1e-10 or better), and |kp| * 2R <= 1e4.  kp_im = 0 is
+ *   lsms_inclusion_scattering_matrix.
  *   Errors: as above, LSMS_ERR_ARG also for a loss beyond that bound. */
 int lsms_inclusion_scattering_matrix_c(int p, double k2, double kp_re, double kp_im, double radius, int n_pts,
                                        const double* curve, double* s_out);

@@ -259,13 +259,16 @@ extern "C" int lsms_inclusion_scattering_matrix(int p, double k2, double kp, dou
 // Muller system and product rule; Im kp = 0 is the call above.  The log part of Kress's split is
 // J_0(kp r), J_1(kp r) over the whole curve, which grows like exp(Im kp r): the product rule and
 // H = J + iY then lose about exp(Im kp * 2R) * 1e-16, hence Im kp * 2R <= 12 (1e-10 and better).
+// |kp| * 2R <= 1e4 bounds the recurrence length (no curve of at most 4096 points resolves more).
 extern "C" int lsms_inclusion_scattering_matrix_c(int p, double k2, double kp_re, double kp_im, double radius,
                                                   int n_pts, const double* curve, double* s_out) {
   if (!inclusion_args_ok(p, k2, radius, n_pts, curve, s_out) || !std::isfinite(kp_re) || !std::isfinite(kp_im) ||
-      kp_re < 0.0 || kp_im < 0.0 || !(std::hypot(kp_re, kp_im) > 0.0) || kp_im * 2.0 * radius > 12.0)
+      kp_re < 0.0 || kp_im < 0.0 || !(std::hypot(kp_re, kp_im) > 0.0) || kp_im * 2.0 * radius > 12.0 ||
+      std::hypot(kp_re, kp_im) * 2.0 * radius > 1e4)
     return ctx_fail(nullptr, LSMS_ERR_ARG,
                     "inclusion_scattering_matrix_c: need 0 <= p <= 15, k2, radius > 0, Re kp >= 0, Im kp >= 0, "
-                    "kp != 0, Im kp * 2 radius <= 12, an even n_pts in [8, 4096], curve and output");
+                    "kp != 0, Im kp * 2 radius <= 12, |kp| * 2 radius <= 1e4, an even n_pts in [8, 4096], "
+                    "curve and output");
   if (kp_im == 0.0) return lsms_inclusion_scattering_matrix(p, k2, kp_re, radius, n_pts, curve, s_out);
   std::vector<cplx> S;
   std::string err;

@@ -205,7 +205,7 @@ def test_library_absorbing_inclusion_arguments(lib):
     k2 = inputs.MEDIUM["k2"]
     real = lib.inclusion_scattering_matrix(6, k2, 7.5, 0.25, cur)
     assert np.array_equal(lib.inclusion_scattering_matrix(6, k2, 7.5 + 0j, 0.25, cur), real)
-    for bad in (7.5 - 0.1j, -1 + 1j, 0j, complex(7.5, np.nan), 3 + 24.1j):      # 24.1 * 0.5 > 12
+    for bad in (7.5 - 0.1j, -1 + 1j, 0j, complex(7.5, np.nan), 3 + 24.1j, 2.1e4 + 1j):  # Im: 24.1 * 0.5 > 12
         with pytest.raises(lib.LsmsError):
             lib.inclusion_scattering_matrix(6, k2, bad, 0.25, cur)
 
