@@ -47,7 +47,7 @@ def test_greedy_panel_rule_parity(L):
         ctx.set_particles(c)
         beta = inputs.random_coefficients(w.n, w.p, 1, 91) / hs[None, None, :]
         assert rel(ctx.apply(beta)[0], pr.apply(beta[0]), hs) < TOL64
-        b_l, info = ctx.solve(w.sources, tol=1e-12, maxiter=400)
+        b_l, info = ctx.solve(w.sources, tol=1e-12, maxiter=1000)
         assert info["status"] == 0
         b_o = pr.solve_dense(w.sources[0])
         assert rel(b_l[0], b_o, hs[None, :]) < TOL64

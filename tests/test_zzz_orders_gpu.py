@@ -71,7 +71,7 @@ def test_operator_at_the_order_range_ends(L, case):
 def test_solve_at_the_order_range_ends(L, case):
     w, c, pr, hs, ctx = case
     src = w.sources[0]
-    beta, info = ctx.solve(w.sources, tol=1e-13, maxiter=400)
+    beta, info = ctx.solve(w.sources, tol=1e-13, maxiter=1000)
     assert info["status"] == 0
     b_o = pr.solve_dense(src)
     assert rel(beta[0], b_o, hs) < TOL64
