@@ -346,6 +346,14 @@ int lsms_pec_scattering_diagonal(int p, double k2, double radius, double* s_diag
  *   |kp| R > 1e5). */
 int lsms_scattering_diagonal_c(int p, double k2, double kp_re, double kp_im, double radius, double* s_diag);
 
+/* lsms_set_scattering_diagonal — replace the discs' diagonal scattering matrix S_n, n = -p..p
+ *   (s_diag: 2p + 1 complex; Sec. 3.1), e.g. by lsms_scattering_diagonal_c (absorbing discs) or
+ *   lsms_pec_scattering_diagonal (perfectly conducting discs), keeping the diagonal combine (a
+ *   dense matrix from lsms_set_scattering_matrix, while set, takes precedence).  NULL restores the
+ *   Mie diagonal of the kp given at creation.  Applies to every layout of lsms_set_layouts, now and
+ *   later.  Errors: LSMS_ERR_ARG (NULL ctx, a non-finite entry), LSMS_ERR_CUDA. */
+int lsms_set_scattering_diagonal(lsms_ctx* ctx, const double* s_diag);
+
 /* lsms_set_fmm — translate through boxes for long layouts of many discs (the FMM acceleration named
  *   in Sec. 3.2; the multipole shifts of Sec. 5.3).  Discs are grouped into boxes of width
  *   box_width along x (centres at the disc layer's mid-height); pairs in the same or adjacent boxes

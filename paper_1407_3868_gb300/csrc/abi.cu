@@ -613,6 +613,40 @@ extern "C" int lsms_get_scattering(const lsms_ctx* c, double* s) {
   }
   return LSMS_OK;
 }
+// Replace the diagonal scattering matrix (absorbing or perfectly conducting discs, Sec. 3.1) in
+// place: the host copy and the device table [S_n; |H_n(k2 R)| S_n] read by the combine and the
+// right-hand side; NULL restores the Mie diagonal of the context's kp.
+extern "C" int lsms_set_scattering_diagonal(lsms_ctx* c, const double* s) {
+  if (!c) return LSMS_ERR_ARG;
+  const int P = c->P;
+  std::vector<cplx> S(P);
+  if (s) {
+    std::memcpy(static_cast<void*>(S.data()), s, P * sizeof(cplx));
+    for (const cplx& v : S)
+      if (!std::isfinite(v.real()) || !std::isfinite(v.imag()))
+        return fail(c, LSMS_ERR_ARG, "set_scattering_diagonal: non-finite entry");
+  } else {
+    S = mie_diagonal(c->p, c->k2, c->kp, c->R);
+  }
+  cudaStreamSynchronize(c->stream);
+  if (c->side) cudaStreamSynchronize(c->side);
+  batch_clear_graphs(c);
+  std::vector<cplx> s_out(2 * P);
+  for (int q = 0; q < P; ++q) {
+    s_out[q] = S[q];
+    s_out[P + q] = c->hscale[q] * S[q];
+  }
+  if (cudaMemcpy(c->d_scale_out, s_out.data(), s_out.size() * sizeof(cplx), cudaMemcpyHostToDevice) != cudaSuccess)
+    return check_cuda(c, "set_scattering_diagonal");
+  c->S = S;
+  c->custom_diag = s != nullptr;
+  for (lsms_ctx* k : c->kids) {
+    const int rc = lsms_set_scattering_diagonal(k, s);
+    if (rc) return fail(c, rc, std::string("set_scattering_diagonal: ") + k->err);
+  }
+  return LSMS_OK;
+}
+
 extern "C" int lsms_num_nodes(const lsms_ctx* c) { return c ? c->ns : LSMS_ERR_ARG; }
 extern "C" int lsms_num_particles(const lsms_ctx* c) { return c ? c->n : LSMS_ERR_ARG; }
 

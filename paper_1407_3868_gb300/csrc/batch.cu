@@ -65,6 +65,11 @@ extern "C" int lsms_set_layouts(lsms_ctx* c, int n_layouts, const int* counts, c
     k->fmm.box_width = c->fmm.box_width;
     k->fmm.order_req = c->fmm.order_req;
     c->kids.push_back(k);
+    if (c->custom_diag && (rc = lsms_set_scattering_diagonal(k, reinterpret_cast<const double*>(c->S.data())))) {
+      const std::string m = k->err;
+      batch_free(c);
+      return ctx_fail(c, rc, "set_layouts: layout " + std::to_string(l) + ": " + m);
+    }
     if (c->dense && (rc = lsms_set_scattering_matrix(k, reinterpret_cast<const double*>(c->smat.data())))) {
       const std::string m = k->err;
       batch_free(c);

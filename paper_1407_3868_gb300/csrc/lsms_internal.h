@@ -81,7 +81,8 @@ struct lsms_ctx {
   lsms_contour contour{};
   int ns = 0;
   NodeTables nodes;
-  std::vector<cplx> S;              // Mie diagonal, P
+  std::vector<cplx> S;              // Mie diagonal, P (or the caller's, custom_diag)
+  bool custom_diag = false;         // S set by lsms_set_scattering_diagonal
   // inclusions of another shape (Sec. 4.1): a dense prototype matrix S[l][n] and per-particle angles
   bool dense = false;
   std::vector<cplx> smat;           // [P][P]

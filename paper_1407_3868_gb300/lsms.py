@@ -27,7 +27,7 @@ APPLY_SCALED, APPLY_MIXED, APPLY_NO_TRANSLATION, APPLY_NO_REFLECTION, APPLY_ALPH
 FIELD_TOTAL, FIELD_SCATTERED, FIELD_PARTICLE = 0, 1, 2
 STATUS = {0: "OK", -1: "ARG", -2: "GEOMETRY", -3: "NOT_CONVERGED", -4: "NONFINITE", -5: "OOM",
           -6: "CUDA", -7: "STATE"}
-EXPORTS = ["lsms_create", "lsms_layer_response", "lsms_build_contour_stack", "lsms_fma_probe", "lsms_pec_scattering_diagonal", "lsms_scattering_diagonal_c", "lsms_inclusion_scattering_matrix_c", "lsms_set_fmm", "lsms_get_fmm", "lsms_fmm_stats", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
+EXPORTS = ["lsms_create", "lsms_layer_response", "lsms_build_contour_stack", "lsms_fma_probe", "lsms_pec_scattering_diagonal", "lsms_scattering_diagonal_c", "lsms_set_scattering_diagonal", "lsms_inclusion_scattering_matrix_c", "lsms_set_fmm", "lsms_get_fmm", "lsms_fmm_stats", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
            "lsms_get_scattering_matrix", "lsms_inclusion_scattering_matrix", "lsms_set_particles", "lsms_apply", "lsms_apply_ex", "lsms_apply_dev",
            "lsms_translate", "lsms_aggregate", "lsms_reflect", "lsms_disaggregate", "lsms_incident",
            "lsms_get_contour", "lsms_get_scattering", "lsms_num_nodes", "lsms_num_particles",
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsms_inclusion_scattering_matrix": (i, [i, d, d, d, i, _D, _D]),
         "lsms_pec_scattering_diagonal": (i, [i, d, d, _D]),
         "lsms_scattering_diagonal_c": (i, [i, d, d, d, d, _D]),
+        "lsms_set_scattering_diagonal": (i, [_P, _D]),
         "lsms_inclusion_scattering_matrix_c": (i, [i, d, d, d, d, i, _D, _D]),
         "lsms_fma_probe": (i, [i, _D]),
         "lsms_apply": (i, [_P, i, _D, _D]),
@@ -233,6 +234,12 @@ class Context:
             return
         s = _c128(smat, (self.P, self.P))
         self._check(self.lib.lsms_set_scattering_matrix(self.h, _dptr(s)))
+
+    def set_scattering_diagonal(self, s=None):
+        """lsms_set_scattering_diagonal: S_n (2p + 1 complex) of every disc, or None for the Mie
+        diagonal of the context's kp."""
+        sd = None if s is None else _c128(s, (self.P,))
+        self._check(self.lib.lsms_set_scattering_diagonal(self.h, _dptr(sd)))
 
     def set_orientations(self, theta=None):
         """Rotation angles of the particles (None: all zero)."""

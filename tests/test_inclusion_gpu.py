@@ -181,15 +181,46 @@ def test_absorbing_discs(L, small, loss):
     s_abs = L.scattering_diagonal(w.p, m["k2"], kp, m["radius"])
     pr = O.Problem(medium_of(w), w.p, small.c, small.lam, small.wt,
                    smat=np.diag(O.mie_coefficients(w.p, m["k2"], kp, m["radius"])))
+    b_o = pr.solve_dense(w.sources[0])
+    u_o = pr.field_layer1(w.sources[0], b_o, w.targets, "scattered")
     with L.context_for(w) as ctx:
         ctx.set_particles(small.c)
         ctx.set_scattering_matrix(np.diag(s_abs))
-        beta, info = ctx.solve(w.sources, tol=1e-12, maxiter=400)
+        beta, info = ctx.solve(w.sources, tol=1e-12, maxiter=1000)
         assert info["status"] == 0
-        b_o = pr.solve_dense(w.sources[0])
         assert rel(beta[0], b_o, small.hs[None, :]) < TOL64
-        u = ctx.eval_field(w.targets, 0, L.FIELD_SCATTERED)
-        assert rel(u, pr.field_layer1(w.sources[0], b_o, w.targets, "scattered")) < TOL64
+        assert rel(ctx.eval_field(w.targets, 0, L.FIELD_SCATTERED), u_o) < TOL64
+        # the same diagonal through lsms_set_scattering_diagonal (the diagonal combine)
+        ctx.set_scattering_matrix(None)
+        ctx.set_scattering_diagonal(s_abs)
+        assert np.array_equal(ctx.scattering(), s_abs)
+        beta, info = ctx.solve(w.sources, tol=1e-12, maxiter=1000)
+        assert info["status"] == 0
+        assert rel(beta[0], b_o, small.hs[None, :]) < TOL64
+        assert rel(ctx.eval_field(w.targets, 0, L.FIELD_SCATTERED), u_o) < TOL64
+        ctx.set_scattering_diagonal(None)                 # back to the lossless Mie diagonal
+        assert np.allclose(ctx.scattering(), O.mie_coefficients(w.p, m["k2"], m["kp"], m["radius"]),
+                           rtol=1e-11, atol=0)
+
+
+def test_absorbing_diagonal_reaches_every_layout(L, small):
+    # a batch of two layouts created after lsms_set_scattering_diagonal carries the diagonal
+    base = small.w
+    m = base.medium
+    kp = m["kp"] + 0.5j
+    s_abs = L.scattering_diagonal(base.p, m["k2"], kp, m["radius"])
+    lay = [inputs.layout(9, -2.0, 2.0, 31), inputs.layout(14, -3.0, 3.0, 32)]
+    x = inputs.random_coefficients(23, base.p, 1, 12)[0] / small.hs[None, :]
+    with L.context_for(base) as ctx:
+        ctx.set_scattering_diagonal(s_abs)
+        ctx.set_layouts(lay)
+        y = ctx.apply(x).reshape(23, -1)
+        off = 0
+        for l, c in enumerate(lay):
+            pr = O.Problem(medium_of(base), base.p, c, small.lam, small.wt,
+                           smat=np.diag(O.mie_coefficients(base.p, m["k2"], kp, m["radius"])))
+            assert rel(y[off:off + len(c)], pr.apply(x[off:off + len(c)]), small.hs) < TOL64, l
+            off += len(c)
 
 
 def test_absorbing_rotated_inclusions(L, small):
