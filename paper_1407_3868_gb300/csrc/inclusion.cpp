@@ -17,7 +17,9 @@
 //   beta_l = (i/4) int [J_l(k2 |y|) e^{-i l theta_y} sigma + n_y . grad(J_l e^{-i l theta}) mu] ds_y.
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -84,6 +86,87 @@ void bessel01(cplx z, cplx& j0, cplx& j1, cplx& h0, cplx& h1) {
   j1 = J[1];
   h0 = j0 + cplx(0.0, 1.0) * y0;
   h1 = j1 + cplx(0.0, 1.0) * y1;
+}
+
+// a x = b for the dense Muller system (n up to 8192 unknowns, nrhs = 2p + 1): right-looking blocked
+// LU with partial pivoting on the augmented rows [a | b].  Each step factors a panel of NB columns
+// over the full height, forward-substitutes its block row, and updates the trailing rows in
+// parallel (row chunks over threads: the O(n^3) part); back substitution follows.  The solution
+// overwrites b.  False for a singular matrix.
+bool solve_blocked(const std::vector<cplx>& a, int n, std::vector<cplx>& b, int nrhs) {
+  constexpr int NB = 64;
+  const int nc = n + nrhs;
+  std::vector<cplx> m((size_t)n * nc);
+  for (int i = 0; i < n; ++i) {
+    std::copy(a.begin() + (size_t)i * n, a.begin() + (size_t)(i + 1) * n, m.begin() + (size_t)i * nc);
+    std::copy(b.begin() + (size_t)i * nrhs, b.begin() + (size_t)(i + 1) * nrhs, m.begin() + (size_t)i * nc + n);
+  }
+  auto row = [&](int i) { return m.data() + (size_t)i * nc; };
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int nthreads = (int)std::max(1u, std::min(hw ? hw : 4u, 16u));
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int k1 = std::min(n, k0 + NB);
+    for (int k = k0; k < k1; ++k) {                      // panel: columns k0 .. k1 - 1
+      int piv = k;
+      for (int i = k + 1; i < n; ++i)
+        if (std::abs(row(i)[k]) > std::abs(row(piv)[k])) piv = i;
+      if (std::abs(row(piv)[k]) == 0.0) return false;
+      if (piv != k) std::swap_ranges(row(k), row(k) + nc, row(piv));
+      const cplx inv = 1.0 / row(k)[k];
+      for (int i = k + 1; i < n; ++i) {
+        cplx* ri = row(i);
+        const cplx f = ri[k] * inv;
+        ri[k] = f;                                       // multiplier, kept as L
+        if (f == cplx(0, 0)) continue;
+        const cplx* rk = row(k);
+        for (int j = k + 1; j < k1; ++j) ri[j] -= f * rk[j];
+      }
+    }
+    for (int k = k0; k < k1; ++k)                        // block row of U (and of the rhs)
+      for (int i = k + 1; i < k1; ++i) {
+        const cplx f = row(i)[k];
+        if (f == cplx(0, 0)) continue;
+        cplx* ri = row(i);
+        const cplx* rk = row(k);
+        for (int j = k1; j < nc; ++j) ri[j] -= f * rk[j];
+      }
+    const int rows = n - k1;                             // trailing update, rows k1 .. n - 1
+    if (rows <= 0) continue;
+    auto update = [&](int r0, int r1) {
+      for (int i = r0; i < r1; ++i) {
+        cplx* ri = row(i);
+        for (int k = k0; k < k1; ++k) {
+          const cplx f = ri[k];
+          if (f == cplx(0, 0)) continue;
+          const cplx* rk = row(k);
+          for (int j = k1; j < nc; ++j) ri[j] -= f * rk[j];
+        }
+      }
+    };
+    const int nt = std::min(nthreads, std::max(1, rows / 32));
+    if (nt == 1) {
+      update(k1, n);
+    } else {
+      std::vector<std::thread> pool;
+      const int chunk = (rows + nt - 1) / nt;
+      for (int t = 1; t < nt; ++t) {
+        const int r0 = k1 + t * chunk, r1 = std::min(n, r0 + chunk);
+        if (r0 < r1) pool.emplace_back(update, r0, r1);
+      }
+      update(k1, std::min(n, k1 + chunk));
+      for (std::thread& th : pool) th.join();
+    }
+  }
+  for (int k = n - 1; k >= 0; --k) {                     // back substitution on the rhs columns
+    cplx* rk = row(k);
+    for (int r = 0; r < nrhs; ++r) {
+      cplx s = rk[n + r];
+      for (int i = k + 1; i < n; ++i) s -= rk[i] * row(i)[n + r];
+      rk[n + r] = s / rk[k];
+    }
+  }
+  for (int i = 0; i < n; ++i) std::copy(row(i) + n, row(i) + nc, b.begin() + (size_t)i * nrhs);
+  return true;
 }
 
 // the four kernels for one wavenumber (real, or complex for an absorbing interior) and one (i, j)
@@ -160,43 +243,57 @@ int inclusion_matrix_t(int p, double k2, K kp, double radius, int n_pts, const d
   const int N2 = 2 * n;
   std::vector<cplx> A((size_t)N2 * N2, cplx(0, 0));
   const K dk2 = k2 * k2 - kp * kp;
-  for (int i = 0; i < n; ++i) {
-    const double nx[2] = {nux[i] / sp[i], nuy[i] / sp[i]};
-    for (int j = 0; j < n; ++j) {
-      cplx ms, md, mn, mt;
-      K m1s, m1d, m1n, m1t;
-      double L = 0.0;
-      if (i == j) {
-        m1s = m1d = m1n = 0.0;
-        m1t = -dk2 * sp[i] / (8.0 * kPi);
-        if constexpr (std::is_same_v<K, double>)
-          ms = cplx(-(sp[i] / (2.0 * kPi)) * std::log(k2 / kp), 0.0);
-        else
-          ms = -(sp[i] / (2.0 * kPi)) * std::log(k2 / kp);
-        md = mn = cplx(0, 0);
-        mt = sp[i] * (cplx((1.0 - 2.0 * kEuler) / (8.0 * kPi), 0.125) * dk2 -
-                      (k2 * k2 * std::log(k2 * sp[i] / 2.0) - kp * kp * std::log(kp * sp[i] / 2.0)) /
-                          (4.0 * kPi));
-      } else {
-        const double dxy[2] = {x[i] - x[j], y[i] - y[j]};
-        const double r = std::hypot(dxy[0], dxy[1]);
-        const double nuj[2] = {nux[j], nuy[j]};
-        const Kernels<double> a = kernels(k2, dxy, r, nx, nuj, sp[j]);
-        const Kernels<K> b = kernels(kp, dxy, r, nx, nuj, sp[j]);
-        const double sn = std::sin(0.5 * h * (i - j));
-        L = std::log(4.0 * sn * sn);
-        m1s = a.s1 - b.s1; m1d = a.d1 - b.d1; m1n = a.n1 - b.n1; m1t = a.t1 - b.t1;
-        ms = (a.s - b.s) - m1s * L;
-        md = (a.d - b.d) - m1d * L;
-        mn = (a.nn - b.nn) - m1n * L;
-        mt = (a.t - b.t) - m1t * L;
+  auto assemble_rows = [&](int i0, int i1) {             // rows i and n + i for i in [i0, i1)
+    for (int i = i0; i < i1; ++i) {
+      const double nx[2] = {nux[i] / sp[i], nuy[i] / sp[i]};
+      for (int j = 0; j < n; ++j) {
+        cplx ms, md, mn, mt;
+        K m1s, m1d, m1n, m1t;
+        double L = 0.0;
+        if (i == j) {
+          m1s = m1d = m1n = 0.0;
+          m1t = -dk2 * sp[i] / (8.0 * kPi);
+          if constexpr (std::is_same_v<K, double>)
+            ms = cplx(-(sp[i] / (2.0 * kPi)) * std::log(k2 / kp), 0.0);
+          else
+            ms = -(sp[i] / (2.0 * kPi)) * std::log(k2 / kp);
+          md = mn = cplx(0, 0);
+          mt = sp[i] * (cplx((1.0 - 2.0 * kEuler) / (8.0 * kPi), 0.125) * dk2 -
+                        (k2 * k2 * std::log(k2 * sp[i] / 2.0) - kp * kp * std::log(kp * sp[i] / 2.0)) /
+                            (4.0 * kPi));
+        } else {
+          const double dxy[2] = {x[i] - x[j], y[i] - y[j]};
+          const double r = std::hypot(dxy[0], dxy[1]);
+          const double nuj[2] = {nux[j], nuy[j]};
+          const Kernels<double> a = kernels(k2, dxy, r, nx, nuj, sp[j]);
+          const Kernels<K> b = kernels(kp, dxy, r, nx, nuj, sp[j]);
+          const double sn = std::sin(0.5 * h * (i - j));
+          L = std::log(4.0 * sn * sn);
+          m1s = a.s1 - b.s1; m1d = a.d1 - b.d1; m1n = a.n1 - b.n1; m1t = a.t1 - b.t1;
+          ms = (a.s - b.s) - m1s * L;
+          md = (a.d - b.d) - m1d * L;
+          mn = (a.nn - b.nn) - m1n * L;
+          mt = (a.t - b.t) - m1t * L;
+        }
+        const double rw = Rw[((i - j) % n + n) % n];
+        A[(size_t)i * N2 + j] = rw * m1d + h * md + (i == j ? 1.0 : 0.0);
+        A[(size_t)i * N2 + n + j] = rw * m1s + h * ms;
+        A[(size_t)(n + i) * N2 + j] = rw * m1t + h * mt;
+        A[(size_t)(n + i) * N2 + n + j] = rw * m1n + h * mn - (i == j ? 1.0 : 0.0);
       }
-      const double rw = Rw[((i - j) % n + n) % n];
-      A[(size_t)i * N2 + j] = rw * m1d + h * md + (i == j ? 1.0 : 0.0);
-      A[(size_t)i * N2 + n + j] = rw * m1s + h * ms;
-      A[(size_t)(n + i) * N2 + j] = rw * m1t + h * mt;
-      A[(size_t)(n + i) * N2 + n + j] = rw * m1n + h * mn - (i == j ? 1.0 : 0.0);
     }
+  };
+  {                                                      // the pairs' Bessel values dominate: rows over threads
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int nt = std::max(1, std::min({(int)(hw ? hw : 4u), 16, n / 16}));
+    const int chunk = (n + nt - 1) / nt;
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) {
+      const int i0 = t * chunk, i1 = std::min(n, i0 + chunk);
+      if (i0 < i1) pool.emplace_back(assemble_rows, i0, i1);
+    }
+    assemble_rows(0, std::min(n, chunk));
+    for (std::thread& th : pool) th.join();
   }
   // right-hand sides: -u_inc, -du_inc/dn for u_inc = J_m(k2 rho) e^{i m theta}, m = -p..p
   std::vector<cplx> B((size_t)N2 * P);
@@ -212,7 +309,7 @@ int inclusion_matrix_t(int p, double k2, K kp, double radius, int n_pts, const d
       B[(size_t)(n + i) * P + m + p] = -(k2 * jmp * nr * e + cplx(0.0, m / rho[i]) * jm * nt * e);
     }
   }
-  if (!solve_small(A, N2, B, P)) { err = "singular Muller system"; return LSMS_ERR_ARG; }
+  if (!solve_blocked(A, N2, B, P)) { err = "singular Muller system"; return LSMS_ERR_ARG; }
   // beta^m_l = (i/4) h sum_j [J_l e^{-i l theta} sigma |x'| + nu . grad(J_l e^{-i l theta}) mu]
   S.assign((size_t)P * P, cplx(0, 0));
   for (int j = 0; j < n; ++j) {
