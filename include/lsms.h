@@ -308,9 +308,9 @@ int lsms_get_scattering_matrix(const lsms_ctx* ctx, double* s);
  *   curve: [n_pts][6] doubles x, y, x', y', x'', y'' at t_j = 2 pi j / n_pts of a smooth closed
  *   curve run counterclockwise, coordinates relative to the enclosing disc's centre; n_pts even,
  *   8 <= n_pts <= 4096 (about 256 gives 1e-13 for the shapes of Sec. 6); radius: the enclosing
- *   disc's.  s_out: [P][P] complex as for lsms_set_scattering_matrix.  O(n_pts^3) host work, spread over the host's
- *   threads (assembly by rows, blocked LU with a parallel trailing update: 1.5 s at 1024 points
- *   on 8 cores).
+ *   disc's.  s_out: [P][P] complex as for lsms_set_scattering_matrix.  O(n_pts^3) host work,
+ *   spread over the host's threads (assembly by rows, blocked LU with a parallel trailing update:
+ *   1.5 s at 1024 points on 8 cores).
  *   Errors: LSMS_ERR_ARG (arguments, a clockwise or degenerate curve, a singular system),
  *   LSMS_ERR_GEOMETRY (a point outside the enclosing disc or at its centre). */
 int lsms_inclusion_scattering_matrix(int p, double k2, double kp, double radius, int n_pts,
