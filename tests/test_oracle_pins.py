@@ -717,6 +717,25 @@ def test_energy_balance_with_absorbing_discs(kp):
     assert np.abs(lossless.absorbed_power(src, lossless.solve_dense(src))).max() < 1e-14
 
 
+def test_energy_balance_with_perfectly_conducting_discs():
+    # PEC discs absorb nothing: radiation through y = +-inf equals the source's power (2e-13), each
+    # disc's absorbed power vanishes, and a sign slip in the PEC coefficients breaks the balance
+    m = medium()
+    c = np.array([[0.1, -0.6], [-0.7, -1.2], [0.8, -1.0]])
+    src = np.array([0.3, 0.5])
+    lam, wt = O.contour(2048, m.k1, m.k2, m.k3, 0.2, 60.0)
+    for sign, ok in ((1.0, True), (-1.0, False)):
+        pr = O.Problem(m, 8, c, lam, wt, smat=np.diag(sign * O.pec_coefficients(8, m.k2, m.radius)))
+        beta = pr.solve_dense(src)
+        up, down = pr.outgoing_power(src, beta)
+        total = 0.25 + pr.field_layer1(src, beta, src[None, :], "scattered")[0].imag
+        if ok:
+            assert abs(up + down - total) < 1e-11 * total
+            assert np.abs(pr.absorbed_power(src, beta)).max() < 1e-14
+        else:
+            assert abs(up + down - total) > 1e-1 * total
+
+
 @pytest.mark.parametrize("loss", [0.5, 2.0])
 def test_energy_balance_with_an_absorbing_substrate(loss):
     # lossless layers 1 and 2 and discs over an absorbing half-space: the source's power
