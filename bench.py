@@ -54,6 +54,14 @@ TRAFFIC = {
 KERNEL_SOURCES = ("mixed.cu", "ff_hankel.cuh")
 
 
+def translation_flop(n, p, nrhs=1):
+    """Algorithmic FLOP of one all-pairs translation (Lemma 3.1): every ordered pair of distinct
+    discs applies a P x P Toeplitz block to each right-hand side, 8 real flop per complex
+    multiply-add."""
+    P = 2 * p + 1
+    return 8.0 * P * P * n * (n - 1) * nrhs
+
+
 def max_over_ranks(vals, world, device):
     """Element-wise maximum of per-rank timings: the slowest replica sets the job's time."""
     import torch
@@ -282,8 +290,7 @@ def run_ours(args, rank, world, local_rank):
     e2e = job_rate(args.steps, world, 1e3 * max_over_ranks([e2e_s], world, dev)[0])
 
     # roofline of the dominant kernel (the FP32 translation)
-    pairs = n * (n - 1)
-    flop = 8.0 * P * P * pairs
+    flop = translation_flop(n, w.p)
     tr_ms = statistics.mean(t_tr_mixed)
     achieved = flop / (tr_ms / 1e3) / 1e12
     tr64_ms = statistics.mean(t_tr_fp64)
@@ -428,7 +435,7 @@ def run_batched(args, dev, flush):
     y = torch.empty_like(x)
     fl_m = lsms.APPLY_SCALED | lsms.APPLY_MIXED
     P = 2 * w.p + 1
-    flop = 8.0 * P * P * w.n * (w.n - 1) * nrhs
+    flop = translation_flop(w.n, w.p, nrhs)
     blk = {"workload": w.name, "discs": w.n, "p": w.p, "contour_nodes": w.n_nodes, "rhs": nrhs}
     for tcmin, key in ((48, "mixed"), (0, "mixed_cuda_cores")):
         ctx.set_tc_translation(tcmin)

@@ -45,3 +45,16 @@ def test_a_failing_further_workload_keeps_the_headline(capsys):
     out = bench.guarded("example1", boom)
     assert out == {"error": "RuntimeError: no convergence"}
     assert "section example1 failed" in capsys.readouterr().err
+
+
+def test_roofline_arithmetic():
+    # the headline kernel's algorithmic work: 5000 discs, p = 14 (P = 29): 8 P^2 N (N - 1) flop per
+    # translation = 1.68e11; the derived FP32 peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.translation_flop(5000, 14) == 8 * 29 * 29 * 5000 * 4999 == 168166360000
+    assert bench.translation_flop(2000, 12, 64) == 8 * 25 * 25 * 2000 * 1999 * 64
+    assert bench.translation_flop(1, 14) == 0
+    assert abs(bench.FP32_PEAK_TFLOPS - 80.54784) < 1e-9
