@@ -92,8 +92,9 @@ void bessel01(cplx z, cplx& j0, cplx& j1, cplx& h0, cplx& h1) {
 // LU with partial pivoting on the augmented rows [a | b].  Each step factors a panel of NB columns
 // over the full height, forward-substitutes its block row, and updates the trailing rows in
 // parallel (row chunks over threads: the O(n^3) part); back substitution follows.  The solution
-// overwrites b.  False for a singular matrix.
-bool solve_blocked(const std::vector<cplx>& a, int n, std::vector<cplx>& b, int nrhs) {
+// overwrites b; a is released once copied (the augmented rows replace it).  False for a singular
+// matrix.
+bool solve_blocked(std::vector<cplx>& a, int n, std::vector<cplx>& b, int nrhs) {
   constexpr int NB = 64;
   const int nc = n + nrhs;
   std::vector<cplx> m((size_t)n * nc);
@@ -101,6 +102,7 @@ bool solve_blocked(const std::vector<cplx>& a, int n, std::vector<cplx>& b, int 
     std::copy(a.begin() + (size_t)i * n, a.begin() + (size_t)(i + 1) * n, m.begin() + (size_t)i * nc);
     std::copy(b.begin() + (size_t)i * nrhs, b.begin() + (size_t)(i + 1) * nrhs, m.begin() + (size_t)i * nc + n);
   }
+  std::vector<cplx>().swap(a);
   auto row = [&](int i) { return m.data() + (size_t)i * nc; };
   const unsigned hw = std::thread::hardware_concurrency();
   const int nthreads = (int)std::max(1u, std::min(hw ? hw : 4u, 16u));
