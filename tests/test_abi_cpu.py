@@ -373,3 +373,22 @@ def test_library_inclusion_matrix_on_random_shapes(lib):
         s_lib = lib.inclusion_scattering_matrix(p, k2, kp, 0.25, cur)
         s_o = O.inclusion_scattering_matrix(cur, p, k2, kp)
         assert np.abs(s_lib - s_o).max() < 1e-12 * np.abs(s_o).max(), (a1, a2, a3, k2, kp, p)
+
+
+def test_library_absorbing_inclusion_matrix_on_random_shapes(lib):
+    # random star-shaped inclusions and random lossy interiors up to the loss bound
+    # (Im k_p * 2R <= 12, R = 0.25): the library's complex-argument Bessel functions in the Nystrom
+    # solve against the oracle's (AMOS)
+    rng = np.random.default_rng(12)
+    for _ in range(5):
+        a1 = float(rng.uniform(0.08, 0.15))
+        a2 = float(rng.uniform(0.0, 0.4 * a1))
+        a3 = int(rng.integers(2, 7))
+        off = rng.uniform(-0.03, 0.03, 2)
+        k2 = float(rng.uniform(2.0, 12.0))
+        kp = complex(rng.uniform(0.5, 15.0), rng.uniform(0.01, 23.0))
+        p = int(rng.integers(4, 12))
+        cur = inputs.star_curve(a1, a2, a3, 128, rotation=float(rng.uniform(0, 6.3)), centre=off)
+        s_lib = lib.inclusion_scattering_matrix(p, k2, kp, 0.25, cur)
+        s_o = O.inclusion_scattering_matrix(cur, p, k2, kp)
+        assert np.abs(s_lib - s_o).max() < 1e-12 * np.abs(s_o).max(), (a1, a2, a3, k2, kp, p)
