@@ -903,6 +903,70 @@ class Problem:
             out[:, j] = self.apply(e).ravel()
         return out
 
+    def operator_rows(self, rows):
+        """Rows of the same matrix for the target particles `rows`, shape (len(rows) P, N P),
+        written from the formulas instead of column by column (which costs N P applications):
+
+        * T: for every source m != l the block T^{lm}[nu][n] = H_{n-nu}(k2 rho) e^{i (n-nu) phi}
+          of Lemma 3.1 (rho, phi of x_l - x_m), from one table of H_s e^{i s phi} per target as in
+          `translate`;
+        * R: aggregate (Theorem 5.2) -> per-node layer response (Eq. "sommerfeldsys") ->
+          disaggregate (Lemma 5.1), each written as a matrix.  The layer response is linear in
+          (P+, Q-) node by node; its coefficients are the densities for a unit P+ and for a unit
+          Q-;
+        * then the rows of x - S (T + R) x.
+
+        Equal to the rows of `dense_operator()` (pinned on small cases)."""
+        rows = list(rows)
+        N, P, p = self.N, self.P, self.p
+        k2, d = self.m.k2, self.m.d
+        nr = len(rows)
+        tr = np.zeros((nr, P, N, P), dtype=complex)          # [r, nu, m, n] of (T + R)
+        s_all = np.arange(-2 * p, 2 * p + 1)
+        idx = self.orders[None, :] - self.orders[:, None] + 2 * p   # [nu, n] -> n - nu + 2p
+        for r, l in enumerate(rows):
+            m = np.array([j for j in range(N) if j != l], dtype=int)
+            if m.size == 0:
+                continue
+            dxy = self.c[l][None, :] - self.c[m]
+            rho = np.hypot(dxy[:, 0], dxy[:, 1])
+            phi = np.arctan2(dxy[:, 1], dxy[:, 0])
+            h = hankel(s_all[None, :], k2 * rho[:, None]) * np.exp(1j * s_all[None, :] * phi[:, None])
+            tr[r][:, m, :] = np.transpose(h[:, idx], (1, 0, 2))
+        tr = tr.reshape(nr * P, N * P)
+        if N:
+            lam = self.lam
+            g2 = gamma(lam, k2)
+            x, y = self.c[:, 0], self.c[:, 1]
+            e_top = np.exp(g2[:, None] * y[None, :] - 1j * lam[:, None] * x[None, :])        # (N_S, N)
+            e_bot = np.exp(-g2[:, None] * (y[None, :] + d) - 1j * lam[:, None] * x[None, :])
+            f_top = m2s_factor(self.orders[None, :], lam[:, None], k2, above=True)           # (N_S, P)
+            f_bot = m2s_factor(self.orders[None, :], lam[:, None], k2, above=False)
+            agg_top = (e_top[:, :, None] * f_top[:, None, :]).reshape(lam.size, N * P)       # dP+/dbeta
+            agg_bot = (e_bot[:, :, None] * f_bot[:, None, :]).reshape(lam.size, N * P)       # dQ-/dbeta
+            one, zero = np.ones(lam.size, dtype=complex), np.zeros(lam.size, dtype=complex)
+            sig_p = self.layer_densities(None, one, zero)
+            sig_q = self.layer_densities(None, zero, one)
+            s2p = sig_p[:, 1][:, None] * agg_top + sig_q[:, 1][:, None] * agg_bot           # dsigma2+/dbeta
+            s2m = sig_p[:, 2][:, None] * agg_top + sig_q[:, 2][:, None] * agg_bot           # dsigma2-/dbeta
+            cr = self.c[rows]
+            q = self.wt / (FOUR_PI * g2)
+            l_top = plane_wave_local_factor(self.orders[None, :], lam[:, None], k2, downward=True)
+            l_bot = plane_wave_local_factor(self.orders[None, :], lam[:, None], k2, downward=False)
+            dt = np.exp(g2[None, :] * cr[:, 1:2] + 1j * lam[None, :] * cr[:, 0:1])         # (nr, N_S)
+            db = np.exp(-g2[None, :] * (cr[:, 1:2] + d) + 1j * lam[None, :] * cr[:, 0:1])
+            dis_top = (dt[:, None, :] * (q[:, None] * l_top).T[None, :, :]).reshape(nr * P, lam.size)
+            dis_bot = (db[:, None, :] * (q[:, None] * l_bot).T[None, :, :]).reshape(nr * P, lam.size)
+            tr += dis_top @ s2p + dis_bot @ s2m
+        tr = tr.reshape(nr, P, N * P)
+        if self.smats is None:
+            out = -self.S[None, :, None] * tr
+        else:
+            out = -np.einsum("rln,rnk->rlk", self.smats[rows], tr)
+        for r, l in enumerate(rows):
+            out[r, np.arange(P), l * P + np.arange(P)] += 1.0
+        return out.reshape(nr * P, N * P)
+
     def solve_dense(self, src):
         """beta from (I - S(T + R)) beta = S a_inc by LU, on the system equilibrated by the order
         scale D = diag(|H_n(k2 R)|) (D A D^{-1} (D beta) = D rhs: the same solution; when k2 R is
@@ -1312,3 +1376,84 @@ def gmres(matvec, b, tol=1e-12, maxiter=500):
     y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
     x = V[:k].T @ y
     return x, k, hist
+
+
+# ----------------------------------------------------------------------------------------------
+# The same sums on several host cores: target particles split into chunks across processes
+# ----------------------------------------------------------------------------------------------
+_POOL_PROBLEM = None
+
+
+def _pool_init(problem):
+    global _POOL_PROBLEM
+    _POOL_PROBLEM = problem
+
+
+def _pool_apply(task):
+    x, rows = task
+    return _POOL_PROBLEM.apply(x, rows=rows)
+
+
+def _pool_operator_rows(rows):
+    return _POOL_PROBLEM.operator_rows(rows)
+
+
+class RowPool:
+    """`Problem.apply` and `Problem.operator_rows` split over target particles in worker processes.
+
+    Each worker holds a copy of the problem and evaluates the unchanged row sums for its chunk of
+    target particles (the global aggregate and layer response are recomputed per chunk, as
+    `Problem.apply(x, rows)` does); the results are concatenated in row order, so `apply` returns
+    `problem.apply(x)` up to the rounding of the row-chunked matrix products.  Workers start with
+    the spawn method and one BLAS thread each.  Use as a context manager, or call `close()`."""
+
+    def __init__(self, problem, workers=None, chunks_per_worker=4):
+        import multiprocessing as mp
+        import os
+        self.problem = problem
+        self.workers = max(1, int(workers or os.cpu_count() or 1))
+        self.chunks = max(1, self.workers * chunks_per_worker)
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.workers, initializer=_pool_init, initargs=(problem,))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def row_chunks(self, rows=None, chunks=None):
+        rows = list(range(self.problem.N)) if rows is None else list(rows)
+        n = max(1, min(chunks or self.chunks, len(rows)))
+        return [c.tolist() for c in np.array_split(np.asarray(rows, dtype=int), n) if c.size]
+
+    def apply(self, x, rows=None, chunks=None):
+        """problem.apply(x, rows) (all rows by default), shape (len(rows), P)."""
+        x = np.asarray(x, dtype=complex).reshape(self.problem.N, self.problem.P)
+        parts = self.pool.map(_pool_apply, [(x, c) for c in self.row_chunks(rows, chunks)])
+        return np.concatenate(parts, axis=0) if parts else np.zeros((0, self.problem.P), dtype=complex)
+
+    def operator_rows(self, rows, chunks=None):
+        """problem.operator_rows(rows) assembled chunk by chunk in the workers."""
+        parts = self.pool.map(_pool_operator_rows, self.row_chunks(rows, chunks))
+        return np.concatenate(parts, axis=0)
+
+    def iter_operator_rows(self, rows=None, chunks=None):
+        """Yield (chunk rows, problem.operator_rows(chunk rows)) in row order, one chunk in memory
+        per worker at a time (for assembling a large matrix in place)."""
+        ch = self.row_chunks(rows, chunks)
+        for c, block in zip(ch, self.pool.imap(_pool_operator_rows, ch)):
+            yield c, block
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

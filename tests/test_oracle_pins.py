@@ -555,6 +555,54 @@ def test_problem_with_inclusion_matrices():
     assert np.abs(b1 - disc.solve_dense(src)).max() > 1e-3 * np.abs(b1).max()
 
 
+def test_operator_rows_are_the_dense_operator_and_solve_like_the_block_system():
+    # the row-by-row assembly (Lemma 3.1 blocks, the reflected coupling as matrices) against the
+    # column-by-column matrix of the operator, for discs, rotated inclusions and a five-layer stack;
+    # then the independent block system of Eq. "finalsys" solved by LU gives the same beta as LU on
+    # the assembled rows (a transposed T block or a dropped reflection term fails both)
+    m = O.Medium(MED["k1"], MED["k2"], MED["k3"], MED["d"], MED["kp"], MED["radius"])
+    p, src = 5, np.array([0.1, 1.0])
+    c = inputs.layout(7, -1.5, 1.5, 4)
+    lam, wt = O.contour(128, m.k1, m.k2, m.k3, 0.2, 80.0)
+    s = inputs.STAR5
+    S = O.inclusion_scattering_matrix(inputs.star_curve(s["a1"], s["a2"], s["a3"], 96), p, m.k2, m.kp)
+    st = inputs.STACK5
+    stack = O.Stack(st["ks"], st["ds"], st["layer"], MED["kp"], MED["radius"])
+    lam5, wt5 = O.contour(128, st["ks"][0], st["ks"][2], st["ks"][-1], 0.2, 80.0)
+    probs = [O.Problem(m, p, c, lam, wt),
+             O.Problem(m, p, c, lam, wt, smat=S, theta=inputs.orientations(7, 2)),
+             O.Problem(stack, p, c, lam5, wt5)]
+    for k, pr in enumerate(probs):
+        a = pr.dense_operator()
+        rows = pr.operator_rows(range(pr.N))
+        assert np.abs(rows - a).max() <= 1e-14 * np.abs(a).max(), k
+        sub = [5, 0, 6]
+        a_sub = a.reshape(pr.N, pr.P, -1)[sub].reshape(len(sub) * pr.P, -1)
+        assert np.abs(pr.operator_rows(sub) - a_sub).max() <= 1e-14 * np.abs(a).max(), k
+        if k < 2:
+            b_rows = np.linalg.solve(rows, pr.rhs(src).ravel()).reshape(pr.N, pr.P)
+            _, b_block = pr.solve_block(src)
+            assert np.abs(b_rows - b_block).max() <= 1e-11 * np.abs(b_block).max(), k
+
+
+def test_row_pool_applies_the_operator_over_target_chunks():
+    m = O.Medium(MED["k1"], MED["k2"], MED["k3"], MED["d"], MED["kp"], MED["radius"])
+    c = inputs.layout(23, -4.0, 4.0, 8)
+    lam, wt = O.contour(96, m.k1, m.k2, m.k3, 0.2, 60.0)
+    pr = O.Problem(m, 4, c, lam, wt)
+    x = inputs.random_coefficients(23, 4, 1, 3)[0]
+    y = pr.apply(x)
+    with O.RowPool(pr, workers=2, chunks_per_worker=3) as rp:
+        assert len(rp.row_chunks()) == 6
+        assert np.abs(rp.apply(x) - y).max() <= 1e-13 * np.abs(y).max()
+        rows = [22, 1, 9]
+        assert np.abs(rp.apply(x, rows=rows) - y[rows]).max() <= 1e-13 * np.abs(y).max()
+        blocks = list(rp.iter_operator_rows(chunks=4))
+        assert [r for r, _ in blocks][0][0] == 0 and sum(len(r) for r, _ in blocks) == 23
+        a = np.concatenate([b for _, b in blocks], axis=0)
+        assert np.abs(a @ x.ravel() - y.ravel()).max() <= 1e-12 * np.abs(y).max()
+
+
 # ---------------------------------------------------------------------------------------------
 # Guided-mode media (k2 > k1, k3): poles of the layer response next to the contour
 # ---------------------------------------------------------------------------------------------
