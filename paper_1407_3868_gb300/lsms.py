@@ -10,7 +10,7 @@ of layouts (set_particles, set_layouts); dense rotated scattering matrices for i
 shape (set_scattering_matrix, set_orientations; inclusion_scattering_matrix,
 pec_scattering_diagonal and, with a complex kp for absorbing particles, scattering_diagonal and
 inclusion_scattering_matrix build them on the host); the translation through boxes (set_fmm); the
-operator and its steps, solves and fields.  fma_probe measures the GPU's FMA ceilings.
+operator and its steps, solves and fields.
 """
 from __future__ import annotations
 
@@ -27,7 +27,7 @@ APPLY_SCALED, APPLY_MIXED, APPLY_NO_TRANSLATION, APPLY_NO_REFLECTION, APPLY_ALPH
 FIELD_TOTAL, FIELD_SCATTERED, FIELD_PARTICLE = 0, 1, 2
 STATUS = {0: "OK", -1: "ARG", -2: "GEOMETRY", -3: "NOT_CONVERGED", -4: "NONFINITE", -5: "OOM",
           -6: "CUDA", -7: "STATE"}
-EXPORTS = ["lsms_create", "lsms_layer_response", "lsms_build_contour_stack", "lsms_fma_probe", "lsms_pec_scattering_diagonal", "lsms_scattering_diagonal_c", "lsms_set_scattering_diagonal", "lsms_inclusion_scattering_matrix_c", "lsms_set_fmm", "lsms_get_fmm", "lsms_fmm_stats", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
+EXPORTS = ["lsms_create", "lsms_layer_response", "lsms_build_contour_stack", "lsms_pec_scattering_diagonal", "lsms_scattering_diagonal_c", "lsms_set_scattering_diagonal", "lsms_inclusion_scattering_matrix_c", "lsms_set_fmm", "lsms_get_fmm", "lsms_fmm_stats", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
            "lsms_get_scattering_matrix", "lsms_inclusion_scattering_matrix", "lsms_set_particles", "lsms_apply", "lsms_apply_ex", "lsms_apply_dev",
            "lsms_translate", "lsms_aggregate", "lsms_reflect", "lsms_disaggregate", "lsms_incident",
            "lsms_get_contour", "lsms_get_scattering", "lsms_num_nodes", "lsms_num_particles",
@@ -84,7 +84,6 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsms_scattering_diagonal_c": (i, [i, d, d, d, d, _D]),
         "lsms_set_scattering_diagonal": (i, [_P, _D]),
         "lsms_inclusion_scattering_matrix_c": (i, [i, d, d, d, d, i, _D, _D]),
-        "lsms_fma_probe": (i, [i, _D]),
         "lsms_apply": (i, [_P, i, _D, _D]),
         "lsms_apply_ex": (i, [_P, i, _D, _D, i]),
         "lsms_apply_dev": (i, [_P, i, _P, _P, i, _P]),
@@ -434,10 +433,37 @@ def translate_mixed_noalloc(centres, beta, alpha, k2, p, stream=None):
     Asynchronous on `stream` (default: torch's current stream)."""
     import torch
     lib = load()
+    p = int(p)
+    dev = torch.cuda.current_device()
+    for name, t, dt in (("centres", centres, torch.float64), ("beta", beta, torch.complex128),
+                        ("alpha", alpha, torch.complex128)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"translate_mixed_noalloc: {name} must be a torch tensor")
+        if not t.is_cuda or t.device.index != dev:
+            raise ValueError(f"translate_mixed_noalloc: {name} must be on the current CUDA device (cuda:{dev}), "
+                             f"got {t.device}")
+        if t.dtype != dt:
+            raise ValueError(f"translate_mixed_noalloc: {name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"translate_mixed_noalloc: {name} must be contiguous")
+    if centres.dim() != 2 or centres.shape[1] != 2:
+        raise ValueError(f"translate_mixed_noalloc: centres must have shape (n, 2), got {tuple(centres.shape)}")
+    n = centres.shape[0]
+    P = 2 * p + 1
+    if p < 0:
+        raise ValueError("translate_mixed_noalloc: p must be >= 0")
+    if n == 0:
+        nrhs = 0
+        if beta.numel() != 0:
+            raise ValueError("translate_mixed_noalloc: beta must be empty when there are no discs")
+    elif beta.numel() % (n * P) != 0:
+        raise ValueError(f"translate_mixed_noalloc: beta ({beta.numel()} elements) is not nrhs x {n} x {P}")
+    else:
+        nrhs = beta.numel() // (n * P)
+    if alpha.shape != beta.shape:
+        raise ValueError(f"translate_mixed_noalloc: alpha {tuple(alpha.shape)} and beta {tuple(beta.shape)} differ")
     if stream is None:
         stream = torch.cuda.current_stream()
-    n = centres.shape[0]
-    nrhs = beta.numel() // max(1, n * (2 * p + 1))
     rc = lib.lsms_translate_mixed_noalloc(n, p, k2, nrhs, ctypes.c_void_p(centres.data_ptr()),
                                           ctypes.c_void_p(beta.data_ptr()),
                                           ctypes.c_void_p(alpha.data_ptr()),
@@ -463,16 +489,6 @@ def inclusion_scattering_matrix(p, k2, kp, radius, curve) -> np.ndarray:
     if rc != 0:
         raise LsmsError(rc, lib.lsms_last_error(None).decode())
     return s
-
-
-def fma_probe(precision) -> float:
-    """lsms_fma_probe: measured FMA TFLOP/s of the GPU (LSMS_FP64 or LSMS_MIXED for FP32)."""
-    lib = load()
-    v = ctypes.c_double()
-    rc = lib.lsms_fma_probe(int(precision), ctypes.byref(v))
-    if rc != 0:
-        raise LsmsError(rc, lib.lsms_last_error(None).decode())
-    return v.value
 
 
 def pec_scattering_diagonal(p, k2, radius) -> np.ndarray:
