@@ -43,7 +43,7 @@ typedef struct lsms_ctx lsms_ctx;
 typedef enum {
   LSMS_OK = 0,
   LSMS_ERR_ARG = -1,           /* invalid argument: non-finite or non-positive k, p < 0, ...   */
-  LSMS_ERR_GEOMETRY = -2,      /* discs closer than 2.2 R or not strictly inside the layer     */
+  LSMS_ERR_GEOMETRY = -2,      /* gap < 0.2 R between discs, or a disc not inside its layer    */
   LSMS_ERR_NOT_CONVERGED = -3, /* GMRES hit maxiter (the iterate is still returned)            */
   LSMS_ERR_NONFINITE = -4,     /* a NaN/Inf appeared in the iteration                          */
   LSMS_ERR_OOM = -5,           /* device allocation failed                                     */
@@ -325,12 +325,6 @@ int lsms_inclusion_scattering_matrix(int p, double k2, double kp, double radius,
  *   Errors: as above, LSMS_ERR_ARG also for a loss beyond that bound. */
 int lsms_inclusion_scattering_matrix_c(int p, double k2, double kp_re, double kp_im, double radius, int n_pts,
                                        const double* curve, double* s_out);
-
-/* lsms_fma_probe — the achievable FMA rate of the current GPU (TFLOP/s, 2 flop per FMA), measured
- *   with independent dependency chains over a grid that fills every SM (precision LSMS_FP64:
- *   FP64; LSMS_MIXED: FP32).  A measured ceiling to set beside the derived ALU peaks.  About a
- *   millisecond of GPU time.  Errors: LSMS_ERR_ARG, LSMS_ERR_CUDA (no device). */
-int lsms_fma_probe(int precision, double* tflops);
 
 /* lsms_pec_scattering_diagonal — host only.  S_n = -J_n(k2 R) / H_n(k2 R), n = -p..p, of a perfectly
  *   conducting disc (Sec. 3.1, remark after Definition 3.1: the total field vanishes on the

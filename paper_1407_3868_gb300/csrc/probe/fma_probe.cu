@@ -1,12 +1,8 @@
-// FMA-pipe probe: the achievable FP32 and FP64 FMA rates of this GPU, measured with independent
-// dependency chains per thread (enough in flight to hide the pipe latency) over a grid that fills
-// every SM.  Used to put the derived peaks (SMs x lanes x 2 x clock) of the ALU-bound kernels
-// beside a measured ceiling.
+// FMA-pipe probe for the benchmark (built as libfmaprobe.so, not part of the library's ABI): the
+// achievable FP32 and FP64 FMA rates of this GPU, measured with independent dependency chains per
+// thread (enough in flight to hide the pipe latency) over a grid that fills every SM.  The
+// benchmark sets it beside the derived peaks (SMs x lanes x 2 x clock) of the ALU-bound kernels.
 #include <cuda_runtime.h>
-
-#include "lsms.h"
-#include "lsms_internal.h"
-#include "lsms_ops.h"
 
 namespace {
 
@@ -30,27 +26,27 @@ __global__ void k_fma_chains(T a, T b, T* out) {
 
 }  // namespace
 
-extern "C" int lsms_fma_probe(int precision, double* tflops) {
-  if (!tflops || (precision != LSMS_FP64 && precision != LSMS_MIXED))
-    return ctx_fail(nullptr, LSMS_ERR_ARG, "fma_probe: precision LSMS_FP64 or LSMS_MIXED (FP32) and an output");
+// fp64 != 0: FP64 FMA, else FP32.  *tflops: 2 flop per FMA over the fastest of three timed
+// launches (after one warm-up).  Returns 0, or a CUDA error code (no device, allocation failure).
+extern "C" int fma_probe_tflops(int fp64, double* tflops) {
+  if (!tflops) return (int)cudaErrorInvalidValue;
   int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-    cudaGetLastError();
-    return ctx_fail(nullptr, LSMS_ERR_CUDA, "fma_probe: no CUDA device");
-  }
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   void* out = nullptr;
-  if (cudaMalloc(&out, 16) != cudaSuccess) {
+  if (err == cudaSuccess) err = cudaMalloc(&out, 16);
+  if (err != cudaSuccess) {
     cudaGetLastError();
-    return ctx_fail(nullptr, LSMS_ERR_OOM, "fma_probe: cudaMalloc failed");
+    return (int)err;
   }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const int threads = 256, blocks = sms * 8;
   float best = 1e30f;
-  for (int rep = 0; rep < 4; ++rep) {       // the first launch warms up; keep the fastest
+  for (int rep = 0; rep < 4; ++rep) {
     cudaEventRecord(e0);
-    if (precision == LSMS_FP64)
+    if (fp64)
       k_fma_chains<double><<<blocks, threads>>>(0.9999999, 1e-7, (double*)out);
     else
       k_fma_chains<float><<<blocks, threads>>>(0.9999f, 1e-4f, (float*)out);
@@ -63,9 +59,9 @@ extern "C" int lsms_fma_probe(int precision, double* tflops) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(out);
-  const cudaError_t err = cudaGetLastError();
-  if (err != cudaSuccess) return ctx_fail(nullptr, LSMS_ERR_CUDA, std::string("fma_probe: ") + cudaGetErrorString(err));
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return (int)err;
   const double flop = 2.0 * kChains * (double)kIters * threads * blocks;
   *tflops = flop / (best / 1e3) / 1e12;
-  return LSMS_OK;
+  return 0;
 }

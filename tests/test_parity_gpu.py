@@ -353,11 +353,10 @@ def test_full_size_solve_satisfies_the_equations_on_sampled_rows(L):
 
 
 def test_fma_probe_is_plausible(L):
-    # the measured FMA ceilings sit near the derived peaks (152 SMs x 128 FP32 lanes, or x 2 FP64
-    # FMA units, x 2 flop x clock): between a quarter of them and a little above
-    f32 = L.fma_probe(L.LSMS_MIXED)
-    f64 = L.fma_probe(L.LSMS_FP64)
+    # the benchmark's measured FMA ceilings sit near the derived peaks (152 SMs x 128 FP32 lanes,
+    # or x 2 FP64 FMA units, x 2 flop x clock): between a quarter of them and a little above
+    import bench
+    f32 = bench.fma_probe(False)
+    f64 = bench.fma_probe(True)
     assert 0.25 * 80.5 < f32 < 1.1 * 80.5, f32
     assert 0.25 * 1.26 < f64 < 1.1 * 1.26, f64
-    with pytest.raises(L.LsmsError):
-        L.fma_probe(7)
