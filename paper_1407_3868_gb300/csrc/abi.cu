@@ -365,6 +365,18 @@ extern "C" int lsms_set_particles(lsms_ctx* c, int n, const double* xy) {
 // ---------------------------------------------------------------------------------------------
 // operator
 // ---------------------------------------------------------------------------------------------
+// True when every one of the n doubles is finite: v * 0 is NaN exactly for NaN and +-Inf, and the
+// sum has no early exit, so the loop vectorises (a 5000-disc vector takes tens of microseconds).
+static bool host_finite(const double* h, size_t n) {
+  double acc = 0.0;
+  for (size_t i = 0; i < n; ++i) acc += h[i] * 0.0;
+  return acc == 0.0;
+}
+static int need_finite(lsms_ctx* c, const double* h, size_t ncplx, const char* what) {
+  if (h && !host_finite(h, 2 * ncplx)) return fail(c, LSMS_ERR_ARG, std::string("non-finite value in ") + what);
+  return LSMS_OK;
+}
+
 static int copy_in(lsms_ctx* c, DevBuf& b, const double* h, size_t ncplx) {
   int rc;
   if ((rc = ensure(c, b, ncplx * sizeof(double2)))) return rc;
@@ -385,6 +397,7 @@ extern "C" int lsms_apply_ex(lsms_ctx* c, int nrhs, const double* x, double* y, 
   if (nrhs < 0 || (nrhs > 0 && c->n > 0 && (!x || !y))) return fail(c, LSMS_ERR_ARG, "bad nrhs or NULL array");
   const size_t len = (size_t)nrhs * c->n * c->P;
   if (len == 0) return LSMS_OK;
+  if ((rc = need_finite(c, x, len, "the coefficients x"))) return rc;
   if ((rc = copy_in(c, c->ws_x, x, len))) return rc;
   if ((rc = ensure(c, c->ws_y, len * sizeof(double2)))) return rc;
   if ((rc = apply_device(c, nrhs, (const double2*)c->ws_x.ptr, (double2*)c->ws_y.ptr, flags, c->stream))) return rc;
@@ -412,6 +425,7 @@ extern "C" int lsms_translate(lsms_ctx* c, int nrhs, const double* beta, double*
   const size_t len = (size_t)nrhs * c->n * c->P;
   if (nrhs < 0) return fail(c, LSMS_ERR_ARG, "nrhs must be >= 0");
   if (len == 0) return LSMS_OK;
+  if ((rc = need_finite(c, beta, len, "beta"))) return rc;
   if ((rc = copy_in(c, c->ws_x, beta, len))) return rc;
   if ((rc = ensure(c, c->ws_alpha, len * sizeof(double2)))) return rc;
   if (c->fmm.ready) {
@@ -435,6 +449,7 @@ extern "C" int lsms_aggregate(lsms_ctx* c, int nrhs, const double* beta, double*
   const int ns = c->ns, P = c->P;
   const size_t len = (size_t)nrhs * c->n * P;
   if (nrhs == 0) return LSMS_OK;
+  if ((rc = need_finite(c, beta, len, "beta"))) return rc;
   if ((rc = copy_in(c, c->ws_x, beta, len ? len : 1))) return rc;
   if ((rc = ensure(c, c->ws_g, (size_t)nrhs * 2 * ns * P * sizeof(double2)))) return rc;
   if ((rc = ensure(c, c->ws_pq, (size_t)nrhs * 2 * ns * sizeof(double2)))) return rc;
@@ -468,12 +483,14 @@ extern "C" int lsms_reflect(lsms_ctx* c, int nrhs, const double* p_plus, const d
   if (!c) return LSMS_ERR_ARG;
   if (nrhs <= 0) return nrhs == 0 ? LSMS_OK : fail(c, LSMS_ERR_ARG, "nrhs must be >= 0");
   const int ns = c->ns;
+  int rc;
+  if ((rc = need_finite(c, p_plus, (size_t)nrhs * ns, "P+"))) return rc;
+  if ((rc = need_finite(c, q_minus, (size_t)nrhs * ns, "Q-"))) return rc;
   std::vector<cplx> pq((size_t)nrhs * 2 * ns);
   for (int r = 0; r < nrhs; ++r) {
     std::memcpy(static_cast<void*>(pq.data() + (size_t)r * 2 * ns), p_plus + (size_t)r * ns * 2, ns * sizeof(cplx));
     std::memcpy(static_cast<void*>(pq.data() + (size_t)r * 2 * ns + ns), q_minus + (size_t)r * ns * 2, ns * sizeof(cplx));
   }
-  int rc;
   if ((rc = copy_in(c, c->ws_pq, (const double*)pq.data(), pq.size()))) return rc;
   if ((rc = ensure(c, c->ws_sig, pq.size() * sizeof(double2)))) return rc;
   launch_node_stage(ns, c->P, nrhs, nullptr, nullptr, (const double2*)c->ws_pq.ptr, c->d_refl, nullptr,
@@ -496,6 +513,8 @@ extern "C" int lsms_disaggregate(lsms_ctx* c, int nrhs, const double* s_plus, co
   const int ns = c->ns, P = c->P;
   const size_t len = (size_t)nrhs * c->n * P;
   if (len == 0) return LSMS_OK;
+  if ((rc = need_finite(c, s_plus, (size_t)nrhs * ns, "sigma+"))) return rc;
+  if ((rc = need_finite(c, s_minus, (size_t)nrhs * ns, "sigma-"))) return rc;
   std::vector<cplx> sg((size_t)nrhs * 2 * ns);
   const std::vector<cplx> ph = shift_phase(c, 1.0);
   const cplx* sp = reinterpret_cast<const cplx*>(s_plus);

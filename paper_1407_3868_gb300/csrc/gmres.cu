@@ -747,6 +747,7 @@ int solve_systems(lsms_ctx* c, const GmSys& s, const double2* rhs, double2* xs, 
   rest.assign(nb, 0.0);
   rel64.assign(nb, -1.0);
   int outer = 0, status = LSMS_OK;
+  c->refine_stagnated = false;
   if (c->precision != LSMS_MIXED) {
     std::vector<double> tv(nb, tol);
     status = gmres_batch(c, s, rhs, xs, nonzero, tv.data(), maxiter, LSMS_APPLY_SCALED, it.data(), rest.data(),
@@ -762,9 +763,10 @@ int solve_systems(lsms_ctx* c, const GmSys& s, const double2* rhs, double2* xs, 
     const int max_outer = 20;
     const double inner_tol = 1e-5;
     status = LSMS_ERR_NOT_CONVERGED;
-    std::vector<int> mask(nb, 1), it_in(nb, 0);
-    std::vector<double> rn(nb, 1.0), tol_in(nb), r_in(nb);
+    std::vector<int> mask(nb, 1), it_in(nb, 0), stall(nb, 0);
+    std::vector<double> rn(nb, 1.0), tol_in(nb), r_in(nb), best(nb, HUGE_VAL);
     int used = 0;
+    bool stagnated = false;
     for (outer = 0; outer < max_outer && used < maxiter; ++outer) {
       if (outer == 0 && !nonzero) {
         cudaMemcpyAsync(resv, rhs, LT * sizeof(double2), cudaMemcpyDeviceToDevice, st);
@@ -781,12 +783,21 @@ int solve_systems(lsms_ctx* c, const GmSys& s, const double2* rhs, double2* xs, 
         rel64[b] = rn[b];
         rest[b] = rn[b];
         if (!std::isfinite(rn[b])) bad = true;
-        mask[b] = rn[b] > tol ? 1 : 0;
+        // stagnation: a refinement step gains about five digits (the inner tolerance); a system
+        // whose FP64 residual has not halved over three steps sits at the floor the FP64
+        // operator's rounding allows and is refined no further
+        if (rn[b] < 0.5 * best[b]) {
+          best[b] = rn[b];
+          stall[b] = 0;
+        } else if (rn[b] > tol && ++stall[b] >= 3) {
+          stagnated = true;
+        }
+        mask[b] = (rn[b] > tol && stall[b] < 3) ? 1 : 0;
         if (mask[b]) all = false;
         tol_in[b] = std::max(inner_tol, 0.5 * tol / std::max(rn[b], 1e-300));
       }
       if (bad) { status = ctx_fail(c, LSMS_ERR_NONFINITE, "non-finite refinement residual"); break; }
-      if (all) { status = LSMS_OK; break; }
+      if (all) { status = stagnated ? LSMS_ERR_NOT_CONVERGED : LSMS_OK; break; }
       cudaMemcpyAsync(d_mask, mask.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st);
       k_mask_zero<<<dim3(grid_for(s.maxlen, 256), nb), 256, 0, st>>>(resv, d_mask, s.d_off);
       const int rci = gmres_batch(c, s, resv, dx, false, tol_in.data(), maxiter - used,
@@ -803,6 +814,7 @@ int solve_systems(lsms_ctx* c, const GmSys& s, const double2* rhs, double2* xs, 
       std::fill(rel64.begin(), rel64.end(), -1.0);
     }
     if (status == LSMS_ERR_NONFINITE) return status;
+    c->refine_stagnated = stagnated;
   }
   // true FP64 residuals of the final iterates (the refinement loop has them when it stopped on a
   // fresh residual)
@@ -852,6 +864,9 @@ extern "C" int lsms_solve(lsms_ctx* c, int nsrc, const double* src_xy, double to
     launch_diag_mul(beta, c->d_scale_out + c->P, rhs, LT, c->P, st);   // D S a_inc
   bool nonzero = false;
   if (x0) {
+    double acc = 0.0;                     // v * 0 is NaN exactly for NaN and +-Inf
+    for (long long i = 0; i < 2 * LT; ++i) acc += x0[i] * 0.0;
+    if (acc != 0.0) return ctx_fail(c, LSMS_ERR_ARG, "non-finite value in the initial guess x0");
     cudaMemcpyAsync(beta, x0, LT * sizeof(double2), cudaMemcpyHostToDevice, st);
     launch_diag_scale(beta, c->d_hscale, xs, LT, c->P, st);
     nonzero = true;
@@ -886,6 +901,8 @@ extern "C" int lsms_solve(lsms_ctx* c, int nsrc, const double* src_xy, double to
     cudaStreamSynchronize(st);
     if ((rc = check_cuda(c, "solve copy"))) return rc;
   }
-  if (status == LSMS_ERR_NOT_CONVERGED) ctx_fail(c, status, "GMRES reached maxiter");
+  if (status == LSMS_ERR_NOT_CONVERGED)
+    ctx_fail(c, status, c->refine_stagnated ? "refinement stagnated: the FP64 residual stopped decreasing above tol"
+                                            : "GMRES reached maxiter");
   return status;
 }

@@ -140,6 +140,7 @@ struct lsms_ctx {
   void* gm_ring_dev = nullptr;      // its device address
   size_t gm_ring_bytes = 0;
   int use_graphs = 1;               // capture each GMRES step as a CUDA graph
+  bool refine_stagnated = false;    // the last mixed solve stopped refining on stagnation
   double split_mult = 1.0;          // source splits of the FP32 translation (autotuned)
   int tc_min_rhs = 48;              // mixed translations of >= this many right-hand sides (p >= 6)
                                     // run on the tensor cores; 0 = never
