@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import math
 import statistics
 import subprocess
 import sys
@@ -62,6 +63,22 @@ def translation_flop(n, p, nrhs=1):
     return 8.0 * P * P * n * (n - 1) * nrhs
 
 
+def fma_probe(fp64: bool) -> float:
+    """Measured FMA TFLOP/s of this GPU (FP64 or FP32) from the benchmark's probe library
+    libfmaprobe.so (built beside liblsms.so, outside its ABI)."""
+    import ctypes
+
+    from paper_1407_3868_gb300 import build as b
+    lib = ctypes.CDLL(b.PROBE_LIB)
+    lib.fma_probe_tflops.restype = ctypes.c_int
+    lib.fma_probe_tflops.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    v = ctypes.c_double()
+    rc = lib.fma_probe_tflops(1 if fp64 else 0, ctypes.byref(v))
+    if rc != 0:
+        raise RuntimeError(f"fma_probe_tflops failed with CUDA error {rc}")
+    return v.value
+
+
 def max_over_ranks(vals, world, device):
     """Element-wise maximum of per-rank timings: the slowest replica sets the job's time."""
     import torch
@@ -97,62 +114,100 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the block and sweep measurements")
     ap.add_argument("--full", action="store_true",
                     help="also solve the 64-source block and the 128-layout sweep (mixed, a few minutes)")
-    ap.add_argument("--oracle-rows", type=int, default=8,
-                    help="target rows of the oracle's bounded sample per reference step")
-    ap.add_argument("--baseline-rows", type=int, default=40,
-                    help="target rows of the oracle's bounded sample for cpu_baseline")
+    ap.add_argument("--oracle-rows", type=int, default=2,
+                    help="target rows per host core in each step of the reference arm (the oracle)")
+    ap.add_argument("--baseline-rows", type=int, default=2,
+                    help="target rows per host core in each pass of the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing")
     ap.add_argument("--section", choices=["large", "example1"], default=None,
                     help="run one extra measurement alone and print its dict (for profiling)")
-    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------------------------------------
-# the oracle's bounded sample (runs in a child process with one BLAS thread)
+# the oracle on every host core, on bounded samples of target rows
 # ------------------------------------------------------------------------------------------------
-def oracle_sample(workload: str, rows: int) -> dict:
-    """Time the oracle on a bounded sample of one operator application: the aggregate and per-node
-    layer solves once (global), the translation and disaggregate for `rows` target discs; return
-    the extrapolated time of a full application."""
+def host_cpu() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform's name)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def host_workers() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_timing(workload: str, rows_per_worker: int, steps: int, warmup: int = 0,
+                  workers: int | None = None) -> dict:
+    """Time the oracle's operator application (`Problem.apply`, FP64 NumPy/SciPy) on every host core:
+    a pool of worker processes (spawn, one BLAS thread each) splits the target particles, one chunk
+    per worker.  A step is one pass over a bounded sample of rows_per_worker target rows per worker
+    (rows spread over the layout); each worker also forms the global aggregate and per-node layer
+    response once per pass, as a full application split the same way would.  Two calibration passes
+    with one row per worker separate that global cost t_g from the cost per row t_r; a full
+    application on the same pool takes t_g + ceil(N / workers) t_r."""
     import numpy as np
 
     from oracle import lsms_oracle as O
     from paper_1407_3868_gb300 import inputs
     w = inputs.WORKLOADS[workload]
     m = w.medium
-    c = w.centres()
     lam, wt = O.contour(w.n_nodes, m["k1"], m["k2"], m["k3"], w.b, w.t_max)
-    pr = O.Problem(O.Medium(m["k1"], m["k2"], m["k3"], m["d"], m["kp"], m["radius"]), w.p, c, lam, wt)
+    pr = O.Problem(O.Medium(m["k1"], m["k2"], m["k3"], m["d"], m["kp"], m["radius"]), w.p, w.centres(), lam, wt)
     x = inputs.random_coefficients(w.n, w.p, 1, 0)[0] / O.order_scale(w.p, m["k2"], m["radius"])
-    sel = list(np.linspace(0, w.n - 1, rows).astype(int))
-    t0 = time.perf_counter()
-    pp, qm = pr.aggregate(x)
-    sig = pr.layer_densities(None, pp, qm)
-    t1 = time.perf_counter()
-    alpha = pr.translation(x, sel) + pr.disaggregate(sig[:, 1], sig[:, 2], sel)
-    _ = x[sel] - pr.S[None, :] * alpha
-    t2 = time.perf_counter()
-    full = (t1 - t0) + (t2 - t1) * w.n / rows
-    return {"global_s": t1 - t0, "rows": rows, "n": w.n, "rows_s": t2 - t1, "full_apply_s": full}
+    workers = workers or host_workers()
+    rows_per_worker = max(2, rows_per_worker)
 
+    def spread(k):
+        return sorted(set(np.linspace(0, w.n - 1, min(k, w.n)).astype(int).tolist()))
 
-def run_oracle_child(workload: str, rows: int) -> dict:
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", "--workload",
-                          workload, "--oracle-rows", str(rows)], capture_output=True, text=True,
-                         env=env, timeout=1800)
-    if out.returncode != 0:
-        raise RuntimeError("oracle sample failed:\n" + out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+    with O.RowPool(pr, workers=workers) as rp:
+        W = rp.workers
+        one, sample = spread(W), spread(W * rows_per_worker)
+
+        def timed_pass(rows):
+            t0 = time.perf_counter()
+            rp.apply(x, rows=rows, chunks=W)
+            return time.perf_counter() - t0
+        timed_pass(one)                                   # imports and first-touch in the workers
+        t_one = min(timed_pass(one) for _ in range(2))
+        for _ in range(warmup):
+            timed_pass(sample)
+        times = [timed_pass(sample) for _ in range(max(1, steps))]
+    per_worker = len(sample) / W
+    t_r = max(0.0, (statistics.mean(times) - t_one) / max(per_worker - len(one) / W, 1e-9))
+    t_g = max(0.0, t_one - t_r * len(one) / W)
+    full = t_g + math.ceil(w.n / W) * t_r
+    return {"workers": W, "cpu": host_cpu(), "n": w.n, "rows_per_step": len(sample), "steps": len(times),
+            "step_s": times, "t_global_s": t_g, "t_row_s": t_r, "full_apply_s": full}
 
 
 def cpu_baseline_entry(s: dict) -> dict:
-    return {"value": 1.0 / s["full_apply_s"], "unit": "applies/s", "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 NumPy/SciPy oracle, one BLAS thread: global aggregate + layer solves "
-                       f"({s['global_s']:.2f} s) and {s['rows']} of {s['n']} target rows "
-                       f"({s['rows_s']:.2f} s), extrapolated to a full application "
-                       f"({s['full_apply_s']:.1f} s)")}
+    return {"value": 1.0 / s["full_apply_s"], "unit": "applies/s", "cores": s["workers"], "kind": "oracle",
+            "cpu": s["cpu"],
+            "sample": (f"FP64 NumPy/SciPy oracle on {s['workers']} host cores ({s['cpu']}), one worker process "
+                       f"per core: {s['steps']} passes over {s['rows_per_step']} of {s['n']} target rows "
+                       f"({statistics.mean(s['step_s']):.2f} s each, incl. each worker's global aggregate and "
+                       f"layer solves, {s['t_global_s']:.2f} s); one application = "
+                       f"{s['t_global_s']:.2f} s + ceil({s['n']}/{s['workers']}) x {s['t_row_s']:.3f} s per "
+                       f"row = {s['full_apply_s']:.1f} s")}
 
 
 # ------------------------------------------------------------------------------------------------
@@ -214,8 +269,8 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     # measured FMA ceilings of this GPU, beside the derived ALU peaks
-    fma = {"fp32_tflops": lsms.fma_probe(lsms.LSMS_MIXED), "fp64_tflops": lsms.fma_probe(lsms.LSMS_FP64),
-           "probe": "lsms_fma_probe: 8 independent FMA chains per thread, 8 CTAs of 256 per SM"}
+    fma = {"fp32_tflops": fma_probe(False), "fp64_tflops": fma_probe(True),
+           "probe": "libfmaprobe.so: 8 independent FMA chains per thread, 8 CTAs of 256 per SM"}
     w = inputs.WORKLOADS[args.workload]
     n, P = w.n, 2 * w.p + 1
     centres = w.centres()
@@ -352,6 +407,9 @@ def run_ours(args, rank, world, local_rank):
         boxes = guarded("boxes", run_boxes, args, w, dev, flush, u_ref_fp64)
         example1 = guarded("example1", run_example1, args)
 
+    c2 = None
+    if world == 1 and not args.no_solve:
+        c2 = guarded("c2", run_c2, args)
     if rank != 0:
         return None
     line = {
@@ -361,11 +419,6 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": w.name, "discs": n, "p": w.p, "contour_nodes": w.n_nodes,
                    "operator": "mixed (FP32 translation)", "nrhs": 1,
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
-        "fp64": {"value": fp64_rate, "unit": "applies/s", "ms_per_step": ms_fp64 / k64, "dtype": "f64",
-                 "translate_ms": tr64_ms,
-                 "translate_frac_of_fp64_peak": (flop / (tr64_ms / 1e3) / 1e12) / FP64_PEAK_TFLOPS},
-        "speedup_mixed_vs_fp64": value / fp64_rate,
-        "solve": solve,
         "batched": batched,
         "stack": stack,
         "inclusions": inclusions,
@@ -373,12 +426,16 @@ def run_ours(args, rank, world, local_rank):
         "large": large,
         "boxes": boxes,
         "example1": example1,
+        "fma_probe": fma,
+        "fp64": {"value": fp64_rate, "unit": "applies/s", "ms_per_step": ms_fp64 / k64, "dtype": "f64",
+                 "translate_ms": tr64_ms,
+                 "translate_frac_of_fp64_peak": (flop / (tr64_ms / 1e3) / 1e12) / FP64_PEAK_TFLOPS},
+        "speedup_mixed_vs_fp64": value / fp64_rate,
         "roofline": {"kernel": "k_translate_f32", "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": traffic, "flop_per_launch": flop, "launch_ms": tr_ms,
                      "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                      "measured_fma_peak": fma["fp32_tflops"], "frac_of_measured_fma": achieved / fma["fp32_tflops"]},
-        "fma_probe": fma,
         "e2e": {"value": e2e, "unit": "applies/s", "h2d_bytes_per_step": n * P * 16,
                 "d2h_bytes_per_step": n * P * 16},
         "gpu_launches": launches * args.steps,
@@ -386,9 +443,12 @@ def run_ours(args, rank, world, local_rank):
     }
     if world == 1 and not args.no_cpu_baseline:
         try:
-            line["cpu_baseline"] = cpu_baseline_entry(run_oracle_child(w.name, args.baseline_rows))
+            line["cpu_baseline"] = cpu_baseline_entry(oracle_timing(w.name, args.baseline_rows, 2))
         except Exception as e:  # pragma: no cover
             line["cpu_baseline"] = {"value": None, "error": str(e)[-300:]}
+    # the solve results last: the end of the line is what a truncated log keeps
+    line["c2"] = c2
+    line["solve"] = solve
     return line
 
 
@@ -416,6 +476,68 @@ def time_device(fn, steps, flush=None):
         torch.cuda.synchronize()
         ms += e0.elapsed_time(e1)
     return ms / steps
+
+
+GOLDEN_C2 = os.path.join(ROOT, "tests", "golden", "disc1000_p12_ns512_oracle.txt")
+
+
+def load_oracle_solution(path=GOLDEN_C2):
+    """The oracle's stored solution of the 1000-disc workload: (discs, beta rows, {field kind: values})."""
+    import numpy as np
+    beta, fields = {}, {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            tag, a, b, *rest = line.split()
+            if tag == "beta":
+                beta[(int(a), int(b))] = complex(float(rest[0]), float(rest[1]))
+            else:
+                fields.setdefault(tag, {})[int(a)] = complex(float(b), float(rest[0]))
+    discs = sorted({j for j, _ in beta})
+    p = max(n for _, n in beta)
+    B = np.array([[beta[(j, n)] for n in range(-p, p + 1)] for j in discs])
+    return discs, B, {k: np.array([v[t] for t in sorted(v)]) for k, v in fields.items()}
+
+
+def run_c2(args):
+    """The plain FP64 GPU method on 1000 discs (p = 12, 512 contour nodes, tol 1e-10) and the mixed
+    solve at 1e-8, each timed (one warm-up solve first) and compared with the oracle's solution of
+    the same discrete problem (dense LU, stored in tests/golden): beta on every tenth disc in the
+    scaled norm and the scattered and particle fields at the 64 targets, as 2-norm and element-wise
+    relative errors."""
+    import numpy as np
+    import torch
+
+    from paper_1407_3868_gb300 import inputs, lsms
+    w = inputs.WORKLOADS["disc1000_p12_ns512"]
+    discs, B, U = load_oracle_solution()
+    from scipy import special
+    hs = np.abs(special.hankel1(np.arange(-w.p, w.p + 1), w.medium["k2"] * w.medium["radius"]))   # scaled norm
+    out = {"workload": w.name, "discs": w.n, "p": w.p, "contour_nodes": w.n_nodes,
+           "oracle": "stored dense-LU solution (tests/golden), scaled residual 2.6e-14"}
+    for prec, key, tol in ((lsms.LSMS_FP64, "fp64_solve", 1e-10), (lsms.LSMS_MIXED, "mixed_solve", 1e-8)):
+        ctx = lsms.context_for(w, prec)
+        ctx.set_particles(w.centres())
+        ctx.solve(w.sources, tol=tol, maxiter=2000)                       # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        beta, info = ctx.solve(w.sources, tol=tol, maxiter=2000)
+        t = time.perf_counter() - t0
+        got = beta[0][discs]
+        wgt = hs
+        row = {"tol": tol, "s": t, "iters": info["iters"], "refinements": info["outer_iters"],
+               "rel_res_fp64": info["rel_res_fp64"],
+               "beta_rel_err": float(np.linalg.norm((got - B) * wgt) / np.linalg.norm(B * wgt)),
+               "beta_max_err": float(np.max(np.abs((got - B) * wgt)) / np.max(np.abs(B * wgt)))}
+        for kind, which in (("scattered", lsms.FIELD_SCATTERED), ("particle", lsms.FIELD_PARTICLE)):
+            u = ctx.eval_field(w.targets, 0, which)
+            row[kind + "_field_rel_err"] = float(np.linalg.norm(u - U[kind]) / np.linalg.norm(U[kind]))
+            row[kind + "_field_max_err"] = float(np.max(np.abs(u - U[kind])) / np.max(np.abs(U[kind])))
+        out[key] = row
+        ctx.close()
+    out["speedup_mixed_vs_fp64"] = out["fp64_solve"]["s"] / out["mixed_solve"]["s"]
+    return out
 
 
 def run_batched(args, dev, flush):
@@ -786,23 +908,20 @@ def run_large(args, dev, flush):
 
 
 def run_reference(args, rank):
+    """The reference arm: the oracle (there is no reference code) on every host core, K timed steps
+    after W warm-up steps, each step one pass over a bounded sample of target rows (oracle_timing).
+    ms_per_step is the measured time of a step; value is the oracle's full applications per second
+    derived from the same passes."""
     if rank != 0:
         return None
-    vals = []
-    last = None
-    for i in range(args.warmup + args.steps):
-        s = run_oracle_child(args.workload, args.oracle_rows)
-        if i >= args.warmup:
-            vals.append(s["full_apply_s"])
-            last = s
-    total = sum(vals)
-    value = len(vals) / total
-    cb = cpu_baseline_entry(last)
-    cb["value"] = value
+    s = oracle_timing(args.workload, args.oracle_rows, args.steps, args.warmup)
+    value = 1.0 / s["full_apply_s"]
+    cb = cpu_baseline_entry(s)
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(vals),
+            "steps": len(s["step_s"]), "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(s["step_s"]),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "operator": "FP64 oracle"},
+            "data": "synthetic", "config": {"workload": args.workload, "operator": "FP64 oracle",
+                                             "step": f"{s['rows_per_step']} of {s['n']} target rows"},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "applies/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -810,9 +929,6 @@ def run_reference(args, rank):
 
 def main():
     args = parse()
-    if args.oracle_sample:
-        print(json.dumps(oracle_sample(args.workload, args.oracle_rows)))
-        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

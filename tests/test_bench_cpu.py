@@ -1,5 +1,6 @@
-"""The reference arm of bench.py (the oracle on the host cores) on the CPU: its JSON line carries the
-contract's keys, and under a multi-rank launch only rank 0 prints it (the others exit 0)."""
+"""The reference arm of bench.py (the oracle on every host core) on the CPU: its JSON line carries
+the contract's keys and the number of cores used, its step time fits in the run's own wall clock,
+and under a multi-rank launch only rank 0 prints it (the others exit 0)."""
 import json
 import os
 import subprocess
@@ -8,14 +9,24 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
+def bench_workers():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench.host_workers()
+
+
 def _run(env_extra):
     env = dict(os.environ, **env_extra)
-    return subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
-                           "--oracle-rows", "2"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    cmd = [sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+           "--oracle-rows", "2", "--workload", "disc1000_p12_ns512"]
+    return subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
 
 
 def test_reference_arm_prints_the_contract_line():
+    import time
+    t0 = time.perf_counter()
     res = _run({})
+    elapsed = time.perf_counter() - t0
     assert res.returncode == 0, res.stderr[-2000:]
     line = json.loads(res.stdout.strip().splitlines()[-1])
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
@@ -24,7 +35,11 @@ def test_reference_arm_prints_the_contract_line():
     assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
-    assert line["config"]["workload"] == "disc5000_p14_ns1024"
+    assert line["config"]["workload"] == "disc1000_p12_ns512"
+    cb = line["cpu_baseline"]
+    assert cb["cores"] == bench_workers() and line["steps"] == 1
+    # the step time is what a step took: the run fits in its own wall clock
+    assert line["ms_per_step"] * line["steps"] < 1e3 * elapsed
 
 
 def test_reference_arm_other_ranks_exit_quietly():
