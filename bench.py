@@ -52,7 +52,7 @@ TRAFFIC = {
     # k_translate_f32<14,1>, 5000 discs: dram__bytes_read.sum 1.307 MB + dram__bytes_write.sum 0.162 MB
     "b202b10ce1f5fdc2": 1.468672e6,
 }
-KERNEL_SOURCES = ("mixed.cu", "ff_hankel.cuh")
+KERNEL_SOURCES = ("mixed.cu", "ff_hankel.cuh")       # k_translate_f32_h2 and its Hankel sequences
 
 
 def translation_flop(n, p, nrhs=1):
@@ -119,8 +119,9 @@ def parse():
     ap.add_argument("--baseline-rows", type=int, default=2,
                     help="target rows per host core in each pass of the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing")
-    ap.add_argument("--section", choices=["large", "example1"], default=None,
-                    help="run one extra measurement alone and print its dict (for profiling)")
+    ap.add_argument("--section", choices=["large", "example1", "translate"], default=None,
+                    help="run one extra measurement alone and print its dict (for profiling); "
+                         "translate: the mixed translation alone on --workload, --steps times")
     return ap.parse_args()
 
 
@@ -431,7 +432,7 @@ def run_ours(args, rank, world, local_rank):
                  "translate_ms": tr64_ms,
                  "translate_frac_of_fp64_peak": (flop / (tr64_ms / 1e3) / 1e12) / FP64_PEAK_TFLOPS},
         "speedup_mixed_vs_fp64": value / fp64_rate,
-        "roofline": {"kernel": "k_translate_f32", "bound": "alu", "achieved": achieved,
+        "roofline": {"kernel": "k_translate_f32_h2", "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": traffic, "flop_per_launch": flop, "launch_ms": tr_ms,
                      "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
@@ -907,6 +908,33 @@ def run_large(args, dev, flush):
     return out
 
 
+def run_translate_only(args):
+    """The mixed translation alone (Lemma 3.1 in FP32: float conversion, the pair kernel, the partial
+    sums' reduction, the near pairs) on --workload's first right-hand side, --steps applications
+    after --warmup; the kernel's CUDA-event time and its algorithmic rate."""
+    import torch
+
+    from paper_1407_3868_gb300 import inputs, lsms
+    w = inputs.WORKLOADS[args.workload]
+    ctx = lsms.context_for(w, lsms.LSMS_MIXED)
+    ctx.set_particles(w.centres())
+    x = torch.from_numpy(inputs.random_coefficients(w.n, w.p, 1, 100)).cuda()
+    y = torch.empty_like(x)
+    flags = lsms.APPLY_SCALED | lsms.APPLY_MIXED | lsms.APPLY_NO_REFLECTION
+    for _ in range(args.warmup):
+        ctx.apply_dev(x, y, flags)
+    ctx.set_timing(True)
+    tr = []
+    for _ in range(args.steps):
+        ctx.apply_dev(x, y, flags)
+        tr.append(ctx.last_timing()[0])
+    ctx.close()
+    ms = statistics.mean(tr)
+    flop = translation_flop(w.n, w.p)
+    return {"workload": w.name, "steps": args.steps, "translate_ms": ms, "flop": flop,
+            "tflops": flop / (ms / 1e3) / 1e12, "frac_of_fp32_peak": flop / (ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS}
+
+
 def run_reference(args, rank):
     """The reference arm: the oracle (there is no reference code) on every host core, K timed steps
     after W warm-up steps, each step one pass over a bounded sample of target rows (oracle_timing).
@@ -941,6 +969,14 @@ def main():
         torch.cuda.set_device(dev)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
         print(json.dumps({"section": "large", "large": run_large(args, dev, flush)}))
+        return
+    if args.section == "translate":
+        import torch
+
+        import __graft_entry__
+        __graft_entry__.build()
+        torch.cuda.set_device(torch.device("cuda", local_rank))
+        print(json.dumps({"section": "translate", "translate": run_translate_only(args)}))
         return
     if args.section == "example1":
         import torch

@@ -149,6 +149,133 @@ k_translate_f32(const float4* __restrict__ cff, int n, float k_hi, float k_lo,
   }
 }
 
+// One right-hand side per CTA, two lanes per target disc.  A warp owns MT2 = 16 target discs; lane
+// (hh, t) owns the outputs nu = VB hh .. VB hh + VB - 1 of target t, VB = p + 1 (so P = 2p + 1
+// orders fill 2 VB - 1 of the 2 VB output slots).  Per step the warp generates 32 pair sequences
+// (lane (hh, t): target t, source s0 + hh) into its 32 slots; then each lane contracts both
+// sources.  Per source order n the lane keeps a rolling window of the VB sequence values
+// h_{n - nu} it needs, loads one new value and the source coefficient, and per output forms the
+// Gauss products with one packed FMA (fma.rn.f32x2: h_r b_r and h_i b_i into the accumulator pair)
+// and one FMA ((h_r + h_i)(b_r + b_i)): two issue slots for three FMAs.  The source orders run in
+// two blocks of VB (the coefficients are staged with one zero order appended, P + 1 = 2 VB), the
+// block loop not unrolled: the contraction's code stays small enough for the instruction cache.  The coefficient and its sum (b_r + b_i) are staged once per
+// chunk, so the contraction spends one FADD (the window value's sum) per 3 VB FMAs.  Slots hold the
+// 4p + 1 values of a pair with stride HS2 = 4p + 3 (odd: the 16 lanes of a half read 16 distinct
+// bank pairs; at least 4p + 3: the upper half's first window read, one entry before its slot, and
+// the padded order's read, two entries past the last value, land in zero margins or the guard).
+template <int PT>
+struct H2 {
+  static constexpr int p = PT;
+  static constexpr int P = 2 * PT + 1;
+  static constexpr int VB = PT + 1;
+  static constexpr int HS = 4 * PT + 3;
+  static constexpr int SLOTS = MW * 32 * HS + 2 * GUARD;
+  static constexpr size_t SMEM = (size_t)SLOTS * sizeof(float2);
+};
+constexpr int MT2 = 16;      // target discs per warp in the two-lanes-per-target kernel
+
+template <int PT>
+__global__ void __launch_bounds__(MW * 32, 3)
+k_translate_f32_h2(const float4* __restrict__ cff, int n, float k_hi, float k_lo,
+                   const float2* __restrict__ xs, float2* __restrict__ part, int src_per_split,
+                   int nrhs, float near_hi, float near_lo) {
+  constexpr int p = PT;
+  constexpr int P = H2<PT>::P;
+  constexpr int VB = H2<PT>::VB;
+  constexpr int HS = H2<PT>::HS;
+  __shared__ float2 sb[MCH][2 * VB];
+  __shared__ float sbs[MCH][2 * VB];
+  __shared__ float4 sc[MCH];
+  extern __shared__ float2 sh[];
+  const int r = blockIdx.z;
+  const int split = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = lane & 15, hh = lane >> 4;       // hh = output half (contraction) = source (generation)
+  const int l = (blockIdx.x * MW + warp) * MT2 + t;
+  const bool lvalid = l < n;
+  const float4 ct = lvalid ? cff[l] : make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = threadIdx.x; i < H2<PT>::SLOTS; i += blockDim.x) sh[i] = make_float2(0.f, 0.f);
+  float2* hw = sh + GUARD + warp * 32 * HS;
+  float2 AB[VB];             // (sum h_r b_r, sum h_i b_i): one packed FMA per window value
+  float C[VB];               // sum (h_r + h_i)(b_r + b_i)
+#pragma unroll
+  for (int i = 0; i < VB; ++i) {
+    AB[i] = make_float2(0.f, 0.f);
+    C[i] = 0.f;
+  }
+  const int jbeg = split * src_per_split;
+  const int jend = min(n, jbeg + src_per_split);
+  const ffl kf = {k_hi, k_lo};
+  const float2* xr = xs + (size_t)r * n * P;
+  for (int j0c = jbeg; j0c < jend; j0c += MCH) {
+    const int cnt = min(MCH, jend - j0c);
+    __syncthreads();
+    for (int i = threadIdx.x; i < MCH * 2 * VB; i += blockDim.x) {
+      const int s = i / (2 * VB), q = i - s * (2 * VB);
+      const float2 v = (s < cnt && q < P) ? xr[(size_t)(j0c + s) * P + q] : make_float2(0.f, 0.f);
+      sb[s][q] = v;
+      sbs[s][q] = v.x + v.y;
+    }
+    if (threadIdx.x < cnt) sc[threadIdx.x] = cff[j0c + threadIdx.x];
+    __syncthreads();
+    for (int s0 = 0; s0 < cnt; s0 += 2) {
+      {
+        const int js = s0 + hh;
+        float2* h = hw + lane * HS;
+        if (js < cnt && lvalid && j0c + js != l) {
+          hankel_sequence_f32<PT>(ct, sc[js], kf, {near_hi, near_lo}, h);
+        } else {
+          for (int q = 0; q <= 4 * p; ++q) h[q] = make_float2(0.f, 0.f);
+        }
+      }
+      __syncwarp();
+      const int nq = min(2, cnt - s0);
+#pragma unroll 1
+      for (int q2 = 0; q2 < nq; ++q2) {
+        const float2* hs = hw + (q2 * 16 + t) * HS + 2 * p - VB * hh;   // hs[n - i] = h_{n - (VB hh + i)}
+        const float2* bq = sb[s0 + q2];
+        const float* bsq = sbs[s0 + q2];
+        float2 win[VB];
+        float ws[VB];
+#pragma unroll
+        for (int i = 0; i < VB - 1; ++i) {        // the window before the first shift: h_{-1 - i}
+          win[i] = hs[-1 - i];
+          ws[i] = win[i].x + win[i].y;
+        }
+#pragma unroll 1
+        for (int nb = 0; nb < 2 * VB; nb += VB) {
+#pragma unroll
+          for (int u = 0; u < VB; ++u) {
+#pragma unroll
+            for (int i = VB - 1; i > 0; --i) {
+              win[i] = win[i - 1];
+              ws[i] = ws[i - 1];
+            }
+            win[0] = hs[nb + u];
+            ws[0] = win[0].x + win[0].y;
+            const float2 b = bq[nb + u];
+            const float bsum = bsq[nb + u];
+#pragma unroll
+            for (int i = 0; i < VB; ++i) {
+              AB[i] = __ffma2_rn(win[i], b, AB[i]);
+              C[i] = __fmaf_rn(ws[i], bsum, C[i]);
+            }
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  if (lvalid) {
+    float2* out = part + (((size_t)split * nrhs + r) * n + l) * P;
+#pragma unroll
+    for (int i = 0; i < VB; ++i) {
+      const int nu = VB * hh + i;
+      if (nu < P) out[nu] = make_float2(AB[i].x - AB[i].y, C[i] - AB[i].x - AB[i].y);
+    }
+  }
+}
+
 // Near pairs (k2 rho < 25, a few per disc): their Hankel sequences are computed once per layout in
 // FP64 (CUDA J0, Y0, J1, Y1 and the forward recurrence) and stored in FP32; the main FP32 kernel
 // leaves these pairs out and k_translate_near adds them.
@@ -255,21 +382,53 @@ void launch_pt(dim3 grid, cudaStream_t st, const float4* cff, int n, float kh, f
   k_translate_f32<PT, RB><<<grid, MW * 32, TRANSLATE_F32_SMEM, st>>>(cff, n, kh, kl, xs, part, sps, nrhs, nh, nl);
 }
 
-// Four or more right-hand sides are contracted four at a time against each generated sequence
-// (orders p >= 6; smaller orders take one at a time).
+template <int PT>
+void launch_h2(dim3 grid, cudaStream_t st, const float4* cff, int n, float kh, float kl,
+               const float2* xs, float2* part, int sps, int nrhs, float nh, float nl) {
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_translate_f32_h2<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)H2<PT>::SMEM);
+  });
+  grid.z = nrhs;
+  k_translate_f32_h2<PT><<<grid, MW * 32, H2<PT>::SMEM, st>>>(cff, n, kh, kl, xs, part, sps, nrhs, nh, nl);
+}
+
+// Four or more right-hand sides (orders p >= 6) are contracted four at a time against each
+// generated sequence (k_translate_f32<p, 4>, 32 target discs per CTA); otherwise one right-hand
+// side per CTA with two lanes per target (k_translate_f32_h2, 64 target discs per CTA).
+bool translate_uses_h2(int nrhs, int p) { return !(nrhs >= 4 && p >= 6); }
+int translate_targets_per_cta(int nrhs, int p) { return translate_uses_h2(nrhs, p) ? MW * MT2 : MW * MT; }
+
+// grid.x must be ceil(n / translate_targets_per_cta(nrhs, p)).
 void launch_translate_kernel(dim3 grid, cudaStream_t st, const float4* cff, int n, int p, float kh,
                              float kl, const float2* xs, float2* part, int sps, int nrhs,
                              float nh = 0.f, float nl = 0.f) {
-  const bool blk = nrhs >= 4;
-#define LSMS_T1(PT) launch_pt<PT, 1>(grid, st, cff, n, kh, kl, xs, part, sps, nrhs, nh, nl)
-#define LSMS_TB(PT) (blk ? launch_pt<PT, 4>(grid, st, cff, n, kh, kl, xs, part, sps, nrhs, nh, nl) : LSMS_T1(PT))
+  if (translate_uses_h2(nrhs, p)) {
+#define LSMS_H2(PT) launch_h2<PT>(grid, st, cff, n, kh, kl, xs, part, sps, nrhs, nh, nl)
+    switch (p) {
+      case 0: LSMS_H2(0); break;
+      case 1: LSMS_H2(1); break;
+      case 2: LSMS_H2(2); break;
+      case 3: LSMS_H2(3); break;
+      case 4: LSMS_H2(4); break;
+      case 5: LSMS_H2(5); break;
+      case 6: LSMS_H2(6); break;
+      case 7: LSMS_H2(7); break;
+      case 8: LSMS_H2(8); break;
+      case 9: LSMS_H2(9); break;
+      case 10: LSMS_H2(10); break;
+      case 11: LSMS_H2(11); break;
+      case 12: LSMS_H2(12); break;
+      case 13: LSMS_H2(13); break;
+      case 14: LSMS_H2(14); break;
+      default: LSMS_H2(15); break;
+    }
+#undef LSMS_H2
+    return;
+  }
+#define LSMS_TB(PT) launch_pt<PT, 4>(grid, st, cff, n, kh, kl, xs, part, sps, nrhs, nh, nl)
   switch (p) {
-    case 0: LSMS_T1(0); break;
-    case 1: LSMS_T1(1); break;
-    case 2: LSMS_T1(2); break;
-    case 3: LSMS_T1(3); break;
-    case 4: LSMS_T1(4); break;
-    case 5: LSMS_T1(5); break;
     case 6: LSMS_TB(6); break;
     case 7: LSMS_TB(7); break;
     case 8: LSMS_TB(8); break;
@@ -281,7 +440,6 @@ void launch_translate_kernel(dim3 grid, cudaStream_t st, const float4* cff, int 
     case 14: LSMS_TB(14); break;
     default: LSMS_TB(15); break;
   }
-#undef LSMS_T1
 #undef LSMS_TB
 }
 
@@ -358,10 +516,12 @@ int build_lowp_tables(lsms_ctx* c) {
 
 // Splits of the source range so that the grid covers the GPU several times (3 CTAs per SM for one
 // right-hand side per CTA, 2 for four).
-static int translate_splits(int n, int nrhs, double mult = 1.0) {
-  const int tiles = (n + MW * MT - 1) / (MW * MT);
-  const int zb = nrhs >= 4 ? (nrhs + 3) / 4 : nrhs;
-  const int per_sm = nrhs >= 4 ? 2 : 3;
+static int translate_splits(int n, int nrhs, int p, double mult = 1.0) {
+  const int tpc = translate_targets_per_cta(nrhs, p);
+  const int tiles = (n + tpc - 1) / tpc;
+  const bool h2 = translate_uses_h2(nrhs, p);
+  const int zb = h2 ? nrhs : (nrhs + 3) / 4;
+  const int per_sm = h2 ? 3 : 2;
   int s = (int)std::ceil(mult * (152 * per_sm * 4) / (double)(tiles * zb));
   const int max_s = (n + MCH - 1) / MCH;
   if (s > max_s) s = max_s;
@@ -386,7 +546,7 @@ int translate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cu
   const bool tc = c->tc_min_rhs > 0 && nrhs >= c->tc_min_rhs && p >= 6 && p <= LSMS_MAX_P;
   int splits = 1, sps = n;
   if (!tc) {
-    splits = translate_splits(n, nrhs, c->split_mult);
+    splits = translate_splits(n, nrhs, p, c->split_mult);
     sps = (n + splits - 1) / splits;
     sps = ((sps + MCH - 1) / MCH) * MCH;
     splits = (n + sps - 1) / sps;
@@ -400,7 +560,8 @@ int translate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cu
   } else {
     float2* part = (float2*)((unsigned char*)c->ws_lp.ptr + b32);
     const float kh = (float)c->k2, kl = (float)(c->k2 - (double)kh);
-    dim3 grid((n + MW * MT - 1) / (MW * MT), splits, nrhs);
+    const int tpc = translate_targets_per_cta(nrhs, p);
+    dim3 grid((n + tpc - 1) / tpc, splits, nrhs);
     const float nh = (float)c->near_r2, nl = (float)(c->near_r2 - (double)nh);
     launch_translate_kernel(grid, st, (const float4*)c->d_lp_misc, n, p, kh, kl, xs32, part, sps, nrhs, nh, nl);
     k_reduce_parts<<<(int)g, 256, 0, st>>>(part, splits, len, alpha);
@@ -479,7 +640,7 @@ extern "C" int lsms_translate_mixed_noalloc(int n, int p, double k2, int nrhs,
   if (cbytes + b32 + per_split > kNoAllocScratchBytes)
     return ctx_fail(nullptr, LSMS_ERR_ARG,
                     "translate_mixed_noalloc: n * (16 + 16 * nrhs * (2p+1)) bytes exceed the 16 MiB scratch");
-  int splits = translate_splits(n, nrhs);
+  int splits = translate_splits(n, nrhs, p);
   while (splits > 1 && cbytes + b32 + (size_t)splits * per_split > kNoAllocScratchBytes) --splits;
   int sps = (n + splits - 1) / splits;
   sps = ((sps + MCH - 1) / MCH) * MCH;
@@ -496,7 +657,8 @@ extern "C" int lsms_translate_mixed_noalloc(int n, int p, double k2, int nrhs,
   if (g > 152 * 16) g = 152 * 16;
   k_to_float<<<(int)g, 256, 0, st>>>((const double2*)beta, xs32, len);
   const float kh = (float)k2, kl = (float)(k2 - (double)kh);
-  dim3 grid((n + MW * MT - 1) / (MW * MT), splits, nrhs);
+  const int tpc = translate_targets_per_cta(nrhs, p);
+  dim3 grid((n + tpc - 1) / tpc, splits, nrhs);
   launch_translate_kernel(grid, st, cff, n, p, kh, kl, xs32, part, sps, nrhs);
   k_reduce_parts<<<(int)g, 256, 0, st>>>(part, splits, len, (double2*)alpha);
   const cudaError_t e = cudaGetLastError();
