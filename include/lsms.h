@@ -369,6 +369,16 @@ int lsms_set_scattering_diagonal(lsms_ctx* ctx, const double* s_diag);
  *   (lsms_set_timing), the device milliseconds of the last box translation's far part (shifts,
  *   FFT convolution) and near part; waits for that translation.  NULL outputs are skipped. */
 int lsms_set_fmm(lsms_ctx* ctx, double box_width, int order);
+/* lsms_set_fmm_scope — where the box translation of lsms_set_fmm is used.  LSMS_FMM_ALL (the
+ *   default): every translation.  LSMS_FMM_RESIDUAL: only the FP64 residuals r = rhs - A beta of the
+ *   mixed-precision refinement (lsms_solve on an LSMS_MIXED context), the step that checks the
+ *   solution; every other application (the inner mixed GMRES, lsms_apply*, lsms_translate) keeps
+ *   the all-pairs translation.  The solve then refines against the box operator, whose translation
+ *   differs from all pairs by the truncation of the box expansions (about 1e-12 relative at the
+ *   default order), far below a refinement tolerance of 1e-8.  Applies to the layouts of a batch.
+ *   Errors: LSMS_ERR_ARG. */
+enum { LSMS_FMM_ALL = 0, LSMS_FMM_RESIDUAL = 1 };
+int lsms_set_fmm_scope(lsms_ctx* ctx, int scope);
 int lsms_get_fmm(const lsms_ctx* ctx, int* n_boxes, int* order);
 int lsms_fmm_stats(lsms_ctx* ctx, long long* near_pairs, double* far_ms, double* near_ms);
 

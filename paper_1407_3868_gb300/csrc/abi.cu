@@ -120,7 +120,7 @@ int apply_device(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags,
     // box method (FP64, either precision): see fmm.cu; FP64: one kernel; mixed: FP32 copy of xs,
     // the translation (+ the partial-sum reduction, or the packing of the tensor-core operands)
     // and the near pairs
-    if (c->fmm.ready) {
+    if (c->fmm.ready && (c->fmm.scope == 0 || (flags & LSMS_APPLY_RESIDUAL_INTERNAL))) {
       launches += (c->fmm.dmin > 2 ? 4 : 3) * nrhs + (mixed ? 3 + (c->near_nnz > 0 ? 1 : 0) : 1);
       if ((rc = fmm_translate(c, nrhs, xs, alpha, mixed, st))) return rc;
     } else if (mixed) {
@@ -428,7 +428,7 @@ extern "C" int lsms_translate(lsms_ctx* c, int nrhs, const double* beta, double*
   if ((rc = need_finite(c, beta, len, "beta"))) return rc;
   if ((rc = copy_in(c, c->ws_x, beta, len))) return rc;
   if ((rc = ensure(c, c->ws_alpha, len * sizeof(double2)))) return rc;
-  if (c->fmm.ready) {
+  if (c->fmm.ready && c->fmm.scope == 0) {
     if ((rc = fmm_translate(c, nrhs, (const double2*)c->ws_x.ptr, (double2*)c->ws_alpha.ptr,
                             precision == LSMS_MIXED, c->stream)))
       return rc;

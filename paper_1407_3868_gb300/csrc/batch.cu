@@ -64,6 +64,7 @@ extern "C" int lsms_set_layouts(lsms_ctx* c, int n_layouts, const int* counts, c
     k->split_mult = c->split_mult;
     k->fmm.box_width = c->fmm.box_width;
     k->fmm.order_req = c->fmm.order_req;
+    k->fmm.scope = c->fmm.scope;
     c->kids.push_back(k);
     if (c->custom_diag && (rc = lsms_set_scattering_diagonal(k, reinterpret_cast<const double*>(c->S.data())))) {
       const std::string m = k->err;

@@ -744,6 +744,17 @@ extern "C" int lsms_set_fmm(lsms_ctx* c, double box_width, int order) {
   return LSMS_OK;
 }
 
+extern "C" int lsms_set_fmm_scope(lsms_ctx* c, int scope) {
+  if (!c) return LSMS_ERR_ARG;
+  if (scope != LSMS_FMM_ALL && scope != LSMS_FMM_RESIDUAL)
+    return ctx_fail(c, LSMS_ERR_ARG, "set_fmm_scope: LSMS_FMM_ALL or LSMS_FMM_RESIDUAL");
+  cudaStreamSynchronize(c->stream);
+  batch_clear_graphs(c);
+  c->fmm.scope = scope;
+  for (lsms_ctx* k : c->kids) k->fmm.scope = scope;
+  return LSMS_OK;
+}
+
 extern "C" int lsms_fmm_stats(lsms_ctx* c, long long* near_pairs, double* far_ms, double* near_ms) {
   if (!c) return LSMS_ERR_ARG;
   FmmState& f = c->fmm;

@@ -772,7 +772,8 @@ int solve_systems(lsms_ctx* c, const GmSys& s, const double2* rhs, double2* xs, 
         cudaMemcpyAsync(resv, rhs, LT * sizeof(double2), cudaMemcpyDeviceToDevice, st);
         std::fill(rn.begin(), rn.end(), 1.0);
       } else {
-        if ((rc = apply_device(c, s.apply_nrhs, xs, tmp, LSMS_APPLY_SCALED, st))) return rc;
+        if ((rc = apply_device(c, s.apply_nrhs, xs, tmp, LSMS_APPLY_SCALED | LSMS_APPLY_RESIDUAL_INTERNAL, st)))
+          return rc;
         k_sub<<<grid_for(LT, 256), 256, 0, st>>>(resv, rhs, tmp, LT);
         std::vector<double> r;
         norms_device(resv, s, tmp, st, r);
@@ -821,7 +822,8 @@ int solve_systems(lsms_ctx* c, const GmSys& s, const double2* rhs, double2* xs, 
   bool need = false;
   for (int b = 0; b < nb; ++b) need = need || rel64[b] < 0.0;
   if (need) {
-    if ((rc = apply_device(c, s.apply_nrhs, xs, tmp, LSMS_APPLY_SCALED, st))) return rc;
+    if ((rc = apply_device(c, s.apply_nrhs, xs, tmp, LSMS_APPLY_SCALED | LSMS_APPLY_RESIDUAL_INTERNAL, st)))
+      return rc;
     k_sub<<<grid_for(LT, 256), 256, 0, st>>>(resv, rhs, tmp, LT);
     std::vector<double> r, b2;
     norms_device(resv, s, tmp, st, r);

@@ -12,6 +12,9 @@
 using cplx = std::complex<double>;
 
 #define LSMS_MAX_P 15          // P = 2p + 1 <= 31 fits one warp of lanes over orders
+// internal apply flag (above the public LSMS_APPLY_* bits): the FP64 residual of the mixed
+// refinement, which takes the box translation when its scope is LSMS_FMM_RESIDUAL
+#define LSMS_APPLY_RESIDUAL_INTERNAL (1 << 12)
 
 // ------------------------------------------------------------------------------------------
 // Device buffer owned by a context (grown on demand, never shrunk).
@@ -37,6 +40,7 @@ struct FmmState {
   double box_width = 0.0;           // > 0: translation through boxes of this width
   int order_req = 0;                // requested box order (0: k2 r_box + 32)
   bool ready = false;
+  int scope = 0;                    // 0: every translation; 1: only the FP64 refinement residuals
   bool far = false;                 // at least three boxes: a far field exists
   int order = 0, S = 0, nb = 0, n1 = 0, n2 = 0, dmin = 2;   // dmin: smallest offset in the FFT
   double x0 = 0.0;

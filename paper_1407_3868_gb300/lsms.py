@@ -25,9 +25,10 @@ LIB_PATH = os.path.join(HERE, "_build", "liblsms.so")
 LSMS_FP64, LSMS_MIXED = 0, 1
 APPLY_SCALED, APPLY_MIXED, APPLY_NO_TRANSLATION, APPLY_NO_REFLECTION, APPLY_ALPHA = 1, 2, 4, 8, 16
 FIELD_TOTAL, FIELD_SCATTERED, FIELD_PARTICLE = 0, 1, 2
+FMM_ALL, FMM_RESIDUAL = 0, 1
 STATUS = {0: "OK", -1: "ARG", -2: "GEOMETRY", -3: "NOT_CONVERGED", -4: "NONFINITE", -5: "OOM",
           -6: "CUDA", -7: "STATE"}
-EXPORTS = ["lsms_create", "lsms_layer_response", "lsms_build_contour_stack", "lsms_pec_scattering_diagonal", "lsms_scattering_diagonal_c", "lsms_set_scattering_diagonal", "lsms_inclusion_scattering_matrix_c", "lsms_set_fmm", "lsms_get_fmm", "lsms_fmm_stats", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
+EXPORTS = ["lsms_create", "lsms_layer_response", "lsms_build_contour_stack", "lsms_pec_scattering_diagonal", "lsms_scattering_diagonal_c", "lsms_set_scattering_diagonal", "lsms_inclusion_scattering_matrix_c", "lsms_set_fmm", "lsms_set_fmm_scope", "lsms_get_fmm", "lsms_fmm_stats", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
            "lsms_get_scattering_matrix", "lsms_inclusion_scattering_matrix", "lsms_set_particles", "lsms_apply", "lsms_apply_ex", "lsms_apply_dev",
            "lsms_translate", "lsms_aggregate", "lsms_reflect", "lsms_disaggregate", "lsms_incident",
            "lsms_get_contour", "lsms_get_scattering", "lsms_num_nodes", "lsms_num_particles",
@@ -75,6 +76,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsms_set_particles": (i, [_P, i, _D]),
         "lsms_set_scattering_matrix": (i, [_P, _D]),
         "lsms_set_fmm": (i, [_P, d, i]),
+        "lsms_set_fmm_scope": (i, [_P, i]),
         "lsms_get_fmm": (i, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "lsms_fmm_stats": (i, [_P, ctypes.POINTER(ctypes.c_longlong), _D, _D]),
         "lsms_set_orientations": (i, [_P, i, _D]),
@@ -214,6 +216,11 @@ class Context:
     def set_fmm(self, box_width: float, order: int = 0):
         """Translation through boxes of this width (0: all pairs); order 0 picks k2 r_box + 32."""
         self._check(self.lib.lsms_set_fmm(self.h, float(box_width), int(order)))
+
+    def set_fmm_scope(self, scope: int):
+        """lsms_set_fmm_scope: FMM_ALL (every translation) or FMM_RESIDUAL (only the FP64 residuals of
+        the mixed refinement)."""
+        self._check(self.lib.lsms_set_fmm_scope(self.h, int(scope)))
 
     def fmm_stats(self):
         """(directly translated pairs, far-part ms, near-part ms of the last timed translation)."""

@@ -100,3 +100,32 @@ def test_solve_and_fields_match_the_oracle_solution(L, golden, precision, tol, t
     ctx.close()
     for key, (e2, emax) in errs.items():
         assert e2 < target and emax < target, (precision, key, e2, emax, info["iters"])
+
+
+def test_mixed_solve_with_box_residuals_matches_the_oracle_solution(L, golden):
+    # the FP64 refinement residual through boxes (lsms_set_fmm_scope(LSMS_FMM_RESIDUAL)): the inner
+    # solves and every other application keep the all-pairs translation
+    discs, B, U = golden
+    w = inputs.WORKLOADS[NAME]
+    m = w.medium
+    hs = O.order_scale(w.p, m["k2"], m["radius"])
+    ctx = L.context_for(w, L.LSMS_MIXED)
+    ctx.set_particles(w.centres())
+    x = inputs.random_coefficients(w.n, w.p, 1, 3) / hs
+    y_all_pairs = ctx.apply(x, L.APPLY_MIXED)
+    ctx.set_fmm(4.0)
+    ctx.set_fmm_scope(L.FMM_RESIDUAL)
+    assert ctx.fmm_info()[0] > 2
+    ctx.set_timing(True)
+    y = ctx.apply(x, L.APPLY_MIXED)                    # applications keep the all-pairs translation:
+    assert ctx.fmm_stats()[1:] == (0.0, 0.0)           # the box translation has not run
+    assert rel(y, y_all_pairs, hs) < 1e-6               # (same kernels; FP32 atomics in another order)
+    beta, info = ctx.solve(w.sources, tol=1e-11, maxiter=1500)
+    assert info["status"] == 0 and info["rel_res_fp64"] < 1e-11, info
+    assert ctx.fmm_stats()[2] > 0.0                    # the residuals went through the boxes
+    ctx.set_timing(False)
+    got = beta[0][discs]
+    assert rel(got, B, hs) < 1e-8 and relmax(got, B, hs) < 1e-8
+    u = ctx.eval_field(w.targets, 0, L.FIELD_SCATTERED)
+    assert rel(u, U["scattered"]) < 1e-8 and relmax(u, U["scattered"]) < 1e-8
+    ctx.close()
