@@ -4,27 +4,30 @@
 // With R right-hand sides, alpha^l(r) = sum_{m != l} T^{lm} beta^m(r) is for every disc pair a
 // complex (P x P) . (P x R) product with the Toeplitz block T^{lm}_{nu n} = h_{n - nu},
 // h_s = H_s(k2 rho) exp(i s phi) (rho, phi: distance and angle of x_l - x_m).  It runs as real BF16
-// MMAs with FP32 accumulation in tensor memory:
+// MMAs (M = 128, N = 128, K = 16) with FP32 accumulation in tensor memory:
 //
-//   D (128 rows: 2 targets x 64, 64 columns: right-hand sides) += A (128 x 64) . B (64 x 64)^T
+//   D (128 rows: TT targets x P orders, 128 columns: Re and Im outputs of 64 right-hand sides)
+//     += A (128 x K) . B (128 x K)^T,   K = 2P padded to 64,
 //
-// A is the real embedding of two targets' Toeplitz blocks for one source disc: a row per Re alpha_nu
-// and per Im alpha_nu (64 rows per target, in the order of the operand stage below); column n
-// multiplies Re beta_n, column P + n Im beta_n; the entries are (Tr, -Ti) and (Ti, Tr).  B holds the source's coefficients for 64 right-hand
-// sides in the same K order.  Both are split into three BF16 planes x = hi + mid + lo and the six
-// plane products with terms down to 2^-16 relative are accumulated.  The Hankel sequences are the
-// FP32 ones of the CUDA-core path; near pairs (k2 rho < 25) and the self pair are left to
-// k_translate_near.
+// A row (target i, order nu) = [Re h_{n - nu}, n = 0..P-1 | Im h_{n - nu}, n = 0..P-1]; B row (Re, r)
+// = [Re beta_n(r) | -Im beta_n(r)], B row (Im, r) = [Im beta_n(r) | Re beta_n(r)], so D(Re, r) =
+// sum Re T Re beta - Im T Im beta and D(Im, r) = sum Re T Im beta + Im T Re beta.  A tile holds
+// TT = floor(128 / P) targets (5 at p = 12: 125 of 128 rows used), and each MMA instruction computes
+// 64 right-hand sides' real and imaginary parts (N = 128: the instruction's fixed cost is shared by
+// twice the columns of an N = 64 embedding with the complex structure in the rows).  Both operands
+// are split into three BF16 planes x = hi + mid + lo and the six plane products with terms down to
+// 2^-16 relative are accumulated.  The Hankel sequences are the FP32 ones of the CUDA-core path;
+// near pairs (k2 rho < 25) and the self pair are left to k_translate_near.
 //
-// A persistent CTA (one per SM) owns a contiguous range of steps (right-hand-side block, group of 8
-// target discs, source disc).  Per step: warp 0 lane 0 copies the source's B planes (24 KB,
+// A persistent CTA (one per SM) owns a contiguous range of steps (right-hand-side block, group of
+// TG = 2 TT target discs, source disc).  Per step: warp 0 lane 0 copies the source's B planes (48 KB,
 // prepared once per application in the 128-byte-swizzled shared-memory image) with a bulk copy into
-// a 3-stage ring; warps 2-5 generate the pair sequences of a chunk of 8 sources once, split them into
-// BF16 planes (two copies shifted by one element, so that every Toeplitz row is a run of aligned
-// 32-bit pairs), and write the four A tiles of the step straight into tensor memory (tcgen05.st,
-// each thread one row, 2-stage ring); warp 1 lane 0 issues 24 tcgen05.mma per tile with A from
-// tensor memory and B from shared memory into 4 accumulators (256 columns).  Every `flush` source
-// discs, warps 2-5 read the accumulators (tcgen05.ld) and add them into the FP64 output with
+// a 2-stage ring; warps 2-5 generate the pair sequences of a chunk of CHS sources once (CHS TG <= 40
+// pairs), split them into BF16 planes (two copies shifted by one element, so that every row is a run
+// of aligned 32-bit pairs), and write the two A tiles of the step straight into tensor memory
+// (tcgen05.st, each thread one row, 2-stage ring); warp 1 lane 0 issues 24 tcgen05.mma per tile with
+// A from tensor memory and B from shared memory into 2 accumulators (256 columns).  Every `flush`
+// source discs, warps 2-5 read the accumulators (tcgen05.ld) and add them into the FP64 output with
 // atomics: the tensor cores sum in FP32 with less than round-to-nearest accuracy, so the error grows
 // with the number of MMAs summed in one accumulator.  Every mbarrier wait is bounded; on a timeout
 // the CTA records an error, waits for its copies in flight, frees its tensor memory and returns.
@@ -40,45 +43,55 @@
 
 namespace {
 
-constexpr int TG = 8;                   // target discs per group
-constexpr int NTILE = TG / 2;           // accumulator tiles per group (two targets each)
-constexpr int RBLK = 64;                // right-hand sides per block (MMA N)
-constexpr int B_PLANE = RBLK * 128;     // bytes: 64 rows x 64 BF16
-constexpr int B_STAGE = 3 * B_PLANE;    // 24576
+constexpr int NTILE = 2;                // accumulator tiles per group
+constexpr int RBLK = 64;                // right-hand sides per block
+constexpr int NCOL = 2 * RBLK;          // MMA N: Re and Im columns
+constexpr int B_PLANE = NCOL * 128;     // bytes: 128 rows x 64 BF16
+constexpr int B_STAGE = 3 * B_PLANE;    // 49152
 constexpr int NA = 2, NBS = 2;          // ring depths (A in tensor memory, B in shared memory)
-constexpr int CHS = 8;                  // source discs per sequence chunk
 constexpr int SEQ = 64;                 // elements per pair sequence (>= 4p + 2)
 constexpr int NTHR = 192;               // warp 0: copies, warp 1: MMA, warps 2-5: operands, epilogue
-// split sequence of one pair: 12 arrays [plane 3][Re, Im][parity 2] of SEQ BF16 (40 words each: the
-// Re and Im arrays of a plane and parity start 16 banks apart); parity 1 is shifted by one element so that a
-// window starting at any index is read as aligned 32-bit pairs.  Pair strides are odd in words (no
-// bank conflicts between the generating threads).
-constexpr int AW = SEQ / 2 + 8;                                  // words per array (Re/Im 80 apart)
+constexpr int MAXPAIRS = 40;            // pairs per sequence chunk (CHS sources x TG targets)
+// split sequence of one pair: 12 arrays [plane 3][Re, Im][parity 2] of SEQ BF16 (40 words each);
+// parity 1 is shifted by one element so that a window starting at any index is read as aligned
+// 32-bit pairs.  Pair strides are odd in words (no bank conflicts between the generating threads).
+constexpr int AW = SEQ / 2 + 8;                                  // words per array
 constexpr int PW = 12 * AW + 1;                                  // words per pair (481, odd)
 constexpr int RAWS = SEQ + 1;                                    // float2 per raw pair sequence
-constexpr int SPLIT_BYTES = CHS * TG * PW * 4;                   // 123136
-constexpr int RAW_BYTES = CHS * TG * RAWS * 8;                   // 33280
+constexpr int SPLIT_BYTES = MAXPAIRS * PW * 4;                   // 76960
+constexpr int RAW_BYTES = MAXPAIRS * RAWS * 8;                   // 20800
 constexpr int BAR_BYTES = 256;
 constexpr size_t TC_SMEM = 1024 + (size_t)NBS * B_STAGE + SPLIT_BYTES + RAW_BYTES + BAR_BYTES;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t ACC_COLS = NTILE * RBLK;                       // 256
+constexpr uint32_t ACC_COLS = NTILE * NCOL;                       // 256
 constexpr uint32_t A_COLS = 3 * 32;                               // one A tile: 3 planes x 32 columns
-constexpr uint32_t IDESC_T = idesc_bf16(128, RBLK);
+constexpr uint32_t IDESC_T = idesc_bf16(128, NCOL);
 // plane products (A plane, B plane): hi.hi, hi.mid, mid.hi, hi.lo, lo.hi, mid.mid
 __host__ __device__ constexpr int plane_a(int q) { return q == 2 || q == 5 ? 1 : (q == 4 ? 2 : 0); }
 __host__ __device__ constexpr int plane_b(int q) { return q == 1 || q == 5 ? 1 : (q == 3 ? 2 : 0); }
 
-// B image of one (right-hand-side block, source disc): 3 planes x 64 rows (right-hand sides) x 128
-// bytes (K: Re beta_n at n, Im beta_n at P + n, zero from 2P), chunk c of row r at c ^ (r mod 8).
+// Targets per tile and group, and sources per sequence chunk, for order p.
+template <int PT>
+struct TcShape {
+  static constexpr int P = 2 * PT + 1;
+  static constexpr int TT = 128 / P;
+  static constexpr int TG = NTILE * TT;
+  static constexpr int CHS = MAXPAIRS / TG > 0 ? MAXPAIRS / TG : 1;
+};
+
+// B image of one (right-hand-side block, source disc): 3 planes x 128 rows x 128 bytes (K: first P
+// entries for Re beta_n ... see the file comment; zero from 2P); row j < 64 is output Re of
+// right-hand side j, row 64 + j its Im; chunk c of row r at c ^ (r mod 8).
 __global__ void k_pack_b_tc(const double2* __restrict__ xs, int n, int P, int nrhs, int nrb,
                             unsigned char* __restrict__ img) {
-  const long long total = (long long)nrb * n * RBLK * 8;
+  const long long total = (long long)nrb * n * NCOL * 8;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
        id += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(id & 7), r = (int)((id >> 3) & (RBLK - 1));
-    const long long sm = id >> 9;                       // rb * n + m
+    const int c = (int)(id & 7), row = (int)((id >> 3) & (NCOL - 1));
+    const long long sm = id >> 10;                      // rb * n + m
     const int m = (int)(sm % n), rb = (int)(sm / n);
-    const int rr = rb * RBLK + r;
+    const bool im_row = row >= RBLK;
+    const int rr = rb * RBLK + (row & (RBLK - 1));
     uint32_t w[3][4];
 #pragma unroll
     for (int e = 0; e < 8; e += 2) {
@@ -88,8 +101,10 @@ __global__ void k_pack_b_tc(const double2* __restrict__ xs, int n, int P, int nr
         const int kk = 8 * c + e + u;
         double x = 0.0;
         if (rr < nrhs) {
-          if (kk < P) x = xs[((size_t)rr * n + m) * P + kk].x;
-          else if (kk < 2 * P) x = xs[((size_t)rr * n + m) * P + kk - P].y;
+          const double2 b = kk < P ? xs[((size_t)rr * n + m) * P + kk]
+                                   : (kk < 2 * P ? xs[((size_t)rr * n + m) * P + kk - P] : make_double2(0.0, 0.0));
+          if (kk < P) x = im_row ? b.y : b.x;
+          else if (kk < 2 * P) x = im_row ? b.x : -b.y;
         }
         split3(x, h[u], md[u], lo[u]);
       }
@@ -97,7 +112,7 @@ __global__ void k_pack_b_tc(const double2* __restrict__ xs, int n, int P, int nr
       w[1][e / 2] = (uint32_t)__bfloat16_as_ushort(md[0]) | ((uint32_t)__bfloat16_as_ushort(md[1]) << 16);
       w[2][e / 2] = (uint32_t)__bfloat16_as_ushort(lo[0]) | ((uint32_t)__bfloat16_as_ushort(lo[1]) << 16);
     }
-    unsigned char* base = img + (size_t)sm * B_STAGE + r * 128 + ((c ^ (r & 7)) * 16);
+    unsigned char* base = img + (size_t)sm * B_STAGE + row * 128 + ((c ^ (row & 7)) * 16);
 #pragma unroll
     for (int pl = 0; pl < 3; ++pl)
       *(uint4*)(base + pl * B_PLANE) = make_uint4(w[pl][0], w[pl][1], w[pl][2], w[pl][3]);
@@ -110,6 +125,7 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
                float near_lo, const unsigned char* __restrict__ bimg, int nrhs, long long nsteps,
                int flush, double2* __restrict__ alpha, int* __restrict__ err) {
   constexpr int p = PT, P = 2 * PT + 1;
+  constexpr int TT = TcShape<PT>::TT, TG = TcShape<PT>::TG, CHS = TcShape<PT>::CHS;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sB = smem;
@@ -216,7 +232,7 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
         for (int q = 0; q < 6; ++q)
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
-            mma_bf16_ta(tmem + tt * RBLK, a0 + plane_a(q) * 32 + kk * 8,
+            mma_bf16_ta(tmem + tt * NCOL, a0 + plane_a(q) * 32 + kk * 8,
                         sw128_desc(b0 + plane_b(q) * B_PLANE + kk * 32), IDESC_T, (!first || q || kk) ? 1u : 0u);
         mma_commit(a_empty + 8 * as);
       }
@@ -234,20 +250,16 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
     mbar_wait(done, 0);
   } else if (warp >= 2) {
     // ---- operands and epilogue: 128 threads, named barrier 1.  Thread (warp, lane) owns row
-    // 32 (warp mod 4) + lane of every A tile and accumulator (its tensor-memory lane quarter).
-    // Row order inside a target's 64 rows: lane quarter e = q4 mod 2 holds the orders nu of parity
-    // e, Re alpha_nu on lanes 0-15 (nu = 2 lane + e) and Im alpha_nu on lanes 16-31; the other lanes
-    // are zero rows.  All lanes of a warp then read one parity, the Re and Im halves 16 banks
-    // apart: the window reads are free of bank conflicts.
+    // 32 (warp mod 4) + lane of every A tile and accumulator (its tensor-memory lane quarter):
+    // row = P i + nu for target i < TT of the tile and order nu; rows from TT P on are zero.
     const int b = threadIdx.x - 64;
     const int q4 = warp & 3;
-    const int half = q4 >> 1;                     // which of the tile's two targets
-    const int e = q4 & 1;
-    const bool im = lane >= 16;
-    const int nu = 2 * (lane & 15) + e;
-    const bool valid = nu < P;
+    const int row = 32 * q4 + lane;
+    const int ti = row / P;                       // target within the tile
+    const int nu = row - ti * P;
+    const bool valid = ti < TT;
     const int w0 = 2 * p - nu;                    // window start: h_{n - nu} = h[w0 + n]
-    const int par = e;                            // = w0 mod 2
+    const int par = w0 & 1;
     const uint32_t lane_addr = (uint32_t)(32 * q4) << 16;
     const ffl kf = {k_hi, k_lo}, nr = {near_hi, near_lo};
     long long t = 0, s = s0;
@@ -307,25 +319,24 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
             break;
           }
           tc_fence_after();
-          // row of the real embedding: K words (2 elements each); first half from A1 (Re for a
-          // Re row, Im for an Im row), second half from A2 (-Im, resp. Re), zero from K = 2P
-          const int i = 2 * tt + half;
-          const uint32_t* base = split + (j * TG + i) * PW;
+          // row (i, nu): K words of two elements; words 0 .. p - 1 are Re h[w0 + n] pairs, word p
+          // joins Re h[w0 + 2p] and Im h[w0], words p + 1 .. P - 1 are Im pairs (start parity
+          // flipped, P being odd), zero from K = 2P
+          const int i = tt * TT + ti;
+          const uint32_t* base = split + (j * TG + (valid ? i : 0)) * PW;
           const uint32_t taddr = tmem + lane_addr + ACC_COLS + as * A_COLS;
 #pragma unroll
           for (int pl = 0; pl < 3; ++pl) {
             uint32_t v[32];
             if (valid) {
-              const uint32_t* a1 = base + ((pl * 2 + (im ? 1 : 0)) * 2 + par) * AW + (w0 + par) / 2;
-              const uint32_t* a2e = base + ((pl * 2 + (im ? 0 : 1)) * 2 + par) * AW + (w0 + par) / 2;
-              const uint32_t* a2o = base + ((pl * 2 + (im ? 0 : 1)) * 2 + (par ^ 1)) * AW + (w0 + 1 + (par ^ 1)) / 2;
-              const uint32_t neg = im ? 0u : 0x80008000u;
+              const uint32_t* a1 = base + ((pl * 2 + 0) * 2 + par) * AW + (w0 + par) / 2;
+              const uint32_t* a2e = base + ((pl * 2 + 1) * 2 + par) * AW + (w0 + par) / 2;
+              const uint32_t* a2o = base + ((pl * 2 + 1) * 2 + (par ^ 1)) * AW + (w0 + 1 + (par ^ 1)) / 2;
 #pragma unroll
               for (int jw = 0; jw < p; ++jw) v[jw] = a1[jw];
-              v[p] = (a1[p] & 0xFFFFu) | (((a2e[0] ^ neg) & 0xFFFFu) << 16);
-              // words j > p hold A2[w0 + 2j - P], A2[w0 + 2j + 1 - P]: start parity is par ^ 1
+              v[p] = (a1[p] & 0xFFFFu) | ((a2e[0] & 0xFFFFu) << 16);
 #pragma unroll
-              for (int jw = p + 1; jw < P; ++jw) v[jw] = a2o[jw - p - 1] ^ neg;
+              for (int jw = p + 1; jw < P; ++jw) v[jw] = a2o[jw - p - 1];
 #pragma unroll
               for (int jw = P; jw < 32; ++jw) v[jw] = 0u;
             } else {
@@ -358,18 +369,19 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
         const int rb = (int)(gkey / ngroups);
 #pragma unroll 1
         for (int tt = 0; tt < NTILE; ++tt) {
-          const int l = g * TG + 2 * tt + half;
-          const bool use = l < n && valid;
-          double* o = (double*)(alpha + (size_t)l * P + (valid ? nu : 0)) + (im ? 1 : 0);
+          const int l = g * TG + tt * TT + ti;
+          const bool use = valid && l < n;
+          double* o = (double*)(alpha + (size_t)(use ? l : 0) * P + (use ? nu : 0));
 #pragma unroll 1
-          for (int cb = 0; cb < RBLK; cb += 16) {
+          for (int cb = 0; cb < NCOL; cb += 16) {
             uint32_t v[16];
-            tmem_ld16(tmem + lane_addr + tt * RBLK + cb, v);
+            tmem_ld16(tmem + lane_addr + tt * NCOL + cb, v);
             if (use) {
+              const int part = cb >= RBLK ? 1 : 0;          // Re columns, then Im
 #pragma unroll
               for (int e = 0; e < 16; ++e) {
-                const int r = rb * RBLK + cb + e;
-                if (r < nrhs) atomicAdd(o + (size_t)r * n * P * 2, (double)__uint_as_float(v[e]));
+                const int r = rb * RBLK + (cb & (RBLK - 1)) + e;
+                if (r < nrhs) atomicAdd(o + (size_t)r * n * P * 2 + part, (double)__uint_as_float(v[e]));
               }
             }
           }
@@ -400,6 +412,8 @@ void launch_tc(int grid, cudaStream_t st, const float4* cff, int n, float kh, fl
   k_translate_tc<PT><<<grid, NTHR, TC_SMEM, st>>>(cff, n, kh, kl, nh, nl, img, nrhs, nsteps, flush, alpha, err);
 }
 
+int tc_group_size(int p) { return NTILE * (128 / (2 * p + 1)); }
+
 int sm_count() {
   static int sms = 0;
   static std::once_flag once;
@@ -429,11 +443,11 @@ int translate_mixed_tc(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha,
   if ((rc = ensure(c, c->ws_tcb, (size_t)nrb * n * B_STAGE))) return rc;
   unsigned char* img = (unsigned char*)c->ws_tcb.ptr;
   cudaMemsetAsync(alpha, 0, (size_t)nrhs * n * P * sizeof(double2), st);
-  long long tot = (long long)nrb * n * RBLK * 8;
+  long long tot = (long long)nrb * n * NCOL * 8;
   long long gb = (tot + 255) / 256;
   if (gb > 152 * 32) gb = 152 * 32;
   k_pack_b_tc<<<(int)gb, 256, 0, st>>>(xs, n, P, nrhs, nrb, img);
-  const long long ngroups = (n + TG - 1) / TG;
+  const long long ngroups = (n + tc_group_size(p) - 1) / tc_group_size(p);
   const long long nsteps = (long long)nrb * ngroups * n;
   const int grid = (int)std::min<long long>(sm_count(), nsteps);
   const float kh = (float)c->k2, kl = (float)(c->k2 - (double)kh);
