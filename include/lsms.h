@@ -158,6 +158,20 @@ int lsms_apply_ex(lsms_ctx* ctx, int nrhs, const double* x, double* y, int flags
 int lsms_apply_dev(lsms_ctx* ctx, int nrhs, const double* x_dev, double* y_dev, int flags,
                    void* stream);
 
+/* lsms_apply_rows_dev — the rows of lsms_apply_dev for the target discs row0 .. row1 - 1: the block
+ *   of the operator one GPU owns when the discs are split among GPUs by rows (Sec. 3.2 Eq.
+ *   "scattmatrix"; the paper names a parallel implementation as the next step, Sec. 7).
+ *   x_dev: [nrhs][N][P] complex, every disc (the gathered coefficients); y_dev: [nrhs][row1 - row0][P]
+ *   complex, written: y_l = x_l - S (T x + R x)_l.  The translation (Lemma 3.1) runs for the owned
+ *   target rows against every source disc; the reflected coupling (Thm 5.2 -> Eq.
+ *   "sommerfeldsys" -> Lemma 5.1) is formed from all of x and its rows taken, so the only exchange
+ *   a split operator needs per application is the gathering of x.  Flags as lsms_apply_dev
+ *   (mixed precision: FP32 translation of the rows, split-BF16 contour).  Not for layout batches,
+ *   nor with the box translation in scope LSMS_FMM_ALL.  Asynchronous on `stream`.
+ *   Errors: LSMS_ERR_ARG (rows outside 0 <= row0 <= row1 <= N), LSMS_ERR_STATE. */
+int lsms_apply_rows_dev(lsms_ctx* ctx, int nrhs, int row0, int row1, const double* x_dev, double* y_dev,
+                        int flags, void* stream);
+
 /* lsms_translate — alpha^l = sum_{m != l} T^{lm} beta^m (Sec. 3.2 Lemma 3.1, Eq. "trans"), with
  *   T^{lm}[nu][n] = H_{n-nu}(k2 rho) exp(i (n - nu) phi), rho = |x_l - x_m|, phi = arg(x_l - x_m).
  *   beta, alpha: [nrhs][N][P] complex, host.  precision: LSMS_FP64 or LSMS_MIXED. */

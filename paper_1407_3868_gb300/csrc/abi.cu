@@ -156,6 +156,80 @@ int apply_device(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags,
   return check_cuda(c, "apply");
 }
 
+// alpha_rows[r][i] += alpha_full[r][row0 + i] for i < nrows (complex, P per disc)
+__global__ void k_add_rows(const double2* __restrict__ full, int n, int row0, int nrows, int P, int nrhs,
+                           double2* __restrict__ rows) {
+  const long long total = (long long)nrhs * nrows * P;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long per = (long long)nrows * P;
+    const long long r = i / per, e = i - r * per;
+    const double2 v = full[(r * n + row0) * P + e];
+    rows[i] = make_double2(rows[i].x + v.x, rows[i].y + v.y);
+  }
+}
+
+// The operator for the target rows row0 .. row1 - 1 of x (all discs): y_rows = x_rows - S (T x + R x)_rows.
+// The translation runs for those rows only (the O(N^2) part, split between ranks); the reflected
+// coupling is formed whole (aggregate over every disc, per-node response, disaggregate) and its
+// rows taken, so that a rank needs only the gathered x.
+int apply_rows_device(lsms_ctx* c, int nrhs, int row0, int row1, const double2* x, double2* y, int flags,
+                      cudaStream_t st) {
+  int rc;
+  if ((rc = need_particles(c))) return rc;
+  if (is_batch(c)) return fail(c, LSMS_ERR_ARG, "apply_rows: not available on a layout batch");
+  const int n = c->n, P = c->P;
+  if (nrhs < 0 || row0 < 0 || row1 < row0 || row1 > n)
+    return fail(c, LSMS_ERR_ARG, "apply_rows: need nrhs >= 0 and 0 <= row0 <= row1 <= number of discs");
+  if (c->fmm.ready && c->fmm.scope == LSMS_FMM_ALL)
+    return fail(c, LSMS_ERR_ARG, "apply_rows: the translation through boxes is on (use LSMS_FMM_RESIDUAL or turn it off)");
+  const int nrows = row1 - row0;
+  const size_t len = (size_t)nrhs * n * P, len_rows = (size_t)nrhs * nrows * P;
+  if (len_rows == 0) return LSMS_OK;
+  const int mode = (flags & LSMS_APPLY_SCALED) ? 1 : 0;
+  const bool mixed = (flags & LSMS_APPLY_MIXED) != 0;
+  if ((rc = ensure(c, c->ws_xs, len * sizeof(double2)))) return rc;
+  if ((rc = ensure(c, c->ws_alpha, len * sizeof(double2)))) return rc;
+  if ((rc = ensure(c, c->ws_rows, len_rows * sizeof(double2)))) return rc;
+  double2* xs = (double2*)c->ws_xs.ptr;
+  double2* alpha = (double2*)c->ws_alpha.ptr;          // reflected coupling, all rows
+  double2* arows = (double2*)c->ws_rows.ptr;           // translation + reflection, the rows
+  launch_scale_in(x, c->d_scale_in + mode * P, xs, nrhs, n, P, st);
+  if (!(flags & LSMS_APPLY_NO_TRANSLATION)) {
+    if (mixed) {
+      if ((rc = translate_mixed_rows(c, nrhs, xs, arows, row0, nrows, st))) return rc;
+    } else {
+      launch_translate_f64(c->d_cx, c->d_cy, n, c->p, c->k2, xs, arows, nrhs, st, row0, nrows);
+    }
+  } else {
+    cudaMemsetAsync(arows, 0, len_rows * sizeof(double2), st);
+  }
+  if (!(flags & LSMS_APPLY_NO_REFLECTION)) {
+    cudaMemsetAsync(alpha, 0, len * sizeof(double2), st);
+    if ((rc = mixed ? reflection_mixed(c, nrhs, xs, alpha, st) : reflection_f64(c, nrhs, xs, alpha, st))) return rc;
+    k_add_rows<<<(int)std::min<long long>((len_rows + 255) / 256, 152 * 16), 256, 0, st>>>(alpha, n, row0, nrows, P,
+                                                                                        nrhs, arows);
+  }
+  for (int r = 0; r < nrhs; ++r) {
+    const double2* xr = x + ((size_t)r * n + row0) * P;
+    const double2* ar = arows + (size_t)r * nrows * P;
+    double2* yr = y + (size_t)r * nrows * P;
+    if (c->dense && !(flags & LSMS_APPLY_ALPHA))
+      launch_scatter_dense(xr, ar, c->d_smt + (size_t)mode * P * P,
+                           c->has_theta ? (const double*)c->theta_buf.ptr + row0 : nullptr, 1, nrows, P, yr, st);
+    else
+      launch_combine(xr, ar, c->d_scale_out + mode * P, yr, 1, nrows, P, (flags & LSMS_APPLY_ALPHA) ? 1 : 0, st);
+  }
+  return check_cuda(c, "apply_rows");
+}
+
+extern "C" int lsms_apply_rows_dev(lsms_ctx* c, int nrhs, int row0, int row1, const double* x_dev, double* y_dev,
+                                   int flags, void* stream) {
+  if (!c) return LSMS_ERR_ARG;
+  if (nrhs > 0 && row1 > row0 && (!x_dev || !y_dev)) return fail(c, LSMS_ERR_ARG, "apply_rows: NULL array");
+  return apply_rows_device(c, nrhs, row0, row1, (const double2*)x_dev, (double2*)y_dev, flags, (cudaStream_t)stream);
+}
+
 // ---------------------------------------------------------------------------------------------
 // create / destroy / particles
 // ---------------------------------------------------------------------------------------------
@@ -290,7 +364,7 @@ extern "C" void lsms_destroy(lsms_ctx* c) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   DevBuf* bufs[] = {&c->ws_x, &c->ws_y, &c->ws_xs, &c->ws_alpha, &c->ws_g, &c->ws_v, &c->ws_pq,
-                    &c->ws_sig, &c->ws_aux, &c->gm_v, &c->gm_h, &c->gm_small, &c->gm_x, &c->gm_r,
+                    &c->ws_sig, &c->ws_aux, &c->ws_rows, &c->gm_v, &c->gm_h, &c->gm_small, &c->gm_x, &c->gm_r,
                     &c->gm_w, &c->sol, &c->ws_lp, &c->ws_tcb, &c->gm_b, &c->gm_mask, &c->gm_off, &c->theta_buf};
   for (DevBuf* b : bufs)
     if (b->ptr) cudaFree(b->ptr);

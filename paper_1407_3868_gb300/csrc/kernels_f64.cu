@@ -40,9 +40,12 @@ constexpr int HS = 65;   // length of a pair's sequence h_s, s = -2p..2p (4p + 1
 // Complex products use three real FMAs (Gauss): A += hr br, B += hi bi, C += (hr+hi)(br+bi);
 // alpha = (A - B) + i (C - A - B).  The sums hr+hi and br+bi are formed once, when the sequence is
 // generated and when the source coefficients are staged.
+// Target discs l = row0 .. row0 + nrows - 1 (all sources); alpha holds those rows only,
+// [nrhs][nrows][P].
 __global__ void __launch_bounds__(TW * 32, 1)
 k_translate_f64(const double* __restrict__ cx, const double* __restrict__ cy, int n, int p,
-                double k, const double2* __restrict__ xs, double2* __restrict__ alpha) {
+                double k, const double2* __restrict__ xs, double2* __restrict__ alpha, int row0,
+                int nrows) {
   extern __shared__ double2 smem[];
   double2* sb = smem;                                   // [CH][32] staged source coefficients
   double* sbs = (double*)(sb + CH * 32);                // [CH][32] their re + im
@@ -52,8 +55,8 @@ k_translate_f64(const double* __restrict__ cx, const double* __restrict__ cy, in
   const int P = 2 * p + 1;
   const int r = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int l = blockIdx.x * TW + warp;
-  const bool lvalid = l < n;
+  const int l = row0 + blockIdx.x * TW + warp;
+  const bool lvalid = l < row0 + nrows && l < n;
   const double xl = lvalid ? cx[l] : 0.0, yl = lvalid ? cy[l] : 0.0;
   const double2* xr = xs + (size_t)r * n * P;
   double2* hw = sh + (size_t)warp * CH * HS;
@@ -101,7 +104,8 @@ k_translate_f64(const double* __restrict__ cx, const double* __restrict__ cy, in
       }
     }
   }
-  if (lvalid && lane < P) alpha[(size_t)r * n * P + (size_t)l * P + lane] = make_double2(A - B, C - A - B);
+  if (lvalid && lane < P)
+    alpha[((size_t)r * nrows + (l - row0)) * P + lane] = make_double2(A - B, C - A - B);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -317,15 +321,17 @@ void launch_scale_in(const double2* x, const double* scale, double2* xs, int nrh
 }
 
 void launch_translate_f64(const double* cx, const double* cy, int n, int p, double k,
-                          const double2* xs, double2* alpha, int nrhs, cudaStream_t st) {
-  if (n == 0 || nrhs == 0) return;
+                          const double2* xs, double2* alpha, int nrhs, cudaStream_t st, int row0,
+                          int nrows) {
+  if (nrows < 0) nrows = n - row0;
+  if (n == 0 || nrhs == 0 || nrows <= 0) return;
   const size_t smem = (size_t)(CH * 32 + TW * CH * HS) * (sizeof(double2) + sizeof(double));
   static std::once_flag attr;
   std::call_once(attr, [smem] {
     cudaFuncSetAttribute(k_translate_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
-  dim3 grid((n + TW - 1) / TW, nrhs);
-  k_translate_f64<<<grid, TW * 32, smem, st>>>(cx, cy, n, p, k, xs, alpha);
+  dim3 grid((nrows + TW - 1) / TW, nrhs);
+  k_translate_f64<<<grid, TW * 32, smem, st>>>(cx, cy, n, p, k, xs, alpha, row0, nrows);
 }
 
 void launch_etables(const double* cx, const double* cy, int n, const double2* lam,

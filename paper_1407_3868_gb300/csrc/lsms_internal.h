@@ -137,6 +137,7 @@ struct lsms_ctx {
 
   // workspaces
   DevBuf ws_x, ws_y, ws_xs, ws_alpha, ws_g, ws_v, ws_pq, ws_sig, ws_aux;
+  DevBuf ws_rows;                   // the target rows of a row-range application (lsms_apply_rows_dev)
   DevBuf gm_v, gm_h, gm_small, gm_x, gm_r, gm_w, gm_b, gm_mask, gm_off;
   double* h_pinned = nullptr;       // small pinned host scratch for residual polling
   cudaEvent_t gm_ev[8] = {};        // events of the GMRES residual ring
@@ -203,8 +204,10 @@ int validate_geometry(const lsms_ctx* c, int n, const double* xy, std::string& e
 // ------------------------------------------------------------------------------------------
 void launch_scale_in(const double2* x, const double* scale, double2* xs, int nrhs, int n, int P,
                      cudaStream_t st);
+// target rows row0 .. row0 + nrows - 1 (nrows < 0: to the last disc); alpha: [nrhs][nrows][P]
 void launch_translate_f64(const double* cx, const double* cy, int n, int p, double k,
-                          const double2* xs, double2* alpha, int nrhs, cudaStream_t st);
+                          const double2* xs, double2* alpha, int nrhs, cudaStream_t st, int row0 = 0,
+                          int nrows = -1);
 void launch_etables(const double* cx, const double* cy, int n, const double2* lam,
                     const double2* g2, int ns, double d, double2* eagg, double2* edis,
                     cudaStream_t st);

@@ -45,8 +45,13 @@ int build_lowp_tables(lsms_ctx* c);
 int translate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st);
 // the same for blocks of right-hand sides on the tensor cores, near pairs excluded (translate_tc.cu)
 int translate_mixed_tc(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st);
-// alpha += near-pair terms of T xs32 (FP64-accurate sequences, FP32 coefficients)
-void launch_translate_near(lsms_ctx* c, int nrhs, const float2* xs32, double2* alpha, cudaStream_t st);
+// alpha += near-pair terms of T xs32 (FP64-accurate sequences, FP32 coefficients); for target rows
+// row0 .. row0 + nrows - 1 (nrows < 0: to the last disc), alpha [nrhs][nrows][P]
+void launch_translate_near(lsms_ctx* c, int nrhs, const float2* xs32, double2* alpha, cudaStream_t st,
+                           int row0 = 0, int nrows = -1);
+// alpha_rows = rows row0 .. row0 + nrows - 1 of T xs (xs: all discs), FP32 arithmetic, [nrhs][nrows][P]
+int translate_mixed_rows(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha_rows, int row0, int nrows,
+                         cudaStream_t st);
 int aggregate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* G, cudaStream_t st);
 int disaggregate_mixed(lsms_ctx* c, int nrhs, const double2* V, double2* alpha, cudaStream_t st);
 int reflection_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st);

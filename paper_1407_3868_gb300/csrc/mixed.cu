@@ -156,13 +156,12 @@ k_translate_f32(const float4* __restrict__ cff, int n, float k_hi, float k_lo,
 // sources.  Per source order n the lane keeps a rolling window of the VB sequence values
 // h_{n - nu} it needs, loads one new value and the source coefficient, and per output forms the
 // Gauss products with one packed FMA (fma.rn.f32x2: h_r b_r and h_i b_i into the accumulator pair)
-// and one FMA ((h_r + h_i)(b_r + b_i)): two issue slots for three FMAs.  The source orders run in
-// two blocks of VB (the coefficients are staged with one zero order appended, P + 1 = 2 VB), the
-// block loop not unrolled: the contraction's code stays small enough for the instruction cache.  The coefficient and its sum (b_r + b_i) are staged once per
-// chunk, so the contraction spends one FADD (the window value's sum) per 3 VB FMAs.  Slots hold the
-// 4p + 1 values of a pair with stride HS2 = 4p + 3 (odd: the 16 lanes of a half read 16 distinct
-// bank pairs; at least 4p + 3: the upper half's first window read, one entry before its slot, and
-// the padded order's read, two entries past the last value, land in zero margins or the guard).
+// and one FMA ((h_r + h_i)(b_r + b_i)): two issue slots for three FMAs.  The P source orders are
+// unrolled (VB + VB - 1 steps; at p = 14 about 900 instructions, within the instruction cache).  The
+// coefficient and its sum (b_r + b_i) are staged once per chunk, so the contraction spends one FADD
+// (the window value's sum) per 3 VB FMAs.  Slots hold the 4p + 1 values of a pair with stride
+// HS = 4p + 3 (odd: the 16 lanes of a half read 16 distinct bank pairs; at least 4p + 2: the upper
+// half's first window read, one entry before its slot, lands in a zero margin or the guard).
 template <int PT>
 struct H2 {
   static constexpr int p = PT;
@@ -178,21 +177,21 @@ template <int PT>
 __global__ void __launch_bounds__(MW * 32, 3)
 k_translate_f32_h2(const float4* __restrict__ cff, int n, float k_hi, float k_lo,
                    const float2* __restrict__ xs, float2* __restrict__ part, int src_per_split,
-                   int nrhs, float near_hi, float near_lo) {
+                   int nrhs, float near_hi, float near_lo, int row0, int nrows) {
   constexpr int p = PT;
   constexpr int P = H2<PT>::P;
   constexpr int VB = H2<PT>::VB;
   constexpr int HS = H2<PT>::HS;
-  __shared__ float2 sb[MCH][2 * VB];
-  __shared__ float sbs[MCH][2 * VB];
+  __shared__ float2 sb[MCH][P];
+  __shared__ float sbs[MCH][P];
   __shared__ float4 sc[MCH];
   extern __shared__ float2 sh[];
   const int r = blockIdx.z;
   const int split = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = lane & 15, hh = lane >> 4;       // hh = output half (contraction) = source (generation)
-  const int l = (blockIdx.x * MW + warp) * MT2 + t;
-  const bool lvalid = l < n;
+  const int l = row0 + (blockIdx.x * MW + warp) * MT2 + t;     // target rows row0 .. row0 + nrows - 1
+  const bool lvalid = l < row0 + nrows && l < n;
   const float4 ct = lvalid ? cff[l] : make_float4(0.f, 0.f, 0.f, 0.f);
   for (int i = threadIdx.x; i < H2<PT>::SLOTS; i += blockDim.x) sh[i] = make_float2(0.f, 0.f);
   float2* hw = sh + GUARD + warp * 32 * HS;
@@ -210,9 +209,9 @@ k_translate_f32_h2(const float4* __restrict__ cff, int n, float k_hi, float k_lo
   for (int j0c = jbeg; j0c < jend; j0c += MCH) {
     const int cnt = min(MCH, jend - j0c);
     __syncthreads();
-    for (int i = threadIdx.x; i < MCH * 2 * VB; i += blockDim.x) {
-      const int s = i / (2 * VB), q = i - s * (2 * VB);
-      const float2 v = (s < cnt && q < P) ? xr[(size_t)(j0c + s) * P + q] : make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < MCH * P; i += blockDim.x) {
+      const int s = i / P, q = i - s * P;
+      const float2 v = s < cnt ? xr[(size_t)(j0c + s) * P + q] : make_float2(0.f, 0.f);
       sb[s][q] = v;
       sbs[s][q] = v.x + v.y;
     }
@@ -242,32 +241,32 @@ k_translate_f32_h2(const float4* __restrict__ cff, int n, float k_hi, float k_lo
           win[i] = hs[-1 - i];
           ws[i] = win[i].x + win[i].y;
         }
-#pragma unroll 1
-        for (int nb = 0; nb < 2 * VB; nb += VB) {
+        auto order = [&](int nn) {                   // source order nn: shift, load, 3 VB FMAs
 #pragma unroll
-          for (int u = 0; u < VB; ++u) {
-#pragma unroll
-            for (int i = VB - 1; i > 0; --i) {
-              win[i] = win[i - 1];
-              ws[i] = ws[i - 1];
-            }
-            win[0] = hs[nb + u];
-            ws[0] = win[0].x + win[0].y;
-            const float2 b = bq[nb + u];
-            const float bsum = bsq[nb + u];
-#pragma unroll
-            for (int i = 0; i < VB; ++i) {
-              AB[i] = __ffma2_rn(win[i], b, AB[i]);
-              C[i] = __fmaf_rn(ws[i], bsum, C[i]);
-            }
+          for (int i = VB - 1; i > 0; --i) {
+            win[i] = win[i - 1];
+            ws[i] = ws[i - 1];
           }
-        }
+          win[0] = hs[nn];
+          ws[0] = win[0].x + win[0].y;
+          const float2 b = bq[nn];
+          const float bsum = bsq[nn];
+#pragma unroll
+          for (int i = 0; i < VB; ++i) {
+            AB[i] = __ffma2_rn(win[i], b, AB[i]);
+            C[i] = __fmaf_rn(ws[i], bsum, C[i]);
+          }
+        };
+#pragma unroll
+        for (int u = 0; u < VB; ++u) order(u);
+#pragma unroll
+        for (int u = 0; u < VB - 1; ++u) order(VB + u);
       }
       __syncwarp();
     }
   }
   if (lvalid) {
-    float2* out = part + (((size_t)split * nrhs + r) * n + l) * P;
+    float2* out = part + (((size_t)split * nrhs + r) * nrows + (l - row0)) * P;
 #pragma unroll
     for (int i = 0; i < VB; ++i) {
       const int nu = VB * hh + i;
@@ -314,15 +313,17 @@ __global__ void k_near_sequences(const double* __restrict__ cx, const double* __
   }
 }
 
-// alpha[r][l][nu] += sum over near sources m of sum_n h^{lm}_{n - nu} xs^m_n; one warp per target.
+// alpha[r][l - row0][nu] += sum over near sources m of sum_n h^{lm}_{n - nu} xs^m_n for the target
+// rows l = row0 .. row0 + nrows - 1; one warp per target.
 __global__ void k_translate_near(const int* __restrict__ ptr, const int* __restrict__ idx,
                                  const float2* __restrict__ table, int n, int p,
-                                 const float2* __restrict__ xs, double2* __restrict__ alpha) {
-  const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+                                 const float2* __restrict__ xs, double2* __restrict__ alpha, int row0,
+                                 int nrows) {
+  const int l = row0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.y;
   const int P = 2 * p + 1, S = 4 * p + 1;
-  if (l >= n || lane >= P) return;
+  if (l >= row0 + nrows || l >= n || lane >= P) return;
   const float2* xr = xs + (size_t)r * n * P;
   float ar = 0.f, ai = 0.f;
   for (int e = ptr[l]; e < ptr[l + 1]; ++e) {
@@ -336,7 +337,7 @@ __global__ void k_translate_near(const int* __restrict__ ptr, const int* __restr
       ai = __fmaf_rn(hv.y, bv.x, ai);
     }
   }
-  double2* o = alpha + ((size_t)r * n + l) * P + lane;
+  double2* o = alpha + ((size_t)r * nrows + (l - row0)) * P + lane;
   o->x += ar;
   o->y += ai;
 }
@@ -384,14 +385,15 @@ void launch_pt(dim3 grid, cudaStream_t st, const float4* cff, int n, float kh, f
 
 template <int PT>
 void launch_h2(dim3 grid, cudaStream_t st, const float4* cff, int n, float kh, float kl,
-               const float2* xs, float2* part, int sps, int nrhs, float nh, float nl) {
+               const float2* xs, float2* part, int sps, int nrhs, float nh, float nl, int row0, int nrows) {
   static std::once_flag attr;
   std::call_once(attr, [] {
     cudaFuncSetAttribute(k_translate_f32_h2<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)H2<PT>::SMEM);
   });
   grid.z = nrhs;
-  k_translate_f32_h2<PT><<<grid, MW * 32, H2<PT>::SMEM, st>>>(cff, n, kh, kl, xs, part, sps, nrhs, nh, nl);
+  k_translate_f32_h2<PT><<<grid, MW * 32, H2<PT>::SMEM, st>>>(cff, n, kh, kl, xs, part, sps, nrhs, nh, nl,
+                                                             row0, nrows);
 }
 
 // Four or more right-hand sides (orders p >= 6) are contracted four at a time against each
@@ -400,12 +402,15 @@ void launch_h2(dim3 grid, cudaStream_t st, const float4* cff, int n, float kh, f
 bool translate_uses_h2(int nrhs, int p) { return !(nrhs >= 4 && p >= 6); }
 int translate_targets_per_cta(int nrhs, int p) { return translate_uses_h2(nrhs, p) ? MW * MT2 : MW * MT; }
 
-// grid.x must be ceil(n / translate_targets_per_cta(nrhs, p)).
+// grid.x must be ceil(n / translate_targets_per_cta(nrhs, p)), or, for a range of target rows
+// (nrows >= 0: rows row0 .. row0 + nrows - 1, always the one-right-hand-side kernel),
+// ceil(nrows / (MW MT2)).
 void launch_translate_kernel(dim3 grid, cudaStream_t st, const float4* cff, int n, int p, float kh,
                              float kl, const float2* xs, float2* part, int sps, int nrhs,
-                             float nh = 0.f, float nl = 0.f) {
-  if (translate_uses_h2(nrhs, p)) {
-#define LSMS_H2(PT) launch_h2<PT>(grid, st, cff, n, kh, kl, xs, part, sps, nrhs, nh, nl)
+                             float nh = 0.f, float nl = 0.f, int row0 = 0, int nrows = -1) {
+  if (nrows >= 0 || translate_uses_h2(nrhs, p)) {
+    if (nrows < 0) nrows = n;
+#define LSMS_H2(PT) launch_h2<PT>(grid, st, cff, n, kh, kl, xs, part, sps, nrhs, nh, nl, row0, nrows)
     switch (p) {
       case 0: LSMS_H2(0); break;
       case 1: LSMS_H2(1); break;
@@ -529,11 +534,13 @@ static int translate_splits(int n, int nrhs, int p, double mult = 1.0) {
   return s;
 }
 
-void launch_translate_near(lsms_ctx* c, int nrhs, const float2* xs32, double2* alpha, cudaStream_t st) {
-  if (c->near_nnz <= 0) return;
-  dim3 gn((unsigned)((c->n * 32 + 127) / 128), (unsigned)nrhs);
+void launch_translate_near(lsms_ctx* c, int nrhs, const float2* xs32, double2* alpha, cudaStream_t st,
+                           int row0, int nrows) {
+  if (nrows < 0) nrows = c->n - row0;
+  if (c->near_nnz <= 0 || nrows <= 0) return;
+  dim3 gn((unsigned)((nrows * 32 + 127) / 128), (unsigned)nrhs);
   k_translate_near<<<gn, 128, 0, st>>>(c->d_near_ptr, c->d_near_idx, (const float2*)c->d_near_h, c->n, c->p,
-                                       xs32, alpha);
+                                       xs32, alpha, row0, nrows);
 }
 
 int translate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st) {
@@ -568,6 +575,38 @@ int translate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cu
   }
   launch_translate_near(c, nrhs, xs32, alpha, st);
   return check_cuda(c, "translate_mixed");
+}
+
+int translate_mixed_rows(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha_rows, int row0, int nrows,
+                         cudaStream_t st) {
+  const int n = c->n, p = c->p, P = c->P;
+  if (n == 0 || nrhs == 0 || nrows == 0) return LSMS_OK;
+  const long long len = (long long)nrhs * n * P, len_rows = (long long)nrhs * nrows * P;
+  const size_t b32 = (((size_t)len * sizeof(float2)) + 255) & ~size_t(255);
+  const int tpc = MW * MT2;
+  const int tiles = (nrows + tpc - 1) / tpc;
+  int splits = (int)std::ceil(c->split_mult * (152 * 3 * 4) / (double)(tiles * nrhs));
+  splits = std::max(1, std::min(splits, (n + MCH - 1) / MCH));
+  int sps = (n + splits - 1) / splits;
+  sps = ((sps + MCH - 1) / MCH) * MCH;
+  splits = (n + sps - 1) / sps;
+  int rc;
+  if ((rc = ensure(c, c->ws_lp, b32 + (size_t)splits * len_rows * sizeof(float2)))) return rc;
+  float2* xs32 = (float2*)c->ws_lp.ptr;
+  float2* part = (float2*)((unsigned char*)c->ws_lp.ptr + b32);
+  long long g = (len + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  k_to_float<<<(int)g, 256, 0, st>>>(xs, xs32, len);
+  const float kh = (float)c->k2, kl = (float)(c->k2 - (double)kh);
+  const float nh = (float)c->near_r2, nl = (float)(c->near_r2 - (double)nh);
+  dim3 grid(tiles, splits, nrhs);
+  launch_translate_kernel(grid, st, (const float4*)c->d_lp_misc, n, p, kh, kl, xs32, part, sps, nrhs, nh, nl,
+                          row0, nrows);
+  long long gr = (len_rows + 255) / 256;
+  if (gr > 152 * 16) gr = 152 * 16;
+  k_reduce_parts<<<(int)gr, 256, 0, st>>>(part, splits, len_rows, alpha_rows);
+  launch_translate_near(c, nrhs, xs32, alpha_rows, st, row0, nrows);
+  return check_cuda(c, "translate_mixed_rows");
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -29,7 +29,7 @@ FMM_ALL, FMM_RESIDUAL = 0, 1
 STATUS = {0: "OK", -1: "ARG", -2: "GEOMETRY", -3: "NOT_CONVERGED", -4: "NONFINITE", -5: "OOM",
           -6: "CUDA", -7: "STATE"}
 EXPORTS = ["lsms_create", "lsms_layer_response", "lsms_build_contour_stack", "lsms_pec_scattering_diagonal", "lsms_scattering_diagonal_c", "lsms_set_scattering_diagonal", "lsms_inclusion_scattering_matrix_c", "lsms_set_fmm", "lsms_set_fmm_scope", "lsms_get_fmm", "lsms_fmm_stats", "lsms_create_stack", "lsms_create_stack_c", "lsms_set_scattering_matrix", "lsms_set_orientations",
-           "lsms_get_scattering_matrix", "lsms_inclusion_scattering_matrix", "lsms_set_particles", "lsms_apply", "lsms_apply_ex", "lsms_apply_dev",
+           "lsms_get_scattering_matrix", "lsms_inclusion_scattering_matrix", "lsms_set_particles", "lsms_apply", "lsms_apply_ex", "lsms_apply_dev", "lsms_apply_rows_dev",
            "lsms_translate", "lsms_aggregate", "lsms_reflect", "lsms_disaggregate", "lsms_incident",
            "lsms_get_contour", "lsms_get_scattering", "lsms_num_nodes", "lsms_num_particles",
            "lsms_solve", "lsms_eval_field", "lsms_last_error", "lsms_destroy",
@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsms_apply": (i, [_P, i, _D, _D]),
         "lsms_apply_ex": (i, [_P, i, _D, _D, i]),
         "lsms_apply_dev": (i, [_P, i, _P, _P, i, _P]),
+        "lsms_apply_rows_dev": (i, [_P, i, i, i, _P, _P, i, _P]),
         "lsms_translate": (i, [_P, i, _D, _D, i]),
         "lsms_aggregate": (i, [_P, i, _D, _D, _D, i]),
         "lsms_reflect": (i, [_P, i, _D, _D, _D, _D]),
@@ -301,6 +302,19 @@ class Context:
         self._check(self.lib.lsms_apply_dev(self.h, nrhs, ctypes.c_void_p(x.data_ptr()),
                                             ctypes.c_void_p(y.data_ptr()), flags,
                                             ctypes.c_void_p(stream.cuda_stream)))
+
+    def apply_rows_dev(self, x, y, row0, row1, flags=0, stream=None):
+        """lsms_apply_rows_dev: y (nrhs, row1 - row0, P) = rows row0 .. row1 - 1 of the operator applied
+        to x (nrhs, N, P); CUDA complex128 tensors, asynchronous on `stream`."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        nrhs = x.numel() // (self.n * self.P) if self.n > 0 else 0
+        if y.numel() != nrhs * (row1 - row0) * self.P:
+            raise ValueError("apply_rows_dev: y must hold nrhs x (row1 - row0) x P values")
+        self._check(self.lib.lsms_apply_rows_dev(self.h, nrhs, int(row0), int(row1), ctypes.c_void_p(x.data_ptr()),
+                                                 ctypes.c_void_p(y.data_ptr()), flags,
+                                                 ctypes.c_void_p(stream.cuda_stream)))
 
     def translate(self, beta, precision=LSMS_FP64):
         x, nrhs = self._coeffs(beta)
