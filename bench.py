@@ -49,8 +49,9 @@ BF16_PEAK_TFLOPS, HBM_PEAK_GBS, PEAK_SOURCE = _measured_peaks()
 # DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by the SHA-256 of the
 # source files it was built from (reported as null once they change).
 TRAFFIC = {
-    # k_translate_f32<14,1>, 5000 discs: dram__bytes_read.sum 1.307 MB + dram__bytes_write.sum 0.162 MB
-    "b202b10ce1f5fdc2": 1.468672e6,
+    # k_translate_f32_h2<14>, 5000 discs: dram__bytes_read.sum 1.307 MB + dram__bytes_write.sum 0.206 MB
+    # (profiles/translate_f32_h2_disc5000_p14_ns1024.md)
+    "ed6acb97ac8199a5": 1.512448e6,
 }
 KERNEL_SOURCES = ("mixed.cu", "ff_hankel.cuh")       # k_translate_f32_h2 and its Hankel sequences
 
@@ -112,6 +113,7 @@ def parse():
     ap.add_argument("--no-solve", action="store_true", help="skip the solve timings")
     ap.add_argument("--no-fp64-solve", action="store_true", help="skip the FP64 solve (about 70 s)")
     ap.add_argument("--no-batched", action="store_true", help="skip the block and sweep measurements")
+    ap.add_argument("--no-sweep", action="store_true", help="in the batched section, skip the 128-layout sweep")
     ap.add_argument("--full", action="store_true",
                     help="also solve the 64-source block and the 128-layout sweep (mixed, a few minutes)")
     ap.add_argument("--oracle-rows", type=int, default=2,
@@ -609,6 +611,8 @@ def run_batched(args, dev, flush):
                         "refinements": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"]}
     ctx.close()
     out["block_rhs"] = blk
+    if args.no_sweep:
+        return out
     # design sweep over 128 layouts
     lay = inputs.sweep_layouts()
     h = inputs.widened_half_width(max(len(c) for c in lay))
