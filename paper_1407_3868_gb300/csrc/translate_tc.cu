@@ -52,13 +52,15 @@ constexpr int NA = 2, NBS = 2;          // ring depths (A in tensor memory, B in
 constexpr int SEQ = 64;                 // elements per pair sequence (>= 4p + 2)
 constexpr int NTHR = 192;               // warp 0: copies, warp 1: MMA, warps 2-5: operands, epilogue
 constexpr int MAXPAIRS = 40;            // pairs per sequence chunk (CHS sources x TG targets)
-// split sequence of one pair: 12 arrays [plane 3][Re, Im][parity 2] of SEQ BF16 (40 words each);
+// split sequence of one pair: 12 arrays [plane 3][Re, Im][parity 2] of SEQ BF16 (AW words each);
 // parity 1 is shifted by one element so that a window starting at any index is read as aligned
 // 32-bit pairs.  Pair strides are odd in words (no bank conflicts between the generating threads).
-constexpr int AW = SEQ / 2 + 8;                                  // words per array
-constexpr int PW = 12 * AW + 1;                                  // words per pair (481, odd)
+// AW = 48 = 16 (mod 32): a row's reads from the parity-0 and parity-1 arrays (consecutive orders nu
+// alternate parity) fall 16 banks apart, so the 32 lanes of a warp read distinct banks.
+constexpr int AW = SEQ / 2 + 16;                                 // words per array
+constexpr int PW = 12 * AW + 1;                                  // words per pair (577, odd)
 constexpr int RAWS = SEQ + 1;                                    // float2 per raw pair sequence
-constexpr int SPLIT_BYTES = MAXPAIRS * PW * 4;                   // 76960
+constexpr int SPLIT_BYTES = MAXPAIRS * PW * 4;                   // 92320
 constexpr int RAW_BYTES = MAXPAIRS * RAWS * 8;                   // 20800
 constexpr int BAR_BYTES = 256;
 constexpr size_t TC_SMEM = 1024 + (size_t)NBS * B_STAGE + SPLIT_BYTES + RAW_BYTES + BAR_BYTES;
