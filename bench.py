@@ -620,7 +620,7 @@ def run_batched(args, dev, flush):
                          inputs.observation_points(-h, h, 64, 1.5), 1e-10)
     b = lsms.context_for(ws, lsms.LSMS_MIXED)
     b.set_layouts(lay)
-    mult = b.autotune()
+    tuning = b.autotune()
     ntot = sum(len(c) for c in lay)
     x = torch.from_numpy(inputs.random_coefficients(ntot, ws.p, 1, 0)[0]).to(dev)
     y = torch.empty_like(x)
@@ -633,7 +633,9 @@ def run_batched(args, dev, flush):
     torch.cuda.synchronize()
     ms_d = time_device(lambda: b.apply_dev(x, y, lsms.APPLY_SCALED), 1, flush)
     sw = {"workload": ws.name, "layouts": len(lay), "discs": ntot, "p": ws.p, "contour_nodes": ws.n_nodes,
-          "split_mult_autotuned": mult,
+          "autotuned": {"layouts_two_lane_tiles": sum(1 for sh, _ in tuning if sh == 0),
+                        "layouts_four_lane_tiles": sum(1 for sh, _ in tuning if sh == 1),
+                        "split_mults": sorted({m for _, m in tuning})},
           "mixed": {"ms_per_sweep_apply": ms_m, "layout_applies_per_s": len(lay) * 1e3 / ms_m,
                     "launch": "one CUDA graph (128 branches)"},
           "fp64": {"ms_per_sweep_apply": ms_d, "layout_applies_per_s": len(lay) * 1e3 / ms_d}}

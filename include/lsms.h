@@ -246,11 +246,19 @@ int lsms_eval_field(lsms_ctx* ctx, int src_index, int n_tgt, const double* tgt_x
 int lsms_set_layouts(lsms_ctx* ctx, int n_layouts, const int* counts, const double* centres_xy);
 int lsms_num_layouts(const lsms_ctx* ctx);
 
-/* lsms_autotune — time candidate source-split factors of the FP32 translation on the current
- *   layout (or on the largest layout of every power-of-two size bucket of a batch) and keep the
- *   fastest; *split_mult (may be NULL) receives it.  No counterpart in the paper: a tuning step of
- *   this implementation. */
+/* lsms_autotune — time the one-right-hand-side FP32 translation on the current layout (or on the
+ *   largest layout of every power-of-two size bucket of a batch, applied to the whole bucket) in its
+ *   two tile shapes (0: two lanes per target disc, 64 targets per CTA; 1: four lanes per target, 32
+ *   per CTA, twice the CTAs for small layouts) under five source-split multipliers (0.5 .. 3), and
+ *   keep the fastest pair; *split_mult (may be NULL) receives the (last bucket's) factor.  No
+ *   counterpart in the paper: a tuning step of this implementation.
+ * lsms_get_translation_tuning / lsms_set_translation_tuning — the (shape, split multiplier) of
+ *   layout `layout` (0 or -1 for a single layout; for a batch its layout index, -1 in the setter:
+ *   every layout), e.g. to store the tuning and apply it again without timing.  shape 0 or 1,
+ *   0 < split_mult <= 64.  Errors: LSMS_ERR_ARG. */
 int lsms_autotune(lsms_ctx* ctx, double* split_mult);
+int lsms_get_translation_tuning(const lsms_ctx* ctx, int layout, int* shape, double* split_mult);
+int lsms_set_translation_tuning(lsms_ctx* ctx, int layout, int shape, double split_mult);
 
 /* lsms_set_tc_translation — mixed-precision translations of at least min_rhs right-hand sides at
  *   once (a block of sources, Sec. 3.2 Lemma 3.1 applied to every column) run on the tensor cores:

@@ -8,7 +8,7 @@
 // a join; the graph is captured on the first application with a given (x, y, flags) and replayed
 // afterwards.  A batched solve runs the layouts' solves (each a graph-captured device GMRES) from a
 // small host thread pool, largest layout first, so that the GPU works on many layouts at once.
-// lsms_autotune picks the FP32 translation's source-split factor by timing candidates.
+// lsms_autotune picks the FP32 translation's tile shape and source-split factor by timing candidates.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -62,6 +62,7 @@ extern "C" int lsms_set_layouts(lsms_ctx* c, int n_layouts, const int* counts, c
     }
     k->use_graphs = c->use_graphs;
     k->split_mult = c->split_mult;
+    k->f32_shape = c->f32_shape;
     k->fmm.box_width = c->fmm.box_width;
     k->fmm.order_req = c->fmm.order_req;
     k->fmm.scope = c->fmm.scope;
@@ -227,10 +228,14 @@ int batch_eval_field(lsms_ctx* c, int layout, int ntgt, const double* tgt, int w
 }
 
 // ---------------------------------------------------------------------------------------------
-// autotuning of the FP32 translation's source splits
+// autotuning of the FP32 translation's tile shape and source splits
 // ---------------------------------------------------------------------------------------------
-static int autotune_one(lsms_ctx* c, double* best_mult) {
+// Times the one-right-hand-side translation of c's layout in both tile shapes (two lanes per target,
+// 64 targets per CTA; four lanes per target, 32 per CTA) under five source-split multipliers and
+// keeps the fastest pair.
+static int autotune_one(lsms_ctx* c, int* best_shape, double* best_mult) {
   *best_mult = c->split_mult;
+  *best_shape = c->f32_shape;
   if (c->n <= 0) return LSMS_OK;
   const size_t len = (size_t)c->n * c->P;
   int rc;
@@ -242,24 +247,28 @@ static int autotune_one(lsms_ctx* c, double* best_mult) {
   cudaEventCreate(&e1);
   const double cand[] = {0.5, 1.0, 1.5, 2.0, 3.0};
   float best = 1e30f;
-  for (double m : cand) {
-    c->split_mult = m;
-    if ((rc = translate_mixed(c, 1, (const double2*)c->ws_xs.ptr, (double2*)c->ws_alpha.ptr, c->stream))) break;
-    cudaEventRecord(e0, c->stream);
-    for (int r = 0; r < 3; ++r)
+  for (int shape = 0; shape < 2 && !rc; ++shape)
+    for (double m : cand) {
+      c->split_mult = m;
+      c->f32_shape = shape;
       if ((rc = translate_mixed(c, 1, (const double2*)c->ws_xs.ptr, (double2*)c->ws_alpha.ptr, c->stream))) break;
-    cudaEventRecord(e1, c->stream);
-    cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) {
-      best = ms;
-      *best_mult = m;
+      cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < 3; ++r)
+        if ((rc = translate_mixed(c, 1, (const double2*)c->ws_xs.ptr, (double2*)c->ws_alpha.ptr, c->stream))) break;
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        *best_mult = m;
+        *best_shape = shape;
+      }
     }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c->split_mult = *best_mult;
+  c->f32_shape = *best_shape;
   if (rc) return rc;
   return check_cuda(c, "autotune");
 }
@@ -268,8 +277,9 @@ extern "C" int lsms_autotune(lsms_ctx* c, double* split_mult) {
   if (!c) return LSMS_ERR_ARG;
   if (c->n < 0) return ctx_fail(c, LSMS_ERR_STATE, "call lsms_set_particles or lsms_set_layouts first");
   double m = c->split_mult;
+  int shape = c->f32_shape;
   if (!is_batch(c)) {
-    const int rc = autotune_one(c, &m);
+    const int rc = autotune_one(c, &shape, &m);
     if (split_mult) *split_mult = m;
     return rc;
   }
@@ -285,12 +295,54 @@ extern "C" int lsms_autotune(lsms_ctx* c, double* split_mult) {
     for (size_t j = l; j < c->kids.size(); ++j)
       if (bucket[j] == b && c->kids[j]->n > c->kids[big]->n) big = j;
     double mb = 1.0;
-    const int rc = autotune_one(c->kids[big], &mb);
+    int sb = 0;
+    const int rc = autotune_one(c->kids[big], &sb, &mb);
     if (rc) return ctx_fail(c, rc, c->kids[big]->err);
     for (size_t j = 0; j < c->kids.size(); ++j)
-      if (bucket[j] == b) c->kids[j]->split_mult = mb;
+      if (bucket[j] == b) {
+        c->kids[j]->split_mult = mb;
+        c->kids[j]->f32_shape = sb;
+      }
     done.push_back(b);
     if (split_mult) *split_mult = mb;   // the last bucket's factor
   }
+  batch_clear_graphs(c);
+  return LSMS_OK;
+}
+
+extern "C" int lsms_get_translation_tuning(const lsms_ctx* c, int layout, int* shape, double* split_mult) {
+  if (!c) return LSMS_ERR_ARG;
+  const lsms_ctx* k = c;
+  if (is_batch(c)) {
+    if (layout < 0 || layout >= (int)c->kids.size()) return LSMS_ERR_ARG;
+    k = c->kids[layout];
+  } else if (layout > 0) {
+    return LSMS_ERR_ARG;
+  }
+  if (shape) *shape = k->f32_shape;
+  if (split_mult) *split_mult = k->split_mult;
+  return LSMS_OK;
+}
+
+extern "C" int lsms_set_translation_tuning(lsms_ctx* c, int layout, int shape, double split_mult) {
+  if (!c) return LSMS_ERR_ARG;
+  if ((shape != 0 && shape != 1) || !std::isfinite(split_mult) || !(split_mult > 0.0) || split_mult > 64.0)
+    return ctx_fail(c, LSMS_ERR_ARG, "set_translation_tuning: shape 0 or 1 and 0 < split_mult <= 64");
+  std::vector<lsms_ctx*> targets;
+  if (!is_batch(c)) {
+    if (layout > 0) return ctx_fail(c, LSMS_ERR_ARG, "set_translation_tuning: a single layout is layout 0 (or -1)");
+    targets.push_back(c);
+  } else if (layout < 0) {
+    targets = c->kids;
+  } else if (layout < (int)c->kids.size()) {
+    targets.push_back(c->kids[layout]);
+  } else {
+    return ctx_fail(c, LSMS_ERR_ARG, "set_translation_tuning: layout out of range");
+  }
+  for (lsms_ctx* k : targets) {
+    k->f32_shape = shape;
+    k->split_mult = split_mult;
+  }
+  if (is_batch(c)) batch_clear_graphs(c);
   return LSMS_OK;
 }

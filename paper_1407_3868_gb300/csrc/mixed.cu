@@ -398,17 +398,45 @@ void launch_h2(dim3 grid, cudaStream_t st, const float4* cff, int n, float kh, f
 
 // Four or more right-hand sides (orders p >= 6) are contracted four at a time against each
 // generated sequence (k_translate_f32<p, 4>, 32 target discs per CTA); otherwise one right-hand
-// side per CTA with two lanes per target (k_translate_f32_h2, 64 target discs per CTA).
-bool translate_uses_h2(int nrhs, int p) { return !(nrhs >= 4 && p >= 6); }
-int translate_targets_per_cta(int nrhs, int p) { return translate_uses_h2(nrhs, p) ? MW * MT2 : MW * MT; }
+// side per CTA in one of two tile shapes (`shape`, chosen by lsms_autotune): 0, two lanes per
+// target (k_translate_f32_h2, 64 target discs per CTA); 1, four lanes per target
+// (k_translate_f32<p, 1>, 32 target discs per CTA: twice the CTAs for small layouts).
+bool translate_uses_block(int nrhs, int p) { return nrhs >= 4 && p >= 6; }
+bool translate_uses_h2(int nrhs, int p, int shape = 0) { return !translate_uses_block(nrhs, p) && shape == 0; }
+int translate_targets_per_cta(int nrhs, int p, int shape = 0) {
+  return translate_uses_h2(nrhs, p, shape) ? MW * MT2 : MW * MT;
+}
 
-// grid.x must be ceil(n / translate_targets_per_cta(nrhs, p)), or, for a range of target rows
-// (nrows >= 0: rows row0 .. row0 + nrows - 1, always the one-right-hand-side kernel),
+// grid.x must be ceil(n / translate_targets_per_cta(nrhs, p, shape)), or, for a range of target
+// rows (nrows >= 0: rows row0 .. row0 + nrows - 1, always the two-lane kernel),
 // ceil(nrows / (MW MT2)).
 void launch_translate_kernel(dim3 grid, cudaStream_t st, const float4* cff, int n, int p, float kh,
                              float kl, const float2* xs, float2* part, int sps, int nrhs,
-                             float nh = 0.f, float nl = 0.f, int row0 = 0, int nrows = -1) {
-  if (nrows >= 0 || translate_uses_h2(nrhs, p)) {
+                             float nh = 0.f, float nl = 0.f, int row0 = 0, int nrows = -1, int shape = 0) {
+  if (!translate_uses_block(nrhs, p) && nrows < 0 && shape == 1) {
+#define LSMS_T1(PT) launch_pt<PT, 1>(grid, st, cff, n, kh, kl, xs, part, sps, nrhs, nh, nl)
+    switch (p) {
+      case 0: LSMS_T1(0); break;
+      case 1: LSMS_T1(1); break;
+      case 2: LSMS_T1(2); break;
+      case 3: LSMS_T1(3); break;
+      case 4: LSMS_T1(4); break;
+      case 5: LSMS_T1(5); break;
+      case 6: LSMS_T1(6); break;
+      case 7: LSMS_T1(7); break;
+      case 8: LSMS_T1(8); break;
+      case 9: LSMS_T1(9); break;
+      case 10: LSMS_T1(10); break;
+      case 11: LSMS_T1(11); break;
+      case 12: LSMS_T1(12); break;
+      case 13: LSMS_T1(13); break;
+      case 14: LSMS_T1(14); break;
+      default: LSMS_T1(15); break;
+    }
+#undef LSMS_T1
+    return;
+  }
+  if (nrows >= 0 || !translate_uses_block(nrhs, p)) {
     if (nrows < 0) nrows = n;
 #define LSMS_H2(PT) launch_h2<PT>(grid, st, cff, n, kh, kl, xs, part, sps, nrhs, nh, nl, row0, nrows)
     switch (p) {
@@ -521,12 +549,12 @@ int build_lowp_tables(lsms_ctx* c) {
 
 // Splits of the source range so that the grid covers the GPU several times (3 CTAs per SM for one
 // right-hand side per CTA, 2 for four).
-static int translate_splits(int n, int nrhs, int p, double mult = 1.0) {
-  const int tpc = translate_targets_per_cta(nrhs, p);
+static int translate_splits(int n, int nrhs, int p, double mult = 1.0, int shape = 0) {
+  const int tpc = translate_targets_per_cta(nrhs, p, shape);
   const int tiles = (n + tpc - 1) / tpc;
-  const bool h2 = translate_uses_h2(nrhs, p);
-  const int zb = h2 ? nrhs : (nrhs + 3) / 4;
-  const int per_sm = h2 ? 3 : 2;
+  const bool blk = translate_uses_block(nrhs, p);
+  const int zb = blk ? (nrhs + 3) / 4 : nrhs;
+  const int per_sm = blk ? 2 : 3;
   int s = (int)std::ceil(mult * (152 * per_sm * 4) / (double)(tiles * zb));
   const int max_s = (n + MCH - 1) / MCH;
   if (s > max_s) s = max_s;
@@ -553,7 +581,7 @@ int translate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cu
   const bool tc = c->tc_min_rhs > 0 && nrhs >= c->tc_min_rhs && p >= 6 && p <= LSMS_MAX_P;
   int splits = 1, sps = n;
   if (!tc) {
-    splits = translate_splits(n, nrhs, p, c->split_mult);
+    splits = translate_splits(n, nrhs, p, c->split_mult, c->f32_shape);
     sps = (n + splits - 1) / splits;
     sps = ((sps + MCH - 1) / MCH) * MCH;
     splits = (n + sps - 1) / sps;
@@ -567,10 +595,11 @@ int translate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cu
   } else {
     float2* part = (float2*)((unsigned char*)c->ws_lp.ptr + b32);
     const float kh = (float)c->k2, kl = (float)(c->k2 - (double)kh);
-    const int tpc = translate_targets_per_cta(nrhs, p);
+    const int tpc = translate_targets_per_cta(nrhs, p, c->f32_shape);
     dim3 grid((n + tpc - 1) / tpc, splits, nrhs);
     const float nh = (float)c->near_r2, nl = (float)(c->near_r2 - (double)nh);
-    launch_translate_kernel(grid, st, (const float4*)c->d_lp_misc, n, p, kh, kl, xs32, part, sps, nrhs, nh, nl);
+    launch_translate_kernel(grid, st, (const float4*)c->d_lp_misc, n, p, kh, kl, xs32, part, sps, nrhs, nh, nl,
+                            0, -1, c->f32_shape);
     k_reduce_parts<<<(int)g, 256, 0, st>>>(part, splits, len, alpha);
   }
   launch_translate_near(c, nrhs, xs32, alpha, st);

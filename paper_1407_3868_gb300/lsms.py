@@ -35,7 +35,8 @@ EXPORTS = ["lsms_create", "lsms_layer_response", "lsms_build_contour_stack", "ls
            "lsms_solve", "lsms_eval_field", "lsms_last_error", "lsms_destroy",
            "lsms_build_contour", "lsms_scattering_diagonal", "lsms_check_geometry",
            "lsms_set_timing", "lsms_last_timing", "lsms_translate_mixed_noalloc",
-           "lsms_set_layouts", "lsms_num_layouts", "lsms_autotune", "lsms_set_tc_translation"]
+           "lsms_set_layouts", "lsms_num_layouts", "lsms_autotune", "lsms_set_tc_translation",
+           "lsms_get_translation_tuning", "lsms_set_translation_tuning"]
 
 
 class LsmsError(RuntimeError):
@@ -114,6 +115,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsms_set_layouts": (i, [_P, i, ctypes.POINTER(ctypes.c_int), _D]),
         "lsms_num_layouts": (i, [_P]),
         "lsms_autotune": (i, [_P, _D]),
+        "lsms_get_translation_tuning": (i, [_P, i, ctypes.POINTER(ctypes.c_int), _D]),
+        "lsms_set_translation_tuning": (i, [_P, i, i, d]),
         "lsms_set_tc_translation": (i, [_P, i, i]),
     }
     for name, (res, args) in sig.items():
@@ -209,10 +212,46 @@ class Context:
         self.n = int(counts.sum())
         self.layout_counts = counts
 
-    def autotune(self):
-        m = ctypes.c_double()
-        self._check(self.lib.lsms_autotune(self.h, ctypes.byref(m)))
-        return m.value
+    def autotune(self, cache=None):
+        """lsms_autotune: the FP32 translation's tile shape and source-split factor per size bucket.
+
+        cache: path of a JSON file of earlier results, keyed by (p, contour nodes, power-of-two size
+        bucket): when every layout's bucket is there the stored tuning is applied without timing,
+        otherwise the library times the candidates and the file is updated.  Returns the list of
+        (shape, split multiplier) per layout."""
+        import json
+        counts = self.layout_counts if getattr(self, "layout_counts", None) is not None else [self.n]
+        keys = [f"p{self.p}_ns{self.ns}_b{int(np.ceil(np.log2(n))) if n > 0 else 0}" for n in counts]
+        table = {}
+        if cache is not None and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+        batch = getattr(self, "layout_counts", None) is not None
+        if cache is not None and all(k in table for k in keys):
+            for layout, k in enumerate(keys):
+                self.set_translation_tuning(layout if batch else -1, table[k]["shape"], table[k]["split_mult"])
+        else:
+            m = ctypes.c_double()
+            self._check(self.lib.lsms_autotune(self.h, ctypes.byref(m)))
+        tuning = [self.translation_tuning(layout if batch else 0) for layout in range(len(counts))]
+        if cache is not None:
+            for k, (shape, mult) in zip(keys, tuning):
+                table[k] = {"shape": shape, "split_mult": mult}
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return tuning
+
+    def translation_tuning(self, layout=0):
+        """lsms_get_translation_tuning: (tile shape, split multiplier) of a layout."""
+        shape, mult = ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.lsms_get_translation_tuning(self.h, int(layout), ctypes.byref(shape), ctypes.byref(mult)))
+        return shape.value, mult.value
+
+    def set_translation_tuning(self, layout, shape, split_mult):
+        """lsms_set_translation_tuning (layout -1: every layout)."""
+        self._check(self.lib.lsms_set_translation_tuning(self.h, int(layout), int(shape), float(split_mult)))
 
     def set_fmm(self, box_width: float, order: int = 0):
         """Translation through boxes of this width (0: all pairs); order 0 picks k2 r_box + 32."""

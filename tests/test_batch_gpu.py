@@ -89,20 +89,40 @@ def test_batch_solve_equals_single_layout_solves(L, precision, tol):
     batch.close()
 
 
-def test_autotune_keeps_results(L):
+def test_autotune_keeps_results(L, tmp_path):
+    # the tuner picks a tile shape and a split factor; both tile shapes give the same translation
     w = inputs.WORKLOADS["disc1000_p12_ns512"]
     ctx = L.context_for(w)
     ctx.set_particles(w.centres())
     x = inputs.random_coefficients(w.n, w.p, 1, 3)
     a0 = ctx.translate(x, precision=L.LSMS_MIXED)
-    mult = ctx.autotune()
-    assert mult > 0
+    (shape, mult), = ctx.autotune()
+    assert shape in (0, 1) and mult > 0 and ctx.translation_tuning() == (shape, mult)
     a1 = ctx.translate(x, precision=L.LSMS_MIXED)
     assert rel(a1, a0) < 1e-5
+    for s in (0, 1):
+        ctx.set_translation_tuning(-1, s, 1.0)
+        assert rel(ctx.translate(x, precision=L.LSMS_MIXED), a0) < 1e-5, s
+    with pytest.raises(L.LsmsError) as e:
+        ctx.set_translation_tuning(-1, 2, 1.0)
+    assert e.value.code == -1
     ctx.close()
-    batch = L.context_for(workload())
-    batch.set_layouts(layouts())
-    assert batch.autotune() > 0
+    # a batch: one tuning per size bucket, stored in a JSON cache and applied again from it
+    lay = layouts() + [inputs.layout(150, -45.0, 45.0, 99)]
+    cache = str(tmp_path / "tuning.json")
+    batch = L.context_for(workload(), L.LSMS_MIXED)
+    batch.set_layouts(lay)
+    xb = np.concatenate([inputs.random_coefficients(len(c), 8, 1, 60 + i)[0] for i, c in enumerate(lay)])
+    y0 = batch.apply(xb, L.APPLY_MIXED)[0]
+    t1 = batch.autotune(cache=cache)
+    assert len(t1) == len(lay) and all(s in (0, 1) and m > 0 for s, m in t1)
+    import json
+    table = json.load(open(cache))
+    assert all(k.startswith("p8_ns192_b") for k in table) and len(table) >= 2
+    batch.set_translation_tuning(-1, 1, 3.0)             # overwrite, then restore from the cache
+    t2 = batch.autotune(cache=cache)
+    assert t2 == t1
+    assert rel(batch.apply(xb, L.APPLY_MIXED)[0], y0) < 1e-5
     batch.close()
 
 
