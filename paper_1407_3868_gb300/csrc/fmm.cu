@@ -302,7 +302,8 @@ k_fmm_near(const double* __restrict__ scx, const double* __restrict__ scy, const
 // FP32 kernel, restricted to adjacent boxes; pairs with k rho < 25 are left to the near-pair kernel
 // (FP64-accurate sequences).  Inputs and outputs in box order.
 // ---------------------------------------------------------------------------------------------
-constexpr int BW = 4;      // warps per CTA
+constexpr int BW = 1;      // warps per CTA: each warp's 8 targets (about one box) get their own
+                           // source window, three to four boxes wide instead of a 32-target CTA's six
 constexpr int BT = 8;      // target discs per warp
 constexpr int BCH = 32;    // sources staged per chunk
 constexpr int BHS = 65;    // pair slot stride (see the all-pairs FP32 kernel: conflict-free windows)
@@ -310,7 +311,7 @@ constexpr int BGUARD = 8;
 constexpr size_t BOX_NEAR_SMEM = (size_t)(2 * BGUARD + BW * 32 * BHS) * sizeof(float2);
 
 template <int PT>
-__global__ void __launch_bounds__(BW * 32, 3)
+__global__ void __launch_bounds__(BW * 32, 8)
 k_box_near_f32(const float4* __restrict__ cff, const int* __restrict__ sbox, const int* __restrict__ bstart,
                int nb, int n, float k_hi, float k_lo, float near_hi, float near_lo,
                const float2* __restrict__ xs, float2* __restrict__ out) {
@@ -334,9 +335,13 @@ k_box_near_f32(const float4* __restrict__ cff, const int* __restrict__ sbox, con
   const int jbeg = bstart[max(b0 - 1, 0)], jend = bstart[min(b1 + 2, nb)];
   for (int i = threadIdx.x; i < 2 * BGUARD + BW * 32 * BHS; i += blockDim.x) sh[i] = make_float2(0.f, 0.f);
   float2* hw = sh + BGUARD + warp * 32 * BHS;
-  float A[VB], B[VB], C[VB];
+  float2 AB[VB];           // (sum h_r b_r, sum h_i b_i), one packed FMA per window value
+  float C[VB];
 #pragma unroll
-  for (int i = 0; i < VB; ++i) A[i] = B[i] = C[i] = 0.f;
+  for (int i = 0; i < VB; ++i) {
+    AB[i] = make_float2(0.f, 0.f);
+    C[i] = 0.f;
+  }
   const ffl kf = {k_hi, k_lo};
   const float2* xr = xs + (size_t)r * n * P;
   for (int j0c = jbeg; j0c < jend; j0c += BCH) {
@@ -387,9 +392,7 @@ k_box_near_f32(const float4* __restrict__ cff, const int* __restrict__ sbox, con
             const float bsum = bv.x + bv.y;
 #pragma unroll
             for (int i = 0; i < VB; ++i) {
-              const float2 hv = win[VB - 1 + u - i];
-              A[i] = __fmaf_rn(hv.x, bv.x, A[i]);
-              B[i] = __fmaf_rn(hv.y, bv.y, B[i]);
+              AB[i] = __ffma2_rn(win[VB - 1 + u - i], bv, AB[i]);
               C[i] = __fmaf_rn(wsum[VB - 1 + u - i], bsum, C[i]);
             }
           }
@@ -408,7 +411,7 @@ k_box_near_f32(const float4* __restrict__ cff, const int* __restrict__ sbox, con
 #pragma unroll
     for (int i = 0; i < VB; ++i) {
       const int nu = VB * hi8 + i;
-      if (nu < P) o[nu] = make_float2(A[i] - B[i], C[i] - A[i] - B[i]);
+      if (nu < P) o[nu] = make_float2(AB[i].x - AB[i].y, C[i] - AB[i].x - AB[i].y);
     }
   }
 }

@@ -22,15 +22,17 @@
 // A persistent CTA (one per SM) owns a contiguous range of steps (right-hand-side block, group of
 // TG = 2 TT target discs, source disc).  Per step: warp 0 lane 0 copies the source's B planes (48 KB,
 // prepared once per application in the 128-byte-swizzled shared-memory image) with a bulk copy into
-// a 2-stage ring; warps 2-5 generate the pair sequences of a chunk of CHS sources once (CHS TG <= 40
-// pairs), split them into BF16 planes (two copies shifted by one element, so that every row is a run
-// of aligned 32-bit pairs), and write the two A tiles of the step straight into tensor memory
-// (tcgen05.st, each thread one row, 2-stage ring); warp 1 lane 0 issues 24 tcgen05.mma per tile with
-// A from tensor memory and B from shared memory into 2 accumulators (256 columns).  Every `flush`
-// source discs, warps 2-5 read the accumulators (tcgen05.ld) and add them into the FP64 output with
-// atomics: the tensor cores sum in FP32 with less than round-to-nearest accuracy, so the error grows
-// with the number of MMAs summed in one accumulator.  Every mbarrier wait is bounded; on a timeout
-// the CTA records an error, waits for its copies in flight, frees its tensor memory and returns.
+// a 3-stage ring; warps 6-7 generate the FP32 pair sequences of the next chunk of CHS sources
+// (CHS TG <= 64 pairs, one per thread) into the other of two chunk buffers, one chunk ahead of their
+// use; warps 2-5 build the two A tiles of the step from the current chunk's sequences (each thread
+// one row: its 2P entries split into three BF16 planes on the fly) and write them straight into
+// tensor memory (tcgen05.st, 2-stage ring); warp 1 lane 0 issues 24 tcgen05.mma per tile with A
+// from tensor memory and B from shared memory into 2 accumulators (256 columns).  Every `flush`
+// source discs, warps 2-5 read the accumulators (tcgen05.ld) and add them into the FP64 output
+// with atomics: the tensor cores sum in FP32 with less than round-to-nearest accuracy, so the error
+// grows with the number of MMAs summed in one accumulator.  Every mbarrier wait is bounded; on a
+// timeout the CTA records an error, waits for its copies in flight, frees its tensor memory and
+// returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -48,22 +50,16 @@ constexpr int RBLK = 64;                // right-hand sides per block
 constexpr int NCOL = 2 * RBLK;          // MMA N: Re and Im columns
 constexpr int B_PLANE = NCOL * 128;     // bytes: 128 rows x 64 BF16
 constexpr int B_STAGE = 3 * B_PLANE;    // 49152
-constexpr int NA = 2, NBS = 2;          // ring depths (A in tensor memory, B in shared memory)
+constexpr int NA = 2, NBS = 3;          // ring depths (A in tensor memory, B in shared memory)
 constexpr int SEQ = 64;                 // elements per pair sequence (>= 4p + 2)
-constexpr int NTHR = 192;               // warp 0: copies, warp 1: MMA, warps 2-5: operands, epilogue
-constexpr int MAXPAIRS = 40;            // pairs per sequence chunk (CHS sources x TG targets)
-// split sequence of one pair: 12 arrays [plane 3][Re, Im][parity 2] of SEQ BF16 (AW words each);
-// parity 1 is shifted by one element so that a window starting at any index is read as aligned
-// 32-bit pairs.  Pair strides are odd in words (no bank conflicts between the generating threads).
-// AW = 48 = 16 (mod 32): a row's reads from the parity-0 and parity-1 arrays (consecutive orders nu
-// alternate parity) fall 16 banks apart, so the 32 lanes of a warp read distinct banks.
-constexpr int AW = SEQ / 2 + 16;                                 // words per array
-constexpr int PW = 12 * AW + 1;                                  // words per pair (577, odd)
-constexpr int RAWS = SEQ + 1;                                    // float2 per raw pair sequence
-constexpr int SPLIT_BYTES = MAXPAIRS * PW * 4;                   // 92320
-constexpr int RAW_BYTES = MAXPAIRS * RAWS * 8;                   // 20800
+constexpr int NTHR = 256;               // warp 0: copies, warp 1: MMA, warps 2-5: operands and epilogue,
+                                        // warps 6-7: pair sequences of the next chunk
+constexpr int NGEN = 64;                // generator threads
+constexpr int MAXPAIRS = NGEN;          // pairs per sequence chunk (CHS sources x TG targets)
+constexpr int RAWS = SEQ + 1;                                    // float2 per pair sequence (odd stride)
+constexpr int RAW_BYTES = 2 * MAXPAIRS * RAWS * 8;               // two chunk buffers: 66560
 constexpr int BAR_BYTES = 256;
-constexpr size_t TC_SMEM = 1024 + (size_t)NBS * B_STAGE + SPLIT_BYTES + RAW_BYTES + BAR_BYTES;
+constexpr size_t TC_SMEM = 1024 + (size_t)NBS * B_STAGE + RAW_BYTES + BAR_BYTES;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC_COLS = NTILE * NCOL;                       // 256
 constexpr uint32_t A_COLS = 3 * 32;                               // one A tile: 3 planes x 32 columns
@@ -131,15 +127,16 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sB = smem;
-  uint32_t* split = (uint32_t*)(sB + NBS * B_STAGE);
-  float2* raw = (float2*)((unsigned char*)split + SPLIT_BYTES);
+  float2* raw = (float2*)(sB + NBS * B_STAGE);               // [2][MAXPAIRS][RAWS] FP32 sequences
   uint64_t* bars = (uint64_t*)((unsigned char*)raw + RAW_BYTES);
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * NA + 2 * NBS + 3);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * NA + 2 * NBS + 3 + 4);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   volatile int* bcast = abort_flag + 1;
+  volatile int* gbcast = abort_flag + 2;
   const uint32_t a_full = smem_u32(bars), a_empty = a_full + 8 * NA;
   const uint32_t b_full = a_empty + 8 * NA, b_empty = b_full + 8 * NBS;
   const uint32_t acc_full = b_empty + 8 * NBS, acc_empty = acc_full + 8, done = acc_empty + 8;
+  const uint32_t raw_full = done + 8, raw_empty = raw_full + 16;   // two chunk buffers each
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ngroups = (n + TG - 1) / TG;
   // accumulation segment of a step: (right-hand-side block, group, block of `flush` sources); the
@@ -162,8 +159,13 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, 1);
     mbar_init(done, 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(raw_full + 8 * s, 1);
+      mbar_init(raw_empty + 8 * s, 1);
+    }
     *abort_flag = 0;
     *bcast = 0;
+    *gbcast = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
@@ -250,10 +252,12 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
     // every MMA issued by this thread has finished before the tensor memory is freed
     mma_commit(done);
     mbar_wait(done, 0);
-  } else if (warp >= 2) {
+  } else if (warp >= 2 && warp < 6) {
     // ---- operands and epilogue: 128 threads, named barrier 1.  Thread (warp, lane) owns row
     // 32 (warp mod 4) + lane of every A tile and accumulator (its tensor-memory lane quarter):
-    // row = P i + nu for target i < TT of the tile and order nu; rows from TT P on are zero.
+    // row = P i + nu for target i < TT of the tile and order nu; rows from TT P on are zero.  The
+    // rows are built from the FP32 sequences the generator warps left in the chunk's buffer: the
+    // 2P entries [Re h_{n - nu} | Im h_{n - nu}] split into three BF16 planes on the fly.
     const int b = threadIdx.x - 64;
     const int q4 = warp & 3;
     const int row = 32 * q4 + lane;
@@ -261,47 +265,25 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
     const int nu = row - ti * P;
     const bool valid = ti < TT;
     const int w0 = 2 * p - nu;                    // window start: h_{n - nu} = h[w0 + n]
-    const int par = w0 & 1;
     const uint32_t lane_addr = (uint32_t)(32 * q4) << 16;
-    const ffl kf = {k_hi, k_lo}, nr = {near_hi, near_lo};
-    long long t = 0, s = s0;
+    long long t = 0, s = s0, chunk = 0;
     int grp = 0;
     while (s < s1) {
       const long long key = segkey(s), gkey = s / n;      // gkey = rb * ngroups + g
       const int g = (int)(gkey % ngroups);
       const int m0 = (int)(s - gkey * n);
       const int cnt = (int)min((long long)min(CHS, flush - m0 % flush), min(s1 - s, (long long)(n - m0)));
-      // the chunk's pair sequences, FP32, then split into BF16 planes with both parities
-      if (b < TG * cnt) {
-        const int i = b % TG, j = b / TG;
-        const int l = g * TG + i, m = m0 + j;
-        float2* h = raw + b * RAWS;
-        if (l < n && l != m) {
-          hankel_sequence_f32<PT>(cff[l], cff[m], kf, nr, h);
-        } else {
-          for (int q = 0; q <= 4 * p; ++q) h[q] = make_float2(0.f, 0.f);
+      const int cb = (int)(chunk & 1);
+      if (b == 0) {                               // the chunk's sequences are in buffer cb
+        bool w = !*abort_flag && mbar_wait(raw_full + 8 * cb, (uint32_t)((chunk >> 1) & 1));
+        if (!w && !*abort_flag) {
+          *abort_flag = 1;
+          atomicExch(err, 15);
         }
-        // word k of (plane pl, part c): parity 0 holds elements (2k, 2k + 1), parity 1 (2k - 1, 2k)
-        uint32_t* sp = split + b * PW;
-        uint32_t prev[3][2] = {{0u, 0u}, {0u, 0u}, {0u, 0u}};
-        for (int k = 0; k < SEQ / 2; ++k) {
-          const float2 e0 = 2 * k <= 4 * p ? h[2 * k] : make_float2(0.f, 0.f);
-          const float2 e1 = 2 * k + 1 <= 4 * p ? h[2 * k + 1] : make_float2(0.f, 0.f);
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            unsigned short u0[3], u1[3];
-            split3f(c ? e0.y : e0.x, u0);
-            split3f(c ? e1.y : e1.x, u1);
-#pragma unroll
-            for (int pl = 0; pl < 3; ++pl) {
-              sp[((pl * 2 + c) * 2 + 0) * AW + k] = (uint32_t)u0[pl] | ((uint32_t)u1[pl] << 16);
-              sp[((pl * 2 + c) * 2 + 1) * AW + k] = prev[pl][c] | ((uint32_t)u0[pl] << 16);
-              prev[pl][c] = u1[pl];
-            }
-          }
-        }
+        *bcast = w ? 1 : 0;
       }
       named_bar_sync(1, 128);
+      if (!*bcast) break;
       bool ok = true;
       for (int j = 0; j < cnt && ok; ++j) {
         for (int tt = 0; tt < NTILE; ++tt, ++t) {
@@ -321,32 +303,31 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
             break;
           }
           tc_fence_after();
-          // row (i, nu): K words of two elements; words 0 .. p - 1 are Re h[w0 + n] pairs, word p
-          // joins Re h[w0 + 2p] and Im h[w0], words p + 1 .. P - 1 are Im pairs (start parity
-          // flipped, P being odd), zero from K = 2P
-          const int i = tt * TT + ti;
-          const uint32_t* base = split + (j * TG + (valid ? i : 0)) * PW;
+          // K element k < P: Re h[w0 + k]; P <= k < 2P: Im h[w0 + k - P]; word k / 2, half k mod 2
+          uint32_t v[3][32];
+#pragma unroll
+          for (int pl = 0; pl < 3; ++pl)
+#pragma unroll
+            for (int jw = 0; jw < 32; ++jw) v[pl][jw] = 0u;
+          if (valid) {
+            const float2* hr = raw + ((size_t)cb * MAXPAIRS + j * TG + tt * TT + ti) * RAWS + w0;
+#pragma unroll
+            for (int nn = 0; nn < P; ++nn) {
+              const float2 hv = hr[nn];
+              unsigned short ur[3], ui[3];
+              split3f(hv.x, ur);
+              split3f(hv.y, ui);
+              const int kr = nn, ki = P + nn;
+#pragma unroll
+              for (int pl = 0; pl < 3; ++pl) {
+                v[pl][kr >> 1] |= (uint32_t)ur[pl] << (16 * (kr & 1));
+                v[pl][ki >> 1] |= (uint32_t)ui[pl] << (16 * (ki & 1));
+              }
+            }
+          }
           const uint32_t taddr = tmem + lane_addr + ACC_COLS + as * A_COLS;
 #pragma unroll
-          for (int pl = 0; pl < 3; ++pl) {
-            uint32_t v[32];
-            if (valid) {
-              const uint32_t* a1 = base + ((pl * 2 + 0) * 2 + par) * AW + (w0 + par) / 2;
-              const uint32_t* a2e = base + ((pl * 2 + 1) * 2 + par) * AW + (w0 + par) / 2;
-              const uint32_t* a2o = base + ((pl * 2 + 1) * 2 + (par ^ 1)) * AW + (w0 + 1 + (par ^ 1)) / 2;
-#pragma unroll
-              for (int jw = 0; jw < p; ++jw) v[jw] = a1[jw];
-              v[p] = (a1[p] & 0xFFFFu) | ((a2e[0] & 0xFFFFu) << 16);
-#pragma unroll
-              for (int jw = p + 1; jw < P; ++jw) v[jw] = a2o[jw - p - 1];
-#pragma unroll
-              for (int jw = P; jw < 32; ++jw) v[jw] = 0u;
-            } else {
-#pragma unroll
-              for (int jw = 0; jw < 32; ++jw) v[jw] = 0u;
-            }
-            tmem_st32(taddr + pl * 32, v);
-          }
+          for (int pl = 0; pl < 3; ++pl) tmem_st32(taddr + pl * 32, v[pl]);
           tmem_wait_st();
           tc_fence_before();
           named_bar_sync(1, 128);
@@ -354,6 +335,8 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
         }
       }
       if (!ok) break;
+      if (b == 0) mbar_arrive(raw_empty + 8 * cb);   // every row of the chunk has been read
+      ++chunk;
       s += cnt;
       if (s == s1 || segkey(s) != key) {
         // segment done: read the accumulators and add them into alpha
@@ -375,15 +358,15 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
           const bool use = valid && l < n;
           double* o = (double*)(alpha + (size_t)(use ? l : 0) * P + (use ? nu : 0));
 #pragma unroll 1
-          for (int cb = 0; cb < NCOL; cb += 16) {
-            uint32_t v[16];
-            tmem_ld16(tmem + lane_addr + tt * NCOL + cb, v);
+          for (int cb2 = 0; cb2 < NCOL; cb2 += 16) {
+            uint32_t vv[16];
+            tmem_ld16(tmem + lane_addr + tt * NCOL + cb2, vv);
             if (use) {
-              const int part = cb >= RBLK ? 1 : 0;          // Re columns, then Im
+              const int part = cb2 >= RBLK ? 1 : 0;          // Re columns, then Im
 #pragma unroll
               for (int e = 0; e < 16; ++e) {
-                const int r = rb * RBLK + (cb & (RBLK - 1)) + e;
-                if (r < nrhs) atomicAdd(o + (size_t)r * n * P * 2 + part, (double)__uint_as_float(v[e]));
+                const int r = rb * RBLK + (cb2 & (RBLK - 1)) + e;
+                if (r < nrhs) atomicAdd(o + (size_t)r * n * P * 2 + part, (double)__uint_as_float(vv[e]));
               }
             }
           }
@@ -393,6 +376,45 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
         if (b == 0) mbar_arrive(acc_empty);
         ++grp;
       }
+    }
+  } else if (warp >= 6) {
+    // ---- generators: 64 threads, named barrier 2.  They walk the same chunks as the operand warps
+    // one chunk ahead, writing the FP32 pair sequences of chunk c into buffer c mod 2 once the
+    // operand warps have released it (chunk c - 2).
+    const int gt = threadIdx.x - 192;
+    const ffl kf = {k_hi, k_lo}, nr = {near_hi, near_lo};
+    long long s = s0, chunk = 0;
+    while (s < s1) {
+      const long long gkey = s / n;
+      const int g = (int)(gkey % ngroups);
+      const int m0 = (int)(s - gkey * n);
+      const int cnt = (int)min((long long)min(CHS, flush - m0 % flush), min(s1 - s, (long long)(n - m0)));
+      const int cb = (int)(chunk & 1);
+      if (gt == 0) {
+        bool w = !*abort_flag;
+        if (w && chunk >= 2) w = mbar_wait(raw_empty + 8 * cb, (uint32_t)(((chunk >> 1) - 1) & 1));
+        if (!w && !*abort_flag) {
+          *abort_flag = 1;
+          atomicExch(err, 16);
+        }
+        *gbcast = w ? 1 : 0;
+      }
+      named_bar_sync(2, NGEN);
+      if (!*gbcast) break;
+      if (gt < TG * cnt) {
+        const int i = gt % TG, j = gt / TG;
+        const int l = g * TG + i, m = m0 + j;
+        float2* h = raw + ((size_t)cb * MAXPAIRS + gt) * RAWS;
+        if (l < n && l != m) {
+          hankel_sequence_f32<PT>(cff[l], cff[m], kf, nr, h);
+        } else {
+          for (int q = 0; q <= 4 * p; ++q) h[q] = make_float2(0.f, 0.f);
+        }
+      }
+      named_bar_sync(2, NGEN);
+      if (gt == 0) mbar_arrive(raw_full + 8 * cb);
+      ++chunk;
+      s += cnt;
     }
   }
   __syncwarp();                                   // reconverge the producer and MMA warps
