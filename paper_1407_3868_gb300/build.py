@@ -72,7 +72,7 @@ def _build_lib(nvcc: str, verbose: bool, jobs: int | None) -> None:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
     cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
-    cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-L" + cuda_lib, "-lcufft",
+    cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-L" + cuda_lib,
            "-Xlinker", "-rpath=" + cuda_lib]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:

@@ -10,14 +10,17 @@
 // with (r_m, phi_m) the polar offset of disc m from its box centre, |q|, |nu| <= Q, and
 // phi_ij = 0 (i > j) or pi (i < j).  On the regular grid of box centres the M2L kernel depends only
 // on the box offset i - j and the order difference q - nu, so the M2L step is one two-dimensional
-// convolution (box index x order), done as a cyclic convolution with cuFFT on an n1 x n2 grid
-// (n1 >= 2 nb - 1, n2 >= 6Q + 1: no wrap-around reaches the outputs).  An FFT spreads its rounding
-// over all outputs in proportion to the largest kernel entry, and H_s(z) grows fast once |s| > z,
-// so offsets with k |d| w < 2Q + 2 (where orders up to 2Q leave the oscillatory range) are
-// translated box by box instead and left out of the FFT kernel.  The Graf shift tables
-// J_s(k r_m) e^{i s phi_m}, |s| <= Q + p, and the transformed box kernel are built once per layout.
-#include <cufft.h>
-
+// cyclic convolution (box index x order) on an n1 x n2 grid (powers of two, n1 >= 2 nb - 1,
+// n2 >= 4Q + 1: no wrap-around reaches the outputs), done with hand-written radix-2 FFTs: along
+// the boxes by the four-step split n1 = A B (A-point transforms at stride B, twiddles, B-point
+// transforms on contiguous runs, leaving the spectrum in transposed order), which the inverse
+// undoes in reverse; along the orders one n2-point transform per frequency row, the product with
+// the transformed kernel and the inverse, in one kernel.  Only the 2Q + 1 order columns that hold
+// data are transformed along the boxes.  An FFT spreads its rounding over all outputs in
+// proportion to the largest kernel entry, and H_s(z) grows fast once |s| > z, so offsets with
+// k |d| w < 2Q + 2 (where orders up to 2Q leave the oscillatory range) are translated box by box
+// instead and left out of the FFT kernel.  The Graf shift tables J_s(k r_m) e^{i s phi_m},
+// |s| <= Q + p, and the transformed box kernel are built once per layout.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -51,16 +54,6 @@ template <typename C> __device__ __forceinline__ C cconj(C a) { C r = a; r.y = -
 template <typename C> __device__ __forceinline__ C czero() { C r; r.x = 0; r.y = 0; return r; }
 template <typename C> __device__ __forceinline__ C from_d2(double2 v) { C r; r.x = v.x; r.y = v.y; return r; }
 
-// smallest n >= m whose prime factors are 2, 3, 5, 7 (sizes cuFFT handles fastest)
-int fft_size(int m) {
-  for (int n = std::max(m, 1);; ++n) {
-    int r = n;
-    for (int f : {2, 3, 5, 7})
-      while (r % f == 0) r /= f;
-    if (r == 1) return n;
-  }
-}
-
 // T_m[s + S] = J_s(k r_m) e^{i s phi_m}, s = -S..S, for every disc (thread per entry).
 __global__ void k_fmm_shift_table(const double* __restrict__ cx, const double* __restrict__ cy,
                                   const int* __restrict__ dbox, int n, double x0, double w, double yc,
@@ -82,9 +75,10 @@ __global__ void k_fmm_shift_table(const double* __restrict__ cx, const double* _
   }
 }
 
-// Box kernel on the cyclic grid: G[d mod n1][s mod n2] = H_s(k |d| w) e^{i s phi_d} for
-// dmin <= |d| <= nb - 1, |s| <= 2Q (phi_d = 0 for d > 0, pi for d < 0); zero elsewhere.  One thread
-// per offset: H_0, H_1 from the CUDA library, forward recurrence (the arguments are >= 2 k w).
+// Box kernel on the cyclic grid, laid out for a correlation over orders: G[d mod n1][(-s) mod n2] =
+// H_s(k |d| w) e^{i s phi_d} for dmin <= |d| <= nb - 1, |s| <= 2Q (phi_d = 0 for d > 0, pi for
+// d < 0); zero elsewhere.  One thread per offset: H_0, H_1 from the CUDA library, forward
+// recurrence (the arguments are >= 2 k w).
 __global__ void k_fmm_box_kernel(int nb, int Q, double k, double w, int n1, int n2, int dmin,
                                  double2* __restrict__ grid) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -101,9 +95,9 @@ __global__ void k_fmm_box_kernel(int nb, int Q, double k, double w, int n1, int 
   g[0] = hm;
   for (int s = 1; s <= 2 * Q; ++s) {
     const double f = (s & 1) ? sg : 1.0;
-    g[s] = make_double2(f * hq.x, f * hq.y);                                   // H_s e^{i s phi}
+    g[n2 - s] = make_double2(f * hq.x, f * hq.y);                              // s > 0 at column -s
     const double fn = (s & 1) ? -f : f;                                        // H_{-s} = (-1)^s H_s
-    g[n2 - s] = make_double2(fn * hq.x, fn * hq.y);
+    g[s] = make_double2(fn * hq.x, fn * hq.y);                                 // -s at column s
     if (s < 2 * Q) {
       const double c = 2.0 * s / z;
       const double2 hn = make_double2(c * hq.x - hm.x, c * hq.y - hm.y);
@@ -119,19 +113,12 @@ __global__ void k_fmm_scale(double2* __restrict__ a, long long total, double s) 
     a[i] = make_double2(a[i].x * s, a[i].y * s);
 }
 
-template <typename C>
-__global__ void k_fmm_mul(C* __restrict__ a, const C* __restrict__ b, long long total) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x)
-    a[i] = cmul(a[i], b[i]);
-}
-
-// M2M: one CTA per box, thread t <-> box order q = t - Q; writes grid[i][(-q) mod n2].  C is the
-// complex type of the tables and the grid (double2, or float2 in mixed precision).
+// M2M: one CTA per box, thread t <-> box order q = t - Q; writes bq[i][q + Q].  C is the complex
+// type of the tables and the box coefficients (double2, or float2 in mixed precision).
 template <typename C>
 __global__ void k_fmm_m2m(const double2* __restrict__ xs, const int* __restrict__ perm,
                           const int* __restrict__ bstart, const C* __restrict__ tab, int p,
-                          int Q, int S, int n2, C* __restrict__ grid, C* __restrict__ bq) {
+                          int Q, int S, C* __restrict__ bq) {
   extern __shared__ unsigned char sraw[];
   C* sbeta = reinterpret_cast<C*>(sraw);             // [P] coefficients of the current disc
   const int i = blockIdx.x, P = 2 * p + 1;
@@ -147,22 +134,165 @@ __global__ void k_fmm_m2m(const double2* __restrict__ xs, const int* __restrict_
       for (int a = 0; a < P; ++a) acc = cfma(cconj(t[-a]), sbeta[a], acc);   // J_{q-n} e^{-i (q-n) phi}
     }
   }
-  if (q >= -Q && q <= Q) {
-    grid[(size_t)i * n2 + ((-q) % n2 + n2) % n2] = acc;
-    bq[(size_t)i * (2 * Q + 1) + q + Q] = acc;
+  if (q >= -Q && q <= Q) bq[(size_t)i * (2 * Q + 1) + q + Q] = acc;
+}
+
+// ---------------------------------------------------------------------------------------------
+// The box-to-box convolution.  smem_fft: radix-2 Stockham (self-sorting) transforms of NF
+// sequences of length L = 2^logL in shared memory, natural order in and out; element (f, pos) at
+// pos NF + f (FFAST: the sequences interleaved) or f L + pos.  Stage s (Ls = 2^s, m = L / (2 Ls)):
+// for t = j Ls + k < L / 2,
+//   y[j 2Ls + k] = x[t] + w x[t + L/2],   y[j 2Ls + k + Ls] = x[t] - w x[t + L/2],   w = tw[k m step]
+// with tw[u] = e^{-2 pi i u / (L step)} (conjugated for the inverse).  Returns the buffer that
+// holds the result (x or y); every thread of the CTA takes part.
+template <typename C> __device__ __forceinline__ C cplus(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C> __device__ __forceinline__ C cminus(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+
+template <typename C, bool FFAST>
+__device__ C* smem_fft(C* x, C* y, int logL, int logNF, const C* __restrict__ tw, int step, bool inv) {
+  const int L = 1 << logL, half = L >> 1, NF = 1 << logNF;
+  const int total = half << logNF;
+  for (int s = 0; s < logL; ++s) {
+    const int Ls = 1 << s, msh = logL - 1 - s;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      int f, t;
+      if (FFAST) {
+        f = idx & (NF - 1);
+        t = idx >> logNF;
+      } else {
+        t = idx & (half - 1);
+        f = idx >> (logL - 1);
+      }
+      const int k = t & (Ls - 1), j = t >> s;
+      C w = tw[(size_t)(k << msh) * step];
+      if (inv) w.y = -w.y;
+      const int o = j * 2 * Ls + k;
+      const int ia = FFAST ? (t << logNF) + f : f * L + t;
+      const int ib = FFAST ? ((t + half) << logNF) + f : f * L + t + half;
+      const int oa = FFAST ? (o << logNF) + f : f * L + o;
+      const int ob = FFAST ? ((o + Ls) << logNF) + f : f * L + o + Ls;
+      const C a = x[ia], b = cmul(w, x[ib]);
+      y[oa] = cplus(a, b);
+      y[ob] = cminus(a, b);
+    }
+    __syncthreads();
+    C* tmp = x;
+    x = y;
+    y = tmp;
+  }
+  return x;
+}
+
+constexpr int FFT_INV = 1;       // inverse transform (conjugate twiddles, no scaling)
+constexpr int FFT_POST_TW = 2;   // forward four-step: output position k times e^{-2 pi i seg k / n1}
+constexpr int FFT_PRE_TW = 4;    // inverse four-step: input position k times e^{+2 pi i seg k / n1}
+constexpr int FFT_THREADS = 256;
+constexpr int FFT_SMEM = 64 * 1024;   // two buffers (ping-pong) per CTA
+
+// Transforms along the box index of the columns 0..ncols-1 of row-major arrays.  CTA (seg, column
+// block of 2^logCT): the L = 2^logL rows seg * seg_stride + pos * rstride; rows >= in_rows read as
+// zero, rows >= out_rows are not stored.  in and out may be the same array (each CTA reads its
+// whole tile before it writes, and the tiles are disjoint).  twn[u] = e^{-2 pi i u / n1}.
+template <typename C>
+__global__ void __launch_bounds__(FFT_THREADS)
+k_box_fft_cols(const C* in, int in_ld, int in_rows, C* out, int out_ld, int out_rows, int ncols,
+               int logL, int logCT, int seg_stride, int rstride, const C* __restrict__ twn, int log_n1,
+               int mode) {
+  extern __shared__ __align__(16) unsigned char fft_raw[];
+  const int L = 1 << logL, CT = 1 << logCT, n = L << logCT;
+  C* x = reinterpret_cast<C*>(fft_raw);
+  C* y = x + n;
+  const int seg = blockIdx.x, c0 = blockIdx.y << logCT;
+  const long long base = (long long)seg * seg_stride;
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const int pos = idx >> logCT, col = c0 + (idx & (CT - 1));
+    const long long row = base + (long long)pos * rstride;
+    C v = czero<C>();
+    if (row < in_rows && col < ncols) v = in[row * in_ld + col];
+    if (mode & FFT_PRE_TW) v = cmul(cconj(twn[(size_t)seg * pos]), v);
+    x[idx] = v;
+  }
+  __syncthreads();
+  const C* r = smem_fft<C, true>(x, y, logL, logCT, twn, 1 << (log_n1 - logL), mode & FFT_INV);
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const int pos = idx >> logCT, col = c0 + (idx & (CT - 1));
+    const long long row = base + (long long)pos * rstride;
+    C v = r[idx];
+    if (mode & FFT_POST_TW) v = cmul(twn[(size_t)seg * pos], v);
+    if (row < out_rows && col < ncols) out[row * out_ld + col] = v;
   }
 }
 
-// M2L for the offsets 2 <= |d| < dmin, box by box: grid[i][(-nu) mod n2] += sum_d sum_q
+// Transforms along the orders, 2^logNR frequency rows per CTA.  conv = 0 (kernel setup): rows of
+// width n2, forward transform in place.  conv = 1: the rows hold the 2Q + 1 orders q = -Q..Q
+// (row width W), placed at q mod n2 and zero elsewhere; forward transform, product with the
+// transformed kernel khat (its row of the same frequency), inverse transform, the orders -Q..Q
+// stored back.  tw2[u] = e^{-2 pi i u / n2}, u < n2 / 2.
+template <typename C>
+__global__ void __launch_bounds__(FFT_THREADS)
+k_box_fft_rows(C* Y, long long nrows, int W, int Q, const C* __restrict__ khat, int logn2,
+               const C* __restrict__ tw2, int logNR, int conv) {
+  extern __shared__ __align__(16) unsigned char fft_raw[];
+  const int n2 = 1 << logn2, n = n2 << logNR;
+  C* x = reinterpret_cast<C*>(fft_raw);
+  C* y = x + n;
+  const long long r0 = (long long)blockIdx.x << logNR;
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const long long row = r0 + (idx >> logn2);
+    const int k = idx & (n2 - 1);
+    C v = czero<C>();
+    if (row < nrows) {
+      if (!conv) {
+        v = Y[row * n2 + k];
+      } else {
+        const int q = k <= Q ? k : k - n2;
+        if (q >= -Q) v = Y[row * W + q + Q];
+      }
+    }
+    x[idx] = v;
+  }
+  __syncthreads();
+  C* r = smem_fft<C, false>(x, y, logn2, logNR, tw2, 1, false);
+  if (conv) {
+    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+      const long long row = r0 + (idx >> logn2);
+      if (row < nrows) r[idx] = cmul(r[idx], khat[row * n2 + (idx & (n2 - 1))]);
+    }
+    __syncthreads();
+    r = smem_fft<C, false>(r, r == x ? y : x, logn2, logNR, tw2, 1, true);
+  }
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const long long row = r0 + (idx >> logn2);
+    const int k = idx & (n2 - 1);
+    if (row >= nrows) continue;
+    if (!conv) {
+      Y[row * n2 + k] = r[idx];
+    } else {
+      const int q = k <= Q ? k : k - n2;
+      if (q >= -Q) Y[row * W + q + Q] = r[idx];
+    }
+  }
+}
+
+// tw[u] = e^{-2 pi i u / n}, u < count (n a power of two: -2 u / n is exact)
+__global__ void k_fft_twiddles(double2* __restrict__ tw, int n, int count) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= count) return;
+  double sn, cs;
+  sincospi(-2.0 * (double)u / (double)n, &sn, &cs);
+  tw[u] = make_double2(cs, sn);
+}
+
+// M2L for the offsets 2 <= |d| < dmin, box by box: acc[i][nu + Q] += sum_d sum_q
 // hd[d][q - nu] B_{i-d}(q), hd[(sign, |d| - 2)][s + 2Q] = H_s(k |d| w) e^{i s phi_d}.
 template <typename C>
 __global__ void k_fmm_m2l_direct(const C* __restrict__ bq, const C* __restrict__ hd, int nb,
-                                 int Q, int dmin, int n2, C* __restrict__ grid) {
+                                 int Q, int dmin, C* __restrict__ acc) {
   const int i = blockIdx.x;
   const int nu = (int)threadIdx.x - Q;
   if (nu < -Q || nu > Q) return;
   const int W = 2 * Q + 1, H = 4 * Q + 1;
-  C acc = czero<C>();
+  C a = czero<C>();
   for (int ad = 2; ad < dmin; ++ad)
     for (int sg = 0; sg < 2; ++sg) {
       const int d = sg ? -ad : ad;
@@ -170,10 +300,10 @@ __global__ void k_fmm_m2l_direct(const C* __restrict__ bq, const C* __restrict__
       if (j < 0 || j >= nb) continue;
       const C* h = hd + (size_t)(2 * (ad - 2) + sg) * H + 2 * Q - nu;   // h[q] <-> s = q - nu
       const C* b = bq + (size_t)j * W + Q;
-      for (int q = -Q; q <= Q; ++q) acc = cfma(h[q], b[q], acc);
+      for (int q = -Q; q <= Q; ++q) a = cfma(h[q], b[q], a);
     }
-  C* g = grid + (size_t)i * n2 + ((-nu) % n2 + n2) % n2;
-  *g = cadd(*g, acc);
+  C* g = acc + (size_t)i * W + nu + Q;
+  *g = cadd(*g, a);
 }
 
 // Direct-offset kernels hd[(sign, |d| - 2)][s + 2Q], 2 <= |d| < dmin (one thread per offset).
@@ -200,21 +330,21 @@ __global__ void k_fmm_direct_table(int Q, double k, double w, int dmin, double2*
   }
 }
 
-// L2L: one warp per disc, lane <-> nu; alpha = sum_q T_l[q - nu] A_box(q), A(q) = grid[b][(-q) mod n2].
+// L2L: one warp per disc, lane <-> nu; alpha = sum_q T_l[q - nu] A_box(q), A(q) = acc[b][q + Q].
 template <typename C>
-__global__ void k_fmm_l2l(const C* __restrict__ grid, const int* __restrict__ dbox,
-                          const C* __restrict__ tab, int n, int p, int Q, int S, int n2,
+__global__ void k_fmm_l2l(const C* __restrict__ acc, const int* __restrict__ dbox,
+                          const C* __restrict__ tab, int n, int p, int Q, int S,
                           double2* __restrict__ alpha) {
   const int l = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   const int P = 2 * p + 1;
   if (l >= n || lane >= P) return;
   const int nu = lane - p;
-  const C* g = grid + (size_t)dbox[l] * n2;
+  const C* g = acc + (size_t)dbox[l] * (2 * Q + 1) + Q;
   const C* t = tab + (size_t)l * (2 * S + 1) + S;
-  C acc = czero<C>();
-  for (int q = -Q; q <= Q; ++q) acc = cfma(t[q - nu], g[((-q) % n2 + n2) % n2], acc);
-  alpha[(size_t)l * P + lane] = make_double2(acc.x, acc.y);
+  C a = czero<C>();
+  for (int q = -Q; q <= Q; ++q) a = cfma(t[q - nu], g[q], a);
+  alpha[(size_t)l * P + lane] = make_double2(a.x, a.y);
 }
 
 // Near field: CTA over FW consecutive targets in box order; sources from the neighbouring boxes,
@@ -500,16 +630,77 @@ inline int blocks_for(long long total, int block) {
   return (int)std::min<long long>(std::max<long long>(b, 1), 152LL * 32);
 }
 
+// log2 of the columns per CTA of k_box_fft_cols for L = 2^logL (at most 16, two buffers in FFT_SMEM)
+template <typename C> int fft_log_tile(int logL) {
+  const int elems = FFT_SMEM / (2 * (int)sizeof(C));
+  int lct = 4;
+  while (lct > 0 && ((1 << logL) << lct) > elems) --lct;
+  return lct;
+}
+
+// One four-step pass along the boxes: step 1 (A-point transforms at stride B, segment n_b) or the
+// B-point transforms on contiguous runs (segment k_a).
+template <typename C>
+void launch_box_cols(const FmmState& f, const C* in, int in_ld, int in_rows, C* out, int out_ld, int out_rows,
+                     int ncols, bool step1, int mode, const C* twn, cudaStream_t st) {
+  const int logL = step1 ? f.logA : f.logB;
+  const int lct = fft_log_tile<C>(logL);
+  dim3 grid(1u << (step1 ? f.logB : f.logA), (unsigned)((ncols + (1 << lct) - 1) >> lct));
+  const size_t smem = 2 * ((size_t)1 << (logL + lct)) * sizeof(C);
+  k_box_fft_cols<C><<<grid, FFT_THREADS, smem, st>>>(in, in_ld, in_rows, out, out_ld, out_rows, ncols, logL, lct,
+                                                     step1 ? 1 : (1 << f.logB), step1 ? (1 << f.logB) : 1, twn,
+                                                     f.logA + f.logB, mode);
+}
+
+template <typename C>
+void launch_box_rows(const FmmState& f, C* Y, long long nrows, const C* khat, const C* tw2, int conv, cudaStream_t st) {
+  const int elems = FFT_SMEM / (2 * (int)sizeof(C));
+  int lnr = 0;
+  while (lnr < 4 && (f.n2 << (lnr + 1)) <= elems) ++lnr;
+  const long long blocks = (nrows + (1 << lnr) - 1) >> lnr;
+  const size_t smem = 2 * ((size_t)f.n2 << lnr) * sizeof(C);
+  k_box_fft_rows<C><<<(unsigned)blocks, FFT_THREADS, smem, st>>>(Y, nrows, 2 * f.order + 1, f.order, khat, f.logn2,
+                                                                 tw2, lnr, conv);
+}
+
+void fft_attributes() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_box_fft_cols<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
+    cudaFuncSetAttribute(k_box_fft_cols<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
+    cudaFuncSetAttribute(k_box_fft_rows<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
+    cudaFuncSetAttribute(k_box_fft_rows<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
+  });
+}
+
+// The far field of one right-hand side: M2M, the convolution (four-step transform along the boxes,
+// the order rows with the kernel product, the inverse four-step transform), the direct offsets,
+// L2L.  C = double2 (FP64) or float2 (mixed precision); xs and alpha are FP64.
+template <typename C>
+void box_far(const lsms_ctx* c, const double2* x, double2* a, const C* tab, C* bq, C* Y, C* acc, const C* khat,
+             const C* hd, const C* twn, const C* tw2, cudaStream_t st) {
+  const FmmState& f = c->fmm;
+  const int n = c->n, p = c->p, P = 2 * p + 1, W = 2 * f.order + 1;
+  const int qthreads = ((W + 31) / 32) * 32;
+  k_fmm_m2m<C><<<f.nb, qthreads, P * sizeof(C), st>>>(x, f.d_perm, f.d_bstart, tab, p, f.order, f.S, bq);
+  launch_box_cols<C>(f, bq, W, f.nb, Y, W, f.n1, W, true, FFT_POST_TW, twn, st);
+  launch_box_cols<C>(f, Y, W, f.n1, Y, W, f.n1, W, false, 0, twn, st);
+  launch_box_rows<C>(f, Y, f.n1, khat, tw2, 1, st);
+  launch_box_cols<C>(f, Y, W, f.n1, Y, W, f.n1, W, false, FFT_INV, twn, st);
+  launch_box_cols<C>(f, Y, W, f.n1, acc, W, f.nb, W, true, FFT_INV | FFT_PRE_TW, twn, st);
+  if (f.dmin > 2) k_fmm_m2l_direct<C><<<f.nb, qthreads, 0, st>>>(bq, hd, f.nb, f.order, f.dmin, acc);
+  k_fmm_l2l<C><<<(int)(((long long)n * 32 + 255) / 256), 256, 0, st>>>(acc, f.d_dbox, tab, n, p, f.order, f.S, a);
+}
+
 }  // namespace
 
 void fmm_free(lsms_ctx* c) {
   FmmState& f = c->fmm;
-  void* ptrs[] = {f.d_perm, f.d_bstart, f.d_dbox, f.d_sbox, f.d_scx, f.d_scy, f.d_tab, f.d_khat, f.d_grid,
-                  f.d_bq, f.d_hd, f.d_scff, f.ws.ptr, f.d_tab32, f.d_khat32, f.d_grid32, f.d_bq32, f.d_hd32};
+  void* ptrs[] = {f.d_perm,  f.d_bstart, f.d_dbox,   f.d_sbox,   f.d_scx,  f.d_scy,   f.d_tab,   f.d_khat,
+                  f.d_grid,  f.d_bq,     f.d_acc,    f.d_hd,     f.d_twn,  f.d_tw2,   f.d_scff,  f.ws.ptr,
+                  f.d_tab32, f.d_khat32, f.d_grid32, f.d_bq32,   f.d_acc32, f.d_hd32, f.d_twn32, f.d_tw232};
   for (void* q : ptrs)
     if (q) cudaFree(q);
-  if (f.has_plan) cufftDestroy((cufftHandle)f.plan);
-  if (f.has_plan32) cufftDestroy((cufftHandle)f.plan32);
   for (cudaEvent_t e : f.ev)
     if (e) cudaEventDestroy(e);
   const double w = f.box_width;
@@ -562,23 +753,30 @@ int fmm_setup(lsms_ctx* c) {
   f.dmin = 2;
   while (c->k2 * f.dmin * w < 2.0 * f.order + 2.0) ++f.dmin;
   f.far = nb >= 3;                 // boxes two apart exist only from three boxes on
-  f.n1 = f.far ? fft_size(2 * nb - 1) : 1;
-  f.n2 = fft_size(6 * f.order + 1);
-  const size_t gsz = (size_t)f.n1 * f.n2;
+  int m1 = 0;
+  while (f.far && (1 << m1) < 2 * nb - 1) ++m1;
+  if (m1 > 18) {
+    fmm_free(c);
+    return ctx_fail(c, LSMS_ERR_ARG, "set_fmm: more than 131072 boxes; use wider boxes");
+  }
+  f.n1 = 1 << m1;
+  f.logA = (m1 + 1) / 2;
+  f.logB = m1 - f.logA;
+  f.logn2 = 0;
+  while ((1 << f.logn2) < 4 * f.order + 1) ++f.logn2;
+  f.n2 = 1 << f.logn2;
+  const int W = 2 * f.order + 1;
+  const size_t gsz = f.far ? (size_t)f.n1 * f.n2 : 1;
+  const size_t ysz = (size_t)f.n1 * W, asz = (size_t)nb * W;
   const size_t tsz = (size_t)n * (2 * f.S + 1);
+  const size_t hsz = (size_t)std::max(1, 2 * (f.dmin - 2)) * (4 * f.order + 1);
   if (cudaMalloc((void**)&f.d_perm, n * sizeof(int)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_bstart, (nb + 1) * sizeof(int)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_dbox, n * sizeof(int)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_sbox, n * sizeof(int)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_scx, n * sizeof(double)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_scy, n * sizeof(double)) != cudaSuccess ||
-      cudaMalloc((void**)&f.d_tab, tsz * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc((void**)&f.d_khat, gsz * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc((void**)&f.d_grid, gsz * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc((void**)&f.d_bq, (size_t)nb * (2 * f.order + 1) * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc((void**)&f.d_scff, (size_t)n * sizeof(float4)) != cudaSuccess ||
-      cudaMalloc((void**)&f.d_hd, (size_t)std::max(1, 2 * (f.dmin - 2)) * (4 * f.order + 1) * sizeof(double2)) !=
-          cudaSuccess) {
+      cudaMalloc((void**)&f.d_scff, (size_t)n * sizeof(float4)) != cudaSuccess) {
     cudaGetLastError();
     fmm_free(c);
     return ctx_fail(c, LSMS_ERR_OOM, "set_fmm: cudaMalloc failed for the box tables");
@@ -596,102 +794,71 @@ int fmm_setup(lsms_ctx* c) {
     f.ready = true;
     return check_cuda(c, "set_fmm");
   }
-  cufftHandle plan;
-  if (cufftPlan2d(&plan, f.n1, f.n2, CUFFT_Z2Z) != CUFFT_SUCCESS) {
+  if (cudaMalloc((void**)&f.d_tab, tsz * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_khat, gsz * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_grid, ysz * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_bq, asz * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_acc, asz * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_hd, hsz * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_twn, (size_t)f.n1 * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_tw2, (size_t)std::max(1, f.n2 / 2) * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_tab32, tsz * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_khat32, gsz * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_grid32, ysz * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_bq32, asz * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_acc32, asz * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_hd32, hsz * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_twn32, (size_t)f.n1 * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_tw232, (size_t)std::max(1, f.n2 / 2) * sizeof(float2)) != cudaSuccess) {
+    cudaGetLastError();
     fmm_free(c);
-    return ctx_fail(c, LSMS_ERR_CUDA, "set_fmm: cuFFT plan creation failed");
+    return ctx_fail(c, LSMS_ERR_OOM, "set_fmm: cudaMalloc failed for the box tables");
   }
-  f.plan = (int)plan;
-  f.has_plan = true;
+  fft_attributes();
   k_fmm_shift_table<<<blocks_for((long long)tsz, 256), 256, 0, st>>>(c->d_cx, c->d_cy, f.d_dbox, n, f.x0, w,
                                                                       -0.5 * c->d, c->k2, f.S, f.d_tab);
+  k_fft_twiddles<<<(f.n1 + 255) / 256, 256, 0, st>>>(f.d_twn, f.n1, f.n1);
+  k_fft_twiddles<<<(f.n2 / 2 + 255) / 256, 256, 0, st>>>(f.d_tw2, f.n2, f.n2 / 2);
+  // the box kernel and its two-dimensional transform (orders, then the four-step split along the
+  // boxes over all n2 columns), scaled by 1 / (n1 n2)
   cudaMemsetAsync(f.d_khat, 0, gsz * sizeof(double2), st);
   const int nd = 2 * (nb - 1) + 1;
   k_fmm_box_kernel<<<(nd + 127) / 128, 128, 0, st>>>(nb, f.order, c->k2, w, f.n1, f.n2, f.dmin, f.d_khat);
   if (f.dmin > 2) k_fmm_direct_table<<<(2 * (f.dmin - 2) + 63) / 64, 64, 0, st>>>(f.order, c->k2, w, f.dmin, f.d_hd);
-  cufftSetStream(plan, st);
-  if (cufftExecZ2Z(plan, (cufftDoubleComplex*)f.d_khat, (cufftDoubleComplex*)f.d_khat, CUFFT_FORWARD) !=
-      CUFFT_SUCCESS) {
-    fmm_free(c);
-    return ctx_fail(c, LSMS_ERR_CUDA, "set_fmm: cuFFT failed");
-  }
+  launch_box_rows<double2>(f, f.d_khat, f.n1, nullptr, f.d_tw2, 0, st);
+  launch_box_cols<double2>(f, f.d_khat, f.n2, f.n1, f.d_khat, f.n2, f.n1, f.n2, true, FFT_POST_TW, f.d_twn, st);
+  launch_box_cols<double2>(f, f.d_khat, f.n2, f.n1, f.d_khat, f.n2, f.n1, f.n2, false, 0, f.d_twn, st);
   k_fmm_scale<<<blocks_for((long long)gsz, 256), 256, 0, st>>>(f.d_khat, (long long)gsz, 1.0 / (double)gsz);
   // FP32 copies for the mixed-precision far field
-  const size_t hsz = (size_t)std::max(1, 2 * (f.dmin - 2)) * (4 * f.order + 1);
-  if (cudaMalloc((void**)&f.d_tab32, tsz * sizeof(float2)) != cudaSuccess ||
-      cudaMalloc((void**)&f.d_khat32, gsz * sizeof(float2)) != cudaSuccess ||
-      cudaMalloc((void**)&f.d_grid32, gsz * sizeof(float2)) != cudaSuccess ||
-      cudaMalloc((void**)&f.d_bq32, (size_t)nb * (2 * f.order + 1) * sizeof(float2)) != cudaSuccess ||
-      cudaMalloc((void**)&f.d_hd32, hsz * sizeof(float2)) != cudaSuccess) {
-    cudaGetLastError();
-    fmm_free(c);
-    return ctx_fail(c, LSMS_ERR_OOM, "set_fmm: cudaMalloc failed for the FP32 box tables");
-  }
   k_fmm_d2f<<<blocks_for((long long)tsz, 256), 256, 0, st>>>(f.d_tab, f.d_tab32, (long long)tsz);
   k_fmm_d2f<<<blocks_for((long long)gsz, 256), 256, 0, st>>>(f.d_khat, f.d_khat32, (long long)gsz);
+  k_fmm_d2f<<<blocks_for((long long)f.n1, 256), 256, 0, st>>>(f.d_twn, f.d_twn32, (long long)f.n1);
+  k_fmm_d2f<<<blocks_for((long long)(f.n2 / 2), 256), 256, 0, st>>>(f.d_tw2, f.d_tw232, (long long)(f.n2 / 2));
   if (f.dmin > 2) k_fmm_d2f<<<blocks_for((long long)hsz, 256), 256, 0, st>>>(f.d_hd, f.d_hd32, (long long)hsz);
-  cufftHandle plan32;
-  if (cufftPlan2d(&plan32, f.n1, f.n2, CUFFT_C2C) != CUFFT_SUCCESS) {
-    fmm_free(c);
-    return ctx_fail(c, LSMS_ERR_CUDA, "set_fmm: cuFFT plan creation failed");
-  }
-  f.plan32 = (int)plan32;
-  f.has_plan32 = true;
   cudaStreamSynchronize(st);
   f.ready = true;
   return check_cuda(c, "set_fmm");
 }
 
-// alpha = T xs for nrhs right-hand sides through the box method (FP64).  Launches: per right-hand
-// side M2M, the pointwise product and L2L, plus one near-field launch (cuFFT's own kernels aside).
+// alpha = T xs for nrhs right-hand sides through the box method.  Launches: per right-hand side
+// M2M, five transform passes, the direct offsets and L2L, plus the near-field launches.
 int fmm_translate(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, bool mixed, cudaStream_t st) {
   FmmState& f = c->fmm;
   const int n = c->n, p = c->p, P = 2 * p + 1;
   if (!f.ready) return ctx_fail(c, LSMS_ERR_STATE, "box translation tables are not built");
-  const size_t gsz = (size_t)f.n1 * f.n2;
-  cufftHandle plan = (cufftHandle)f.plan;
-  cufftSetStream(plan, st);
   const bool timed = c->timing && !c->kids.size();
   if (timed && !f.ev[0])
     for (cudaEvent_t& e : f.ev) cudaEventCreate(&e);
   if (timed) cudaEventRecord(f.ev[0], st);
-  const int qthreads = ((2 * f.order + 1 + 31) / 32) * 32;
   if (!f.far) cudaMemsetAsync(alpha, 0, (size_t)nrhs * n * P * sizeof(double2), st);
   for (int r = 0; r < nrhs && f.far; ++r) {
     const double2* x = xs + (size_t)r * n * P;
     double2* a = alpha + (size_t)r * n * P;
-    if (mixed) {
-      cufftHandle p32 = (cufftHandle)f.plan32;
-      cufftSetStream(p32, st);
-      cudaMemsetAsync(f.d_grid32, 0, gsz * sizeof(float2), st);
-      k_fmm_m2m<float2><<<f.nb, qthreads, P * sizeof(float2), st>>>(x, f.d_perm, f.d_bstart, f.d_tab32, p, f.order,
-                                                                    f.S, f.n2, f.d_grid32, f.d_bq32);
-      if (cufftExecC2C(p32, (cufftComplex*)f.d_grid32, (cufftComplex*)f.d_grid32, CUFFT_FORWARD) != CUFFT_SUCCESS)
-        return ctx_fail(c, LSMS_ERR_CUDA, "box translation: cuFFT failed");
-      k_fmm_mul<float2><<<blocks_for((long long)gsz, 256), 256, 0, st>>>(f.d_grid32, f.d_khat32, (long long)gsz);
-      if (cufftExecC2C(p32, (cufftComplex*)f.d_grid32, (cufftComplex*)f.d_grid32, CUFFT_INVERSE) != CUFFT_SUCCESS)
-        return ctx_fail(c, LSMS_ERR_CUDA, "box translation: cuFFT failed");
-      if (f.dmin > 2)
-        k_fmm_m2l_direct<float2><<<f.nb, qthreads, 0, st>>>(f.d_bq32, f.d_hd32, f.nb, f.order, f.dmin, f.n2,
-                                                            f.d_grid32);
-      k_fmm_l2l<float2><<<(int)(((long long)n * 32 + 255) / 256), 256, 0, st>>>(f.d_grid32, f.d_dbox, f.d_tab32, n, p,
-                                                                                f.order, f.S, f.n2, a);
-      continue;
-    }
-    cudaMemsetAsync(f.d_grid, 0, gsz * sizeof(double2), st);
-    k_fmm_m2m<double2><<<f.nb, qthreads, P * sizeof(double2), st>>>(x, f.d_perm, f.d_bstart, f.d_tab, p, f.order,
-                                                                     f.S, f.n2, f.d_grid, f.d_bq);
-    if (cufftExecZ2Z(plan, (cufftDoubleComplex*)f.d_grid, (cufftDoubleComplex*)f.d_grid, CUFFT_FORWARD) !=
-        CUFFT_SUCCESS)
-      return ctx_fail(c, LSMS_ERR_CUDA, "box translation: cuFFT failed");
-    k_fmm_mul<double2><<<blocks_for((long long)gsz, 256), 256, 0, st>>>(f.d_grid, f.d_khat, (long long)gsz);
-    if (cufftExecZ2Z(plan, (cufftDoubleComplex*)f.d_grid, (cufftDoubleComplex*)f.d_grid, CUFFT_INVERSE) !=
-        CUFFT_SUCCESS)
-      return ctx_fail(c, LSMS_ERR_CUDA, "box translation: cuFFT failed");
-    if (f.dmin > 2)
-      k_fmm_m2l_direct<double2><<<f.nb, qthreads, 0, st>>>(f.d_bq, f.d_hd, f.nb, f.order, f.dmin, f.n2, f.d_grid);
-    k_fmm_l2l<double2><<<(int)(((long long)n * 32 + 255) / 256), 256, 0, st>>>(f.d_grid, f.d_dbox, f.d_tab, n, p,
-                                                                                f.order, f.S, f.n2, a);
+    if (mixed)
+      box_far<float2>(c, x, a, f.d_tab32, f.d_bq32, f.d_grid32, f.d_acc32, f.d_khat32, f.d_hd32, f.d_twn32,
+                      f.d_tw232, st);
+    else
+      box_far<double2>(c, x, a, f.d_tab, f.d_bq, f.d_grid, f.d_acc, f.d_khat, f.d_hd, f.d_twn, f.d_tw2, st);
   }
   if (mixed) {
     // near field in FP32: box-order copies, the adjacent-box kernel, scatter-add, the near pairs

@@ -43,6 +43,7 @@ struct FmmState {
   int scope = 0;                    // 0: every translation; 1: only the FP64 refinement residuals
   bool far = false;                 // at least three boxes: a far field exists
   int order = 0, S = 0, nb = 0, n1 = 0, n2 = 0, dmin = 2;   // dmin: smallest offset in the FFT
+  int logA = 0, logB = 0, logn2 = 0;   // n1 = 2^(logA + logB) (four-step split), n2 = 2^logn2
   double x0 = 0.0;
   int* d_perm = nullptr;            // [n] discs sorted by box
   int* d_bstart = nullptr;          // [nb + 1]
@@ -52,20 +53,22 @@ struct FmmState {
   double* d_scy = nullptr;
   double2* d_tab = nullptr;         // [n][2S + 1] J_s(k r) e^{i s phi}
   double2* d_khat = nullptr;        // [n1][n2] transformed box kernel / (n1 n2)
-  double2* d_grid = nullptr;        // [n1][n2] work grid
-  double2* d_bq = nullptr;          // [nb][2Q + 1] box coefficients (for the direct offsets)
+  double2* d_grid = nullptr;        // [n1][2Q + 1] work array (spectrum along the boxes)
+  double2* d_bq = nullptr;          // [nb][2Q + 1] box coefficients B_i(q)
+  double2* d_acc = nullptr;         // [nb][2Q + 1] local expansions A_i(nu)
   double2* d_hd = nullptr;          // [2 (dmin - 2)][4Q + 1] kernels of the direct offsets
+  double2* d_twn = nullptr;         // [n1] e^{-2 pi i u / n1}
+  double2* d_tw2 = nullptr;         // [n2 / 2] e^{-2 pi i u / n2}
   float4* d_scff = nullptr;         // [n] sorted centres, float-float (mixed near field)
   float2* d_tab32 = nullptr;        // FP32 copies of the shift tables, the transformed kernel, the
-  float2* d_khat32 = nullptr;       // work grid, the box coefficients and the direct-offset kernels
-  float2* d_grid32 = nullptr;       // (mixed-precision far field)
-  float2* d_bq32 = nullptr;
+  float2* d_khat32 = nullptr;       // work array, the box coefficients and expansions, the
+  float2* d_grid32 = nullptr;       // direct-offset kernels and the twiddles (mixed-precision far
+  float2* d_bq32 = nullptr;         // field)
+  float2* d_acc32 = nullptr;
   float2* d_hd32 = nullptr;
-  int plan32 = 0;                   // cufftHandle (C2C)
-  bool has_plan32 = false;
+  float2* d_twn32 = nullptr;
+  float2* d_tw232 = nullptr;
   DevBuf ws;                        // FP32 copies and partial sums of the mixed near field
-  int plan = 0;                     // cufftHandle
-  bool has_plan = false;
   long long near_pairs = 0;         // ordered pairs translated directly
   bool timed = false;               // the last translation recorded the events
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // far start, near start, near end (timing)

@@ -39,6 +39,21 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(lib.EXPORTS) == set(names)
 
 
+def test_library_links_no_vendor_fft_or_blas(lib):
+    # every step of the path runs in the library's own kernels: no cuFFT / cuBLAS dependency or
+    # symbol in the shared library (tool output: its dynamic section and dynamic symbol table)
+    import shutil
+    import subprocess
+    readelf, nm = shutil.which("readelf"), shutil.which("nm")
+    if not readelf or not nm:
+        pytest.skip("binutils not installed")
+    needed = subprocess.run([readelf, "-d", lib.LIB_PATH], capture_output=True, text=True, check=True).stdout
+    syms = subprocess.run([nm, "-D", lib.LIB_PATH], capture_output=True, text=True, check=True).stdout
+    for name in ("cufft", "cublas", "cusparse", "cudnn"):
+        assert name not in needed.lower(), name
+        assert name not in syms.lower(), name
+
+
 @pytest.mark.parametrize("name", ["disc16_p10_ns256", "disc1000_p12_ns512", "disc5000_p14_ns1024",
                                   "disc2000_p12_ns768_src64"])
 def test_library_contour_equals_oracle_contour(lib, name):

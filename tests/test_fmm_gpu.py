@@ -2,10 +2,12 @@
 with the multipole shifts of Sec. 5.3) against the oracle.
 
 (a) With a low box order the library reproduces the oracle's own box translation (the same
-    approximation, the same boxes) to 1e-10, its FFT rounding (~4e-12) far below the truncation
-    (> 1e-6); (b) at the default order it matches the all-pairs
-    translation of Lemma 3.1 to 1e-10 in the scaled norm (the FP64 bar), on layouts of 400 and 1000
-    discs with ragged boxes, for several right-hand sides; (c) the operator and the solves with boxes
+    approximation, the same boxes) to 1e-10, the rounding of its FFT convolution (~4e-12) far below
+    the truncation (> 1e-6); (b) at the default order it matches the all-pairs
+    translation of Lemma 3.1 to 1e-10 in the scaled norm (the FP64 bar), on layouts of 400, 600 and
+    1000 discs with ragged boxes, for several right-hand sides, with box counts whose transform
+    length along the boxes splits evenly and unevenly (n1 = A B, A = B or 2B) and a high box order
+    whose transform along the orders is 1024 long; (c) the operator and the solves with boxes
     agree with the all-pairs ones; (d) at 50,000 discs (10x the bench layout, 6136 boxes) sampled rows
     match the oracle's row-by-row translation; (e) batches of layouts carry the setting."""
 import numpy as np
@@ -65,8 +67,9 @@ def test_box_translation_equals_the_oracles_box_translation(L):
                                                   # convolution rounds near 4e-12 relative)
 
 
-@pytest.mark.parametrize("n,width,nrhs", [(400, 4.0, 3), (1000, 6.0, 1)])
-def test_box_translation_matches_all_pairs(L, n, width, nrhs):
+@pytest.mark.parametrize("n,width,nrhs,order", [(400, 4.0, 3, 0), (1000, 6.0, 1, 0), (1000, 3.0, 1, 0),
+                                                (600, 3.0, 1, 140)])
+def test_box_translation_matches_all_pairs(L, n, width, nrhs, order):
     w = workload(n, 12, 52)
     c = w.centres()
     hs, ws = weights(w)
@@ -74,7 +77,9 @@ def test_box_translation_matches_all_pairs(L, n, width, nrhs):
     with L.context_for(w) as ctx:
         ctx.set_particles(c)
         dense = ctx.translate(beta)
-        ctx.set_fmm(width)
+        ctx.set_fmm(width, order)
+        nb, q = ctx.fmm_info()
+        assert nb >= 3 and (order == 0 or q == order)
         a = ctx.translate(beta)
     for r in range(nrhs):
         assert rel(a[r], dense[r], ws) < TOL64, r
