@@ -377,15 +377,15 @@ int lsms_set_scattering_diagonal(lsms_ctx* ctx, const double* s_diag);
  *   box_width along x (centres at the disc layer's mid-height); pairs in the same or adjacent boxes
  *   are translated directly; farther pairs through box expansions of order `order`: Graf shifts
  *   disc -> box (H -> H) and box -> disc (J -> J), and Lemma 3.1 between boxes two or more apart,
- *   evaluated for all boxes at once as a convolution over (box offset, order difference) with
- *   cuFFT.  Used by lsms_apply*, lsms_translate and lsms_solve in both precisions (FP32 shifts,
+ *   evaluated for all boxes at once as a cyclic convolution over (box offset, order difference)
+ *   with the library's own FFTs.  Used by lsms_apply*, lsms_translate and lsms_solve in both precisions (FP32 shifts,
  *   convolution and near field in mixed precision, FP64 otherwise), in place of the all-pairs and
  *   the tensor-core block translations.
  *   order = 0: ceil(k2 r_box) + 32 with r_box = hypot(box_width, d) / 2 (about 1e-12 relative
  *   in the scaled norm).  box_width <= 0 turns it off (all-pairs translation).  box_width must be
  *   at least the disc layer's thickness d (boxes two apart are then well separated); order in
  *   [p, 400].  The tables follow each lsms_set_particles / lsms_set_layouts (one set per layout).
- *   Errors: LSMS_ERR_ARG, LSMS_ERR_OOM, LSMS_ERR_CUDA (cuFFT).
+ *   Errors: LSMS_ERR_ARG (also more than 131072 boxes), LSMS_ERR_OOM, LSMS_ERR_CUDA.
  * lsms_get_fmm — number of boxes and the order in use (0, 0 when off or before particles).
  * lsms_fmm_stats — ordered disc pairs translated directly (adjacent boxes), and, when timing is on
  *   (lsms_set_timing), the device milliseconds of the last box translation's far part (shifts,

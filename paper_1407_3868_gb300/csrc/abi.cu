@@ -117,11 +117,13 @@ int apply_device(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags,
     cudaEventRecord(c->ev_join, c->side);
   }
   if (!(flags & LSMS_APPLY_NO_TRANSLATION)) {
-    // box method (FP64, either precision): see fmm.cu; FP64: one kernel; mixed: FP32 copy of xs,
-    // the translation (+ the partial-sum reduction, or the packing of the tensor-core operands)
-    // and the near pairs
+    // box method (fmm.cu): per right-hand side M2M, five transform passes, the direct offsets
+    // and L2L; then the near field (FP64: one kernel; mixed: FP32 copy of xs and the pair-list
+    // kernel).  All pairs: FP64 one kernel; mixed: FP32 copy of xs, the translation (+ the
+    // partial-sum reduction, or the packing of the tensor-core operands) and the near pairs
     if (c->fmm.ready && (c->fmm.scope == 0 || (flags & LSMS_APPLY_RESIDUAL_INTERNAL))) {
-      launches += (c->fmm.dmin > 2 ? 4 : 3) * nrhs + (mixed ? 3 + (c->near_nnz > 0 ? 1 : 0) : 1);
+      if (c->fmm.far) launches += (c->fmm.dmin > 2 ? 8 : 7) * nrhs;
+      launches += mixed ? 2 : 1;
       if ((rc = fmm_translate(c, nrhs, xs, alpha, mixed, st))) return rc;
     } else if (mixed) {
       launches += 3 + (c->near_nnz > 0 ? 1 : 0);

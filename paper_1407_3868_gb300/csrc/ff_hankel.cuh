@@ -87,35 +87,45 @@ __device__ __noinline__ void hankel01_near(double z, float2* h0, float2* h1) {
   *h1 = make_float2((float)j1(z), (float)y1(z));
 }
 
-// Pair sequence h[s + 2p] = H_s(k rho) exp(i s phi), s = -2p..2p, for centres a (target) and b
-// (source) given as float-float (x_hi, x_lo, y_hi, y_lo).
-// near_r2: squared distance (float-float) below which the pair is left to the near-pair kernel and
-// its sequence is zero here; near_r2.hi <= 0 computes every pair here.
-// The order p is a template parameter, so the recurrence is unrolled.
-template <int PT>
-__device__ __forceinline__ void hankel_sequence_f32(float4 a, float4 b, ffl k, ffl near_r2, float2* h) {
-  constexpr int p = PT;
+// Geometry of a disc pair from float-float centres a (target) and b (source), given as
+// (x_hi, x_lo, y_hi, y_lo): squared distance r2, the argument z = k rho (float-float and rounded)
+// and the unit vector e1 = (cos phi, sin phi) of a - b.
+struct PairGeom {
+  ffl r2, z;
+  float zf;
+  float2 e1;
+};
+__device__ __forceinline__ PairGeom pair_geometry(float4 a, float4 b, ffl k) {
+  PairGeom g;
   const ffl dx = ff_sub({a.x, a.y}, {b.x, b.y});
   const ffl dy = ff_sub({a.z, a.w}, {b.z, b.w});
-  const ffl r2 = ff_add(ff_mul(dx, dx), ff_mul(dy, dy));
-  if (near_r2.hi > 0.0f && (r2.hi < near_r2.hi || (r2.hi == near_r2.hi && r2.lo < near_r2.lo))) {
-#pragma unroll
-    for (int q = 0; q <= 4 * p; ++q) h[q] = make_float2(0.f, 0.f);
-    return;
-  }
-  const ffl rho = ff_sqrt(r2);
-  const ffl z = ff_mul(rho, k);
-  const float zf = z.hi + z.lo;
+  g.r2 = ff_add(ff_mul(dx, dx), ff_mul(dy, dy));
+  const ffl rho = ff_sqrt(g.r2);
+  g.z = ff_mul(rho, k);
+  g.zf = g.z.hi + g.z.lo;
   const float irho = 1.0f / rho.hi;
-  const float2 e1 = make_float2((dx.hi + dx.lo) * irho, (dy.hi + dy.lo) * irho);
-  float2 h0, h1;
-  if (zf >= kZAsym) {
-    const float nq = rintf(z.hi * kInvTwoPi);
-    const ffl t = ff_sub(z, ff_add(ff_mul_f({kTwoPiHi, 0.0f}, nq), ff_mul_f({kTwoPiLo, 0.0f}, nq)));
-    hankel01_asym(zf, t.hi + t.lo, h0, h1);
+  g.e1 = make_float2((dx.hi + dx.lo) * irho, (dy.hi + dy.lo) * irho);
+  return g;
+}
+
+// H_0, H_1 at the pair's argument: Hankel's expansion with the float-float phase reduction for
+// z >= 25, the FP64 library functions below.
+__device__ __forceinline__ void hankel01_f32(const PairGeom& g, float2& h0, float2& h1) {
+  if (g.zf >= kZAsym) {
+    const float nq = rintf(g.z.hi * kInvTwoPi);
+    const ffl t = ff_sub(g.z, ff_add(ff_mul_f({kTwoPiHi, 0.0f}, nq), ff_mul_f({kTwoPiLo, 0.0f}, nq)));
+    hankel01_asym(g.zf, t.hi + t.lo, h0, h1);
   } else {
-    hankel01_near((double)z.hi + (double)z.lo, &h0, &h1);
+    hankel01_near((double)g.z.hi + (double)g.z.lo, &h0, &h1);
   }
+}
+
+// h[s + 2p] = H_s(z) exp(i s phi), s = -2p..2p, from H_0 and H_1: the forward recurrence
+// H_{q+1} = (2q / z) H_q - H_{q-1}, the angular factors e1^q, and H_{-q} e^{-i q phi} =
+// (-1)^q H_q conj(e1^q).  The order p is a template parameter, so the recurrence is unrolled.
+template <int PT>
+__device__ __forceinline__ void hankel_recurrence_f32(float2 h0, float2 h1, float2 e1, float zf, float2* h) {
+  constexpr int p = PT;
   const int c0 = 2 * p;
   h[c0] = h0;
   float2 hm = h0, hq = h1, eq = e1;
@@ -134,6 +144,22 @@ __device__ __forceinline__ void hankel_sequence_f32(float4 a, float4 b, ffl k, f
       eq = cmulf(eq, e1);
     }
   }
+}
+
+// Pair sequence h[s + 2p] = H_s(k rho) exp(i s phi), s = -2p..2p, for centres a (target) and b
+// (source).  near_r2: squared distance (float-float) below which the pair is left to the near-pair
+// kernel and its sequence is zero here; near_r2.hi <= 0 computes every pair here.
+template <int PT>
+__device__ __forceinline__ void hankel_sequence_f32(float4 a, float4 b, ffl k, ffl near_r2, float2* h) {
+  const PairGeom g = pair_geometry(a, b, k);
+  if (near_r2.hi > 0.0f && (g.r2.hi < near_r2.hi || (g.r2.hi == near_r2.hi && g.r2.lo < near_r2.lo))) {
+#pragma unroll
+    for (int q = 0; q <= 4 * PT; ++q) h[q] = make_float2(0.f, 0.f);
+    return;
+  }
+  float2 h0, h1;
+  hankel01_f32(g, h0, h1);
+  hankel_recurrence_f32<PT>(h0, h1, g.e1, g.zf, h);
 }
 
 }  // namespace

@@ -29,6 +29,7 @@
 
 #include "c64.cuh"
 #include "ff_hankel.cuh"
+#include "near_pairs.cuh"
 #include "lsms_internal.h"
 #include "lsms_ops.h"
 
@@ -113,67 +114,145 @@ __global__ void k_fmm_scale(double2* __restrict__ a, long long total, double s) 
     a[i] = make_double2(a[i].x * s, a[i].y * s);
 }
 
-// M2M: one CTA per box, thread t <-> box order q = t - Q; writes bq[i][q + Q].  C is the complex
-// type of the tables and the box coefficients (double2, or float2 in mixed precision).
+// The shift kernels (M2M, L2L, the direct offsets) are Toeplitz contractions: a lane owns 4
+// consecutive outputs and keeps the 4 sequence entries they need for the current input in
+// registers, so that each input costs one shared-memory load of the sequence (the window slides by
+// one) and one of the input.  A sequence row is stored as four sub-arrays by index mod 4, so the
+// lanes of a warp, whose windows start 4 entries apart, read consecutive words.
+constexpr int SH_W = 4;   // warps per CTA of the shift kernels
+
 template <typename C>
-__global__ void k_fmm_m2m(const double2* __restrict__ xs, const int* __restrict__ perm,
-                          const int* __restrict__ bstart, const C* __restrict__ tab, int p,
-                          int Q, int S, C* __restrict__ bq) {
-  extern __shared__ unsigned char sraw[];
-  C* sbeta = reinterpret_cast<C*>(sraw);             // [P] coefficients of the current disc
-  const int i = blockIdx.x, P = 2 * p + 1;
-  const int q = (int)threadIdx.x - Q;
-  C acc = czero<C>();
-  for (int jj = bstart[i]; jj < bstart[i + 1]; ++jj) {
-    const int m = perm[jj];
-    __syncthreads();
-    if (threadIdx.x < P) sbeta[threadIdx.x] = from_d2<C>(xs[(size_t)m * P + threadIdx.x]);
-    __syncthreads();
-    if (q >= -Q && q <= Q) {
-      const C* t = tab + (size_t)m * (2 * S + 1) + S + q + p;           // t[-(n + p)] <-> s = q - n
-      for (int a = 0; a < P; ++a) acc = cfma(cconj(t[-a]), sbeta[a], acc);   // J_{q-n} e^{-i (q-n) phi}
+__device__ __forceinline__ void row_put(C* sub, int L4, int j, C v) { sub[(j & 3) * L4 + (j >> 2)] = v; }
+template <typename C>
+__device__ __forceinline__ C row_get(const C* sub, int L4, int j, int jmax) {
+  return (j >= 0 && j <= jmax) ? sub[(j & 3) * L4 + (j >> 2)] : czero<C>();
+}
+
+// M2M: one warp per box; lane <-> box orders w = w0 + 4 lane + i (w = q + Q, chunks of 128).
+// B_i(q) = sum_{m in box i} sum_n conj(T_m[q - n]) beta^m_n, T_m[s] = J_s(k r_m) e^{i s phi_m}; with
+// a = n + p the entry is T_m row index w - a + 2p.  Writes bq[i][w].  C: the complex type of the
+// tables and the box coefficients (double2, or float2 in mixed precision); xs is FP64.
+template <typename C>
+__global__ void __launch_bounds__(SH_W * 32)
+k_fmm_m2m(const double2* __restrict__ xs, const int* __restrict__ perm, const int* __restrict__ bstart,
+          const C* __restrict__ tab, int nb, int p, int Q, int S, C* __restrict__ bq) {
+  extern __shared__ __align__(16) unsigned char sh_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int P = 2 * p + 1, W = 2 * Q + 1, jmax = 2 * S, L4 = (2 * S + 4) / 4;
+  C* sub = reinterpret_cast<C*>(sh_raw) + (size_t)warp * (4 * L4 + P);
+  C* beta = sub + 4 * L4;
+  const int box = blockIdx.x * SH_W + warp;
+  if (box >= nb) return;
+  const int j0 = bstart[box], j1 = bstart[box + 1];
+  for (int w0 = 0; w0 < W; w0 += 128) {
+    C acc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i] = czero<C>();
+    const int base = w0 + 4 * lane + 2 * p;
+    for (int jj = j0; jj < j1; ++jj) {
+      const int m = perm[jj];
+      __syncwarp();
+      for (int j = lane; j <= jmax; j += 32) row_put(sub, L4, j, tab[(size_t)m * (2 * S + 1) + j]);
+      for (int a = lane; a < P; a += 32) beta[a] = from_d2<C>(xs[(size_t)m * P + a]);
+      __syncwarp();
+      C win[4];                                          // win[i] = T_m[base + i - a]
+#pragma unroll
+      for (int i = 0; i < 4; ++i) win[i] = row_get(sub, L4, base + i, jmax);
+      for (int a = 0; a < P; ++a) {
+        const C b = beta[a];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i] = cfma(cconj(win[i]), b, acc[i]);
+        win[3] = win[2];
+        win[2] = win[1];
+        win[1] = win[0];
+        win[0] = row_get(sub, L4, base - a - 1, jmax);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int w = w0 + 4 * lane + i;
+      if (w < W) bq[(size_t)box * W + w] = acc[i];
     }
   }
-  if (q >= -Q && q <= Q) bq[(size_t)i * (2 * Q + 1) + q + Q] = acc;
 }
 
 // ---------------------------------------------------------------------------------------------
-// The box-to-box convolution.  smem_fft: radix-2 Stockham (self-sorting) transforms of NF
-// sequences of length L = 2^logL in shared memory, natural order in and out; element (f, pos) at
-// pos NF + f (FFAST: the sequences interleaved) or f L + pos.  Stage s (Ls = 2^s, m = L / (2 Ls)):
-// for t = j Ls + k < L / 2,
-//   y[j 2Ls + k] = x[t] + w x[t + L/2],   y[j 2Ls + k + Ls] = x[t] - w x[t + L/2],   w = tw[k m step]
-// with tw[u] = e^{-2 pi i u / (L step)} (conjugated for the inverse).  Returns the buffer that
-// holds the result (x or y); every thread of the CTA takes part.
+// The box-to-box convolution.  smem_fft: Stockham (self-sorting) transforms of NF sequences of
+// length L = 2^logL held in shared memory, natural order in and out; element (f, pos) at
+// pos NF + f (FFAST: the sequences interleaved) or f L + pos.  Radix-4 stages while two or more
+// factors of 2 remain, then one radix-2 stage.  With Ls the length already transformed,
+// tw[u] = e^{-2 pi i u / (L step)} (conjugated for the inverse), t = j Ls + k:
+//   radix 4 (t < L/4, m = L / (4 Ls), w^r = tw[r k m step]):  a_r = w^r x[t + r L/4],
+//     y[j 4Ls + k + q Ls] = sum_r (-i)^{q r} a_r   (+i for the inverse), q = 0..3;
+//   radix 2 (t < L/2, m = L / (2 Ls), w = tw[k m step]):
+//     y[j 2Ls + k] = x[t] + w x[t + L/2],   y[j 2Ls + k + Ls] = x[t] - w x[t + L/2].
+// Returns the buffer that holds the result (x or y); every thread of the CTA takes part.
 template <typename C> __device__ __forceinline__ C cplus(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename C> __device__ __forceinline__ C cminus(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
 
 template <typename C, bool FFAST>
 __device__ C* smem_fft(C* x, C* y, int logL, int logNF, const C* __restrict__ tw, int step, bool inv) {
-  const int L = 1 << logL, half = L >> 1, NF = 1 << logNF;
-  const int total = half << logNF;
-  for (int s = 0; s < logL; ++s) {
-    const int Ls = 1 << s, msh = logL - 1 - s;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      int f, t;
-      if (FFAST) {
-        f = idx & (NF - 1);
-        t = idx >> logNF;
-      } else {
-        t = idx & (half - 1);
-        f = idx >> (logL - 1);
+  const int L = 1 << logL, NF = 1 << logNF;
+  auto at = [&](int f, int pos) { return FFAST ? (pos << logNF) + f : f * L + pos; };
+  int s = 0;
+  while (s < logL) {
+    const int Ls = 1 << s;
+    if (logL - s >= 2) {
+      const int q4 = L >> 2, msh = logL - 2 - s;
+      const int total = q4 << logNF;
+      for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int f, t;
+        if (FFAST) {
+          f = idx & (NF - 1);
+          t = idx >> logNF;
+        } else {
+          t = idx & (q4 - 1);
+          f = idx >> (logL - 2);
+        }
+        const int k = t & (Ls - 1), j = t >> s;
+        const size_t u = (size_t)(k << msh) * step;
+        C w1 = tw[u], w2 = tw[2 * u], w3 = tw[3 * u];
+        if (inv) {
+          w1.y = -w1.y;
+          w2.y = -w2.y;
+          w3.y = -w3.y;
+        }
+        const C a0 = x[at(f, t)];
+        const C a1 = cmul(w1, x[at(f, t + q4)]);
+        const C a2 = cmul(w2, x[at(f, t + 2 * q4)]);
+        const C a3 = cmul(w3, x[at(f, t + 3 * q4)]);
+        const C c0 = cplus(a0, a2), c1 = cminus(a0, a2), c2 = cplus(a1, a3), d = cminus(a1, a3);
+        C c3;                                      // d (-i) forward, d (+i) inverse
+        c3.x = inv ? -d.y : d.y;
+        c3.y = inv ? d.x : -d.x;
+        const int o = j * 4 * Ls + k;
+        y[at(f, o)] = cplus(c0, c2);
+        y[at(f, o + Ls)] = cplus(c1, c3);
+        y[at(f, o + 2 * Ls)] = cminus(c0, c2);
+        y[at(f, o + 3 * Ls)] = cminus(c1, c3);
       }
-      const int k = t & (Ls - 1), j = t >> s;
-      C w = tw[(size_t)(k << msh) * step];
-      if (inv) w.y = -w.y;
-      const int o = j * 2 * Ls + k;
-      const int ia = FFAST ? (t << logNF) + f : f * L + t;
-      const int ib = FFAST ? ((t + half) << logNF) + f : f * L + t + half;
-      const int oa = FFAST ? (o << logNF) + f : f * L + o;
-      const int ob = FFAST ? ((o + Ls) << logNF) + f : f * L + o + Ls;
-      const C a = x[ia], b = cmul(w, x[ib]);
-      y[oa] = cplus(a, b);
-      y[ob] = cminus(a, b);
+      s += 2;
+    } else {
+      const int half = L >> 1, msh = logL - 1 - s;
+      const int total = half << logNF;
+      for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int f, t;
+        if (FFAST) {
+          f = idx & (NF - 1);
+          t = idx >> logNF;
+        } else {
+          t = idx & (half - 1);
+          f = idx >> (logL - 1);
+        }
+        const int k = t & (Ls - 1), j = t >> s;
+        C w = tw[(size_t)(k << msh) * step];
+        if (inv) w.y = -w.y;
+        const C a = x[at(f, t)], b = cmul(w, x[at(f, t + half)]);
+        const int o = j * 2 * Ls + k;
+        y[at(f, o)] = cplus(a, b);
+        y[at(f, o + Ls)] = cminus(a, b);
+      }
+      s += 1;
     }
     __syncthreads();
     C* tmp = x;
@@ -227,7 +306,7 @@ k_box_fft_cols(const C* in, int in_ld, int in_rows, C* out, int out_ld, int out_
 // width n2, forward transform in place.  conv = 1: the rows hold the 2Q + 1 orders q = -Q..Q
 // (row width W), placed at q mod n2 and zero elsewhere; forward transform, product with the
 // transformed kernel khat (its row of the same frequency), inverse transform, the orders -Q..Q
-// stored back.  tw2[u] = e^{-2 pi i u / n2}, u < n2 / 2.
+// stored back.  tw2[u] = e^{-2 pi i u / n2}, u < n2.
 template <typename C>
 __global__ void __launch_bounds__(FFT_THREADS)
 k_box_fft_rows(C* Y, long long nrows, int W, int Q, const C* __restrict__ khat, int logn2,
@@ -284,26 +363,57 @@ __global__ void k_fft_twiddles(double2* __restrict__ tw, int n, int count) {
 }
 
 // M2L for the offsets 2 <= |d| < dmin, box by box: acc[i][nu + Q] += sum_d sum_q
-// hd[d][q - nu] B_{i-d}(q), hd[(sign, |d| - 2)][s + 2Q] = H_s(k |d| w) e^{i s phi_d}.
+// hd[d][q - nu + 2Q] B_{i-d}(q), hd[(sign, |d| - 2)][s + 2Q] = H_s(k |d| w) e^{i s phi_d}.  One warp
+// per box; lane <-> outputs o = o0 + 4 lane + i (o = nu + Q, chunks of 128); the entry for input
+// w = q + Q is hd row index 2Q + w - o.  Per offset the warp stages the kernel row and the source
+// box's coefficients in shared memory.
 template <typename C>
-__global__ void k_fmm_m2l_direct(const C* __restrict__ bq, const C* __restrict__ hd, int nb,
-                                 int Q, int dmin, C* __restrict__ acc) {
-  const int i = blockIdx.x;
-  const int nu = (int)threadIdx.x - Q;
-  if (nu < -Q || nu > Q) return;
-  const int W = 2 * Q + 1, H = 4 * Q + 1;
-  C a = czero<C>();
-  for (int ad = 2; ad < dmin; ++ad)
-    for (int sg = 0; sg < 2; ++sg) {
-      const int d = sg ? -ad : ad;
-      const int j = i - d;
-      if (j < 0 || j >= nb) continue;
-      const C* h = hd + (size_t)(2 * (ad - 2) + sg) * H + 2 * Q - nu;   // h[q] <-> s = q - nu
-      const C* b = bq + (size_t)j * W + Q;
-      for (int q = -Q; q <= Q; ++q) a = cfma(h[q], b[q], a);
+__global__ void __launch_bounds__(SH_W * 32)
+k_fmm_m2l_direct(const C* __restrict__ bq, const C* __restrict__ hd, int nb, int Q, int dmin,
+                 C* __restrict__ acc) {
+  extern __shared__ __align__(16) unsigned char sh_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int W = 2 * Q + 1, H = 4 * Q + 1, jmax = 4 * Q, L4 = (H + 3) / 4;
+  C* sub = reinterpret_cast<C*>(sh_raw) + (size_t)warp * (4 * L4 + W);
+  C* brow = sub + 4 * L4;
+  const int box = blockIdx.x * SH_W + warp;
+  if (box >= nb) return;
+  for (int o0 = 0; o0 < W; o0 += 128) {
+    C a4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a4[i] = czero<C>();
+    const int base = 2 * Q - o0 - 4 * lane;
+    for (int ad = 2; ad < dmin; ++ad)
+      for (int sg = 0; sg < 2; ++sg) {
+        const int src = box - (sg ? -ad : ad);
+        if (src < 0 || src >= nb) continue;
+        const C* h = hd + (size_t)(2 * (ad - 2) + sg) * H;
+        __syncwarp();
+        for (int j = lane; j < H; j += 32) row_put(sub, L4, j, h[j]);
+        for (int w = lane; w < W; w += 32) brow[w] = bq[(size_t)src * W + w];
+        __syncwarp();
+        C win[4];                                        // win[i] = hd[base + w - i]
+#pragma unroll
+        for (int i = 0; i < 4; ++i) win[i] = row_get(sub, L4, base - i, jmax);
+        for (int w = 0; w < W; ++w) {
+          const C b = brow[w];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a4[i] = cfma(win[i], b, a4[i]);
+          win[3] = win[2];
+          win[2] = win[1];
+          win[1] = win[0];
+          win[0] = row_get(sub, L4, base + w + 1, jmax);
+        }
+      }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int o = o0 + 4 * lane + i;
+      if (o < W) {
+        C* g = acc + (size_t)box * W + o;
+        *g = cadd(*g, a4[i]);
+      }
     }
-  C* g = acc + (size_t)i * W + nu + Q;
-  *g = cadd(*g, a);
+  }
 }
 
 // Direct-offset kernels hd[(sign, |d| - 2)][s + 2Q], 2 <= |d| < dmin (one thread per offset).
@@ -330,21 +440,46 @@ __global__ void k_fmm_direct_table(int Q, double k, double w, int dmin, double2*
   }
 }
 
-// L2L: one warp per disc, lane <-> nu; alpha = sum_q T_l[q - nu] A_box(q), A(q) = acc[b][q + Q].
+// L2L: 4 discs per warp, 8 lanes per disc; lane <-> outputs o = 4 (lane & 7) + i (o = nu + p).
+// alpha_l(nu) = sum_q T_l[q - nu] A_box(q), A(q) = acc[b][q + Q]; with w = q + Q the entry is T_l row
+// index w - o + 2p.  The discs' T rows are staged in shared memory, A is read through the cache.
 template <typename C>
-__global__ void k_fmm_l2l(const C* __restrict__ acc, const int* __restrict__ dbox,
-                          const C* __restrict__ tab, int n, int p, int Q, int S,
-                          double2* __restrict__ alpha) {
-  const int l = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  const int P = 2 * p + 1;
-  if (l >= n || lane >= P) return;
-  const int nu = lane - p;
-  const C* g = acc + (size_t)dbox[l] * (2 * Q + 1) + Q;
-  const C* t = tab + (size_t)l * (2 * S + 1) + S;
-  C a = czero<C>();
-  for (int q = -Q; q <= Q; ++q) a = cfma(t[q - nu], g[q], a);
-  alpha[(size_t)l * P + lane] = make_double2(a.x, a.y);
+__global__ void __launch_bounds__(SH_W * 32)
+k_fmm_l2l(const C* __restrict__ acc, const int* __restrict__ dbox, const C* __restrict__ tab, int n, int p,
+          int Q, int S, double2* __restrict__ alpha) {
+  extern __shared__ __align__(16) unsigned char sh_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 3, j8 = lane & 7;
+  const int P = 2 * p + 1, W = 2 * Q + 1, jmax = 2 * S, L4 = (2 * S + 4) / 4;
+  C* sub = reinterpret_cast<C*>(sh_raw) + (size_t)(warp * 4 + g) * 4 * L4;
+  const int l = (blockIdx.x * SH_W + warp) * 4 + g;
+  const bool valid = l < n;
+  if (valid)
+    for (int j = j8; j <= jmax; j += 8) row_put(sub, L4, j, tab[(size_t)l * (2 * S + 1) + j]);
+  __syncwarp();
+  if (!valid) return;
+  const C* arow = acc + (size_t)dbox[l] * W;
+  const int base = 2 * p - 4 * j8;
+  C a4[4], win[4];                                       // win[i] = T_l[base + w - i]
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    a4[i] = czero<C>();
+    win[i] = row_get(sub, L4, base - i, jmax);
+  }
+  for (int w = 0; w < W; ++w) {
+    const C b = arow[w];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a4[i] = cfma(win[i], b, a4[i]);
+    win[3] = win[2];
+    win[2] = win[1];
+    win[1] = win[0];
+    win[0] = row_get(sub, L4, base + w + 1, jmax);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int o = 4 * j8 + i;
+    if (o < P) alpha[(size_t)l * P + o] = make_double2(a4[i].x, a4[i].y);
+  }
 }
 
 // Near field: CTA over FW consecutive targets in box order; sources from the neighbouring boxes,
@@ -426,203 +561,11 @@ k_fmm_near(const double* __restrict__ scx, const double* __restrict__ scy, const
   }
 }
 
-// ---------------------------------------------------------------------------------------------
-// Mixed precision: the near field in FP32 (float-float phases, Hankel's asymptotic H_0, H_1 for
-// k rho >= 25, forward recurrence) with the register-blocked Toeplitz contraction of the all-pairs
-// FP32 kernel, restricted to adjacent boxes; pairs with k rho < 25 are left to the near-pair kernel
-// (FP64-accurate sequences).  Inputs and outputs in box order.
-// ---------------------------------------------------------------------------------------------
-constexpr int BW = 1;      // warps per CTA: each warp's 8 targets (about one box) get their own
-                           // source window, three to four boxes wide instead of a 32-target CTA's six
-constexpr int BT = 8;      // target discs per warp
-constexpr int BCH = 32;    // sources staged per chunk
-constexpr int BHS = 65;    // pair slot stride (see the all-pairs FP32 kernel: conflict-free windows)
-constexpr int BGUARD = 8;
-constexpr size_t BOX_NEAR_SMEM = (size_t)(2 * BGUARD + BW * 32 * BHS) * sizeof(float2);
-
-template <int PT>
-__global__ void __launch_bounds__(BW * 32, 8)
-k_box_near_f32(const float4* __restrict__ cff, const int* __restrict__ sbox, const int* __restrict__ bstart,
-               int nb, int n, float k_hi, float k_lo, float near_hi, float near_lo,
-               const float2* __restrict__ xs, float2* __restrict__ out) {
-  constexpr int p = PT;
-  constexpr int P = 2 * PT + 1;
-  constexpr int VB = (P + 3) / 4;
-  constexpr int NB = (P + VB - 1) / VB;
-  __shared__ float2 sb[BCH][VB * NB + 1];
-  __shared__ float4 sc[BCH];
-  __shared__ int sbx[BCH];
-  extern __shared__ float2 sh[];
-  const int r = blockIdx.z;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = lane & 7, hi8 = lane >> 3;
-  const int l0 = blockIdx.x * BW * BT;
-  const int l = l0 + warp * BT + t;
-  const bool lvalid = l < n;
-  const float4 ct = lvalid ? cff[l] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const int bl = lvalid ? sbox[l] : 0;
-  const int b0 = sbox[l0], b1 = sbox[min(l0 + BW * BT, n) - 1];
-  const int jbeg = bstart[max(b0 - 1, 0)], jend = bstart[min(b1 + 2, nb)];
-  for (int i = threadIdx.x; i < 2 * BGUARD + BW * 32 * BHS; i += blockDim.x) sh[i] = make_float2(0.f, 0.f);
-  float2* hw = sh + BGUARD + warp * 32 * BHS;
-  float2 AB[VB];           // (sum h_r b_r, sum h_i b_i), one packed FMA per window value
-  float C[VB];
-#pragma unroll
-  for (int i = 0; i < VB; ++i) {
-    AB[i] = make_float2(0.f, 0.f);
-    C[i] = 0.f;
-  }
-  const ffl kf = {k_hi, k_lo};
-  const float2* xr = xs + (size_t)r * n * P;
-  for (int j0c = jbeg; j0c < jend; j0c += BCH) {
-    const int cnt = min(BCH, jend - j0c);
-    __syncthreads();
-    for (int i = threadIdx.x; i < BCH * VB * NB; i += blockDim.x) {
-      const int s = i / (VB * NB), q = i - s * (VB * NB);
-      sb[s][q] = (s < cnt && q < P) ? xr[(size_t)(j0c + s) * P + q] : make_float2(0.f, 0.f);
-    }
-    if (threadIdx.x < cnt) {
-      sc[threadIdx.x] = cff[j0c + threadIdx.x];
-      sbx[threadIdx.x] = sbox[j0c + threadIdx.x];
-    }
-    __syncthreads();
-    for (int s0 = 0; s0 < cnt; s0 += 4) {
-      {
-        const int js = s0 + hi8;
-        float2* h = hw + lane * BHS;
-        const int db = js < cnt ? sbx[js] - bl : 2;
-        if (js < cnt && lvalid && j0c + js != l && db >= -1 && db <= 1) {
-          hankel_sequence_f32<PT>(ct, sc[js], kf, {near_hi, near_lo}, h);
-        } else {
-          for (int q = 0; q <= 4 * p; ++q) h[q] = make_float2(0.f, 0.f);
-        }
-      }
-      __syncwarp();
-      const int nq4 = min(4, cnt - s0);
-      for (int q4 = 0; q4 < nq4; ++q4) {
-        const float2* hs = hw + (q4 * 8 + t) * BHS + 2 * p - VB * hi8;
-        float2 win[2 * VB - 1];
-        float wsum[2 * VB - 1];
-#pragma unroll
-        for (int j = 0; j < VB - 1; ++j) {
-          win[j] = hs[j - (VB - 1)];
-          wsum[j] = win[j].x + win[j].y;
-        }
-#pragma unroll
-        for (int nbk = 0; nbk < NB; ++nbk) {
-#pragma unroll
-          for (int j = 0; j < VB; ++j) {
-            win[VB - 1 + j] = hs[nbk * VB + j];
-            wsum[VB - 1 + j] = win[VB - 1 + j].x + win[VB - 1 + j].y;
-          }
-#pragma unroll
-          for (int u = 0; u < VB; ++u) {
-            if (nbk * VB + u >= P) break;
-            const float2 bv = sb[s0 + q4][nbk * VB + u];
-            const float bsum = bv.x + bv.y;
-#pragma unroll
-            for (int i = 0; i < VB; ++i) {
-              AB[i] = __ffma2_rn(win[VB - 1 + u - i], bv, AB[i]);
-              C[i] = __fmaf_rn(wsum[VB - 1 + u - i], bsum, C[i]);
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < VB - 1; ++j) {
-            win[j] = win[VB + j];
-            wsum[j] = wsum[VB + j];
-          }
-        }
-      }
-      __syncwarp();
-    }
-  }
-  if (lvalid) {
-    float2* o = out + ((size_t)r * n + l) * P;
-#pragma unroll
-    for (int i = 0; i < VB; ++i) {
-      const int nu = VB * hi8 + i;
-      if (nu < P) o[nu] = make_float2(AB[i].x - AB[i].y, C[i] - AB[i].x - AB[i].y);
-    }
-  }
-}
-
-template <int PT>
-void launch_box_near_pt(dim3 grid, cudaStream_t st, const float4* cff, const int* sbox, const int* bstart, int nb,
-                        int n, float kh, float kl, float nh, float nl, const float2* xs, float2* out) {
-  static std::once_flag attr;
-  std::call_once(attr, [] {
-    cudaFuncSetAttribute(k_box_near_f32<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BOX_NEAR_SMEM);
-  });
-  k_box_near_f32<PT><<<grid, BW * 32, BOX_NEAR_SMEM, st>>>(cff, sbox, bstart, nb, n, kh, kl, nh, nl, xs, out);
-}
-
-void launch_box_near(int p, dim3 grid, cudaStream_t st, const float4* cff, const int* sbox, const int* bstart,
-                     int nb, int n, float kh, float kl, float nh, float nl, const float2* xs, float2* out) {
-#define LSMS_BN(PT) launch_box_near_pt<PT>(grid, st, cff, sbox, bstart, nb, n, kh, kl, nh, nl, xs, out)
-  switch (p) {
-    case 0: LSMS_BN(0); break;
-    case 1: LSMS_BN(1); break;
-    case 2: LSMS_BN(2); break;
-    case 3: LSMS_BN(3); break;
-    case 4: LSMS_BN(4); break;
-    case 5: LSMS_BN(5); break;
-    case 6: LSMS_BN(6); break;
-    case 7: LSMS_BN(7); break;
-    case 8: LSMS_BN(8); break;
-    case 9: LSMS_BN(9); break;
-    case 10: LSMS_BN(10); break;
-    case 11: LSMS_BN(11); break;
-    case 12: LSMS_BN(12); break;
-    case 13: LSMS_BN(13); break;
-    case 14: LSMS_BN(14); break;
-    default: LSMS_BN(15); break;
-  }
-#undef LSMS_BN
-}
-
-// FP32 copies of the coefficients in both orders: x32 (disc order), xs32 (box order).
-__global__ void k_fmm_to_f32(const double2* __restrict__ x, const int* __restrict__ perm, int n, int P,
-                             long long len, float2* __restrict__ x32, float2* __restrict__ xs32) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long rt = i / P;
-    const int q = (int)(i - rt * P);
-    const long long r = rt / n;
-    const int tt = (int)(rt - r * n);
-    const double2 v = x[i];
-    x32[i] = make_float2((float)v.x, (float)v.y);
-    const double2 w = x[((size_t)r * n + perm[tt]) * P + q];
-    xs32[i] = make_float2((float)w.x, (float)w.y);
-  }
-}
-
-// alpha[r][perm[t]][nu] += part[r][t][nu]
-__global__ void k_fmm_scatter_add(const float2* __restrict__ part, const int* __restrict__ perm, int n, int P,
-                                  long long len, double2* __restrict__ alpha) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long rt = i / P;
-    const int q = (int)(i - rt * P);
-    const long long r = rt / n;
-    const int tt = (int)(rt - r * n);
-    double2* o = alpha + ((size_t)r * n + perm[tt]) * P + q;
-    const float2 v = part[i];
-    *o = make_double2(o->x + v.x, o->y + v.y);
-  }
-}
 
 __global__ void k_fmm_d2f(const double2* __restrict__ a, float2* __restrict__ b, long long total) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x)
     b[i] = make_float2((float)a[i].x, (float)a[i].y);
-}
-
-__global__ void k_fmm_ff_centres(const double* __restrict__ cx, const double* __restrict__ cy, int n,
-                                 float4* __restrict__ out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const float xh = (float)cx[j], yh = (float)cy[j];
-  out[j] = make_float4(xh, (float)(cx[j] - (double)xh), yh, (float)(cy[j] - (double)yh));
 }
 
 inline int blocks_for(long long total, int block) {
@@ -670,6 +613,14 @@ void fft_attributes() {
     cudaFuncSetAttribute(k_box_fft_cols<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
     cudaFuncSetAttribute(k_box_fft_rows<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
     cudaFuncSetAttribute(k_box_fft_rows<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
+    // the shift kernels need up to 4 warps x 4 rows x (2 (400 + 15) + 4) FP64 entries (L2L, order 400)
+    const int sh = 220 * 1024;
+    cudaFuncSetAttribute(k_fmm_m2m<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh);
+    cudaFuncSetAttribute(k_fmm_m2m<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh);
+    cudaFuncSetAttribute(k_fmm_l2l<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh);
+    cudaFuncSetAttribute(k_fmm_l2l<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh);
+    cudaFuncSetAttribute(k_fmm_m2l_direct<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh);
+    cudaFuncSetAttribute(k_fmm_m2l_direct<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh);
   });
 }
 
@@ -681,15 +632,19 @@ void box_far(const lsms_ctx* c, const double2* x, double2* a, const C* tab, C* b
              const C* hd, const C* twn, const C* tw2, cudaStream_t st) {
   const FmmState& f = c->fmm;
   const int n = c->n, p = c->p, P = 2 * p + 1, W = 2 * f.order + 1;
-  const int qthreads = ((W + 31) / 32) * 32;
-  k_fmm_m2m<C><<<f.nb, qthreads, P * sizeof(C), st>>>(x, f.d_perm, f.d_bstart, tab, p, f.order, f.S, bq);
+  const int L4s = (2 * f.S + 4) / 4, L4h = (4 * f.order + 4) / 4;
+  const unsigned gb = (unsigned)((f.nb + SH_W - 1) / SH_W);
+  k_fmm_m2m<C><<<gb, SH_W * 32, SH_W * (4 * L4s + P) * sizeof(C), st>>>(x, f.d_perm, f.d_bstart, tab, f.nb, p,
+                                                                      f.order, f.S, bq);
   launch_box_cols<C>(f, bq, W, f.nb, Y, W, f.n1, W, true, FFT_POST_TW, twn, st);
   launch_box_cols<C>(f, Y, W, f.n1, Y, W, f.n1, W, false, 0, twn, st);
   launch_box_rows<C>(f, Y, f.n1, khat, tw2, 1, st);
   launch_box_cols<C>(f, Y, W, f.n1, Y, W, f.n1, W, false, FFT_INV, twn, st);
   launch_box_cols<C>(f, Y, W, f.n1, acc, W, f.nb, W, true, FFT_INV | FFT_PRE_TW, twn, st);
-  if (f.dmin > 2) k_fmm_m2l_direct<C><<<f.nb, qthreads, 0, st>>>(bq, hd, f.nb, f.order, f.dmin, acc);
-  k_fmm_l2l<C><<<(int)(((long long)n * 32 + 255) / 256), 256, 0, st>>>(acc, f.d_dbox, tab, n, p, f.order, f.S, a);
+  if (f.dmin > 2)
+    k_fmm_m2l_direct<C><<<gb, SH_W * 32, SH_W * (4 * L4h + W) * sizeof(C), st>>>(bq, hd, f.nb, f.order, f.dmin, acc);
+  k_fmm_l2l<C><<<(unsigned)((n + 4 * SH_W - 1) / (4 * SH_W)), SH_W * 32, SH_W * 4 * 4 * L4s * sizeof(C), st>>>(
+      acc, f.d_dbox, tab, n, p, f.order, f.S, a);
 }
 
 }  // namespace
@@ -697,7 +652,8 @@ void box_far(const lsms_ctx* c, const double2* x, double2* a, const C* tab, C* b
 void fmm_free(lsms_ctx* c) {
   FmmState& f = c->fmm;
   void* ptrs[] = {f.d_perm,  f.d_bstart, f.d_dbox,   f.d_sbox,   f.d_scx,  f.d_scy,   f.d_tab,   f.d_khat,
-                  f.d_grid,  f.d_bq,     f.d_acc,    f.d_hd,     f.d_twn,  f.d_tw2,   f.d_scff,  f.ws.ptr,
+                  f.d_grid,  f.d_bq,     f.d_acc,    f.d_hd,     f.d_twn,  f.d_tw2,   f.d_cptr,  f.d_csrc,
+                  f.d_crow,  f.ws.ptr,
                   f.d_tab32, f.d_khat32, f.d_grid32, f.d_bq32,   f.d_acc32, f.d_hd32, f.d_twn32, f.d_tw232};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -749,6 +705,31 @@ int fmm_setup(lsms_ctx* c) {
     scx[t] = x[perm[t]];
     scy[t] = c->cy[perm[t]];
   }
+  // pair lists of the mixed near field by target in box order: every pair in the same or adjacent
+  // boxes, with its row in the near-pair table (CSR by disc, sorted by source) when it is one
+  std::vector<int> nptr(n + 1, 0), nidx((size_t)std::max(c->near_nnz, 0));
+  if (c->d_near_ptr && c->near_nnz >= 0) {
+    if (cudaMemcpy(nptr.data(), c->d_near_ptr, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        (c->near_nnz > 0 && cudaMemcpy(nidx.data(), c->d_near_idx, (size_t)c->near_nnz * sizeof(int),
+                                       cudaMemcpyDeviceToHost) != cudaSuccess))
+      return check_cuda(c, "set_fmm");
+  }
+  std::vector<int> cptr(n + 1, 0), csrc, crow;
+  csrc.reserve((size_t)f.near_pairs);
+  crow.reserve((size_t)f.near_pairs);
+  for (int t = 0; t < n; ++t) {
+    const int l = perm[t], b = dbox[l];
+    const int* nb0 = nidx.data() + nptr[l];
+    const int* nb1 = nidx.data() + nptr[l + 1];
+    for (int j = bstart[std::max(b - 1, 0)]; j < bstart[std::min(b + 2, nb)]; ++j) {
+      const int m = perm[j];
+      if (m == l) continue;
+      const int* it = std::lower_bound(nb0, nb1, m);
+      csrc.push_back(m);
+      crow.push_back(it != nb1 && *it == m ? (int)(it - nidx.data()) : -1);
+    }
+    cptr[t + 1] = (int)csrc.size();
+  }
   // offsets below dmin go box by box (k |d| w < 2Q + 2)
   f.dmin = 2;
   while (c->k2 * f.dmin * w < 2.0 * f.order + 2.0) ++f.dmin;
@@ -776,7 +757,9 @@ int fmm_setup(lsms_ctx* c) {
       cudaMalloc((void**)&f.d_sbox, n * sizeof(int)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_scx, n * sizeof(double)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_scy, n * sizeof(double)) != cudaSuccess ||
-      cudaMalloc((void**)&f.d_scff, (size_t)n * sizeof(float4)) != cudaSuccess) {
+      cudaMalloc((void**)&f.d_cptr, (n + 1) * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_csrc, std::max<size_t>(1, csrc.size()) * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_crow, std::max<size_t>(1, crow.size()) * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     fmm_free(c);
     return ctx_fail(c, LSMS_ERR_OOM, "set_fmm: cudaMalloc failed for the box tables");
@@ -787,8 +770,12 @@ int fmm_setup(lsms_ctx* c) {
   cudaMemcpy(f.d_sbox, sbox.data(), n * sizeof(int), cudaMemcpyHostToDevice);
   cudaMemcpy(f.d_scx, scx.data(), n * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(f.d_scy, scy.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(f.d_cptr, cptr.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice);
+  if (!csrc.empty()) {
+    cudaMemcpy(f.d_csrc, csrc.data(), csrc.size() * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(f.d_crow, crow.data(), crow.size() * sizeof(int), cudaMemcpyHostToDevice);
+  }
   cudaStream_t st = c->stream;
-  k_fmm_ff_centres<<<(n + 255) / 256, 256, 0, st>>>(f.d_scx, f.d_scy, n, f.d_scff);
   if (!f.far) {                    // near field only
     cudaStreamSynchronize(st);
     f.ready = true;
@@ -801,7 +788,7 @@ int fmm_setup(lsms_ctx* c) {
       cudaMalloc((void**)&f.d_acc, asz * sizeof(double2)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_hd, hsz * sizeof(double2)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_twn, (size_t)f.n1 * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc((void**)&f.d_tw2, (size_t)std::max(1, f.n2 / 2) * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&f.d_tw2, (size_t)f.n2 * sizeof(double2)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_tab32, tsz * sizeof(float2)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_khat32, gsz * sizeof(float2)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_grid32, ysz * sizeof(float2)) != cudaSuccess ||
@@ -809,7 +796,7 @@ int fmm_setup(lsms_ctx* c) {
       cudaMalloc((void**)&f.d_acc32, asz * sizeof(float2)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_hd32, hsz * sizeof(float2)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_twn32, (size_t)f.n1 * sizeof(float2)) != cudaSuccess ||
-      cudaMalloc((void**)&f.d_tw232, (size_t)std::max(1, f.n2 / 2) * sizeof(float2)) != cudaSuccess) {
+      cudaMalloc((void**)&f.d_tw232, (size_t)f.n2 * sizeof(float2)) != cudaSuccess) {
     cudaGetLastError();
     fmm_free(c);
     return ctx_fail(c, LSMS_ERR_OOM, "set_fmm: cudaMalloc failed for the box tables");
@@ -818,7 +805,7 @@ int fmm_setup(lsms_ctx* c) {
   k_fmm_shift_table<<<blocks_for((long long)tsz, 256), 256, 0, st>>>(c->d_cx, c->d_cy, f.d_dbox, n, f.x0, w,
                                                                       -0.5 * c->d, c->k2, f.S, f.d_tab);
   k_fft_twiddles<<<(f.n1 + 255) / 256, 256, 0, st>>>(f.d_twn, f.n1, f.n1);
-  k_fft_twiddles<<<(f.n2 / 2 + 255) / 256, 256, 0, st>>>(f.d_tw2, f.n2, f.n2 / 2);
+  k_fft_twiddles<<<(f.n2 + 255) / 256, 256, 0, st>>>(f.d_tw2, f.n2, f.n2);
   // the box kernel and its two-dimensional transform (orders, then the four-step split along the
   // boxes over all n2 columns), scaled by 1 / (n1 n2)
   cudaMemsetAsync(f.d_khat, 0, gsz * sizeof(double2), st);
@@ -833,7 +820,7 @@ int fmm_setup(lsms_ctx* c) {
   k_fmm_d2f<<<blocks_for((long long)tsz, 256), 256, 0, st>>>(f.d_tab, f.d_tab32, (long long)tsz);
   k_fmm_d2f<<<blocks_for((long long)gsz, 256), 256, 0, st>>>(f.d_khat, f.d_khat32, (long long)gsz);
   k_fmm_d2f<<<blocks_for((long long)f.n1, 256), 256, 0, st>>>(f.d_twn, f.d_twn32, (long long)f.n1);
-  k_fmm_d2f<<<blocks_for((long long)(f.n2 / 2), 256), 256, 0, st>>>(f.d_tw2, f.d_tw232, (long long)(f.n2 / 2));
+  k_fmm_d2f<<<blocks_for((long long)f.n2, 256), 256, 0, st>>>(f.d_tw2, f.d_tw232, (long long)f.n2);
   if (f.dmin > 2) k_fmm_d2f<<<blocks_for((long long)hsz, 256), 256, 0, st>>>(f.d_hd, f.d_hd32, (long long)hsz);
   cudaStreamSynchronize(st);
   f.ready = true;
@@ -861,22 +848,16 @@ int fmm_translate(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, bool
       box_far<double2>(c, x, a, f.d_tab, f.d_bq, f.d_grid, f.d_acc, f.d_khat, f.d_hd, f.d_twn, f.d_tw2, st);
   }
   if (mixed) {
-    // near field in FP32: box-order copies, the adjacent-box kernel, scatter-add, the near pairs
+    // near field in FP32: an FP32 copy of the coefficients, then the pair-list kernel
+    // (near_pairs.cuh) adds the same-box and adjacent-box pairs, in box order, into alpha
     const long long len = (long long)nrhs * n * P;
-    const size_t b = (((size_t)len * sizeof(float2)) + 255) & ~size_t(255);
     int rc;
-    if ((rc = ensure(c, f.ws, 3 * b))) return rc;
+    if ((rc = ensure(c, f.ws, (size_t)len * sizeof(float2)))) return rc;
     float2* x32 = (float2*)f.ws.ptr;
-    float2* xs32 = (float2*)((unsigned char*)f.ws.ptr + b);
-    float2* part = (float2*)((unsigned char*)f.ws.ptr + 2 * b);
     if (timed) cudaEventRecord(f.ev[1], st);
-    k_fmm_to_f32<<<blocks_for(len, 256), 256, 0, st>>>(xs, f.d_perm, n, P, len, x32, xs32);
-    const float kh = (float)c->k2, kl = (float)(c->k2 - (double)kh);
-    const float nh = (float)c->near_r2, nl = (float)(c->near_r2 - (double)nh);
-    dim3 grid((n + BW * BT - 1) / (BW * BT), 1, nrhs);
-    launch_box_near(p, grid, st, f.d_scff, f.d_sbox, f.d_bstart, f.nb, n, kh, kl, nh, nl, xs32, part);
-    k_fmm_scatter_add<<<blocks_for(len, 256), 256, 0, st>>>(part, f.d_perm, n, P, len, alpha);
-    launch_translate_near(c, nrhs, x32, alpha, st);
+    k_fmm_d2f<<<blocks_for(len, 256), 256, 0, st>>>(xs, x32, len);
+    launch_pair_lists(p, nrhs, st, f.d_perm, 0, n, n, (const float4*)c->d_lp_misc, f.d_cptr, f.d_csrc, f.d_crow,
+                      (const float4*)c->d_near_h, n, c->k2, x32, alpha);
     if (timed) cudaEventRecord(f.ev[2], st);
     f.timed = timed;
     return LSMS_OK;

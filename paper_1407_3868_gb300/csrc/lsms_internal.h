@@ -58,8 +58,10 @@ struct FmmState {
   double2* d_acc = nullptr;         // [nb][2Q + 1] local expansions A_i(nu)
   double2* d_hd = nullptr;          // [2 (dmin - 2)][4Q + 1] kernels of the direct offsets
   double2* d_twn = nullptr;         // [n1] e^{-2 pi i u / n1}
-  double2* d_tw2 = nullptr;         // [n2 / 2] e^{-2 pi i u / n2}
-  float4* d_scff = nullptr;         // [n] sorted centres, float-float (mixed near field)
+  double2* d_tw2 = nullptr;         // [n2] e^{-2 pi i u / n2}
+  int* d_cptr = nullptr;            // [n + 1] mixed near field: pairs in the same or adjacent box by
+  int* d_csrc = nullptr;            //   target in box order; source disc of each pair and its row in
+  int* d_crow = nullptr;            //   the near-pair table (k rho < 25), or -1 (k rho >= 25)
   float2* d_tab32 = nullptr;        // FP32 copies of the shift tables, the transformed kernel, the
   float2* d_khat32 = nullptr;       // work array, the box coefficients and expansions, the
   float2* d_grid32 = nullptr;       // direct-offset kernels and the twiddles (mixed-precision far
@@ -136,7 +138,7 @@ struct lsms_ctx {
   double near_r2 = 0.0;             // squared distance threshold
   int* d_near_ptr = nullptr;        // [n + 1]
   int* d_near_idx = nullptr;        // [nnz]
-  void* d_near_h = nullptr;         // float2 [nnz][4p + 1]
+  void* d_near_h = nullptr;         // float4 [nnz]: H_0, H_1 of each near pair (FP64-built)
 
   // workspaces
   DevBuf ws_x, ws_y, ws_xs, ws_alpha, ws_g, ws_v, ws_pq, ws_sig, ws_aux;

@@ -18,6 +18,7 @@
 #include "lsms_internal.h"
 #include "lsms_ops.h"
 #include "ff_hankel.cuh"
+#include "near_pairs.cuh"
 
 namespace {
 
@@ -275,71 +276,20 @@ k_translate_f32_h2(const float4* __restrict__ cff, int n, float k_hi, float k_lo
   }
 }
 
-// Near pairs (k2 rho < 25, a few per disc): their Hankel sequences are computed once per layout in
-// FP64 (CUDA J0, Y0, J1, Y1 and the forward recurrence) and stored in FP32; the main FP32 kernel
-// leaves these pairs out and k_translate_near adds them.
-__device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-__global__ void k_near_sequences(const double* __restrict__ cx, const double* __restrict__ cy,
-                                 const int* __restrict__ ptr, const int* __restrict__ idx, int n,
-                                 int p, double k, float2* __restrict__ table) {
+// Near pairs (k2 rho < 25, a few per disc): Hankel's expansion does not hold there, so H_0 and H_1
+// of every near pair are computed once per layout in FP64 (CUDA J0, Y0, J1, Y1) and stored in FP32
+// (float4: H_0, H_1); the near-pair kernels generate the other orders by the FP32 forward recurrence
+// from them.  The main FP32 kernel leaves these pairs out and k_translate_near adds them.
+__global__ void k_near_h01(const double* __restrict__ cx, const double* __restrict__ cy,
+                           const int* __restrict__ ptr, const int* __restrict__ idx, int n, double k,
+                           float4* __restrict__ table) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n) return;
-  const int S = 4 * p + 1, c0 = 2 * p;
   for (int e = ptr[l]; e < ptr[l + 1]; ++e) {
     const int m = idx[e];
-    const double dx = cx[l] - cx[m], dy = cy[l] - cy[m];
-    const double rho = hypot(dx, dy), z = k * rho;
-    const double2 e1 = make_double2(dx / rho, dy / rho);
-    float2* h = table + (size_t)e * S;
-    double2 hm = make_double2(j0(z), y0(z)), hq = make_double2(j1(z), y1(z)), eq = e1;
-    h[c0] = make_float2((float)hm.x, (float)hm.y);
-    for (int q = 1; q <= 2 * p; ++q) {
-      const double2 v = cmul_d(hq, eq);
-      const double2 u = cmul_d(hq, make_double2(eq.x, -eq.y));
-      const double sg = (q & 1) ? -1.0 : 1.0;
-      h[c0 + q] = make_float2((float)v.x, (float)v.y);
-      h[c0 - q] = make_float2((float)(sg * u.x), (float)(sg * u.y));
-      if (q < 2 * p) {
-        const double f = 2.0 * q / z;
-        const double2 hn = make_double2(f * hq.x - hm.x, f * hq.y - hm.y);
-        hm = hq;
-        hq = hn;
-        eq = cmul_d(eq, e1);
-      }
-    }
+    const double z = k * hypot(cx[l] - cx[m], cy[l] - cy[m]);
+    table[e] = make_float4((float)j0(z), (float)y0(z), (float)j1(z), (float)y1(z));
   }
-}
-
-// alpha[r][l - row0][nu] += sum over near sources m of sum_n h^{lm}_{n - nu} xs^m_n for the target
-// rows l = row0 .. row0 + nrows - 1; one warp per target.
-__global__ void k_translate_near(const int* __restrict__ ptr, const int* __restrict__ idx,
-                                 const float2* __restrict__ table, int n, int p,
-                                 const float2* __restrict__ xs, double2* __restrict__ alpha, int row0,
-                                 int nrows) {
-  const int l = row0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  const int r = blockIdx.y;
-  const int P = 2 * p + 1, S = 4 * p + 1;
-  if (l >= row0 + nrows || l >= n || lane >= P) return;
-  const float2* xr = xs + (size_t)r * n * P;
-  float ar = 0.f, ai = 0.f;
-  for (int e = ptr[l]; e < ptr[l + 1]; ++e) {
-    const float2* hs = table + (size_t)e * S + 2 * p - lane;   // hs[q] = h_{n - nu}
-    const float2* b = xr + (size_t)idx[e] * P;
-    for (int q = 0; q < P; ++q) {
-      const float2 hv = hs[q], bv = b[q];
-      ar = __fmaf_rn(hv.x, bv.x, ar);
-      ar = __fmaf_rn(-hv.y, bv.y, ar);
-      ai = __fmaf_rn(hv.x, bv.y, ai);
-      ai = __fmaf_rn(hv.y, bv.x, ai);
-    }
-  }
-  double2* o = alpha + ((size_t)r * nrows + (l - row0)) * P + lane;
-  o->x += ar;
-  o->y += ai;
 }
 
 // alpha[r][l][nu] = sum_split part[split][r][l][nu]   (double accumulation)
@@ -478,7 +428,7 @@ void launch_translate_kernel(dim3 grid, cudaStream_t st, const float4* cff, int 
 
 }  // namespace
 
-// CSR list of near pairs (k2 rho < 25) by target, from a cell grid, and their FP64 sequences.
+// CSR list of near pairs (k2 rho < 25) by target, from a cell grid, and their H_0, H_1 (FP64-built).
 static int build_near_pairs(lsms_ctx* c) {
   void* old[] = {c->d_near_ptr, c->d_near_idx, c->d_near_h};
   for (void* q : old)
@@ -515,7 +465,7 @@ static int build_near_pairs(lsms_ctx* c) {
     ptr[l + 1] = (int)idx.size();
   }
   c->near_nnz = (int)idx.size();
-  const size_t hb = (size_t)(c->near_nnz > 0 ? c->near_nnz : 1) * (4 * c->p + 1) * sizeof(float2);
+  const size_t hb = (size_t)(c->near_nnz > 0 ? c->near_nnz : 1) * sizeof(float4);
   if (cudaMalloc((void**)&c->d_near_ptr, (n + 1) * sizeof(int)) != cudaSuccess ||
       cudaMalloc((void**)&c->d_near_idx, (idx.empty() ? 1 : idx.size()) * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&c->d_near_h, hb) != cudaSuccess) {
@@ -525,8 +475,8 @@ static int build_near_pairs(lsms_ctx* c) {
   cudaMemcpy(c->d_near_ptr, ptr.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice);
   if (!idx.empty()) cudaMemcpy(c->d_near_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (n > 0 && c->near_nnz > 0)
-    k_near_sequences<<<(n + 127) / 128, 128, 0, c->stream>>>(c->d_cx, c->d_cy, c->d_near_ptr, c->d_near_idx,
-                                                            n, c->p, c->k2, (float2*)c->d_near_h);
+    k_near_h01<<<(n + 127) / 128, 128, 0, c->stream>>>(c->d_cx, c->d_cy, c->d_near_ptr, c->d_near_idx, n, c->k2,
+                                                       (float4*)c->d_near_h);
   cudaStreamSynchronize(c->stream);
   return check_cuda(c, "build_near_pairs");
 }
@@ -562,13 +512,15 @@ static int translate_splits(int n, int nrhs, int p, double mult = 1.0, int shape
   return s;
 }
 
+// The near pairs (k2 rho < 25) of the target rows row0 .. row0 + nrows - 1, added into alpha
+// (rows of nrows): the pair-list kernel with the near-pair CSR (table row = list entry).
 void launch_translate_near(lsms_ctx* c, int nrhs, const float2* xs32, double2* alpha, cudaStream_t st,
                            int row0, int nrows) {
   if (nrows < 0) nrows = c->n - row0;
   if (c->near_nnz <= 0 || nrows <= 0) return;
-  dim3 gn((unsigned)((nrows * 32 + 127) / 128), (unsigned)nrhs);
-  k_translate_near<<<gn, 128, 0, st>>>(c->d_near_ptr, c->d_near_idx, (const float2*)c->d_near_h, c->n, c->p,
-                                       xs32, alpha, row0, nrows);
+  launch_pair_lists(c->p, nrhs, st, nullptr, row0, std::min(nrows, c->n - row0), nrows,
+                    (const float4*)c->d_lp_misc, c->d_near_ptr, c->d_near_idx, nullptr,
+                    (const float4*)c->d_near_h, c->n, c->k2, xs32, alpha);
 }
 
 int translate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cudaStream_t st) {

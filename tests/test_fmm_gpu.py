@@ -88,17 +88,19 @@ def test_box_translation_matches_all_pairs(L, n, width, nrhs, order):
     assert rel(a[0][rows], a_o, ws) < TOL64
 
 
-@pytest.mark.parametrize("n,p", [(1000, 12), (300, 6)])
-def test_mixed_box_translation_matches_all_pairs(L, n, p):
+@pytest.mark.parametrize("n,p,width", [(1000, 12, 4.0), (300, 6, 4.0), (400, 8, 2.0)])
+def test_mixed_box_translation_matches_all_pairs(L, n, p, width):
     # mixed precision: the adjacent-box pairs in FP32 (pairs with k rho < 25 through the FP64-accurate
-    # near-pair tables), the far field through the FP64 boxes; the mixed-operator tolerance 2e-5
+    # near-pair tables), the far field through the FP32 boxes; the mixed-operator tolerance 2e-5.
+    # Boxes of width 2 are narrower than the near-pair radius 25 / k2 (2.65): some near pairs lie
+    # two boxes apart and belong to the far field, not to the near field as well.
     w = workload(n, p, 56)
     c = w.centres()
     hs, ws = weights(w)
     beta = inputs.random_coefficients(w.n, w.p, 2, 7) / hs[None, None, :]
     with L.context_for(w, L.LSMS_MIXED) as ctx:
         ctx.set_particles(c)
-        ctx.set_fmm(4.0)
+        ctx.set_fmm(width)
         a = ctx.translate(beta, precision=L.LSMS_MIXED)
         a64 = ctx.translate(beta, precision=L.LSMS_FP64)
     rows = [0, 3, n // 2, n - 1]
