@@ -182,7 +182,8 @@ k_fmm_m2m(const double2* __restrict__ xs, const int* __restrict__ perm, const in
 // pos NF + f (FFAST: the sequences interleaved) or f L + pos.  Radix-4 stages while two or more
 // factors of 2 remain, then one radix-2 stage.  With Ls the length already transformed,
 // tw[u] = e^{-2 pi i u / (L step)} (conjugated for the inverse), t = j Ls + k:
-//   radix 4 (t < L/4, m = L / (4 Ls), w^r = tw[r k m step]):  a_r = w^r x[t + r L/4],
+//   radix 4 (t < L/4, m = L / (4 Ls), w = tw[k m step], w^2, w^3 from the table (FP64) or as
+//     products (FP32)):  a_r = w^r x[t + r L/4],
 //     y[j 4Ls + k + q Ls] = sum_r (-i)^{q r} a_r   (+i for the inverse), q = 0..3;
 //   radix 2 (t < L/2, m = L / (2 Ls), w = tw[k m step]):
 //     y[j 2Ls + k] = x[t] + w x[t + L/2],   y[j 2Ls + k + Ls] = x[t] - w x[t + L/2].
@@ -211,7 +212,14 @@ __device__ C* smem_fft(C* x, C* y, int logL, int logNF, const C* __restrict__ tw
         }
         const int k = t & (Ls - 1), j = t >> s;
         const size_t u = (size_t)(k << msh) * step;
-        C w1 = tw[u], w2 = tw[2 * u], w3 = tw[3 * u];
+        C w1 = tw[u], w2, w3;
+        if (sizeof(C) == sizeof(double2)) {        // FP64: the table (the FP64 pipe is the limit)
+          w2 = tw[2 * u];
+          w3 = tw[3 * u];
+        } else {                                   // FP32: products (the loads cost more)
+          w2 = cmul(w1, w1);
+          w3 = cmul(w1, w2);
+        }
         if (inv) {
           w1.y = -w1.y;
           w2.y = -w2.y;
