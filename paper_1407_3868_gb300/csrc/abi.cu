@@ -101,7 +101,8 @@ int apply_device(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags,
   if ((rc = ensure(c, c->ws_xs, len * sizeof(double2)))) return rc;
   if ((rc = ensure(c, c->ws_alpha, len * sizeof(double2)))) return rc;
   double2* xs = (double2*)c->ws_xs.ptr;
-  double2* alpha = (double2*)c->ws_alpha.ptr;
+  const bool given = (flags & LSMS_APPLY_TRANSLATION_GIVEN) && c->alpha_given;
+  double2* alpha = given ? c->alpha_given : (double2*)c->ws_alpha.ptr;
   int launches = 0;
   launch_scale_in(x, c->d_scale_in + mode * P, xs, nrhs, n, P, st);
   ++launches;
@@ -121,7 +122,10 @@ int apply_device(lsms_ctx* c, int nrhs, const double2* x, double2* y, int flags,
     // and L2L; then the near field (FP64: one kernel; mixed: FP32 copy of xs and the pair-list
     // kernel).  All pairs: FP64 one kernel; mixed: FP32 copy of xs, the translation (+ the
     // partial-sum reduction, or the packing of the tensor-core operands) and the near pairs
-    if (c->fmm.ready && (c->fmm.scope == 0 || (flags & LSMS_APPLY_RESIDUAL_INTERNAL))) {
+    if (given) {
+      // computed for every layout of the batch at once (translate_mixed_batch)
+      cudaStreamWaitEvent(st, c->alpha_ready, 0);
+    } else if (c->fmm.ready && (c->fmm.scope == 0 || (flags & LSMS_APPLY_RESIDUAL_INTERNAL))) {
       if (c->fmm.far) launches += (c->fmm.dmin > 2 ? 8 : 7) * nrhs;
       launches += mixed ? 2 : 1;
       if ((rc = fmm_translate(c, nrhs, xs, alpha, mixed, st))) return rc;

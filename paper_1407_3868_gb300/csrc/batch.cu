@@ -30,6 +30,7 @@ void batch_clear_graphs(lsms_ctx* c) {
 
 void batch_free(lsms_ctx* c) {
   batch_clear_graphs(c);
+  batch_translation_free(c);
   for (cudaEvent_t e : c->kid_ev)
     if (e) cudaEventDestroy(e);
   c->kid_ev.clear();
@@ -94,6 +95,13 @@ extern "C" int lsms_set_layouts(lsms_ctx* c, int n_layouts, const int* counts, c
       return check_cuda(c, "set_layouts events");
     }
   c->n = (int)total;
+  int rc = batch_translation_setup(c);
+  if (rc) {
+    const std::string m = c->err;
+    batch_free(c);
+    c->n = -1;
+    return ctx_fail(c, rc, m);
+  }
   return LSMS_OK;
 }
 
@@ -102,18 +110,48 @@ extern "C" int lsms_num_layouts(const lsms_ctx* c) {
   return is_batch(c) ? (int)c->kids.size() : 1;
 }
 
-// Fork from st into every layout's stream, apply, join back into st.
+// The layouts' mixed all-pairs translations run as one launch over all layouts (one right-hand
+// side, every layout translating all pairs in FP32 for this application).
+static bool use_batch_translation(const lsms_ctx* c, int flags) {
+  if (!c->bt_ready || !(flags & LSMS_APPLY_MIXED) || (flags & LSMS_APPLY_NO_TRANSLATION)) return false;
+  for (const lsms_ctx* k : c->kids)
+    if (k->fmm.ready && (k->fmm.scope == 0 || (flags & LSMS_APPLY_RESIDUAL_INTERNAL))) return false;
+  return true;
+}
+
+// Fork from st into every layout's stream, apply, join back into st.  With the batched translation
+// the parent computes every layout's translation on st beside the layouts' reflected couplings; each
+// layout waits for it before it adds its reflection and combines.
 static int fork_join_apply(lsms_ctx* c, const double2* x, double2* y, int flags, cudaStream_t st) {
   const int nl = (int)c->kids.size();
   cudaEvent_t fork = c->kid_ev[nl];
   cudaEventRecord(fork, st);
+  const bool bt = use_batch_translation(c, flags);
+  double2* alpha_all = nullptr;
+  if (bt) {
+    const long long len = c->kid_off.back() * c->P;
+    int rc;
+    if ((rc = ensure(c, c->ws_xs, len * sizeof(double2)))) return rc;
+    if ((rc = ensure(c, c->ws_alpha, len * sizeof(double2)))) return rc;
+    double2* xs = (double2*)c->ws_xs.ptr;
+    alpha_all = (double2*)c->ws_alpha.ptr;
+    const int mode = (flags & LSMS_APPLY_SCALED) ? 1 : 0;
+    launch_scale_in(x, c->d_scale_in + mode * c->P, xs, 1, (int)c->kid_off.back(), c->P, st);
+    if ((rc = translate_mixed_batch(c, xs, alpha_all, st))) return rc;
+    cudaEventRecord(c->bt_ev, st);
+  }
   for (int l = 0; l < nl; ++l) {
     lsms_ctx* k = c->kids[l];
     const long long o = c->kid_off[l] * c->P;
     cudaStreamWaitEvent(k->stream, fork, 0);
     const int timing = k->timing;
     k->timing = 0;
-    const int rc = apply_device(k, 1, x + o, y + o, flags, k->stream);
+    k->alpha_given = bt ? alpha_all + o : nullptr;
+    k->alpha_ready = bt ? c->bt_ev : nullptr;
+    const int rc = apply_device(k, 1, x + o, y + o, bt ? (flags | LSMS_APPLY_TRANSLATION_GIVEN) : flags,
+                                k->stream);
+    k->alpha_given = nullptr;
+    k->alpha_ready = nullptr;
     k->timing = timing;
     if (rc) return ctx_fail(c, rc, "layout " + std::to_string(l) + ": " + k->err);
     cudaEventRecord(c->kid_ev[l], k->stream);

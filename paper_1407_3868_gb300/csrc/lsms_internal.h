@@ -15,6 +15,9 @@ using cplx = std::complex<double>;
 // internal apply flag (above the public LSMS_APPLY_* bits): the FP64 residual of the mixed
 // refinement, which takes the box translation when its scope is LSMS_FMM_RESIDUAL
 #define LSMS_APPLY_RESIDUAL_INTERNAL (1 << 12)
+// child of a layout batch: the translation of this application was computed for every layout at
+// once by the parent (alpha_given, ready at the event alpha_ready); skip it and add to it
+#define LSMS_APPLY_TRANSLATION_GIVEN (1 << 13)
 
 // ------------------------------------------------------------------------------------------
 // Device buffer owned by a context (grown on demand, never shrunk).
@@ -170,6 +173,20 @@ struct lsms_ctx {
   };
   std::vector<GraphEntry> graphs;   // captured batched applications
   std::vector<cudaEvent_t> kid_ev;  // join events (one per layout) and a fork event at the end
+  // the mixed all-pairs translation of every layout in one launch (mixed.cu, translate_mixed_batch)
+  bool bt_ready = false;
+  int bt_ncta = 0;                  // work items (layout, target tile, source split), largest first
+  void* d_bt_items = nullptr;       // int4 [bt_ncta]
+  void* d_bt_lays = nullptr;        // longlong4 [layouts]: disc offset, discs, sources per split, part offset
+  void* d_bt_cff = nullptr;         // float4 [total discs]: every layout's float-float centres
+  int* d_bt_nptr = nullptr;         // near pairs of all layouts: CSR by disc [total + 1] (global indices)
+  int* d_bt_nidx = nullptr;
+  void* d_bt_ntab = nullptr;        // float4 [nnz]: H_0, H_1
+  long long bt_part = 0;            // float2 partial sums of all layouts
+  DevBuf ws_bt;                     // scaled coefficients (FP64, FP32), partial sums, translation
+  cudaEvent_t bt_ev = nullptr;      // the batched translation is done
+  double2* alpha_given = nullptr;   // child: its rows of the parent's batched translation
+  cudaEvent_t alpha_ready = nullptr;
 
   cudaStream_t stream = nullptr;    // internal stream of the host-pointer entry points
 

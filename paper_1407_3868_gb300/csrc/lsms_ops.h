@@ -87,3 +87,9 @@ void launch_diag_mul(const double2* x, const double2* s, double2* y, long long t
                      cudaStream_t st);
 void launch_diag_scale(const double2* x, const double* s, double2* y, long long total, int P,
                        cudaStream_t st);
+
+// The mixed all-pairs translation of every layout of a batch in one launch (mixed.cu): the tables
+// (after lsms_set_layouts), and alpha of all layouts from their scaled coefficients xs.
+int batch_translation_setup(lsms_ctx* c);
+void batch_translation_free(lsms_ctx* c);
+int translate_mixed_batch(lsms_ctx* c, const double2* xs, double2* alpha, cudaStream_t st);

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <numeric>
 #include <unordered_map>
 #include <vector>
 
@@ -174,11 +175,13 @@ struct H2 {
 };
 constexpr int MT2 = 16;      // target discs per warp in the two-lanes-per-target kernel
 
+// One CTA of the two-lanes-per-target translation: target tile `tile` (64 discs), source split
+// `split`, right-hand side r.
 template <int PT>
-__global__ void __launch_bounds__(MW * 32, 3)
-k_translate_f32_h2(const float4* __restrict__ cff, int n, float k_hi, float k_lo,
-                   const float2* __restrict__ xs, float2* __restrict__ part, int src_per_split,
-                   int nrhs, float near_hi, float near_lo, int row0, int nrows) {
+__device__ __forceinline__ void h2_tile(const float4* __restrict__ cff, int n, float k_hi, float k_lo,
+                                        const float2* __restrict__ xs, float2* __restrict__ part,
+                                        int src_per_split, int nrhs, float near_hi, float near_lo, int row0,
+                                        int nrows, int tile, int split, int r) {
   constexpr int p = PT;
   constexpr int P = H2<PT>::P;
   constexpr int VB = H2<PT>::VB;
@@ -187,11 +190,9 @@ k_translate_f32_h2(const float4* __restrict__ cff, int n, float k_hi, float k_lo
   __shared__ float sbs[MCH][P];
   __shared__ float4 sc[MCH];
   extern __shared__ float2 sh[];
-  const int r = blockIdx.z;
-  const int split = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = lane & 15, hh = lane >> 4;       // hh = output half (contraction) = source (generation)
-  const int l = row0 + (blockIdx.x * MW + warp) * MT2 + t;     // target rows row0 .. row0 + nrows - 1
+  const int l = row0 + (tile * MW + warp) * MT2 + t;           // target rows row0 .. row0 + nrows - 1
   const bool lvalid = l < row0 + nrows && l < n;
   const float4 ct = lvalid ? cff[l] : make_float4(0.f, 0.f, 0.f, 0.f);
   for (int i = threadIdx.x; i < H2<PT>::SLOTS; i += blockDim.x) sh[i] = make_float2(0.f, 0.f);
@@ -276,6 +277,32 @@ k_translate_f32_h2(const float4* __restrict__ cff, int n, float k_hi, float k_lo
   }
 }
 
+template <int PT>
+__global__ void __launch_bounds__(MW * 32, 3)
+k_translate_f32_h2(const float4* __restrict__ cff, int n, float k_hi, float k_lo,
+                   const float2* __restrict__ xs, float2* __restrict__ part, int src_per_split,
+                   int nrhs, float near_hi, float near_lo, int row0, int nrows) {
+  h2_tile<PT>(cff, n, k_hi, k_lo, xs, part, src_per_split, nrhs, near_hi, near_lo, row0, nrows, blockIdx.x,
+              blockIdx.y, blockIdx.z);
+}
+
+// A batch of independent layouts in one launch: CTA b runs work item items[b] = (layout, tile,
+// split) of the layout table (disc offset, disc count, sources per split, partial-sum offset);
+// items are ordered by their layout's cost, largest first.  Centres, coefficients and partial sums
+// of all layouts are concatenated.
+template <int PT>
+__global__ void __launch_bounds__(MW * 32, 3)
+k_translate_f32_h2_batch(const float4* __restrict__ cff, const float2* __restrict__ xs,
+                         float2* __restrict__ part, const int4* __restrict__ items,
+                         const longlong4* __restrict__ lays, float k_hi, float k_lo, float near_hi,
+                         float near_lo) {
+  const int4 it = items[blockIdx.x];
+  const longlong4 L = lays[it.x];                 // (disc offset, discs, sources per split, part offset)
+  const int n = (int)L.y;
+  h2_tile<PT>(cff + L.x, n, k_hi, k_lo, xs + L.x * H2<PT>::P, part + L.w, (int)L.z, 1, near_hi, near_lo, 0, n,
+              it.y, it.z, 0);
+}
+
 // Near pairs (k2 rho < 25, a few per disc): Hankel's expansion does not hold there, so H_0 and H_1
 // of every near pair are computed once per layout in FP64 (CUDA J0, Y0, J1, Y1) and stored in FP32
 // (float4: H_0, H_1); the near-pair kernels generate the other orders by the FP32 forward recurrence
@@ -290,6 +317,43 @@ __global__ void k_near_h01(const double* __restrict__ cx, const double* __restri
     const double z = k * hypot(cx[l] - cx[m], cy[l] - cy[m]);
     table[e] = make_float4((float)j0(z), (float)y0(z), (float)j1(z), (float)y1(z));
   }
+}
+
+// Batched reduction: alpha[i] = sum over the splits of element i's layout of its partial sums
+// (one right-hand side; layouts by disc offset lays[l].x, ascending).
+__global__ void k_reduce_parts_batch(const float2* __restrict__ part, const longlong4* __restrict__ lays, int nlay,
+                                     long long total, int P, double2* __restrict__ alpha) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long d = i / P;
+    int lo = 0, hi = nlay - 1;                     // last layout with offset <= d
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (lays[mid].x <= d) lo = mid;
+      else hi = mid - 1;
+    }
+    const longlong4 L = lays[lo];
+    const long long per = L.y * P, e = i - L.x * P;
+    const int splits = (int)((L.y + L.z - 1) / L.z);
+    double ax = 0.0, ay = 0.0;
+    for (int sp = 0; sp < splits; ++sp) {
+      const float2 v = part[L.w + sp * per + e];
+      ax += v.x;
+      ay += v.y;
+    }
+    alpha[i] = make_double2(ax, ay);
+  }
+}
+
+template <int PT>
+void launch_h2_batch(int ncta, cudaStream_t st, const float4* cff, const float2* xs, float2* part, const int4* items,
+                     const longlong4* lays, float kh, float kl, float nh, float nl) {
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_translate_f32_h2_batch<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)H2<PT>::SMEM);
+  });
+  k_translate_f32_h2_batch<PT><<<ncta, MW * 32, H2<PT>::SMEM, st>>>(cff, xs, part, items, lays, kh, kl, nh, nl);
 }
 
 // alpha[r][l][nu] = sum_split part[split][r][l][nu]   (double accumulation)
@@ -588,6 +652,152 @@ int translate_mixed_rows(lsms_ctx* c, int nrhs, const double2* xs, double2* alph
   k_reduce_parts<<<(int)gr, 256, 0, st>>>(part, splits, len_rows, alpha_rows);
   launch_translate_near(c, nrhs, xs32, alpha_rows, st, row0, nrows);
   return check_cuda(c, "translate_mixed_rows");
+}
+
+// ---------------------------------------------------------------------------------------------
+// A layout batch's mixed all-pairs translation in one launch.  The work items (layout, target tile of
+// 64 discs, source split) of every layout form one grid, ordered by the layout's size, largest
+// first, so that the long tiles start early; the splits are chosen so that the grid covers the GPU
+// about four times.  The centres and the near-pair lists of all layouts are concatenated (pairs
+// never cross layouts).
+void batch_translation_free(lsms_ctx* c) {
+  void* ptrs[] = {c->d_bt_items, c->d_bt_lays, c->d_bt_cff, c->d_bt_nptr, c->d_bt_nidx, c->d_bt_ntab};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  c->d_bt_items = c->d_bt_lays = c->d_bt_cff = c->d_bt_ntab = nullptr;
+  c->d_bt_nptr = c->d_bt_nidx = nullptr;
+  if (c->bt_ev) cudaEventDestroy(c->bt_ev);
+  c->bt_ev = nullptr;
+  if (c->ws_bt.ptr) cudaFree(c->ws_bt.ptr);
+  c->ws_bt = DevBuf();
+  c->bt_ready = false;
+  c->bt_ncta = 0;
+  c->bt_part = 0;
+}
+
+int batch_translation_setup(lsms_ctx* c) {
+  batch_translation_free(c);
+  const int nl = (int)c->kids.size();
+  if (nl == 0 || c->p > LSMS_MAX_P || c->kid_off.back() == 0) return LSMS_OK;
+  const int P = c->P;
+  const long long total = c->kid_off.back();
+  const int tpc = MW * MT2;
+  long long tiles_all = 0;
+  for (int l = 0; l < nl; ++l) tiles_all += (c->kids[l]->n + tpc - 1) / tpc;
+  const int want = (int)std::max<long long>(1, (152LL * 3 * 4 + tiles_all - 1) / std::max<long long>(tiles_all, 1));
+  std::vector<longlong4> lays(nl);
+  std::vector<int> splits(nl);
+  long long part = 0;
+  for (int l = 0; l < nl; ++l) {
+    const int n = c->kids[l]->n;
+    int sp = std::max(1, std::min(want, (n + MCH - 1) / MCH));
+    int sps = std::max(1, (n + sp - 1) / sp);
+    sps = ((sps + MCH - 1) / MCH) * MCH;
+    sp = n > 0 ? (n + sps - 1) / sps : 0;
+    splits[l] = sp;
+    lays[l] = make_longlong4(c->kid_off[l], n, sps, part);
+    part += (long long)sp * n * P;
+  }
+  std::vector<int> order(nl);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return c->kids[a]->n > c->kids[b]->n; });
+  std::vector<int4> items;
+  for (int l : order) {
+    const int tiles = (c->kids[l]->n + tpc - 1) / tpc;
+    for (int t = 0; t < tiles; ++t)
+      for (int sp = 0; sp < splits[l]; ++sp) items.push_back(make_int4(l, t, sp, 0));
+  }
+  // near pairs of all layouts, global disc indices
+  std::vector<int> nptr(total + 1, 0), nidx;
+  long long nnz = 0;
+  for (int l = 0; l < nl; ++l) nnz += std::max(c->kids[l]->near_nnz, 0);
+  nidx.resize((size_t)std::max<long long>(nnz, 1));
+  if (cudaMalloc(&c->d_bt_items, std::max<size_t>(1, items.size()) * sizeof(int4)) != cudaSuccess ||
+      cudaMalloc(&c->d_bt_lays, nl * sizeof(longlong4)) != cudaSuccess ||
+      cudaMalloc(&c->d_bt_cff, total * sizeof(float4)) != cudaSuccess ||
+      cudaMalloc((void**)&c->d_bt_nptr, (total + 1) * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&c->d_bt_nidx, (size_t)std::max<long long>(nnz, 1) * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&c->d_bt_ntab, (size_t)std::max<long long>(nnz, 1) * sizeof(float4)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->bt_ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    batch_translation_free(c);
+    return ctx_fail(c, LSMS_ERR_OOM, "set_layouts: cudaMalloc failed for the batched translation");
+  }
+  long long e0 = 0;
+  for (int l = 0; l < nl; ++l) {
+    lsms_ctx* k = c->kids[l];
+    const long long off = c->kid_off[l];
+    const int n = k->n, kn = std::max(k->near_nnz, 0);
+    if (n <= 0) continue;
+    std::vector<int> kp(n + 1), ki((size_t)std::max(kn, 1));
+    if (cudaMemcpy((float4*)c->d_bt_cff + off, k->d_lp_misc, n * sizeof(float4), cudaMemcpyDeviceToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(kp.data(), k->d_near_ptr, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        (kn > 0 && (cudaMemcpy(ki.data(), k->d_near_idx, kn * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+                    cudaMemcpy((float4*)c->d_bt_ntab + e0, k->d_near_h, kn * sizeof(float4),
+                               cudaMemcpyDeviceToDevice) != cudaSuccess))) {
+      batch_translation_free(c);
+      return check_cuda(c, "set_layouts: batched translation tables");
+    }
+    for (int i = 0; i < n; ++i) nptr[off + i] = (int)(e0 + kp[i]);
+    for (int e = 0; e < kn; ++e) nidx[e0 + e] = (int)(off + ki[e]);
+    e0 += kn;
+  }
+  nptr[total] = (int)e0;
+  cudaMemcpy(c->d_bt_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_bt_lays, lays.data(), nl * sizeof(longlong4), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_bt_nptr, nptr.data(), (total + 1) * sizeof(int), cudaMemcpyHostToDevice);
+  if (nnz > 0) cudaMemcpy(c->d_bt_nidx, nidx.data(), nnz * sizeof(int), cudaMemcpyHostToDevice);
+  c->bt_ncta = (int)items.size();
+  c->bt_part = part;
+  c->bt_ready = true;
+  return check_cuda(c, "set_layouts: batched translation tables");
+}
+
+int translate_mixed_batch(lsms_ctx* c, const double2* xs, double2* alpha, cudaStream_t st) {
+  if (!c->bt_ready) return ctx_fail(c, LSMS_ERR_STATE, "batched translation tables are not built");
+  const int p = c->p, P = c->P;
+  const long long total = c->kid_off.back(), len = total * P;
+  const size_t b32 = (((size_t)len * sizeof(float2)) + 255) & ~size_t(255);
+  int rc;
+  if ((rc = ensure(c, c->ws_bt, b32 + (size_t)c->bt_part * sizeof(float2)))) return rc;
+  float2* xs32 = (float2*)c->ws_bt.ptr;
+  float2* part = (float2*)((unsigned char*)c->ws_bt.ptr + b32);
+  long long g = (len + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  k_to_float<<<(int)g, 256, 0, st>>>(xs, xs32, len);
+  const float kh = (float)c->k2, kl = (float)(c->k2 - (double)kh);
+  const double nr = c->kids[0]->near_r2;
+  const float nh = (float)nr, nl = (float)(nr - (double)nh);
+  const float4* cff = (const float4*)c->d_bt_cff;
+  const int4* items = (const int4*)c->d_bt_items;
+  const longlong4* lays = (const longlong4*)c->d_bt_lays;
+  if (c->bt_ncta > 0) {
+#define LSMS_HB(PT) launch_h2_batch<PT>(c->bt_ncta, st, cff, xs32, part, items, lays, kh, kl, nh, nl)
+    switch (p) {
+      case 0: LSMS_HB(0); break;
+      case 1: LSMS_HB(1); break;
+      case 2: LSMS_HB(2); break;
+      case 3: LSMS_HB(3); break;
+      case 4: LSMS_HB(4); break;
+      case 5: LSMS_HB(5); break;
+      case 6: LSMS_HB(6); break;
+      case 7: LSMS_HB(7); break;
+      case 8: LSMS_HB(8); break;
+      case 9: LSMS_HB(9); break;
+      case 10: LSMS_HB(10); break;
+      case 11: LSMS_HB(11); break;
+      case 12: LSMS_HB(12); break;
+      case 13: LSMS_HB(13); break;
+      case 14: LSMS_HB(14); break;
+      default: LSMS_HB(15); break;
+    }
+#undef LSMS_HB
+  }
+  k_reduce_parts_batch<<<(int)g, 256, 0, st>>>(part, lays, (int)c->kids.size(), len, P, alpha);
+  launch_pair_lists(p, 1, st, nullptr, 0, (int)total, (int)total, cff, c->d_bt_nptr, c->d_bt_nidx, nullptr,
+                    (const float4*)c->d_bt_ntab, (int)total, c->k2, xs32, alpha);
+  return check_cuda(c, "translate_mixed_batch");
 }
 
 // ---------------------------------------------------------------------------------------------

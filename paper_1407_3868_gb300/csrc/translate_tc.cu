@@ -9,25 +9,28 @@
 //   D (128 rows: TT targets x P orders, 128 columns: Re and Im outputs of 64 right-hand sides)
 //     += A (128 x K) . B (128 x K)^T,   K = 2P padded to 64,
 //
-// A row (target i, order nu) = [Re h_{n - nu}, n = 0..P-1 | Im h_{n - nu}, n = 0..P-1]; B row (Re, r)
-// = [Re beta_n(r) | -Im beta_n(r)], B row (Im, r) = [Im beta_n(r) | Re beta_n(r)], so D(Re, r) =
-// sum Re T Re beta - Im T Im beta and D(Im, r) = sum Re T Im beta + Im T Re beta.  A tile holds
+// with the K elements in pairs by source order n: A row (target i, order nu) has Re h_{n - nu} at
+// K = 2n and Im h_{n - nu} at 2n + 1; B row (Re, r) has Re beta_n(r), -Im beta_n(r) there, B row
+// (Im, r) Im beta_n(r), Re beta_n(r), so D(Re, r) = sum Re T Re beta - Im T Im beta and D(Im, r) =
+// sum Re T Im beta + Im T Re beta.  An A row is then a contiguous run of the pair sequence's packed
+// (Re, Im) words.  A tile holds
 // TT = floor(128 / P) targets (5 at p = 12: 125 of 128 rows used), and each MMA instruction computes
 // 64 right-hand sides' real and imaginary parts (N = 128: the instruction's fixed cost is shared by
 // twice the columns of an N = 64 embedding with the complex structure in the rows).  Both operands
 // are split into three BF16 planes x = hi + mid + lo and the six plane products with terms down to
 // 2^-16 relative are accumulated.  The Hankel sequences are the FP32 ones of the CUDA-core path;
-// near pairs (k2 rho < 25) and the self pair are left to k_translate_near.
+// near pairs (k2 rho < 25) and the self pair are left to the near-pair kernel.
 //
 // A persistent CTA (one per SM) owns a contiguous range of steps (right-hand-side block, group of
 // TG = 2 TT target discs, source disc).  Per step: warp 0 lane 0 copies the source's B planes (48 KB,
 // prepared once per application in the 128-byte-swizzled shared-memory image) with a bulk copy into
 // a 3-stage ring; warps 6-7 generate the FP32 pair sequences of the next chunk of CHS sources
-// (CHS TG <= 64 pairs, one per thread) into the other of two chunk buffers, one chunk ahead of their
-// use; warps 2-5 build the two A tiles of the step from the current chunk's sequences (each thread
-// one row: its 2P entries split into three BF16 planes on the fly) and write them straight into
-// tensor memory (tcgen05.st, 2-stage ring); warp 1 lane 0 issues 24 tcgen05.mma per tile with A
-// from tensor memory and B from shared memory into 2 accumulators (256 columns).  Every `flush`
+// (CHS TG <= 40 pairs, one per thread; fewer where the buffers would not fit), already split into three BF16 planes of packed (Re, Im)
+// words, into the other of two chunk buffers, one chunk ahead of their use; warps 2-5 build the two
+// A tiles of the step from the current chunk's planes (each thread one row: P words per plane,
+// copied) and write them straight into tensor memory (tcgen05.st, 2-stage ring); warp 1 lane 0
+// issues 24 tcgen05.mma per tile with A from tensor memory and B from shared memory into 2
+// accumulators (256 columns).  Every `flush`
 // source discs, warps 2-5 read the accumulators (tcgen05.ld) and add them into the FP64 output
 // with atomics: the tensor cores sum in FP32 with less than round-to-nearest accuracy, so the error
 // grows with the number of MMAs summed in one accumulator.  Every mbarrier wait is bounded; on a
@@ -51,15 +54,12 @@ constexpr int NCOL = 2 * RBLK;          // MMA N: Re and Im columns
 constexpr int B_PLANE = NCOL * 128;     // bytes: 128 rows x 64 BF16
 constexpr int B_STAGE = 3 * B_PLANE;    // 49152
 constexpr int NA = 2, NBS = 3;          // ring depths (A in tensor memory, B in shared memory)
-constexpr int SEQ = 64;                 // elements per pair sequence (>= 4p + 2)
 constexpr int NTHR = 256;               // warp 0: copies, warp 1: MMA, warps 2-5: operands and epilogue,
                                         // warps 6-7: pair sequences of the next chunk
 constexpr int NGEN = 64;                // generator threads
-constexpr int MAXPAIRS = NGEN;          // pairs per sequence chunk (CHS sources x TG targets)
-constexpr int RAWS = SEQ + 1;                                    // float2 per pair sequence (odd stride)
-constexpr int RAW_BYTES = 2 * MAXPAIRS * RAWS * 8;               // two chunk buffers: 66560
+constexpr int MAXPAIRS = 40;            // pairs per sequence chunk at most (CHS sources x TG targets)
 constexpr int BAR_BYTES = 256;
-constexpr size_t TC_SMEM = 1024 + (size_t)NBS * B_STAGE + RAW_BYTES + BAR_BYTES;
+constexpr int SMEM_LIMIT = 227 * 1024;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC_COLS = NTILE * NCOL;                       // 256
 constexpr uint32_t A_COLS = 3 * 32;                               // one A tile: 3 planes x 32 columns
@@ -68,17 +68,33 @@ constexpr uint32_t IDESC_T = idesc_bf16(128, NCOL);
 __host__ __device__ constexpr int plane_a(int q) { return q == 2 || q == 5 ? 1 : (q == 4 ? 2 : 0); }
 __host__ __device__ constexpr int plane_b(int q) { return q == 1 || q == 5 ? 1 : (q == 3 ? 2 : 0); }
 
-// Targets per tile and group, and sources per sequence chunk, for order p.
+// Words per plane of a pair sequence in the chunk buffers: the smallest R >= 4p + 1 with
+// 3 R + 2p + 1 = 0 mod 32.  An operand thread (row r = P i + nu of a tile) reads word w0 + n =
+// 2p - nu + n of pair i, at (pair base) + 3 R i + 2p - nu + n = const + i (3 R + P) - r + n, so with
+// 3 R + P = 0 mod 32 the 32 rows of a warp read 32 consecutive banks.
+__host__ __device__ constexpr int tc_rws(int p) {
+  int r = 4 * p + 1;
+  while ((3 * r + 2 * p + 1) % 32 != 0) ++r;
+  return r;
+}
+
+// Targets per tile and group, sources per sequence chunk and the chunk buffers, for order p.
 template <int PT>
 struct TcShape {
   static constexpr int P = 2 * PT + 1;
   static constexpr int TT = 128 / P;
   static constexpr int TG = NTILE * TT;
-  static constexpr int CHS = MAXPAIRS / TG > 0 ? MAXPAIRS / TG : 1;
+  static constexpr int RWS = tc_rws(PT);
+  static constexpr int FIT = (SMEM_LIMIT - 1024 - NBS * B_STAGE - BAR_BYTES) / (2 * 3 * RWS * 4);
+  static constexpr int PAIRS = MAXPAIRS < FIT ? MAXPAIRS : FIT;
+  static constexpr int CHS = PAIRS / TG > 0 ? PAIRS / TG : 1;
+  static constexpr int NPAIR = CHS * TG;                                    // pairs per chunk buffer
+  static constexpr int RAW_BYTES = 2 * NPAIR * 3 * RWS * 4;                 // two chunk buffers
+  static constexpr size_t SMEM = 1024 + (size_t)NBS * B_STAGE + RAW_BYTES + BAR_BYTES;
 };
 
-// B image of one (right-hand-side block, source disc): 3 planes x 128 rows x 128 bytes (K: first P
-// entries for Re beta_n ... see the file comment; zero from 2P); row j < 64 is output Re of
+// B image of one (right-hand-side block, source disc): 3 planes x 128 rows x 128 bytes (K element
+// 2n and 2n + 1 for order n, see the file comment; zero from 2P); row j < 64 is output Re of
 // right-hand side j, row 64 + j its Im; chunk c of row r at c ^ (r mod 8).
 __global__ void k_pack_b_tc(const double2* __restrict__ xs, int n, int P, int nrhs, int nrb,
                             unsigned char* __restrict__ img) {
@@ -96,13 +112,11 @@ __global__ void k_pack_b_tc(const double2* __restrict__ xs, int n, int P, int nr
       __nv_bfloat16 h[2], md[2], lo[2];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        const int kk = 8 * c + e + u;
+        const int kk = 8 * c + e + u, nn = kk >> 1;
         double x = 0.0;
-        if (rr < nrhs) {
-          const double2 b = kk < P ? xs[((size_t)rr * n + m) * P + kk]
-                                   : (kk < 2 * P ? xs[((size_t)rr * n + m) * P + kk - P] : make_double2(0.0, 0.0));
-          if (kk < P) x = im_row ? b.y : b.x;
-          else if (kk < 2 * P) x = im_row ? b.x : -b.y;
+        if (rr < nrhs && nn < P) {
+          const double2 b = xs[((size_t)rr * n + m) * P + nn];
+          x = (kk & 1) ? (im_row ? b.x : -b.y) : (im_row ? b.y : b.x);
         }
         split3(x, h[u], md[u], lo[u]);
       }
@@ -117,6 +131,48 @@ __global__ void k_pack_b_tc(const double2* __restrict__ xs, int n, int P, int nr
   }
 }
 
+// Pair sequence h[s + 2p] = H_s(k rho) e^{i s phi}, s = -2p..2p, as the generators store it: for
+// every element s, plane pl of words [pl][s] holds (BF16 plane pl of Re h | that of Im h << 16),
+// Re h = hi + mid + lo in BF16.  Near pairs (r2 below near_r2) are zero, as in hankel_sequence_f32.
+template <int RWS>
+__device__ __forceinline__ void put_planes(uint32_t* w, int s, float2 v) {
+  unsigned short ur[3], ui[3];
+  split3f(v.x, ur);
+  split3f(v.y, ui);
+#pragma unroll
+  for (int pl = 0; pl < 3; ++pl) w[pl * RWS + s] = (uint32_t)ur[pl] | ((uint32_t)ui[pl] << 16);
+}
+
+template <int PT>
+__device__ __forceinline__ void hankel_planes(float4 a, float4 b, ffl k, ffl near_r2, uint32_t* w) {
+  constexpr int p = PT;
+  constexpr int RWS = TcShape<PT>::RWS;
+  const PairGeom g = pair_geometry(a, b, k);
+  if (near_r2.hi > 0.0f && (g.r2.hi < near_r2.hi || (g.r2.hi == near_r2.hi && g.r2.lo < near_r2.lo))) {
+    for (int q = 0; q < 3 * RWS; ++q) w[q] = 0u;
+    return;
+  }
+  float2 h0, h1;
+  hankel01_f32(g, h0, h1);
+  const int c0 = 2 * p;
+  put_planes<RWS>(w, c0, h0);
+  float2 hm = h0, hq = h1, eq = g.e1;
+  const float iz = 1.0f / g.zf;
+#pragma unroll
+  for (int q = 1; q <= 2 * p; ++q) {
+    put_planes<RWS>(w, c0 + q, cmulf(hq, eq));
+    const float2 u = cmulf(hq, make_float2(eq.x, -eq.y));
+    put_planes<RWS>(w, c0 - q, (q & 1) ? make_float2(-u.x, -u.y) : u);
+    if (q < 2 * p) {
+      const float f = 2.0f * q * iz;
+      const float2 hn = make_float2(f * hq.x - hm.x, f * hq.y - hm.y);
+      hm = hq;
+      hq = hn;
+      eq = cmulf(eq, g.e1);
+    }
+  }
+}
+
 template <int PT>
 __global__ void __launch_bounds__(NTHR, 1)
 k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, float near_hi,
@@ -124,11 +180,12 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
                int flush, double2* __restrict__ alpha, int* __restrict__ err) {
   constexpr int p = PT, P = 2 * PT + 1;
   constexpr int TT = TcShape<PT>::TT, TG = TcShape<PT>::TG, CHS = TcShape<PT>::CHS;
+  constexpr int RWS = TcShape<PT>::RWS, NPAIR = TcShape<PT>::NPAIR;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sB = smem;
-  float2* raw = (float2*)(sB + NBS * B_STAGE);               // [2][MAXPAIRS][RAWS] FP32 sequences
-  uint64_t* bars = (uint64_t*)((unsigned char*)raw + RAW_BYTES);
+  uint32_t* raw = (uint32_t*)(sB + NBS * B_STAGE);          // [2][NPAIR][3][RWS] BF16-plane words
+  uint64_t* bars = (uint64_t*)((unsigned char*)raw + TcShape<PT>::RAW_BYTES);
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * NA + 2 * NBS + 3 + 4);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   volatile int* bcast = abort_flag + 1;
@@ -303,28 +360,14 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
             break;
           }
           tc_fence_after();
-          // K element k < P: Re h[w0 + k]; P <= k < 2P: Im h[w0 + k - P]; word k / 2, half k mod 2
+          // K element 2n: Re h[w0 + n], 2n + 1: Im h[w0 + n]: word n of plane pl is the generators'
+          // packed word (Re, Im) of sequence element w0 + n
           uint32_t v[3][32];
+          const uint32_t* hr = raw + ((size_t)cb * NPAIR + j * TG + tt * TT + (valid ? ti : 0)) * 3 * RWS + w0;
 #pragma unroll
           for (int pl = 0; pl < 3; ++pl)
 #pragma unroll
-            for (int jw = 0; jw < 32; ++jw) v[pl][jw] = 0u;
-          if (valid) {
-            const float2* hr = raw + ((size_t)cb * MAXPAIRS + j * TG + tt * TT + ti) * RAWS + w0;
-#pragma unroll
-            for (int nn = 0; nn < P; ++nn) {
-              const float2 hv = hr[nn];
-              unsigned short ur[3], ui[3];
-              split3f(hv.x, ur);
-              split3f(hv.y, ui);
-              const int kr = nn, ki = P + nn;
-#pragma unroll
-              for (int pl = 0; pl < 3; ++pl) {
-                v[pl][kr >> 1] |= (uint32_t)ur[pl] << (16 * (kr & 1));
-                v[pl][ki >> 1] |= (uint32_t)ui[pl] << (16 * (ki & 1));
-              }
-            }
-          }
+            for (int jw = 0; jw < 32; ++jw) v[pl][jw] = (valid && jw < P) ? hr[pl * RWS + jw] : 0u;
           const uint32_t taddr = tmem + lane_addr + ACC_COLS + as * A_COLS;
 #pragma unroll
           for (int pl = 0; pl < 3; ++pl) tmem_st32(taddr + pl * 32, v[pl]);
@@ -379,8 +422,8 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
     }
   } else if (warp >= 6) {
     // ---- generators: 64 threads, named barrier 2.  They walk the same chunks as the operand warps
-    // one chunk ahead, writing the FP32 pair sequences of chunk c into buffer c mod 2 once the
-    // operand warps have released it (chunk c - 2).
+    // one chunk ahead, writing the pair sequences of chunk c, split into BF16 planes, into buffer
+    // c mod 2 once the operand warps have released it (chunk c - 2).
     const int gt = threadIdx.x - 192;
     const ffl kf = {k_hi, k_lo}, nr = {near_hi, near_lo};
     long long s = s0, chunk = 0;
@@ -404,11 +447,11 @@ k_translate_tc(const float4* __restrict__ cff, int n, float k_hi, float k_lo, fl
       if (gt < TG * cnt) {
         const int i = gt % TG, j = gt / TG;
         const int l = g * TG + i, m = m0 + j;
-        float2* h = raw + ((size_t)cb * MAXPAIRS + gt) * RAWS;
+        uint32_t* h = raw + ((size_t)cb * NPAIR + gt) * 3 * RWS;
         if (l < n && l != m) {
-          hankel_sequence_f32<PT>(cff[l], cff[m], kf, nr, h);
+          hankel_planes<PT>(cff[l], cff[m], kf, nr, h);
         } else {
-          for (int q = 0; q <= 4 * p; ++q) h[q] = make_float2(0.f, 0.f);
+          for (int q = 0; q < 3 * RWS; ++q) h[q] = 0u;
         }
       }
       named_bar_sync(2, NGEN);
@@ -431,9 +474,10 @@ void launch_tc(int grid, cudaStream_t st, const float4* cff, int n, float kh, fl
                const unsigned char* img, int nrhs, long long nsteps, int flush, double2* alpha, int* err) {
   static std::once_flag attr;
   std::call_once(attr, [] {
-    cudaFuncSetAttribute(k_translate_tc<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+    cudaFuncSetAttribute(k_translate_tc<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)TcShape<PT>::SMEM);
   });
-  k_translate_tc<PT><<<grid, NTHR, TC_SMEM, st>>>(cff, n, kh, kl, nh, nl, img, nrhs, nsteps, flush, alpha, err);
+  k_translate_tc<PT><<<grid, NTHR, TcShape<PT>::SMEM, st>>>(cff, n, kh, kl, nh, nl, img, nrhs, nsteps, flush, alpha, err);
 }
 
 int tc_group_size(int p) { return NTILE * (128 / (2 * p + 1)); }

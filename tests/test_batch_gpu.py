@@ -1,7 +1,8 @@
 """GPU tests of the batched forms: a batch of independent layouts (design sweep) and the autotuner.
 
 A layout batch must give, layout by layout, what a context holding that layout alone gives (same
-kernels, so to rounding), and one of its layouts is also checked against the FP64 oracle.
+kernels, so to rounding; in mixed precision the batch translates every layout in one launch, whose
+source splits differ), and one of its layouts is also checked against the FP64 oracle.
 """
 import numpy as np
 import pytest
@@ -64,6 +65,33 @@ def test_batch_apply_equals_single_layout_contexts(L, precision):
         ctx.close()
         off += len(c)
     batch.close()
+
+
+def test_batched_translation_with_ragged_layouts(L):
+    # layouts of 1, 63, 64, 65 and 130 discs straddle the 64-target tiles of the one-launch
+    # translation; every layout against a context holding it alone, one against the oracle
+    w = workload()
+    sizes = (65, 1, 130, 64, 63)
+    lay = [inputs.layout(n, -0.3 * n - 1.0, 0.3 * n + 1.0, 70 + n) for n in sizes]
+    m = w.medium
+    hs = O.order_scale(w.p, m["k2"], m["radius"])
+    x = np.concatenate([inputs.random_coefficients(len(c), w.p, 1, 80 + i)[0] / hs for i, c in enumerate(lay)])
+    with L.context_for(w, L.LSMS_MIXED) as batch:
+        batch.set_layouts(lay)
+        y = batch.apply(x, L.APPLY_MIXED)[0]
+        y_again = batch.apply(x, L.APPLY_MIXED)[0]
+    off = 0
+    for i, c in enumerate(lay):
+        with L.context_for(w, L.LSMS_MIXED) as ctx:
+            ctx.set_particles(c)
+            ys = ctx.apply(x[off:off + len(c)], L.APPLY_MIXED)[0]
+        assert rel(y[off:off + len(c)], ys, hs) < 1e-6, sizes[i]
+        assert rel(y_again[off:off + len(c)], ys, hs) < 1e-6, sizes[i]
+        if sizes[i] == 65:
+            lam, wt = O.contour(w.n_nodes, m["k1"], m["k2"], m["k3"], w.b, w.t_max)
+            pr = O.Problem(O.Medium(m["k1"], m["k2"], m["k3"], m["d"], m["kp"], m["radius"]), w.p, c, lam, wt)
+            assert rel(y[off:off + len(c)], pr.apply(x[off:off + len(c)]), hs) < 2e-5
+        off += len(c)
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-8)])
