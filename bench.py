@@ -632,12 +632,18 @@ def run_batched(args, dev, flush):
         b.apply_dev(x, y, lsms.APPLY_SCALED)
     torch.cuda.synchronize()
     ms_d = time_device(lambda: b.apply_dev(x, y, lsms.APPLY_SCALED), 1, flush)
+    waves, items = b.batch_translation()
+    sweep_flop = sum(translation_flop(len(c), ws.p) for c in lay)
     sw = {"workload": ws.name, "layouts": len(lay), "discs": ntot, "p": ws.p, "contour_nodes": ws.n_nodes,
           "autotuned": {"layouts_two_lane_tiles": sum(1 for sh, _ in tuning if sh == 0),
                         "layouts_four_lane_tiles": sum(1 for sh, _ in tuning if sh == 1),
-                        "split_mults": sorted({m for _, m in tuning})},
+                        "split_mults": sorted({m for _, m in tuning}),
+                        "batched_translation": {"waves": waves, "work_items": items}},
           "mixed": {"ms_per_sweep_apply": ms_m, "layout_applies_per_s": len(lay) * 1e3 / ms_m,
-                    "launch": "one CUDA graph (128 branches)"},
+                    "launch": "one CUDA graph: the layouts' translations in one kernel launch (work items "
+                              "largest layout first), their reflected couplings in 128 branches",
+                    "translation_flop": sweep_flop,
+                    "apply_frac_of_fp32_peak": sweep_flop / (ms_m / 1e3) / 1e12 / FP32_PEAK_TFLOPS},
           "fp64": {"ms_per_sweep_apply": ms_d, "layout_applies_per_s": len(lay) * 1e3 / ms_d}}
     sw["speedup_mixed_vs_fp64"] = ms_d / ms_m
     if not args.no_solve:

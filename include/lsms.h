@@ -250,8 +250,10 @@ int lsms_num_layouts(const lsms_ctx* ctx);
  *   largest layout of every power-of-two size bucket of a batch, applied to the whole bucket) in its
  *   two tile shapes (0: two lanes per target disc, 64 targets per CTA; 1: four lanes per target, 32
  *   per CTA, twice the CTAs for small layouts) under five source-split multipliers (0.5 .. 3), and
- *   keep the fastest pair; *split_mult (may be NULL) receives the (last bucket's) factor.  No
- *   counterpart in the paper: a tuning step of this implementation.
+ *   keep the fastest pair; *split_mult (may be NULL) receives the (last bucket's) factor.  For a
+ *   batch it then times the one-launch translation of all layouts (used by the batched mixed
+ *   application) with its work items covering the GPU 1, 2, 4 or 8 times and keeps the fastest.
+ *   No counterpart in the paper: a tuning step of this implementation.
  * lsms_get_translation_tuning / lsms_set_translation_tuning — the (shape, split multiplier) of
  *   layout `layout` (0 or -1 for a single layout; for a batch its layout index, -1 in the setter:
  *   every layout), e.g. to store the tuning and apply it again without timing.  shape 0 or 1,
@@ -259,6 +261,11 @@ int lsms_num_layouts(const lsms_ctx* ctx);
 int lsms_autotune(lsms_ctx* ctx, double* split_mult);
 int lsms_get_translation_tuning(const lsms_ctx* ctx, int layout, int* shape, double* split_mult);
 int lsms_set_translation_tuning(lsms_ctx* ctx, int layout, int shape, double split_mult);
+/* lsms_get_batch_translation — for a layout batch, the one-launch translation of all layouts: how
+ *   many times its work items (layout, tile of 64 target discs, source split) cover the GPU (4 until
+ *   lsms_autotune picks) and their number; (0, 0) for a single layout or when the batch has none.
+ *   NULL outputs are skipped.  Errors: LSMS_ERR_ARG (NULL ctx). */
+int lsms_get_batch_translation(const lsms_ctx* ctx, int* waves, int* work_items);
 
 /* lsms_set_tc_translation — mixed-precision translations of at least min_rhs right-hand sides at
  *   once (a block of sources, Sec. 3.2 Lemma 3.1 applied to every column) run on the tensor cores:

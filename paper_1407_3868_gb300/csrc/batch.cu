@@ -8,7 +8,8 @@
 // a join; the graph is captured on the first application with a given (x, y, flags) and replayed
 // afterwards.  A batched solve runs the layouts' solves (each a graph-captured device GMRES) from a
 // small host thread pool, largest layout first, so that the GPU works on many layouts at once.
-// lsms_autotune picks the FP32 translation's tile shape and source-split factor by timing candidates.
+// lsms_autotune picks the FP32 translation's tile shape and source-split factor by timing candidates,
+// and for a batch how finely the one-launch translation of all layouts splits its sources.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -344,7 +345,52 @@ extern "C" int lsms_autotune(lsms_ctx* c, double* split_mult) {
     done.push_back(b);
     if (split_mult) *split_mult = mb;   // the last bucket's factor
   }
+  // the one-launch translation of all layouts: how many times its work items cover the GPU
+  if (c->bt_ready) {
+    const size_t len = (size_t)c->kid_off.back() * c->P;
+    int rc;
+    if ((rc = ensure(c, c->ws_xs, len * sizeof(double2))) || (rc = ensure(c, c->ws_alpha, len * sizeof(double2))))
+      return rc;
+    cudaMemsetAsync(c->ws_xs.ptr, 0, len * sizeof(double2), c->stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_w = c->bt_waves;
+    for (int w : {1, 2, 4, 8}) {
+      c->bt_waves = w;
+      if ((rc = batch_translation_items(c))) break;
+      const double2* xs = (const double2*)c->ws_xs.ptr;
+      double2* a = (double2*)c->ws_alpha.ptr;
+      if ((rc = translate_mixed_batch(c, xs, a, c->stream))) break;
+      cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < 3 && !rc; ++r) rc = translate_mixed_batch(c, xs, a, c->stream);
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rc) break;
+      if (ms < best) {
+        best = ms;
+        best_w = w;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->bt_waves = best_w;
+    const int rc2 = batch_translation_items(c);
+    if (rc) return rc;
+    if (rc2) return rc2;
+  }
   batch_clear_graphs(c);
+  return LSMS_OK;
+}
+
+extern "C" int lsms_get_batch_translation(const lsms_ctx* c, int* waves, int* work_items) {
+  if (!c) return LSMS_ERR_ARG;
+  const bool on = is_batch(c) && c->bt_ready;
+  if (waves) *waves = on ? c->bt_waves : 0;
+  if (work_items) *work_items = on ? c->bt_ncta : 0;
   return LSMS_OK;
 }
 

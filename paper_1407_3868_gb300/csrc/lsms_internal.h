@@ -176,6 +176,7 @@ struct lsms_ctx {
   // the mixed all-pairs translation of every layout in one launch (mixed.cu, translate_mixed_batch)
   bool bt_ready = false;
   int bt_ncta = 0;                  // work items (layout, target tile, source split), largest first
+  int bt_waves = 4;                 // the items cover the GPU about this many times (autotuned)
   void* d_bt_items = nullptr;       // int4 [bt_ncta]
   void* d_bt_lays = nullptr;        // longlong4 [layouts]: disc offset, discs, sources per split, part offset
   void* d_bt_cff = nullptr;         // float4 [total discs]: every layout's float-float centres

@@ -91,5 +91,6 @@ void launch_diag_scale(const double2* x, const double* s, double2* y, long long 
 // The mixed all-pairs translation of every layout of a batch in one launch (mixed.cu): the tables
 // (after lsms_set_layouts), and alpha of all layouts from their scaled coefficients xs.
 int batch_translation_setup(lsms_ctx* c);
+int batch_translation_items(lsms_ctx* c);   // the work items for c->bt_waves (setup and autotune)
 void batch_translation_free(lsms_ctx* c);
 int translate_mixed_batch(lsms_ctx* c, const double2* xs, double2* alpha, cudaStream_t st);

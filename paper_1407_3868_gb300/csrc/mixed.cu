@@ -675,16 +675,14 @@ void batch_translation_free(lsms_ctx* c) {
   c->bt_part = 0;
 }
 
-int batch_translation_setup(lsms_ctx* c) {
-  batch_translation_free(c);
+int batch_translation_items(lsms_ctx* c) {
   const int nl = (int)c->kids.size();
-  if (nl == 0 || c->p > LSMS_MAX_P || c->kid_off.back() == 0) return LSMS_OK;
   const int P = c->P;
-  const long long total = c->kid_off.back();
   const int tpc = MW * MT2;
   long long tiles_all = 0;
   for (int l = 0; l < nl; ++l) tiles_all += (c->kids[l]->n + tpc - 1) / tpc;
-  const int want = (int)std::max<long long>(1, (152LL * 3 * 4 + tiles_all - 1) / std::max<long long>(tiles_all, 1));
+  const long long target = 152LL * 3 * std::max(1, c->bt_waves);
+  const int want = (int)std::max<long long>(1, (target + tiles_all - 1) / std::max<long long>(tiles_all, 1));
   std::vector<longlong4> lays(nl);
   std::vector<int> splits(nl);
   long long part = 0;
@@ -707,14 +705,32 @@ int batch_translation_setup(lsms_ctx* c) {
     for (int t = 0; t < tiles; ++t)
       for (int sp = 0; sp < splits[l]; ++sp) items.push_back(make_int4(l, t, sp, 0));
   }
+  if (c->d_bt_items) cudaFree(c->d_bt_items);
+  if (c->d_bt_lays) cudaFree(c->d_bt_lays);
+  c->d_bt_items = c->d_bt_lays = nullptr;
+  if (cudaMalloc(&c->d_bt_items, std::max<size_t>(1, items.size()) * sizeof(int4)) != cudaSuccess ||
+      cudaMalloc(&c->d_bt_lays, nl * sizeof(longlong4)) != cudaSuccess) {
+    cudaGetLastError();
+    return ctx_fail(c, LSMS_ERR_OOM, "batched translation: cudaMalloc failed for the work items");
+  }
+  cudaMemcpy(c->d_bt_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_bt_lays, lays.data(), nl * sizeof(longlong4), cudaMemcpyHostToDevice);
+  c->bt_ncta = (int)items.size();
+  c->bt_part = part;
+  return check_cuda(c, "batched translation work items");
+}
+
+int batch_translation_setup(lsms_ctx* c) {
+  batch_translation_free(c);
+  const int nl = (int)c->kids.size();
+  if (nl == 0 || c->p > LSMS_MAX_P || c->kid_off.back() == 0) return LSMS_OK;
+  const long long total = c->kid_off.back();
   // near pairs of all layouts, global disc indices
   std::vector<int> nptr(total + 1, 0), nidx;
   long long nnz = 0;
   for (int l = 0; l < nl; ++l) nnz += std::max(c->kids[l]->near_nnz, 0);
   nidx.resize((size_t)std::max<long long>(nnz, 1));
-  if (cudaMalloc(&c->d_bt_items, std::max<size_t>(1, items.size()) * sizeof(int4)) != cudaSuccess ||
-      cudaMalloc(&c->d_bt_lays, nl * sizeof(longlong4)) != cudaSuccess ||
-      cudaMalloc(&c->d_bt_cff, total * sizeof(float4)) != cudaSuccess ||
+  if (cudaMalloc(&c->d_bt_cff, total * sizeof(float4)) != cudaSuccess ||
       cudaMalloc((void**)&c->d_bt_nptr, (total + 1) * sizeof(int)) != cudaSuccess ||
       cudaMalloc((void**)&c->d_bt_nidx, (size_t)std::max<long long>(nnz, 1) * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&c->d_bt_ntab, (size_t)std::max<long long>(nnz, 1) * sizeof(float4)) != cudaSuccess ||
@@ -744,12 +760,13 @@ int batch_translation_setup(lsms_ctx* c) {
     e0 += kn;
   }
   nptr[total] = (int)e0;
-  cudaMemcpy(c->d_bt_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
-  cudaMemcpy(c->d_bt_lays, lays.data(), nl * sizeof(longlong4), cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_bt_nptr, nptr.data(), (total + 1) * sizeof(int), cudaMemcpyHostToDevice);
   if (nnz > 0) cudaMemcpy(c->d_bt_nidx, nidx.data(), nnz * sizeof(int), cudaMemcpyHostToDevice);
-  c->bt_ncta = (int)items.size();
-  c->bt_part = part;
+  int rc = batch_translation_items(c);
+  if (rc) {
+    batch_translation_free(c);
+    return rc;
+  }
   c->bt_ready = true;
   return check_cuda(c, "set_layouts: batched translation tables");
 }

@@ -36,7 +36,7 @@ EXPORTS = ["lsms_create", "lsms_layer_response", "lsms_build_contour_stack", "ls
            "lsms_build_contour", "lsms_scattering_diagonal", "lsms_check_geometry",
            "lsms_set_timing", "lsms_last_timing", "lsms_translate_mixed_noalloc",
            "lsms_set_layouts", "lsms_num_layouts", "lsms_autotune", "lsms_set_tc_translation",
-           "lsms_get_translation_tuning", "lsms_set_translation_tuning"]
+           "lsms_get_translation_tuning", "lsms_set_translation_tuning", "lsms_get_batch_translation"]
 
 
 class LsmsError(RuntimeError):
@@ -117,6 +117,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsms_autotune": (i, [_P, _D]),
         "lsms_get_translation_tuning": (i, [_P, i, ctypes.POINTER(ctypes.c_int), _D]),
         "lsms_set_translation_tuning": (i, [_P, i, i, d]),
+        "lsms_get_batch_translation": (i, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "lsms_set_tc_translation": (i, [_P, i, i]),
     }
     for name, (res, args) in sig.items():
@@ -248,6 +249,12 @@ class Context:
         shape, mult = ctypes.c_int(), ctypes.c_double()
         self._check(self.lib.lsms_get_translation_tuning(self.h, int(layout), ctypes.byref(shape), ctypes.byref(mult)))
         return shape.value, mult.value
+
+    def batch_translation(self):
+        """lsms_get_batch_translation: (waves, work items) of a batch's one-launch translation."""
+        waves, items = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.lsms_get_batch_translation(self.h, ctypes.byref(waves), ctypes.byref(items)))
+        return waves.value, items.value
 
     def set_translation_tuning(self, layout, shape, split_mult):
         """lsms_set_translation_tuning (layout -1: every layout)."""

@@ -78,6 +78,8 @@ def test_batched_translation_with_ragged_layouts(L):
     x = np.concatenate([inputs.random_coefficients(len(c), w.p, 1, 80 + i)[0] / hs for i, c in enumerate(lay)])
     with L.context_for(w, L.LSMS_MIXED) as batch:
         batch.set_layouts(lay)
+        waves, items = batch.batch_translation()
+        assert waves == 4 and items >= sum((n + 63) // 64 for n in sizes)
         y = batch.apply(x, L.APPLY_MIXED)[0]
         y_again = batch.apply(x, L.APPLY_MIXED)[0]
     off = 0
@@ -150,6 +152,10 @@ def test_autotune_keeps_results(L, tmp_path):
     batch.set_translation_tuning(-1, 1, 3.0)             # overwrite, then restore from the cache
     t2 = batch.autotune(cache=cache)
     assert t2 == t1
+    assert rel(batch.apply(xb, L.APPLY_MIXED)[0], y0) < 1e-5
+    batch.autotune()                                     # timed again: also the one-launch translation
+    waves, items = batch.batch_translation()
+    assert waves in (1, 2, 4, 8) and items > 0
     assert rel(batch.apply(xb, L.APPLY_MIXED)[0], y0) < 1e-5
     batch.close()
 
