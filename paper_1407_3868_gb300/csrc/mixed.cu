@@ -176,12 +176,12 @@ struct H2 {
 constexpr int MT2 = 16;      // target discs per warp in the two-lanes-per-target kernel
 
 // One CTA of the two-lanes-per-target translation: target tile `tile` (64 discs), source split
-// `split`, right-hand side r.
-template <int PT>
+// `split`, right-hand side r (GRID: the block's own indices, as in a plain launch).
+template <int PT, bool GRID>
 __device__ __forceinline__ void h2_tile(const float4* __restrict__ cff, int n, float k_hi, float k_lo,
                                         const float2* __restrict__ xs, float2* __restrict__ part,
                                         int src_per_split, int nrhs, float near_hi, float near_lo, int row0,
-                                        int nrows, int tile, int split, int r) {
+                                        int nrows, int tile_arg, int split_arg, int r_arg) {
   constexpr int p = PT;
   constexpr int P = H2<PT>::P;
   constexpr int VB = H2<PT>::VB;
@@ -190,8 +190,11 @@ __device__ __forceinline__ void h2_tile(const float4* __restrict__ cff, int n, f
   __shared__ float sbs[MCH][P];
   __shared__ float4 sc[MCH];
   extern __shared__ float2 sh[];
+  const int r = GRID ? (int)blockIdx.z : r_arg;
+  const int split = GRID ? (int)blockIdx.y : split_arg;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = lane & 15, hh = lane >> 4;       // hh = output half (contraction) = source (generation)
+  const int tile = GRID ? (int)blockIdx.x : tile_arg;
   const int l = row0 + (tile * MW + warp) * MT2 + t;           // target rows row0 .. row0 + nrows - 1
   const bool lvalid = l < row0 + nrows && l < n;
   const float4 ct = lvalid ? cff[l] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -282,8 +285,7 @@ __global__ void __launch_bounds__(MW * 32, 3)
 k_translate_f32_h2(const float4* __restrict__ cff, int n, float k_hi, float k_lo,
                    const float2* __restrict__ xs, float2* __restrict__ part, int src_per_split,
                    int nrhs, float near_hi, float near_lo, int row0, int nrows) {
-  h2_tile<PT>(cff, n, k_hi, k_lo, xs, part, src_per_split, nrhs, near_hi, near_lo, row0, nrows, blockIdx.x,
-              blockIdx.y, blockIdx.z);
+  h2_tile<PT, true>(cff, n, k_hi, k_lo, xs, part, src_per_split, nrhs, near_hi, near_lo, row0, nrows, 0, 0, 0);
 }
 
 // A batch of independent layouts in one launch: CTA b runs work item items[b] = (layout, tile,
@@ -299,8 +301,8 @@ k_translate_f32_h2_batch(const float4* __restrict__ cff, const float2* __restric
   const int4 it = items[blockIdx.x];
   const longlong4 L = lays[it.x];                 // (disc offset, discs, sources per split, part offset)
   const int n = (int)L.y;
-  h2_tile<PT>(cff + L.x, n, k_hi, k_lo, xs + L.x * H2<PT>::P, part + L.w, (int)L.z, 1, near_hi, near_lo, 0, n,
-              it.y, it.z, 0);
+  h2_tile<PT, false>(cff + L.x, n, k_hi, k_lo, xs + L.x * H2<PT>::P, part + L.w, (int)L.z, 1, near_hi, near_lo,
+                     0, n, it.y, it.z, 0);
 }
 
 // Near pairs (k2 rho < 25, a few per disc): Hankel's expansion does not hold there, so H_0 and H_1
