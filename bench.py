@@ -51,7 +51,7 @@ BF16_PEAK_TFLOPS, HBM_PEAK_GBS, PEAK_SOURCE = _measured_peaks()
 TRAFFIC = {
     # k_translate_f32_h2<14>, 5000 discs: dram__bytes_read.sum 1.307 MB + dram__bytes_write.sum 0.206 MB
     # (profiles/translate_f32_h2_disc5000_p14_ns1024.md)
-    "ed6acb97ac8199a5": 1.512448e6,
+    "4cb0389a9c0c8a30": 1.513216e6,
 }
 KERNEL_SOURCES = ("mixed.cu", "ff_hankel.cuh")       # k_translate_f32_h2 and its Hankel sequences
 
