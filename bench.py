@@ -908,7 +908,7 @@ def run_large(args, dev, flush):
         ach = flop / (ms_ / 1e3) / 1e12
         return {"kernel": kernel, "bound": "alu", "pairs": pairs, "flop_per_launch": flop, "launch_ms": ms_,
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "peak_note": note}
-    out["roofline_near_mixed"] = roof("k_pair_lists_f32 (+ the FP32 copy of the coefficients)", near_ms,
+    out["roofline_near_mixed"] = roof("k_pair_seq_f32 (+ the FP32 copy of the coefficients)", near_ms,
                                       FP32_PEAK_TFLOPS, "derived FP32: 152 SMs x 128 lanes x 2 x 2070 MHz")
     pairs, tr64, far64, near64 = staged(lsms.APPLY_SCALED)
     out["boxes_fp64_stages"] = {"translate_ms": tr64, "far_ms": far64, "near_ms": near64}

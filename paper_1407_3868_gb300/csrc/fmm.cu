@@ -76,6 +76,41 @@ __global__ void k_fmm_shift_table(const double* __restrict__ cx, const double* _
   }
 }
 
+// The mixed near field's pair sequences: row k of seq = h[s + 2p] = H_s(k rho) e^{i s phi}, s =
+// -2p..2p (then one zero), for list entry k (target perm[t], source csrc[k]); built in FP64 (CUDA
+// J0, Y0, J1, Y1, forward recurrence, angular powers) and stored in FP32.  One thread per target.
+__global__ void k_fmm_pair_seq(const double* __restrict__ cx, const double* __restrict__ cy,
+                               const int* __restrict__ perm, const int* __restrict__ cptr,
+                               const int* __restrict__ csrc, int n, int p, double k, float2* __restrict__ seq) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int l = perm[t], RS = 4 * p + 2, c0 = 2 * p;
+  for (int e = cptr[t]; e < cptr[t + 1]; ++e) {
+    const int m = csrc[e];
+    const double dx = cx[l] - cx[m], dy = cy[l] - cy[m];
+    const double rho = hypot(dx, dy), z = k * rho;
+    const double2 e1 = make_double2(dx / rho, dy / rho);
+    float2* h = seq + (size_t)e * RS;
+    double2 hm = make_double2(j0(z), y0(z)), hq = make_double2(j1(z), y1(z)), eq = e1;
+    h[c0] = make_float2((float)hm.x, (float)hm.y);
+    for (int q = 1; q <= 2 * p; ++q) {
+      const double2 v = cmul(hq, eq);
+      const double2 u = cmul(hq, make_double2(eq.x, -eq.y));
+      const double sg = (q & 1) ? -1.0 : 1.0;
+      h[c0 + q] = make_float2((float)v.x, (float)v.y);
+      h[c0 - q] = make_float2((float)(sg * u.x), (float)(sg * u.y));
+      if (q < 2 * p) {
+        const double f = 2.0 * q / z;
+        const double2 hn = make_double2(f * hq.x - hm.x, f * hq.y - hm.y);
+        hm = hq;
+        hq = hn;
+        eq = cmul(eq, e1);
+      }
+    }
+    h[4 * p + 1] = make_float2(0.f, 0.f);
+  }
+}
+
 // Box kernel on the cyclic grid, laid out for a correlation over orders: G[d mod n1][(-s) mod n2] =
 // H_s(k |d| w) e^{i s phi_d} for dmin <= |d| <= nb - 1, |s| <= 2Q (phi_d = 0 for d > 0, pi for
 // d < 0); zero elsewhere.  One thread per offset: H_0, H_1 from the CUDA library, forward
@@ -661,7 +696,7 @@ void fmm_free(lsms_ctx* c) {
   FmmState& f = c->fmm;
   void* ptrs[] = {f.d_perm,  f.d_bstart, f.d_dbox,   f.d_sbox,   f.d_scx,  f.d_scy,   f.d_tab,   f.d_khat,
                   f.d_grid,  f.d_bq,     f.d_acc,    f.d_hd,     f.d_twn,  f.d_tw2,   f.d_cptr,  f.d_csrc,
-                  f.d_crow,  f.ws.ptr,
+                  f.d_cseq,  f.ws.ptr,
                   f.d_tab32, f.d_khat32, f.d_grid32, f.d_bq32,   f.d_acc32, f.d_hd32, f.d_twn32, f.d_tw232};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -714,28 +749,13 @@ int fmm_setup(lsms_ctx* c) {
     scy[t] = c->cy[perm[t]];
   }
   // pair lists of the mixed near field by target in box order: every pair in the same or adjacent
-  // boxes, with its row in the near-pair table (CSR by disc, sorted by source) when it is one
-  std::vector<int> nptr(n + 1, 0), nidx((size_t)std::max(c->near_nnz, 0));
-  if (c->d_near_ptr && c->near_nnz >= 0) {
-    if (cudaMemcpy(nptr.data(), c->d_near_ptr, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
-        (c->near_nnz > 0 && cudaMemcpy(nidx.data(), c->d_near_idx, (size_t)c->near_nnz * sizeof(int),
-                                       cudaMemcpyDeviceToHost) != cudaSuccess))
-      return check_cuda(c, "set_fmm");
-  }
-  std::vector<int> cptr(n + 1, 0), csrc, crow;
+  // boxes (their sequences are built on the device below)
+  std::vector<int> cptr(n + 1, 0), csrc;
   csrc.reserve((size_t)f.near_pairs);
-  crow.reserve((size_t)f.near_pairs);
   for (int t = 0; t < n; ++t) {
     const int l = perm[t], b = dbox[l];
-    const int* nb0 = nidx.data() + nptr[l];
-    const int* nb1 = nidx.data() + nptr[l + 1];
-    for (int j = bstart[std::max(b - 1, 0)]; j < bstart[std::min(b + 2, nb)]; ++j) {
-      const int m = perm[j];
-      if (m == l) continue;
-      const int* it = std::lower_bound(nb0, nb1, m);
-      csrc.push_back(m);
-      crow.push_back(it != nb1 && *it == m ? (int)(it - nidx.data()) : -1);
-    }
+    for (int j = bstart[std::max(b - 1, 0)]; j < bstart[std::min(b + 2, nb)]; ++j)
+      if (perm[j] != l) csrc.push_back(perm[j]);
     cptr[t + 1] = (int)csrc.size();
   }
   // offsets below dmin go box by box (k |d| w < 2Q + 2)
@@ -767,7 +787,8 @@ int fmm_setup(lsms_ctx* c) {
       cudaMalloc((void**)&f.d_scy, n * sizeof(double)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_cptr, (n + 1) * sizeof(int)) != cudaSuccess ||
       cudaMalloc((void**)&f.d_csrc, std::max<size_t>(1, csrc.size()) * sizeof(int)) != cudaSuccess ||
-      cudaMalloc((void**)&f.d_crow, std::max<size_t>(1, crow.size()) * sizeof(int)) != cudaSuccess) {
+      cudaMalloc((void**)&f.d_cseq, std::max<size_t>(1, csrc.size()) * (4 * p + 2) * sizeof(float2)) !=
+          cudaSuccess) {
     cudaGetLastError();
     fmm_free(c);
     return ctx_fail(c, LSMS_ERR_OOM, "set_fmm: cudaMalloc failed for the box tables");
@@ -779,11 +800,10 @@ int fmm_setup(lsms_ctx* c) {
   cudaMemcpy(f.d_scx, scx.data(), n * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(f.d_scy, scy.data(), n * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(f.d_cptr, cptr.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice);
-  if (!csrc.empty()) {
-    cudaMemcpy(f.d_csrc, csrc.data(), csrc.size() * sizeof(int), cudaMemcpyHostToDevice);
-    cudaMemcpy(f.d_crow, crow.data(), crow.size() * sizeof(int), cudaMemcpyHostToDevice);
-  }
+  if (!csrc.empty()) cudaMemcpy(f.d_csrc, csrc.data(), csrc.size() * sizeof(int), cudaMemcpyHostToDevice);
   cudaStream_t st = c->stream;
+  k_fmm_pair_seq<<<(n + 127) / 128, 128, 0, st>>>(c->d_cx, c->d_cy, f.d_perm, f.d_cptr, f.d_csrc, n, p, c->k2,
+                                                  f.d_cseq);
   if (!f.far) {                    // near field only
     cudaStreamSynchronize(st);
     f.ready = true;
@@ -856,7 +876,7 @@ int fmm_translate(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, bool
       box_far<double2>(c, x, a, f.d_tab, f.d_bq, f.d_grid, f.d_acc, f.d_khat, f.d_hd, f.d_twn, f.d_tw2, st);
   }
   if (mixed) {
-    // near field in FP32: an FP32 copy of the coefficients, then the pair-list kernel
+    // near field in FP32: an FP32 copy of the coefficients, then the stored-sequence kernel
     // (near_pairs.cuh) adds the same-box and adjacent-box pairs, in box order, into alpha
     const long long len = (long long)nrhs * n * P;
     int rc;
@@ -864,8 +884,7 @@ int fmm_translate(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, bool
     float2* x32 = (float2*)f.ws.ptr;
     if (timed) cudaEventRecord(f.ev[1], st);
     k_fmm_d2f<<<blocks_for(len, 256), 256, 0, st>>>(xs, x32, len);
-    launch_pair_lists(p, nrhs, st, f.d_perm, 0, n, n, (const float4*)c->d_lp_misc, f.d_cptr, f.d_csrc, f.d_crow,
-                      (const float4*)c->d_near_h, n, c->k2, x32, alpha);
+    launch_pair_seq(p, nrhs, st, f.d_perm, f.d_cptr, f.d_csrc, f.d_cseq, n, x32, alpha);
     if (timed) cudaEventRecord(f.ev[2], st);
     f.timed = timed;
     return LSMS_OK;

@@ -63,8 +63,8 @@ struct FmmState {
   double2* d_twn = nullptr;         // [n1] e^{-2 pi i u / n1}
   double2* d_tw2 = nullptr;         // [n2] e^{-2 pi i u / n2}
   int* d_cptr = nullptr;            // [n + 1] mixed near field: pairs in the same or adjacent box by
-  int* d_csrc = nullptr;            //   target in box order; source disc of each pair and its row in
-  int* d_crow = nullptr;            //   the near-pair table (k rho < 25), or -1 (k rho >= 25)
+  int* d_csrc = nullptr;            //   target in box order, source disc of each pair
+  float2* d_cseq = nullptr;         // [pairs][4p + 2] their Hankel sequences (FP64-built, stored FP32)
   float2* d_tab32 = nullptr;        // FP32 copies of the shift tables, the transformed kernel, the
   float2* d_khat32 = nullptr;       // work array, the box coefficients and expansions, the
   float2* d_grid32 = nullptr;       // direct-offset kernels and the twiddles (mixed-precision far

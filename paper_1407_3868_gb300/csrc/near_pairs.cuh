@@ -190,3 +190,152 @@ inline void launch_pair_lists(int p, int nrhs, cudaStream_t st, const int* perm,
 }
 
 }  // namespace
+
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// The same near field from stored sequences (the box translation's pair lists, whose geometry is
+// fixed for a layout): every list entry k has its sequence h[s + 2p], s = -2p..2p, built once in
+// FP64 and stored in FP32 as row k of `seq` (RS = 4p + 2 float2 per row: 16-byte rows, and
+// 2 RS / 4 = 2p + 1 odd, so the 8 targets' windows fall in distinct banks).  A warp serves 8
+// targets, 4 lanes per target; rounds of PS_PAIRS pairs per target are double-buffered: the rows
+// and source coefficients of the next round are in flight (cp.async groups) while the current
+// round is contracted.  One pair per round keeps a warp's buffers at 5.6 KB (p = 14), so that 16
+// or more warps share an SM.
+// ---------------------------------------------------------------------------------------------
+constexpr int PS_W = 4;          // warps per CTA
+constexpr int PS_PAIRS = 1;      // pairs per target and round
+constexpr int PS_SLOTS = 8 * PS_PAIRS;
+constexpr int PS_GUARD = 8;
+
+template <int PT> struct PsShape {
+  static constexpr int P = 2 * PT + 1;
+  static constexpr int RS = 4 * PT + 2;                    // float2 per stored row
+  static constexpr int BUF = PS_SLOTS * (RS + P);          // one round: the rows and coefficient vectors
+  static constexpr int WORDS = 2 * PS_GUARD + 2 * BUF;     // per warp, float2
+  static constexpr size_t SMEM = (size_t)PS_W * WORDS * sizeof(float2);
+};
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Targets t = 0 .. n-1 in box order (disc perm[t]); list entries k = cptr[t] .. cptr[t + 1] - 1 with
+// source csrc[k] and stored row k.  Adds the sum into alpha[r][perm[t]][.], r = blockIdx.y.
+template <int PT>
+__global__ void __launch_bounds__(PS_W * 32)
+k_pair_seq_f32(const int* __restrict__ perm, const int* __restrict__ cptr, const int* __restrict__ csrc,
+               const float2* __restrict__ seq, int n, const float2* __restrict__ xs, double2* __restrict__ alpha) {
+  constexpr int p = PT, P = PsShape<PT>::P, RS = PsShape<PT>::RS, BUF = PsShape<PT>::BUF;
+  constexpr int VB = Toe4<PT>::VB;
+  extern __shared__ __align__(16) float2 ps_sh[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tt = lane & 7, hb = lane >> 3;
+  float2* base = ps_sh + (size_t)warp * PsShape<PT>::WORDS + PS_GUARD;   // two round buffers
+  const int r = blockIdx.y;
+  const int tbase = (blockIdx.x * PS_W + warp) * 8;
+  const int t = tbase + tt;
+  const bool tvalid = t < n;
+  const int c0 = tvalid ? cptr[t] : 0, c1 = tvalid ? cptr[t + 1] : 0;
+  const int maxlen = __reduce_max_sync(0xffffffffu, c1 - c0);
+  for (int i = lane; i < PsShape<PT>::WORDS; i += 32) base[i - PS_GUARD] = make_float2(0.f, 0.f);
+  __syncwarp();
+  const float2* xr = xs + (size_t)r * n * P;
+  // slot s = lane mod PS_SLOTS of a round: pair (s >> 3) of target s & 7; this lane's view of it
+  const int ts = lane & (PS_SLOTS - 1);
+  const int sc0 = __shfl_sync(0xffffffffu, c0, ts & 7), sc1 = __shfl_sync(0xffffffffu, c1, ts & 7);
+  auto issue = [&](int r0, float2* buf) {
+    const int k = sc0 + r0 + (ts >> 3);
+    const int kk = k < sc1 ? k : -1;
+    const int m = kk >= 0 ? csrc[kk] : -1;
+    float2* hw = buf;
+    float2* bw = buf + PS_SLOTS * RS;
+#pragma unroll 4
+    for (int s = 0; s < PS_SLOTS; ++s) {
+      const int ks = __shfl_sync(0xffffffffu, kk, s);
+      const int ms = __shfl_sync(0xffffffffu, m, s);
+      if (ks >= 0) {
+        if (lane < RS / 2) cp_async16(hw + s * RS + 2 * lane, seq + (size_t)ks * RS + 2 * lane);
+        if (lane < P) cp_async8(bw + s * P + lane, xr + (size_t)ms * P + lane, true);
+      } else {
+        for (int c = lane; c < RS; c += 32) hw[s * RS + c] = make_float2(0.f, 0.f);
+        if (lane < P) bw[s * P + lane] = make_float2(0.f, 0.f);
+      }
+    }
+    cp_async_commit();
+  };
+  float2 AB[VB];
+  float C[VB];
+#pragma unroll
+  for (int i = 0; i < VB; ++i) {
+    AB[i] = make_float2(0.f, 0.f);
+    C[i] = 0.f;
+  }
+  if (maxlen > 0) issue(0, base);
+  for (int r0 = 0, cur = 0; r0 < maxlen; r0 += PS_PAIRS, cur ^= 1) {
+    float2* buf = base + cur * BUF;
+    if (r0 + PS_PAIRS < maxlen) issue(r0 + PS_PAIRS, base + (cur ^ 1) * BUF);
+    else cp_async_commit();                       // an empty group keeps the wait count uniform
+    cp_async_wait_one();                          // this round's copies have landed
+    __syncwarp();
+    const int nq2 = min(PS_PAIRS, maxlen - r0);
+    for (int q2 = 0; q2 < nq2; ++q2) {
+      const int slot = q2 * 8 + tt;
+      toeplitz_contract4<PT>(buf + slot * RS + 2 * p - VB * hb, buf + PS_SLOTS * RS + slot * P, AB, C);
+    }
+    __syncwarp();                                 // the buffer is refilled two rounds later
+  }
+  if (tvalid && maxlen > 0) {
+    double2* o = alpha + ((size_t)r * n + perm[t]) * P;
+#pragma unroll
+    for (int i = 0; i < VB; ++i) {
+      const int nu = VB * hb + i;
+      if (nu < P) {
+        o[nu].x += (double)(AB[i].x - AB[i].y);
+        o[nu].y += (double)(C[i] - AB[i].x - AB[i].y);
+      }
+    }
+  }
+}
+
+template <int PT>
+void launch_pair_seq_pt(dim3 grid, cudaStream_t st, const int* perm, const int* cptr, const int* csrc,
+                        const float2* seq, int n, const float2* xs, double2* alpha) {
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_pair_seq_f32<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PsShape<PT>::SMEM);
+  });
+  k_pair_seq_f32<PT><<<grid, PS_W * 32, PsShape<PT>::SMEM, st>>>(perm, cptr, csrc, seq, n, xs, alpha);
+}
+
+// Host entry (order p 0..15): n targets in box order, nrhs right-hand sides.
+inline void launch_pair_seq(int p, int nrhs, cudaStream_t st, const int* perm, const int* cptr, const int* csrc,
+                            const float2* seq, int n, const float2* xs, double2* alpha) {
+  if (n <= 0 || nrhs <= 0) return;
+  dim3 grid((unsigned)((n + PS_W * 8 - 1) / (PS_W * 8)), (unsigned)nrhs);
+#define LSMS_PS(PT) launch_pair_seq_pt<PT>(grid, st, perm, cptr, csrc, seq, n, xs, alpha)
+  switch (p) {
+    case 0: LSMS_PS(0); break;
+    case 1: LSMS_PS(1); break;
+    case 2: LSMS_PS(2); break;
+    case 3: LSMS_PS(3); break;
+    case 4: LSMS_PS(4); break;
+    case 5: LSMS_PS(5); break;
+    case 6: LSMS_PS(6); break;
+    case 7: LSMS_PS(7); break;
+    case 8: LSMS_PS(8); break;
+    case 9: LSMS_PS(9); break;
+    case 10: LSMS_PS(10); break;
+    case 11: LSMS_PS(11); break;
+    case 12: LSMS_PS(12); break;
+    case 13: LSMS_PS(13); break;
+    case 14: LSMS_PS(14); break;
+    default: LSMS_PS(15); break;
+  }
+#undef LSMS_PS
+}
+
+}  // namespace
