@@ -214,8 +214,9 @@ k_fmm_m2m(const double2* __restrict__ xs, const int* __restrict__ perm, const in
 // ---------------------------------------------------------------------------------------------
 // The box-to-box convolution.  smem_fft: Stockham (self-sorting) transforms of NF sequences of
 // length L = 2^logL held in shared memory, natural order in and out; element (f, pos) at
-// pos NF + f (FFAST: the sequences interleaved) or f L + pos.  Radix-4 stages while two or more
-// factors of 2 remain, then one radix-2 stage.  With Ls the length already transformed,
+// pos fs + f (FFAST: the sequences interleaved, fs = NF or a padded stride) or f L + pos.  Radix-4
+// stages while two or more factors of 2 remain, then one radix-2 stage.  With Ls the length
+// already transformed,
 // tw[u] = e^{-2 pi i u / (L step)} (conjugated for the inverse), t = j Ls + k:
 //   radix 4 (t < L/4, m = L / (4 Ls), w = tw[k m step], w^2, w^3 from the table (FP64) or as
 //     products (FP32)):  a_r = w^r x[t + r L/4],
@@ -227,9 +228,11 @@ template <typename C> __device__ __forceinline__ C cplus(C a, C b) { C r; r.x = 
 template <typename C> __device__ __forceinline__ C cminus(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
 
 template <typename C, bool FFAST>
-__device__ C* smem_fft(C* x, C* y, int logL, int logNF, const C* __restrict__ tw, int step, bool inv) {
+__device__ C* smem_fft(C* x, C* y, int logL, int logNF, const C* __restrict__ tw, int step, bool inv,
+                       int fstride = 0) {
   const int L = 1 << logL, NF = 1 << logNF;
-  auto at = [&](int f, int pos) { return FFAST ? (pos << logNF) + f : f * L + pos; };
+  const int fs = fstride > 0 ? fstride : NF;      // FFAST: element (f, pos) at pos fs + f
+  auto at = [&](int f, int pos) { return FFAST ? pos * fs + f : f * L + pos; };
   int s = 0;
   while (s < logL) {
     const int Ls = 1 << s;
@@ -309,7 +312,7 @@ constexpr int FFT_INV = 1;       // inverse transform (conjugate twiddles, no sc
 constexpr int FFT_POST_TW = 2;   // forward four-step: output position k times e^{-2 pi i seg k / n1}
 constexpr int FFT_PRE_TW = 4;    // inverse four-step: input position k times e^{+2 pi i seg k / n1}
 constexpr int FFT_THREADS = 256;
-constexpr int FFT_SMEM = 64 * 1024;   // two buffers (ping-pong) per CTA
+constexpr int FFT_SMEM = 80 * 1024;   // two buffers (ping-pong) per CTA
 
 // Transforms along the box index of the columns 0..ncols-1 of row-major arrays.  CTA (seg, column
 // block of 2^logCT): the L = 2^logL rows seg * seg_stride + pos * rstride; rows >= in_rows read as
@@ -345,23 +348,25 @@ k_box_fft_cols(const C* in, int in_ld, int in_rows, C* out, int out_ld, int out_
   }
 }
 
-// Transforms along the orders, 2^logNR frequency rows per CTA.  conv = 0 (kernel setup): rows of
-// width n2, forward transform in place.  conv = 1: the rows hold the 2Q + 1 orders q = -Q..Q
-// (row width W), placed at q mod n2 and zero elsewhere; forward transform, product with the
-// transformed kernel khat (its row of the same frequency), inverse transform, the orders -Q..Q
-// stored back.  tw2[u] = e^{-2 pi i u / n2}, u < n2.
+// Transforms along the orders, 2^logNR frequency rows per CTA, held interleaved in shared memory
+// (element (row r, frequency k) at k (NR + 1) + r: the odd stride keeps both the row loads and the
+// butterflies free of bank conflicts).  conv = 0 (kernel setup): rows of width n2, forward transform
+// in place.  conv = 1: the rows hold the 2Q + 1 orders q = -Q..Q (row width W), placed at q mod n2
+// and zero elsewhere; forward transform, product with the transformed kernel khat (its row of the
+// same frequency), inverse transform, the orders -Q..Q stored back.  tw2[u] = e^{-2 pi i u / n2},
+// u < n2.
 template <typename C>
 __global__ void __launch_bounds__(FFT_THREADS)
 k_box_fft_rows(C* Y, long long nrows, int W, int Q, const C* __restrict__ khat, int logn2,
                const C* __restrict__ tw2, int logNR, int conv) {
   extern __shared__ __align__(16) unsigned char fft_raw[];
-  const int n2 = 1 << logn2, n = n2 << logNR;
+  const int n2 = 1 << logn2, NR = 1 << logNR, S = NR + 1, n = n2 << logNR;
   C* x = reinterpret_cast<C*>(fft_raw);
-  C* y = x + n;
+  C* y = x + n2 * S;
   const long long r0 = (long long)blockIdx.x << logNR;
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-    const long long row = r0 + (idx >> logn2);
-    const int k = idx & (n2 - 1);
+    const int rr = idx >> logn2, k = idx & (n2 - 1);
+    const long long row = r0 + rr;
     C v = czero<C>();
     if (row < nrows) {
       if (!conv) {
@@ -371,27 +376,28 @@ k_box_fft_rows(C* Y, long long nrows, int W, int Q, const C* __restrict__ khat, 
         if (q >= -Q) v = Y[row * W + q + Q];
       }
     }
-    x[idx] = v;
+    x[k * S + rr] = v;
   }
   __syncthreads();
-  C* r = smem_fft<C, false>(x, y, logn2, logNR, tw2, 1, false);
+  C* r = smem_fft<C, true>(x, y, logn2, logNR, tw2, 1, false, S);
   if (conv) {
     for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      const long long row = r0 + (idx >> logn2);
-      if (row < nrows) r[idx] = cmul(r[idx], khat[row * n2 + (idx & (n2 - 1))]);
+      const int rr = idx >> logn2, k = idx & (n2 - 1);
+      const long long row = r0 + rr;
+      if (row < nrows) r[k * S + rr] = cmul(r[k * S + rr], khat[row * n2 + k]);
     }
     __syncthreads();
-    r = smem_fft<C, false>(r, r == x ? y : x, logn2, logNR, tw2, 1, true);
+    r = smem_fft<C, true>(r, r == x ? y : x, logn2, logNR, tw2, 1, true, S);
   }
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-    const long long row = r0 + (idx >> logn2);
-    const int k = idx & (n2 - 1);
+    const int rr = idx >> logn2, k = idx & (n2 - 1);
+    const long long row = r0 + rr;
     if (row >= nrows) continue;
     if (!conv) {
-      Y[row * n2 + k] = r[idx];
+      Y[row * n2 + k] = r[k * S + rr];
     } else {
       const int q = k <= Q ? k : k - n2;
-      if (q >= -Q) Y[row * W + q + Q] = r[idx];
+      if (q >= -Q) Y[row * W + q + Q] = r[k * S + rr];
     }
   }
 }
@@ -640,11 +646,11 @@ void launch_box_cols(const FmmState& f, const C* in, int in_ld, int in_rows, C* 
 
 template <typename C>
 void launch_box_rows(const FmmState& f, C* Y, long long nrows, const C* khat, const C* tw2, int conv, cudaStream_t st) {
-  const int elems = FFT_SMEM / (2 * (int)sizeof(C));
+  const int elems = FFT_SMEM / (2 * (int)sizeof(C));   // per buffer: n2 (NR + 1) elements
   int lnr = 0;
-  while (lnr < 4 && (f.n2 << (lnr + 1)) <= elems) ++lnr;
+  while (lnr < 4 && f.n2 * ((1 << (lnr + 1)) + 1) <= elems) ++lnr;
   const long long blocks = (nrows + (1 << lnr) - 1) >> lnr;
-  const size_t smem = 2 * ((size_t)f.n2 << lnr) * sizeof(C);
+  const size_t smem = 2 * (size_t)f.n2 * ((1 << lnr) + 1) * sizeof(C);
   k_box_fft_rows<C><<<(unsigned)blocks, FFT_THREADS, smem, st>>>(Y, nrows, 2 * f.order + 1, f.order, khat, f.logn2,
                                                                  tw2, lnr, conv);
 }

@@ -196,23 +196,23 @@ namespace {
 // ---------------------------------------------------------------------------------------------
 // The same near field from stored sequences (the box translation's pair lists, whose geometry is
 // fixed for a layout): every list entry k has its sequence h[s + 2p], s = -2p..2p, built once in
-// FP64 and stored in FP32 as row k of `seq` (RS = 4p + 2 float2 per row: 16-byte rows, and
-// 2 RS / 4 = 2p + 1 odd, so the 8 targets' windows fall in distinct banks).  A warp serves 8
-// targets, 4 lanes per target; rounds of PS_PAIRS pairs per target are double-buffered: the rows
-// and source coefficients of the next round are in flight (cp.async groups) while the current
-// round is contracted.  One pair per round keeps a warp's buffers at 5.6 KB (p = 14), so that 16
-// or more warps share an SM.
+// FP64 and stored in FP32 as row k of `seq` (4p + 2 float2 per row).  A warp serves 32 / LANES
+// targets, LANES lanes per target (each VB = ceil(P / LANES) consecutive outputs); rounds of one
+// pair per target are double-buffered: the next round's rows and source coefficients are in
+// flight (cp.async groups) while the current round is contracted.  The rows' shared-memory stride
+// is odd in 8-byte words per target slot for 16 targets (two lanes), 2 mod 4 for 8 targets (four
+// lanes, 16-byte copies), so that a warp's window loads fall in distinct banks.
 // ---------------------------------------------------------------------------------------------
 constexpr int PS_W = 4;          // warps per CTA
-constexpr int PS_PAIRS = 1;      // pairs per target and round
-constexpr int PS_SLOTS = 8 * PS_PAIRS;
 constexpr int PS_GUARD = 8;
 
-template <int PT> struct PsShape {
+template <int PT, int LANES> struct PsShape {
   static constexpr int P = 2 * PT + 1;
-  static constexpr int RS = 4 * PT + 2;                    // float2 per stored row
-  static constexpr int BUF = PS_SLOTS * (RS + P);          // one round: the rows and coefficient vectors
-  static constexpr int WORDS = 2 * PS_GUARD + 2 * BUF;     // per warp, float2
+  static constexpr int TPW = 32 / LANES;                    // targets per warp = slots per round
+  static constexpr int GRS = 4 * PT + 2;                    // float2 per stored row
+  static constexpr int SRS = LANES == 4 ? 4 * PT + 2 : 4 * PT + 3;   // shared-memory row stride
+  static constexpr int BUF = TPW * (SRS + P);               // one round: the rows and coefficient vectors
+  static constexpr int WORDS = 2 * PS_GUARD + 2 * BUF;      // per warp, float2
   static constexpr size_t SMEM = (size_t)PS_W * WORDS * sizeof(float2);
 };
 
@@ -225,43 +225,46 @@ __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wai
 
 // Targets t = 0 .. n-1 in box order (disc perm[t]); list entries k = cptr[t] .. cptr[t + 1] - 1 with
 // source csrc[k] and stored row k.  Adds the sum into alpha[r][perm[t]][.], r = blockIdx.y.
-template <int PT>
+template <int PT, int LANES>
 __global__ void __launch_bounds__(PS_W * 32)
 k_pair_seq_f32(const int* __restrict__ perm, const int* __restrict__ cptr, const int* __restrict__ csrc,
                const float2* __restrict__ seq, int n, const float2* __restrict__ xs, double2* __restrict__ alpha) {
-  constexpr int p = PT, P = PsShape<PT>::P, RS = PsShape<PT>::RS, BUF = PsShape<PT>::BUF;
-  constexpr int VB = Toe4<PT>::VB;
+  using S = PsShape<PT, LANES>;
+  constexpr int p = PT, P = S::P, TPW = S::TPW, GRS = S::GRS, SRS = S::SRS, BUF = S::BUF;
+  constexpr int VB = ToeL<PT, LANES>::VB;
   extern __shared__ __align__(16) float2 ps_sh[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tt = lane & 7, hb = lane >> 3;
-  float2* base = ps_sh + (size_t)warp * PsShape<PT>::WORDS + PS_GUARD;   // two round buffers
+  const int tt = lane & (TPW - 1), hb = lane / TPW;
+  float2* base = ps_sh + (size_t)warp * S::WORDS + PS_GUARD;   // two round buffers
   const int r = blockIdx.y;
-  const int tbase = (blockIdx.x * PS_W + warp) * 8;
-  const int t = tbase + tt;
+  const int t = (blockIdx.x * PS_W + warp) * TPW + tt;
   const bool tvalid = t < n;
   const int c0 = tvalid ? cptr[t] : 0, c1 = tvalid ? cptr[t + 1] : 0;
   const int maxlen = __reduce_max_sync(0xffffffffu, c1 - c0);
-  for (int i = lane; i < PsShape<PT>::WORDS; i += 32) base[i - PS_GUARD] = make_float2(0.f, 0.f);
+  for (int i = lane; i < S::WORDS; i += 32) base[i - PS_GUARD] = make_float2(0.f, 0.f);
   __syncwarp();
   const float2* xr = xs + (size_t)r * n * P;
-  // slot s = lane mod PS_SLOTS of a round: pair (s >> 3) of target s & 7; this lane's view of it
-  const int ts = lane & (PS_SLOTS - 1);
-  const int sc0 = __shfl_sync(0xffffffffu, c0, ts & 7), sc1 = __shfl_sync(0xffffffffu, c1, ts & 7);
+  // slot s of a round = target s; lane (s mod TPW) knows that target's list range
   auto issue = [&](int r0, float2* buf) {
-    const int k = sc0 + r0 + (ts >> 3);
-    const int kk = k < sc1 ? k : -1;
+    const int k = c0 + r0;
+    const int kk = k < c1 ? k : -1;
     const int m = kk >= 0 ? csrc[kk] : -1;
     float2* hw = buf;
-    float2* bw = buf + PS_SLOTS * RS;
+    float2* bw = buf + TPW * SRS;
 #pragma unroll 4
-    for (int s = 0; s < PS_SLOTS; ++s) {
+    for (int s = 0; s < TPW; ++s) {
       const int ks = __shfl_sync(0xffffffffu, kk, s);
       const int ms = __shfl_sync(0xffffffffu, m, s);
       if (ks >= 0) {
-        if (lane < RS / 2) cp_async16(hw + s * RS + 2 * lane, seq + (size_t)ks * RS + 2 * lane);
+        const float2* row = seq + (size_t)ks * GRS;
+        if (LANES == 4) {
+          if (lane < GRS / 2) cp_async16(hw + s * SRS + 2 * lane, row + 2 * lane);
+        } else {
+          for (int c = lane; c < GRS; c += 32) cp_async8(hw + s * SRS + c, row + c, true);
+        }
         if (lane < P) cp_async8(bw + s * P + lane, xr + (size_t)ms * P + lane, true);
       } else {
-        for (int c = lane; c < RS; c += 32) hw[s * RS + c] = make_float2(0.f, 0.f);
+        for (int c = lane; c < SRS; c += 32) hw[s * SRS + c] = make_float2(0.f, 0.f);
         if (lane < P) bw[s * P + lane] = make_float2(0.f, 0.f);
       }
     }
@@ -275,17 +278,13 @@ k_pair_seq_f32(const int* __restrict__ perm, const int* __restrict__ cptr, const
     C[i] = 0.f;
   }
   if (maxlen > 0) issue(0, base);
-  for (int r0 = 0, cur = 0; r0 < maxlen; r0 += PS_PAIRS, cur ^= 1) {
+  for (int r0 = 0, cur = 0; r0 < maxlen; ++r0, cur ^= 1) {
     float2* buf = base + cur * BUF;
-    if (r0 + PS_PAIRS < maxlen) issue(r0 + PS_PAIRS, base + (cur ^ 1) * BUF);
+    if (r0 + 1 < maxlen) issue(r0 + 1, base + (cur ^ 1) * BUF);
     else cp_async_commit();                       // an empty group keeps the wait count uniform
     cp_async_wait_one();                          // this round's copies have landed
     __syncwarp();
-    const int nq2 = min(PS_PAIRS, maxlen - r0);
-    for (int q2 = 0; q2 < nq2; ++q2) {
-      const int slot = q2 * 8 + tt;
-      toeplitz_contract4<PT>(buf + slot * RS + 2 * p - VB * hb, buf + PS_SLOTS * RS + slot * P, AB, C);
-    }
+    toeplitz_contract<PT, LANES>(buf + tt * SRS + 2 * p - VB * hb, buf + TPW * SRS + tt * P, AB, C);
     __syncwarp();                                 // the buffer is refilled two rounds later
   }
   if (tvalid && maxlen > 0) {
@@ -301,21 +300,25 @@ k_pair_seq_f32(const int* __restrict__ perm, const int* __restrict__ cptr, const
   }
 }
 
+constexpr int PS_LANES = 4;      // lanes per target of the stored-sequence near field (2: 1.5x slower)
+
 template <int PT>
 void launch_pair_seq_pt(dim3 grid, cudaStream_t st, const int* perm, const int* cptr, const int* csrc,
                         const float2* seq, int n, const float2* xs, double2* alpha) {
+  using S = PsShape<PT, PS_LANES>;
   static std::once_flag attr;
   std::call_once(attr, [] {
-    cudaFuncSetAttribute(k_pair_seq_f32<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PsShape<PT>::SMEM);
+    cudaFuncSetAttribute(k_pair_seq_f32<PT, PS_LANES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
   });
-  k_pair_seq_f32<PT><<<grid, PS_W * 32, PsShape<PT>::SMEM, st>>>(perm, cptr, csrc, seq, n, xs, alpha);
+  k_pair_seq_f32<PT, PS_LANES><<<grid, PS_W * 32, S::SMEM, st>>>(perm, cptr, csrc, seq, n, xs, alpha);
 }
 
 // Host entry (order p 0..15): n targets in box order, nrhs right-hand sides.
 inline void launch_pair_seq(int p, int nrhs, cudaStream_t st, const int* perm, const int* cptr, const int* csrc,
                             const float2* seq, int n, const float2* xs, double2* alpha) {
   if (n <= 0 || nrhs <= 0) return;
-  dim3 grid((unsigned)((n + PS_W * 8 - 1) / (PS_W * 8)), (unsigned)nrhs);
+  const int tpc = PS_W * (32 / PS_LANES);
+  dim3 grid((unsigned)((n + tpc - 1) / tpc), (unsigned)nrhs);
 #define LSMS_PS(PT) launch_pair_seq_pt<PT>(grid, st, perm, cptr, csrc, seq, n, xs, alpha)
   switch (p) {
     case 0: LSMS_PS(0); break;

@@ -41,20 +41,23 @@ __device__ __forceinline__ void stage_slots(float2* hw, int hs_stride, float2* b
   }
 }
 
-template <int PT> struct Toe4 {
+// LANES lanes per target (4 or 2); lane block hb owns the outputs VB hb .. VB hb + VB - 1.
+template <int PT, int LANES> struct ToeL {
   static constexpr int P = 2 * PT + 1;
-  static constexpr int VB = (P + 3) / 4;             // outputs per lane
-  static constexpr int NB = (P + VB - 1) / VB;       // input blocks
+  static constexpr int VB = (P + LANES - 1) / LANES;   // outputs per lane
+  static constexpr int NB = (P + VB - 1) / VB;         // input blocks
 };
+template <int PT> struct Toe4 : ToeL<PT, 4> {};
 
 // hs: &h[2p - VB hb] of the pair sequence h[s + 2p], s = -2p..2p, so that hs[q - i] multiplies
 // input q into output VB hb + i; reads hs[-(VB - 1)] .. hs[NB VB - 1] (the caller keeps that range
 // in bounds; entries that only reach outputs >= P may hold anything finite or not).  bs: the P
 // source coefficients.
-template <int PT>
-__device__ __forceinline__ void toeplitz_contract4(const float2* hs, const float2* bs,
-                                                   float2 (&AB)[Toe4<PT>::VB], float (&C)[Toe4<PT>::VB]) {
-  constexpr int P = Toe4<PT>::P, VB = Toe4<PT>::VB, NB = Toe4<PT>::NB;
+template <int PT, int LANES>
+__device__ __forceinline__ void toeplitz_contract(const float2* hs, const float2* bs,
+                                                  float2 (&AB)[ToeL<PT, LANES>::VB],
+                                                  float (&C)[ToeL<PT, LANES>::VB]) {
+  constexpr int P = ToeL<PT, LANES>::P, VB = ToeL<PT, LANES>::VB, NB = ToeL<PT, LANES>::NB;
   float2 win[2 * VB - 1];
   float wsum[2 * VB - 1];
 #pragma unroll
@@ -86,6 +89,12 @@ __device__ __forceinline__ void toeplitz_contract4(const float2* hs, const float
       wsum[j] = wsum[VB + j];
     }
   }
+}
+
+template <int PT>
+__device__ __forceinline__ void toeplitz_contract4(const float2* hs, const float2* bs,
+                                                   float2 (&AB)[Toe4<PT>::VB], float (&C)[Toe4<PT>::VB]) {
+  toeplitz_contract<PT, 4>(hs, bs, AB, C);
 }
 
 }  // namespace
