@@ -6,10 +6,12 @@
 // [iteration][system][N P], so every Arnoldi step is one multi-right-hand-side application of the
 // operator.  Each system keeps its own Hessenberg matrix, Givens rotations and residual estimate on
 // the device; classical Gram-Schmidt takes a second pass only when the first one cancels much of the
-// new vector.  The host reads the per-system residual estimates two iterations late (pinned ring +
-// events), so the next Arnoldi steps are always queued, and records for each system the iteration at
-// which it met its tolerance; later iterations are discarded by solving its least-squares problem on
-// that many columns only.
+// new vector.  The iteration runs on the device as one graph launch: a conditional while node
+// whose body is one Arnoldi step of all systems followed by the stopping test, which records for
+// each system the iteration at which it met its tolerance (later iterations are discarded by solving
+// its least-squares problem on that many columns only) and ends the loop when none is left.  Where
+// that graph cannot be built, the host launches the captured step once per step and reads the
+// residual estimates two iterations late (pinned ring + events), so the next steps stay queued.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -370,6 +372,40 @@ __global__ void k_gm_snapshot(const GmState* __restrict__ st, int nb, GmState* _
   if (threadIdx.x == 0) *kp = k + 1;
 }
 
+// The stopping test of the graph-resident loop, after the step counter has counted this Arnoldi
+// step (k steps done): a system that met its tolerance, broke down (hn = 0) or saw a non-finite
+// value keeps k as its iteration count; the loop's condition becomes 0 when no system is left, a
+// non-finite value appeared or k reached maxiter.  hist (one system): its residual after each step.
+// One block.
+__global__ void k_gm_decide(const GmState* __restrict__ st, int nb, const double* __restrict__ tol,
+                            int* __restrict__ kdone, double* __restrict__ res, const int* __restrict__ kp,
+                            int maxiter, int* __restrict__ nonfinite, int* __restrict__ guard,
+                            double* __restrict__ hist, int hist_cap, cudaGraphConditionalHandle cond) {
+  __shared__ int active, bad;
+  if (threadIdx.x == 0) {
+    active = 0;
+    bad = 0;
+  }
+  __syncthreads();
+  const int k = *kp;
+  const int runs = *guard + 1;                    // executions of this test: bounds the loop by itself
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    if (kdone[b] >= 0) continue;
+    const GmState sb = st[b];
+    res[b] = sb.res;
+    if (sb.flag) atomicOr(&bad, 1);
+    if (sb.flag || sb.res <= tol[b] || sb.hn == 0.0) kdone[b] = k;
+    else atomicAdd(&active, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (hist && k >= 1 && k <= hist_cap) hist[k - 1] = st[0].res;
+    if (bad) *nonfinite = 1;
+    *guard = runs;
+    cudaGraphSetConditional(cond, (active > 0 && !bad && k < maxiter && runs < maxiter) ? 1u : 0u);
+  }
+}
+
 // Start of system b = blockIdx.x: beta0 = ||r0||, ref = ||rhs|| (nrm[2b], nrm[2b + 1] hold their
 // squares), g = (beta0, 0, ...).
 __global__ void k_gm_start(const double2* __restrict__ nrm, GmState* __restrict__ st,
@@ -563,6 +599,115 @@ void launch_diag_scale(const double2* x, const double* s, double2* y, long long 
   if (total) k_diag_scale<<<grid_for(total, 256), 256, 0, st>>>(x, s, y, total, P);
 }
 
+// The end of a batched GMRES run: systems still iterating keep `done` iterations; solve each
+// system's least-squares problem on its columns and add V y to x.
+template <typename T>
+int gmres_finish(lsms_ctx* c, const GmPtrs& g, const GmSys& s, std::vector<int>& kdone, int done, int maxiter,
+                 int flags, int* iters, double2* x, cudaStream_t stream) {
+  int rc;
+  (void)maxiter;
+  if ((flags & LSMS_APPLY_MIXED) && (rc = mixed_check(c))) return rc;
+  const int nb = s.nb;
+  bool all = true;
+  for (int b = 0; b < nb; ++b) {
+    if (kdone[b] < 0) {
+      kdone[b] = done;
+      all = false;
+    }
+    iters[b] = kdone[b];
+  }
+  cudaMemcpyAsync(g.kk, kdone.data(), nb * sizeof(int), cudaMemcpyHostToDevice, stream);
+  k_gm_backsolve<<<nb, 32, 0, stream>>>(g.kk, g.H, g.hstride, g.ldh, g.g, g.stride, g.y);
+  int kmax = 0;
+  for (int b = 0; b < nb; ++b) kmax = std::max(kmax, kdone[b]);
+  if (kmax > 0) maxpy<T>((const vec2<T>*)g.V, s.slot, kmax, g.kk, g.y, g.stride, x, s, 1.0, stream);
+  cudaStreamSynchronize(stream);
+  if ((rc = check_cuda(c, "gmres update"))) return rc;
+  return all ? LSMS_OK : LSMS_ERR_NOT_CONVERGED;
+}
+
+// The iteration of a batched GMRES run as one graph launch (see gmres_batch_t).  On return
+// *loop_k = the Arnoldi steps done, or -1 when the conditional graph could not be built (nothing
+// ran; the caller falls back to the host loop); kdone, res, hist and *nonfinite as the host loop
+// leaves them.
+template <typename T>
+int gmres_device_loop(lsms_ctx* c, const GmPtrs& g, const GmSys& s, const double* tol, std::vector<int>& kdone,
+                      int maxiter, int flags, double* res, double* hist, int hist_cap, int* n_hist,
+                      cudaStream_t stream, int* loop_k, bool* nonfinite) {
+  *loop_k = -1;
+  const int nb = s.nb;
+  const int hcap = (nb == 1 && hist && n_hist) ? std::max(0, std::min(hist_cap - *n_hist, maxiter)) : 0;
+  const size_t need =
+      (size_t)nb * (sizeof(double) * 2 + sizeof(int)) + 2 * sizeof(int) + (size_t)hcap * sizeof(double) + 64;
+  int rc;
+  if ((rc = ensure(c, c->gm_loop, need))) return rc;
+  double* d_tol = (double*)c->gm_loop.ptr;
+  double* d_res = d_tol + nb;
+  double* d_hist = d_res + nb;
+  int* d_kdone = (int*)(d_hist + hcap);
+  int* d_bad = d_kdone + nb;
+  int* d_guard = d_bad + 1;
+  cudaMemcpyAsync(d_tol, tol, nb * sizeof(double), cudaMemcpyHostToDevice, stream);
+  cudaMemcpyAsync(d_res, res, nb * sizeof(double), cudaMemcpyHostToDevice, stream);
+  cudaMemcpyAsync(d_kdone, kdone.data(), nb * sizeof(int), cudaMemcpyHostToDevice, stream);
+  cudaMemsetAsync(d_bad, 0, 2 * sizeof(int), stream);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool built = false;
+  const int timing = c->timing;
+  c->timing = 0;
+  if (cudaGraphCreate(&graph, 0) == cudaSuccess) {
+    cudaGraphConditionalHandle cond;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cudaGraphNode_t node;
+    if (cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess) {
+      cp.conditional.handle = cond;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp) == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if (cudaStreamBeginCaptureToGraph(stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+            cudaSuccess) {
+          int erc = enqueue_iteration<T>(c, g, s, maxiter, flags, stream);
+          if (erc == LSMS_OK)
+            k_gm_decide<<<1, 256, 0, stream>>>(g.st, nb, d_tol, d_kdone, d_res, g.dk, maxiter, d_bad, d_guard,
+                                                hcap ? d_hist : nullptr, hcap, cond);
+          cudaGraph_t cap = nullptr;
+          const cudaError_t e = cudaStreamEndCapture(stream, &cap);
+          built = erc == LSMS_OK && e == cudaSuccess && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        }
+      }
+    }
+  }
+  c->timing = timing;
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+  c->err.clear();
+  if (!built) {
+    if (exec) cudaGraphExecDestroy(exec);
+    return LSMS_OK;
+  }
+  const cudaError_t le = cudaGraphLaunch(exec, stream);
+  cudaStreamSynchronize(stream);
+  cudaGraphExecDestroy(exec);
+  if (le != cudaSuccess) return check_cuda(c, "gmres loop graph");
+  if ((rc = check_cuda(c, "gmres loop"))) return rc;
+  int k = 0, bad = 0;
+  cudaMemcpy(&k, g.dk, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpy(kdone.data(), d_kdone, nb * sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpy(res, d_res, nb * sizeof(double), cudaMemcpyDeviceToHost);
+  if (hcap > 0) {
+    const int got = std::min(k, hcap);
+    if (got > 0) cudaMemcpy(hist + *n_hist, d_hist, got * sizeof(double), cudaMemcpyDeviceToHost);
+    *n_hist += got;
+  }
+  *nonfinite = bad != 0;
+  *loop_k = k;
+  return check_cuda(c, "gmres loop results");
+}
+
 // Batched GMRES for A x_b = rhs_b over the systems of s (rhs, x: one slot).  x: initial guesses if
 // x_nonzero, solutions on return.  tol[b]: relative tolerance per system.  iters[b], res[b]:
 // iterations used and final residual estimate.  Returns LSMS_OK when every system converged,
@@ -613,11 +758,27 @@ int gmres_batch_t(lsms_ctx* c, const GmSys& s, const double2* rhs, double2* x, b
     else ++active;
   }
   if (nonfinite) return ctx_fail(c, LSMS_ERR_NONFINITE, "non-finite right-hand side");
-  // Capture one Arnoldi step of all systems as a CUDA graph (after one uncaptured application, so
-  // that every workspace the operator needs exists); launch it once per step.
-  cudaGraphExec_t exec = nullptr;
+  // The whole iteration as one graph launch: a conditional while node whose body is one Arnoldi
+  // step of all systems followed by the stopping test on the device (after one uncaptured
+  // application, so that every workspace the operator needs exists).  If the graph cannot be built,
+  // the step is captured alone and launched once per step from the host loop below.
   if (active > 0 && c->use_graphs) {
     if ((rc = apply_device(c, s.apply_nrhs, g.X, g.W, flags, stream))) return rc;
+    int loop_k = -1;
+    if ((rc = gmres_device_loop<T>(c, g, s, tol, kdone, maxiter, flags, res, hist, hist_cap, n_hist, stream,
+                                   &loop_k, &nonfinite)))
+      return rc;
+    if (loop_k >= 0) {
+      if (nonfinite) {
+        if ((flags & LSMS_APPLY_MIXED) && (rc = mixed_check(c))) return rc;
+        return ctx_fail(c, LSMS_ERR_NONFINITE, "non-finite value in GMRES");
+      }
+      return gmres_finish<T>(c, g, s, kdone, loop_k, maxiter, flags, iters, x, stream);
+    }
+  }
+  // Capture one Arnoldi step of all systems as a CUDA graph; launch it once per step.
+  cudaGraphExec_t exec = nullptr;
+  if (active > 0 && c->use_graphs) {
     const int timing = c->timing;
     c->timing = 0;
     cudaGraph_t graph = nullptr;
@@ -665,24 +826,11 @@ int gmres_batch_t(lsms_ctx* c, const GmSys& s, const double2* rhs, double2* x, b
   while (active > 0 && !nonfinite && checked < k) check(checked);   // drain
   if (exec) cudaGraphExecDestroy(exec);
   cudaStreamSynchronize(stream);
-  if ((flags & LSMS_APPLY_MIXED) && (rc = mixed_check(c))) return rc;
-  if (nonfinite) return ctx_fail(c, LSMS_ERR_NONFINITE, "non-finite value in GMRES");
-  bool all = true;
-  for (int b = 0; b < nb; ++b) {
-    if (kdone[b] < 0) {
-      kdone[b] = checked;
-      all = false;
-    }
-    iters[b] = kdone[b];
+  if (nonfinite) {
+    if ((flags & LSMS_APPLY_MIXED) && (rc = mixed_check(c))) return rc;
+    return ctx_fail(c, LSMS_ERR_NONFINITE, "non-finite value in GMRES");
   }
-  cudaMemcpyAsync(g.kk, kdone.data(), nb * sizeof(int), cudaMemcpyHostToDevice, stream);
-  k_gm_backsolve<<<nb, 32, 0, stream>>>(g.kk, g.H, g.hstride, g.ldh, g.g, g.stride, g.y);
-  int kmax = 0;
-  for (int b = 0; b < nb; ++b) kmax = std::max(kmax, kdone[b]);
-  if (kmax > 0) maxpy<T>(V, slot, kmax, g.kk, g.y, g.stride, x, s, 1.0, stream);
-  cudaStreamSynchronize(stream);
-  if ((rc = check_cuda(c, "gmres update"))) return rc;
-  return all ? LSMS_OK : LSMS_ERR_NOT_CONVERGED;
+  return gmres_finish<T>(c, g, s, kdone, checked, maxiter, flags, iters, x, stream);
 }
 
 // Batched GMRES for A x_b = rhs_b over the systems of s: the inner solves of the mixed refinement

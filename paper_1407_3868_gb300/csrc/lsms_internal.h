@@ -153,6 +153,7 @@ struct lsms_ctx {
   void* gm_ring_dev = nullptr;      // its device address
   size_t gm_ring_bytes = 0;
   int use_graphs = 1;               // capture each GMRES step as a CUDA graph
+  DevBuf gm_loop;                   // device state of the graph-resident GMRES loop (gmres.cu)
   bool refine_stagnated = false;    // the last mixed solve stopped refining on stagnation
   double split_mult = 1.0;          // source splits of the FP32 translation (autotuned)
   int f32_shape = 0;                // FP32 translation tile shape (autotuned): 0 = two lanes per target,
