@@ -96,6 +96,30 @@ def test_batched_translation_with_ragged_layouts(L):
         off += len(c)
 
 
+def test_batch_with_an_empty_layout(L):
+    # a layout without discs contributes nothing and leaves the others (and the one-launch mixed
+    # translation of the batch) unchanged
+    w = workload()
+    m = w.medium
+    hs = O.order_scale(w.p, m["k2"], m["radius"])
+    lay = [inputs.layout(30, -9.0, 9.0, 91), np.zeros((0, 2)), inputs.layout(20, -6.0, 6.0, 92)]
+    x = np.concatenate([inputs.random_coefficients(len(c), w.p, 1, 95 + i)[0] / hs if len(c) else
+                        np.zeros((0, 2 * w.p + 1), complex) for i, c in enumerate(lay)])
+    for precision, flags in ((0, 0), (1, L.APPLY_MIXED)):
+        with L.context_for(w, precision) as batch:
+            batch.set_layouts(lay)
+            y = batch.apply(x, flags)[0]
+        assert y.shape == x.shape
+        off = 0
+        for c in lay:
+            if len(c):
+                with L.context_for(w, precision) as ctx:
+                    ctx.set_particles(c)
+                    ys = ctx.apply(x[off:off + len(c)], flags)[0]
+                assert rel(y[off:off + len(c)], ys, hs) < (1e-12 if precision == 0 else 1e-6)
+            off += len(c)
+
+
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-8)])
 def test_batch_solve_equals_single_layout_solves(L, precision, tol):
     w = workload()
