@@ -46,14 +46,16 @@ def _measured_peaks():
 
 
 BF16_PEAK_TFLOPS, HBM_PEAK_GBS, PEAK_SOURCE = _measured_peaks()
-# DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by the SHA-256 of the
-# source files it was built from (reported as null once they change).
+# DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by the kernel's name and
+# the SHA-256 of the source files it was built from (reported as null once they change).
 TRAFFIC = {
-    # k_translate_f32_h2<14>, 5000 discs: dram__bytes_read.sum 1.307 MB + dram__bytes_write.sum 0.206 MB
-    # (profiles/translate_f32_h2_disc5000_p14_ns1024.md)
-    "4cb0389a9c0c8a30": 1.513216e6,
+    # k_translate_f32_sym<14>, 5000 discs: dram__bytes_read.sum 2.467 MB + dram__bytes_write.sum 0.070 MB
+    # (profiles/translate_f32_sym_disc5000_p14_ns1024.md)
+    "k_translate_f32_sym:2194d1ce25763bee": 2.537216e6,
 }
-KERNEL_SOURCES = ("mixed.cu", "ff_hankel.cuh")       # k_translate_f32_h2 and its Hankel sequences
+KERNEL_SOURCES = ("mixed.cu", "ff_hankel.cuh")       # the FP32 translation kernels and their Hankel sequences
+# the FP32 translation kernel of each tile shape (lsms_get_translation_tuning)
+SHAPE_KERNEL = {0: "k_translate_f32_h2", 1: "k_translate_f32", 2: "k_translate_f32_sym"}
 
 
 def translation_flop(n, p, nrhs=1):
@@ -317,6 +319,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clocks = ClockSampler(local_rank) if rank == 0 else None
     ms_mixed, t_tr_mixed, launches = timed(flags_mixed, args.steps)
+    shape = ctx.translation_tuning()[0]
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop() if clocks else None
@@ -353,7 +356,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = flop / (tr_ms / 1e3) / 1e12
     tr64_ms = statistics.mean(t_tr_fp64)
     key = src_hash([os.path.join(ROOT, "paper_1407_3868_gb300", "csrc", f) for f in KERNEL_SOURCES])
-    traffic = TRAFFIC.get(key)
+    traffic = TRAFFIC.get(SHAPE_KERNEL[shape] + ":" + key)
 
     solve = None
     u_ref_fp64 = None
@@ -439,7 +442,7 @@ def run_ours(args, rank, world, local_rank):
                  "translate_ms": tr64_ms,
                  "translate_frac_of_fp64_peak": (flop / (tr64_ms / 1e3) / 1e12) / FP64_PEAK_TFLOPS},
         "speedup_mixed_vs_fp64": value / fp64_rate,
-        "roofline": {"kernel": "k_translate_f32_h2", "bound": "alu", "achieved": achieved,
+        "roofline": {"kernel": SHAPE_KERNEL[shape], "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": traffic, "flop_per_launch": flop, "launch_ms": tr_ms,
                      "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
@@ -962,10 +965,11 @@ def run_translate_only(args):
     for _ in range(args.steps):
         ctx.apply_dev(x, y, flags)
         tr.append(ctx.last_timing()[0])
+    shape = ctx.translation_tuning()[0]
     ctx.close()
     ms = statistics.mean(tr)
     flop = translation_flop(w.n, w.p)
-    return {"workload": w.name, "steps": args.steps, "translate_ms": ms, "flop": flop,
+    return {"workload": w.name, "kernel": SHAPE_KERNEL[shape], "steps": args.steps, "translate_ms": ms, "flop": flop,
             "tflops": flop / (ms / 1e3) / 1e12, "frac_of_fp32_peak": flop / (ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS}
 
 

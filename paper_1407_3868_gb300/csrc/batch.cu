@@ -269,9 +269,9 @@ int batch_eval_field(lsms_ctx* c, int layout, int ntgt, const double* tgt, int w
 // ---------------------------------------------------------------------------------------------
 // autotuning of the FP32 translation's tile shape and source splits
 // ---------------------------------------------------------------------------------------------
-// Times the one-right-hand-side translation of c's layout in both tile shapes (two lanes per target,
-// 64 targets per CTA; four lanes per target, 32 per CTA) under five source-split multipliers and
-// keeps the fastest pair.
+// Times the one-right-hand-side translation of c's layout in its three tile shapes (two lanes per
+// target, 64 targets per CTA; four lanes per target, 32 per CTA; one sequence per unordered pair)
+// under five split multipliers and keeps the fastest pair.
 static int autotune_one(lsms_ctx* c, int* best_shape, double* best_mult) {
   *best_mult = c->split_mult;
   *best_shape = c->f32_shape;
@@ -286,7 +286,7 @@ static int autotune_one(lsms_ctx* c, int* best_shape, double* best_mult) {
   cudaEventCreate(&e1);
   const double cand[] = {0.5, 1.0, 1.5, 2.0, 3.0};
   float best = 1e30f;
-  for (int shape = 0; shape < 2 && !rc; ++shape)
+  for (int shape = 0; shape < 3 && !rc; ++shape)
     for (double m : cand) {
       c->split_mult = m;
       c->f32_shape = shape;
@@ -410,8 +410,8 @@ extern "C" int lsms_get_translation_tuning(const lsms_ctx* c, int layout, int* s
 
 extern "C" int lsms_set_translation_tuning(lsms_ctx* c, int layout, int shape, double split_mult) {
   if (!c) return LSMS_ERR_ARG;
-  if ((shape != 0 && shape != 1) || !std::isfinite(split_mult) || !(split_mult > 0.0) || split_mult > 64.0)
-    return ctx_fail(c, LSMS_ERR_ARG, "set_translation_tuning: shape 0 or 1 and 0 < split_mult <= 64");
+  if (shape < 0 || shape > 2 || !std::isfinite(split_mult) || !(split_mult > 0.0) || split_mult > 64.0)
+    return ctx_fail(c, LSMS_ERR_ARG, "set_translation_tuning: shape 0, 1 or 2 and 0 < split_mult <= 64");
   std::vector<lsms_ctx*> targets;
   if (!is_batch(c)) {
     if (layout > 0) return ctx_fail(c, LSMS_ERR_ARG, "set_translation_tuning: a single layout is layout 0 (or -1)");

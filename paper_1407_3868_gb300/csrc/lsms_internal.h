@@ -156,8 +156,9 @@ struct lsms_ctx {
   DevBuf gm_loop;                   // device state of the graph-resident GMRES loop (gmres.cu)
   bool refine_stagnated = false;    // the last mixed solve stopped refining on stagnation
   double split_mult = 1.0;          // source splits of the FP32 translation (autotuned)
-  int f32_shape = 0;                // FP32 translation tile shape (autotuned): 0 = two lanes per target,
-                                    // 16 targets per warp; 1 = four lanes per target, 8 per warp
+  int f32_shape = 2;                // FP32 translation tile shape (autotuned): 0 = two lanes per target,
+                                    // 16 targets per warp; 1 = four lanes per target, 8 per warp;
+                                    // 2 = one sequence per unordered pair (both directions)
   int tc_min_rhs = 48;              // mixed translations of >= this many right-hand sides (p >= 6)
                                     // run on the tensor cores; 0 = never
   int tc_flush = 32;                // source discs summed per FP32 tensor-memory accumulation

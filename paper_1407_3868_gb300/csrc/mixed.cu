@@ -305,6 +305,203 @@ k_translate_f32_h2_batch(const float4* __restrict__ cff, const float2* __restric
                      0, n, it.y, it.z, 0);
 }
 
+// One pair sequence for both directions of a pair.  Turning phi by pi gives the reversed pair's
+// sequence, h_s(m <- l) = (-1)^s h_s(l <- m), so out_nu(m) = (-1)^nu sum_n h_{n-nu}(l <- m)
+// ((-1)^n x_n(l)): the sequence generated for l <- m, read with the same window as for the forward
+// direction, also contracts l's sign-flipped coefficients into m's outputs, whose signs are
+// flipped when they are written.  A CTA of two warps takes blocks (g1, g2), g1 <= g2, of 16-disc
+// groups: eight steps per block, step k pairing target t of g1 with sources t + k and t + k + 8
+// (mod 16) of g2, so that every disc of either group sits in two of the step's 32 pairs.  The
+// warps take turns generating a step's 32 sequences into shared memory; then warp 0 contracts them
+// into the targets' outputs and warp 1 into the sources' outputs, each with the two-lanes-per-disc
+// register window of k_translate_f32_h2 (lane (hh, t): VB orders of disc t) and the same code
+// (the role only picks the slot and the coefficient row).  Diagonal blocks (g1 = g2) already hold
+// both directions of their pairs and are contracted by warp 0 alone.  Blocks form double rows h
+// (g1 = h, g2 = h .. G - 1; then g1 = G - 1 - h, g2 = G - 1 - h .. G - 1: G + 1 blocks), and a CTA
+// takes a run of `blocks_per_cta` blocks of one double row.  Outputs go into an FP32 accumulator
+// (zeroed beforehand) by vector atomic adds: warp 0's when the target group changes, warp 1's after
+// every block.
+template <int PT>
+struct Sym {
+  static constexpr int P = 2 * PT + 1;
+  static constexpr int VB = PT + 1;
+  static constexpr int HS = 4 * PT + 3;                // slot stride, as in H2
+  // float2 words: guard, 32 slots, warp 0's coefficients (source group), warp 1's (target group,
+  // signs (-1)^nu), both groups' (re + im) sums as floats, the source group's centres (float4)
+  static constexpr int WORDS = GUARD + 32 * HS + 3 * 16 * P + 32;   // + the source group's centres
+  static constexpr size_t SMEM = (size_t)WORDS * sizeof(float2);
+};
+
+// out_nu += sum_n hs[n - i] b_n for the lane's VB outputs nu (window and Gauss products as in
+// h2_tile); hs points at the sequence value h_{-nu_0} of the lane's first output nu_0.
+template <int PT>
+__device__ __forceinline__ void window_contract(const float2* __restrict__ hs, const float2* __restrict__ bq,
+                                                const float* __restrict__ bsq, float2 (&AB)[PT + 1],
+                                                float (&C)[PT + 1]) {
+  constexpr int VB = PT + 1;
+  float2 win[VB];
+  float ws[VB];
+#pragma unroll
+  for (int i = 0; i < VB - 1; ++i) {
+    win[i] = hs[-1 - i];
+    ws[i] = win[i].x + win[i].y;
+  }
+  auto order = [&](int nn) {
+#pragma unroll
+    for (int i = VB - 1; i > 0; --i) {
+      win[i] = win[i - 1];
+      ws[i] = ws[i - 1];
+    }
+    win[0] = hs[nn];
+    ws[0] = win[0].x + win[0].y;
+    const float2 b = bq[nn];
+    const float bsum = bsq[nn];
+#pragma unroll
+    for (int i = 0; i < VB; ++i) {
+      AB[i] = __ffma2_rn(win[i], b, AB[i]);
+      C[i] = __fmaf_rn(ws[i], bsum, C[i]);
+    }
+  };
+#pragma unroll
+  for (int u = 0; u < VB; ++u) order(u);
+#pragma unroll
+  for (int u = 0; u < VB - 1; ++u) order(VB + u);
+}
+
+// Adds the lane's VB outputs of disc d (orders VB hh ..) into acc, times (-1)^nu when `flip`, and
+// clears the accumulators.
+template <int PT>
+__device__ __forceinline__ void flush_outputs(float2* __restrict__ acc, int d, int n, int hh, bool flip,
+                                              float2 (&AB)[PT + 1], float (&C)[PT + 1]) {
+  constexpr int P = 2 * PT + 1, VB = PT + 1;
+  if (d < n) {
+#pragma unroll
+    for (int i = 0; i < VB; ++i) {
+      const int nu = VB * hh + i;
+      if (nu < P) {
+        const float sg = (flip && (nu & 1)) ? -1.0f : 1.0f;
+        atomicAdd(acc + (size_t)d * P + nu,
+                  make_float2(sg * (AB[i].x - AB[i].y), sg * (C[i] - AB[i].x - AB[i].y)));
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < VB; ++i) {
+    AB[i] = make_float2(0.f, 0.f);
+    C[i] = 0.f;
+  }
+}
+
+// Stages the coefficients of group g (16 discs, zero past n) and their (re + im) sums, times
+// (-1)^nu when `flip`.
+template <int PT>
+__device__ __forceinline__ void stage_group(const float2* __restrict__ xr, int g, int n, bool flip, int lane,
+                                            float2* __restrict__ dst, float* __restrict__ dsum) {
+  constexpr int P = 2 * PT + 1;
+  const int d0 = 16 * g;
+  for (int i = lane; i < 16 * P; i += 32) {
+    const int s = i / P, q = i - s * P;
+    float2 v = d0 + s < n ? xr[(size_t)d0 * P + i] : make_float2(0.f, 0.f);
+    if (flip && (q & 1)) v = make_float2(-v.x, -v.y);
+    dst[i] = v;
+    dsum[i] = v.x + v.y;
+  }
+}
+
+template <int PT>
+__global__ void __launch_bounds__(64, 6)
+k_translate_f32_sym(const float4* __restrict__ cff, int n, float k_hi, float k_lo,
+                    const float2* __restrict__ xs, float2* __restrict__ acc, int blocks_per_cta,
+                    float near_hi, float near_lo) {
+  constexpr int p = PT;
+  constexpr int P = Sym<PT>::P;
+  constexpr int VB = Sym<PT>::VB;
+  constexpr int HS = Sym<PT>::HS;
+  extern __shared__ float2 sh[];
+  const int role = threadIdx.x >> 5, lane = threadIdx.x & 31;   // role 0: forward, 1: reverse
+  const int t = lane & 15, hh = lane >> 4;
+  for (int i = threadIdx.x; i < Sym<PT>::WORDS; i += blockDim.x) sh[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  float2* slots = sh + GUARD;
+  float2* sbF = slots + 32 * HS;
+  float2* sbR = sbF + 16 * P;
+  float* sFs = (float*)(sbR + 16 * P);
+  float* sRs = sFs + 16 * P;
+  float4* sc = (float4*)(sRs + 16 * P);
+  const float2* coef = role ? sbR : sbF;
+  const float* csum = role ? sRs : sFs;
+  const int G = (n + 15) >> 4;
+  const int per_row = (G + blocks_per_cta) / blocks_per_cta;       // ceil((G + 1) / blocks_per_cta)
+  const int h = blockIdx.x / per_row;                              // the grid holds H per_row CTAs
+  const int b0 = (blockIdx.x - h * per_row) * blocks_per_cta;
+  const int b1 = min(G + 1, b0 + blocks_per_cta);
+  const int r = blockIdx.y;
+  const float2* xr = xs + (size_t)r * n * P;
+  float2* ar = acc + (size_t)r * n * P;
+  const ffl kf = {k_hi, k_lo};
+  const ffl nr = {near_hi, near_lo};
+  float2 AB[VB];
+  float C[VB];
+#pragma unroll
+  for (int i = 0; i < VB; ++i) {
+    AB[i] = make_float2(0.f, 0.f);
+    C[i] = 0.f;
+  }
+  int g1cur = -1;
+  float4 ct = make_float4(0.f, 0.f, 0.f, 0.f);
+  // Control flow is the same for both warps (it depends on the block index and the loop counters
+  // only), so every __syncthreads below is reached by all 64 threads.
+  for (int b = b0; b < b1; ++b) {
+    int g1, g2;
+    if (b < G - h) {
+      g1 = h;
+      g2 = h + b;
+    } else {
+      g1 = G - 1 - h;
+      if (g1 == h) break;                             // the middle row of an odd G stands alone
+      g2 = g1 + (b - (G - h));
+    }
+    if (g1 != g1cur) {
+      if (g1cur >= 0 && role == 0) flush_outputs<PT>(ar, 16 * g1cur + t, n, hh, false, AB, C);
+      g1cur = g1;
+      if (role == 1) stage_group<PT>(xr, g1, n, true, lane, sbR, sRs);
+      ct = 16 * g1 + t < n ? cff[16 * g1 + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (role == 0) {
+      stage_group<PT>(xr, g2, n, false, lane, sbF, sFs);
+      if (lane < 16) sc[lane] = 16 * g2 + lane < n ? cff[16 * g2 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+      __syncwarp();
+    }
+    const bool diag = g1 == g2;
+    for (int k = 0; k < 8; ++k) {
+      if (role == (k & 1)) {                          // the warps take turns generating
+        const int s = (t + k + 8 * hh) & 15;
+        const int a = 16 * g1 + t, m = 16 * g2 + s;
+        float2* hq = slots + lane * HS;
+        if (a < n && m < n && a != m) {
+          hankel_sequence_f32<PT>(ct, sc[s], kf, nr, hq);
+        } else {
+          for (int q = 0; q <= 4 * p; ++q) hq[q] = make_float2(0.f, 0.f);
+        }
+      }
+      __syncthreads();
+      if (role == 0 || !diag) {
+#pragma unroll 1
+        for (int q2 = 0; q2 < 2; ++q2) {
+          // warp 0: target t, source u = t + k + 8 q2 (slot q2 16 + t); warp 1: source t, target
+          // u = t - k - 8 q2 (slot q2 16 + u, generated for u <- t)
+          const int u = role ? ((t - k - 8 * q2) & 15) : ((t + k + 8 * q2) & 15);
+          const int sl = q2 * 16 + (role ? u : t);
+          window_contract<PT>(slots + sl * HS + 2 * p - VB * hh, coef + u * P, csum + u * P, AB, C);
+        }
+      }
+      __syncthreads();
+    }
+    if (role == 1 && !diag) flush_outputs<PT>(ar, 16 * g2 + t, n, hh, true, AB, C);
+  }
+  if (role == 0 && g1cur >= 0) flush_outputs<PT>(ar, 16 * g1cur + t, n, hh, false, AB, C);
+}
+
 // Near pairs (k2 rho < 25, a few per disc): Hankel's expansion does not hold there, so H_0 and H_1
 // of every near pair are computed once per layout in FP64 (CUDA J0, Y0, J1, Y1) and stored in FP32
 // (float4: H_0, H_1); the near-pair kernels generate the other orders by the FP32 forward recurrence
@@ -492,6 +689,46 @@ void launch_translate_kernel(dim3 grid, cudaStream_t st, const float4* cff, int 
 #undef LSMS_TB
 }
 
+
+// The symmetric translation (one sequence per unordered pair) of all n discs into acc (zeroed by the
+// caller), runs of blocks sized so that the CTAs cover the GPU about 28 mult times (6 CTAs of two
+// warps per SM).
+template <int PT>
+void launch_sym(cudaStream_t st, const float4* cff, int n, float kh, float kl, const float2* xs, float2* acc,
+                int nrhs, float nh, float nl, double mult) {
+  const int G = (n + 15) / 16, H = (G + 1) / 2;
+  const double blocks = (double)H * (G + 1);
+  const double ctas = std::max(1.0, mult * 152 * 6 * 28 / std::max(1, nrhs));
+  const int L = std::max(1, std::min(G + 1, (int)std::ceil(blocks / ctas)));
+  dim3 grid((unsigned)(H * ((G + L) / L)), nrhs);
+  k_translate_f32_sym<PT><<<grid, 64, Sym<PT>::SMEM, st>>>(cff, n, kh, kl, xs, acc, L, nh, nl);
+}
+
+void launch_translate_sym(cudaStream_t st, const float4* cff, int n, int p, float kh, float kl,
+                          const float2* xs, float2* acc, int nrhs, float nh, float nl, double mult) {
+  if (n <= 0 || nrhs <= 0) return;
+#define LSMS_SY(PT) launch_sym<PT>(st, cff, n, kh, kl, xs, acc, nrhs, nh, nl, mult)
+  switch (p) {
+    case 0: LSMS_SY(0); break;
+    case 1: LSMS_SY(1); break;
+    case 2: LSMS_SY(2); break;
+    case 3: LSMS_SY(3); break;
+    case 4: LSMS_SY(4); break;
+    case 5: LSMS_SY(5); break;
+    case 6: LSMS_SY(6); break;
+    case 7: LSMS_SY(7); break;
+    case 8: LSMS_SY(8); break;
+    case 9: LSMS_SY(9); break;
+    case 10: LSMS_SY(10); break;
+    case 11: LSMS_SY(11); break;
+    case 12: LSMS_SY(12); break;
+    case 13: LSMS_SY(13); break;
+    case 14: LSMS_SY(14); break;
+    default: LSMS_SY(15); break;
+  }
+#undef LSMS_SY
+}
+
 }  // namespace
 
 // CSR list of near pairs (k2 rho < 25) by target, from a cell grid, and their H_0, H_1 (FP64-built).
@@ -597,8 +834,9 @@ int translate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cu
   long long g = (len + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
   const bool tc = c->tc_min_rhs > 0 && nrhs >= c->tc_min_rhs && p >= 6 && p <= LSMS_MAX_P;
+  const bool sym = !tc && c->f32_shape == 2 && !translate_uses_block(nrhs, p);
   int splits = 1, sps = n;
-  if (!tc) {
+  if (!tc && !sym) {
     splits = translate_splits(n, nrhs, p, c->split_mult, c->f32_shape);
     sps = (n + splits - 1) / splits;
     sps = ((sps + MCH - 1) / MCH) * MCH;
@@ -610,6 +848,13 @@ int translate_mixed(lsms_ctx* c, int nrhs, const double2* xs, double2* alpha, cu
   k_to_float<<<(int)g, 256, 0, st>>>(xs, xs32, len);
   if (tc) {
     if ((rc = translate_mixed_tc(c, nrhs, xs, alpha, st))) return rc;
+  } else if (sym) {
+    float2* acc = (float2*)((unsigned char*)c->ws_lp.ptr + b32);
+    const float kh = (float)c->k2, kl = (float)(c->k2 - (double)kh);
+    const float nh = (float)c->near_r2, nl = (float)(c->near_r2 - (double)nh);
+    cudaMemsetAsync(acc, 0, (size_t)len * sizeof(float2), st);
+    launch_translate_sym(st, (const float4*)c->d_lp_misc, n, p, kh, kl, xs32, acc, nrhs, nh, nl, c->split_mult);
+    k_reduce_parts<<<(int)g, 256, 0, st>>>(acc, 1, len, alpha);
   } else {
     float2* part = (float2*)((unsigned char*)c->ws_lp.ptr + b32);
     const float kh = (float)c->k2, kl = (float)(c->k2 - (double)kh);

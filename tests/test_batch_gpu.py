@@ -151,14 +151,14 @@ def test_autotune_keeps_results(L, tmp_path):
     x = inputs.random_coefficients(w.n, w.p, 1, 3)
     a0 = ctx.translate(x, precision=L.LSMS_MIXED)
     (shape, mult), = ctx.autotune()
-    assert shape in (0, 1) and mult > 0 and ctx.translation_tuning() == (shape, mult)
+    assert shape in (0, 1, 2) and mult > 0 and ctx.translation_tuning() == (shape, mult)
     a1 = ctx.translate(x, precision=L.LSMS_MIXED)
     assert rel(a1, a0) < 1e-5
-    for s in (0, 1):
+    for s in (0, 1, 2):
         ctx.set_translation_tuning(-1, s, 1.0)
         assert rel(ctx.translate(x, precision=L.LSMS_MIXED), a0) < 1e-5, s
     with pytest.raises(L.LsmsError) as e:
-        ctx.set_translation_tuning(-1, 2, 1.0)
+        ctx.set_translation_tuning(-1, 3, 1.0)
     assert e.value.code == -1
     ctx.close()
     # a batch: one tuning per size bucket, stored in a JSON cache and applied again from it
@@ -169,7 +169,7 @@ def test_autotune_keeps_results(L, tmp_path):
     xb = np.concatenate([inputs.random_coefficients(len(c), 8, 1, 60 + i)[0] for i, c in enumerate(lay)])
     y0 = batch.apply(xb, L.APPLY_MIXED)[0]
     t1 = batch.autotune(cache=cache)
-    assert len(t1) == len(lay) and all(s in (0, 1) and m > 0 for s, m in t1)
+    assert len(t1) == len(lay) and all(s in (0, 1, 2) and m > 0 for s, m in t1)
     import json
     table = json.load(open(cache))
     assert all(k.startswith("p8_ns192_b") for k in table) and len(table) >= 2
