@@ -49,9 +49,9 @@ BF16_PEAK_TFLOPS, HBM_PEAK_GBS, PEAK_SOURCE = _measured_peaks()
 # DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by the kernel's name and
 # the SHA-256 of the source files it was built from (reported as null once they change).
 TRAFFIC = {
-    # k_translate_f32_sym<14>, 5000 discs: dram__bytes_read.sum 2.467 MB + dram__bytes_write.sum 0.070 MB
+    # k_translate_f32_sym<14>, 5000 discs: dram__bytes_read.sum 2.467 MB + dram__bytes_write.sum 0.068 MB
     # (profiles/translate_f32_sym_disc5000_p14_ns1024.md)
-    "k_translate_f32_sym:2194d1ce25763bee": 2.537216e6,
+    "k_translate_f32_sym:ab0d5d3b92ae1b35": 2.5344e6,
 }
 KERNEL_SOURCES = ("mixed.cu", "ff_hankel.cuh")       # the FP32 translation kernels and their Hankel sequences
 # the FP32 translation kernel of each tile shape (lsms_get_translation_tuning)
@@ -655,6 +655,7 @@ def run_batched(args, dev, flush):
     sw = {"workload": ws.name, "layouts": len(lay), "discs": ntot, "p": ws.p, "contour_nodes": ws.n_nodes,
           "autotuned": {"layouts_two_lane_tiles": sum(1 for sh, _ in tuning if sh == 0),
                         "layouts_four_lane_tiles": sum(1 for sh, _ in tuning if sh == 1),
+                        "layouts_unordered_pair_tiles": sum(1 for sh, _ in tuning if sh == 2),
                         "split_mults": sorted({m for _, m in tuning}),
                         "batched_translation": {"waves": waves, "work_items": items}},
           "mixed": {"ms_per_sweep_apply": ms_m, "layout_applies_per_s": len(lay) * 1e3 / ms_m,

@@ -248,25 +248,28 @@ int lsms_num_layouts(const lsms_ctx* ctx);
 
 /* lsms_autotune — time the one-right-hand-side FP32 translation on the current layout (or on the
  *   largest layout of every power-of-two size bucket of a batch, applied to the whole bucket) in its
- *   three tile shapes (0: two lanes per target disc, 64 targets per CTA; 1: four lanes per target, 32
- *   per CTA, twice the CTAs for small layouts; 2: one Hankel sequence per unordered disc pair,
- *   contracted into both discs' outputs, h_s(m <- l) = (-1)^s h_s(l <- m) (Sec. 3.2 Lemma 3.1), FP32
- *   atomic sums) under five split multipliers (0.5 .. 3: source splits of shapes 0 and 1, the
- *   length of shape 2's block runs), and keep the fastest pair; *split_mult (may be NULL) receives the (last bucket's) factor.  For a
- *   batch it then times the one-launch translation of all layouts (used by the batched mixed
- *   application) with its work items covering the GPU 1, 2, 4 or 8 times and keeps the fastest.
+ *   three tile shapes (0: two lanes per target disc, 64 targets per CTA; 1: four lanes per target,
+ *   32 per CTA, twice the CTAs for small layouts; 2: one Hankel sequence per unordered disc pair,
+ *   contracted into both discs' outputs, h_s(m <- l) = (-1)^s h_s(l <- m) (Sec. 3.2 Lemma 3.1),
+ *   FP32 atomic sums; the default) under five split multipliers (0.5 .. 3: the source splits of
+ *   shapes 0 and 1, the length of shape 2's block runs), and keep the fastest pair; *split_mult
+ *   (may be NULL) receives the (last bucket's) factor.  For a batch it then times the one-launch
+ *   translation of all layouts (used by the batched mixed application) in its two kernels (one
+ *   sequence per unordered pair, the default; two lanes per target) with the work items covering
+ *   the GPU 1, 2, 4 or 8 times, and keeps the fastest.
  *   No counterpart in the paper: a tuning step of this implementation.
  * lsms_get_translation_tuning / lsms_set_translation_tuning — the (shape, split multiplier) of
  *   layout `layout` (0 or -1 for a single layout; for a batch its layout index, -1 in the setter:
  *   every layout), e.g. to store the tuning and apply it again without timing.  shape 0, 1 or 2,
- *   0 < split_mult <= 64.  A layout batch's one-launch translation uses shape 0 whatever the
- *   setting.  Errors: LSMS_ERR_ARG. */
+ *   0 < split_mult <= 64.  A layout batch's one-launch translation keeps its own kernel choice
+ *   (lsms_autotune).  Errors: LSMS_ERR_ARG. */
 int lsms_autotune(lsms_ctx* ctx, double* split_mult);
 int lsms_get_translation_tuning(const lsms_ctx* ctx, int layout, int* shape, double* split_mult);
 int lsms_set_translation_tuning(lsms_ctx* ctx, int layout, int shape, double split_mult);
 /* lsms_get_batch_translation — for a layout batch, the one-launch translation of all layouts: how
- *   many times its work items (layout, tile of 64 target discs, source split) cover the GPU (4 until
- *   lsms_autotune picks) and their number; (0, 0) for a single layout or when the batch has none.
+ *   many times its work items (layout, CTA of two warps over runs of 16 x 16 disc blocks; or layout,
+ *   tile of 64 target discs, source split) cover the GPU (4 until lsms_autotune picks) and their
+ *   number; (0, 0) for a single layout or when the batch has none.
  *   NULL outputs are skipped.  Errors: LSMS_ERR_ARG (NULL ctx). */
 int lsms_get_batch_translation(const lsms_ctx* ctx, int* waves, int* work_items);
 

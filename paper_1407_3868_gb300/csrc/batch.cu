@@ -356,8 +356,10 @@ extern "C" int lsms_autotune(lsms_ctx* c, double* split_mult) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int best_w = c->bt_waves;
-    for (int w : {1, 2, 4, 8}) {
+    int best_w = c->bt_waves, best_s = c->bt_shape;
+    for (int trial = 0; trial < 8 && !rc; ++trial) {
+      const int sh = trial < 4 ? 2 : 0, w = 1 << (trial & 3);
+      c->bt_shape = sh;
       c->bt_waves = w;
       if ((rc = batch_translation_items(c))) break;
       const double2* xs = (const double2*)c->ws_xs.ptr;
@@ -373,11 +375,13 @@ extern "C" int lsms_autotune(lsms_ctx* c, double* split_mult) {
       if (ms < best) {
         best = ms;
         best_w = w;
+        best_s = sh;
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->bt_waves = best_w;
+    c->bt_shape = best_s;
     const int rc2 = batch_translation_items(c);
     if (rc) return rc;
     if (rc2) return rc2;

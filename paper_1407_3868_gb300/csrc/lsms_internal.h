@@ -177,8 +177,11 @@ struct lsms_ctx {
   std::vector<cudaEvent_t> kid_ev;  // join events (one per layout) and a fork event at the end
   // the mixed all-pairs translation of every layout in one launch (mixed.cu, translate_mixed_batch)
   bool bt_ready = false;
-  int bt_ncta = 0;                  // work items (layout, target tile, source split), largest first
+  int bt_ncta = 0;                  // work items, largest layout first: (layout, target tile, source
+                                    // split) of shape 0; (layout, CTA, blocks per CTA) of shape 2
   int bt_waves = 4;                 // the items cover the GPU about this many times (autotuned)
+  int bt_shape = 2;                 // 0: two lanes per target (k_translate_f32_h2_batch); 2: one
+                                    // sequence per unordered pair (k_translate_f32_sym_batch); autotuned
   void* d_bt_items = nullptr;       // int4 [bt_ncta]
   void* d_bt_lays = nullptr;        // longlong4 [layouts]: disc offset, discs, sources per split, part offset
   void* d_bt_cff = nullptr;         // float4 [total discs]: every layout's float-float centres

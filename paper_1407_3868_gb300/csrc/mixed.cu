@@ -328,7 +328,7 @@ struct Sym {
   static constexpr int HS = 4 * PT + 3;                // slot stride, as in H2
   // float2 words: guard, 32 slots, warp 0's coefficients (source group), warp 1's (target group,
   // signs (-1)^nu), both groups' (re + im) sums as floats, the source group's centres (float4)
-  static constexpr int WORDS = GUARD + 32 * HS + 3 * 16 * P + 32;   // + the source group's centres
+  static constexpr int WORDS = GUARD + 32 * HS + 3 * 16 * P + 32;
   static constexpr size_t SMEM = (size_t)WORDS * sizeof(float2);
 };
 
@@ -408,11 +408,13 @@ __device__ __forceinline__ void stage_group(const float2* __restrict__ xr, int g
   }
 }
 
-template <int PT>
-__global__ void __launch_bounds__(64, 6)
-k_translate_f32_sym(const float4* __restrict__ cff, int n, float k_hi, float k_lo,
-                    const float2* __restrict__ xs, float2* __restrict__ acc, int blocks_per_cta,
-                    float near_hi, float near_lo) {
+// One CTA of the symmetric translation: CTA `cta` of the layout's H per_row, right-hand side r
+// (GRID: the block's own indices, as in a plain launch).
+template <int PT, bool GRID>
+__device__ __forceinline__ void sym_cta(const float4* __restrict__ cff, int n, float k_hi, float k_lo,
+                                        const float2* __restrict__ xs, float2* __restrict__ acc,
+                                        int blocks_per_cta, float near_hi, float near_lo, int cta_arg,
+                                        int r_arg) {
   constexpr int p = PT;
   constexpr int P = Sym<PT>::P;
   constexpr int VB = Sym<PT>::VB;
@@ -432,10 +434,11 @@ k_translate_f32_sym(const float4* __restrict__ cff, int n, float k_hi, float k_l
   const float* csum = role ? sRs : sFs;
   const int G = (n + 15) >> 4;
   const int per_row = (G + blocks_per_cta) / blocks_per_cta;       // ceil((G + 1) / blocks_per_cta)
-  const int h = blockIdx.x / per_row;                              // the grid holds H per_row CTAs
-  const int b0 = (blockIdx.x - h * per_row) * blocks_per_cta;
+  const int cta = GRID ? (int)blockIdx.x : cta_arg;                // cta < H per_row
+  const int h = cta / per_row;
+  const int b0 = (cta - h * per_row) * blocks_per_cta;
   const int b1 = min(G + 1, b0 + blocks_per_cta);
-  const int r = blockIdx.y;
+  const int r = GRID ? (int)blockIdx.y : r_arg;
   const float2* xr = xs + (size_t)r * n * P;
   float2* ar = acc + (size_t)r * n * P;
   const ffl kf = {k_hi, k_lo};
@@ -502,6 +505,29 @@ k_translate_f32_sym(const float4* __restrict__ cff, int n, float k_hi, float k_l
   if (role == 0 && g1cur >= 0) flush_outputs<PT>(ar, 16 * g1cur + t, n, hh, false, AB, C);
 }
 
+template <int PT>
+__global__ void __launch_bounds__(64, 6)
+k_translate_f32_sym(const float4* __restrict__ cff, int n, float k_hi, float k_lo,
+                    const float2* __restrict__ xs, float2* __restrict__ acc, int blocks_per_cta,
+                    float near_hi, float near_lo) {
+  sym_cta<PT, true>(cff, n, k_hi, k_lo, xs, acc, blocks_per_cta, near_hi, near_lo, 0, 0);
+}
+
+// A batch of independent layouts in one launch: CTA b runs work item items[b] = (layout, CTA of
+// that layout, blocks per CTA) of the layout table (disc offset, disc count); items are ordered by
+// their layout's size, largest first.  Centres, coefficients and accumulators are concatenated.
+template <int PT>
+__global__ void __launch_bounds__(64, 6)
+k_translate_f32_sym_batch(const float4* __restrict__ cff, const float2* __restrict__ xs,
+                          float2* __restrict__ acc, const int4* __restrict__ items,
+                          const longlong4* __restrict__ lays, float k_hi, float k_lo, float near_hi,
+                          float near_lo) {
+  const int4 it = items[blockIdx.x];
+  const longlong4 L = lays[it.x];
+  sym_cta<PT, false>(cff + L.x, (int)L.y, k_hi, k_lo, xs + L.x * Sym<PT>::P, acc + L.x * Sym<PT>::P, it.z,
+                     near_hi, near_lo, it.y, 0);
+}
+
 // Near pairs (k2 rho < 25, a few per disc): Hankel's expansion does not hold there, so H_0 and H_1
 // of every near pair are computed once per layout in FP64 (CUDA J0, Y0, J1, Y1) and stored in FP32
 // (float4: H_0, H_1); the near-pair kernels generate the other orders by the FP32 forward recurrence
@@ -542,6 +568,12 @@ __global__ void k_reduce_parts_batch(const float2* __restrict__ part, const long
     }
     alpha[i] = make_double2(ax, ay);
   }
+}
+
+template <int PT>
+void launch_sym_batch(int ncta, cudaStream_t st, const float4* cff, const float2* xs, float2* acc, const int4* items,
+                      const longlong4* lays, float kh, float kl, float nh, float nl) {
+  k_translate_f32_sym_batch<PT><<<ncta, 64, Sym<PT>::SMEM, st>>>(cff, xs, acc, items, lays, kh, kl, nh, nl);
 }
 
 template <int PT>
@@ -922,6 +954,29 @@ void batch_translation_free(lsms_ctx* c) {
   c->bt_part = 0;
 }
 
+// Work items of the symmetric kernel: one run length for all layouts (clamped to each layout's
+// double-row length), CTAs of the largest layout first.
+static void sym_batch_items(lsms_ctx* c, std::vector<longlong4>& lays, std::vector<int4>& items) {
+  const int nl = (int)c->kids.size();
+  double blocks = 0.0;
+  for (int l = 0; l < nl; ++l) {
+    const int G = (c->kids[l]->n + 15) / 16;
+    blocks += (double)((G + 1) / 2) * (G + 1);
+    lays[l] = make_longlong4(c->kid_off[l], c->kids[l]->n, 0, 0);
+  }
+  const double target = 152.0 * 6 * 7 * std::max(1, c->bt_waves);
+  const int Lg = std::max(1, (int)std::ceil(blocks / target));
+  std::vector<int> order(nl);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return c->kids[a]->n > c->kids[b]->n; });
+  for (int l : order) {
+    const int G = (c->kids[l]->n + 15) / 16, H = (G + 1) / 2;
+    const int L = std::min(Lg, G + 1);
+    const int ctas = H * ((G + L) / L);
+    for (int k = 0; k < ctas; ++k) items.push_back(make_int4(l, k, L, 0));
+  }
+}
+
 int batch_translation_items(lsms_ctx* c) {
   const int nl = (int)c->kids.size();
   const int P = c->P;
@@ -947,10 +1002,15 @@ int batch_translation_items(lsms_ctx* c) {
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return c->kids[a]->n > c->kids[b]->n; });
   std::vector<int4> items;
-  for (int l : order) {
-    const int tiles = (c->kids[l]->n + tpc - 1) / tpc;
-    for (int t = 0; t < tiles; ++t)
-      for (int sp = 0; sp < splits[l]; ++sp) items.push_back(make_int4(l, t, sp, 0));
+  if (c->bt_shape == 2) {
+    sym_batch_items(c, lays, items);
+    part = c->kid_off.back() * P;                    // one FP32 accumulator
+  } else {
+    for (int l : order) {
+      const int tiles = (c->kids[l]->n + tpc - 1) / tpc;
+      for (int t = 0; t < tiles; ++t)
+        for (int sp = 0; sp < splits[l]; ++sp) items.push_back(make_int4(l, t, sp, 0));
+    }
   }
   if (c->d_bt_items) cudaFree(c->d_bt_items);
   if (c->d_bt_lays) cudaFree(c->d_bt_lays);
@@ -1036,29 +1096,56 @@ int translate_mixed_batch(lsms_ctx* c, const double2* xs, double2* alpha, cudaSt
   const float4* cff = (const float4*)c->d_bt_cff;
   const int4* items = (const int4*)c->d_bt_items;
   const longlong4* lays = (const longlong4*)c->d_bt_lays;
-  if (c->bt_ncta > 0) {
-#define LSMS_HB(PT) launch_h2_batch<PT>(c->bt_ncta, st, cff, xs32, part, items, lays, kh, kl, nh, nl)
-    switch (p) {
-      case 0: LSMS_HB(0); break;
-      case 1: LSMS_HB(1); break;
-      case 2: LSMS_HB(2); break;
-      case 3: LSMS_HB(3); break;
-      case 4: LSMS_HB(4); break;
-      case 5: LSMS_HB(5); break;
-      case 6: LSMS_HB(6); break;
-      case 7: LSMS_HB(7); break;
-      case 8: LSMS_HB(8); break;
-      case 9: LSMS_HB(9); break;
-      case 10: LSMS_HB(10); break;
-      case 11: LSMS_HB(11); break;
-      case 12: LSMS_HB(12); break;
-      case 13: LSMS_HB(13); break;
-      case 14: LSMS_HB(14); break;
-      default: LSMS_HB(15); break;
+  if (c->bt_shape == 2) {
+    cudaMemsetAsync(part, 0, (size_t)len * sizeof(float2), st);
+    if (c->bt_ncta > 0) {
+#define LSMS_SB(PT) launch_sym_batch<PT>(c->bt_ncta, st, cff, xs32, part, items, lays, kh, kl, nh, nl)
+      switch (p) {
+        case 0: LSMS_SB(0); break;
+        case 1: LSMS_SB(1); break;
+        case 2: LSMS_SB(2); break;
+        case 3: LSMS_SB(3); break;
+        case 4: LSMS_SB(4); break;
+        case 5: LSMS_SB(5); break;
+        case 6: LSMS_SB(6); break;
+        case 7: LSMS_SB(7); break;
+        case 8: LSMS_SB(8); break;
+        case 9: LSMS_SB(9); break;
+        case 10: LSMS_SB(10); break;
+        case 11: LSMS_SB(11); break;
+        case 12: LSMS_SB(12); break;
+        case 13: LSMS_SB(13); break;
+        case 14: LSMS_SB(14); break;
+        default: LSMS_SB(15); break;
+      }
+#undef LSMS_SB
     }
+    k_reduce_parts<<<(int)g, 256, 0, st>>>(part, 1, len, alpha);
+  } else {
+    if (c->bt_ncta > 0) {
+#define LSMS_HB(PT) launch_h2_batch<PT>(c->bt_ncta, st, cff, xs32, part, items, lays, kh, kl, nh, nl)
+      switch (p) {
+        case 0: LSMS_HB(0); break;
+        case 1: LSMS_HB(1); break;
+        case 2: LSMS_HB(2); break;
+        case 3: LSMS_HB(3); break;
+        case 4: LSMS_HB(4); break;
+        case 5: LSMS_HB(5); break;
+        case 6: LSMS_HB(6); break;
+        case 7: LSMS_HB(7); break;
+        case 8: LSMS_HB(8); break;
+        case 9: LSMS_HB(9); break;
+        case 10: LSMS_HB(10); break;
+        case 11: LSMS_HB(11); break;
+        case 12: LSMS_HB(12); break;
+        case 13: LSMS_HB(13); break;
+        case 14: LSMS_HB(14); break;
+        default: LSMS_HB(15); break;
+      }
 #undef LSMS_HB
+    }
+    k_reduce_parts_batch<<<(int)g, 256, 0, st>>>(part, lays, (int)c->kids.size(), len, P, alpha);
   }
-  k_reduce_parts_batch<<<(int)g, 256, 0, st>>>(part, lays, (int)c->kids.size(), len, P, alpha);
   launch_pair_lists(p, 1, st, nullptr, 0, (int)total, (int)total, cff, c->d_bt_nptr, c->d_bt_nidx, nullptr,
                     (const float4*)c->d_bt_ntab, (int)total, c->k2, xs32, alpha);
   return check_cuda(c, "translate_mixed_batch");
