@@ -7,6 +7,7 @@
 //   aggregate / disaggregate (Sec. 5.3 Thm 5.2; Sec. 5.2.1 Lemma 5.1): complex GEMMs against the
 //     precomputed plane-wave tables, then per-node order-factor dots.
 //   per-node reflection (Sec. 2 Eq. "sommerfeldsys"): closed-form 2x2 response per node.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -106,6 +107,133 @@ k_translate_f64(const double* __restrict__ cx, const double* __restrict__ cy, in
   }
   if (lvalid && lane < P)
     alpha[((size_t)r * nrows + (l - row0)) * P + lane] = make_double2(A - B, C - A - B);
+}
+
+// One sequence per unordered pair.  Turning phi by pi gives h_s(m <- l) = (-1)^s h_s(l <- m), so
+// alpha^m_nu = (-1)^nu sum_n h^{lm}_{n - nu} ((-1)^n xs^l_n): the sequence generated for l <- m,
+// read with the same window, also contracts l's sign-flipped coefficients into m's outputs.  A CTA
+// of TW warps owns a block of TW target discs and a run of CH-disc source chunks; warp w (target
+// l = TW b + w) generates the sequences of its pairs with the chunk's sources m > l (one per
+// lane), contracts them into l's outputs (lanes over nu, as in k_translate_f64) and into every
+// source's outputs, which it adds into alpha with FP64 atomics; l's own outputs are added when
+// the CTA's target block changes.  Blocks form double rows (block h with its chunks, then block
+// B - 1 - h with its chunks: about as many chunks as one full row), cut into runs of
+// `chunks_per_cta` chunks.  alpha must be zero on entry; all n discs are targets.
+__global__ void __launch_bounds__(TW * 32, 1)
+k_translate_f64_sym(const double* __restrict__ cx, const double* __restrict__ cy, int n, int p,
+                    double k, const double2* __restrict__ xs, double2* __restrict__ alpha,
+                    int chunks_per_cta, int per_row) {
+  extern __shared__ double2 smem[];
+  double2* sb = smem;                                   // [CH][32] staged source coefficients
+  double* sbs = (double*)(sb + CH * 32);                // [CH][32] their re + im
+  double2* sh = (double2*)(sbs + CH * 32);              // [TW][CH][HS] pair sequences
+  double* shs = (double*)(sh + TW * CH * HS);           // [TW][CH][HS] their re + im
+  double2* sl = (double2*)(shs + TW * CH * HS);         // [TW][32] (-1)^n xs^l_n of each warp's target
+  double* sls = (double*)(sl + TW * 32);                // [TW][32] their re + im
+  __shared__ double scx[CH], scy[CH];
+  const int P = 2 * p + 1;
+  const int r = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nb = (n + TW - 1) / TW, nc = (n + CH - 1) / CH;
+  const int h = blockIdx.x / per_row;                   // the grid holds ceil(nb / 2) per_row CTAs
+  const int b1 = h, b2 = nb - 1 - h;
+  const int c1 = (TW * b1 + 1) / CH, c2 = (TW * b2 + 1) / CH;   // first chunk with a source > TW b
+  const int len1 = max(0, nc - c1), len2 = b2 != b1 ? max(0, nc - c2) : 0;
+  const int pos0 = (blockIdx.x - h * per_row) * chunks_per_cta;
+  const int pos1 = min(len1 + len2, pos0 + chunks_per_cta);
+  const double2* xr = xs + (size_t)r * n * P;
+  double2* ar = alpha + (size_t)r * n * P;
+  double2* hw = sh + (size_t)warp * CH * HS;
+  double* hsw = shs + (size_t)warp * CH * HS;
+  double2* slw = sl + warp * 32;
+  double* slsw = sls + warp * 32;
+  const double sgn = (lane & 1) ? -1.0 : 1.0;           // (-1)^nu of the lane's output
+  double A = 0.0, B = 0.0, C = 0.0;
+  int bcur = -1, l = 0;
+  bool lvalid = false;
+  double xl = 0.0, yl = 0.0;
+  // the chunk loop is the same for every warp of the CTA (it depends on blockIdx only)
+  for (int pos = pos0; pos < pos1; ++pos) {
+    const int b = pos < len1 ? b1 : b2;
+    const int c = pos < len1 ? c1 + pos : c2 + (pos - len1);
+    if (b != bcur) {
+      if (lvalid && lane < P) {
+        atomicAdd(&ar[(size_t)l * P + lane].x, A - B);
+        atomicAdd(&ar[(size_t)l * P + lane].y, C - A - B);
+      }
+      A = B = C = 0.0;
+      bcur = b;
+      l = TW * b + warp;
+      lvalid = l < n;
+      xl = lvalid ? cx[l] : 0.0;
+      yl = lvalid ? cy[l] : 0.0;
+      __syncwarp();
+      double2 v = lvalid && lane < P ? xr[(size_t)l * P + lane] : make_double2(0.0, 0.0);
+      if (lane & 1) v = make_double2(-v.x, -v.y);
+      slw[lane] = v;
+      slsw[lane] = v.x + v.y;
+      __syncwarp();
+    }
+    const int j0c = c * CH;
+    const int cnt = min(CH, n - j0c);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt * P; i += blockDim.x) {
+      const int s = i / P, q = i - s * P;
+      const double2 v = xr[(size_t)(j0c + s) * P + q];
+      sb[s * 32 + q] = v;
+      sbs[s * 32 + q] = v.x + v.y;
+    }
+    if (threadIdx.x < cnt) {
+      scx[threadIdx.x] = cx[j0c + threadIdx.x];
+      scy[threadIdx.x] = cy[j0c + threadIdx.x];
+    }
+    __syncthreads();
+    if (lane < cnt) {
+      double2* hq = hw + lane * HS;
+      double* hsm = hsw + lane * HS;
+      if (lvalid && j0c + lane > l) {
+        hankel_sequence_f64(xl - scx[lane], yl - scy[lane], k, p, hq, hsm);
+      } else {
+        for (int q = 0; q <= 4 * p; ++q) {
+          hq[q] = make_double2(0.0, 0.0);
+          hsm[q] = 0.0;
+        }
+      }
+    }
+    __syncwarp();
+    if (lvalid && lane < P) {
+      for (int s = 0; s < cnt; ++s) {                   // l <- m
+        const double2* hs = hw + s * HS + 2 * p - lane;   // hs[q] = h_{n - nu}, n = q - p
+        const double* hss = hsw + s * HS + 2 * p - lane;
+        const double2* bs = sb + s * 32;
+        const double* bss = sbs + s * 32;
+        for (int q = 0; q < P; ++q) {
+          const double2 hv = hs[q], bv = bs[q];
+          A = fma(hv.x, bv.x, A);
+          B = fma(hv.y, bv.y, B);
+          C = fma(hss[q], bss[q], C);
+        }
+      }
+      for (int s = max(0, l + 1 - j0c); s < cnt; ++s) {  // m <- l, sources m = j0c + s > l
+        const double2* hs = hw + s * HS + 2 * p - lane;
+        const double* hss = hsw + s * HS + 2 * p - lane;
+        double Ar = 0.0, Br = 0.0, Cr = 0.0;
+        for (int q = 0; q < P; ++q) {
+          const double2 hv = hs[q], bv = slw[q];
+          Ar = fma(hv.x, bv.x, Ar);
+          Br = fma(hv.y, bv.y, Br);
+          Cr = fma(hss[q], slsw[q], Cr);
+        }
+        double2* o = &ar[(size_t)(j0c + s) * P + lane];
+        atomicAdd(&o->x, sgn * (Ar - Br));
+        atomicAdd(&o->y, sgn * (Cr - Ar - Br));
+      }
+    }
+  }
+  if (lvalid && lane < P) {
+    atomicAdd(&ar[(size_t)l * P + lane].x, A - B);
+    atomicAdd(&ar[(size_t)l * P + lane].y, C - A - B);
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -330,6 +458,30 @@ void launch_translate_f64(const double* cx, const double* cy, int n, int p, doub
   std::call_once(attr, [smem] {
     cudaFuncSetAttribute(k_translate_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
+  if (row0 == 0 && nrows == n) {
+    // all rows: one sequence per unordered pair, runs of chunks sized for about 24 waves of one
+    // CTA per SM
+    const size_t smem_sym = smem + (size_t)TW * 32 * (sizeof(double2) + sizeof(double));
+    static std::once_flag attr_sym;
+    std::call_once(attr_sym, [smem_sym] {
+      cudaFuncSetAttribute(k_translate_f64_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sym);
+    });
+    const int nb = (n + TW - 1) / TW, nc = (n + CH - 1) / CH, H = (nb + 1) / 2;
+    long long total = 0;
+    int dmax = 0;
+    for (int h = 0; h < H; ++h) {
+      const int b2 = nb - 1 - h;
+      const int d = std::max(0, nc - (TW * h + 1) / CH) + (b2 != h ? std::max(0, nc - (TW * b2 + 1) / CH) : 0);
+      total += d;
+      dmax = std::max(dmax, d);
+    }
+    const int run = (int)std::max<long long>(1, (total + 152 * 24 - 1) / (152 * 24));
+    const int per_row = std::max(1, (dmax + run - 1) / run);
+    cudaMemsetAsync(alpha, 0, (size_t)nrhs * n * (2 * p + 1) * sizeof(double2), st);
+    dim3 grid(H * per_row, nrhs);
+    k_translate_f64_sym<<<grid, TW * 32, smem_sym, st>>>(cx, cy, n, p, k, xs, alpha, run, per_row);
+    return;
+  }
   dim3 grid((nrows + TW - 1) / TW, nrhs);
   k_translate_f64<<<grid, TW * 32, smem, st>>>(cx, cy, n, p, k, xs, alpha, row0, nrows);
 }
