@@ -458,9 +458,10 @@ void launch_translate_f64(const double* cx, const double* cy, int n, int p, doub
   std::call_once(attr, [smem] {
     cudaFuncSetAttribute(k_translate_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
-  if (row0 == 0 && nrows == n) {
-    // all rows: one sequence per unordered pair, runs of chunks sized for about 24 waves of one
-    // CTA per SM
+  if (row0 == 0 && nrows == n && n > CH) {
+    // all rows of more than one chunk: one sequence per unordered pair, runs of chunks sized for
+    // about 24 waves of one CTA per SM (with a single chunk both kernels launch the same CTAs, and
+    // the one-way kernel's single contraction pass has less latency)
     const size_t smem_sym = smem + (size_t)TW * 32 * (sizeof(double2) + sizeof(double));
     static std::once_flag attr_sym;
     std::call_once(attr_sym, [smem_sym] {
