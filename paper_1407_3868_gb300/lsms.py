@@ -214,12 +214,16 @@ class Context:
         self.layout_counts = counts
 
     def autotune(self, cache=None):
-        """lsms_autotune: the FP32 translation's tile shape and source-split factor per size bucket.
+        """lsms_autotune: the FP32 translation's tile shape (0: two lanes per target disc, 1: four
+        lanes per target, 2: one Hankel sequence per unordered pair) and split factor per size
+        bucket; for a batch, when timed, also the one-launch translation's kernel and coverage
+        (batch_translation()).
 
         cache: path of a JSON file of earlier results, keyed by (p, contour nodes, power-of-two size
-        bucket): when every layout's bucket is there the stored tuning is applied without timing,
-        otherwise the library times the candidates and the file is updated.  Returns the list of
-        (shape, split multiplier) per layout."""
+        bucket): when every layout's bucket is there the stored tuning is applied without timing
+        (the batch's one-launch translation then keeps its defaults), otherwise the library times
+        the candidates and the file is updated.  Returns the list of (shape, split multiplier) per
+        layout."""
         import json
         counts = self.layout_counts if getattr(self, "layout_counts", None) is not None else [self.n]
         keys = [f"p{self.p}_ns{self.ns}_b{int(np.ceil(np.log2(n))) if n > 0 else 0}" for n in counts]
