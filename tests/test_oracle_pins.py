@@ -151,6 +151,24 @@ def test_graf_translation_against_direct_field():
             assert abs(local - direct) <= 1e-10 * abs(direct)
 
 
+def test_reversed_pair_translation_is_the_sign_flipped_one():
+    # the identity the unordered-pair kernels rest on: turning the pair's angle by pi multiplies
+    # H_s(k rho) e^{i s phi} by (-1)^s, so T^{ml}_{nu n} = (-1)^(n - nu) T^{lm}_{nu n}, i.e.
+    # T^{ml} beta = D T^{lm} D beta with D = diag((-1)^k); each direction here is formed on its own
+    # (atan2 of its own difference vector)
+    k = 3.0 * math.pi
+    rng = np.random.default_rng(11)
+    p = 10
+    sign = (-1.0) ** np.arange(-p, p + 1)
+    for _ in range(6):
+        xl, xm = rng.uniform(-3.0, 3.0, 2), rng.uniform(-3.0, 3.0, 2)
+        t_lm = O.translation_matrix(xl, xm, k, p, p)
+        t_ml = O.translation_matrix(xm, xl, k, p, p)
+        assert np.max(np.abs(t_ml - sign[:, None] * t_lm * sign[None, :])) <= 1e-12 * np.max(np.abs(t_lm))
+        beta = rng.standard_normal(2 * p + 1) + 1j * rng.standard_normal(2 * p + 1)
+        assert np.allclose(t_ml @ beta, sign * (t_lm @ (sign * beta)), rtol=1e-12, atol=0.0)
+
+
 def test_translate_equals_pairwise_brute_force():
     rng = np.random.default_rng(2)
     c = inputs.layout(5, -1.5, 1.5, 7)
